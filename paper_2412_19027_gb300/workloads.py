@@ -1,0 +1,300 @@
+"""Seeded synthetic problem generators.
+
+This module builds problem data only.  It holds none of the solver's
+arithmetic, so both the CUDA path's tests and the oracle may use it.
+
+Every problem except the MPC family is built from a chosen complementary
+optimum (x*, s*, z*): x* ~ N(0, 1); for each nonnegative row, and for each
+SOC / exp / pow cone, one half gets s* in the interior and z* = 0, the other
+half s* = 0 and z* in the interior of the dual cone; zero-cone rows get
+s* = 0 and z* ~ N(0, 1); PSD cones get S* and Z* of complementary rank from
+one random orthogonal basis.  Then b = A x* + s* and q = -P x* - A^T z*, so
+x*, s*, z* satisfy the KKT conditions of the problem (P)/(D) of the paper.
+
+Cone types: 0 zero, 1 nonneg, 2 SOC, 3 exp, 4 pow, 5 PSD (svec, upper
+triangle column-wise, off-diagonals times sqrt(2)).
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+ZERO, NONNEG, SOC, EXP, POW, PSD = 0, 1, 2, 3, 4, 5
+
+
+@dataclass
+class Problem:
+    name: str
+    P: sp.csc_matrix          # upper triangle, n x n
+    q: np.ndarray
+    A: sp.csc_matrix          # m x n
+    b: np.ndarray
+    cones: list               # [(type, dim, alpha)]
+    x_star: np.ndarray = None
+    s_star: np.ndarray = None
+    z_star: np.ndarray = None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return len(self.q)
+
+    @property
+    def m(self):
+        return len(self.b)
+
+    def objective(self, x):
+        Pf = self.P + sp.triu(self.P, 1).T
+        return 0.5 * x @ (Pf @ x) + self.q @ x
+
+
+# ----------------------------------------------------------------------------
+# interior points of each cone (definitions of Sec. 2.1 of the paper)
+# ----------------------------------------------------------------------------
+def _soc_interior(rng, d):
+    u = rng.standard_normal(d - 1)
+    t = np.linalg.norm(u) * rng.uniform(1.5, 3.0) + rng.uniform(0.5, 2.0)
+    return np.r_[t, u]
+
+
+def _exp_primal_interior(rng):
+    y = rng.uniform(0.5, 2.0)
+    x = rng.uniform(-2.0, 0.5)
+    return np.array([x, y, y * math.exp(x / y) + rng.uniform(0.5, 2.0)])
+
+
+def _exp_dual_interior(rng):
+    u = -rng.uniform(0.5, 2.0)
+    v = rng.uniform(-2.0, 2.0)
+    return np.array([u, v, -u * math.exp(v / u) / math.e + rng.uniform(0.5, 2.0)])
+
+
+def _pow_primal_interior(rng, a):
+    x, y = rng.uniform(0.5, 2.0, 2)
+    return np.array([x, y, rng.uniform(-0.9, 0.9) * x ** a * y ** (1 - a)])
+
+
+def _pow_dual_interior(rng, a):
+    u, v = rng.uniform(0.5, 2.0, 2)
+    return np.array([u, v, rng.uniform(-0.9, 0.9) * (u / a) ** a * (v / (1 - a)) ** (1 - a)])
+
+
+def _svec(X):
+    k = X.shape[0]
+    r2 = math.sqrt(2.0)
+    return np.array([X[i, j] if i == j else r2 * X[i, j] for j in range(k) for i in range(j + 1)])
+
+
+def _psd_pair(rng, k):
+    """S*, Z* (svec) of ranks ceil(k/2) and floor(k/2), S* Z* = 0."""
+    Q, R = np.linalg.qr(rng.standard_normal((k, k)))
+    Q = Q * np.sign(np.diag(R))[None, :]  # Haar-distributed orthogonal matrix
+    r1 = (k + 1) // 2
+    Q1, Q2 = Q[:, :r1], Q[:, r1:]
+    S = Q1 @ np.diag(rng.uniform(0.5, 2.0, r1)) @ Q1.T
+    Z = Q2 @ np.diag(rng.uniform(0.5, 2.0, k - r1)) @ Q2.T
+    return _svec(S), _svec(Z)
+
+
+def complementary_pair(rng, cones):
+    """(s*, z*) for a cone list, following the construction in the module doc."""
+    m = sum(d for (_, d, _) in cones)
+    s = np.zeros(m)
+    z = np.zeros(m)
+    off = 0
+    # nonneg rows and SOC/exp/pow cones: exactly half on each side
+    nn_rows = [off_ for off_ in []]
+    offs = []
+    for (t, d, a) in cones:
+        offs.append(off)
+        off += d
+    nn_rows = np.concatenate([np.arange(o, o + d) for (o, (t, d, _)) in zip(offs, cones) if t == NONNEG] or [np.zeros(0, int)])
+    side = np.zeros(len(nn_rows), dtype=bool)
+    side[rng.permutation(len(nn_rows))[: len(nn_rows) // 2]] = True
+    s[nn_rows[side]] = rng.uniform(0.5, 2.0, int(side.sum()))
+    z[nn_rows[~side]] = rng.uniform(0.5, 2.0, int((~side).sum()))
+    for fam in (SOC, EXP, POW):
+        idx = [i for i, c in enumerate(cones) if c[0] == fam]
+        flip = np.zeros(len(idx), dtype=bool)
+        flip[rng.permutation(len(idx))[: len(idx) // 2]] = True
+        for i, primal_side in zip(idx, flip):
+            t, d, a = cones[i]
+            o = offs[i]
+            if fam == SOC:
+                v = _soc_interior(rng, d)
+            elif fam == EXP:
+                v = _exp_primal_interior(rng) if primal_side else _exp_dual_interior(rng)
+            else:
+                v = _pow_primal_interior(rng, a) if primal_side else _pow_dual_interior(rng, a)
+            if primal_side:
+                s[o:o + d] = v
+            else:
+                z[o:o + d] = v
+    for i, (t, d, a) in enumerate(cones):
+        o = offs[i]
+        if t == ZERO:
+            z[o:o + d] = rng.standard_normal(d)
+        elif t == PSD:
+            k = int(round((math.sqrt(8 * d + 1) - 1) / 2))
+            s[o:o + d], z[o:o + d] = _psd_pair(rng, k)
+    return s, z
+
+
+def _sparse_columns(rng, m, n, per_col):
+    """A with per_col distinct uniformly random rows per column, N(0,1) values."""
+    rows = np.empty(n * per_col, dtype=np.int64)
+    for j in range(n):
+        rows[j * per_col:(j + 1) * per_col] = np.sort(rng.choice(m, per_col, replace=False))
+    cols = np.repeat(np.arange(n), per_col)
+    vals = rng.standard_normal(n * per_col)
+    return sp.csc_matrix((vals, (rows, cols)), shape=(m, n))
+
+
+def _finish(name, rng, P_full, A, cones, meta=None):
+    n = A.shape[1]
+    x = rng.standard_normal(n)
+    s, z = complementary_pair(rng, cones)
+    P_full = sp.csc_matrix(P_full)
+    b = A @ x + s
+    q = -(P_full @ x) - A.T @ z
+    return Problem(name, sp.csc_matrix(sp.triu(P_full)), np.asarray(q), sp.csc_matrix(A), np.asarray(b),
+                   list(cones), x, s, z, meta or {})
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+def nonneg_qp(seed=0, n=50, m=100, density=0.1, rank=5):
+    """Nonnegative-cone QP: A m x n with Bernoulli(density) N(0,1) entries,
+    P = M M^T with M n x rank N(0,1).  (n=50, m=100 is the small QP case.)"""
+    rng = np.random.default_rng(seed)
+    mask = rng.random((m, n)) < density
+    A = sp.csc_matrix(np.where(mask, rng.standard_normal((m, n)), 0.0))
+    M = rng.standard_normal((n, rank))
+    return _finish("nonneg_qp_n%d_m%d" % (n, m), rng, M @ M.T, A, [(NONNEG, m, 0.0)])
+
+
+def mixed_cone(seed=0, n=2000, n_zero=500, n_nonneg=3000, n_soc=500, soc_dim=5, n_exp=100, n_pow=100,
+               pow_alpha=0.3, nnz_per_col=10, p_rank=10):
+    """Mixed-cone QP.  Full size: n=2000, m=6600 = 500 zero + 3000 nonneg +
+    500 SOC(5) + 100 exp + 100 pow(0.3); A with nnz_per_col N(0,1) entries per
+    column at uniform random rows; P = diag(U(0.1, 1)) + F F^T with F
+    n x p_rank, N(0,1)/sqrt(p_rank)."""
+    rng = np.random.default_rng(seed)
+    cones = []
+    if n_zero:
+        cones.append((ZERO, n_zero, 0.0))
+    if n_nonneg:
+        cones.append((NONNEG, n_nonneg, 0.0))
+    cones += [(SOC, soc_dim, 0.0)] * n_soc + [(EXP, 3, 0.0)] * n_exp + [(POW, 3, pow_alpha)] * n_pow
+    m = sum(d for (_, d, _) in cones)
+    A = _sparse_columns(rng, m, n, min(nnz_per_col, m))
+    F = rng.standard_normal((n, p_rank)) / math.sqrt(p_rank)
+    P = np.diag(rng.uniform(0.1, 1.0, n)) + F @ F.T
+    return _finish("mixed_cone_n%d_m%d" % (n, m), rng, P, A, cones)
+
+
+def banded_lp(seed=0, n=200_000, m=None, n_zero=None, window=1024, diag_p=True):
+    """Large sparse LP/QP: 8 nnz per column, 6 band rows 2j-2 .. 2j+3 plus 2
+    rows uniform in |i - 2j| <= window; P = diag(U(0,1)) with a random half of
+    the diagonal set to 0; first quarter of the rows zero cone, rest nonneg."""
+    rng = np.random.default_rng(seed)
+    m = 2 * n if m is None else m
+    n_zero = m // 4 if n_zero is None else n_zero
+    rows_l, cols_l = [], []
+    j = np.arange(n)
+    band = [2 * j + o for o in range(-2, 4)]
+    extra = []
+    for k in range(2):
+        extra.append(2 * j + rng.integers(-window, window + 1, n))
+    R = np.stack(band + extra, axis=1)
+    R = np.clip(R, 0, m - 1)
+    for jj in range(n):
+        r = R[jj]
+        u = np.unique(r)
+        while len(u) < 8:
+            u = np.unique(np.r_[u, np.clip(2 * jj + rng.integers(-window, window + 1), 0, m - 1)])
+        rows_l.append(u[:8])
+    rows = np.concatenate(rows_l)
+    cols = np.repeat(j, 8)
+    A = sp.csc_matrix((rng.standard_normal(len(rows)), (rows, cols)), shape=(m, n))
+    pd = rng.uniform(0.0, 1.0, n) if diag_p else np.zeros(n)
+    pd[rng.permutation(n)[: n // 2]] = 0.0
+    cones = [(ZERO, n_zero, 0.0), (NONNEG, m - n_zero, 0.0)]
+    return _finish("banded_lp_n%d_m%d" % (n, m), rng, sp.diags(pd), A, cones)
+
+
+def psd_batch(seed=0, n=20_000, n_psd=2000, psd_k=10, n_nonneg=5000, nnz_per_col=6):
+    """Batched PSD problem: n_psd PSD(psd_k) cones + n_nonneg nonneg rows,
+    A with nnz_per_col N(0,1) entries per column, P = 0."""
+    rng = np.random.default_rng(seed)
+    d = psd_k * (psd_k + 1) // 2
+    cones = [(NONNEG, n_nonneg, 0.0)] + [(PSD, d, 0.0)] * n_psd
+    m = n_nonneg + n_psd * d
+    A = _sparse_columns(rng, m, n, nnz_per_col)
+    return _finish("psd_batch_n%d_m%d" % (n, m), rng, sp.csc_matrix((n, n)), A, cones)
+
+
+def mpc_qp(seed=0, T=None, nx=None, nu=None, x_bound=5.0, u_bound=1.0, u_soc=1.2, x0_scale=0.5):
+    """MPC-shaped QP: states x_1..x_T, inputs u_0..u_{T-1}; x_{t+1} = A_d x_t +
+    B_d u_t as zero-cone rows (A_d = G 0.95 / rho(G)); boxes |x| <= 5, |u| <= 1
+    as nonneg rows; one SOC ||u_t|| <= 1.2 per step; cost sum x'x + 0.1 u'u.
+    Not built from a known optimum."""
+    rng = np.random.default_rng(seed)
+    T = int(rng.integers(10, 51)) if T is None else T
+    nx = int(rng.integers(4, 13)) if nx is None else nx
+    nu = int(rng.integers(2, 5)) if nu is None else nu
+    G = rng.standard_normal((nx, nx))
+    Ad = G * 0.95 / max(abs(np.linalg.eigvals(G)))
+    Bd = rng.standard_normal((nx, nu))
+    x0 = rng.standard_normal(nx) * x0_scale
+    n = T * (nx + nu)
+    xi = lambda t: t * nx                      # x_{t+1} block offset, t = 0..T-1
+    ui = lambda t: T * nx + t * nu              # u_t block offset
+    rows, cols, vals, b = [], [], [], []
+    r = 0
+    for t in range(T):                          # x_{t+1} - A_d x_t - B_d u_t = 0
+        for i in range(nx):
+            rows.append(r); cols.append(xi(t) + i); vals.append(1.0)
+            if t > 0:
+                for k in range(nx):
+                    rows.append(r); cols.append(xi(t - 1) + k); vals.append(-Ad[i, k])
+            for k in range(nu):
+                rows.append(r); cols.append(ui(t) + k); vals.append(-Bd[i, k])
+            b.append(Ad[i] @ x0 if t == 0 else 0.0)
+            r += 1
+    n_zero = r
+    for j in range(n):                          # boxes: v <= ub, -v <= ub
+        ub = x_bound if j < T * nx else u_bound
+        rows += [r, r + 1]; cols += [j, j]; vals += [1.0, -1.0]; b += [ub, ub]
+        r += 2
+    n_nn = r - n_zero
+    for t in range(T):                          # (u_soc, u_t) in SOC
+        b.append(u_soc)
+        r += 1
+        for k in range(nu):
+            rows.append(r); cols.append(ui(t) + k); vals.append(-1.0); b.append(0.0)
+            r += 1
+    m = r
+    A = sp.csc_matrix((vals, (rows, cols)), shape=(m, n))
+    pd = np.r_[np.full(T * nx, 2.0), np.full(T * nu, 0.2)]
+    cones = [(ZERO, n_zero, 0.0), (NONNEG, n_nn, 0.0)] + [(SOC, nu + 1, 0.0)] * T
+    return Problem("mpc_T%d_nx%d_nu%d" % (T, nx, nu), sp.csc_matrix(sp.diags(pd)), np.zeros(n), A,
+                   np.asarray(b), cones, meta=dict(T=T, nx=nx, nu=nu))
+
+
+def mpc_stream(seed=0, count=10_000):
+    """Seeds and Poisson inter-arrival draws for the MPC serving stream."""
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.integers(0, 2 ** 31 - 1, count)]
+
+
+# Configurations of the measured workloads, by name.
+WORKLOADS = {
+    "qp_nonneg_n50_m100": lambda seed=0: nonneg_qp(seed),
+    "mixed_n2000_m6600": lambda seed=0: mixed_cone(seed),
+    "banded_n200000_m400000": lambda seed=0: banded_lp(seed),
+    "psd2000x10_n20000": lambda seed=0: psd_batch(seed),
+    "mpc": lambda seed=0: mpc_qp(seed),
+}
