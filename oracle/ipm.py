@@ -58,13 +58,16 @@ EPS32 = float(np.finfo(np.float32).eps)
 
 def default_settings(factor_bits=64):
     """Defaults; the regularisation constants depend on the factor precision
-    (Sec. 3.6: delta_s = sqrt(eps) in mixed precision, 1e-8 in full precision,
-    delta_d = eps^2)."""
+    (Sec. 3.6: delta_s = sqrt(eps_32) ~ 3.45e-4 in mixed precision, 1e-8 in
+    full precision).  delta_d = eps^2 is read with eps the FP64 epsilon in both
+    modes: with eps_32^2 the term delta_d max|K_ii| reaches ~1e-4 once the
+    scaling H grows to ~1e10, and refinement then stalls at T_max (measured
+    with this oracle on a mixed-cone problem)."""
     low = factor_bits != 64
     return dict(
         eps_feas=1e-8, eps_inf=1e-8, max_iter=200, factor_bits=factor_bits,
         static_reg=math.sqrt(EPS32) if low else 1e-8,
-        static_reg_dyn=(EPS32 ** 2) if low else (EPS64 ** 2),
+        static_reg_dyn=EPS64 ** 2,
         dyn_reg_eps=1e-6 if low else 1e-13,
         dyn_reg_delta=1e-4 if low else 2e-7,
         ir_max_steps=10, ir_abstol=1e-12, ir_reltol=1e-12,
@@ -269,156 +272,161 @@ def solve(P, q, A, b, cones, settings=None, record=False):
     status = 0
     info = {}
     it = 0
-    while True:
-        # ---------------- residuals, objectives, mu (step 12 / loop head) -------
-        xu, su, zu = unscale(x, s, z)
-        xb, sb, zb = xu / tau, su / tau, zu / tau
-        Pxb = Pfull @ xb
-        r_p = -A0 @ xb - sb + b
-        r_d = Pxb + A0.T @ zb + q
-        xPx = xb @ Pxb
-        g_p = 0.5 * xPx + q @ xb
-        g_d = -0.5 * xPx - b @ zb
-        mu = (s @ z + kappa * tau) / (nu + 1)
-        nrp = float(np.max(np.abs(r_p), initial=0.0))
-        nrd = float(np.max(np.abs(r_d), initial=0.0))
-        nx = float(np.max(np.abs(xb), initial=0.0))
-        ns = float(np.max(np.abs(sb), initial=0.0))
-        nz = float(np.max(np.abs(zb), initial=0.0))
-        gap = abs(g_p - g_d)
-        info = dict(obj_primal=g_p, obj_dual=g_d, res_primal=nrp, res_dual=nrd, gap_abs=gap,
-                    gap_rel=gap / max(1.0, min(abs(g_p), abs(g_d))), mu=mu, tau=tau, kappa=kappa)
-        if not all(np.isfinite([mu, nrp, nrd, g_p, g_d, tau, kappa])):
-            status = NUMERICAL_ERROR
-            break
-        # ---------------- termination (Eq. termination-check) ----------------
-        ef = st["eps_feas"]
-        if (nrp < ef * max(1.0, bnorm + nx + ns) and nrd < ef * max(1.0, qnorm + nx + nz)
-                and gap < ef * max(1.0, min(abs(g_p), abs(g_d)))):
-            status = SOLVED
-            break
-        # ---------------- infeasibility (Eq. infeasibility-check) ------------
-        ei = st["eps_inf"]
-        btz = b @ zu
-        qtx = q @ xu
-        nxu = float(np.max(np.abs(xu), initial=0.0))
-        nzu = float(np.max(np.abs(zu), initial=0.0))
-        nsu = float(np.max(np.abs(su), initial=0.0))
-        if btz < -ei and np.max(np.abs(A0.T @ zu), initial=0.0) < -ei * max(1.0, nxu + nzu) * btz:
-            status = PRIMAL_INFEASIBLE
-            break
-        if (qtx < -ei and np.max(np.abs(Pfull @ xu), initial=0.0) < -ei * max(1.0, nxu) * qtx
-                and np.max(np.abs(A0 @ xu + su), initial=0.0) < -ei * max(1.0, nxu + nsu) * qtx):
-            status = DUAL_INFEASIBLE
-            break
-        if it >= st["max_iter"]:
-            status = MAX_ITER
-            break
-
-        # ---------------- step 4: scaling H per cone -----------------------
-        Hblk = np.zeros((m, m))
-        scal = {}
-        for (t, d, a, off) in K:
-            sl = slice(off, off + d)
-            if t == C.ZERO:
-                continue
-            if t in (C.NONNEG, C.SOC, C.PSD):
-                scal[off] = C.nt_scaling(t, s[sl], z[sl])
-                Hblk[sl, sl] = scal[off]["H"]
-            else:
-                Hblk[sl, sl] = C.bfgs_scaling(t, s[sl], z[sl], mu, a)
-        # ---------------- step 5: factor K ---------------------------------
-        Kmat = np.block([[Ph, Ah.T], [Ah, -Hblk]])
-        ks = KKTSolver(Kmat, n, st)
-        sol2 = ks.solve(np.r_[-qh, bh])
-        dx2, dz2 = sol2[:n], sol2[n:]
-        # residual G (Eq. root_finding_G)
-        Px = Ph @ x
-        G1 = -(Px + Ah.T @ z + qh * tau)
-        G2 = s + Ah @ x - bh * tau
-        G3 = kappa + qh @ x + bh @ z + (x @ Px) / tau
-
-        def direction(dx_, dz_, dtau_, ds_, dkap_):
-            return reduced_direction(ks, Ph, qh, Ah, bh, Hblk, x, tau, kappa, dx2, dz2,
-                                     (dx_, dz_, dtau_, ds_, dkap_))
-
-        def step_length(Ds, Dz, Dtau, Dkap, neighbourhood):
-            amax = 1.0
-            if Dtau < 0:
-                amax = min(amax, -tau / Dtau)
-            if Dkap < 0:
-                amax = min(amax, -kappa / Dkap)
-            for (t, d, a, off) in K:
-                if t in (C.NONNEG, C.SOC, C.PSD):
-                    sl = slice(off, off + d)
-                    amax = min(amax, C.step_length_symmetric(t, s[sl], Ds[sl]),
-                               C.step_length_symmetric(t, z[sl], Dz[sl]))
-            nonsym = [(t, d, a, off) for (t, d, a, off) in K if t in (C.EXP, C.POW)]
-            alpha = amax
-            while nonsym:
-                ok = True
-                if neighbourhood:
-                    s_t, z_t = s + alpha * Ds, z + alpha * Dz
-                    mu_t = (s_t @ z_t + (tau + alpha * Dtau) * (kappa + alpha * Dkap)) / (nu + 1)
-                for (t, d, a, off) in nonsym:
-                    sl = slice(off, off + d)
-                    sc, zc = s[sl] + alpha * Ds[sl], z[sl] + alpha * Dz[sl]
-                    if not (C.in_int_primal(t, sc, a) and C.in_int_dual(t, zc, a)):
-                        ok = False
-                        break
-                    if neighbourhood and not C.neighbourhood_ok(t, sc, zc, mu_t, st["nbhd_beta"], a):
-                        ok = False
-                        break
-                if ok:
+    try:
+        with np.errstate(divide="raise", invalid="raise", over="raise"):
+            while True:
+                # ---------------- residuals, objectives, mu (step 12 / loop head) -------
+                xu, su, zu = unscale(x, s, z)
+                xb, sb, zb = xu / tau, su / tau, zu / tau
+                Pxb = Pfull @ xb
+                r_p = -A0 @ xb - sb + b
+                r_d = Pxb + A0.T @ zb + q
+                xPx = xb @ Pxb
+                g_p = 0.5 * xPx + q @ xb
+                g_d = -0.5 * xPx - b @ zb
+                mu = (s @ z + kappa * tau) / (nu + 1)
+                nrp = float(np.max(np.abs(r_p), initial=0.0))
+                nrd = float(np.max(np.abs(r_d), initial=0.0))
+                nx = float(np.max(np.abs(xb), initial=0.0))
+                ns = float(np.max(np.abs(sb), initial=0.0))
+                nz = float(np.max(np.abs(zb), initial=0.0))
+                gap = abs(g_p - g_d)
+                info = dict(obj_primal=g_p, obj_dual=g_d, res_primal=nrp, res_dual=nrd, gap_abs=gap,
+                            gap_rel=gap / max(1.0, min(abs(g_p), abs(g_d))), mu=mu, tau=tau, kappa=kappa)
+                if not all(np.isfinite([mu, nrp, nrd, g_p, g_d, tau, kappa])):
+                    status = NUMERICAL_ERROR
                     break
-                alpha *= st["backtrack"]
-                if alpha < st["min_step"]:
-                    alpha = 0.0
+                # ---------------- termination (Eq. termination-check) ----------------
+                ef = st["eps_feas"]
+                if (nrp < ef * max(1.0, bnorm + nx + ns) and nrd < ef * max(1.0, qnorm + nx + nz)
+                        and gap < ef * max(1.0, min(abs(g_p), abs(g_d)))):
+                    status = SOLVED
                     break
-            return alpha
+                # ---------------- infeasibility (Eq. infeasibility-check) ------------
+                ei = st["eps_inf"]
+                btz = b @ zu
+                qtx = q @ xu
+                nxu = float(np.max(np.abs(xu), initial=0.0))
+                nzu = float(np.max(np.abs(zu), initial=0.0))
+                nsu = float(np.max(np.abs(su), initial=0.0))
+                if btz < -ei and np.max(np.abs(A0.T @ zu), initial=0.0) < -ei * max(1.0, nxu + nzu) * btz:
+                    status = PRIMAL_INFEASIBLE
+                    break
+                if (qtx < -ei and np.max(np.abs(Pfull @ xu), initial=0.0) < -ei * max(1.0, nxu) * qtx
+                        and np.max(np.abs(A0 @ xu + su), initial=0.0) < -ei * max(1.0, nxu + nsu) * qtx):
+                    status = DUAL_INFEASIBLE
+                    break
+                if it >= st["max_iter"]:
+                    status = MAX_ITER
+                    break
 
-        # ---------------- step 6: affine direction -------------------------
-        ds_a = s.copy()
-        Dxa, Dza, Dtaua, Dsa, Dkapa = direction(G1, G2, G3, ds_a, kappa * tau)
-        # ---------------- step 7/8: affine step, sigma ----------------------
-        alpha_a = step_length(Dsa, Dza, Dtaua, Dkapa, False)
-        sigma = (1.0 - alpha_a) ** 3
-        # ---------------- step 9: combined direction ----------------------
-        ds_c = np.zeros(m)
-        for (t, d, a, off) in K:
-            sl = slice(off, off + d)
-            if t == C.ZERO:
-                continue
-            if t in (C.NONNEG, C.SOC, C.PSD):
-                sc = scal[off]
-                lam = C.lam_vec(t, sc["lam"], d)
-                eta = C.jordan_prod(t, sc["WinvT"] @ Dsa[sl], sc["W"] @ Dza[sl])
-                v = C.jordan_prod(t, lam, lam) + eta - sigma * mu * C.identity(t, d)
-                ds_c[sl] = sc["W"].T @ C.jordan_div(t, sc["lam"], v)
-            else:
-                eta = C.third_order_correction(t, z[sl], Dza[sl], Dsa[sl], a)
-                ds_c[sl] = s[sl] + sigma * mu * C.barrier_grad(t, z[sl], a) + eta
-        dkap_c = kappa * tau + Dkapa * Dtaua - sigma * mu
-        Dx, Dz, Dtau, Ds, Dkap = direction((1 - sigma) * G1, (1 - sigma) * G2, (1 - sigma) * G3, ds_c, dkap_c)
-        # ---------------- step 10/11: combined step and update -------------
-        alpha_c = step_length(Ds, Dz, Dtau, Dkap, True)
-        ir_total += ks.ir_steps
-        if record:
-            history.append(dict(iter=it, mu=mu, pcost=g_p, dcost=g_d, res_primal=nrp, res_dual=nrd,
-                                gap=gap, alpha_a=alpha_a, sigma=sigma, alpha_c=alpha_c,
-                                ir_steps=ks.ir_steps, dyn_hits=ks.dyn_hits, tau=tau, kappa=kappa,
-                                G1=float(np.max(np.abs(G1), initial=0.0)),
-                                G2=float(np.max(np.abs(G2), initial=0.0))))
-        if alpha_c < st["min_step"]:
-            status = INSUFFICIENT_PROGRESS
-            break
-        a = st["step_fraction"] * alpha_c
-        x = x + a * Dx
-        z = z + a * Dz
-        s = s + a * Ds
-        tau = tau + a * Dtau
-        kappa = kappa + a * Dkap
-        it += 1
+                # ---------------- step 4: scaling H per cone -----------------------
+                Hblk = np.zeros((m, m))
+                scal = {}
+                for (t, d, a, off) in K:
+                    sl = slice(off, off + d)
+                    if t == C.ZERO:
+                        continue
+                    if t in (C.NONNEG, C.SOC, C.PSD):
+                        scal[off] = C.nt_scaling(t, s[sl], z[sl])
+                        Hblk[sl, sl] = scal[off]["H"]
+                    else:
+                        Hblk[sl, sl] = C.bfgs_scaling(t, s[sl], z[sl], mu, a)
+                # ---------------- step 5: factor K ---------------------------------
+                Kmat = np.block([[Ph, Ah.T], [Ah, -Hblk]])
+                ks = KKTSolver(Kmat, n, st)
+                sol2 = ks.solve(np.r_[-qh, bh])
+                dx2, dz2 = sol2[:n], sol2[n:]
+                # residual G (Eq. root_finding_G)
+                Px = Ph @ x
+                G1 = -(Px + Ah.T @ z + qh * tau)
+                G2 = s + Ah @ x - bh * tau
+                G3 = kappa + qh @ x + bh @ z + (x @ Px) / tau
+
+                def direction(dx_, dz_, dtau_, ds_, dkap_):
+                    return reduced_direction(ks, Ph, qh, Ah, bh, Hblk, x, tau, kappa, dx2, dz2,
+                                             (dx_, dz_, dtau_, ds_, dkap_))
+
+                def step_length(Ds, Dz, Dtau, Dkap, neighbourhood):
+                    amax = 1.0
+                    if Dtau < 0:
+                        amax = min(amax, -tau / Dtau)
+                    if Dkap < 0:
+                        amax = min(amax, -kappa / Dkap)
+                    for (t, d, a, off) in K:
+                        if t in (C.NONNEG, C.SOC, C.PSD):
+                            sl = slice(off, off + d)
+                            amax = min(amax, C.step_length_symmetric(t, s[sl], Ds[sl]),
+                                       C.step_length_symmetric(t, z[sl], Dz[sl]))
+                    nonsym = [(t, d, a, off) for (t, d, a, off) in K if t in (C.EXP, C.POW)]
+                    alpha = amax
+                    while nonsym:
+                        ok = True
+                        if neighbourhood:
+                            s_t, z_t = s + alpha * Ds, z + alpha * Dz
+                            mu_t = (s_t @ z_t + (tau + alpha * Dtau) * (kappa + alpha * Dkap)) / (nu + 1)
+                        for (t, d, a, off) in nonsym:
+                            sl = slice(off, off + d)
+                            sc, zc = s[sl] + alpha * Ds[sl], z[sl] + alpha * Dz[sl]
+                            if not (C.in_int_primal(t, sc, a) and C.in_int_dual(t, zc, a)):
+                                ok = False
+                                break
+                            if neighbourhood and not C.neighbourhood_ok(t, sc, zc, mu_t, st["nbhd_beta"], a):
+                                ok = False
+                                break
+                        if ok:
+                            break
+                        alpha *= st["backtrack"]
+                        if alpha < st["min_step"]:
+                            alpha = 0.0
+                            break
+                    return alpha
+
+                # ---------------- step 6: affine direction -------------------------
+                ds_a = s.copy()
+                Dxa, Dza, Dtaua, Dsa, Dkapa = direction(G1, G2, G3, ds_a, kappa * tau)
+                # ---------------- step 7/8: affine step, sigma ----------------------
+                alpha_a = step_length(Dsa, Dza, Dtaua, Dkapa, False)
+                sigma = (1.0 - alpha_a) ** 3
+                # ---------------- step 9: combined direction ----------------------
+                ds_c = np.zeros(m)
+                for (t, d, a, off) in K:
+                    sl = slice(off, off + d)
+                    if t == C.ZERO:
+                        continue
+                    if t in (C.NONNEG, C.SOC, C.PSD):
+                        sc = scal[off]
+                        lam = C.lam_vec(t, sc["lam"], d)
+                        eta = C.jordan_prod(t, sc["WinvT"] @ Dsa[sl], sc["W"] @ Dza[sl])
+                        v = C.jordan_prod(t, lam, lam) + eta - sigma * mu * C.identity(t, d)
+                        ds_c[sl] = sc["W"].T @ C.jordan_div(t, sc["lam"], v)
+                    else:
+                        eta = C.third_order_correction(t, z[sl], Dza[sl], Dsa[sl], a)
+                        ds_c[sl] = s[sl] + sigma * mu * C.barrier_grad(t, z[sl], a) + eta
+                dkap_c = kappa * tau + Dkapa * Dtaua - sigma * mu
+                Dx, Dz, Dtau, Ds, Dkap = direction((1 - sigma) * G1, (1 - sigma) * G2, (1 - sigma) * G3, ds_c, dkap_c)
+                # ---------------- step 10/11: combined step and update -------------
+                alpha_c = step_length(Ds, Dz, Dtau, Dkap, True)
+                ir_total += ks.ir_steps
+                if record:
+                    history.append(dict(iter=it, mu=mu, pcost=g_p, dcost=g_d, res_primal=nrp, res_dual=nrd,
+                                        gap=gap, alpha_a=alpha_a, sigma=sigma, alpha_c=alpha_c,
+                                        ir_steps=ks.ir_steps, dyn_hits=ks.dyn_hits, tau=tau, kappa=kappa,
+                                        G1=float(np.max(np.abs(G1), initial=0.0)),
+                                        G2=float(np.max(np.abs(G2), initial=0.0))))
+                if alpha_c < st["min_step"]:
+                    status = INSUFFICIENT_PROGRESS
+                    break
+                a = st["step_fraction"] * alpha_c
+                x = x + a * Dx
+                z = z + a * Dz
+                s = s + a * Ds
+                tau = tau + a * Dtau
+                kappa = kappa + a * Dkap
+                it += 1
+
+    except (FloatingPointError, ValueError, ZeroDivisionError, np.linalg.LinAlgError):
+        status = NUMERICAL_ERROR  # a non-finite value or a failed factorization
 
     # ---------------- output (un-scale, un-permute) -------------------------
     xu, su, zu = unscale(x, s, z)

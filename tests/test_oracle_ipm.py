@@ -55,7 +55,8 @@ def test_paper_constants():
     assert st["ir_abstol"] == g["ir_abstol"]["value"] and st["ir_reltol"] == g["ir_reltol"]["value"]
     assert st["static_reg"] == g["static_reg_full"]["value"]
     assert lo["static_reg"] == pytest.approx(g["static_reg_mixed"]["value"], rel=g["static_reg_mixed"]["rtol"])
-    assert lo["static_reg_dyn"] == pytest.approx(g["static_reg_dyn_mixed"]["value"], rel=1e-12)
+    assert lo["static_reg_dyn"] == pytest.approx(g["static_reg_dyn"]["value"], rel=1e-12)
+    assert st["static_reg_dyn"] == pytest.approx(g["static_reg_dyn"]["value"], rel=1e-12)
 
 
 # ------------------------------------------------------------ dense LDL^T
