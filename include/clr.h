@@ -1,0 +1,269 @@
+/*
+ * clr.h -- C ABI of the GB300 interior-point conic solver.
+ *
+ * Problem (Eq. P of arXiv:2412.19027, "CuClarabel", Sec. 1):
+ *
+ *     minimize    1/2 x'Px + q'x
+ *     subject to  Ax + s = b,  s in K = K_1 x ... x K_p
+ *
+ * with dual (Eq. D)  maximize -1/2 x'Px - b'z  s.t.  Px + A'z = -q, z in K*.
+ * K is a product of zero, nonnegative, second-order, exponential, power and
+ * positive-semidefinite cones (Sec. 2.1).  The solver runs the homogeneous-
+ * embedding predictor-corrector interior-point method of Algorithm 1 (Sec.
+ * 3.2): setup (equilibration, initialisation, symbolic KKT analysis) on the
+ * host, then every iteration on one GPU.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: int status code, CLR_OK (0) on success, a negative CLR_E_*
+ *    on failure.  No entry point exits, aborts or traps.  The solver's own
+ *    outcome (solved, infeasible, ...) is a separate clr_status in clr_info;
+ *    a solve that ends in MAX_ITER is still a successful call.
+ *  - Ownership: every input array is caller-owned HOST memory, read during
+ *    the call and deep-copied; the library keeps no caller pointer.  Outputs
+ *    go into caller-owned host buffers of the stated length.  Device memory
+ *    is owned by the solver object and freed by clr_free.
+ *  - Threads: a clr_solver may be used by one host thread at a time.
+ *  - Index types: column pointers int64, row indices int32, values double.
+ */
+#ifndef CLR_H
+#define CLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum clr_error {
+  CLR_OK = 0,
+  CLR_E_INVALID = -1,     /* malformed input: NaN/Inf, bad pattern, bad cone list */
+  CLR_E_DIM = -2,         /* dimensions disagree (cone dims vs m, vector lengths) */
+  CLR_E_UNSUPPORTED = -3, /* e.g. PSD cones of different orders or order > 32 */
+  CLR_E_OOM = -4,         /* device or host allocation failed */
+  CLR_E_CUDA = -5,        /* a CUDA call failed; clr_last_cuda_error() has details */
+  CLR_E_TIMEOUT = -6,     /* a bounded device wait ran out */
+  CLR_E_AGAIN = -7,       /* result not ready yet */
+  CLR_E_STATE = -8        /* call out of order (e.g. solution before solve) */
+};
+
+/* Solver outcome (Sec. 2.2 termination and infeasibility tests). */
+enum clr_status {
+  CLR_UNSOLVED = 0,
+  CLR_SOLVED = 1,
+  CLR_PRIMAL_INFEASIBLE = 2,
+  CLR_DUAL_INFEASIBLE = 3,
+  CLR_MAX_ITER = 4,
+  CLR_INSUFFICIENT_PROGRESS = 5,
+  CLR_NUMERICAL_ERROR = 6
+};
+
+/* Cone types (Sec. 2.1).  CLR_PSD_TRI: dim = k(k+1)/2 rows holding the svec
+ * of a k x k symmetric matrix -- upper triangle, column by column, entries
+ * above the diagonal multiplied by sqrt(2).  All PSD cones of one problem
+ * must have the same order k <= 32 (the paper's restriction, Sec. 2.1
+ * footnote and Sec. 3.4).  CLR_EXP and CLR_POW have dim 3; alpha is the power
+ * cone exponent in (0, 1). */
+enum clr_cone_type { CLR_ZERO = 0, CLR_NONNEG = 1, CLR_SOC = 2, CLR_EXP = 3, CLR_POW = 4, CLR_PSD_TRI = 5 };
+
+typedef struct {
+  int32_t type;  /* clr_cone_type */
+  int32_t dim;   /* number of rows of s (and of A, b) the cone covers */
+  double alpha;  /* power-cone exponent; ignored otherwise */
+} clr_cone;
+
+/* Compressed sparse column matrix: colptr[ncols+1], rowind[nnz], val[nnz].
+ * Row indices within a column must be strictly increasing. */
+typedef struct {
+  int64_t nrows, ncols, nnz;
+  const int64_t* colptr;
+  const int32_t* rowind;
+  const double* val;
+} clr_csc;
+
+/* Settings.  clr_default_settings fills the values below; each one is
+ * printed in the paper where noted, otherwise it is this library's reading. */
+typedef struct {
+  double eps_feas;        /* termination tolerance (Eq. termination-check); default 1e-8 */
+  double eps_inf;         /* infeasibility tolerance (Eq. infeasibility-check); 1e-8 */
+  int32_t max_iter;       /* 200 */
+  int32_t factor_bits;    /* LDL^T precision: 64 (FP64) or 32 (FP32) (Sec. 3.6) */
+  double static_reg;      /* delta_s: 1e-8 (FP64), sqrt(eps_32) ~ 3.45e-4 (FP32) (Sec. 3.6) */
+  double static_reg_dyn;  /* delta_d in delta = delta_s + delta_d max|K_ii|: eps_64^2 */
+  double dyn_reg_eps;     /* pivot threshold of dynamic regularisation: 1e-13 (FP64), 1e-6 (FP32) */
+  double dyn_reg_delta;   /* replacement pivot magnitude: 2e-7 (FP64), 1e-4 (FP32) */
+  int32_t ir_max_steps;   /* T_max = 10 (Sec. 3.6) */
+  double ir_abstol;       /* t_abs = 1e-12 (Sec. 3.6) */
+  double ir_reltol;       /* t_rel = 1e-12 (Sec. 3.6) */
+  int32_t equilibrate;    /* 1: modified Ruiz scaling at setup (Alg. 1 step 1) */
+  int32_t ruiz_passes;    /* 10 */
+  double scale_min;       /* 1e-4: clamp of every equilibration factor */
+  double scale_max;       /* 1e4 */
+  double step_fraction;   /* 0.99 (Alg. 1 step 11) */
+  double backtrack;       /* 0.8 (Sec. 2.2, exp/pow step length) */
+  double nbhd_beta;       /* 1e-6 (Sec. 2.2, neighbourhood N(beta)) */
+  double min_step;        /* 1e-10: smaller combined steps end the solve */
+  int32_t use_graph;      /* 1: replay each iteration as a captured CUDA graph */
+  int32_t verbose;        /* 0 */
+} clr_settings;
+
+typedef struct {
+  int32_t status;          /* clr_status */
+  int32_t iterations;
+  int32_t ir_steps_total;  /* refinement steps summed over all KKT solves */
+  int32_t dyn_reg_hits;    /* pivots replaced by dynamic regularisation (last factor) */
+  double obj_primal;       /* g_p (Eq. residuals-objectives), unscaled */
+  double obj_dual;         /* g_d */
+  double res_primal;       /* ||r_p||_inf */
+  double res_dual;         /* ||r_d||_inf */
+  double gap_abs;          /* |g_p - g_d| */
+  double gap_rel;          /* |g_p - g_d| / max(1, min(|g_p|, |g_d|)) */
+  double mu, tau, kappa;   /* complementarity measure (scaled space) and the embedding scalars */
+  double setup_s;          /* host wall time of clr_setup */
+  double solve_s;          /* host wall time of the last clr_solve */
+} clr_info;
+
+/* Statistics of the symbolic KKT analysis done at setup. */
+typedef struct {
+  int64_t n, m, kkt_dim;   /* N = n + m */
+  int64_t kkt_nnz_lower;   /* structural nonzeros of the lower triangle of K */
+  int64_t l_nnz;           /* nonzeros of L (supernodal, including the diagonal) */
+  double factor_flops;     /* multiply-adds x 2 of one numeric factorization */
+  int64_t n_supernodes;
+  int64_t n_levels;        /* depth of the supernodal elimination tree */
+  int64_t max_front;       /* largest frontal matrix order */
+  int64_t front_pool_entries; /* entries of the frontal-matrix pool */
+  int64_t n_dense_rows;    /* rows treated as dense by the ordering */
+} clr_symbolic_stats;
+
+typedef struct clr_solver clr_solver;
+
+/* Fill *out with the defaults for a factorization precision (64 or 32).
+ * CLR_E_INVALID for any other factor_bits or a NULL out. */
+int clr_default_settings(clr_settings* out, int32_t factor_bits);
+
+/* Setup phase of Algorithm 1 (steps 1-2): validate, reorder the cones into
+ * zero, nonneg, SOC, exp, pow, PSD with all zero and all nonneg cones merged
+ * (Sec. 3.3, 3.5), equilibrate, assemble the KKT pattern of Eq. linsys_2x2,
+ * compute the AMD ordering, elimination tree and supernodes, and upload the
+ * data to the current CUDA device.
+ *   P_upper  n x n, upper triangle of P only (entries below the diagonal give
+ *            CLR_E_INVALID); P must be positive semidefinite (not checked).
+ *   q        length n.   A  m x n.   b  length m.
+ *   cones    ncones entries whose dims add up to m, in row order of A and b.
+ *   st       settings, or NULL for clr_default_settings(.., 64).
+ * On success *out owns device memory; free it with clr_free.  On failure
+ * *out is NULL.  Errors: CLR_E_INVALID (NaN/Inf, pattern), CLR_E_DIM,
+ * CLR_E_UNSUPPORTED, CLR_E_OOM, CLR_E_CUDA. */
+int clr_setup(clr_solver** out, const clr_csc* P_upper, const double* q, const clr_csc* A, const double* b,
+              const clr_cone* cones, int32_t ncones, const clr_settings* st);
+
+/* Host-only part of clr_setup (validation, reordering, equilibration, KKT
+ * pattern, ordering, symbolic factorization); touches no GPU.  The object can
+ * be queried with clr_get_symbolic_stats / clr_get_symbolic and freed with
+ * clr_free, but not solved. */
+int clr_analyze(clr_solver** out, const clr_csc* P_upper, const double* q, const clr_csc* A, const double* b,
+                const clr_cone* cones, int32_t ncones, const clr_settings* st);
+
+/* Solve phase of Algorithm 1: initial point, then iterations until the
+ * termination or infeasibility tests pass, max_iter is reached, or the step
+ * length falls below min_step.  Blocking.  Each call starts from scratch
+ * (data as set up, or as replaced by clr_update_qb). */
+int clr_solve(clr_solver* s);
+
+/* Copy the result to host buffers (any may be NULL): x (n), s (m), z (m) in
+ * the caller's original row order, un-scaled.  SOLVED: x/tau, s/tau, z/tau.
+ * PRIMAL_INFEASIBLE: z = certificate normalised to b'z = -1, x and s NaN.
+ * DUAL_INFEASIBLE: x, s normalised to q'x = -1, z NaN.
+ * CLR_E_STATE before the first clr_solve. */
+int clr_get_solution(const clr_solver* s, double* x, double* sl, double* z, clr_info* info);
+
+/* Replace q and b (host, lengths n and m, caller's row order) keeping P, A,
+ * the cones and the symbolic analysis (parametric re-solve, Sec. 4.6).  The
+ * equilibration computed at setup is kept.  CLR_E_INVALID on NaN/Inf. */
+int clr_update_qb(clr_solver* s, const double* q, const double* b);
+
+int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out);
+
+/* Export the symbolic factorization for inspection.  perm (length N): the
+ * fill-reducing order, perm[k] = KKT index eliminated k-th (KKT index i < n is
+ * x_i, n + j is row j of the reordered constraint block).  sn_ptr (n_supernodes
+ * + 1): columns of supernode J are perm-positions sn_ptr[J] .. sn_ptr[J+1]-1.
+ * sn_parent (n_supernodes): parent supernode or -1.  row_ptr (n_supernodes+1)
+ * and rows (row_ptr[n_supernodes]): perm-positions of the rows of each front,
+ * its own columns first.  row_perm (m): reordered constraint row i is caller
+ * row row_perm[i].  Any output may be NULL; sizes from clr_get_symbolic_stats
+ * (rows total: query with rows == NULL and read *rows_len). */
+int clr_get_symbolic(const clr_solver* s, int64_t* perm, int64_t* sn_ptr, int64_t* sn_parent, int64_t* row_ptr,
+                     int64_t* rows, int64_t* rows_len, int64_t* row_perm);
+
+/* Equilibration scalings: D (n), E (m, reordered rows), c (1 value). */
+int clr_get_scaling(const clr_solver* s, double* D, double* E, double* c);
+
+/* Per-iteration log of the last solve, up to cap rows of 12 doubles:
+ * iter, mu, pcost, dcost, res_primal, res_dual, gap, alpha_a, sigma,
+ * alpha_c, ir_steps, tau.  Returns the number of rows written in *rows. */
+int clr_get_history(const clr_solver* s, double* out, int32_t cap, int32_t* rows);
+
+/* Bind the solver's work to a CUDA stream (cudaStream_t passed as void*;
+ * NULL = the solver's own stream).  The stream must outlive the solver. */
+int clr_set_stream(clr_solver* s, void* cuda_stream);
+
+/* Device-memory allocator used by every later clr_setup (process-wide).
+ * alloc returns NULL on failure; both are called on the setup thread.
+ * Passing NULL functions restores cudaMalloc/cudaFree. */
+typedef void* (*clr_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*clr_free_fn)(void* ptr, size_t bytes, void* ctx);
+int clr_set_allocator(clr_alloc_fn alloc_fn, clr_free_fn free_fn, void* ctx);
+
+void clr_free(clr_solver* s);
+const char* clr_error_string(int code);
+const char* clr_status_string(int status);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* clr_last_cuda_error(void);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points.  Each runs one step of the per-iteration device
+ * path on its own, on host arrays, so that it can be checked against a
+ * reference.  They allocate and free their own device memory per call.
+ * ------------------------------------------------------------------------ */
+
+/* Scaling matrices H of one cone list (Alg. 1 step 4, Appendix A): for each
+ * cone, its dense dim x dim block H (row-major) is written to H_out at the
+ * cone's packed offset sum(dim_i^2).  s, z: length sum(dim).  mu: global
+ * complementarity measure used by the exp/pow BFGS scaling.  Zero cones give
+ * H = 0.  The cones are not reordered. */
+int clr_cones_scaling(const clr_cone* cones, int32_t ncones, const double* s, const double* z, double mu,
+                      double* H_out);
+
+/* Largest step alpha <= alpha_max with s + alpha ds in K and z + alpha dz in
+ * K* (Sec. 2.2), over the given cones, as the affine step computes it
+ * (symmetric cones exact, exp/pow by backtracking with ratio 0.8 from the
+ * symmetric-cone value). */
+int clr_cones_step_length(const clr_cone* cones, int32_t ncones, const double* s, const double* z,
+                          const double* ds, const double* dz, double alpha_max, double* alpha_out);
+
+/* Combined-step d_s of Eq. ds-correction-step for every cone, with the
+ * Mehrotra (symmetric) or third-order (exp/pow) correction built from the
+ * affine directions ds_a, dz_a.  Zero cones give 0. */
+int clr_cones_combined_ds(const clr_cone* cones, int32_t ncones, const double* s, const double* z,
+                          const double* ds_a, const double* dz_a, double sigma_mu, double* ds_out);
+
+/* Sparse LDL^T of a symmetric quasi-definite matrix (Sec. 3.6) with the same
+ * supernodal factorization the solver uses.  K_lower: lower triangle (CSC,
+ * diagonal present in every column).  signs[N]: +1 or -1, the expected sign
+ * of each pivot (dynamic regularisation replaces a pivot d with
+ * sign*dyn_reg_delta when sign*d <= dyn_reg_eps).  No static regularisation
+ * is added here.  order: NULL for the library's AMD ordering, else a
+ * caller permutation (order[k] = index eliminated k-th).  factor_bits 64/32.
+ * x_out = K^{-1} rhs (no refinement); D_out (optional, N): pivots in the
+ * caller's numbering. */
+int clr_ldl_solve(const clr_csc* K_lower, const double* signs, const int64_t* order, int32_t factor_bits,
+                  double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
+                  int32_t* dyn_hits_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLR_H */

@@ -1,0 +1,293 @@
+"""Python binding of libclr.so (ctypes).  Argument marshalling only: every step
+of the solver runs in the library.  Function names follow include/clr.h.
+
+The library is built in-tree by ``paper_2412_19027_gb300.build.build()``; if
+it is missing every call raises ``RuntimeError`` (there is no fallback)."""
+import ctypes as C
+import os
+
+import numpy as np
+import scipy.sparse as sp
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libclr.so")
+
+STATUS = {0: "UNSOLVED", 1: "SOLVED", 2: "PRIMAL_INFEASIBLE", 3: "DUAL_INFEASIBLE", 4: "MAX_ITER",
+          5: "INSUFFICIENT_PROGRESS", 6: "NUMERICAL_ERROR"}
+
+
+class ClrError(RuntimeError):
+    def __init__(self, code, where):
+        msg = "%s failed: %s (%d)" % (where, _err_string(code), code)
+        if code == -5:
+            msg += ": " + _lib().clr_last_cuda_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+class clr_cone(C.Structure):
+    _fields_ = [("type", C.c_int32), ("dim", C.c_int32), ("alpha", C.c_double)]
+
+
+class clr_csc(C.Structure):
+    _fields_ = [("nrows", C.c_int64), ("ncols", C.c_int64), ("nnz", C.c_int64), ("colptr", C.POINTER(C.c_int64)),
+                ("rowind", C.POINTER(C.c_int32)), ("val", C.POINTER(C.c_double))]
+
+
+class clr_settings(C.Structure):
+    _fields_ = [("eps_feas", C.c_double), ("eps_inf", C.c_double), ("max_iter", C.c_int32),
+                ("factor_bits", C.c_int32), ("static_reg", C.c_double), ("static_reg_dyn", C.c_double),
+                ("dyn_reg_eps", C.c_double), ("dyn_reg_delta", C.c_double), ("ir_max_steps", C.c_int32),
+                ("ir_abstol", C.c_double), ("ir_reltol", C.c_double), ("equilibrate", C.c_int32),
+                ("ruiz_passes", C.c_int32), ("scale_min", C.c_double), ("scale_max", C.c_double),
+                ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
+                ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32)]
+
+
+class clr_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("ir_steps_total", C.c_int32),
+                ("dyn_reg_hits", C.c_int32), ("obj_primal", C.c_double), ("obj_dual", C.c_double),
+                ("res_primal", C.c_double), ("res_dual", C.c_double), ("gap_abs", C.c_double),
+                ("gap_rel", C.c_double), ("mu", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
+                ("setup_s", C.c_double), ("solve_s", C.c_double)]
+
+
+class clr_symbolic_stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("kkt_dim", C.c_int64), ("kkt_nnz_lower", C.c_int64),
+                ("l_nnz", C.c_int64), ("factor_flops", C.c_double), ("n_supernodes", C.c_int64),
+                ("n_levels", C.c_int64), ("max_front", C.c_int64), ("front_pool_entries", C.c_int64),
+                ("n_dense_rows", C.c_int64)]
+
+
+_LIB = None
+EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr_get_solution", "clr_update_qb",
+           "clr_get_symbolic_stats", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
+           "clr_set_allocator", "clr_free", "clr_error_string", "clr_status_string", "clr_last_cuda_error",
+           "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_ldl_solve"]
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libclr.so is not built; run paper_2412_19027_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        vp = C.c_void_p
+        L.clr_default_settings.argtypes = [P(clr_settings), C.c_int32]
+        for name in ("clr_setup", "clr_analyze"):
+            getattr(L, name).argtypes = [P(vp), P(clr_csc), P(C.c_double), P(clr_csc), P(C.c_double), P(clr_cone),
+                                         C.c_int32, P(clr_settings)]
+        L.clr_solve.argtypes = [vp]
+        L.clr_get_solution.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double), P(clr_info)]
+        L.clr_update_qb.argtypes = [vp, P(C.c_double), P(C.c_double)]
+        L.clr_get_symbolic_stats.argtypes = [vp, P(clr_symbolic_stats)]
+        L.clr_get_symbolic.argtypes = [vp] + [P(C.c_int64)] * 7
+        L.clr_get_scaling.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.clr_get_history.argtypes = [vp, P(C.c_double), C.c_int32, P(C.c_int32)]
+        L.clr_set_stream.argtypes = [vp, vp]
+        L.clr_free.argtypes = [vp]
+        L.clr_free.restype = None
+        L.clr_error_string.restype = C.c_char_p
+        L.clr_status_string.restype = C.c_char_p
+        L.clr_last_cuda_error.restype = C.c_char_p
+        L.clr_cones_scaling.argtypes = [P(clr_cone), C.c_int32, P(C.c_double), P(C.c_double), C.c_double,
+                                        P(C.c_double)]
+        L.clr_cones_step_length.argtypes = [P(clr_cone), C.c_int32] + [P(C.c_double)] * 4 + [C.c_double,
+                                                                                            P(C.c_double)]
+        L.clr_cones_combined_ds.argtypes = [P(clr_cone), C.c_int32] + [P(C.c_double)] * 4 + [C.c_double,
+                                                                                            P(C.c_double)]
+        L.clr_ldl_solve.argtypes = [P(clr_csc), P(C.c_double), P(C.c_int64), C.c_int32, C.c_double, C.c_double,
+                                    P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
+        _LIB = L
+    return _LIB
+
+
+def _err_string(code):
+    try:
+        return _lib().clr_error_string(code).decode()
+    except Exception:
+        return "error"
+
+
+def _check(rc, where):
+    if rc != 0:
+        raise ClrError(rc, where)
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _csc(M, keep):
+    M = sp.csc_matrix(M)
+    M.sort_indices()
+    colptr = np.ascontiguousarray(M.indptr, dtype=np.int64)
+    rowind = np.ascontiguousarray(M.indices, dtype=np.int32)
+    val = np.ascontiguousarray(M.data, dtype=np.float64)
+    keep += [colptr, rowind, val]
+    return clr_csc(M.shape[0], M.shape[1], len(val), colptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                   rowind.ctypes.data_as(C.POINTER(C.c_int32)), val.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+def _cones(cones):
+    arr = (clr_cone * max(len(cones), 1))()
+    for i, (t, d, a) in enumerate(cones):
+        arr[i] = clr_cone(int(t), int(d), float(a))
+    return arr
+
+
+def clr_default_settings(factor_bits=64, **overrides):
+    s = clr_settings()
+    _check(_lib().clr_default_settings(C.byref(s), factor_bits), "clr_default_settings")
+    for k, v in overrides.items():
+        setattr(s, k, v)
+    return s
+
+
+def settings_dict(s):
+    return {name: getattr(s, name) for name, _ in clr_settings._fields_}
+
+
+class Solver:
+    """Owner of one clr_solver handle."""
+
+    def __init__(self, P_upper, q, A, b, cones, settings=None, device=True):
+        keep = []
+        Pc = _csc(sp.triu(sp.csc_matrix(P_upper)) if not _is_upper(P_upper) else P_upper, keep)
+        Ac = _csc(A, keep)
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        self.n, self.m = len(q), len(b)
+        cz = _cones(cones)
+        st = settings if isinstance(settings, clr_settings) else clr_default_settings(**(settings or {}))
+        self.settings = st
+        h = C.c_void_p()
+        fn = _lib().clr_setup if device else _lib().clr_analyze
+        _check(fn(C.byref(h), C.byref(Pc), _dptr(q), C.byref(Ac), _dptr(b), cz, len(cones), C.byref(st)),
+               "clr_setup" if device else "clr_analyze")
+        self.h = h
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "h", None) and self.h.value:
+            _lib().clr_free(self.h)
+            self.h = C.c_void_p()
+
+    def solve(self):
+        _check(_lib().clr_solve(self.h), "clr_solve")
+        return self.info()["status"]
+
+    def info(self):
+        inf = clr_info()
+        _check(_lib().clr_get_solution(self.h, None, None, None, C.byref(inf)), "clr_get_solution")
+        d = {name: getattr(inf, name) for name, _ in clr_info._fields_}
+        d["status_name"] = STATUS.get(d["status"], "UNKNOWN")
+        return d
+
+    def solution(self):
+        x, s, z = np.empty(self.n), np.empty(self.m), np.empty(self.m)
+        inf = clr_info()
+        _check(_lib().clr_get_solution(self.h, _dptr(x), _dptr(s), _dptr(z), C.byref(inf)), "clr_get_solution")
+        d = {name: getattr(inf, name) for name, _ in clr_info._fields_}
+        d["status_name"] = STATUS.get(d["status"], "UNKNOWN")
+        return x, s, z, d
+
+    def update_qb(self, q, b):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        _check(_lib().clr_update_qb(self.h, _dptr(q), _dptr(b)), "clr_update_qb")
+
+    def set_stream(self, stream_ptr):
+        _check(_lib().clr_set_stream(self.h, C.c_void_p(stream_ptr)), "clr_set_stream")
+
+    def symbolic_stats(self):
+        s = clr_symbolic_stats()
+        _check(_lib().clr_get_symbolic_stats(self.h, C.byref(s)), "clr_get_symbolic_stats")
+        return {name: getattr(s, name) for name, _ in clr_symbolic_stats._fields_}
+
+    def symbolic(self):
+        st = self.symbolic_stats()
+        N, nsn = st["kkt_dim"], st["n_supernodes"]
+        L = C.POINTER(C.c_int64)
+        rl = C.c_int64()
+        _check(_lib().clr_get_symbolic(self.h, None, None, None, None, None, C.byref(rl), None), "clr_get_symbolic")
+        perm, snp, par = np.empty(N, np.int64), np.empty(nsn + 1, np.int64), np.empty(nsn, np.int64)
+        rp, rows, rowperm = np.empty(nsn + 1, np.int64), np.empty(rl.value, np.int64), np.empty(self.m, np.int64)
+        ptr = lambda a: a.ctypes.data_as(L)
+        _check(_lib().clr_get_symbolic(self.h, ptr(perm), ptr(snp), ptr(par), ptr(rp), ptr(rows), C.byref(rl),
+                                       ptr(rowperm)), "clr_get_symbolic")
+        return dict(perm=perm, sn_ptr=snp, sn_parent=par, row_ptr=rp, rows=rows, row_perm=rowperm)
+
+    def scaling(self):
+        D, E, c = np.empty(self.n), np.empty(self.m), C.c_double()
+        _check(_lib().clr_get_scaling(self.h, _dptr(D), _dptr(E), C.byref(c)), "clr_get_scaling")
+        return D, E, c.value
+
+    def history(self):
+        cap = self.settings.max_iter + 2
+        out = np.zeros((cap, 12))
+        rows = C.c_int32()
+        _check(_lib().clr_get_history(self.h, _dptr(out), cap, C.byref(rows)), "clr_get_history")
+        return out[: rows.value]
+
+
+def _is_upper(P):
+    P = sp.coo_matrix(P)
+    return bool(np.all(P.row <= P.col))
+
+
+def clr_setup(P_upper, q, A, b, cones, settings=None):
+    return Solver(P_upper, q, A, b, cones, settings, device=True)
+
+
+def clr_analyze(P_upper, q, A, b, cones, settings=None):
+    return Solver(P_upper, q, A, b, cones, settings, device=False)
+
+
+def clr_cones_scaling(cones, s, z, mu):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    H = np.zeros(sum(int(d) * int(d) for (_, d, _) in cones))
+    _check(_lib().clr_cones_scaling(_cones(cones), len(cones), _dptr(s), _dptr(z), float(mu), _dptr(H)),
+           "clr_cones_scaling")
+    out, off = [], 0
+    for (_, d, _) in cones:
+        out.append(H[off:off + d * d].reshape(d, d))
+        off += d * d
+    return out
+
+
+def clr_cones_step_length(cones, s, z, ds, dz, alpha_max=1.0):
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (s, z, ds, dz)]
+    a = C.c_double()
+    _check(_lib().clr_cones_step_length(_cones(cones), len(cones), *[_dptr(v) for v in arrs], float(alpha_max),
+                                        C.byref(a)), "clr_cones_step_length")
+    return a.value
+
+
+def clr_cones_combined_ds(cones, s, z, ds_a, dz_a, sigma_mu):
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (s, z, ds_a, dz_a)]
+    out = np.zeros(len(arrs[0]))
+    _check(_lib().clr_cones_combined_ds(_cones(cones), len(cones), *[_dptr(v) for v in arrs], float(sigma_mu),
+                                        _dptr(out)), "clr_cones_combined_ds")
+    return out
+
+
+def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1e-13, dyn_reg_delta=2e-7):
+    keep = []
+    Kc = _csc(sp.tril(sp.csc_matrix(K_lower)), keep)
+    signs = np.ascontiguousarray(signs, dtype=np.float64)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    N = len(rhs)
+    x, D = np.zeros(N), np.zeros(N)
+    hits = C.c_int32()
+    ordp = None
+    if order is not None:
+        order = np.ascontiguousarray(order, dtype=np.int64)
+        ordp = order.ctypes.data_as(C.POINTER(C.c_int64))
+    _check(_lib().clr_ldl_solve(C.byref(Kc), _dptr(signs), ordp, factor_bits, dyn_reg_eps, dyn_reg_delta, _dptr(rhs),
+                                _dptr(x), _dptr(D), C.byref(hits)), "clr_ldl_solve")
+    return x, D, hits.value

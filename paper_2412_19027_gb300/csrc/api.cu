@@ -1,0 +1,207 @@
+// extern "C" entry points declared in include/clr.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ipm.cuh"
+
+struct clr_solver {
+  clr::Solver impl;
+};
+
+namespace clr {
+const char* last_cuda_error();
+void set_allocator(clr_alloc_fn a, clr_free_fn f, void* ctx);
+}  // namespace clr
+
+using clr::Solver;
+
+extern "C" {
+
+int clr_default_settings(clr_settings* out, int32_t factor_bits) {
+  if (!out || (factor_bits != 64 && factor_bits != 32)) return CLR_E_INVALID;
+  const bool low = factor_bits != 64;
+  const double eps64 = 2.220446049250313e-16;
+  const double eps32 = 1.1920928955078125e-07;
+  clr_settings s{};
+  s.eps_feas = 1e-8;
+  s.eps_inf = 1e-8;
+  s.max_iter = 200;
+  s.factor_bits = factor_bits;
+  s.static_reg = low ? std::sqrt(eps32) : 1e-8;
+  s.static_reg_dyn = eps64 * eps64;
+  s.dyn_reg_eps = low ? 1e-6 : 1e-13;
+  s.dyn_reg_delta = low ? 1e-4 : 2e-7;
+  s.ir_max_steps = 10;
+  s.ir_abstol = 1e-12;
+  s.ir_reltol = 1e-12;
+  s.equilibrate = 1;
+  s.ruiz_passes = 10;
+  s.scale_min = 1e-4;
+  s.scale_max = 1e4;
+  s.step_fraction = 0.99;
+  s.backtrack = 0.8;
+  s.nbhd_beta = 1e-6;
+  s.min_step = 1e-10;
+  s.use_graph = 1;
+  s.verbose = 0;
+  *out = s;
+  return CLR_OK;
+}
+
+static int check_settings(const clr_settings& s) {
+  if (s.factor_bits != 64 && s.factor_bits != 32) return CLR_E_INVALID;
+  if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0)
+    return CLR_E_INVALID;
+  if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
+  if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;
+  return CLR_OK;
+}
+
+static int make(clr_solver** out, const clr_csc* P, const double* q, const clr_csc* A, const double* b,
+                const clr_cone* cones, int32_t ncones, const clr_settings* st, bool device) {
+  if (!out) return CLR_E_INVALID;
+  *out = nullptr;
+  clr_settings s;
+  if (st) s = *st;
+  else clr_default_settings(&s, 64);
+  int rc = check_settings(s);
+  if (rc) return rc;
+  clr_solver* h = new (std::nothrow) clr_solver;
+  if (!h) return CLR_E_OOM;
+  try {
+    rc = h->impl.analyze(P, q, A, b, cones, ncones, s);
+    if (rc == CLR_OK && device) rc = h->impl.upload();
+  } catch (const std::bad_alloc&) {
+    rc = CLR_E_OOM;
+  }
+  if (rc != CLR_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return CLR_OK;
+}
+
+int clr_setup(clr_solver** out, const clr_csc* P_upper, const double* q, const clr_csc* A, const double* b,
+              const clr_cone* cones, int32_t ncones, const clr_settings* st) {
+  return make(out, P_upper, q, A, b, cones, ncones, st, true);
+}
+
+int clr_analyze(clr_solver** out, const clr_csc* P_upper, const double* q, const clr_csc* A, const double* b,
+                const clr_cone* cones, int32_t ncones, const clr_settings* st) {
+  return make(out, P_upper, q, A, b, cones, ncones, st, false);
+}
+
+int clr_solve(clr_solver* s) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.solve();
+}
+
+int clr_get_solution(const clr_solver* s, double* x, double* sl, double* z, clr_info* info) {
+  if (!s) return CLR_E_INVALID;
+  return const_cast<clr_solver*>(s)->impl.get_solution(x, sl, z, info);
+}
+
+int clr_update_qb(clr_solver* s, const double* q, const double* b) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.update_qb(q, b);
+}
+
+int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out) {
+  if (!s || !out) return CLR_E_INVALID;
+  const Solver& v = s->impl;
+  clr_symbolic_stats r{};
+  r.n = v.hp.n;
+  r.m = v.hp.m;
+  r.kkt_dim = v.hp.n + v.hp.m;
+  r.kkt_nnz_lower = (int64_t)v.hp.krow.size();
+  r.l_nnz = v.sy.l_nnz;
+  r.factor_flops = v.sy.flops;
+  r.n_supernodes = v.sy.nsn;
+  r.n_levels = v.sy.nlev;
+  r.max_front = v.sy.max_front;
+  r.front_pool_entries = v.sy.pool;
+  r.n_dense_rows = v.sy.n_dense;
+  *out = r;
+  return CLR_OK;
+}
+
+int clr_get_symbolic(const clr_solver* s, int64_t* perm, int64_t* sn_ptr, int64_t* sn_parent, int64_t* row_ptr,
+                     int64_t* rows, int64_t* rows_len, int64_t* row_perm) {
+  if (!s) return CLR_E_INVALID;
+  const Solver& v = s->impl;
+  if (perm) std::copy(v.sy.perm.begin(), v.sy.perm.end(), perm);
+  if (sn_ptr) std::copy(v.sy.sn_ptr.begin(), v.sy.sn_ptr.end(), sn_ptr);
+  if (sn_parent) std::copy(v.sy.sn_parent.begin(), v.sy.sn_parent.end(), sn_parent);
+  if (row_ptr) std::copy(v.sy.row_ptr.begin(), v.sy.row_ptr.end(), row_ptr);
+  if (rows) std::copy(v.sy.rows.begin(), v.sy.rows.end(), rows);
+  if (rows_len) *rows_len = (int64_t)v.sy.rows.size();
+  if (row_perm) std::copy(v.hp.row_perm.begin(), v.hp.row_perm.end(), row_perm);
+  return CLR_OK;
+}
+
+int clr_get_scaling(const clr_solver* s, double* D, double* E, double* c) {
+  if (!s) return CLR_E_INVALID;
+  const Solver& v = s->impl;
+  if (D) std::copy(v.hp.D.begin(), v.hp.D.end(), D);
+  if (E) std::copy(v.hp.E.begin(), v.hp.E.end(), E);
+  if (c) *c = v.hp.c;
+  return CLR_OK;
+}
+
+int clr_get_history(const clr_solver* s, double* out, int32_t cap, int32_t* rows) {
+  if (!s) return CLR_E_INVALID;
+  const Solver& v = s->impl;
+  const int32_t have = (int32_t)(v.history.size() / 12);
+  const int32_t k = std::min(have, std::max(cap, 0));
+  if (out) std::copy(v.history.begin(), v.history.begin() + 12 * (size_t)k, out);
+  if (rows) *rows = k;
+  return CLR_OK;
+}
+
+int clr_set_stream(clr_solver* s, void* cuda_stream) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.set_stream(cuda_stream);
+}
+
+int clr_set_allocator(clr_alloc_fn alloc_fn, clr_free_fn free_fn, void* ctx) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return CLR_E_INVALID;
+  clr::set_allocator(alloc_fn, free_fn, ctx);
+  return CLR_OK;
+}
+
+void clr_free(clr_solver* s) { delete s; }
+
+const char* clr_error_string(int code) {
+  switch (code) {
+    case CLR_OK: return "ok";
+    case CLR_E_INVALID: return "invalid input";
+    case CLR_E_DIM: return "dimension mismatch";
+    case CLR_E_UNSUPPORTED: return "unsupported problem";
+    case CLR_E_OOM: return "out of memory";
+    case CLR_E_CUDA: return "CUDA error";
+    case CLR_E_TIMEOUT: return "device wait timed out";
+    case CLR_E_AGAIN: return "not ready";
+    case CLR_E_STATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* clr_status_string(int status) {
+  switch (status) {
+    case CLR_UNSOLVED: return "UNSOLVED";
+    case CLR_SOLVED: return "SOLVED";
+    case CLR_PRIMAL_INFEASIBLE: return "PRIMAL_INFEASIBLE";
+    case CLR_DUAL_INFEASIBLE: return "DUAL_INFEASIBLE";
+    case CLR_MAX_ITER: return "MAX_ITER";
+    case CLR_INSUFFICIENT_PROGRESS: return "INSUFFICIENT_PROGRESS";
+    case CLR_NUMERICAL_ERROR: return "NUMERICAL_ERROR";
+    default: return "UNKNOWN";
+  }
+}
+
+const char* clr_last_cuda_error(void) { return clr::last_cuda_error(); }
+
+}  // extern "C"

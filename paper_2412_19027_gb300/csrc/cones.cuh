@@ -1,0 +1,72 @@
+// Cone kernels of the per-iteration device step (Alg. 1 steps 4, 7, 8, 10 of
+// the paper): scaling H written into the KKT values, step lengths, and the
+// combined-step d_s.  Families are handled as Sec. 3.3 proposes, mapped to
+// GB300: zero/nonneg one flat pass, SOC one warp per cone (shuffle
+// reductions), exp/pow one thread per cone, PSD one block per cone.
+#pragma once
+
+#include "device.cuh"
+
+namespace clr {
+
+// Device view of the reordered cone layout and the per-cone scaling data.
+struct ConeDev {
+  int64_t m = 0, m_zero = 0, m_nonneg = 0;
+  // SOC cones: row offset, dimension, offset of the packed H block in kval
+  int64_t n_soc = 0;
+  const int64_t* soc_off = nullptr;
+  const int32_t* soc_dim = nullptr;
+  const int64_t* soc_kb = nullptr;
+  // exp / pow cones: rows row0 + 3 i, packed H at kb0 + 6 i
+  int64_t n_exp = 0, exp_row0 = 0, exp_kb0 = 0;
+  int64_t n_pow = 0, pow_row0 = 0, pow_kb0 = 0;
+  const double* pow_alpha = nullptr;
+  // PSD cones: order k, svec dim d, rows row0 + d i, packed H at kb0 + d(d+1)/2 i
+  int64_t n_psd = 0, psd_row0 = 0, psd_kb0 = 0;
+  int psd_k = 0, psd_d = 0;
+  int64_t nn_kb = 0;  // packed offset of the first nonneg diagonal (after the zero cone)
+  double* kvz = nullptr;  // z part of the KKT values (-H blocks)
+  int64_t nkz = 0;        // number of entries of kvz
+  double* scratch = nullptr;  // m doubles of work space for the SOC corrector
+  // scaling data written by the scaling kernels
+  double* nn_w = nullptr;     // sqrt(s/z) per nonneg row
+  double* nn_lam = nullptr;   // sqrt(s z)
+  double* soc_eta = nullptr;  // per SOC cone
+  double* soc_wb = nullptr;   // w-bar, indexed by row (m entries, used on SOC rows)
+  double* soc_lam = nullptr;  // lambda, indexed by row
+  double* psd_R = nullptr;    // k*k per cone (column-major)
+  double* psd_Ri = nullptr;   // R^{-1}
+  double* psd_lam = nullptr;  // k per cone
+  double exp_center[3] = {0, 0, 0};  // central point of the exp cone (u = -grad f(u))
+};
+
+// All scalars of one iteration that several kernels share live in device memory.
+struct IterScalars;
+
+// Scaling H (-H into kvz) for every cone; max |H_ii| into *hmax_bits (atomicMax on the bit pattern).
+int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* mu,
+                  unsigned long long* hmax_bits, const int* skip);
+// H = I on every cone block (initialisation solves), zero cone included.
+int cones_identity_H(cudaStream_t st, const ConeDev& cd, const int* skip);
+// Symmetric-cone step length over s/ds and z/dz -> atomicMin into *amin_bits.
+int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
+                         const double* dz, unsigned long long* amin_bits, const int* skip);
+// exp/pow backtracking: for candidates a_j = a0 * backtrack^(j0 + j), j < 64, bit j of *mask
+// stays set iff every exp/pow cone passes (interior; plus N(beta) with the trial mu when
+// nbhd != 0).  mu_coef = {s'z + tau kappa, s'dz + ds'z + tau dkappa + kappa dtau,
+// ds'dz + dtau dkappa} / (nu + 1).
+int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
+                      const double* dz, const double* a0, double backtrack, int j0, int nbhd, double beta,
+                      const double* mu_coef, unsigned long long* mask, const int* skip);
+// Combined-step d_s (Eq. ds-correction-step) for every cone.
+int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* dsa,
+                      const double* dza, const double* sigma_mu, double* ds_out, const int* skip);
+// Initial point shift (symmetric init): v += (1 - a) e where a = least Jordan eigenvalue < sqrt(eps).
+// Zero-cone entries are set to 0.  nn_min_bits: scratch for the nonneg minimum (one per vector).
+int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, double* nn_min, const int* skip);
+// Unit initialisation: v = central point of each cone (0 on the zero cone).
+int cones_unit_init(cudaStream_t st, const ConeDev& cd, double* v, const int* skip);
+
+__host__ double exp_central_point_host(double out[3]);
+
+}  // namespace clr

@@ -1,0 +1,54 @@
+// Numeric supernodal (multifrontal) LDL^T of the quasi-definite KKT matrix
+// and its level-scheduled triangular solves (Sec. 3.6 of the paper, Alg. 1
+// steps 5, 6 and 9).  T is the factor precision (double or float).
+#pragma once
+
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+#include "symbolic.h"
+
+namespace clr {
+
+// Device arrays of the symbolic structure and the index maps (shared by the
+// FP64 and FP32 factors).
+struct LdlStructure {
+  int64_t N = 0, nsn = 0, nlev = 0, pool = 0, wtot = 0, nk = 0;
+  int64_t *sn_ptr = nullptr, *row_ptr = nullptr, *front_off = nullptr, *upd_off = nullptr, *lev_sn = nullptr;
+  int32_t* rows_kkt = nullptr;
+  int32_t* w_init = nullptr;   // solve slot -> KKT index of the right-hand side, or -1
+  int8_t* dsign = nullptr;     // expected pivot sign by position
+  int64_t *kdest = nullptr, *diag_pos = nullptr;
+  int64_t *fa_tgt = nullptr, *fa_ptr = nullptr, *fa_src = nullptr;
+  int64_t *sv_tgt = nullptr, *sv_ptr = nullptr, *sv_src = nullptr;
+  // host copies used to configure launches
+  std::vector<int64_t> h_lev_ptr, h_lev_sn, h_fa_lev_ptr, h_sv_lev_ptr;
+  std::vector<int64_t> h_sn_ptr, h_row_ptr, h_front_off;
+  std::vector<int> lev_small_maxf;               // largest small front of each level
+  std::vector<std::vector<int64_t>> lev_big;     // big fronts of each level
+  int small_max = 0;
+  int64_t max_front = 0;
+};
+
+int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps& mp, const std::vector<int8_t>& dsign,
+                         int small_max, LdlStructure& st);
+
+template <typename T>
+struct LdlFactor {
+  const LdlStructure* s = nullptr;
+  T* F = nullptr;   // frontal-matrix pool
+  T* Dp = nullptr;  // pivots by elimination position
+  T* w = nullptr;   // forward-solve slots
+  T* xs = nullptr;  // solution in KKT order
+  int* dyn_hits = nullptr;
+  int alloc(DeviceArena& ar, const LdlStructure& st);
+  // Factor K: kval (FP64, lower triangle entries in kval order) scattered into
+  // the fronts, +/- (*delta) added on the diagonal (x rows +, z rows -).
+  int factor(cudaStream_t st, const double* kval, const double* delta, double dyn_eps, double dyn_delta,
+             const int* skip) const;
+  // xs = (L D L^T)^{-1} rhs (rhs FP64 in KKT order).
+  int solve(cudaStream_t st, const double* rhs, const int* skip) const;
+};
+
+}  // namespace clr

@@ -1,0 +1,389 @@
+// Setup phase, host side: validation, cone reordering and merging, modified
+// Ruiz equilibration, scaled CSR copies of P, A, A^T and the value layout of
+// the KKT matrix K = [P A^T; A -H] (Algorithm 1 steps 1-2 of the paper).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "internal.h"
+
+namespace clr {
+
+namespace {
+
+bool finite_all(const double* v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+int check_csc(const clr_csc* M, int64_t nrows, int64_t ncols, bool upper, std::string& err, const char* name) {
+  if (!M) {
+    err = std::string(name) + " is NULL";
+    return CLR_E_INVALID;
+  }
+  if (M->nrows != nrows || M->ncols != ncols) {
+    err = std::string(name) + " has the wrong shape";
+    return CLR_E_DIM;
+  }
+  if (M->nnz < 0 || (M->nnz > 0 && (!M->colptr || !M->rowind || !M->val)) || (ncols > 0 && !M->colptr)) {
+    err = std::string(name) + ": missing arrays";
+    return CLR_E_INVALID;
+  }
+  if (ncols > 0 && (M->colptr[0] != 0 || M->colptr[ncols] != M->nnz)) {
+    err = std::string(name) + ": colptr[0] must be 0 and colptr[ncols] == nnz";
+    return CLR_E_INVALID;
+  }
+  for (int64_t j = 0; j < ncols; ++j) {
+    if (M->colptr[j + 1] < M->colptr[j]) {
+      err = std::string(name) + ": colptr not monotone";
+      return CLR_E_INVALID;
+    }
+    for (int64_t p = M->colptr[j]; p < M->colptr[j + 1]; ++p) {
+      int64_t i = M->rowind[p];
+      if (i < 0 || i >= nrows || (p > M->colptr[j] && i <= M->rowind[p - 1])) {
+        err = std::string(name) + ": row indices out of range or not increasing";
+        return CLR_E_INVALID;
+      }
+      if (upper && i > j) {
+        err = std::string(name) + ": entry below the diagonal (pass the upper triangle)";
+        return CLR_E_INVALID;
+      }
+    }
+  }
+  if (!finite_all(M->val, M->nnz)) {
+    err = std::string(name) + " has a NaN or Inf";
+    return CLR_E_INVALID;
+  }
+  return CLR_OK;
+}
+
+int psd_order_of(int64_t d) {
+  int k = (int)std::lround((std::sqrt(8.0 * (double)d + 1.0) - 1.0) / 2.0);
+  return ((int64_t)k * (k + 1) / 2 == d) ? k : -1;
+}
+
+int64_t packed(int64_t d) { return d * (d + 1) / 2; }
+
+double scale_factor(double norm, const clr_settings& st) {
+  if (norm < 1e-8) return 1.0;
+  double f = 1.0 / std::sqrt(norm);
+  return std::min(std::max(f, st.scale_min), st.scale_max);
+}
+
+}  // namespace
+
+int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_csc* A, const double* b,
+                  const clr_cone* cones, int32_t ncones, const clr_settings& st, std::string& err) {
+  if (!A || !P) {
+    err = "P or A is NULL";
+    return CLR_E_INVALID;
+  }
+  const int64_t n = A->ncols, m = A->nrows;
+  if (n < 0 || m < 0) return CLR_E_DIM;
+  int rc;
+  if ((rc = check_csc(P, n, n, true, err, "P")) != CLR_OK) return rc;
+  if ((rc = check_csc(A, m, n, false, err, "A")) != CLR_OK) return rc;
+  if ((n > 0 && !q) || (m > 0 && !b) || (ncones > 0 && !cones) || ncones < 0) {
+    err = "q, b or cones is NULL";
+    return CLR_E_INVALID;
+  }
+  if (!finite_all(q, n) || !finite_all(b, m)) {
+    err = "q or b has a NaN or Inf";
+    return CLR_E_INVALID;
+  }
+  // ---- cones (Sec. 2.1) ----
+  int64_t total = 0;
+  int psd_k = 0;
+  for (int32_t i = 0; i < ncones; ++i) {
+    const clr_cone& c = cones[i];
+    if (c.type < CLR_ZERO || c.type > CLR_PSD_TRI || c.dim < 0) {
+      err = "bad cone type or dimension";
+      return CLR_E_INVALID;
+    }
+    if ((c.type == CLR_EXP || c.type == CLR_POW) && c.dim != 3) {
+      err = "exponential and power cones have dimension 3";
+      return CLR_E_INVALID;
+    }
+    if (c.type == CLR_POW && !(c.alpha > 0.0 && c.alpha < 1.0)) {
+      err = "power cone exponent must lie in (0, 1)";
+      return CLR_E_INVALID;
+    }
+    if (c.type == CLR_SOC && c.dim < 1) {
+      err = "second-order cone dimension must be >= 1";
+      return CLR_E_INVALID;
+    }
+    if (c.type == CLR_PSD_TRI) {
+      int k = psd_order_of(c.dim);
+      if (k < 1) {
+        err = "PSD cone dimension is not k(k+1)/2";
+        return CLR_E_INVALID;
+      }
+      if (psd_k == 0) psd_k = k;
+      if (k != psd_k || k > 32) {
+        err = "all PSD cones must share one order <= 32";
+        return CLR_E_UNSUPPORTED;
+      }
+    }
+    total += c.dim;
+  }
+  if (total != m) {
+    err = "cone dimensions do not add up to the rows of A";
+    return CLR_E_DIM;
+  }
+  hp.n = n;
+  hp.m = m;
+
+  // ---- reorder: zero, nonneg, SOC, exp, pow, PSD; merge zero and nonneg ----
+  std::vector<int64_t> coff(ncones + 1, 0);
+  for (int32_t i = 0; i < ncones; ++i) coff[i + 1] = coff[i] + cones[i].dim;
+  ConeLayout& cl = hp.cl;
+  cl = ConeLayout();
+  hp.row_perm.clear();
+  hp.row_perm.reserve(m);
+  const int fam_order[6] = {CLR_ZERO, CLR_NONNEG, CLR_SOC, CLR_EXP, CLR_POW, CLR_PSD_TRI};
+  for (int fi = 0; fi < 6; ++fi) {
+    const int fam = fam_order[fi];
+    if (fam == CLR_SOC) cl.soc_begin = (int64_t)cl.cones.size();
+    if (fam == CLR_EXP) cl.exp_begin = (int64_t)cl.cones.size();
+    if (fam == CLR_POW) cl.pow_begin = (int64_t)cl.cones.size();
+    if (fam == CLR_PSD_TRI) cl.psd_begin = (int64_t)cl.cones.size();
+    if (fam == CLR_ZERO || fam == CLR_NONNEG) {
+      int64_t start = (int64_t)hp.row_perm.size();
+      for (int32_t i = 0; i < ncones; ++i)
+        if (cones[i].type == fam)
+          for (int64_t r = coff[i]; r < coff[i + 1]; ++r) hp.row_perm.push_back(r);
+      int64_t d = (int64_t)hp.row_perm.size() - start;
+      if (fam == CLR_ZERO) cl.m_zero = d;
+      else cl.m_nonneg = d;
+      if (d > 0) cl.cones.push_back(Cone{fam, d, 0.0, start, 0});
+    } else {
+      for (int32_t i = 0; i < ncones; ++i) {
+        if (cones[i].type != fam || cones[i].dim == 0) continue;
+        cl.cones.push_back(Cone{fam, cones[i].dim, cones[i].alpha, (int64_t)hp.row_perm.size(), 0});
+        for (int64_t r = coff[i]; r < coff[i + 1]; ++r) hp.row_perm.push_back(r);
+      }
+    }
+    if (fam == CLR_SOC) cl.soc_end = (int64_t)cl.cones.size();
+    if (fam == CLR_EXP) cl.exp_end = (int64_t)cl.cones.size();
+    if (fam == CLR_POW) cl.pow_end = (int64_t)cl.cones.size();
+    if (fam == CLR_PSD_TRI) cl.psd_end = (int64_t)cl.cones.size();
+  }
+  cl.psd_k = psd_k;
+  cl.nu = 0;
+  cl.kval_z = 0;
+  for (Cone& c : cl.cones) {
+    c.kbase = cl.kval_z;
+    switch (c.type) {
+      case CLR_ZERO: cl.kval_z += c.dim; break;
+      case CLR_NONNEG: cl.kval_z += c.dim; cl.nu += c.dim; break;
+      case CLR_SOC: cl.kval_z += packed(c.dim); cl.nu += 1; cl.soc_max_dim = std::max(cl.soc_max_dim, c.dim); break;
+      case CLR_EXP: case CLR_POW: cl.kval_z += 6; cl.nu += 3; cl.symmetric_only = false; break;
+      case CLR_PSD_TRI: cl.kval_z += packed(c.dim); cl.nu += psd_k; break;
+    }
+  }
+
+  // ---- reordered A as CSR (unscaled) and full P as CSR ----
+  std::vector<int64_t> inv_row(m);
+  for (int64_t r = 0; r < m; ++r) inv_row[hp.row_perm[r]] = r;
+  Sparse& Ar = hp.A;
+  Ar = Sparse();
+  Ar.nrows = m;
+  Ar.ncols = n;
+  Ar.ptr.assign(m + 1, 0);
+  for (int64_t p = 0; p < A->nnz; ++p) Ar.ptr[inv_row[A->rowind[p]] + 1]++;
+  for (int64_t r = 0; r < m; ++r) Ar.ptr[r + 1] += Ar.ptr[r];
+  Ar.idx.resize(A->nnz);
+  Ar.val.resize(A->nnz);
+  {
+    std::vector<int64_t> next(Ar.ptr.begin(), Ar.ptr.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = A->colptr[j]; p < A->colptr[j + 1]; ++p) {
+        int64_t r = inv_row[A->rowind[p]];
+        Ar.idx[next[r]] = (int32_t)j;
+        Ar.val[next[r]++] = A->val[p];
+      }
+  }
+  // full symmetric P: upper entries (i <= j) plus their mirror
+  Sparse& Pf = hp.Pf;
+  Pf = Sparse();
+  Pf.nrows = Pf.ncols = n;
+  Pf.ptr.assign(n + 1, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = P->colptr[j]; p < P->colptr[j + 1]; ++p) {
+      int64_t i = P->rowind[p];
+      Pf.ptr[j + 1]++;
+      if (i != j) Pf.ptr[i + 1]++;
+    }
+  for (int64_t j = 0; j < n; ++j) Pf.ptr[j + 1] += Pf.ptr[j];
+  Pf.idx.resize(Pf.ptr[n]);
+  Pf.val.resize(Pf.ptr[n]);
+  {
+    // row j of the full matrix: entries (j, i) for i < j come from column j's upper part mirrored
+    // (P(i, j) stored in column j gives row i col j and row j col i).  Fill rows in column order so
+    // every row comes out sorted.
+    std::vector<int64_t> next(Pf.ptr.begin(), Pf.ptr.end() - 1);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = P->colptr[j]; p < P->colptr[j + 1]; ++p) {
+        int64_t i = P->rowind[p];  // i <= j
+        // row i gets column j (j >= i: appended in increasing j order)
+        Pf.idx[next[i]] = (int32_t)j;
+        Pf.val[next[i]++] = P->val[p];
+        if (i != j) {
+          // row j gets column i; columns i < j arrive in increasing i order for fixed j, and
+          // before any entry (j, j') with j' >= j is appended, since those come from column j' >= j.
+          Pf.idx[next[j]] = (int32_t)i;
+          Pf.val[next[j]++] = P->val[p];
+        }
+      }
+  }
+
+  // ---- modified Ruiz equilibration (reading of Alg. 1 step 1) ----
+  hp.D.assign(n, 1.0);
+  hp.E.assign(m, 1.0);
+  hp.c = 1.0;
+  std::vector<double> colx(n), rowz(m);
+  if (st.equilibrate) {
+    for (int pass = 0; pass < st.ruiz_passes; ++pass) {
+      std::fill(colx.begin(), colx.end(), 0.0);
+      std::fill(rowz.begin(), rowz.end(), 0.0);
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = Pf.ptr[i]; p < Pf.ptr[i + 1]; ++p) {
+          double v = std::fabs(hp.D[i] * Pf.val[p] * hp.D[Pf.idx[p]]);
+          colx[i] = std::max(colx[i], v);
+        }
+      for (int64_t r = 0; r < m; ++r)
+        for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) {
+          int64_t j = Ar.idx[p];
+          double v = std::fabs(hp.E[r] * Ar.val[p] * hp.D[j]);
+          colx[j] = std::max(colx[j], v);
+          rowz[r] = std::max(rowz[r], v);
+        }
+      for (const Cone& c : cl.cones) {
+        if (c.type == CLR_ZERO || c.type == CLR_NONNEG) continue;
+        double mx = 0.0;
+        for (int64_t r = c.off; r < c.off + c.dim; ++r) mx = std::max(mx, rowz[r]);
+        for (int64_t r = c.off; r < c.off + c.dim; ++r) rowz[r] = mx;
+      }
+      for (int64_t j = 0; j < n; ++j)
+        hp.D[j] = std::min(std::max(hp.D[j] * scale_factor(colx[j], st), st.scale_min), st.scale_max);
+      for (int64_t r = 0; r < m; ++r)
+        hp.E[r] = std::min(std::max(hp.E[r] * scale_factor(rowz[r], st), st.scale_min), st.scale_max);
+    }
+    // cost scaling
+    double sum = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      double mx = 0.0;
+      for (int64_t p = Pf.ptr[i]; p < Pf.ptr[i + 1]; ++p)
+        mx = std::max(mx, std::fabs(hp.D[i] * Pf.val[p] * hp.D[Pf.idx[p]]));
+      sum += mx;
+    }
+    double mean = n ? sum / (double)n : 0.0;
+    double qn = 0.0;
+    for (int64_t j = 0; j < n; ++j) qn = std::max(qn, std::fabs(hp.D[j] * q[j]));
+    double gamma = std::max(mean, qn);
+    hp.c = (gamma < 1e-8) ? 1.0 : 1.0 / std::min(std::max(gamma, st.scale_min), st.scale_max);
+  }
+  // ---- scale P, A; build A^T ----
+  hp.maxPdiag = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = Pf.ptr[i]; p < Pf.ptr[i + 1]; ++p) {
+      Pf.val[p] *= hp.c * hp.D[i] * hp.D[Pf.idx[p]];
+      if (Pf.idx[p] == i) hp.maxPdiag = std::max(hp.maxPdiag, std::fabs(Pf.val[p]));
+    }
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) Ar.val[p] *= hp.E[r] * hp.D[Ar.idx[p]];
+  Sparse& At = hp.At;
+  At = Sparse();
+  At.nrows = n;
+  At.ncols = m;
+  At.ptr.assign(n + 1, 0);
+  for (int64_t p = 0; p < Ar.nnz(); ++p) At.ptr[Ar.idx[p] + 1]++;
+  for (int64_t j = 0; j < n; ++j) At.ptr[j + 1] += At.ptr[j];
+  At.idx.resize(Ar.nnz());
+  At.val.resize(Ar.nnz());
+  {
+    std::vector<int64_t> next(At.ptr.begin(), At.ptr.end() - 1);
+    for (int64_t r = 0; r < m; ++r)
+      for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) {
+        int64_t j = Ar.idx[p];
+        At.idx[next[j]] = (int32_t)r;
+        At.val[next[j]++] = Ar.val[p];
+      }
+  }
+  int rcq = set_qb(hp, q, b);
+  if (rcq != CLR_OK) return rcq;
+
+  // ---- KKT lower triangle (CSC over KKT indices) and the kval layout ----
+  // x column j: P(i, j) for i >= j with an explicit diagonal, then A(:, j) as rows n + r.
+  // z block of each cone: packed lower triangle of its H block (column-major).
+  const int64_t N = n + m;
+  hp.kcol_ptr.assign(N + 1, 0);
+  hp.krow.clear();
+  hp.kval.clear();
+  hp.kdiag.assign(N, -1);
+  for (int64_t j = 0; j < n; ++j) {
+    // P row j == column j (symmetric); entries with index >= j
+    bool has_diag = false;
+    for (int64_t p = Pf.ptr[j]; p < Pf.ptr[j + 1]; ++p)
+      if (Pf.idx[p] == j) has_diag = true;
+    if (!has_diag) {
+      hp.kdiag[j] = (int64_t)hp.kval.size();
+      hp.krow.push_back(j);
+      hp.kval.push_back(0.0);
+    }
+    for (int64_t p = Pf.ptr[j]; p < Pf.ptr[j + 1]; ++p) {
+      int64_t i = Pf.idx[p];
+      if (i < j) continue;
+      if (i == j) hp.kdiag[j] = (int64_t)hp.kval.size();
+      hp.krow.push_back(i);
+      hp.kval.push_back(Pf.val[p]);
+    }
+    for (int64_t p = At.ptr[j]; p < At.ptr[j + 1]; ++p) {
+      hp.krow.push_back(n + At.idx[p]);
+      hp.kval.push_back(At.val[p]);
+    }
+    hp.kcol_ptr[j + 1] = (int64_t)hp.kval.size();
+  }
+  hp.kval_x = (int64_t)hp.kval.size();
+  // z columns: for each cone, columns off..off+dim-1; column c of a dense block has rows c..dim-1
+  int64_t zcol = n;
+  for (const Cone& c : cl.cones) {
+    bool dense = (c.type != CLR_ZERO && c.type != CLR_NONNEG);
+    for (int64_t a = 0; a < c.dim; ++a) {
+      const int64_t col = n + c.off + a;
+      hp.kdiag[col] = (int64_t)hp.kval.size();
+      int64_t last = dense ? c.dim : a + 1;
+      for (int64_t r = a; r < last; ++r) {
+        hp.krow.push_back(n + c.off + r);
+        hp.kval.push_back(0.0);
+      }
+      hp.kcol_ptr[col + 1] = (int64_t)hp.kval.size();
+      ++zcol;
+    }
+  }
+  (void)zcol;
+  return CLR_OK;
+}
+
+// q, b in the caller's order -> scaled, reordered copies and unscaled norms.
+int set_qb(HostProblem& hp, const double* q, const double* b) {
+  if ((hp.n && !q) || (hp.m && !b)) return CLR_E_INVALID;
+  if (!finite_all(q, hp.n) || !finite_all(b, hp.m)) return CLR_E_INVALID;
+  hp.q.resize(hp.n);
+  hp.b.resize(hp.m);
+  hp.qnorm = 0.0;
+  hp.bnorm = 0.0;
+  for (int64_t j = 0; j < hp.n; ++j) {
+    hp.q[j] = hp.c * hp.D[j] * q[j];
+    hp.qnorm = std::max(hp.qnorm, std::fabs(q[j]));
+  }
+  for (int64_t r = 0; r < hp.m; ++r) {
+    double v = b[hp.row_perm[r]];
+    hp.b[r] = hp.E[r] * v;
+    hp.bnorm = std::max(hp.bnorm, std::fabs(v));
+  }
+  return CLR_OK;
+}
+
+}  // namespace clr

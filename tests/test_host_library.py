@@ -1,0 +1,176 @@
+"""Host-side tests of the C-ABI library (no GPU): exported symbols, settings,
+input validation, equilibration against the oracle, and the symbolic
+factorization against an explicit symbolic elimination."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from oracle import ipm as OI
+from paper_2412_19027_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def clr():
+    from paper_2412_19027_gb300 import build
+    build.build()
+    from paper_2412_19027_gb300 import clr as mod
+    mod._lib()
+    return mod
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "clr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(clr_[a-z_0-9]+)\s*\(", text)) - {"clr_alloc_fn", "clr_free_fn"})
+
+
+def test_library_exports_every_declared_symbol(clr):
+    lib = clr._lib()
+    names = _declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(clr.EXPORTS)
+
+
+def test_default_settings_follow_the_paper(clr):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    s64, s32 = clr.clr_default_settings(64), clr.clr_default_settings(32)
+    assert s64.backtrack == g["backtrack_ratio"]["value"]
+    assert s64.step_fraction == g["step_fraction"]["value"]
+    assert s64.nbhd_beta == g["neighbourhood_beta"]["value"]
+    assert s64.ir_max_steps == g["ir_max_steps"]["value"]
+    assert s64.ir_abstol == g["ir_abstol"]["value"] and s64.ir_reltol == g["ir_reltol"]["value"]
+    assert s64.static_reg == g["static_reg_full"]["value"]
+    assert s32.static_reg == pytest.approx(g["static_reg_mixed"]["value"], rel=g["static_reg_mixed"]["rtol"])
+    assert s64.static_reg_dyn == pytest.approx(g["static_reg_dyn"]["value"], rel=1e-12)
+    # the same readings as the oracle's defaults
+    for bits, s in ((64, s64), (32, s32)):
+        o = oracle.default_settings(bits)
+        for key in ("eps_feas", "eps_inf", "max_iter", "static_reg", "static_reg_dyn", "dyn_reg_eps",
+                    "dyn_reg_delta", "ruiz_passes", "scale_min", "scale_max", "min_step"):
+            assert getattr(s, key) == pytest.approx(o[key], rel=1e-15), key
+    with pytest.raises(clr.ClrError):
+        clr.clr_default_settings(16)
+
+
+def test_validation_errors(clr):
+    prob = W.nonneg_qp(0)
+    with pytest.raises(clr.ClrError) as e:
+        clr.clr_analyze(prob.P, np.r_[prob.q[:-1], np.nan], prob.A, prob.b, prob.cones)
+    assert e.value.code == -1
+    with pytest.raises(clr.ClrError) as e:
+        clr.clr_analyze(prob.P, prob.q, prob.A, prob.b, [(1, 99, 0.0)])
+    assert e.value.code == -2
+    with pytest.raises(clr.ClrError) as e:
+        clr.clr_analyze(prob.P, prob.q, prob.A[:6], prob.b[:6], [(5, 3, 0.0), (5, 1, 0.0), (1, 2, 0.0)])
+    assert e.value.code == -3
+    with pytest.raises(clr.ClrError) as e:
+        clr.clr_analyze(prob.P, prob.q, prob.A[:3], prob.b[:3], [(4, 3, 1.5)])
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("make", [lambda: W.nonneg_qp(0),
+                                  lambda: W.mixed_cone(3, n=50, n_zero=7, n_nonneg=40, n_soc=6, n_exp=4, n_pow=4,
+                                                       nnz_per_col=4),
+                                  lambda: W.psd_batch(0, n=40, n_psd=3, psd_k=4, n_nonneg=10, nnz_per_col=4)])
+def test_equilibration_matches_oracle(clr, make):
+    prob = make()
+    s = clr.clr_analyze(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    D, E, c = s.scaling()
+    st = oracle.default_settings(64)
+    perm, K = OI.reorder_cones(prob.cones)
+    Pu = prob.P.toarray()
+    Pf = np.triu(Pu) + np.triu(Pu, 1).T
+    Dr, Er, cr = OI.equilibrate(Pf, prob.A.toarray()[perm], prob.q, K, st)
+    np.testing.assert_allclose(D, Dr, rtol=1e-13)
+    np.testing.assert_allclose(E, Er, rtol=1e-13)
+    assert c == pytest.approx(cr, rel=1e-13)
+    sym = s.symbolic()
+    np.testing.assert_array_equal(sym["row_perm"], perm)
+
+
+def _kkt_pattern(prob, perm_rows, cones):
+    """Lower pattern of K = [P A^T; A -H] with H's block structure (reordered rows)."""
+    n, m = prob.n, prob.m
+    Pu = sp.csc_matrix(prob.P)
+    A = sp.csr_matrix(prob.A)[perm_rows]
+    Hp = np.zeros((m, m), dtype=bool)
+    for (t, d, a, off) in cones:
+        if t in (0, 1):
+            for i in range(off, off + d):
+                Hp[i, i] = True
+        else:
+            Hp[off:off + d, off:off + d] = True
+    K = np.zeros((n + m, n + m), dtype=bool)
+    Pf = (Pu + Pu.T).toarray() != 0
+    K[:n, :n] = Pf | np.eye(n, dtype=bool)
+    K[n:, :n] = A.toarray() != 0
+    K[:n, n:] = K[n:, :n].T
+    K[n:, n:] = Hp
+    return K
+
+
+@pytest.mark.parametrize("make", [lambda: W.nonneg_qp(1),
+                                  lambda: W.mixed_cone(4, n=40, n_zero=6, n_nonneg=30, n_soc=5, n_exp=3, n_pow=3,
+                                                       nnz_per_col=4),
+                                  lambda: W.banded_lp(2, n=80, window=8)])
+def test_symbolic_factor_covers_fill(clr, make):
+    prob = make()
+    s = clr.clr_analyze(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    sym = s.symbolic()
+    stats = s.symbolic_stats()
+    N = stats["kkt_dim"]
+    perm = sym["perm"]
+    assert sorted(perm.tolist()) == list(range(N))
+    _, cones = OI.reorder_cones(prob.cones)
+    K = _kkt_pattern(prob, sym["row_perm"], cones)
+    Kp = K[np.ix_(perm, perm)]
+    # explicit symbolic elimination: column j of L = rows reached from j
+    L = np.tril(Kp).copy()
+    for j in range(N):
+        rows = np.nonzero(L[j + 1:, j])[0] + j + 1
+        for r in rows:
+            L[rows[rows > r], r] = True
+    snp, rp, rows = sym["sn_ptr"], sym["row_ptr"], sym["rows"]
+    owner = np.empty(N, dtype=np.int64)
+    for J in range(len(snp) - 1):
+        owner[snp[J]:snp[J + 1]] = J
+        fr = rows[rp[J]:rp[J + 1]]
+        assert list(fr[: snp[J + 1] - snp[J]]) == list(range(snp[J], snp[J + 1]))  # own columns first
+        assert np.all(np.diff(fr) > 0)
+    for j in range(N):
+        J = owner[j]
+        fr = set(rows[rp[J]:rp[J + 1]].tolist())
+        need = set(np.nonzero(L[:, j])[0].tolist())
+        assert need <= fr, (j, need - fr)
+    # every child's update rows lie in its parent's front
+    par = sym["sn_parent"]
+    for J in range(len(par)):
+        if par[J] >= 0:
+            c = snp[J + 1] - snp[J]
+            upd = set(rows[rp[J] + c:rp[J + 1]].tolist())
+            assert upd <= set(rows[rp[par[J]]:rp[par[J] + 1]].tolist())
+        else:
+            assert rp[J + 1] - rp[J] == snp[J + 1] - snp[J]  # roots have no update rows
+    # nnz(L) agrees with the explicit elimination when supernodes add no explicit zeros
+    assert stats["l_nnz"] >= int(np.count_nonzero(np.tril(L)))
+
+
+def test_analysis_of_full_size_mixed_cone_problem(clr):
+    """The 2000 dense x columns of the mixed-cone QP (P = diag + rank 10) form one
+    root front; the constraint rows are eliminated first."""
+    prob = W.mixed_cone(0)
+    s = clr.clr_analyze(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    st = s.symbolic_stats()
+    assert st["kkt_dim"] == 8600
+    assert st["max_front"] == 2000
+    assert st["n_levels"] <= 8
+    assert st["front_pool_entries"] < 10_000_000
