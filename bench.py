@@ -1,0 +1,332 @@
+"""Benchmark of the GPU interior-point solver (one JSON line on rank 0).
+
+A step is one complete solve (initial point, then IPM iterations until the
+termination tests pass at eps_feas = 1e-8) of the mixed-cone QP workload:
+n = 2000, m = 6600 (500 zero, 3000 nonneg, 500 SOC(5), 100 exp, 100
+pow(0.3) rows/cones), P = diag + rank 10, A with 10 nnz per column, built
+from a planted optimum (seeded synthetic data).  Every step passes through
+all rows of the per-iteration device path.
+
+metric  IPM iterations per second (total iterations / device time), for the
+        FP32-factor + FP64-refinement path; the FP64-factor path is measured
+        in the same run and reported under "fp64_factor"; time-to-1e-8 of
+        both under "time_to_tol_ms".
+N > 1   independent replicas, one problem per GPU (weak scaling, no
+        collective on the data path).
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IPM iterations/s to eps_feas=1e-8 (time-to-1e-8 in time_to_tol_ms)"
+UNIT = "iter/s"
+WORKLOAD = "mixed-cone QP n=2000 m=6600 (500 zero, 3000 nonneg, 500 SOC5, 100 exp, 100 pow0.3), P=diag+rank10"
+FP64_PEAK_TFLOPS = 1.25            # GB300 FP64 (FFMA and DMMA), nominal
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--factor-bits", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--ir-stop-ratio", type=float, default=None)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seed, iters=2):
+    """The oracle, as it stands, on the host cores: a bounded sample of the
+    workload (its first `iters` IPM iterations; setup time subtracted)."""
+    code = r"""
+import sys, time, json
+sys.path.insert(0, %r)
+import oracle
+from paper_2412_19027_gb300 import workloads as W
+prob = W.mixed_cone(%d)
+t0 = time.perf_counter(); oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=0)); t1 = time.perf_counter()
+r = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=%d)); t2 = time.perf_counter()
+print(json.dumps(dict(iters=r.iterations, setup=t1 - t0, total=t2 - t1)))
+""" % (ROOT, seed, iters)
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    t = max(d["total"] - d["setup"], 1e-9)
+    return {"value": d["iters"] / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d IPM iterations of the same workload (FP64 NumPy/LAPACK oracle, dense KKT "
+                      "8600x8600), setup time subtracted; %.1f s of CPU work" % (d["iters"], d["total"])}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    iters_per_step = 1
+    sample_times = []
+    code_iters = 0
+    import oracle
+    from paper_2412_19027_gb300 import workloads as W
+    prob = W.mixed_cone(args.seed)
+    t0 = time.perf_counter()
+    oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=0))
+    setup = time.perf_counter() - t0
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        r = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=iters_per_step))
+        dt = time.perf_counter() - t - setup
+        if k >= args.warmup:
+            sample_times.append(max(dt, 1e-9))
+            code_iters += r.iterations
+    total = sum(sample_times)
+    value = code_iters / total
+    cores = os.cpu_count() or 1
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "seed": args.seed,
+                       "step": "one IPM iteration of the oracle (bounded sample of the solve)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": "%d steps x %d IPM iteration(s), setup subtracted" % (args.steps,
+                                                                                            iters_per_step)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2412_19027_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    from paper_2412_19027_gb300 import clr, workloads as W
+    prob = W.mixed_cone(args.seed + rank)
+    n, m = prob.n, prob.m
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+
+    def make(bits):
+        kw = {}
+        if args.ir_stop_ratio is not None:
+            kw["ir_stop_ratio"] = args.ir_stop_ratio
+        st = clr.clr_default_settings(bits, **kw)
+        s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+        s.set_stream(stream.cuda_stream)
+        return s
+
+    def timed(solver, steps, warmup):
+        for _ in range(warmup):
+            solver.solve()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        iters, launches, perfs, infos = 0, 0, [], []
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                starts[k].record(stream)
+            solver.solve()
+            ends[k].record(stream)
+            info = solver.info()
+            p = solver.perf()
+            iters += info["iterations"]
+            launches += p["kernel_launches"]
+            perfs.append(p)
+            infos.append(info)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        times = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+        return times, iters, launches, perfs, infos
+
+    main = make(args.factor_bits)
+    sym = main.symbolic_stats()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, iters, launches, perfs, infos = timed(main, args.steps, args.warmup)
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if ws > 1:
+        t = torch.tensor([total_ms, float(iters)], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        total_ms_max, iters_all = float(tmax[0]), float(tsum[1])
+    else:
+        total_ms_max, iters_all = total_ms, float(iters)
+    value = iters_all / (total_ms_max / 1e3)
+    x, s_, z, info = main.solution()
+    f_star = prob.objective(prob.x_star)
+    obj_err = abs(prob.objective(x) - f_star) / max(1.0, abs(f_star))
+
+    # the FP64-factor path on the same problem
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = main if args.factor_bits == 64 else make(64)
+        t64, it64, _, p64, inf64 = timed(s64, args.fp64_steps, 1)
+        x64, _, _, _ = s64.solution()
+        fp64 = {"time_to_tol_ms": float(np.median(t64)), "iterations": inf64[-1]["iterations"],
+                "iters_per_s": it64 / (sum(t64) / 1e3), "status": inf64[-1]["status_name"],
+                "objective_rel_err_vs_planted": abs(prob.objective(x64) - f_star) / max(1.0, abs(f_star)),
+                "factor_ms_per_factorization": p64[-1]["factor_ms"] / max(1, p64[-1]["factorizations"])}
+        if s64 is not main:
+            s64.free()
+
+    # end to end through the C ABI with host buffers: q, b in; x, s, z out
+    e2e = None
+    if not args.no_e2e:
+        e_iters, e_time = 0, 0.0
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            main.update_qb(prob.q, prob.b)
+            main.solve()
+            xo, so, zo, info_e = main.solution()
+            e_time += time.perf_counter() - t0
+            e_iters += info_e["iterations"]
+        e2e = {"value": e_iters / e_time, "unit": UNIT, "h2d_bytes_per_step": 8 * (n + m),
+               "d2h_bytes_per_step": 8 * (n + 2 * m)}
+
+    # dominant phase and its roofline
+    p = perfs[-1]
+    nf = max(1, p["factorizations"])
+    phases = {"residuals+cones": p["resid_cones_ms"], "factorization": p["factor_ms"],
+              "solves+steps": p["solve_step_ms"], "init": p["init_ms"]}
+    fact_ms = p["factor_ms"] / nf
+    peak = FP32_PEAK_TFLOPS if args.factor_bits == 32 else FP64_PEAK_TFLOPS
+    achieved = sym["factor_flops"] / (fact_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "numeric LDL^T (multifrontal, FP%d)" % args.factor_bits,
+                "flops_per_launch": sym["factor_flops"], "ms_per_launch": fact_ms,
+                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if args.factor_bits == 32
+                                                else "GB300 FP64 nominal 1.25 TFLOP/s")}
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            try:
+                cpu = cpu_baseline(args.seed)
+            except Exception as e:  # the baseline is informative only
+                cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                       "sample": "failed: %s" % str(e)[:200]}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 (f%d factor)" % args.factor_bits, "data": "synthetic",
+                "config": {"workload": WORKLOAD, "seed": args.seed, "factor_bits": args.factor_bits,
+                           "eps_feas": 1e-8, "l2": "flushed (256 MB write) before every timed solve",
+                           "parallelism": "replicas" if ws > 1 else "single GPU",
+                           "ir_stop_ratio": main.settings.ir_stop_ratio},
+                "time_to_tol_ms": {"median": float(np.median(times)), "fp64_factor": fp64["time_to_tol_ms"] if fp64
+                                   else None},
+                "iterations": infos[-1]["iterations"], "status": infos[-1]["status_name"],
+                "objective_rel_err_vs_planted": obj_err, "res_primal": infos[-1]["res_primal"],
+                "res_dual": infos[-1]["res_dual"], "ir_steps_total": infos[-1]["ir_steps_total"],
+                "fp64_factor": fp64, "phase_ms_per_solve": phases, "roofline": roofline,
+                "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+                "symbolic": {k: sym[k] for k in ("kkt_dim", "l_nnz", "factor_flops", "n_supernodes", "n_levels",
+                                                 "max_front")}}
+        print(json.dumps(line), flush=True)
+    main.free()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

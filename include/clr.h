@@ -96,6 +96,7 @@ typedef struct {
   int32_t ir_max_steps;   /* T_max = 10 (Sec. 3.6) */
   double ir_abstol;       /* t_abs = 1e-12 (Sec. 3.6) */
   double ir_reltol;       /* t_rel = 1e-12 (Sec. 3.6) */
+  double ir_stop_ratio;   /* 0 (off): else stop refining once a step reduces ||r|| by less than this factor */
   int32_t equilibrate;    /* 1: modified Ruiz scaling at setup (Alg. 1 step 1) */
   int32_t ruiz_passes;    /* 10 */
   double scale_min;       /* 1e-4: clamp of every equilibration factor */
@@ -136,6 +137,19 @@ typedef struct {
   int64_t front_pool_entries; /* entries of the frontal-matrix pool */
   int64_t n_dense_rows;    /* rows treated as dense by the ordering */
 } clr_symbolic_stats;
+
+/* Device-side timing of the last clr_solve, from CUDA events recorded inside
+ * the captured graphs on the solver's stream. */
+typedef struct {
+  int64_t kernel_launches;  /* kernels launched by the last solve (graph nodes x replays) */
+  int32_t iterations;
+  int32_t factorizations;   /* numeric factorizations (initialisation included) */
+  double init_ms;           /* initial point (incl. its factorization and solves) */
+  double resid_cones_ms;    /* residuals, termination tests, scaling H (all iterations) */
+  double factor_ms;         /* numeric LDL^T (all iterations) */
+  double solve_step_ms;     /* KKT solves with refinement, directions, step lengths, update */
+  double factor_flops;      /* flops of one numeric factorization (symbolic count) */
+} clr_perf;
 
 typedef struct clr_solver clr_solver;
 
@@ -185,6 +199,9 @@ int clr_get_solution(const clr_solver* s, double* x, double* sl, double* z, clr_
 int clr_update_qb(clr_solver* s, const double* q, const double* b);
 
 int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out);
+
+/* Device timing and launch count of the last clr_solve (CLR_E_STATE before it). */
+int clr_get_perf(const clr_solver* s, clr_perf* out);
 
 /* Export the symbolic factorization for inspection.  perm (length N): the
  * fill-reducing order, perm[k] = KKT index eliminated k-th (KKT index i < n is

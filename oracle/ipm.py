@@ -70,7 +70,7 @@ def default_settings(factor_bits=64):
         static_reg_dyn=EPS64 ** 2,
         dyn_reg_eps=1e-6 if low else 1e-13,
         dyn_reg_delta=1e-4 if low else 2e-7,
-        ir_max_steps=10, ir_abstol=1e-12, ir_reltol=1e-12,
+        ir_max_steps=10, ir_abstol=1e-12, ir_reltol=1e-12, ir_stop_ratio=0.0,
         equilibrate=True, ruiz_passes=10, scale_min=1e-4, scale_max=1e4,
         step_fraction=0.99, backtrack=0.8, nbhd_beta=1e-6, min_step=1e-10,
     )

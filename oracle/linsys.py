@@ -12,7 +12,9 @@ Follows Sec. 3.6 "Solving linear systems" of the paper:
   absolute constants, a reading: the paper scales only the static term);
 * iterative refinement: x0 = (LDL^T)^{-1} b, then r = b - K x on the
   UNREGULARISED K in FP64, stop when ||r||_inf <= t_abs + t_rel ||b||_inf or
-  after T_max refinement steps, else x += (LDL^T)^{-1} r.
+  after T_max refinement steps, else x += (LDL^T)^{-1} r.  An optional stall
+  test (setting ir_stop_ratio > 0, off by default, not in the paper) also
+  stops once a step has reduced ||r||_inf by less than that factor.
 
 Two factorizations are provided:
 * ``ldl_factor``: the unpivoted LDL^T with dynamic regularisation, in the
@@ -80,6 +82,7 @@ class KKTSolver:
         self.ir_max = settings["ir_max_steps"]
         self.ir_abs = settings["ir_abstol"]
         self.ir_rel = settings["ir_reltol"]
+        self.ir_stop = settings.get("ir_stop_ratio", 0.0)
         self.ir_steps = 0
 
     def _solve_reg(self, r):
@@ -99,10 +102,15 @@ class KKTSolver:
     def solve(self, rhs):
         x = self._solve_reg(rhs)
         bnorm = float(np.max(np.abs(rhs))) if len(rhs) else 0.0
+        prev = np.inf
         for _ in range(self.ir_max):
             r = rhs - self.K @ x
-            if float(np.max(np.abs(r))) <= self.ir_abs + self.ir_rel * bnorm:
+            rn = float(np.max(np.abs(r)))
+            if rn <= self.ir_abs + self.ir_rel * bnorm:
                 break
+            if self.ir_stop > 0 and not (rn * self.ir_stop < prev):
+                break  # optional stall test: the last step gained less than ir_stop_ratio
+            prev = rn
             x = x + self._solve_reg(r)
             self.ir_steps += 1
         return x

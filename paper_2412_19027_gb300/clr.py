@@ -38,7 +38,8 @@ class clr_settings(C.Structure):
     _fields_ = [("eps_feas", C.c_double), ("eps_inf", C.c_double), ("max_iter", C.c_int32),
                 ("factor_bits", C.c_int32), ("static_reg", C.c_double), ("static_reg_dyn", C.c_double),
                 ("dyn_reg_eps", C.c_double), ("dyn_reg_delta", C.c_double), ("ir_max_steps", C.c_int32),
-                ("ir_abstol", C.c_double), ("ir_reltol", C.c_double), ("equilibrate", C.c_int32),
+                ("ir_abstol", C.c_double), ("ir_reltol", C.c_double), ("ir_stop_ratio", C.c_double),
+                ("equilibrate", C.c_int32),
                 ("ruiz_passes", C.c_int32), ("scale_min", C.c_double), ("scale_max", C.c_double),
                 ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
                 ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32)]
@@ -59,9 +60,15 @@ class clr_symbolic_stats(C.Structure):
                 ("n_dense_rows", C.c_int64)]
 
 
+class clr_perf(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("iterations", C.c_int32), ("factorizations", C.c_int32),
+                ("init_ms", C.c_double), ("resid_cones_ms", C.c_double), ("factor_ms", C.c_double),
+                ("solve_step_ms", C.c_double), ("factor_flops", C.c_double)]
+
+
 _LIB = None
 EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr_get_solution", "clr_update_qb",
-           "clr_get_symbolic_stats", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
+           "clr_get_symbolic_stats", "clr_get_perf", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
            "clr_set_allocator", "clr_free", "clr_error_string", "clr_status_string", "clr_last_cuda_error",
            "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_ldl_solve"]
 
@@ -82,6 +89,7 @@ def _lib():
         L.clr_get_solution.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double), P(clr_info)]
         L.clr_update_qb.argtypes = [vp, P(C.c_double), P(C.c_double)]
         L.clr_get_symbolic_stats.argtypes = [vp, P(clr_symbolic_stats)]
+        L.clr_get_perf.argtypes = [vp, P(clr_perf)]
         L.clr_get_symbolic.argtypes = [vp] + [P(C.c_int64)] * 7
         L.clr_get_scaling.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double)]
         L.clr_get_history.argtypes = [vp, P(C.c_double), C.c_int32, P(C.c_int32)]
@@ -207,6 +215,11 @@ class Solver:
         s = clr_symbolic_stats()
         _check(_lib().clr_get_symbolic_stats(self.h, C.byref(s)), "clr_get_symbolic_stats")
         return {name: getattr(s, name) for name, _ in clr_symbolic_stats._fields_}
+
+    def perf(self):
+        s = clr_perf()
+        _check(_lib().clr_get_perf(self.h, C.byref(s)), "clr_get_perf")
+        return {name: getattr(s, name) for name, _ in clr_perf._fields_}
 
     def symbolic(self):
         st = self.symbolic_stats()

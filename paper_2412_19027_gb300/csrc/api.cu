@@ -36,6 +36,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.ir_max_steps = 10;
   s.ir_abstol = 1e-12;
   s.ir_reltol = 1e-12;
+  s.ir_stop_ratio = 0.0;
   s.equilibrate = 1;
   s.ruiz_passes = 10;
   s.scale_min = 1e-4;
@@ -52,7 +53,8 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
 
 static int check_settings(const clr_settings& s) {
   if (s.factor_bits != 64 && s.factor_bits != 32) return CLR_E_INVALID;
-  if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0)
+  if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0 ||
+      !(s.ir_stop_ratio >= 0))
     return CLR_E_INVALID;
   if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
   if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;
@@ -125,6 +127,13 @@ int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out) {
   r.front_pool_entries = v.sy.pool;
   r.n_dense_rows = v.sy.n_dense;
   *out = r;
+  return CLR_OK;
+}
+
+int clr_get_perf(const clr_solver* s, clr_perf* out) {
+  if (!s || !out) return CLR_E_INVALID;
+  if (!s->impl.solved_once) return CLR_E_STATE;
+  *out = s->impl.perf;
   return CLR_OK;
 }
 

@@ -244,6 +244,7 @@ __global__ void k_ir_begin(IterScal* sc, const unsigned long long* rhsmax) {
   sc->ir_skip = sc->halt;
   sc->ir_cur = 0;
   sc->rhs_norm = bitsd(*rhsmax);
+  sc->ir_prev = INFINITY;
 }
 
 template <typename T>
@@ -253,11 +254,15 @@ __global__ void k_set_from(double* __restrict__ dst, const T* __restrict__ src, 
     dst[i] = add ? dst[i] + (double)src[i] : (double)src[i];
 }
 
-__global__ void k_ir_check(IterScal* sc, unsigned long long* rmax, double abstol, double reltol) {
+// Refinement stops at the tolerance (Sec. 3.6), or, when stop_ratio > 0, as soon as a
+// step has reduced ||r||_inf by less than stop_ratio (the last correction is kept).
+__global__ void k_ir_check(IterScal* sc, unsigned long long* rmax, double abstol, double reltol, double stop_ratio) {
   if (sc->ir_skip) return;
   const double r = bitsd(*rmax);
   *rmax = 0ull;
-  if (!(r > abstol + reltol * sc->rhs_norm)) sc->ir_skip = 1;  // converged (NaN also stops)
+  const bool stalled = stop_ratio > 0 && !(r * stop_ratio < sc->ir_prev);
+  sc->ir_prev = r;
+  if (!(r > abstol + reltol * sc->rhs_norm) || stalled) sc->ir_skip = 1;  // converged (NaN also stops)
   else {
     sc->ir_cur += 1;
     sc->ir_total += 1;
@@ -482,9 +487,45 @@ void DeviceArena::release() {
   nblocks_ = cap_ = total_ = 0;
 }
 
-Solver::~Solver() {
+void Solver::drop_graphs() {
   if (gexec_) cudaGraphExecDestroy(gexec_);
   if (graph_) cudaGraphDestroy(graph_);
+  if (igexec_) cudaGraphExecDestroy(igexec_);
+  if (igraph_) cudaGraphDestroy(igraph_);
+  gexec_ = nullptr;
+  graph_ = nullptr;
+  igexec_ = nullptr;
+  igraph_ = nullptr;
+}
+
+// Event marks: 0/1 bracket the initialisation, 2 = iteration start, 3 = before the
+// factorization, 4 = after it, 5 = iteration end.
+void Solver::mark(int i) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(stream_, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev_[i], stream_, cudaEventRecordExternal);
+  else cudaEventRecord(ev_[i], stream_);
+}
+
+namespace {
+int64_t count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  int64_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+}  // namespace
+
+Solver::~Solver() {
+  drop_graphs();
+  for (cudaEvent_t e : ev_)
+    if (e) cudaEventDestroy(e);
   if (sc_host_) cudaFreeHost(sc_host_);
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
 }
@@ -510,6 +551,7 @@ int Solver::upload() {
     own_stream_ = true;
   }
   CLR_CUDA(cudaMallocHost(&sc_host_, sizeof(IterScal)));
+  for (cudaEvent_t& e : ev_) CLR_CUDA(cudaEventCreate(&e));
   // expected pivot sign by elimination position: + for x, - for z
   std::vector<int8_t> dsign(N);
   for (int64_t k = 0; k < N; ++k) dsign[k] = sy.perm[k] < n ? 1 : -1;
@@ -640,14 +682,7 @@ int Solver::upload() {
 }
 
 int Solver::set_stream(void* stream) {
-  if (gexec_) {
-    cudaGraphExecDestroy(gexec_);
-    gexec_ = nullptr;
-  }
-  if (graph_) {
-    cudaGraphDestroy(graph_);
-    graph_ = nullptr;
-  }
+  drop_graphs();
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
   own_stream_ = false;
   stream_ = (cudaStream_t)stream;
@@ -695,7 +730,7 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
       case 8: k_kmv<8><<<kg, 256, 0, s>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
       default: k_kmv<4><<<kg, 256, 0, s>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
     }
-    k_ir_check<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol);
+    k_ir_check<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio);
     if (st.factor_bits == 64) {
       int rc = f64_.solve(s, v_.r, irs);
       if (rc) return rc;
@@ -783,6 +818,7 @@ int Solver::iteration() {
   const int* halt = &sc_->halt;
   unsigned long long* maxb = reinterpret_cast<unsigned long long*>(v_.r);  // r is free here; 8 slots
   int rc;
+  mark(2);
   // ---- residuals, objectives, mu, termination ----
   kmv(csr_group_, s, 0, 0, N, n, v_, v_.xz, v_.lo, v_.hi, nullptr, nullptr, halt);
   CLR_CUDA(cudaMemsetAsync(maxb, 0, sizeof(unsigned long long) * M_NMAX, s));
@@ -797,8 +833,10 @@ int Solver::iteration() {
   if (rc) return rc;
   k_fin_delta<<<1, 1, 0, s>>>(sc_, st.static_reg, st.static_reg_dyn, hp.maxPdiag, halt);
   // ---- step 5: factor ----
+  mark(3);
   rc = factor();
   if (rc) return rc;
+  mark(4);
   // ---- constant right-hand side [-q; b] ----
   k_build_rhs_init<<<grid_for(N, 256), 256, 0, s>>>(v_.rhs, v_.q, v_.b, n, m, 1);
   // k_build_rhs_init(which=1) gives [-q; 0]; add b on the z part
@@ -829,6 +867,7 @@ int Solver::iteration() {
   k_update<<<grid_for(N, 256), 256, 0, s>>>(v_.xz, v_.s, v_.dir, v_.ds, N, m, sc_, st.step_fraction, halt);
   const int* dh = (st.factor_bits == 64) ? f64_.dyn_hits : f32_.dyn_hits;
   k_fin_update<<<1, 1, 0, s>>>(sc_, st.step_fraction, dh, halt);
+  mark(5);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -836,6 +875,7 @@ int Solver::iteration() {
 int Solver::initialise() {
   const int64_t n = hp.n, m = hp.m, N = n + m;
   cudaStream_t s = stream_;
+  mark(0);
   k_init_scal<<<1, 1, 0, s>>>(sc_);
   CLR_CUDA(cudaMemsetAsync(v_.xz, 0, sizeof(double) * (size_t)N, s));
   CLR_CUDA(cudaMemsetAsync(v_.s, 0, sizeof(double) * (size_t)m, s));
@@ -864,6 +904,7 @@ int Solver::initialise() {
     if (rc) return rc;
   }
   k_init_scal<<<1, 1, 0, s>>>(sc_);  // tau = kappa = 1, counters reset (ir_total of the init dropped)
+  mark(1);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -884,26 +925,71 @@ int Solver::launch_iteration() {
       return CLR_E_CUDA;
     }
     graph_ = g;
+    iter_kernels_ = count_kernel_nodes(graph_);
     CLR_CUDA(cudaGraphInstantiate(&gexec_, graph_, 0));
   }
   CLR_CUDA(cudaGraphLaunch(gexec_, stream_));
   return CLR_OK;
 }
 
+int Solver::launch_init() {
+  if (!st.use_graph) return initialise();
+  if (!igexec_) {
+    CLR_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+    int rc = initialise();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(stream_, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) {
+      set_cuda_error(e, "cudaStreamEndCapture");
+      return CLR_E_CUDA;
+    }
+    igraph_ = g;
+    init_kernels_ = count_kernel_nodes(igraph_);
+    CLR_CUDA(cudaGraphInstantiate(&igexec_, igraph_, 0));
+  }
+  CLR_CUDA(cudaGraphLaunch(igexec_, stream_));
+  return CLR_OK;
+}
+
 int Solver::solve() {
   if (!device_ready) return CLR_E_STATE;
   auto t0 = std::chrono::steady_clock::now();
-  int rc = initialise();
+  perf = clr_perf{};
+  int rc = launch_init();
   if (rc) return rc;
+  perf.kernel_launches += init_kernels_;
+  perf.factorizations += hp.cl.symmetric_only ? 1 : 0;
+  bool first = true;
   int status = 0;
   for (int it = 0; it <= st.max_iter + 1; ++it) {
     rc = launch_iteration();
     if (rc) return rc;
+    perf.kernel_launches += iter_kernels_;
     CLR_CUDA(cudaMemcpyAsync(sc_host_, sc_, sizeof(IterScal), cudaMemcpyDeviceToHost, stream_));
     CLR_CUDA(cudaStreamSynchronize(stream_));
+    float ms = 0.f;
+    if (first) {
+      if (cudaEventElapsedTime(&ms, ev_[0], ev_[1]) == cudaSuccess) perf.init_ms += ms;
+      first = false;
+    }
     status = sc_host_->status;
+    if (status == 0 || status == CLR_INSUFFICIENT_PROGRESS) {
+      // a full iteration ran (or stopped at its step-length test, after the factorization)
+      if (cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) perf.resid_cones_ms += ms;
+      if (cudaEventElapsedTime(&ms, ev_[3], ev_[4]) == cudaSuccess) perf.factor_ms += ms;
+      if (cudaEventElapsedTime(&ms, ev_[4], ev_[5]) == cudaSuccess) perf.solve_step_ms += ms;
+      perf.factorizations += 1;
+    } else if (cudaEventElapsedTime(&ms, ev_[2], ev_[5]) == cudaSuccess) {
+      perf.resid_cones_ms += ms;  // the terminating pass only evaluates the residuals
+    }
     if (status != 0) break;
   }
+  perf.iterations = sc_host_->iter;
+  perf.factor_flops = sy.flops;
   CLR_CUDA(cudaStreamSynchronize(stream_));
   solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   const IterScal& h = *sc_host_;

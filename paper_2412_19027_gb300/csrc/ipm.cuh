@@ -33,7 +33,7 @@ struct IterScal {
   double mu_coef[3];
   // iterative refinement
   int ir_skip, ir_steps, ir_total, ir_cur;
-  double rhs_norm;
+  double rhs_norm, ir_prev;
   unsigned long long rnorm_bits;
   int dyn_hits, pad1;
 };
@@ -69,6 +69,7 @@ class Solver {
   double setup_s = 0, solve_s = 0;
   int last_status = 0, last_iters = 0;
   clr_info info{};
+  clr_perf perf{};
   std::vector<double> history;  // rows of 12
   std::string err;
 
@@ -95,6 +96,13 @@ class Solver {
   int csr_group_ = 32;
   cudaGraph_t graph_ = nullptr;
   cudaGraphExec_t gexec_ = nullptr;
+  cudaGraph_t igraph_ = nullptr;
+  cudaGraphExec_t igexec_ = nullptr;
+  int64_t iter_kernels_ = 0, init_kernels_ = 0;
+  cudaEvent_t ev_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void mark(int i);
+  void drop_graphs();
+  int launch_init();
 
   int factor();
   int kkt_solve(const double* rhs, double* sol);
