@@ -148,9 +148,11 @@ __device__ void central_point(bool is_exp, double a, const double* exp_c, double
   }
 }
 
-// z~ = -grad f*(s): damped Newton on f(u) + <s, u>, started at the central point.
-__device__ bool dual_shadow(bool is_exp, const double* s, double a, const double* exp_c, double* u) {
-  central_point(is_exp, a, exp_c, u);
+// z~ = -grad f*(s): damped Newton on f(u) + <s, u> from `start` (a point of int K*).
+__device__ bool dual_shadow(bool is_exp, const double* s, double a, const double* start, double* u) {
+  u[0] = start[0];
+  u[1] = start[1];
+  u[2] = start[2];
   for (int it = 0; it < 100; ++it) {
     double g[3], H[3][3], du[3], mg[3];
     barrier_grad(is_exp, u, a, g);
@@ -180,15 +182,15 @@ __device__ void inv2(const double M[2][2], double R[2][2]) {
   R[1][0] = -M[1][0] / det;
 }
 
-__device__ void bfgs_H(bool is_exp, const double* s, const double* z, double mu, double a, const double* exp_c,
-                       double H[3][3]) {
-  double g[3], Ha[3][3], st[3], zt[3];
+__device__ void bfgs_H(bool is_exp, const double* s, const double* z, double mu, double a, const double* start,
+                       double H[3][3], double* zt) {
+  double g[3], Ha[3][3], st[3];
   barrier_grad(is_exp, z, a, g);
   for (int i = 0; i < 3; ++i) st[i] = -g[i];
   barrier_hess(is_exp, z, a, Ha);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) Ha[i][j] *= mu;
-  const bool ok = dual_shadow(is_exp, s, a, exp_c, zt);
+  const bool ok = dual_shadow(is_exp, s, a, start, zt);
   const double sz = s[0] * z[0] + s[1] * z[1] + s[2] * z[2];
   const double stzt = st[0] * zt[0] + st[1] * zt[1] + st[2] * zt[2];
   if (!ok || !(1.0 - 9.0 / (sz * stzt) > kBfgsDegeneracy)) {
@@ -337,8 +339,15 @@ __global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const d
   const int64_t kb = is_exp ? cd.exp_kb0 + 6 * i : cd.pow_kb0 + 6 * i;
   const double a = is_exp ? 0.0 : cd.pow_alpha[i];
   double sv[3] = {s[row], s[row + 1], s[row + 2]}, zv[3] = {z[row], z[row + 1], z[row + 2]};
-  double H[3][3];
-  bfgs_H(is_exp, sv, zv, *mu_p, a, cd.exp_center, H);
+  double H[3][3], zt[3];
+  double* zs = cd.ep_zt + 3 * t;
+  const double start[3] = {zs[0], zs[1], zs[2]};
+  bfgs_H(is_exp, sv, zv, *mu_p, a, start, H, zt);
+  if (isfinite(zt[0]) && isfinite(zt[1]) && isfinite(zt[2]) && in_int_dual(is_exp, zt, a)) {
+    zs[0] = zt[0];
+    zs[1] = zt[1];
+    zs[2] = zt[2];
+  }
   int q = 0;
   double mx = 0.0;
   for (int c = 0; c < 3; ++c)
@@ -789,48 +798,132 @@ int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, co
   return CLR_OK;
 }
 
-__global__ void k_step_nonsym(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
+namespace {
+struct NsCone {
+  bool is_exp;
+  double a, sv[3], zv[3], dsv[3], dzv[3];
+  const double* zt0;
+};
+__device__ NsCone load_cone(const ConeDev& cd, int64_t t, const double* s, const double* ds, const double* z,
+                            const double* dz) {
+  NsCone c;
+  c.is_exp = t < cd.n_exp;
+  const int64_t i = c.is_exp ? t : t - cd.n_exp;
+  const int64_t row = c.is_exp ? cd.exp_row0 + 3 * i : cd.pow_row0 + 3 * i;
+  c.a = c.is_exp ? 0.0 : cd.pow_alpha[i];
+  for (int q = 0; q < 3; ++q) {
+    c.sv[q] = s[row + q];
+    c.zv[q] = z[row + q];
+    c.dsv[q] = ds[row + q];
+    c.dzv[q] = dz[row + q];
+  }
+  c.zt0 = cd.ep_zt + 3 * t;
+  return c;
+}
+__device__ bool ns_interior(const NsCone& c, double alpha) {
+  double sc[3], zc[3];
+  for (int q = 0; q < 3; ++q) {
+    sc[q] = c.sv[q] + alpha * c.dsv[q];
+    zc[q] = c.zv[q] + alpha * c.dzv[q];
+  }
+  return in_int_primal(c.is_exp, sc, c.a) && in_int_dual(c.is_exp, zc, c.a);
+}
+// nu <grad f*(s), grad f(z)>^{-1} >= beta mu at the trial point (nu = 3)
+__device__ bool ns_nbhd(const NsCone& c, double alpha, const double* mu_coef, double beta) {
+  double sc[3], zc[3], zt[3], g[3];
+  for (int q = 0; q < 3; ++q) {
+    sc[q] = c.sv[q] + alpha * c.dsv[q];
+    zc[q] = c.zv[q] + alpha * c.dzv[q];
+  }
+  const double mu_t = mu_coef[0] + alpha * (mu_coef[1] + alpha * mu_coef[2]);
+  const double start[3] = {c.zt0[0], c.zt0[1], c.zt0[2]};
+  dual_shadow(c.is_exp, sc, c.a, start, zt);
+  barrier_grad(c.is_exp, zc, c.a, g);
+  const double dot = -(zt[0] * g[0] + zt[1] * g[1] + zt[2] * g[2]);  // <z~, s~>, s~ = -grad f(z)
+  return 3.0 / dot >= beta * mu_t;
+}
+}  // namespace
+
+__global__ void k_ns_reset(NonsymStep* o, const int* skip) {
+  if (skip && *skip) return;
+  o->jint = 0;
+  o->fail = 0;
+  o->mask = ~0ull;
+}
+
+__global__ void k_ns_interior(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
                               const double* __restrict__ z, const double* __restrict__ dz, const double* a0p,
-                              double backtrack, int j0, int nbhd, double beta, const double* mu_coef,
-                              unsigned long long* mask, const int* skip) {
+                              double backtrack, NonsymStep* o, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= cd.n_exp + cd.n_pow) return;
+  const NsCone c = load_cone(cd, t, s, ds, z, dz);
+  double alpha = *a0p;
+  int j = 0;
+  while (j < 120 && !ns_interior(c, alpha)) {
+    alpha *= backtrack;
+    ++j;
+  }
+  atomicMax(&o->jint, j);
+}
+
+__global__ void k_ns_first(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
+                           const double* __restrict__ z, const double* __restrict__ dz, const double* a0p,
+                           double backtrack, double beta, const double* mu_coef, NonsymStep* o, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= cd.n_exp + cd.n_pow) return;
+  const NsCone c = load_cone(cd, t, s, ds, z, dz);
+  const double alpha = *a0p * pow(backtrack, (double)o->jint);
+  if (!ns_nbhd(c, alpha, mu_coef, beta)) atomicOr(&o->fail, 1);
+}
+
+__global__ void k_ns_window(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
+                            const double* __restrict__ z, const double* __restrict__ dz, const double* a0p,
+                            double backtrack, double beta, const double* mu_coef, NonsymStep* o, const int* skip) {
+  if (skip && *skip) return;
+  if (!o->fail) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= cd.n_exp + cd.n_pow) return;
+  const NsCone c = load_cone(cd, t, s, ds, z, dz);
+  double alpha = *a0p * pow(backtrack, (double)(o->jint + 1));
+  unsigned long long bits = 0ull;
+  for (int k = 0; k < 64; ++k) {
+    if (ns_nbhd(c, alpha, mu_coef, beta)) bits |= (1ull << k);
+    alpha *= backtrack;
+  }
+  atomicAnd(&o->mask, bits);
+}
+
+int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
+                      const double* dz, const double* a0, double backtrack, int nbhd, double beta,
+                      const double* mu_coef, NonsymStep* out, const int* skip) {
+  k_ns_reset<<<1, 1, 0, st>>>(out, skip);
+  const int64_t nc = cd.n_exp + cd.n_pow;
+  if (nc == 0) return CLR_OK;
+  const unsigned g = (unsigned)((nc + 63) / 64);
+  k_ns_interior<<<g, 64, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, out, skip);
+  if (nbhd) {
+    k_ns_first<<<g, 64, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, beta, mu_coef, out, skip);
+    k_ns_window<<<g, 64, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, beta, mu_coef, out, skip);
+  }
+  CLR_CHECK_LAUNCH();
+  return CLR_OK;
+}
+
+__global__ void k_init_shadow(ConeDev cd, const int* skip) {
   if (skip && *skip) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cd.n_exp + cd.n_pow) return;
   const bool is_exp = t < cd.n_exp;
-  const int64_t i = is_exp ? t : t - cd.n_exp;
-  const int64_t row = is_exp ? cd.exp_row0 + 3 * i : cd.pow_row0 + 3 * i;
-  const double a = is_exp ? 0.0 : cd.pow_alpha[i];
-  const double sv[3] = {s[row], s[row + 1], s[row + 2]}, zv[3] = {z[row], z[row + 1], z[row + 2]};
-  const double dsv[3] = {ds[row], ds[row + 1], ds[row + 2]}, dzv[3] = {dz[row], dz[row + 1], dz[row + 2]};
-  unsigned long long bits = 0ull;
-  double alpha = *a0p * pow(backtrack, (double)j0);
-  for (int j = 0; j < 64; ++j) {
-    double sc[3], zc[3];
-    for (int q = 0; q < 3; ++q) {
-      sc[q] = sv[q] + alpha * dsv[q];
-      zc[q] = zv[q] + alpha * dzv[q];
-    }
-    bool ok = in_int_primal(is_exp, sc, a) && in_int_dual(is_exp, zc, a);
-    if (ok && nbhd) {
-      const double mu_t = mu_coef[0] + alpha * (mu_coef[1] + alpha * mu_coef[2]);
-      double zt[3], g[3];
-      dual_shadow(is_exp, sc, a, cd.exp_center, zt);
-      barrier_grad(is_exp, zc, a, g);
-      const double dot = -(zt[0] * g[0] + zt[1] * g[1] + zt[2] * g[2]);  // <z~, s~>, s~ = -grad f(z)
-      ok = (3.0 / dot >= beta * mu_t);
-    }
-    if (ok) bits |= (1ull << j);
-    alpha *= backtrack;
-  }
-  atomicAnd(mask, bits);
+  const double a = is_exp ? 0.0 : cd.pow_alpha[t - cd.n_exp];
+  central_point(is_exp, a, cd.exp_center, cd.ep_zt + 3 * t);
 }
 
-int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
-                      const double* dz, const double* a0, double backtrack, int j0, int nbhd, double beta,
-                      const double* mu_coef, unsigned long long* mask, const int* skip) {
-  if (cd.n_exp + cd.n_pow == 0) return CLR_OK;
-  k_step_nonsym<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, j0,
-                                                                               nbhd, beta, mu_coef, mask, skip);
+int cones_init_shadow(cudaStream_t st, const ConeDev& cd, const int* skip) {
+  const int64_t nc = cd.n_exp + cd.n_pow;
+  if (nc == 0) return CLR_OK;
+  k_init_shadow<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(cd, skip);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }

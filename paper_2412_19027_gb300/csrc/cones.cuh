@@ -37,7 +37,15 @@ struct ConeDev {
   double* psd_R = nullptr;    // k*k per cone (column-major)
   double* psd_Ri = nullptr;   // R^{-1}
   double* psd_lam = nullptr;  // k per cone
+  double* ep_zt = nullptr;   // 3 per exp/pow cone: z~ = -grad f*(s) at the current s (Newton warm start)
   double exp_center[3] = {0, 0, 0};  // central point of the exp cone (u = -grad f(u))
+};
+
+// Result of the exp/pow backtracking (see cones_step_nonsym).
+struct NonsymStep {
+  int jint;                 // smallest j with every cone interior at a0 * backtrack^j
+  int fail;                 // some cone fails N(beta) at jint
+  unsigned long long mask;  // bit k: every cone passes N(beta) at jint + 1 + k
 };
 
 // All scalars of one iteration that several kernels share live in device memory.
@@ -51,13 +59,17 @@ int cones_identity_H(cudaStream_t st, const ConeDev& cd, const int* skip);
 // Symmetric-cone step length over s/ds and z/dz -> atomicMin into *amin_bits.
 int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
                          const double* dz, unsigned long long* amin_bits, const int* skip);
-// exp/pow backtracking: for candidates a_j = a0 * backtrack^(j0 + j), j < 64, bit j of *mask
-// stays set iff every exp/pow cone passes (interior; plus N(beta) with the trial mu when
-// nbhd != 0).  mu_coef = {s'z + tau kappa, s'dz + ds'z + tau dkappa + kappa dtau,
-// ds'dz + dtau dkappa} / (nu + 1).
+// exp/pow backtracking from a0 (Sec. 2.2: ratio 0.8): the candidates are
+// a_j = a0 backtrack^j.  Interior-ness is monotone along the ray, so the joint
+// first interior candidate is the largest per-cone one (jint).  With nbhd != 0
+// the N(beta) test (trial mu from mu_coef = {c0, c1, c2}: mu(a) = c0 + a c1 +
+// a^2 c2) is evaluated at jint and, only if some cone fails there, on the 64
+// candidates after it; the step is the first candidate every cone passes.
 int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
-                      const double* dz, const double* a0, double backtrack, int j0, int nbhd, double beta,
-                      const double* mu_coef, unsigned long long* mask, const int* skip);
+                      const double* dz, const double* a0, double backtrack, int nbhd, double beta,
+                      const double* mu_coef, NonsymStep* out, const int* skip);
+// z~ of every exp/pow cone set to its central point (start of a solve).
+int cones_init_shadow(cudaStream_t st, const ConeDev& cd, const int* skip);
 // Combined-step d_s (Eq. ds-correction-step) for every cone.
 int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* dsa,
                       const double* dza, const double* sigma_mu, double* ds_out, const int* skip);

@@ -341,7 +341,6 @@ struct StepParams {
 __global__ void k_step_begin(IterScal* sc, const int* skip) {
   if (skip && *skip) return;
   sc->amin_bits = dbits(INFINITY);
-  sc->mask = ~0ull;
 }
 
 __global__ void k_fin_step_sym(IterScal* sc, const int* skip) {
@@ -366,9 +365,12 @@ __global__ void k_fin_step(IterScal* sc, StepParams sp, int combined, double* hi
   if (skip && *skip) return;
   double a = sc->alpha_sym;
   if (sp.nonsym) {
-    const unsigned long long m = sc->mask;
-    if (m == 0ull) a = 0.0;
-    else a = a * pow(sp.backtrack, (double)(__ffsll((long long)m) - 1));
+    int j = sc->ns.jint;
+    if (combined && sc->ns.fail) {
+      const unsigned long long m = sc->ns.mask;
+      j = (m == 0ull) ? -1 : j + __ffsll((long long)m);  // first common pass after jint
+    }
+    a = (j < 0) ? 0.0 : a * pow(sp.backtrack, (double)j);
   }
   double* h = (sc->iter < sp.hist_cap) ? hist + 12 * sc->iter : nullptr;
   if (!combined) {
@@ -673,6 +675,7 @@ int Solver::upload() {
   cd_.psd_R = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k * cl.psd_k);
   cd_.psd_Ri = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k * cl.psd_k);
   cd_.psd_lam = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k);
+  cd_.ep_zt = ar_.alloc_n<double>(3 * (cd_.n_exp + cd_.n_pow));
   exp_central_point_host(cd_.exp_center);
   if (!v_.kptr || !v_.kcol || !v_.kvi || !v_.kval || !v_.xz || !v_.part || !sc_ || !cd_.scratch) return CLR_E_OOM;
   CLR_CUDA(cudaStreamSynchronize(stream_));
@@ -800,8 +803,8 @@ int Solver::step_length(bool combined) {
                                                 halt);
       k_mu_coef<<<1, 256, 0, s>>>(sc_, v_.part, hp.cl.nu, halt);
     }
-    rc = cones_step_nonsym(s, cd_, v_.s, ds, v_.xz + n, dir + n, &sc_->alpha_sym, st.backtrack, 0, combined ? 1 : 0,
-                           st.nbhd_beta, sc_->mu_coef, &sc_->mask, halt);
+    rc = cones_step_nonsym(s, cd_, v_.s, ds, v_.xz + n, dir + n, &sc_->alpha_sym, st.backtrack, combined ? 1 : 0,
+                           st.nbhd_beta, sc_->mu_coef, &sc_->ns, halt);
     if (rc) return rc;
   }
   StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hp.cl.nu,
@@ -899,6 +902,8 @@ int Solver::initialise() {
     if (rc) return rc;
   } else {
     int rc = cones_unit_init(s, cd_, v_.s, nullptr);
+    if (rc) return rc;
+    rc = cones_init_shadow(s, cd_, nullptr);
     if (rc) return rc;
     rc = cones_unit_init(s, cd_, v_.xz + n, nullptr);
     if (rc) return rc;

@@ -28,7 +28,8 @@ struct IterScal {
   double d_tau, d_kap, dtau, dkap;
   double dtau_a, dkap_a;
   // step length
-  unsigned long long amin_bits, mask;
+  unsigned long long amin_bits;
+  clr::NonsymStep ns;
   double alpha_sym, alpha_a, alpha_c, sigma, sigma_mu;
   double mu_coef[3];
   // iterative refinement

@@ -100,123 +100,6 @@ __global__ void k_factor_small(T* __restrict__ F, T* __restrict__ Dp, const int6
   for (int q = threadIdx.x; q < f * f; q += blockDim.x) G[q] = S[q];
 }
 
-// Large fronts, panel of pw <= 32 columns starting at k0.
-// k_big_diag (one warp): LDL^T of the pw x pw diagonal block, in place, pivots to Dp.
-template <typename T>
-__global__ void k_big_diag(T* __restrict__ G, int64_t f, int64_t k0, int pw, T* __restrict__ Dp,
-                           const int8_t* __restrict__ dsg, double eps_d, double delta_d, int* dyn_hits,
-                           const int* skip) {
-  if (skip && *skip) return;
-  __shared__ T Ld[32][33];
-  __shared__ T dd[32];
-  const int tid = threadIdx.x;  // blockDim.x == 32
-  for (int j = 0; j < 32; ++j) Ld[tid][j] = (tid < pw && j < pw && tid >= j) ? G[(k0 + tid) + (k0 + j) * f] : (T)0;
-  __syncwarp();
-  const T eps = (T)eps_d, delta = (T)delta_d;
-  for (int kk = 0; kk < pw; ++kk) {
-    if (tid == 0) {
-      bool hit;
-      T d = regularise(Ld[kk][kk], (int)dsg[k0 + kk], eps, delta, &hit);
-      if (hit) atomicAdd(dyn_hits, 1);
-      Ld[kk][kk] = d;
-      dd[kk] = d;
-    }
-    __syncwarp();
-    const T inv = (T)1 / dd[kk];
-    if (tid > kk && tid < pw) {
-      const T lik = Ld[tid][kk];
-      for (int j = kk + 1; j <= tid; ++j) Ld[tid][j] -= lik * Ld[j][kk] * inv;
-    }
-    __syncwarp();
-    if (tid > kk && tid < pw) Ld[tid][kk] *= inv;
-    __syncwarp();
-  }
-  for (int j = 0; j < pw; ++j)
-    if (tid >= j && tid < pw) G[(k0 + tid) + (k0 + j) * f] = Ld[tid][j];
-  if (tid < pw) Dp[k0 + tid] = dd[tid];
-}
-
-// k_big_trsm: rows r0 = k0+pw+32 b ... of L21 = F21 L11^{-T} D^{-1}, one row per thread,
-// reading the factored diagonal block written by k_big_diag.
-template <typename T>
-__global__ void k_big_trsm(T* __restrict__ G, int64_t f, int64_t k0, int pw, const T* __restrict__ Dp,
-                           const int* skip) {
-  if (skip && *skip) return;
-  __shared__ T Ld[32][33];
-  __shared__ T dd[32];
-  const int tid = threadIdx.x;  // blockDim.x == 32
-  for (int j = 0; j < 32; ++j) Ld[tid][j] = (tid < pw && j < pw && tid > j) ? G[(k0 + tid) + (k0 + j) * f] : (T)0;
-  if (tid < pw) dd[tid] = Dp[k0 + tid];
-  __syncwarp();
-  const int64_t r = k0 + pw + (int64_t)blockIdx.x * 32 + tid;
-  if (r >= f) return;
-  T x[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (j < pw) {
-      T v = G[r + (k0 + j) * f];
-      for (int l = 0; l < j; ++l) v -= x[l] * dd[l] * Ld[j][l];
-      x[j] = v / dd[j];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 32; ++j)
-    if (j < pw) G[r + (k0 + j) * f] = x[j];
-}
-
-// Trailing update of a large front: C(i, j) -= sum_l L(i, l) d_l L(j, l) over
-// the panel columns, lower tiles of 64 x 64 (256 threads, 4 x 4 per thread).
-template <typename T>
-__global__ void k_big_update(T* __restrict__ G, int64_t f, int64_t k0, int pw, const T* __restrict__ Dp, int64_t t0,
-                             const int* skip) {
-  if (skip && *skip) return;
-  constexpr int TS = 64;
-  __shared__ T As[TS][33];
-  __shared__ T Bs[TS][33];
-  // lower-tile index -> (bi, bj), bi >= bj
-  const int64_t bid = blockIdx.x;
-  int64_t bi = (int64_t)((sqrt(8.0 * (double)bid + 1.0) - 1.0) / 2.0);
-  while (bi * (bi + 1) / 2 > bid) --bi;
-  while ((bi + 1) * (bi + 2) / 2 <= bid) ++bi;
-  const int64_t bj = bid - bi * (bi + 1) / 2;
-  const int64_t i0 = t0 + bi * TS, j0 = t0 + bj * TS;
-  const int tid = threadIdx.x;
-  for (int q = tid; q < TS * 32; q += blockDim.x) {
-    const int rr = q % TS, l = q / TS;
-    const int64_t ia = i0 + rr, ib = j0 + rr;
-    As[rr][l] = (l < pw && ia < f) ? G[ia + (k0 + l) * f] : (T)0;
-    Bs[rr][l] = (l < pw && ib < f) ? G[ib + (k0 + l) * f] * Dp[k0 + l] : (T)0;
-  }
-  __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;
-  T acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
-  for (int l = 0; l < pw; ++l) {
-    T av[4], bv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = As[tr + 16 * a][l];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) bv[b] = Bs[tc + 16 * b][l];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-  }
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const int64_t j = j0 + tc + 16 * b;
-    if (j >= f) continue;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int64_t i = i0 + tr + 16 * a;
-      if (i < f && i >= j) G[i + j * f] -= acc[a][b];
-    }
-  }
-}
-
 // ------------------------------------------------------------------ solve
 template <typename T>
 __global__ void k_init_w(T* __restrict__ w, const int32_t* __restrict__ w_init, const double* __restrict__ rhs,
@@ -234,12 +117,13 @@ template <typename T>
 __global__ void k_fwd_front(const T* __restrict__ F, T* __restrict__ w, const int64_t* __restrict__ fronts,
                             const int64_t* __restrict__ sn_ptr, const int64_t* __restrict__ row_ptr,
                             const int64_t* __restrict__ front_off, const int64_t* __restrict__ upd_off,
-                            const int* skip) {
+                            int small_max, const int* skip) {
   if (skip && *skip) return;
   __shared__ T xb[32];
   const int64_t J = fronts[blockIdx.x];
   const int64_t c = sn_ptr[J + 1] - sn_ptr[J];
   const int64_t f = row_ptr[J + 1] - row_ptr[J];
+  if (f > small_max) return;
   const T* G = F + front_off[J];
   T* wj = w + upd_off[J];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -273,11 +157,12 @@ __global__ void k_bwd_front(const T* __restrict__ F, const T* __restrict__ Dp, T
                             const int64_t* __restrict__ fronts, const int64_t* __restrict__ sn_ptr,
                             const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ front_off,
                             const int64_t* __restrict__ upd_off, const int32_t* __restrict__ rows_kkt,
-                            const int* skip) {
+                            int small_max, const int* skip) {
   if (skip && *skip) return;
   const int64_t J = fronts[blockIdx.x];
   const int64_t c = sn_ptr[J + 1] - sn_ptr[J];
   const int64_t f = row_ptr[J + 1] - row_ptr[J];
+  if (f > small_max) return;
   const T* G = F + front_off[J];
   T* X = w + upd_off[J];
   const int32_t* rk = rows_kkt + row_ptr[J];
@@ -348,6 +233,104 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       if (f > small_max) st.lev_big[l].push_back(J);
       else st.lev_small_maxf[l] = std::max(st.lev_small_maxf[l], (int)f);
     }
+  // ---- big fronts: arrays, E / y pools, launch plans per level ----
+  {
+    std::vector<int64_t> bf_f, bf_c, bf_goff, bf_eoff, bf_k0, bf_woff, bf_yoff, bf_rk;
+    std::vector<int64_t> bid_of(sy.nsn, -1);
+    int64_t epool = 0, ypool = 0;
+    for (int64_t l = 0; l < sy.nlev; ++l)
+      for (int64_t J : st.lev_big[l]) {
+        const int64_t f = sy.row_ptr[J + 1] - sy.row_ptr[J], c = sy.sn_ptr[J + 1] - sy.sn_ptr[J];
+        bid_of[J] = (int64_t)bf_f.size();
+        bf_f.push_back(f);
+        bf_c.push_back(c);
+        bf_goff.push_back(sy.front_off[J]);
+        bf_eoff.push_back(epool);
+        bf_k0.push_back(sy.sn_ptr[J]);
+        bf_woff.push_back(sy.upd_off[J]);
+        bf_yoff.push_back(ypool);
+        bf_rk.push_back(sy.row_ptr[J]);
+        epool += f * c;
+        ypool += c;
+      }
+    BigFrontDev& bd = st.bfd;
+    bd.n = (int64_t)bf_f.size();
+    bd.epool = epool;
+    bd.ypool = ypool;
+    bd.f = up(ar, bf_f);
+    bd.c = up(ar, bf_c);
+    bd.goff = up(ar, bf_goff);
+    bd.eoff = up(ar, bf_eoff);
+    bd.k0pos = up(ar, bf_k0);
+    bd.woff = up(ar, bf_woff);
+    bd.yoff = up(ar, bf_yoff);
+    bd.rk = up(ar, bf_rk);
+    // work lists: host-built (front ids, prefix sums), uploaded in one buffer
+    std::vector<int64_t> buf;
+    struct Pending {
+      WorkList* wl;
+      size_t fo, po;
+    };
+    std::vector<Pending> pend;
+    st.bplans.assign(sy.nlev, BigLevelPlan());
+    auto add_list = [&](WorkList& wl, const std::vector<int64_t>& fronts, const std::vector<int64_t>& counts) {
+      wl.nfront = 0;
+      wl.nblocks = 0;
+      std::vector<int64_t> fr, pr;
+      for (size_t i = 0; i < fronts.size(); ++i)
+        if (counts[i] > 0) {
+          fr.push_back(fronts[i]);
+          pr.push_back(wl.nblocks);
+          wl.nblocks += counts[i];
+        }
+      pr.push_back(wl.nblocks);
+      wl.nfront = (int64_t)fr.size();
+      if (wl.nfront == 0) return;
+      Pending pd{&wl, buf.size(), 0};
+      buf.insert(buf.end(), fr.begin(), fr.end());
+      pd.po = buf.size();
+      buf.insert(buf.end(), pr.begin(), pr.end());
+      pend.push_back(pd);
+    };
+    for (int64_t l = 0; l < sy.nlev; ++l) {
+      if (st.lev_big[l].empty()) continue;
+      BigLevelPlan& pl = st.bplans[l];
+      std::vector<int64_t> ids;
+      int maxp = 0;
+      for (int64_t J : st.lev_big[l]) {
+        ids.push_back(bid_of[J]);
+        maxp = std::max<int>(maxp, (int)((bf_c[bid_of[J]] + kBfNB - 1) / kBfNB));
+      }
+      pl.A.resize(maxp + 1);
+      pl.B.resize(maxp + 1);
+      pl.C.resize(maxp + 1);
+      for (int p = 0; p <= maxp; ++p) {
+        std::vector<int64_t> ca, cb, cc;
+        for (int64_t b : ids) {
+          const int64_t f = bf_f[b], c = bf_c[b];
+          ca.push_back((int64_t)p * kBfNB < c ? 1 : 0);
+          cb.push_back(bf_trsm_blocks(f, c, p) + bf_fin_blocks(c, p - 1));
+          cc.push_back(bf_update_tiles(f, c, p));
+        }
+        add_list(pl.A[p], ids, ca);
+        add_list(pl.B[p], ids, cb);
+        add_list(pl.C[p], ids, cc);
+      }
+      std::vector<int64_t> cf, cbw;
+      for (int64_t b : ids) {
+        cf.push_back((bf_f[b] + 31) / 32);
+        cbw.push_back((bf_c[b] + 7) / 8);
+      }
+      add_list(pl.fwd, ids, cf);
+      add_list(pl.bwd, ids, cbw);
+    }
+    int64_t* dbuf = buf.empty() ? nullptr : ar.upload(buf.data(), (int64_t)buf.size());
+    if (!buf.empty() && !dbuf) return CLR_E_OOM;
+    for (Pending& pd : pend) {
+      pd.wl->front = dbuf + pd.fo;
+      pd.wl->pref = dbuf + pd.po;
+    }
+  }
   st.sn_ptr = up(ar, sy.sn_ptr);
   st.row_ptr = up(ar, sy.row_ptr);
   st.front_off = up(ar, sy.front_off);
@@ -379,7 +362,11 @@ int LdlFactor<T>::alloc(DeviceArena& ar, const LdlStructure& st) {
   w = ar.alloc_n<T>(st.wtot);
   xs = ar.alloc_n<T>(st.N);
   dyn_hits = ar.alloc_n<int>(1);
-  if (!F || !Dp || !w || !xs || !dyn_hits) return CLR_E_OOM;
+  E = ar.alloc_n<T>(st.bfd.epool);
+  ybuf = ar.alloc_n<T>(st.bfd.ypool);
+  Linv = ar.alloc_n<T>(st.bfd.n * 2 * kBfNB * kBfNB);
+  if (!F || !Dp || !w || !xs || !dyn_hits || !E || !ybuf || !Linv) return CLR_E_OOM;
+  if (BigFrontOps<T>::setup_attributes() != CLR_OK) return CLR_E_CUDA;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_factor_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -394,6 +381,7 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const double* del
   const LdlStructure& S = *s;
   CLR_CUDA(cudaMemsetAsync(dyn_hits, 0, sizeof(int), stm));
   CLR_CUDA(cudaMemsetAsync(F, 0, sizeof(T) * (size_t)S.pool, stm));
+  if (S.bfd.epool > 0) CLR_CUDA(cudaMemsetAsync(E, 0, sizeof(T) * (size_t)S.bfd.epool, stm));
   k_scatter_kval<T><<<grid_for(S.nk, 256), 256, 0, stm>>>(F, kval, S.kdest, S.nk, skip);
   k_add_reg<T><<<grid_for(S.N, 256), 256, 0, stm>>>(F, S.diag_pos, S.dsign, S.N, delta, skip);
   CLR_CHECK_LAUNCH();
@@ -409,22 +397,10 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const double* del
                                                                S.front_off, S.dsign, S.small_max, dyn_eps, dyn_delta,
                                                                dyn_hits, skip);
     }
-    for (int64_t J : S.lev_big[l]) {
-      const int64_t c = S.h_sn_ptr[J + 1] - S.h_sn_ptr[J];
-      const int64_t f = S.h_row_ptr[J + 1] - S.h_row_ptr[J];
-      T* G = F + S.h_front_off[J];
-      T* DpJ = Dp + S.h_sn_ptr[J];
-      const int8_t* dsJ = S.dsign + S.h_sn_ptr[J];
-      for (int64_t k0 = 0; k0 < c; k0 += 32) {
-        const int pw = (int)std::min<int64_t>(32, c - k0);
-        const int64_t below = f - k0 - pw;
-        k_big_diag<T><<<1, 32, 0, stm>>>(G, f, k0, pw, DpJ, dsJ, dyn_eps, dyn_delta, dyn_hits, skip);
-        if (below > 0) {
-          k_big_trsm<T><<<(unsigned)((below + 31) / 32), 32, 0, stm>>>(G, f, k0, pw, DpJ, skip);
-          const int64_t nt = (below + 63) / 64;
-          k_big_update<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, stm>>>(G, f, k0, pw, DpJ, k0 + pw, skip);
-        }
-      }
+    if (!S.lev_big[l].empty()) {
+      int rc = BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps, dyn_delta,
+                                            dyn_hits, skip);
+      if (rc) return rc;
     }
     CLR_CHECK_LAUNCH();
   }
@@ -439,13 +415,23 @@ int LdlFactor<T>::solve(cudaStream_t stm, const double* rhs, const int* skip) co
     const int64_t t0 = S.h_sv_lev_ptr[l], t1 = S.h_sv_lev_ptr[l + 1];
     if (t1 > t0) k_pull<T><<<grid_for(t1 - t0, 256), 256, 0, stm>>>(w, S.sv_tgt, S.sv_ptr, S.sv_src, t0, t1, skip);
     const int64_t nf = S.h_lev_ptr[l + 1] - S.h_lev_ptr[l];
-    k_fwd_front<T><<<(unsigned)nf, 256, 0, stm>>>(F, w, S.lev_sn + S.h_lev_ptr[l], S.sn_ptr, S.row_ptr, S.front_off,
-                                                   S.upd_off, skip);
+    if ((int64_t)S.lev_big[l].size() < nf)
+      k_fwd_front<T><<<(unsigned)nf, 256, 0, stm>>>(F, w, S.lev_sn + S.h_lev_ptr[l], S.sn_ptr, S.row_ptr,
+                                                     S.front_off, S.upd_off, S.small_max, skip);
+    if (!S.lev_big[l].empty()) {
+      int rc = BigFrontOps<T>::fwd(stm, S.bfd, S.bplans[l].fwd, E, w, ybuf, skip);
+      if (rc) return rc;
+    }
   }
   for (int64_t l = S.nlev - 1; l >= 0; --l) {
     const int64_t nf = S.h_lev_ptr[l + 1] - S.h_lev_ptr[l];
-    k_bwd_front<T><<<(unsigned)nf, 256, 0, stm>>>(F, Dp, w, xs, S.lev_sn + S.h_lev_ptr[l], S.sn_ptr, S.row_ptr,
-                                                  S.front_off, S.upd_off, S.rows_kkt, skip);
+    if ((int64_t)S.lev_big[l].size() < nf)
+      k_bwd_front<T><<<(unsigned)nf, 256, 0, stm>>>(F, Dp, w, xs, S.lev_sn + S.h_lev_ptr[l], S.sn_ptr, S.row_ptr,
+                                                    S.front_off, S.upd_off, S.rows_kkt, S.small_max, skip);
+    if (!S.lev_big[l].empty()) {
+      int rc = BigFrontOps<T>::bwd(stm, S.bfd, S.bplans[l].bwd, E, Dp, ybuf, xs, S.rows_kkt, skip);
+      if (rc) return rc;
+    }
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;

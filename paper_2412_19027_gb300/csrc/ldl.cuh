@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "bigfront.cuh"
 #include "device.cuh"
 #include "internal.h"
 #include "symbolic.h"
@@ -27,6 +28,8 @@ struct LdlStructure {
   std::vector<int64_t> h_sn_ptr, h_row_ptr, h_front_off;
   std::vector<int> lev_small_maxf;               // largest small front of each level
   std::vector<std::vector<int64_t>> lev_big;     // big fronts of each level
+  BigFrontDev bfd;                               // big-front arrays (device)
+  std::vector<BigLevelPlan> bplans;              // per level
   int small_max = 0;
   int64_t max_front = 0;
 };
@@ -41,6 +44,9 @@ struct LdlFactor {
   T* Dp = nullptr;  // pivots by elimination position
   T* w = nullptr;   // forward-solve slots
   T* xs = nullptr;  // solution in KKT order
+  T* E = nullptr;     // augmented inverse blocks of the big fronts
+  T* ybuf = nullptr;  // forward results of the big fronts
+  T* Linv = nullptr;  // per big front, two 64 x 64 diagonal-block inverses
   int* dyn_hits = nullptr;
   int alloc(DeviceArena& ar, const LdlStructure& st);
   // Factor K: kval (FP64, lower triangle entries in kval order) scattered into

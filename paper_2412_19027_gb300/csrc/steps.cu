@@ -111,7 +111,9 @@ struct ConeBench {
     cd.psd_R = ar.alloc_n<double>(cd.n_psd * psd_k * psd_k);
     cd.psd_Ri = ar.alloc_n<double>(cd.n_psd * psd_k * psd_k);
     cd.psd_lam = ar.alloc_n<double>(cd.n_psd * psd_k);
+    cd.ep_zt = ar.alloc_n<double>(3 * (cd.n_exp + cd.n_pow));
     exp_central_point_host(cd.exp_center);
+    if (cones_init_shadow(nullptr, cd, nullptr) != CLR_OK) rc = CLR_E_CUDA;
     if (!cd.kvz || !cd.scratch || !cd.soc_wb) rc = CLR_E_OOM;
   }
 
@@ -189,7 +191,8 @@ int clr_cones_step_length(const clr_cone* cones, int32_t ncones, const double* s
   unsigned long long* amin = cb.ar.alloc_n<unsigned long long>(2);
   double* a0 = cb.ar.alloc_n<double>(1);
   double* coef = cb.ar.alloc_n<double>(3);
-  if (!d_s || !d_z || !d_ds || !d_dz || !amin || !a0 || !coef) return CLR_E_OOM;
+  NonsymStep* ns = cb.ar.alloc_n<NonsymStep>(1);
+  if (!d_s || !d_z || !d_ds || !d_dz || !amin || !a0 || !coef || !ns) return CLR_E_OOM;
   const double inf = INFINITY;
   unsigned long long init[2];
   std::memcpy(&init[0], &inf, 8);
@@ -204,15 +207,11 @@ int clr_cones_step_length(const clr_cone* cones, int32_t ncones, const double* s
   double a = std::min(alpha_max, amin_v);
   if (cb.cd.n_exp + cb.cd.n_pow > 0) {
     CLR_CUDA(cudaMemcpy(a0, &a, 8, cudaMemcpyHostToDevice));
-    rc = cones_step_nonsym(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, a0, 0.8, 0, 0, 1e-6, coef, amin + 1, nullptr);
+    rc = cones_step_nonsym(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, a0, 0.8, 0, 1e-6, coef, ns, nullptr);
     if (rc) return rc;
-    CLR_CUDA(cudaMemcpy(hb, amin, 16, cudaMemcpyDeviceToHost));
-    if (hb[1] == 0ull) a = 0.0;
-    else {
-      int j = 0;
-      while (!((hb[1] >> j) & 1ull)) ++j;
-      a = a * std::pow(0.8, (double)j);
-    }
+    NonsymStep h;
+    CLR_CUDA(cudaMemcpy(&h, ns, sizeof(NonsymStep), cudaMemcpyDeviceToHost));
+    a = a * std::pow(0.8, (double)h.jint);
   }
   *alpha_out = a;
   return CLR_OK;

@@ -235,3 +235,28 @@ def test_solve_matches_oracle_fp64(name, make):
 def test_solve_matches_oracle_fp32_factor(name, make):
     """FP32 factorization + FP64 refinement reaches the FP64 oracle's answer."""
     _compare_solve(make(), 32, iters_tol=4)
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_ldl_big_fronts_with_update_rows(bits):
+    """Natural order on [P A^T; A -H] with dense P (180) and dense H (160): the
+    first front has 180 pivots and 160 update rows, the root 160 pivots; both
+    exceed one CTA's shared memory and take the blocked big-front path."""
+    rng = np.random.default_rng(11)
+    n, m = 180, 160
+    M = rng.standard_normal((n, n))
+    P = M @ M.T / n + np.eye(n)
+    B = rng.standard_normal((m, m))
+    H = B @ B.T / m + np.eye(m)
+    A = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.2)
+    K = np.block([[P, A.T], [A, -H]])
+    N = n + m
+    signs = np.r_[np.ones(n), -np.ones(m)]
+    rhs = rng.standard_normal(N)
+    x, D, hits = clr.clr_ldl_solve(K, signs, rhs, order=np.arange(N), factor_bits=bits)
+    assert hits == 0
+    L, Dref, _ = ldl_factor(K, signs, 1e-13, 2e-7)
+    tol = 1e-10 if bits == 64 else 1e-4
+    np.testing.assert_allclose(D, Dref, rtol=tol)
+    xref = np.linalg.solve(K, rhs)
+    np.testing.assert_allclose(x, xref, rtol=tol, atol=tol * np.abs(xref).max())
