@@ -41,140 +41,98 @@ __device__ __forceinline__ T reg_pivot(T d, int sgn, T eps, T delta, bool* hit) 
 }  // namespace
 
 // ------------------------------------------------------------------ A: diagonal block
-// LDL^T of a 32-column sub-panel by one warp, rows held in registers: lane l owns
-// row c0 + l (the 32 x 32 triangle, tri[]) and, when `below`, row c0 + 32 + l (bot[]).
-// Pivot columns are broadcast with shuffles; every loop is unrolled so that the
-// register arrays are indexed statically.
-template <typename T>
-__device__ __forceinline__ void warp_ldl32(T* S, int c0, int cw, int nbot, const int8_t* dsg, T eps, T delta,
-                                           int* hits, T* dd) {
-  const int lane = threadIdx.x & 31;
-  T tri[32], bot[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    tri[j] = (lane < cw && j < cw) ? S[(c0 + lane) * LD + c0 + j] : (T)0;
-    bot[j] = (lane < nbot && j < cw) ? S[(c0 + 32 + lane) * LD + c0 + j] : (T)0;
-  }
-#pragma unroll
-  for (int kk = 0; kk < 32; ++kk) {
-    if (kk < cw) {
-      T d = __shfl_sync(0xffffffffu, tri[kk], kk);
-      bool hit = false;
-      if ((T)dsg[c0 + kk] * d <= eps) {
-        d = (T)dsg[c0 + kk] * delta;
-        hit = true;
-      }
-      if (lane == 0) {
-        if (hit) atomicAdd(hits, 1);
-        dd[c0 + kk] = d;
-      }
-      const T inv = (T)1 / d;
-      const T fik = tri[kk], fbk = bot[kk];
-#pragma unroll
-      for (int j = kk + 1; j < 32; ++j) {
-        const T fjk = __shfl_sync(0xffffffffu, tri[kk], j);
-        if (lane >= j) tri[j] -= fik * fjk * inv;
-        bot[j] -= fbk * fjk * inv;
-      }
-      if (lane == kk) tri[kk] = d;
-      if (lane > kk) tri[kk] = fik * inv;
-      bot[kk] = fbk * inv;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (lane < cw && j < cw && j <= lane) S[(c0 + lane) * LD + c0 + j] = tri[j];
-    if (lane < nbot && j < cw) S[(c0 + 32 + lane) * LD + c0 + j] = bot[j];
-  }
-}
-
-// Inverse of a unit lower 32 x 32 block held in S (rows/cols from r0), one warp,
-// lane j computes column j; result into Li (same offsets).
+// Inverse of a unit lower n x n block (n <= 32) held in S (rows/cols from r0):
+// lane j of the calling warp computes column j in Li (same offsets), reading the
+// already computed entries of its column from shared memory.
 template <typename T>
 __device__ __forceinline__ void warp_inv32(const T* S, T* Li, int r0, int n) {
   const int j = threadIdx.x & 31;
-  T x[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    T v = (i == j) ? (T)1 : (T)0;
-    if (i > j && i < n) {
+  if (j < n) {
+    Li[(r0 + j) * LD + r0 + j] = (T)1;
+    for (int i = j + 1; i < n; ++i) {
       T acc = (T)0;
-#pragma unroll
-      for (int l = 0; l < i; ++l)
-        if (l >= j) acc += S[(r0 + i) * LD + r0 + l] * x[l];
-      v = -acc;
+      for (int l = j; l < i; ++l) acc += S[(r0 + i) * LD + r0 + l] * Li[(r0 + l) * LD + r0 + j];
+      Li[(r0 + i) * LD + r0 + j] = -acc;
     }
-    x[i] = v;
   }
-#pragma unroll
-  for (int i = 0; i < 32; ++i)
-    if (i < n && j < n) Li[(r0 + i) * LD + r0 + j] = (i >= j) ? x[i] : (T)0;
 }
 
+// Diagonal block of panel p: LDL^T by the whole CTA, right-looking, one barrier
+// per pivot: 4 threads per row update that row's entries left of the diagonal;
+// the pivot column is read unscaled from S (never written again) and its scaled
+// values go to Lo.  Pivots to Dp; then Linv = [A^-1 0; -B^-1 C A^-1  B^-1] for
+// L = [A 0; C B] (32-blocks).
 template <typename T>
 __global__ void k_bf_diag(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F, T* __restrict__ Dp,
                           T* __restrict__ Linv, const int8_t* __restrict__ dsign, double eps_d, double delta_d,
                           int* hits, const int* skip) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* S = reinterpret_cast<T*>(smraw);  // NB x LD
-  T* Li = S + NB * LD;                 // NB x LD
+  T* S = reinterpret_cast<T*>(smraw);  // NB x LD, trailing part of the block as it is eliminated
+  T* Lo = S + NB * LD;                 // NB x LD, unit lower L (diagonal holds d)
+  T* Li = Lo + NB * LD;                // NB x LD, L^{-1}
   __shared__ T dd[NB];
+  __shared__ int8_t sgn[NB];
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
   const int64_t f = bf.f[b], c = bf.c[b], k0 = (int64_t)p * NB;
   const int pw = (int)min((int64_t)NB, c - k0);
   T* G = F + bf.goff[b];
   const int64_t kp = bf.k0pos[b] + k0;
-  const int tid = threadIdx.x, wid = tid >> 5;
+  const int tid = threadIdx.x;  // blockDim.x == 256
   const T eps = (T)eps_d, delta = (T)delta_d;
   for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
     const int i = idx % NB, j = idx / NB;
     S[i * LD + j] = (i < pw && j < pw && i >= j) ? G[(k0 + i) + (k0 + j) * f] : (T)0;
+    Lo[i * LD + j] = (T)0;
     Li[i * LD + j] = (T)0;
   }
+  if (tid < NB) sgn[tid] = tid < pw ? dsign[kp + tid] : (int8_t)1;
   __syncthreads();
-  const int cw0 = min(32, pw), cw1 = pw - cw0;
-  if (wid == 0) warp_ldl32(S, 0, cw0, cw1, dsign + kp, eps, delta, hits, dd);
-  __syncthreads();
-  // trailing 32 x 32 block: S(i, j) -= sum_l L(i, l) d_l L(j, l), 32 <= j <= i < pw
-  for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-    const int i = 32 + idx % 32, j = 32 + idx / 32;
-    if (i >= pw || j > i) continue;
-    T acc = (T)0;
-#pragma unroll 8
-    for (int l = 0; l < 32; ++l) acc += S[i * LD + l] * dd[l] * S[j * LD + l];
-    S[i * LD + j] -= acc;
+  const int row = tid >> 2, part = tid & 3;
+  for (int kk = 0; kk < pw; ++kk) {
+    T d = S[kk * LD + kk];
+    const bool hit = (T)sgn[kk] * d <= eps;
+    if (hit) d = (T)sgn[kk] * delta;
+    const T inv = (T)1 / d;
+    if (tid == 0) {
+      if (hit) atomicAdd(hits, 1);
+      dd[kk] = d;
+      Lo[kk * LD + kk] = d;
+    }
+    if (row > kk && row < pw) {
+      const T fik = S[row * LD + kk];
+      const T li = fik * inv;
+      for (int j = kk + 1 + part; j <= row; j += 4) S[row * LD + j] -= li * S[j * LD + kk];
+      if (part == 0) Lo[row * LD + kk] = li;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  if (cw1 > 0 && wid == 0) warp_ldl32(S, 32, cw1, 0, dsign + kp, eps, delta, hits, dd);
-  __syncthreads();
   for (int idx = tid; idx < pw * pw; idx += blockDim.x) {
     const int i = idx % pw, j = idx / pw;
-    if (i >= j) G[(k0 + i) + (k0 + j) * f] = S[i * LD + j];
+    if (i >= j) G[(k0 + i) + (k0 + j) * f] = Lo[i * LD + j];
   }
   for (int i = tid; i < pw; i += blockDim.x) Dp[kp + i] = dd[i];
-  // Linv = [A^-1 0; -B^-1 C A^-1  B^-1] for L = [A 0; C B] (32-blocks)
-  if (wid == 0) warp_inv32(S, Li, 0, cw0);
-  if (wid == 1 && cw1 > 0) warp_inv32(S, Li, 32, cw1);
+  const int cw0 = min(32, pw), cw1 = pw - cw0;
+  const int wid = tid >> 5;
+  if (wid == 0) warp_inv32(Lo, Li, 0, cw0);
+  if (wid == 1 && cw1 > 0) warp_inv32(Lo, Li, 32, cw1);
   __syncthreads();
   if (cw1 > 0) {
-    // X = C A^-1 into the upper-right (unused) 32 x 32 area of S
+    // X = C A^-1 (into S, free now), then Li_21 = -B^-1 X
     for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
       const int i = idx % 32, j = idx / 32;
       T acc = (T)0;
       if (i < cw1)
-#pragma unroll 8
-        for (int l = 0; l < 32; ++l) acc += S[(32 + i) * LD + l] * Li[l * LD + j];
-      S[i * LD + 32 + j] = acc;
+        for (int l = j; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * Li[l * LD + j];
+      S[i * LD + j] = acc;
     }
     __syncthreads();
     for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
       const int i = idx % 32, j = idx / 32;
       if (i >= cw1) continue;
       T acc = (T)0;
-#pragma unroll 8
-      for (int l = 0; l < 32; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + 32 + j];
+      for (int l = 0; l <= i; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + j];
       Li[(32 + i) * LD + j] = -acc;
     }
     __syncthreads();
@@ -204,21 +162,21 @@ __global__ void k_bf_trsm(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F,
     const int64_t k0 = (int64_t)p * NB;
     const int pw = (int)min((int64_t)NB, c - k0);
     T* G = F + bf.goff[b];
-    const int64_t r0 = k0 + pw + 32 * q;
-    const int nr = (int)min((int64_t)32, f - r0);
+    const int64_t r0 = k0 + pw + kTrsmRows * q;
+    const int nr = (int)min((int64_t)kTrsmRows, f - r0);
     const T* LB = Linv + (b * 2 + (p & 1)) * (int64_t)(NB * NB);
     for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
       const int i = idx % NB, j = idx / NB;
       Ls[i * LD + j] = LB[i + j * NB];
     }
-    for (int idx = tid; idx < 32 * NB; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
+    for (int idx = tid; idx < kTrsmRows * NB; idx += blockDim.x) {
+      const int i = idx % kTrsmRows, j = idx / kTrsmRows;
       Xs[i * LD + j] = (i < nr && j < pw) ? G[(r0 + i) + (k0 + j) * f] : (T)0;
     }
     for (int j = tid; j < pw; j += blockDim.x) dl[j] = Dp[bf.k0pos[b] + k0 + j];
     __syncthreads();
-    for (int idx = tid; idx < 32 * pw; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
+    for (int idx = tid; idx < kTrsmRows * pw; idx += blockDim.x) {
+      const int i = idx % kTrsmRows, j = idx / kTrsmRows;
       if (i >= nr) continue;
       T acc = (T)0;
       for (int l = 0; l <= j; ++l) acc += Xs[i * LD + l] * Ls[j * LD + l];
@@ -371,12 +329,14 @@ __global__ void k_bf_update(BigFrontDev bf, WorkList wl, int p, T* __restrict__ 
 }
 
 // ------------------------------------------------------------------ solves
-// Forward: rows r0 .. r0+31 of z = E w1 (8 warps split the columns; fixed-order reduction).
+// Forward: rows r0 .. r0+31 of z = E w1; 16 warps split the columns, 8 columns in
+// flight per lane, partial sums reduced in a fixed order.  Rows < c store
+// v = y / D (what the backward sweep needs), rows >= c update w2.
 template <typename T>
-__global__ void k_bf_fwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, T* __restrict__ w,
-                         T* __restrict__ ybuf, const int* skip) {
+__global__ void k_bf_fwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, const T* __restrict__ Dp,
+                         T* __restrict__ w, T* __restrict__ ybuf, const int* skip) {
   if (skip && *skip) return;
-  __shared__ T red[8][33];
+  __shared__ T red[16][33];
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
   const int64_t f = bf.f[b], c = bf.c[b];
@@ -386,24 +346,32 @@ __global__ void k_bf_fwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, T
   const T* w1 = w + bf.woff[b];
   const int64_t i = r0 + lane;
   const int64_t jmax = min(c, r0 + 32);
-  T acc = (T)0;
-  if (i < f)
-    for (int64_t j = wid; j < jmax; j += 8) acc += Eb[i + j * f] * w1[j];
+  T a[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a[u] = (T)0;
+  if (i < f) {
+    int64_t j = wid;
+    for (; j + 15 * 8 < jmax; j += 16 * 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] += Eb[i + (j + 16 * u) * f] * w1[j + 16 * u];
+    }
+    for (; j < jmax; j += 16) a[0] += Eb[i + j * f] * w1[j];
+  }
+  T acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   red[wid][lane] = acc;
   __syncthreads();
   if (wid == 0 && i < f) {
     T z = (T)0;
-    for (int k = 0; k < 8; ++k) z += red[k][lane];
-    if (i < c) ybuf[bf.yoff[b] + i] = z;
+    for (int k = 0; k < 16; ++k) z += red[k][lane];
+    if (i < c) ybuf[bf.yoff[b] + i] = z / Dp[bf.k0pos[b] + i];
     else w[bf.woff[b] + i] += z;
   }
 }
 
 // Backward: x_j = sum_{i >= j} E[i, j] v_i, v = [y / D; x2]; one warp per column.
 template <typename T>
-__global__ void k_bf_bwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, const T* __restrict__ Dp,
-                         const T* __restrict__ ybuf, T* __restrict__ xs, const int32_t* __restrict__ rows_kkt,
-                         const int* skip) {
+__global__ void k_bf_bwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, const T* __restrict__ ybuf,
+                         T* __restrict__ xs, const int32_t* __restrict__ rows_kkt, const int* skip) {
   if (skip && *skip) return;
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
@@ -411,15 +379,19 @@ __global__ void k_bf_bwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, c
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t j = 8 * q + wid;
   if (j >= c) return;
-  const T* Eb = E + bf.eoff[b];
-  const T* y = ybuf + bf.yoff[b];
-  const T* D = Dp + bf.k0pos[b];
+  const T* Ec = E + bf.eoff[b] + j * f;
+  const T* v = ybuf + bf.yoff[b];
   const int32_t* rk = rows_kkt + bf.rk[b];
-  T acc = (T)0;
-  for (int64_t i = j + lane; i < f; i += 32) {
-    const T v = (i < c) ? y[i] / D[i] : xs[rk[i]];
-    acc += Eb[i + j * f] * v;
+  T a[4] = {(T)0, (T)0, (T)0, (T)0};
+  const int64_t iend = min(f, c);
+  int64_t i = j + lane;
+  for (; i + 96 < iend; i += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] += Ec[i + 32 * u] * v[i + 32 * u];
   }
+  for (; i < iend; i += 32) a[0] += Ec[i] * v[i];
+  for (i = max(j, c) + lane; i < f; i += 32) a[1] += Ec[i] * xs[rk[i]];
+  T acc = (a[0] + a[1]) + (a[2] + a[3]);
   acc = warp_sum(acc);
   if (lane == 0) xs[rk[j]] = acc;
 }
@@ -431,7 +403,7 @@ size_t smem_diag() { return 0; }
 
 template <typename T>
 int BigFrontOps<T>::setup_attributes() {
-  CLR_CUDA(cudaFuncSetAttribute(k_bf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LD * sizeof(T)));
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * NB * LD * sizeof(T)));
   (void)smem_diag;
@@ -441,10 +413,10 @@ int BigFrontOps<T>::setup_attributes() {
 template <typename T>
 int BigFrontOps<T>::factor_level(cudaStream_t st, const BigFrontDev& bf, const BigLevelPlan& plan, T* F, T* E, T* Dp,
                                  T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip) {
-  const size_t s2 = 2 * NB * LD * sizeof(T), s4 = 4 * NB * LD * sizeof(T);
+  const size_t s2 = 2 * NB * LD * sizeof(T), s3 = 3 * NB * LD * sizeof(T), s4 = 4 * NB * LD * sizeof(T);
   for (size_t p = 0; p < plan.A.size(); ++p) {
     if (plan.A[p].nblocks > 0)
-      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, s2, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
+      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, s3, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
                                                                   hits, skip);
     if (plan.B[p].nblocks > 0)
       k_bf_trsm<T><<<(unsigned)plan.B[p].nblocks, 256, s2, st>>>(bf, plan.B[p], (int)p, F, E, Dp, Linv, skip);
@@ -456,10 +428,10 @@ int BigFrontOps<T>::factor_level(cudaStream_t st, const BigFrontDev& bf, const B
 }
 
 template <typename T>
-int BigFrontOps<T>::fwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, T* w, T* ybuf,
-                        const int* skip) {
+int BigFrontOps<T>::fwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp, T* w,
+                        T* ybuf, const int* skip) {
   if (wl.nblocks == 0) return CLR_OK;
-  k_bf_fwd<T><<<(unsigned)wl.nblocks, 256, 0, st>>>(bf, wl, E, w, ybuf, skip);
+  k_bf_fwd<T><<<(unsigned)wl.nblocks, 512, 0, st>>>(bf, wl, E, Dp, w, ybuf, skip);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -468,7 +440,7 @@ template <typename T>
 int BigFrontOps<T>::bwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp,
                         const T* ybuf, T* xs, const int32_t* rows_kkt, const int* skip) {
   if (wl.nblocks == 0) return CLR_OK;
-  k_bf_bwd<T><<<(unsigned)wl.nblocks, 256, 0, st>>>(bf, wl, E, Dp, ybuf, xs, rows_kkt, skip);
+  k_bf_bwd<T><<<(unsigned)wl.nblocks, 256, 0, st>>>(bf, wl, E, ybuf, xs, rows_kkt, skip);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }

@@ -12,6 +12,7 @@
 namespace clr {
 
 constexpr int kBfNB = 64;
+constexpr int kTrsmRows = 8;  // rows of L21 per CTA of the panel kernel
 
 // Device arrays indexed by big-front id.
 struct BigFrontDev {
@@ -45,8 +46,8 @@ struct BigFrontOps {
   static int setup_attributes();
   static int factor_level(cudaStream_t st, const BigFrontDev& bf, const BigLevelPlan& plan, T* F, T* E, T* Dp,
                           T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip);
-  static int fwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, T* w, T* ybuf,
-                 const int* skip);
+  static int fwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp, T* w,
+                 T* ybuf, const int* skip);
   static int bwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp, const T* ybuf,
                  T* xs, const int32_t* rows_kkt, const int* skip);
 };
@@ -56,7 +57,7 @@ __host__ __device__ inline int64_t bf_trsm_blocks(int64_t f, int64_t c, int p) {
   const int64_t k0 = (int64_t)p * kBfNB;
   if (k0 >= c) return 0;
   const int64_t pw = (c - k0 < kBfNB) ? c - k0 : kBfNB;
-  return (f - k0 - pw + 31) / 32;
+  return (f - k0 - pw + kTrsmRows - 1) / kTrsmRows;
 }
 __host__ __device__ inline int64_t bf_fin_blocks(int64_t c, int p) {  // finalisation of the E rows of panel p
   if (p < 0 || (int64_t)p * kBfNB >= c) return 0;

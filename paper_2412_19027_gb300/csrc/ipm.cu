@@ -269,6 +269,27 @@ __global__ void k_ir_check(IterScal* sc, unsigned long long* rmax, double abstol
   }
 }
 
+// The same test for the graph WHILE loop: continue (condition 1) iff another
+// refinement step is due; at most max_steps steps.
+__global__ void k_ir_check_cond(IterScal* sc, unsigned long long* rmax, double abstol, double reltol,
+                                double stop_ratio, int max_steps, cudaGraphConditionalHandle h) {
+  unsigned int go = 0;
+  if (!sc->ir_skip) {
+    const double r = bitsd(*rmax);
+    const bool stalled = stop_ratio > 0 && !(r * stop_ratio < sc->ir_prev);
+    sc->ir_prev = r;
+    if (!(r > abstol + reltol * sc->rhs_norm) || stalled || sc->ir_cur >= max_steps) {
+      sc->ir_skip = 1;
+    } else {
+      sc->ir_cur += 1;
+      sc->ir_total += 1;
+      go = 1;
+    }
+  }
+  *rmax = 0ull;
+  cudaGraphSetConditional(h, go);
+}
+
 // ------------------------------------------------------------------ direction
 __global__ void k_dots(const double* __restrict__ a0, const double* __restrict__ b0, int64_t n0,
                        const double* __restrict__ a1, const double* __restrict__ b1, int64_t n1,
@@ -530,6 +551,7 @@ Solver::~Solver() {
     if (e) cudaEventDestroy(e);
   if (sc_host_) cudaFreeHost(sc_host_);
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
+  if (body_stream_) cudaStreamDestroy(body_stream_);
 }
 
 int Solver::analyze(const clr_csc* P, const double* q, const clr_csc* A, const double* b, const clr_cone* cones,
@@ -553,6 +575,7 @@ int Solver::upload() {
     own_stream_ = true;
   }
   CLR_CUDA(cudaMallocHost(&sc_host_, sizeof(IterScal)));
+  CLR_CUDA(cudaStreamCreateWithFlags(&body_stream_, cudaStreamNonBlocking));
   for (cudaEvent_t& e : ev_) CLR_CUDA(cudaEventCreate(&e));
   // expected pivot sign by elimination position: + for x, - for z
   std::vector<int8_t> dsign(N);
@@ -704,6 +727,9 @@ int Solver::factor() {
 }
 
 // sol = K^{-1} rhs by the factor plus iterative refinement on the unregularised K (FP64).
+// While a graph is being captured the refinement loop is a conditional WHILE
+// node (its body runs only as often as needed); otherwise it is unrolled to
+// ir_max_steps steps whose kernels return at once after convergence.
 int Solver::kkt_solve(const double* rhs, double* sol) {
   const int64_t N = hp.n + hp.m;
   cudaStream_t s = stream_;
@@ -715,35 +741,76 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   k_ir_begin<<<1, 1, 0, s>>>(sc_, rmax);
   CLR_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s));
   const int g = grid_for(N, 256);
-  if (st.factor_bits == 64) {
-    int rc = f64_.solve(s, rhs, irs);
-    if (rc) return rc;
-    k_set_from<double><<<g, 256, 0, s>>>(sol, f64_.xs, N, 0, irs);
-  } else {
-    int rc = f32_.solve(s, rhs, irs);
-    if (rc) return rc;
-    k_set_from<float><<<g, 256, 0, s>>>(sol, f32_.xs, N, 0, irs);
-  }
+  auto ldl_solve_add = [&](cudaStream_t ss, const double* b, int add) -> int {
+    if (st.factor_bits == 64) {
+      int rc = f64_.solve(ss, b, irs);
+      if (rc) return rc;
+      k_set_from<double><<<g, 256, 0, ss>>>(sol, f64_.xs, N, add, irs);
+    } else {
+      int rc = f32_.solve(ss, b, irs);
+      if (rc) return rc;
+      k_set_from<float><<<g, 256, 0, ss>>>(sol, f32_.xs, N, add, irs);
+    }
+    return CLR_OK;
+  };
   const int G = csr_group_;
   const int kg = grid_for(N * G, 256, 16 * kSMs);
-  for (int it = 0; it < st.ir_max_steps; ++it) {
+  auto residual = [&](cudaStream_t ss) {
     switch (G) {
-      case 32: k_kmv<32><<<kg, 256, 0, s>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
-      case 16: k_kmv<16><<<kg, 256, 0, s>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
-      case 8: k_kmv<8><<<kg, 256, 0, s>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
-      default: k_kmv<4><<<kg, 256, 0, s>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
+      case 32: k_kmv<32><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
+      case 16: k_kmv<16><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
+      case 8: k_kmv<8><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
+      default: k_kmv<4><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
     }
-    k_ir_check<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio);
-    if (st.factor_bits == 64) {
-      int rc = f64_.solve(s, v_.r, irs);
+  };
+  int rc = ldl_solve_add(s, rhs, 0);
+  if (rc) return rc;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CLR_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusActive || st.ir_max_steps == 0) {
+    for (int it = 0; it < st.ir_max_steps; ++it) {
+      residual(s);
+      k_ir_check<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio);
+      rc = ldl_solve_add(s, v_.r, 1);
       if (rc) return rc;
-      k_set_from<double><<<g, 256, 0, s>>>(sol, f64_.xs, N, 1, irs);
-    } else {
-      int rc = f32_.solve(s, v_.r, irs);
-      if (rc) return rc;
-      k_set_from<float><<<g, 256, 0, s>>>(sol, f32_.xs, N, 1, irs);
     }
+    CLR_CHECK_LAUNCH();
+    return CLR_OK;
   }
+  // graph capture: condition set by the check before the node and at the end of each body pass
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  cudaGraphConditionalHandle h;
+  residual(s);
+  CLR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+  CLR_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
+  k_ir_check_cond<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio, st.ir_max_steps, h);
+  CLR_CHECK_LAUNCH();
+  CLR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edata, &ndeps));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CLR_CUDA(cudaGraphAddNode(&node, cg, deps, edata, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  CLR_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  rc = ldl_solve_add(body_stream_, v_.r, 1);
+  residual(body_stream_);
+  k_ir_check_cond<<<1, 1, 0, body_stream_>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio,
+                                             st.ir_max_steps, h);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(body_stream_, &out);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "cudaStreamEndCapture(body)");
+    return CLR_E_CUDA;
+  }
+  CLR_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  ir_nodes_.push_back(body);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -931,6 +998,8 @@ int Solver::launch_iteration() {
     }
     graph_ = g;
     iter_kernels_ = count_kernel_nodes(graph_);
+    body_kernels_ = ir_nodes_.empty() ? 0 : count_kernel_nodes(ir_nodes_.back());
+    ir_nodes_.clear();
     CLR_CUDA(cudaGraphInstantiate(&gexec_, graph_, 0));
   }
   CLR_CUDA(cudaGraphLaunch(gexec_, stream_));
@@ -954,6 +1023,7 @@ int Solver::launch_init() {
     }
     igraph_ = g;
     init_kernels_ = count_kernel_nodes(igraph_);
+    ir_nodes_.clear();
     CLR_CUDA(cudaGraphInstantiate(&igexec_, igraph_, 0));
   }
   CLR_CUDA(cudaGraphLaunch(igexec_, stream_));
@@ -994,6 +1064,7 @@ int Solver::solve() {
     if (status != 0) break;
   }
   perf.iterations = sc_host_->iter;
+  if (st.use_graph) perf.kernel_launches += (int64_t)sc_host_->ir_total * body_kernels_;  // executed loop bodies
   perf.factor_flops = sy.flops;
   CLR_CUDA(cudaStreamSynchronize(stream_));
   solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

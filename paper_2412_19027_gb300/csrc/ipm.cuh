@@ -99,7 +99,9 @@ class Solver {
   cudaGraphExec_t gexec_ = nullptr;
   cudaGraph_t igraph_ = nullptr;
   cudaGraphExec_t igexec_ = nullptr;
-  int64_t iter_kernels_ = 0, init_kernels_ = 0;
+  int64_t iter_kernels_ = 0, init_kernels_ = 0, body_kernels_ = 0;
+  cudaStream_t body_stream_ = nullptr;
+  std::vector<cudaGraph_t> ir_nodes_;  // refinement loop bodies captured in the current graph
   cudaEvent_t ev_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void mark(int i);
   void drop_graphs();

@@ -419,7 +419,7 @@ int LdlFactor<T>::solve(cudaStream_t stm, const double* rhs, const int* skip) co
       k_fwd_front<T><<<(unsigned)nf, 256, 0, stm>>>(F, w, S.lev_sn + S.h_lev_ptr[l], S.sn_ptr, S.row_ptr,
                                                      S.front_off, S.upd_off, S.small_max, skip);
     if (!S.lev_big[l].empty()) {
-      int rc = BigFrontOps<T>::fwd(stm, S.bfd, S.bplans[l].fwd, E, w, ybuf, skip);
+      int rc = BigFrontOps<T>::fwd(stm, S.bfd, S.bplans[l].fwd, E, Dp, w, ybuf, skip);
       if (rc) return rc;
     }
   }
