@@ -280,6 +280,38 @@ int clr_ldl_solve(const clr_csc* K_lower, const double* signs, const int64_t* or
                   double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
                   int32_t* dyn_hits_out);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory where they need a
+ * solve -- code running while a CUDA graph is being captured (cudaMalloc is
+ * not allowed there), real-time control loops that must not allocate after
+ * start-up (e.g. one small KKT solve per period of a predictive controller),
+ * and plug-ins whose device memory belongs to a host framework.
+ * ------------------------------------------------------------------------ */
+
+/* Largest system order accepted by clr_dense_ldl_solve_noalloc. */
+#define CLR_NOALLOC_MAX_N 128
+
+/* Dense LDL^T (natural order, no pivoting, dynamic regularisation as in
+ * clr_ldl_solve) and solve of one quasi-definite system, on DEVICE pointers:
+ *   K      N x N column-major, lower triangle read (upper ignored)
+ *   signs  N expected pivot signs (> 0: +1, else -1)
+ *   rhs    N;  x (output) N;  D (output, may be NULL) N pivots
+ *   dyn_hits (output, device int, may be NULL): pivots replaced
+ *   stream cudaStream_t as void* (NULL: legacy default stream)
+ * No device memory is allocated or freed: the working matrix lives in one
+ * static device array of CLR_NOALLOC_MAX_N^2 doubles (128 KiB) that every GPU
+ * loading the library keeps until the process exits.  N > CLR_NOALLOC_MAX_N
+ * gives CLR_E_UNSUPPORTED; N < 0 or a NULL required pointer CLR_E_INVALID.
+ * The first call on a device resolves that array's address with
+ * cudaGetSymbolAddress (with the device current); make the first call on each
+ * device before any stream capture.  All calls on a device share the array:
+ * calls whose kernels overlap on the GPU (different streams without ordering)
+ * race on it.  Asynchronous: the results are ready when the stream is. */
+int clr_dense_ldl_solve_noalloc(const double* K, const double* signs, int32_t N, const double* rhs, double* x,
+                                double* D, double dyn_reg_eps, double dyn_reg_delta, int32_t* dyn_hits,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,8 @@ _LIB = None
 EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr_get_solution", "clr_update_qb",
            "clr_get_symbolic_stats", "clr_get_perf", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
            "clr_set_allocator", "clr_free", "clr_error_string", "clr_status_string", "clr_last_cuda_error",
-           "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_ldl_solve"]
+           "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_ldl_solve",
+           "clr_dense_ldl_solve_noalloc"]
 
 
 def _lib():
@@ -107,6 +108,7 @@ def _lib():
                                                                                             P(C.c_double)]
         L.clr_ldl_solve.argtypes = [P(clr_csc), P(C.c_double), P(C.c_int64), C.c_int32, C.c_double, C.c_double,
                                     P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
+        L.clr_dense_ldl_solve_noalloc.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_double, C.c_double, vp, vp]
         _LIB = L
     return _LIB
 
@@ -304,3 +306,12 @@ def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1
     _check(_lib().clr_ldl_solve(C.byref(Kc), _dptr(signs), ordp, factor_bits, dyn_reg_eps, dyn_reg_delta, _dptr(rhs),
                                 _dptr(x), _dptr(D), C.byref(hits)), "clr_ldl_solve")
     return x, D, hits.value
+
+
+def clr_dense_ldl_solve_noalloc(K_ptr, signs_ptr, N, rhs_ptr, x_ptr, D_ptr=None, dyn_reg_eps=1e-13,
+                                dyn_reg_delta=2e-7, hits_ptr=None, stream_ptr=None):
+    """Device-pointer call of the allocation-free dense LDL^T solve (pointers as ints)."""
+    _check(_lib().clr_dense_ldl_solve_noalloc(C.c_void_p(K_ptr), C.c_void_p(signs_ptr), int(N), C.c_void_p(rhs_ptr),
+                                              C.c_void_p(x_ptr), C.c_void_p(D_ptr), float(dyn_reg_eps),
+                                              float(dyn_reg_delta), C.c_void_p(hits_ptr), C.c_void_p(stream_ptr)),
+           "clr_dense_ldl_solve_noalloc")
