@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--factor-bits", type=int, default=32, choices=[32, 64])
-    ap.add_argument("--ir-stop-ratio", type=float, default=None)
+    ap.add_argument("--ir-stop-ratio", type=float, default=5.0,
+                    help="refinement stall test (0 = the paper's rule only: tolerance or T_max)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch kernels directly instead of replaying captured graphs (for per-kernel profiling)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -188,9 +191,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
 
     def make(bits):
-        kw = {}
-        if args.ir_stop_ratio is not None:
-            kw["ir_stop_ratio"] = args.ir_stop_ratio
+        kw = {"ir_stop_ratio": args.ir_stop_ratio, "use_graph": 0 if args.no_graph else 1}
         st = clr.clr_default_settings(bits, **kw)
         s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
         s.set_stream(stream.cuda_stream)
@@ -304,7 +305,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "seed": args.seed, "factor_bits": args.factor_bits,
                            "eps_feas": 1e-8, "l2": "flushed (256 MB write) before every timed solve",
                            "parallelism": "replicas" if ws > 1 else "single GPU",
-                           "ir_stop_ratio": main.settings.ir_stop_ratio},
+                           "ir_stop_ratio": main.settings.ir_stop_ratio, "cuda_graphs": not args.no_graph},
                 "time_to_tol_ms": {"median": float(np.median(times)), "fp64_factor": fp64["time_to_tol_ms"] if fp64
                                    else None},
                 "iterations": infos[-1]["iterations"], "status": infos[-1]["status_name"],
