@@ -14,6 +14,13 @@ metric  IPM iterations per second (total iterations / device time), for the
 N > 1   independent replicas, one problem per GPU (weak scaling, no
         collective on the data path).
 
+serving  the MPC request stream (10 000 QPs, horizon U{10..50}, states
+        U{4..12}, inputs U{2..4}, stable random dynamics, boxes and one SOC
+        per step) through the continuous-batching server: solves/s and
+        p50/p99 latency (submit -> result readable) at Poisson arrivals, next
+        to one-at-a-time solves (clr_setup + clr_solve + read-back + free per
+        problem), under "serving".
+
 --impl reference times the FP64 CPU oracle on the host cores instead.
 """
 import argparse
@@ -51,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10_000)
+    ap.add_argument("--serve-bits", type=int, default=64, choices=[32, 64])
     return ap.parse_args()
 
 
@@ -134,6 +144,101 @@ print(json.dumps(dict(iters=r.iterations, setup=t1 - t0, total=t2 - t1)))
     return {"value": d["iters"] / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "first %d IPM iterations of the same workload (FP64 NumPy/LAPACK oracle, dense KKT "
                       "8600x8600), setup time subtracted; %.1f s of CPU work" % (d["iters"], d["total"])}
+
+
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def serve_stream(clr, sv, reqs, rate):
+    """Submit reqs at Poisson arrivals of the given rate (per s; None = all at
+    once) from a thread, wait for every result; latencies measured by the
+    server (submit -> result readable)."""
+    rng = np.random.default_rng(12345)
+    gaps = rng.exponential(1.0 / rate, len(reqs)) if rate else np.zeros(len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    tickets = [None] * len(reqs)
+    ready = threading.Event()
+
+    def submitter():
+        t0 = time.perf_counter()
+        for k, r in enumerate(reqs):
+            ta = t0 + arrivals[k]
+            while True:
+                d = ta - time.perf_counter()
+                if d <= 0:
+                    break
+                if d > 2e-3:
+                    time.sleep(d - 1e-3)
+            tickets[k] = sv.submit(r)
+            if k == 0:
+                ready.set()
+        ready.set()
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    lat, iters, statuses = [], [], {}
+    for k in range(len(reqs)):
+        while tickets[k] is None:
+            time.sleep(1e-4)
+        res = sv.wait(tickets[k], 600.0)
+        if res is None:
+            raise RuntimeError("serving request timed out")
+        info = res[3]
+        lat.append(info["solve_s"])
+        iters.append(info["iterations"])
+        statuses[info["status_name"]] = statuses.get(info["status_name"], 0) + 1
+    t_end = time.perf_counter()
+    th.join()
+    return {"requests": len(reqs), "offered_per_s": rate, "solves_per_s": len(reqs) / (t_end - t_start),
+            "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99), "mean_iterations": float(np.mean(iters)),
+            "statuses": statuses}
+
+
+def run_serving(args, clr, W):
+    """The MPC request stream through the continuous-batching server, next to one-at-a-time solves."""
+    t_gen = time.perf_counter()
+    seeds = W.mpc_stream(args.seed, args.serve_requests)
+    probs = [W.mpc_qp(sd) for sd in seeds]
+    reqs = [clr.Request(p.P, p.q, p.A, p.b, p.cones) for p in probs]
+    t_gen = time.perf_counter() - t_gen
+    st = clr.clr_default_settings(args.serve_bits)
+    # one at a time: the whole public call sequence per problem
+    k1 = min(200, len(probs))
+    lat1 = []
+    t0 = time.perf_counter()
+    for p in probs[:k1]:
+        a = time.perf_counter()
+        s_ = clr.clr_setup(p.P, p.q, p.A, p.b, p.cones, st)
+        s_.solve()
+        s_.solution()
+        s_.free()
+        lat1.append(time.perf_counter() - a)
+    rate1 = k1 / (time.perf_counter() - t0)
+    one = {"solves_per_s": rate1, "p50_ms": 1e3 * _pct(lat1, 50), "p99_ms": 1e3 * _pct(lat1, 99),
+           "sample": "first %d problems of the stream, sequential" % k1}
+    sv = clr.Server(device_bytes=16 << 30, max_cohort=256, max_active=4, settings=st)
+    serve_stream(clr, sv, reqs[:200], None)  # warm-up (pools, module load)
+    sat = serve_stream(clr, sv, reqs, None)
+    sat["arrivals"] = "all submitted at once (saturation)"
+    pois = serve_stream(clr, sv, reqs, 0.8 * sat["solves_per_s"])
+    pois["arrivals"] = "Poisson at 0.8 x saturation throughput"
+    sweep = []
+    for f in (0.25, 0.5, 0.8, 1.0, 1.2):
+        nsw = int(min(500, len(reqs), max(50, 10.0 * f * rate1)))  # at most ~10 s per point
+        r = serve_stream(clr, sv, reqs[:nsw], f * rate1)
+        r["offered_x_one_at_a_time"] = f
+        sweep.append(r)
+    stats = sv.stats()
+    sv.close()
+    return {"workload": "MPC QP stream: %d requests, T U{10..50}, nx U{4..12}, nu U{2..4}, |x|<=5, |u|<=1, "
+                        "||u_t||<=1.2, cost x'x + 0.1 u'u; FP%d factor" % (len(reqs), args.serve_bits),
+            "server": {"max_cohort": 256, "max_active": 4, "device_budget_bytes": 16 << 30,
+                       "cohorts": stats["cohorts"], "max_cohort_seen": stats["max_cohort_seen"],
+                       "peak_device_bytes": stats["peak_bytes"]},
+            "one_at_a_time": one, "saturation": sat, "poisson": pois, "sweep_vs_one_at_a_time": sweep,
+            "speedup_solves_per_s": sat["solves_per_s"] / rate1, "generation_s": t_gen}
 
 
 def run_reference(args):
@@ -290,6 +395,10 @@ def run_ours(args):
                 "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if args.factor_bits == 32
                                                 else "GB300 FP64 nominal 1.25 TFLOP/s")}
 
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(args, clr, W)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
@@ -313,6 +422,7 @@ def run_ours(args):
                 "res_dual": infos[-1]["res_dual"], "ir_steps_total": infos[-1]["ir_steps_total"],
                 "fp64_factor": fp64, "phase_ms_per_solve": phases, "roofline": roofline,
                 "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+                "serving": serving,
                 "symbolic": {k: sym[k] for k in ("kkt_dim", "l_nnz", "factor_flops", "n_supernodes", "n_levels",
                                                  "max_front")}}
         print(json.dumps(line), flush=True)

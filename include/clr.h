@@ -200,6 +200,106 @@ int clr_update_qb(clr_solver* s, const double* q, const double* b);
 
 int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out);
 
+/* ------------------------------------------------------------------------
+ * Cohorts ("batches"): many independent problems in one solver.  The paper
+ * solves one problem at a time; for many small problems of uneven size the
+ * per-iteration device step runs over all of them at once: the problems are
+ * merged block-diagonally (x stacked; constraint rows family-major, each
+ * family holding its rows of every problem in turn) and one launch of each
+ * kernel -- one replay of the iteration's CUDA graph -- advances every
+ * problem.  Every scalar of Algorithm 1 (tau, kappa, mu, step lengths,
+ * sigma, regularisation, refinement counters, status) is kept per problem,
+ * reductions are summed per problem in a fixed order, and each problem keeps
+ * its own equilibration and fill-reducing order, so a problem's iterates are
+ * the ones it has when solved alone (up to the row grouping of the K
+ * products).  A problem that stops (solved, infeasible, ...) is frozen while
+ * the others go on; the solve returns when every problem has stopped.
+ * ------------------------------------------------------------------------ */
+
+/* One problem of a cohort: the arguments of clr_setup, all host, read during
+ * the call only. */
+typedef struct {
+  const clr_csc* P_upper;
+  const double* q;
+  const clr_csc* A;
+  const double* b;
+  const clr_cone* cones;
+  int32_t ncones;
+} clr_problem;
+
+/* Setup of nprob >= 1 problems as one solver (the host analysis of each
+ * problem runs on worker threads).  All PSD cones of the cohort must share one
+ * order (else CLR_E_UNSUPPORTED).  Errors as clr_setup, for the first failing
+ * problem.  clr_solve solves every problem; clr_get_solution and
+ * clr_update_qb act on problem 0; clr_get_perf covers the cohort. */
+int clr_batch_setup(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st);
+
+/* Host-only part of clr_batch_setup (as clr_analyze for one problem): the
+ * merged cohort can be inspected with clr_get_symbolic_stats but not solved. */
+int clr_batch_analyze(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st);
+
+/* Number of problems held by a solver (1 after clr_setup). */
+int32_t clr_batch_size(const clr_solver* s);
+
+/* clr_get_solution for problem i of the cohort (CLR_E_INVALID if i is out of range). */
+int clr_batch_get(const clr_solver* s, int32_t i, double* x, double* sl, double* z, clr_info* info);
+
+/* clr_update_qb for problem i of the cohort. */
+int clr_batch_update_qb(clr_solver* s, int32_t i, const double* q, const double* b);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  The paper has no
+ * serving layer; this is the production pattern for streams of small solves
+ * (e.g. one model-predictive-control QP per controller and period).
+ * Submitted problems are copied, analysed on host worker threads, and
+ * admitted as cohorts (see clr_batch_setup) whenever one of max_active slots
+ * is free and the device memory in use is below device_bytes: every analysed
+ * request waiting at that moment joins the new cohort (at most max_cohort).
+ * Up to max_active cohorts run at once on their own CUDA streams with their
+ * IPM iterations interleaved, so requests that arrive while others are on the
+ * GPU start as soon as a slot and memory free up.  A result is handed out as
+ * soon as its problem stops, not when its cohort does; it equals the result
+ * of clr_setup + clr_solve on the same problem up to the rounding of the K
+ * products.  All host threads are owned by the server.
+ * ------------------------------------------------------------------------ */
+typedef struct clr_server clr_server;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed;
+  int64_t cohorts;          /* cohorts formed so far */
+  int64_t max_cohort_seen;  /* largest cohort formed */
+  int64_t peak_bytes;       /* device memory held by live cohorts, peak */
+  int64_t bytes_in_use;     /* ... now */
+} clr_server_stats;
+
+/* Start a server on the current CUDA device.  st: settings of every solve
+ * (NULL: clr_default_settings(.., 64); use_graph is forced on).  Errors:
+ * CLR_E_INVALID (zero budget, max_cohort < 1, max_active < 1), CLR_E_CUDA. */
+int clr_server_create(clr_server** out, size_t device_bytes, int32_t max_cohort, int32_t max_active,
+                      const clr_settings* st);
+
+/* Queue one problem (deep-copied; never waits for the GPU).  *ticket
+ * identifies it in clr_server_poll / clr_server_wait.  Input errors found by
+ * the analysis are returned by poll/wait for that ticket. */
+int clr_server_submit(clr_server* sv, const clr_problem* p, uint64_t* ticket);
+
+/* CLR_E_AGAIN while the ticket is not done.  Once done: its result as
+ * clr_get_solution gives it (any output may be NULL), or its error code; the
+ * ticket is then released (CLR_E_INVALID afterwards).  In info, setup_s is the
+ * time from submit to the end of the host analysis and solve_s the latency
+ * from submit to the result being readable. */
+int clr_server_poll(clr_server* sv, uint64_t ticket, double* x, double* sl, double* z, clr_info* info);
+
+/* As clr_server_poll, waiting up to timeout_s seconds (CLR_E_TIMEOUT). */
+int clr_server_wait(clr_server* sv, uint64_t ticket, double timeout_s, double* x, double* sl, double* z,
+                    clr_info* info);
+
+int clr_server_get_stats(clr_server* sv, clr_server_stats* out);
+
+/* Stop the threads, wait for work on the device, free everything.  Tickets
+ * not yet done are dropped. */
+int clr_server_destroy(clr_server* sv);
+
 /* Device timing and launch count of the last clr_solve (CLR_E_STATE before it). */
 int clr_get_perf(const clr_solver* s, clr_perf* out);
 

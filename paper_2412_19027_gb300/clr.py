@@ -60,6 +60,17 @@ class clr_symbolic_stats(C.Structure):
                 ("n_dense_rows", C.c_int64)]
 
 
+class clr_problem(C.Structure):
+    _fields_ = [("P_upper", C.POINTER(clr_csc)), ("q", C.POINTER(C.c_double)), ("A", C.POINTER(clr_csc)),
+                ("b", C.POINTER(C.c_double)), ("cones", C.POINTER(clr_cone)), ("ncones", C.c_int32)]
+
+
+class clr_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("cohorts", C.c_int64), ("max_cohort_seen", C.c_int64), ("peak_bytes", C.c_int64),
+                ("bytes_in_use", C.c_int64)]
+
+
 class clr_perf(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("iterations", C.c_int32), ("factorizations", C.c_int32),
                 ("init_ms", C.c_double), ("resid_cones_ms", C.c_double), ("factor_ms", C.c_double),
@@ -71,7 +82,9 @@ EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr
            "clr_get_symbolic_stats", "clr_get_perf", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
            "clr_set_allocator", "clr_free", "clr_error_string", "clr_status_string", "clr_last_cuda_error",
            "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_ldl_solve",
-           "clr_dense_ldl_solve_noalloc"]
+           "clr_dense_ldl_solve_noalloc", "clr_batch_setup", "clr_batch_analyze", "clr_batch_size", "clr_batch_get",
+           "clr_batch_update_qb", "clr_server_create", "clr_server_submit", "clr_server_poll", "clr_server_wait",
+           "clr_server_get_stats", "clr_server_destroy"]
 
 
 def _lib():
@@ -109,6 +122,19 @@ def _lib():
         L.clr_ldl_solve.argtypes = [P(clr_csc), P(C.c_double), P(C.c_int64), C.c_int32, C.c_double, C.c_double,
                                     P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
         L.clr_dense_ldl_solve_noalloc.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_double, C.c_double, vp, vp]
+        L.clr_batch_setup.argtypes = [P(vp), C.c_int32, P(clr_problem), P(clr_settings)]
+        L.clr_batch_analyze.argtypes = [P(vp), C.c_int32, P(clr_problem), P(clr_settings)]
+        L.clr_batch_size.argtypes = [vp]
+        L.clr_batch_size.restype = C.c_int32
+        L.clr_batch_get.argtypes = [vp, C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double), P(clr_info)]
+        L.clr_batch_update_qb.argtypes = [vp, C.c_int32, P(C.c_double), P(C.c_double)]
+        L.clr_server_create.argtypes = [P(vp), C.c_size_t, C.c_int32, C.c_int32, P(clr_settings)]
+        L.clr_server_submit.argtypes = [vp, P(clr_problem), P(C.c_uint64)]
+        L.clr_server_poll.argtypes = [vp, C.c_uint64, P(C.c_double), P(C.c_double), P(C.c_double), P(clr_info)]
+        L.clr_server_wait.argtypes = [vp, C.c_uint64, C.c_double, P(C.c_double), P(C.c_double), P(C.c_double),
+                                      P(clr_info)]
+        L.clr_server_get_stats.argtypes = [vp, P(clr_server_stats)]
+        L.clr_server_destroy.argtypes = [vp]
         _LIB = L
     return _LIB
 
@@ -247,6 +273,135 @@ class Solver:
         rows = C.c_int32()
         _check(_lib().clr_get_history(self.h, _dptr(out), cap, C.byref(rows)), "clr_get_history")
         return out[: rows.value]
+
+
+def _info_dict(inf):
+    d = {name: getattr(inf, name) for name, _ in clr_info._fields_}
+    d["status_name"] = STATUS.get(d["status"], "UNKNOWN")
+    return d
+
+
+def _settings(settings):
+    return settings if isinstance(settings, clr_settings) else clr_default_settings(**(settings or {}))
+
+
+class Batch(Solver):
+    """A cohort of independent problems solved together (clr_batch_setup).
+
+    problems: sequence of (P_upper, q, A, b, cones)."""
+
+    def __init__(self, problems, settings=None, device=True):
+        keep = []
+        arr = (clr_problem * len(problems))()
+        self.sizes = []
+        for i, (P, q, A, b, cones) in enumerate(problems):
+            Pc = _csc(sp.triu(sp.csc_matrix(P)) if not _is_upper(P) else P, keep)
+            Ac = _csc(A, keep)
+            q = np.ascontiguousarray(q, dtype=np.float64)
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            cz = _cones(cones)
+            keep += [Pc, Ac, q, b, cz]
+            arr[i] = clr_problem(C.pointer(Pc), _dptr(q), C.pointer(Ac), _dptr(b), cz, len(cones))
+            self.sizes.append((len(q), len(b)))
+        self.n, self.m = self.sizes[0]
+        st = _settings(settings)
+        self.settings = st
+        h = C.c_void_p()
+        fn = _lib().clr_batch_setup if device else _lib().clr_batch_analyze
+        _check(fn(C.byref(h), len(problems), arr, C.byref(st)), "clr_batch_setup" if device else "clr_batch_analyze")
+        self.h = h
+
+    def size(self):
+        return _lib().clr_batch_size(self.h)
+
+    def info_of(self, i):
+        inf = clr_info()
+        _check(_lib().clr_batch_get(self.h, i, None, None, None, C.byref(inf)), "clr_batch_get")
+        return _info_dict(inf)
+
+    def solution_of(self, i):
+        n, m = self.sizes[i]
+        x, s, z = np.empty(n), np.empty(m), np.empty(m)
+        inf = clr_info()
+        _check(_lib().clr_batch_get(self.h, i, _dptr(x), _dptr(s), _dptr(z), C.byref(inf)), "clr_batch_get")
+        return x, s, z, _info_dict(inf)
+
+    def update_qb_of(self, i, q, b):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        _check(_lib().clr_batch_update_qb(self.h, i, _dptr(q), _dptr(b)), "clr_batch_update_qb")
+
+
+def clr_batch_setup(problems, settings=None):
+    return Batch(problems, settings)
+
+
+def clr_batch_analyze(problems, settings=None):
+    return Batch(problems, settings, device=False)
+
+
+class Request:
+    """Marshalled arguments of one problem, ready to submit (built ahead of time)."""
+
+    def __init__(self, P_upper, q, A, b, cones):
+        self.keep = []
+        self.Pc = _csc(sp.triu(sp.csc_matrix(P_upper)) if not _is_upper(P_upper) else P_upper, self.keep)
+        self.Ac = _csc(A, self.keep)
+        self.q = np.ascontiguousarray(q, dtype=np.float64)
+        self.b = np.ascontiguousarray(b, dtype=np.float64)
+        self.cz = _cones(cones)
+        self.n, self.m = len(self.q), len(self.b)
+        self.prob = clr_problem(C.pointer(self.Pc), _dptr(self.q), C.pointer(self.Ac), _dptr(self.b), self.cz,
+                                len(cones))
+
+
+class Server:
+    """clr_server_*: continuous-batching request loop on the current device."""
+
+    def __init__(self, device_bytes=8 << 30, max_cohort=256, max_active=4, settings=None):
+        st = _settings(settings)
+        self.settings = st
+        h = C.c_void_p()
+        _check(_lib().clr_server_create(C.byref(h), int(device_bytes), int(max_cohort), int(max_active),
+                                        C.byref(st)), "clr_server_create")
+        self.h = h
+        self.sizes = {}
+
+    def submit(self, req):
+        t = C.c_uint64()
+        _check(_lib().clr_server_submit(self.h, C.byref(req.prob), C.byref(t)), "clr_server_submit")
+        self.sizes[t.value] = (req.n, req.m)
+        return t.value
+
+    def _result(self, fn, ticket, *extra):
+        n, m = self.sizes[ticket]
+        x, s, z = np.empty(n), np.empty(m), np.empty(m)
+        inf = clr_info()
+        rc = fn(self.h, C.c_uint64(ticket), *extra, _dptr(x), _dptr(s), _dptr(z), C.byref(inf))
+        if rc in (-6, -7):  # CLR_E_TIMEOUT, CLR_E_AGAIN
+            return None
+        self.sizes.pop(ticket, None)
+        _check(rc, "clr_server_poll")
+        return x, s, z, _info_dict(inf)
+
+    def poll(self, ticket):
+        return self._result(_lib().clr_server_poll, ticket)
+
+    def wait(self, ticket, timeout_s=60.0):
+        return self._result(_lib().clr_server_wait, ticket, C.c_double(timeout_s))
+
+    def stats(self):
+        s = clr_server_stats()
+        _check(_lib().clr_server_get_stats(self.h, C.byref(s)), "clr_server_get_stats")
+        return {name: getattr(s, name) for name, _ in clr_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _lib().clr_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        self.close()
 
 
 def _is_upper(P):

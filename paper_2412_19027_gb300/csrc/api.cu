@@ -1,8 +1,10 @@
 // extern "C" entry points declared in include/clr.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "ipm.cuh"
 
@@ -103,12 +105,80 @@ int clr_solve(clr_solver* s) {
 
 int clr_get_solution(const clr_solver* s, double* x, double* sl, double* z, clr_info* info) {
   if (!s) return CLR_E_INVALID;
-  return const_cast<clr_solver*>(s)->impl.get_solution(x, sl, z, info);
+  return const_cast<clr_solver*>(s)->impl.get_solution(0, x, sl, z, info);
 }
 
 int clr_update_qb(clr_solver* s, const double* q, const double* b) {
   if (!s) return CLR_E_INVALID;
-  return s->impl.update_qb(q, b);
+  return s->impl.update_qb(0, q, b);
+}
+
+// ---- cohorts ----
+static int make_batch(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st,
+                      bool device) {
+  if (!out || nprob < 1 || !probs) return CLR_E_INVALID;
+  *out = nullptr;
+  clr_settings s;
+  if (st) s = *st;
+  else clr_default_settings(&s, 64);
+  int rc = check_settings(s);
+  if (rc) return rc;
+  clr_solver* h = new (std::nothrow) clr_solver;
+  if (!h) return CLR_E_OOM;
+  try {
+    // host setup of every problem (validation, equilibration, KKT layout, AMD) on worker threads
+    std::vector<clr::HostProblem> hps(nprob);
+    std::vector<std::vector<int64_t>> orders(nprob);
+    std::vector<int> rcs(nprob, CLR_OK);
+    std::vector<std::string> errs(nprob);
+    std::atomic<int32_t> next{0};
+    auto work = [&]() {
+      for (int32_t i = next++; i < nprob; i = next++) {
+        const clr_problem& pr = probs[i];
+        rcs[i] = clr::build_problem(hps[i], pr.P_upper, pr.q, pr.A, pr.b, pr.cones, pr.ncones, s, errs[i]);
+        if (rcs[i] == CLR_OK) {
+          int64_t nd = 0;
+          clr::kkt_amd_order(hps[i].n + hps[i].m, hps[i].kcol_ptr, hps[i].krow, orders[i], nd);
+        }
+      }
+    };
+    const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), 16));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < std::min<int>(nt, nprob); ++t) pool.emplace_back(work);
+    work();
+    for (std::thread& t : pool) t.join();
+    for (int32_t i = 0; i < nprob && rc == CLR_OK; ++i) rc = rcs[i];
+    if (rc == CLR_OK) rc = h->impl.analyze_cohort(std::move(hps), orders, s);
+    if (rc == CLR_OK && device) rc = h->impl.upload();
+  } catch (const std::bad_alloc&) {
+    rc = CLR_E_OOM;
+  }
+  if (rc != CLR_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return CLR_OK;
+}
+
+int clr_batch_setup(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st) {
+  return make_batch(out, nprob, probs, st, true);
+}
+
+int clr_batch_analyze(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st) {
+  return make_batch(out, nprob, probs, st, false);
+}
+
+int32_t clr_batch_size(const clr_solver* s) { return s ? (int32_t)s->impl.nprob() : 0; }
+
+int clr_batch_get(const clr_solver* s, int32_t i, double* x, double* sl, double* z, clr_info* info) {
+  if (!s) return CLR_E_INVALID;
+  return const_cast<clr_solver*>(s)->impl.get_solution(i, x, sl, z, info);
+}
+
+int clr_batch_update_qb(clr_solver* s, int32_t i, const double* q, const double* b) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.update_qb(i, q, b);
 }
 
 int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out) {
@@ -163,9 +233,14 @@ int clr_get_scaling(const clr_solver* s, double* D, double* E, double* c) {
 int clr_get_history(const clr_solver* s, double* out, int32_t cap, int32_t* rows) {
   if (!s) return CLR_E_INVALID;
   const Solver& v = s->impl;
-  const int32_t have = (int32_t)(v.history.size() / 12);
+  if (v.history.empty()) {
+    if (rows) *rows = 0;
+    return CLR_OK;
+  }
+  const std::vector<double>& h = v.history[0];
+  const int32_t have = (int32_t)(h.size() / 12);
   const int32_t k = std::min(have, std::max(cap, 0));
-  if (out) std::copy(v.history.begin(), v.history.begin() + 12 * (size_t)k, out);
+  if (out) std::copy(h.begin(), h.begin() + 12 * (size_t)k, out);
   if (rows) *rows = k;
   return CLR_OK;
 }

@@ -230,6 +230,7 @@ __device__ void bfgs_H(bool is_exp, const double* s, const double* z, double mu,
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 
+
 // ------------------------------------------------------------------ SOC helpers
 // Warp-cooperative: lanes stride over the d entries of one cone.
 struct SocScal {
@@ -239,10 +240,10 @@ struct SocScal {
 }  // namespace
 
 // ====================================================================== scaling
-__global__ void k_scale_nonneg(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z,
-                               unsigned long long* hmax, const int* skip) {
+__global__ void k_scale_nonneg(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
+                               const int* skip) {
   if (skip && *skip) return;
-  double mx = 0.0;
+  RunExt<true> mx;
   const int64_t nz = cd.m_zero, nn = cd.m_nonneg;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nz + nn; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < nz) {
@@ -254,25 +255,24 @@ __global__ void k_scale_nonneg(ConeDev cd, const double* __restrict__ s, const d
     cd.kvz[i] = -h;
     cd.nn_w[i - nz] = sqrt(h);
     cd.nn_lam[i - nz] = sqrt(si * zi);
-    mx = fmax(mx, h);
+    if (h > 0) mx.add(sc, &IterScal::hmax_bits, cd.row_pid[i], dbits(h));
   }
-  mx = warp_max(mx);
-  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(hmax, dbits(mx));
+  mx.flush(sc, &IterScal::hmax_bits);
 }
 
-__global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z,
-                            unsigned long long* hmax, const int* skip) {
+__global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
+                            const int* skip) {
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
   const int64_t cone = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (cone >= cd.n_soc) return;
   const int64_t off = cd.soc_off[cone];
   const int d = cd.soc_dim[cone];
-  const double* sc = s + off;
+  const double* sv = s + off;
   const double* zc = z + off;
   double s1 = 0, z1 = 0, sz = 0;
   for (int j = lane; j < d; j += 32) {
-    const double a = sc[j], b = zc[j];
+    const double a = sv[j], b = zc[j];
     if (j > 0) {
       s1 += a * a;
       z1 += b * b;
@@ -282,7 +282,7 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
   s1 = warp_sum(s1);
   z1 = warp_sum(z1);
   sz = warp_sum(sz);
-  const double s0 = sc[0], z0 = zc[0];
+  const double s0 = sv[0], z0 = zc[0];
   const double ns1 = sqrt(s1), nz1 = sqrt(z1);
   const double ns = sqrt((s0 - ns1) * (s0 + ns1)), nzj = sqrt((z0 - nz1) * (z0 + nz1));
   const double sbzb = sz / (ns * nzj);
@@ -292,7 +292,7 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
   // w-bar and the products needed for lambda = eta W-bar z
   double wz = 0, w1z1 = 0;
   for (int j = lane; j < d; j += 32) {
-    const double wb = (j == 0) ? (s0 / ns + z0 / nzj) * inv2g : (sc[j] / ns - zc[j] / nzj) * inv2g;
+    const double wb = (j == 0) ? (s0 / ns + z0 / nzj) * inv2g : (sv[j] / ns - zc[j] / nzj) * inv2g;
     cd.soc_wb[off + j] = wb;
     wz += wb * zc[j];
     if (j > 0) w1z1 += wb * zc[j];
@@ -325,11 +325,11 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
     base += d - c;
   }
   mx = warp_max(mx);
-  if (lane == 0) atomicMax(hmax, dbits(mx));
+  if (lane == 0) atomicMax(&sc[cd.row_pid[off]].hmax_bits, dbits(mx));
 }
 
-__global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z,
-                               const double* mu_p, unsigned long long* hmax, const int* skip) {
+__global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
+                               const int* skip) {
   if (skip && *skip) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cd.n_exp + cd.n_pow) return;
@@ -342,7 +342,8 @@ __global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const d
   double H[3][3], zt[3];
   double* zs = cd.ep_zt + 3 * t;
   const double start[3] = {zs[0], zs[1], zs[2]};
-  bfgs_H(is_exp, sv, zv, *mu_p, a, start, H, zt);
+  const int pid = cd.row_pid[row];
+  bfgs_H(is_exp, sv, zv, sc[pid].mu, a, start, H, zt);
   if (isfinite(zt[0]) && isfinite(zt[1]) && isfinite(zt[2]) && in_int_dual(is_exp, zt, a)) {
     zs[0] = zt[0];
     zs[1] = zt[1];
@@ -355,7 +356,7 @@ __global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const d
       cd.kvz[kb + q++] = -H[r][c];
       if (r == c) mx = fmax(mx, fabs(H[r][c]));
     }
-  atomicMax(hmax, dbits(mx));
+  atomicMax(&sc[pid].hmax_bits, dbits(mx));
 }
 
 // ---------------------------------------------------------------- PSD helpers
@@ -525,8 +526,8 @@ __device__ double jacobi_eigmin(double* A, int k, double* cs_buf, int* flag) {
 
 // PSD scaling: L_s L_s' = S, L_z L_z' = Z, L_z' L_s = U Lambda V', R = L_s V Lambda^{-1/2},
 // R^{-1} = Lambda^{-1/2} U' L_z', H(X) = (R R') X (R R') written as the svec block.
-__global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z,
-                            unsigned long long* hmax, const int* skip) {
+__global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
+                            const int* skip) {
   if (skip && *skip) return;
   __shared__ double Ls[32 * LDP], Lz[32 * LDP], M[32 * LDP], V[32 * LDP], sig[32];
   __shared__ int bad, flag;
@@ -608,19 +609,19 @@ __global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const doub
     if (ridx == cidx) mx = fmax(mx, fabs(h));
   }
   mx = warp_max(mx);
-  if ((threadIdx.x & 31) == 0) atomicMax(hmax, dbits(mx));
+  if ((threadIdx.x & 31) == 0) atomicMax(&sc[cd.row_pid[row]].hmax_bits, dbits(mx));
 }
 
-int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* mu,
-                  unsigned long long* hmax_bits, const int* skip) {
+int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, IterScal* sc,
+                  const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0)
-    k_scale_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, s, z, hmax_bits, skip);
-  if (cd.n_soc > 0) k_scale_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, s, z, hmax_bits, skip);
+    k_scale_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, s, z, sc, skip);
+  if (cd.n_soc > 0) k_scale_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, s, z, sc, skip);
   if (cd.n_exp + cd.n_pow > 0)
-    k_scale_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, mu, hmax_bits, skip);
+    k_scale_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, sc, skip);
   if (cd.n_psd > 0) {
     const int threads = 32 * ((cd.psd_k + 1) / 2 > 0 ? (cd.psd_k + 1) / 2 : 1);
-    k_scale_psd<<<(unsigned)cd.n_psd, threads < 64 ? 64 : threads, 0, st>>>(cd, s, z, hmax_bits, skip);
+    k_scale_psd<<<(unsigned)cd.n_psd, threads < 64 ? 64 : threads, 0, st>>>(cd, s, z, sc, skip);
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -676,18 +677,19 @@ int cones_identity_H(cudaStream_t st, const ConeDev& cd, const int* skip) {
 
 // ====================================================================== step length
 __global__ void k_step_nonneg(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                              const double* __restrict__ z, const double* __restrict__ dz, unsigned long long* amin,
+                              const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
                               const int* skip) {
   if (skip && *skip) return;
-  double a = INFINITY;
+  RunExt<false> mn;
   const int64_t b0 = cd.m_zero, b1 = cd.m_zero + cd.m_nonneg;
   for (int64_t i = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b1; i += (int64_t)gridDim.x * blockDim.x) {
     const double dsi = ds[i], dzi = dz[i];
+    double a = INFINITY;
     if (dsi < 0) a = fmin(a, -s[i] / dsi);
     if (dzi < 0) a = fmin(a, -z[i] / dzi);
+    if (a < INFINITY) mn.add(sc, &IterScal::amin_bits, cd.row_pid[i], dbits(a));
   }
-  a = warp_min(a);
-  if ((threadIdx.x & 31) == 0 && a < INFINITY) atomicMin(amin, dbits(a));
+  mn.flush(sc, &IterScal::amin_bits);
 }
 
 namespace {
@@ -726,7 +728,7 @@ __device__ double soc_step(const double* x, const double* dx, int d) {
 }  // namespace
 
 __global__ void k_step_soc(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                           const double* __restrict__ z, const double* __restrict__ dz, unsigned long long* amin,
+                           const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
                            const int* skip) {
   if (skip && *skip) return;
   const int64_t cone = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -734,11 +736,11 @@ __global__ void k_step_soc(ConeDev cd, const double* __restrict__ s, const doubl
   const int64_t off = cd.soc_off[cone];
   const int d = cd.soc_dim[cone];
   const double a = fmin(soc_step(s + off, ds + off, d), soc_step(z + off, dz + off, d));
-  if ((threadIdx.x & 31) == 0 && a < INFINITY) atomicMin(amin, dbits(a));
+  if ((threadIdx.x & 31) == 0 && a < INFINITY) atomicMin(&sc[cd.row_pid[off]].amin_bits, dbits(a));
 }
 
 __global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                           const double* __restrict__ z, const double* __restrict__ dz, unsigned long long* amin,
+                           const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
                            const int* skip) {
   if (skip && *skip) return;
   __shared__ double L[32 * LDP], X[32 * LDP], Y[32 * LDP], csb[64];
@@ -782,17 +784,17 @@ __global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const doubl
     if (lmin < 0) amax = fmin(amax, -1.0 / lmin);
     __syncthreads();
   }
-  if (threadIdx.x == 0 && amax < INFINITY) atomicMin(amin, dbits(amax));
+  if (threadIdx.x == 0 && amax < INFINITY) atomicMin(&sc[cd.row_pid[row]].amin_bits, dbits(amax));
 }
 
 int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
-                         const double* dz, unsigned long long* amin_bits, const int* skip) {
-  if (cd.m_nonneg > 0) k_step_nonneg<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, s, ds, z, dz, amin_bits, skip);
+                         const double* dz, IterScal* sc, const int* skip) {
+  if (cd.m_nonneg > 0) k_step_nonneg<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   if (cd.n_soc > 0)
-    k_step_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, s, ds, z, dz, amin_bits, skip);
+    k_step_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   if (cd.n_psd > 0) {
     const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));
-    k_step_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, s, ds, z, dz, amin_bits, skip);
+    k_step_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -801,6 +803,7 @@ int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, co
 namespace {
 struct NsCone {
   bool is_exp;
+  int pid;
   double a, sv[3], zv[3], dsv[3], dzv[3];
   const double* zt0;
 };
@@ -811,6 +814,7 @@ __device__ NsCone load_cone(const ConeDev& cd, int64_t t, const double* s, const
   const int64_t i = c.is_exp ? t : t - cd.n_exp;
   const int64_t row = c.is_exp ? cd.exp_row0 + 3 * i : cd.pow_row0 + 3 * i;
   c.a = c.is_exp ? 0.0 : cd.pow_alpha[i];
+  c.pid = cd.row_pid[row];
   for (int q = 0; q < 3; ++q) {
     c.sv[q] = s[row + q];
     c.zv[q] = z[row + q];
@@ -844,68 +848,71 @@ __device__ bool ns_nbhd(const NsCone& c, double alpha, const double* mu_coef, do
 }
 }  // namespace
 
-__global__ void k_ns_reset(NonsymStep* o, const int* skip) {
+__global__ void k_ns_reset(IterScal* sc, int64_t nprob, const int* skip) {
   if (skip && *skip) return;
-  o->jint = 0;
-  o->fail = 0;
-  o->mask = ~0ull;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nprob; p += (int64_t)gridDim.x * blockDim.x) {
+    sc[p].ns.jint = 0;
+    sc[p].ns.fail = 0;
+    sc[p].ns.mask = ~0ull;
+  }
 }
 
 __global__ void k_ns_interior(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                              const double* __restrict__ z, const double* __restrict__ dz, const double* a0p,
-                              double backtrack, NonsymStep* o, const int* skip) {
+                              const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
+                              double backtrack, const int* skip) {
   if (skip && *skip) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cd.n_exp + cd.n_pow) return;
   const NsCone c = load_cone(cd, t, s, ds, z, dz);
-  double alpha = *a0p;
+  double alpha = sc[c.pid].alpha_sym;
   int j = 0;
   while (j < 120 && !ns_interior(c, alpha)) {
     alpha *= backtrack;
     ++j;
   }
-  atomicMax(&o->jint, j);
+  atomicMax(&sc[c.pid].ns.jint, j);
 }
 
 __global__ void k_ns_first(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                           const double* __restrict__ z, const double* __restrict__ dz, const double* a0p,
-                           double backtrack, double beta, const double* mu_coef, NonsymStep* o, const int* skip) {
+                           const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
+                           double backtrack, double beta, const int* skip) {
   if (skip && *skip) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cd.n_exp + cd.n_pow) return;
   const NsCone c = load_cone(cd, t, s, ds, z, dz);
-  const double alpha = *a0p * pow(backtrack, (double)o->jint);
-  if (!ns_nbhd(c, alpha, mu_coef, beta)) atomicOr(&o->fail, 1);
+  IterScal& q = sc[c.pid];
+  const double alpha = q.alpha_sym * pow(backtrack, (double)q.ns.jint);
+  if (!ns_nbhd(c, alpha, q.mu_coef, beta)) atomicOr(&q.ns.fail, 1);
 }
 
 __global__ void k_ns_window(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                            const double* __restrict__ z, const double* __restrict__ dz, const double* a0p,
-                            double backtrack, double beta, const double* mu_coef, NonsymStep* o, const int* skip) {
+                            const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
+                            double backtrack, double beta, const int* skip) {
   if (skip && *skip) return;
-  if (!o->fail) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cd.n_exp + cd.n_pow) return;
   const NsCone c = load_cone(cd, t, s, ds, z, dz);
-  double alpha = *a0p * pow(backtrack, (double)(o->jint + 1));
+  IterScal& q = sc[c.pid];
+  if (!q.ns.fail) return;
+  double alpha = q.alpha_sym * pow(backtrack, (double)(q.ns.jint + 1));
   unsigned long long bits = 0ull;
   for (int k = 0; k < 64; ++k) {
-    if (ns_nbhd(c, alpha, mu_coef, beta)) bits |= (1ull << k);
+    if (ns_nbhd(c, alpha, q.mu_coef, beta)) bits |= (1ull << k);
     alpha *= backtrack;
   }
-  atomicAnd(&o->mask, bits);
+  atomicAnd(&q.ns.mask, bits);
 }
 
 int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
-                      const double* dz, const double* a0, double backtrack, int nbhd, double beta,
-                      const double* mu_coef, NonsymStep* out, const int* skip) {
-  k_ns_reset<<<1, 1, 0, st>>>(out, skip);
+                      const double* dz, IterScal* sc, double backtrack, int nbhd, double beta, const int* skip) {
+  k_ns_reset<<<grid_for(cd.nprob, 128), 128, 0, st>>>(sc, cd.nprob, skip);
   const int64_t nc = cd.n_exp + cd.n_pow;
   if (nc == 0) return CLR_OK;
   const unsigned g = (unsigned)((nc + 63) / 64);
-  k_ns_interior<<<g, 64, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, out, skip);
+  k_ns_interior<<<g, 64, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, skip);
   if (nbhd) {
-    k_ns_first<<<g, 64, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, beta, mu_coef, out, skip);
-    k_ns_window<<<g, 64, 0, st>>>(cd, s, ds, z, dz, a0, backtrack, beta, mu_coef, out, skip);
+    k_ns_first<<<g, 64, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, beta, skip);
+    k_ns_window<<<g, 64, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, beta, skip);
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -930,9 +937,8 @@ int cones_init_shadow(cudaStream_t st, const ConeDev& cd, const int* skip) {
 
 // ====================================================================== combined d_s
 __global__ void k_ds_nonneg(ConeDev cd, const double* __restrict__ dsa, const double* __restrict__ dza,
-                            const double* sigma_mu, double* __restrict__ out, const int* skip) {
+                            const IterScal* sc, double* __restrict__ out, const int* skip) {
   if (skip && *skip) return;
-  const double smu = *sigma_mu;
   const int64_t nz = cd.m_zero, nn = cd.m_nonneg;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nz + nn; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < nz) {
@@ -941,7 +947,7 @@ __global__ void k_ds_nonneg(ConeDev cd, const double* __restrict__ dsa, const do
     }
     const double w = cd.nn_w[i - nz], lam = cd.nn_lam[i - nz];
     const double eta = (dsa[i] / w) * (w * dza[i]);
-    const double v = lam * lam + eta - smu;
+    const double v = lam * lam + eta - sc[cd.row_pid[i]].sigma_mu;
     out[i] = w * (v / lam);
   }
 }
@@ -971,7 +977,7 @@ __device__ void soc_wbar(const double* wb, const double* x, double* y, int d, bo
 // SOC: d_s = W (lambda \ (lambda o lambda + (W^{-1} ds_a) o (W dz_a) - sigma mu e)); W symmetric.
 // Uses `out` on the cone's rows as scratch.
 __global__ void k_ds_soc(ConeDev cd, const double* __restrict__ dsa, const double* __restrict__ dza,
-                         const double* sigma_mu, double* __restrict__ out, double* __restrict__ scratch,
+                         const IterScal* sc, double* __restrict__ out, double* __restrict__ scratch,
                          const int* skip) {
   if (skip && *skip) return;
   const int lane = threadIdx.x & 31;
@@ -1000,7 +1006,7 @@ __global__ void k_ds_soc(ConeDev cd, const double* __restrict__ dsa, const doubl
   uv = warp_sum(uv);
   ll = warp_sum(ll);
   const double u0 = u[0], v0 = v[0], l0 = lam[0];
-  const double smu = *sigma_mu;
+  const double smu = sc[cd.row_pid[off]].sigma_mu;
   __syncwarp();
   // w = lam o lam + eta_c - sigma mu e
   for (int j = lane; j < d; j += 32) {
@@ -1026,7 +1032,7 @@ __global__ void k_ds_soc(ConeDev cd, const double* __restrict__ dsa, const doubl
 }
 
 __global__ void k_ds_exppow(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z,
-                            const double* __restrict__ dsa, const double* __restrict__ dza, const double* sigma_mu,
+                            const double* __restrict__ dsa, const double* __restrict__ dza, const IterScal* sc,
                             double* __restrict__ out, const int* skip) {
   if (skip && *skip) return;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1046,7 +1052,7 @@ __global__ void k_ds_exppow(ConeDev cd, const double* __restrict__ s, const doub
   psi_parts(is_exp, zv, a, P);
   const double phi = is_exp ? 0.0 : P.psi + zv[2] * zv[2];
   const double ip = 1.0 / P.psi, ip2 = ip * ip, ip3 = ip2 * ip;
-  const double smu = *sigma_mu;
+  const double smu = sc[cd.row_pid[row]].sigma_mu;
   for (int r = 0; r < 3; ++r) {
     double acc = 0.0;
     for (int j = 0; j < 3; ++j)
@@ -1063,7 +1069,7 @@ __global__ void k_ds_exppow(ConeDev cd, const double* __restrict__ s, const doub
 
 // PSD: d_s = R (Lambda \ (Lambda^2 + eta - sigma mu I)) R', eta = (R^{-1} dS R^{-T}) o (R' dZ R).
 __global__ void k_ds_psd(ConeDev cd, const double* __restrict__ dsa, const double* __restrict__ dza,
-                         const double* sigma_mu, double* __restrict__ out, const int* skip) {
+                         const IterScal* sc, double* __restrict__ out, const int* skip) {
   if (skip && *skip) return;
   __shared__ double A[32 * LDP], B[32 * LDP], T[32 * LDP];
   const int k = cd.psd_k, d = cd.psd_d;
@@ -1072,7 +1078,7 @@ __global__ void k_ds_psd(ConeDev cd, const double* __restrict__ dsa, const doubl
   const double* R = cd.psd_R + (int64_t)k * k * cone;
   const double* Ri = cd.psd_Ri + (int64_t)k * k * cone;
   const double* lam = cd.psd_lam + (int64_t)k * cone;
-  const double smu = *sigma_mu;
+  const double smu = sc[cd.row_pid[row]].sigma_mu;
   // A = Ri dS Ri'
   load_smat(dsa + row, k, A);
   for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
@@ -1140,51 +1146,54 @@ __global__ void k_ds_psd(ConeDev cd, const double* __restrict__ dsa, const doubl
 }
 
 int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* dsa,
-                      const double* dza, const double* sigma_mu, double* ds_out, const int* skip) {
+                      const double* dza, IterScal* sc, double* ds_out, const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0)
-    k_ds_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, dsa, dza, sigma_mu, ds_out, skip);
+    k_ds_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
   if (cd.n_soc > 0)
-    k_ds_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, dsa, dza, sigma_mu, ds_out, cd.scratch,
-                                                                      skip);
+    k_ds_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
   if (cd.n_exp + cd.n_pow > 0)
-    k_ds_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, dsa, dza, sigma_mu, ds_out,
+    k_ds_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, dsa, dza, sc, ds_out,
                                                                                skip);
   if (cd.n_psd > 0) {
     const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));
-    k_ds_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, dsa, dza, sigma_mu, ds_out, skip);
+    k_ds_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
 
 // ====================================================================== initial point
-__global__ void k_nn_min(ConeDev cd, const double* __restrict__ v, unsigned long long* minbits, const int* skip) {
+__global__ void k_nn_min_reset(IterScal* sc, int64_t nprob, const int* skip) {
   if (skip && *skip) return;
-  // min over nonneg entries, shifted by +inf-safe mapping: store as ordered bits of (v + 0) using
-  // the monotone map for doubles of any sign
-  double mn = INFINITY;
-  for (int64_t i = cd.m_zero + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cd.m_zero + cd.m_nonneg;
-       i += (int64_t)gridDim.x * blockDim.x)
-    mn = fmin(mn, v[i]);
-  mn = warp_min(mn);
-  if ((threadIdx.x & 31) == 0) {
-    unsigned long long b = dbits(mn);
-    b = (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);  // order-preserving
-    atomicMin(minbits, b);
-  }
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nprob; p += (int64_t)gridDim.x * blockDim.x)
+    sc[p].nn_min_bits = ~0ull;
 }
 
-__global__ void k_shift_nonneg(ConeDev cd, double* __restrict__ v, const unsigned long long* minbits,
-                               const int* skip) {
+// least nonneg entry of each problem, as order-preserving bits of a double of any sign
+__global__ void k_nn_min(ConeDev cd, const double* __restrict__ v, IterScal* sc, const int* skip) {
   if (skip && *skip) return;
-  unsigned long long b = *minbits;
-  b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
-  const double a = __longlong_as_double((long long)b);
-  const bool shift = a < 1.4901161193847656e-08;  // sqrt(eps_64)
+  RunExt<false> mn;
+  for (int64_t i = cd.m_zero + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cd.m_zero + cd.m_nonneg;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long b = dbits(v[i]);
+    b = (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+    mn.add(sc, &IterScal::nn_min_bits, cd.row_pid[i], b);
+  }
+  mn.flush(sc, &IterScal::nn_min_bits);
+}
+
+__global__ void k_shift_nonneg(ConeDev cd, double* __restrict__ v, const IterScal* sc, const int* skip) {
+  if (skip && *skip) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cd.m_zero + cd.m_nonneg;
        i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < cd.m_zero) v[i] = 0.0;
-    else if (shift) v[i] += 1.0 - a;
+    if (i < cd.m_zero) {
+      v[i] = 0.0;
+      continue;
+    }
+    unsigned long long b = sc[cd.row_pid[i]].nn_min_bits;
+    b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
+    const double a = __longlong_as_double((long long)b);
+    if (a < 1.4901161193847656e-08) v[i] += 1.0 - a;  // sqrt(eps_64)
   }
 }
 
@@ -1216,12 +1225,11 @@ __global__ void k_shift_psd(ConeDev cd, double* __restrict__ v, const int* skip)
     for (int j = threadIdx.x; j < k; j += blockDim.x) v[row + smat_index(j, j)] += 1.0 - a;
 }
 
-int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, double* nn_min, const int* skip) {
-  unsigned long long* mb = reinterpret_cast<unsigned long long*>(nn_min);
+int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, IterScal* sc, const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0) {
-    CLR_CUDA(cudaMemsetAsync(mb, 0xff, sizeof(unsigned long long), st));
-    k_nn_min<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, v, mb, skip);
-    k_shift_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, v, mb, skip);
+    k_nn_min_reset<<<grid_for(cd.nprob, 128), 128, 0, st>>>(sc, cd.nprob, skip);
+    if (cd.m_nonneg > 0) k_nn_min<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, v, sc, skip);
+    k_shift_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, v, sc, skip);
   }
   if (cd.n_soc > 0) k_shift_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, v, skip);
   if (cd.n_psd > 0) {
@@ -1235,6 +1243,7 @@ int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, double* nn_m
 __global__ void k_unit_init(ConeDev cd, double* __restrict__ v, const int* skip) {
   if (skip && *skip) return;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < cd.m; r += (int64_t)gridDim.x * blockDim.x) {
+    if (cd.pc[cd.row_pid[r]].sym) continue;  // symmetric problems keep their symmetric initial point
     double val = 0.0;
     if (r < cd.m_zero) val = 0.0;
     else if (r < cd.m_zero + cd.m_nonneg) val = 1.0;

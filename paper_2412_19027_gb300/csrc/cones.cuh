@@ -6,6 +6,7 @@
 #pragma once
 
 #include "device.cuh"
+#include "scal.cuh"
 
 namespace clr {
 
@@ -39,44 +40,44 @@ struct ConeDev {
   double* psd_lam = nullptr;  // k per cone
   double* ep_zt = nullptr;   // 3 per exp/pow cone: z~ = -grad f*(s) at the current s (Newton warm start)
   double exp_center[3] = {0, 0, 0};  // central point of the exp cone (u = -grad f(u))
+  // cohort: problem of every (reordered, family-major) row and per-problem constants
+  int64_t nprob = 1;
+  const int32_t* row_pid = nullptr;
+  const ProbConst* pc = nullptr;
 };
 
-// Result of the exp/pow backtracking (see cones_step_nonsym).
-struct NonsymStep {
-  int jint;                 // smallest j with every cone interior at a0 * backtrack^j
-  int fail;                 // some cone fails N(beta) at jint
-  unsigned long long mask;  // bit k: every cone passes N(beta) at jint + 1 + k
-};
+// Per-problem scalars are read from and written to sc[row_pid[row]]; `skip`
+// (when non-null and set) makes every kernel return at once.
 
-// All scalars of one iteration that several kernels share live in device memory.
-struct IterScalars;
-
-// Scaling H (-H into kvz) for every cone; max |H_ii| into *hmax_bits (atomicMax on the bit pattern).
-int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* mu,
-                  unsigned long long* hmax_bits, const int* skip);
+// Scaling H (-H into kvz) for every cone (exp/pow use the problem's mu); max |H_ii| of
+// each problem into sc[p].hmax_bits (atomicMax on the bit pattern; caller zeroes it).
+int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, IterScal* sc,
+                  const int* skip);
 // H = I on every cone block (initialisation solves), zero cone included.
 int cones_identity_H(cudaStream_t st, const ConeDev& cd, const int* skip);
-// Symmetric-cone step length over s/ds and z/dz -> atomicMin into *amin_bits.
+// Symmetric-cone step length over s/ds and z/dz -> atomicMin into sc[p].amin_bits.
 int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
-                         const double* dz, unsigned long long* amin_bits, const int* skip);
-// exp/pow backtracking from a0 (Sec. 2.2: ratio 0.8): the candidates are
-// a_j = a0 backtrack^j.  Interior-ness is monotone along the ray, so the joint
-// first interior candidate is the largest per-cone one (jint).  With nbhd != 0
-// the N(beta) test (trial mu from mu_coef = {c0, c1, c2}: mu(a) = c0 + a c1 +
-// a^2 c2) is evaluated at jint and, only if some cone fails there, on the 64
-// candidates after it; the step is the first candidate every cone passes.
+                         const double* dz, IterScal* sc, const int* skip);
+// exp/pow backtracking from a0 = sc[p].alpha_sym (Sec. 2.2: ratio 0.8): the
+// candidates are a_j = a0 backtrack^j.  Interior-ness is monotone along the
+// ray, so the joint first interior candidate is the largest per-cone one
+// (jint).  With nbhd != 0 the N(beta) test (trial mu from sc[p].mu_coef =
+// {c0, c1, c2}: mu(a) = c0 + a c1 + a^2 c2) is evaluated at jint and, only if
+// some cone of the problem fails there, on the 64 candidates after it; the
+// step is the first candidate every cone of the problem passes.  Result in sc[p].ns.
 int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
-                      const double* dz, const double* a0, double backtrack, int nbhd, double beta,
-                      const double* mu_coef, NonsymStep* out, const int* skip);
+                      const double* dz, IterScal* sc, double backtrack, int nbhd, double beta, const int* skip);
 // z~ of every exp/pow cone set to its central point (start of a solve).
 int cones_init_shadow(cudaStream_t st, const ConeDev& cd, const int* skip);
-// Combined-step d_s (Eq. ds-correction-step) for every cone.
+// Combined-step d_s (Eq. ds-correction-step) for every cone, with the problem's sigma mu.
 int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* dsa,
-                      const double* dza, const double* sigma_mu, double* ds_out, const int* skip);
+                      const double* dza, IterScal* sc, double* ds_out, const int* skip);
 // Initial point shift (symmetric init): v += (1 - a) e where a = least Jordan eigenvalue < sqrt(eps).
-// Zero-cone entries are set to 0.  nn_min_bits: scratch for the nonneg minimum (one per vector).
-int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, double* nn_min, const int* skip);
-// Unit initialisation: v = central point of each cone (0 on the zero cone).
+// Zero-cone entries are set to 0; the merged nonneg cone of each problem shifts by its own
+// minimum (sc[p].nn_min_bits is scratch).
+int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, IterScal* sc, const int* skip);
+// Unit initialisation: v = central point of each cone (0 on the zero cone), on the rows of
+// problems whose ProbConst::sym is 0 (problems with exp/pow cones); other rows untouched.
 int cones_unit_init(cudaStream_t st, const ConeDev& cd, double* v, const int* skip);
 
 __host__ double exp_central_point_host(double out[3]);

@@ -110,11 +110,18 @@ class DeviceArena {
   template <typename T>
   T* upload(const T* h, int64_t n) {
     T* d = alloc_n<T>(n);
-    if (d && n > 0 && cudaMemcpy(d, h, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
-    return d;
+    if (!d || n <= 0) return d;
+    const cudaError_t e = async_ ? cudaMemcpyAsync(d, h, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice, async_)
+                                 : cudaMemcpy(d, h, sizeof(T) * (size_t)n, cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? d : nullptr;
   }
   void release();
   size_t bytes() const { return total_; }
+  // Stream-ordered mode: allocations and frees go through cudaMallocAsync /
+  // cudaFreeAsync on `s` and uploads are ordered on it, so that a solver built
+  // and torn down while other solvers run does not synchronise the device.
+  // Only without a user allocator hook; set before the first allocation.
+  void set_stream_ordered(cudaStream_t s) { async_ = s; }
 
  private:
   struct Block {
@@ -123,6 +130,13 @@ class DeviceArena {
   };
   Block* blocks_ = nullptr;
   size_t nblocks_ = 0, cap_ = 0, total_ = 0;
+  cudaStream_t async_ = nullptr;
 };
+
+// Pinned host buffers reused across solvers (cudaMallocHost / cudaFreeHost
+// synchronise the device; a serving loop creates and drops solvers while
+// others run).  Blocks are kept for the life of the process.
+void* pinned_get(size_t bytes);
+void pinned_put(void* p, size_t bytes);
 
 }  // namespace clr

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/clr.h"
+#include "scal.cuh"
 
 namespace clr {
 
@@ -97,6 +98,23 @@ struct HostProblem {
   int64_t kval_x = 0;              // entries of the x part of kval
 };
 
+// Where the problems of a cohort live in the merged vectors (host side).
+struct CohortLayout {
+  int64_t B = 1;
+  std::vector<int64_t> xo;                 // B + 1: x_p = x[xo[p] .. xo[p+1])
+  std::vector<std::vector<int64_t>> zrow;  // per problem: its reordered row r -> cohort row
+  std::vector<Chunk> ckx, ckz;             // chunk lists; a problem's chunks are contiguous
+  std::vector<int64_t> ckx_ptr, ckz_ptr;   // B + 1
+  std::vector<int32_t> pid;                // KKT index -> problem (N)
+  std::vector<ProbConst> pc;
+};
+
+// Merge the problems (each already through build_problem and with its own
+// fill-reducing order `orders[p]`, or none) into one cohort problem `hp` and
+// its symbolic factorization.  The big per-problem arrays are released.
+int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<int64_t>>& orders, HostProblem& hp,
+                 CohortLayout& lay, Symbolic& sy, std::string& err);
+
 // ---- host routines (setup.cpp / amd.cpp / symbolic.cpp) ----
 int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_csc* A, const double* b,
                   const clr_cone* cones, int32_t ncones, const clr_settings& st, std::string& err);
@@ -105,5 +123,8 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
                std::vector<int64_t>& perm, int64_t& n_dense);
 int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
                      const std::vector<int64_t>* user_order, Symbolic& sy);
+// The fill-reducing order symbolic_analyze uses when given none (AMD on the KKT pattern).
+void kkt_amd_order(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                   std::vector<int64_t>& order, int64_t& n_dense);
 
 }  // namespace clr

@@ -1,7 +1,15 @@
 // Per-iteration device step of Algorithm 1 (arXiv:2412.19027) and the solver
 // object.  Every step of an iteration runs in the kernels below or in
 // cones.cu / ldl.cu; the host only launches them (replaying one captured CUDA
-// graph per iteration) and reads back the status word.
+// graph per iteration) and reads back the status words.
+//
+// A solver holds a cohort of B >= 1 problems merged block-diagonally
+// (cohort.cpp): x = [x_1; ...; x_B], the constraint rows family-major (all
+// zero rows, all nonneg rows, SOCs, exp, pow, PSD cones; each problem's rows in
+// problem order inside a family).  Every scalar of the method is per problem
+// (IterScal[B]); vector reductions run over chunks that never straddle two
+// problems and are summed per problem in a fixed order, so a problem's
+// iterates do not depend on the rest of its cohort.
 //
 // Scaled space: the device holds P^ = c D P D, q^ = c D q, A^ = E A D,
 // b^ = E b (setup.cpp) and iterates x^, s^, z^, tau, kappa; residuals and the
@@ -12,34 +20,55 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "ipm.cuh"
 
 namespace clr {
 
 // ------------------------------------------------------------------ slots
-enum SumSlot { S_XPX = 0, S_QX, S_BZ, S_SZ, S_D0, S_D1, S_D2, S_D3, S_NSLOT };
+enum SumSlot { S_XPX = 0, S_QX, S_BZ, S_SZ, S_D0, S_D1, S_D2, S_NSLOT };
 enum MaxSlot { M_RD = 0, M_X, M_RP, M_S, M_Z, M_ATZ, M_PX, M_AXS, M_NMAX };
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
 
+// Launch geometry of the chunked kernels: one block per chunk, x chunks first.
+struct ChunkGrid {
+  const Chunk* ck;
+  int64_t nckx, pst, n;  // pst: stride of a partial-sum slot
+};
+// KKT index range of block b's chunk: [i0, i0 + len); z chunks start at n.
+__device__ __forceinline__ void chunk_range(const ChunkGrid& g, int64_t* i0, int64_t* len, int* pid, bool* zpart) {
+  const Chunk c = g.ck[blockIdx.x];
+  *zpart = blockIdx.x >= g.nckx;
+  *i0 = *zpart ? g.n + c.begin : c.begin;
+  *len = c.len;
+  *pid = c.pid;
+}
+// index of block b's chunk inside its own (x or z) list
+__device__ __forceinline__ int64_t chunk_slot(const ChunkGrid& g) {
+  return blockIdx.x >= g.nckx ? blockIdx.x - g.nckx : blockIdx.x;
+}
+
 // ------------------------------------------------------------------ K products
 // G lanes per row of the full (both triangles) KKT CSR; values through kvi into kval.
 // mode 0: lo[i] = sum_{col < n} K_ij v_j, hi[i] = sum_{col >= n} K_ij v_j
-// mode 1: out[i] = rhs[i] - (K v)_i and max |out| -> *maxb
+// mode 1: out[i] = rhs[i] - (K v)_i and max |out| of each problem -> sc[p].rnorm_bits
 // mode 2 (rows n..N-1): out[i-n] = -rhs[i-n] + hi   (Delta s = -d_s - H Delta z; K_zz = -H)
 template <int G>
 __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t* __restrict__ kptr,
                       const int32_t* __restrict__ kcol, const int32_t* __restrict__ kvi, const double* __restrict__ kval,
                       const double* __restrict__ v, double* __restrict__ lo, double* __restrict__ hi,
-                      const double* __restrict__ rhs, double* __restrict__ out, unsigned long long* maxb,
-                      const int* skip) {
+                      const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ pid,
+                      IterScal* sc, const int* skip) {
   if (skip && *skip) return;
   const int lane = threadIdx.x % G;
+  // the G lanes of a row group share its trip count: shuffles name only their own group
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
   const int64_t gid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
   const int64_t gstride = ((int64_t)gridDim.x * blockDim.x) / G;
-  double mx = 0.0;
+  RunExt<true> mx;
   for (int64_t i = r0 + gid; i < r1; i += gstride) {
     double a = 0.0, b = 0.0;
     for (int64_t p = kptr[i] + lane; p < kptr[i + 1]; p += G) {
@@ -50,8 +79,8 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o, G);
-      b += __shfl_xor_sync(0xffffffffu, b, o, G);
+      a += __shfl_xor_sync(gmask, a, o, G);
+      b += __shfl_xor_sync(gmask, b, o, G);
     }
     if (lane == 0) {
       if (mode == 0) {
@@ -60,157 +89,165 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
       } else if (mode == 1) {
         const double r = rhs[i] - (a + b);
         out[i] = r;
-        mx = fmax(mx, fabs(r));
+        mx.add(sc, &IterScal::rnorm_bits, pid[i], dbits(fabs(r)));
       } else {
         out[i - n] = -rhs[i - n] + b;
       }
     }
   }
-  if (mode == 1) {
-    mx = warp_max(mx);
-    if ((threadIdx.x & 31) == 0) atomicMax(maxb, dbits(mx));
-  }
+  if (mode == 1) mx.flush(sc, &IterScal::rnorm_bits);
 }
 
 // ------------------------------------------------------------------ residuals
-__device__ void block_write_sum(double v, double* part, int slot) {
+// x chunks: G1 = -(P x + A' z + q tau), qp = q + 2 P x / tau, sums x'Px, q'x and maxima;
+// z chunks: G2 = s + A x - b tau, sums b'z, s'z and maxima.
+__global__ void k_resid(ChunkGrid g, const double* __restrict__ xz, const double* __restrict__ s,
+                        const double* __restrict__ lo, const double* __restrict__ hi, const double* __restrict__ q,
+                        const double* __restrict__ b, const double* __restrict__ D, const double* __restrict__ E,
+                        const IterScal* sc, double* __restrict__ G, double* __restrict__ qp, double* part,
+                        unsigned long long* maxb, const int* skip) {
+  if (skip && *skip) return;
   __shared__ double sh[32];
-  v = block_sum(v, sh);
-  if (threadIdx.x == 0) part[slot * kRedBlocks + blockIdx.x] = v;
-}
-
-__global__ void k_resid_x(int64_t n, const double* __restrict__ xz, const double* __restrict__ lo,
-                          const double* __restrict__ hi, const double* __restrict__ q, const double* __restrict__ D,
-                          IterScal* sc, double* __restrict__ G, double* __restrict__ qp, double* part,
-                          unsigned long long* maxb, const int* skip) {
-  if (skip && *skip) return;
-  const double tau = sc->tau;
-  double xpx = 0, qx = 0, mrd = 0, mx = 0, matz = 0, mpx = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = xz[i], px = lo[i], atz = hi[i], qi = q[i], di = D[i];
-    const double g1 = -(px + atz + qi * tau);
-    G[i] = g1;
-    qp[i] = qi + 2.0 * px / tau;
-    xpx += x * px;
-    qx += qi * x;
-    mrd = fmax(mrd, fabs(g1) / di);
-    mx = fmax(mx, fabs(di * x));
-    matz = fmax(matz, fabs(atz) / di);
-    mpx = fmax(mpx, fabs(px) / di);
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  const int64_t slot = chunk_slot(g);
+  const double tau = sc[pid].tau;
+  unsigned long long* mb = maxb + (int64_t)M_NMAX * pid;
+  double s0 = 0, s1 = 0, m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  if (!zp) {
+    for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
+      const double x = xz[i], px = lo[i], atz = hi[i], qi = q[i], di = D[i];
+      const double g1 = -(px + atz + qi * tau);
+      G[i] = g1;
+      qp[i] = qi + 2.0 * px / tau;
+      s0 += x * px;
+      s1 += qi * x;
+      m0 = fmax(m0, fabs(g1) / di);
+      m1 = fmax(m1, fabs(di * x));
+      m2 = fmax(m2, fabs(atz) / di);
+      m3 = fmax(m3, fabs(px) / di);
+    }
+  } else {
+    const int64_t n = g.n;
+    for (int64_t k = i0 + threadIdx.x; k < i0 + len; k += blockDim.x) {
+      const int64_t i = k - n;
+      const double zi = xz[k], si = s[i], ax = lo[k], bi = b[i], ei = E[i];
+      const double g2 = si + ax - bi * tau;
+      G[k] = g2;
+      s0 += bi * zi;
+      s1 += si * zi;
+      m0 = fmax(m0, fabs(g2) / ei);
+      m1 = fmax(m1, fabs(si) / ei);
+      m2 = fmax(m2, fabs(ei * zi));
+      m3 = fmax(m3, fabs(ax + si) / ei);
+    }
   }
-  block_write_sum(xpx, part, S_XPX);
-  block_write_sum(qx, part, S_QX);
-  mrd = warp_max(mrd);
-  mx = warp_max(mx);
-  matz = warp_max(matz);
-  mpx = warp_max(mpx);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(maxb + M_RD, dbits(mrd));
-    atomicMax(maxb + M_X, dbits(mx));
-    atomicMax(maxb + M_ATZ, dbits(matz));
-    atomicMax(maxb + M_PX, dbits(mpx));
-  }
-}
-
-__global__ void k_resid_z(int64_t n, int64_t m, const double* __restrict__ xz, const double* __restrict__ s,
-                          const double* __restrict__ lo, const double* __restrict__ b, const double* __restrict__ E,
-                          IterScal* sc, double* __restrict__ G, double* part, unsigned long long* maxb,
-                          const int* skip) {
-  if (skip && *skip) return;
-  const double tau = sc->tau;
-  double bz = 0, sz = 0, mrp = 0, ms = 0, mz = 0, maxs = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = xz[n + i], si = s[i], ax = lo[n + i], bi = b[i], ei = E[i];
-    const double g2 = si + ax - bi * tau;
-    G[n + i] = g2;
-    bz += bi * zi;
-    sz += si * zi;
-    mrp = fmax(mrp, fabs(g2) / ei);
-    ms = fmax(ms, fabs(si) / ei);
-    mz = fmax(mz, fabs(ei * zi));
-    maxs = fmax(maxs, fabs(ax + si) / ei);
-  }
-  block_write_sum(bz, part, S_BZ);
-  block_write_sum(sz, part, S_SZ);
-  mrp = warp_max(mrp);
-  ms = warp_max(ms);
-  mz = warp_max(mz);
-  maxs = warp_max(maxs);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(maxb + M_RP, dbits(mrp));
-    atomicMax(maxb + M_S, dbits(ms));
-    atomicMax(maxb + M_Z, dbits(mz));
-    atomicMax(maxb + M_AXS, dbits(maxs));
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  m0 = block_max(m0, sh);
+  m1 = block_max(m1, sh);
+  m2 = block_max(m2, sh);
+  m3 = block_max(m3, sh);
+  if (threadIdx.x == 0) {
+    part[(zp ? S_BZ : S_XPX) * g.pst + slot] = s0;
+    part[(zp ? S_SZ : S_QX) * g.pst + slot] = s1;
+    if (!zp) {
+      atomicMax(mb + M_RD, dbits(m0));
+      atomicMax(mb + M_X, dbits(m1));
+      atomicMax(mb + M_ATZ, dbits(m2));
+      atomicMax(mb + M_PX, dbits(m3));
+    } else {
+      atomicMax(mb + M_RP, dbits(m0));
+      atomicMax(mb + M_S, dbits(m1));
+      atomicMax(mb + M_Z, dbits(m2));
+      atomicMax(mb + M_AXS, dbits(m3));
+    }
   }
 }
 
-__device__ double fin_sum(const double* part, int slot) {
+// Sum of slot `slot` over chunks [c0, c1) of one problem, in a fixed order; valid in thread 0.
+__device__ double fin_sum(const double* part, int slot, int64_t pst, int64_t c0, int64_t c1) {
   __shared__ double sh[32];
   double v = 0.0;
-  for (int b = threadIdx.x; b < kRedBlocks; b += blockDim.x) v += part[slot * kRedBlocks + b];
+  for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) v += part[slot * pst + c];
   v = block_sum(v, sh);
   __syncthreads();
-  return v;  // valid in thread 0
+  return v;
+}
+
+// Transition of problem p to "stopped": the last one to stop raises all_halt.
+__device__ void halt_problem(IterScal& q, BatchFlags* bf) {
+  if (q.halt) return;
+  q.halt = 1;
+  if (atomicSub(&bf->n_running, 1) == 1) bf->all_halt = 1;
 }
 
 struct TermParams {
-  double c, bnorm, qnorm, eps_feas, eps_inf;
-  int64_t nu;
+  double eps_feas, eps_inf;
   int max_iter;
   int hist_cap;
 };
 
-// Residuals, objectives, mu and the termination / infeasibility tests.
-__global__ void k_fin_resid(IterScal* sc, const double* part, const unsigned long long* maxb, TermParams tp,
-                            double* hist, const int* skip) {
+// Residuals, objectives, mu and the termination / infeasibility tests; one block per problem.
+__global__ void k_fin_resid(IterScal* scs, const ProbConst* pcs, const double* part, int64_t pst,
+                            const int64_t* ckx_ptr, const int64_t* ckz_ptr, const unsigned long long* maxb,
+                            TermParams tp, double* hist, BatchFlags* bf, const int* skip) {
   if (skip && *skip) return;
-  const double xpx = fin_sum(part, S_XPX), qx = fin_sum(part, S_QX), bz = fin_sum(part, S_BZ),
-               sz = fin_sum(part, S_SZ);
+  const int64_t p = blockIdx.x;
+  IterScal& sc = scs[p];
+  if (sc.halt) return;
+  const double xpx = fin_sum(part, S_XPX, pst, ckx_ptr[p], ckx_ptr[p + 1]);
+  const double qx = fin_sum(part, S_QX, pst, ckx_ptr[p], ckx_ptr[p + 1]);
+  const double bz = fin_sum(part, S_BZ, pst, ckz_ptr[p], ckz_ptr[p + 1]);
+  const double sz = fin_sum(part, S_SZ, pst, ckz_ptr[p], ckz_ptr[p + 1]);
   if (threadIdx.x != 0) return;
-  const double tau = sc->tau, kappa = sc->kappa, c = tp.c;
-  const double mu = (sz + kappa * tau) / (double)(tp.nu + 1);
-  const double nrp = bitsd(maxb[M_RP]) / tau;
-  const double nrd = bitsd(maxb[M_RD]) / (c * tau);
-  const double nx = bitsd(maxb[M_X]) / tau, ns = bitsd(maxb[M_S]) / tau, nz = bitsd(maxb[M_Z]) / (c * tau);
+  const ProbConst pc = pcs[p];
+  const unsigned long long* mb = maxb + (int64_t)M_NMAX * p;
+  const double tau = sc.tau, kappa = sc.kappa, c = pc.c;
+  const double mu = (sz + kappa * tau) / (double)(pc.nu + 1);
+  const double nrp = bitsd(mb[M_RP]) / tau;
+  const double nrd = bitsd(mb[M_RD]) / (c * tau);
+  const double nx = bitsd(mb[M_X]) / tau, ns = bitsd(mb[M_S]) / tau, nz = bitsd(mb[M_Z]) / (c * tau);
   const double gp = (0.5 * xpx / (tau * tau) + qx / tau) / c;
   const double gd = (-0.5 * xpx / (tau * tau) - bz / tau) / c;
   const double gap = fabs(gp - gd);
-  sc->mu = mu;
-  sc->xPx = xpx;
-  sc->qx = qx;
-  sc->bz = bz;
-  sc->sz = sz;
-  sc->G3 = kappa + qx + bz + xpx / tau;
-  sc->pcost = gp;
-  sc->dcost = gd;
-  sc->res_p = nrp;
-  sc->res_d = nrd;
-  sc->gap_abs = gap;
-  sc->gap_rel = gap / fmax(1.0, fmin(fabs(gp), fabs(gd)));
+  sc.mu = mu;
+  sc.xPx = xpx;
+  sc.qx = qx;
+  sc.bz = bz;
+  sc.sz = sz;
+  sc.G3 = kappa + qx + bz + xpx / tau;
+  sc.pcost = gp;
+  sc.dcost = gd;
+  sc.res_p = nrp;
+  sc.res_d = nrd;
+  sc.gap_abs = gap;
+  sc.gap_rel = gap / fmax(1.0, fmin(fabs(gp), fabs(gd)));
   int status = 0;
   if (!isfinite(mu) || !isfinite(nrp) || !isfinite(nrd) || !isfinite(gp) || !isfinite(gd) || !isfinite(tau) ||
       !isfinite(kappa)) {
     status = CLR_NUMERICAL_ERROR;
-  } else if (nrp < tp.eps_feas * fmax(1.0, tp.bnorm + nx + ns) && nrd < tp.eps_feas * fmax(1.0, tp.qnorm + nx + nz) &&
+  } else if (nrp < tp.eps_feas * fmax(1.0, pc.bnorm + nx + ns) && nrd < tp.eps_feas * fmax(1.0, pc.qnorm + nx + nz) &&
              gap < tp.eps_feas * fmax(1.0, fmin(fabs(gp), fabs(gd)))) {
     status = CLR_SOLVED;
   } else {
     // infeasibility on the unnormalised unscaled iterates
     const double btz = bz / c, qtx = qx / c;
-    const double nxu = bitsd(maxb[M_X]), nzu = bitsd(maxb[M_Z]) / c, nsu = bitsd(maxb[M_S]);
-    const double natz = bitsd(maxb[M_ATZ]) / c, npx = bitsd(maxb[M_PX]) / c, naxs = bitsd(maxb[M_AXS]);
+    const double nxu = bitsd(mb[M_X]), nzu = bitsd(mb[M_Z]) / c, nsu = bitsd(mb[M_S]);
+    const double natz = bitsd(mb[M_ATZ]) / c, npx = bitsd(mb[M_PX]) / c, naxs = bitsd(mb[M_AXS]);
     if (btz < -tp.eps_inf && natz < -tp.eps_inf * fmax(1.0, nxu + nzu) * btz) status = CLR_PRIMAL_INFEASIBLE;
     else if (qtx < -tp.eps_inf && npx < -tp.eps_inf * fmax(1.0, nxu) * qtx &&
              naxs < -tp.eps_inf * fmax(1.0, nxu + nsu) * qtx)
       status = CLR_DUAL_INFEASIBLE;
-    else if (sc->iter >= tp.max_iter)
+    else if (sc.iter >= tp.max_iter)
       status = CLR_MAX_ITER;
   }
-  sc->status = status;
-  if (status != 0) sc->halt = 1;
-  if (sc->iter < tp.hist_cap) {
-    double* h = hist + 12 * sc->iter;
-    h[0] = sc->iter;
+  sc.status = status;
+  if (sc.iter < tp.hist_cap) {
+    double* h = hist + (int64_t)12 * tp.hist_cap * p + 12 * sc.iter;
+    h[0] = sc.iter;
     h[1] = mu;
     h[2] = gp;
     h[3] = gd;
@@ -220,248 +257,346 @@ __global__ void k_fin_resid(IterScal* sc, const double* part, const unsigned lon
     h[7] = h[8] = h[9] = h[10] = 0.0;
     h[11] = tau;
   }
+  if (status != 0) halt_problem(sc, bf);
 }
 
-// ------------------------------------------------------------------ regularisation
-__global__ void k_fin_delta(IterScal* sc, double static_reg, double static_reg_dyn, double maxPdiag,
+// ------------------------------------------------------------------ per-problem small kernels
+// problems p = tid, tid + stride, ...
+#define FOR_PROBLEMS(B) \
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < (B); p += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_hmax_reset(IterScal* sc, int64_t B, const int* skip) {
+  if (skip && *skip) return;
+  FOR_PROBLEMS(B) sc[p].hmax_bits = 0ull;
+}
+
+// static + proportional regularisation
+__global__ void k_fin_delta(IterScal* sc, const ProbConst* pc, int64_t B, double static_reg, double static_reg_dyn,
                             const int* skip) {
   if (skip && *skip) return;
-  const double hm = bitsd(sc->hmax_bits);
-  sc->delta = static_reg + static_reg_dyn * fmax(maxPdiag, hm);
+  FOR_PROBLEMS(B) sc[p].delta = static_reg + static_reg_dyn * fmax(pc[p].maxPdiag, bitsd(sc[p].hmax_bits));
 }
 
 // ------------------------------------------------------------------ solves / refinement
-__global__ void k_inf_norm(const double* __restrict__ v, int64_t N, unsigned long long* maxb, const int* skip) {
+// per-problem max |v| over the chunks -> sc[p].rnorm_bits
+__global__ void k_inf_norm(ChunkGrid g, const double* __restrict__ v, IterScal* sc, const int* skip) {
   if (skip && *skip) return;
+  __shared__ double sh[32];
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
   double mx = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    mx = fmax(mx, fabs(v[i]));
-  mx = warp_max(mx);
-  if ((threadIdx.x & 31) == 0) atomicMax(maxb, dbits(mx));
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) mx = fmax(mx, fabs(v[i]));
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) atomicMax(&sc[pid].rnorm_bits, dbits(mx));
 }
 
-__global__ void k_ir_begin(IterScal* sc, const unsigned long long* rhsmax) {
-  sc->ir_skip = sc->halt;
-  sc->ir_cur = 0;
-  sc->rhs_norm = bitsd(*rhsmax);
-  sc->ir_prev = INFINITY;
+__global__ void k_ir_begin(IterScal* sc, int64_t B, BatchFlags* bf) {
+  FOR_PROBLEMS(B) {
+    IterScal& q = sc[p];
+    q.ir_skip = q.halt;
+    q.ir_cur = 0;
+    q.rhs_norm = bitsd(q.rnorm_bits);
+    q.rnorm_bits = 0ull;
+    q.ir_prev = INFINITY;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) bf->ir_none = bf->all_halt;
 }
 
+// dst (+)= src on the chunks of problems still refining (add) or of every problem (set)
 template <typename T>
-__global__ void k_set_from(double* __restrict__ dst, const T* __restrict__ src, int64_t N, int add, const int* skip) {
+__global__ void k_set_from(ChunkGrid g, double* __restrict__ dst, const T* __restrict__ src, int add,
+                           const IterScal* sc, const int* skip) {
   if (skip && *skip) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  if (add && sc[pid].ir_skip) return;
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x)
     dst[i] = add ? dst[i] + (double)src[i] : (double)src[i];
 }
 
-// Refinement stops at the tolerance (Sec. 3.6), or, when stop_ratio > 0, as soon as a
-// step has reduced ||r||_inf by less than stop_ratio (the last correction is kept).
-__global__ void k_ir_check(IterScal* sc, unsigned long long* rmax, double abstol, double reltol, double stop_ratio) {
-  if (sc->ir_skip) return;
-  const double r = bitsd(*rmax);
-  *rmax = 0ull;
-  const bool stalled = stop_ratio > 0 && !(r * stop_ratio < sc->ir_prev);
-  sc->ir_prev = r;
-  if (!(r > abstol + reltol * sc->rhs_norm) || stalled) sc->ir_skip = 1;  // converged (NaN also stops)
-  else {
-    sc->ir_cur += 1;
-    sc->ir_total += 1;
+// Refinement test of one problem (Sec. 3.6): stop at the tolerance, or, when
+// stop_ratio > 0, as soon as a step has reduced ||r||_inf by less than
+// stop_ratio (the last correction is kept), or after max_steps steps.
+__device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double stop_ratio, int max_steps) {
+  const double r = bitsd(q.rnorm_bits);
+  q.rnorm_bits = 0ull;
+  if (q.ir_skip) return false;
+  const bool stalled = stop_ratio > 0 && !(r * stop_ratio < q.ir_prev);
+  q.ir_prev = r;
+  if (!(r > abstol + reltol * q.rhs_norm) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
+    q.ir_skip = 1;
+    return false;
   }
+  q.ir_cur += 1;
+  q.ir_total += 1;
+  return true;
 }
 
-// The same test for the graph WHILE loop: continue (condition 1) iff another
-// refinement step is due; at most max_steps steps.
-__global__ void k_ir_check_cond(IterScal* sc, unsigned long long* rmax, double abstol, double reltol,
+// Unrolled loop (no graph): per-problem test, ir_none = no problem continues.
+__global__ void k_ir_check(IterScal* sc, int64_t B, BatchFlags* bf, double abstol, double reltol, double stop_ratio,
+                           int max_steps) {
+  int go = 0;
+  for (int64_t p = threadIdx.x; p < B; p += blockDim.x)
+    go |= ir_step_due(sc[p], abstol, reltol, stop_ratio, max_steps) ? 1 : 0;
+  go = __syncthreads_or(go);
+  if (threadIdx.x == 0) bf->ir_none = go ? 0 : 1;
+}
+
+// Graph WHILE loop: the same test; the body runs again iff some problem continues.
+__global__ void k_ir_check_cond(IterScal* sc, int64_t B, BatchFlags* bf, double abstol, double reltol,
                                 double stop_ratio, int max_steps, cudaGraphConditionalHandle h) {
-  unsigned int go = 0;
-  if (!sc->ir_skip) {
-    const double r = bitsd(*rmax);
-    const bool stalled = stop_ratio > 0 && !(r * stop_ratio < sc->ir_prev);
-    sc->ir_prev = r;
-    if (!(r > abstol + reltol * sc->rhs_norm) || stalled || sc->ir_cur >= max_steps) {
-      sc->ir_skip = 1;
-    } else {
-      sc->ir_cur += 1;
-      sc->ir_total += 1;
-      go = 1;
-    }
+  int go = 0;
+  for (int64_t p = threadIdx.x; p < B; p += blockDim.x)
+    go |= ir_step_due(sc[p], abstol, reltol, stop_ratio, max_steps) ? 1 : 0;
+  go = __syncthreads_or(go);
+  if (threadIdx.x == 0) {
+    bf->ir_none = go ? 0 : 1;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
   }
-  *rmax = 0ull;
-  cudaGraphSetConditional(h, go);
 }
 
 // ------------------------------------------------------------------ direction
-__global__ void k_dots(const double* __restrict__ a0, const double* __restrict__ b0, int64_t n0,
-                       const double* __restrict__ a1, const double* __restrict__ b1, int64_t n1,
-                       const double* __restrict__ a2, const double* __restrict__ b2, int64_t n2, double* part,
-                       int slot0, const int* skip) {
+// Up to three dot products; product k runs over the x chunks (xs[k] = 1) or the z
+// chunks, with a[k], b[k] indexed by the chunk's local index (x index or row).
+struct DotArgs {
+  const double* a[3];
+  const double* b[3];
+  int xs[3];
+  int np;
+};
+__global__ void k_dots(ChunkGrid g, DotArgs d, double* part, int slot0, const int* skip) {
   if (skip && *skip) return;
-  double s0 = 0, s1 = 0, s2 = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t i = t; i < n0; i += stride) s0 += a0[i] * b0[i];
-  for (int64_t i = t; i < n1; i += stride) s1 += a1[i] * b1[i];
-  for (int64_t i = t; i < n2; i += stride) s2 += a2[i] * b2[i];
-  block_write_sum(s0, part, slot0);
-  block_write_sum(s1, part, slot0 + 1);
-  block_write_sum(s2, part, slot0 + 2);
+  __shared__ double sh[32];
+  const bool zp = blockIdx.x >= g.nckx;
+  const Chunk c = g.ck[blockIdx.x];
+  const int64_t slot = chunk_slot(g);
+  for (int k = 0; k < d.np; ++k) {
+    if ((d.xs[k] != 0) == zp) continue;
+    double v = 0.0;
+    for (int64_t i = c.begin + threadIdx.x; i < c.begin + c.len; i += blockDim.x) v += d.a[k][i] * d.b[k][i];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) part[(slot0 + k) * g.pst + slot] = v;
+  }
 }
 
-__global__ void k_fin_const(IterScal* sc, const double* part, const int* skip) {
+__global__ void k_fin_const(IterScal* sc, const double* part, int64_t pst, const int64_t* ckx_ptr,
+                            const int64_t* ckz_ptr, const int* skip) {
   if (skip && *skip) return;
-  const double a = fin_sum(part, S_D0), b = fin_sum(part, S_D1);
+  const int64_t p = blockIdx.x;
+  const double a = fin_sum(part, S_D0, pst, ckx_ptr[p], ckx_ptr[p + 1]);
+  const double b = fin_sum(part, S_D1, pst, ckz_ptr[p], ckz_ptr[p + 1]);
   if (threadIdx.x == 0) {
-    sc->qp_dx2 = a;
-    sc->b_dz2 = b;
+    sc[p].qp_dx2 = a;
+    sc[p].b_dz2 = b;
   }
 }
 
 // Delta tau (first form of Eq. step-direction) and Delta kappa.
-__global__ void k_fin_dtau(IterScal* sc, const double* part, const int* skip) {
+__global__ void k_fin_dtau(IterScal* sc, const double* part, int64_t pst, const int64_t* ckx_ptr,
+                           const int64_t* ckz_ptr, const int* skip) {
   if (skip && *skip) return;
-  const double qpdx1 = fin_sum(part, S_D0), bdz1 = fin_sum(part, S_D1);
+  const int64_t p = blockIdx.x;
+  const double qpdx1 = fin_sum(part, S_D0, pst, ckx_ptr[p], ckx_ptr[p + 1]);
+  const double bdz1 = fin_sum(part, S_D1, pst, ckz_ptr[p], ckz_ptr[p + 1]);
   if (threadIdx.x != 0) return;
-  const double tau = sc->tau, kappa = sc->kappa;
-  const double num = sc->d_tau - sc->d_kap / tau + qpdx1 + bdz1;
-  const double den = kappa / tau + sc->xPx / (tau * tau) - sc->qp_dx2 - sc->b_dz2;
+  IterScal& q = sc[p];
+  const double tau = q.tau, kappa = q.kappa;
+  const double num = q.d_tau - q.d_kap / tau + qpdx1 + bdz1;
+  const double den = kappa / tau + q.xPx / (tau * tau) - q.qp_dx2 - q.b_dz2;
   const double dtau = num / den;
-  sc->dtau = dtau;
-  sc->dkap = -(sc->d_kap + kappa * dtau) / tau;
+  q.dtau = dtau;
+  q.dkap = -(q.d_kap + kappa * dtau) / tau;
 }
 
-__global__ void k_recover(double* __restrict__ dir, const double* __restrict__ sol1, const double* __restrict__ sol2,
-                          int64_t N, const IterScal* sc, const int* skip) {
+__global__ void k_recover(ChunkGrid g, double* __restrict__ dir, const double* __restrict__ sol1,
+                          const double* __restrict__ sol2, const IterScal* sc, const int* skip) {
   if (skip && *skip) return;
-  const double dtau = sc->dtau;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    dir[i] = sol1[i] + dtau * sol2[i];
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  const double dtau = sc[pid].dtau;
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) dir[i] = sol1[i] + dtau * sol2[i];
 }
 
 // right-hand side [d_x; -(d_z - d_s)] with (d_x, d_z, d_tau) = f G, d_s given, d_kappa given
-__global__ void k_rhs(double* __restrict__ rhs, const double* __restrict__ G, const double* __restrict__ ds,
-                      int64_t n, int64_t m, double f_dummy, IterScal* sc, int affine, const int* skip) {
+__global__ void k_rhs(ChunkGrid g, double* __restrict__ rhs, const double* __restrict__ G,
+                      const double* __restrict__ ds, IterScal* sc, int64_t B, int affine, const int* skip) {
   if (skip && *skip) return;
-  const double f = affine ? 1.0 : (1.0 - sc->sigma);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)gridDim.x * blockDim.x)
-    rhs[i] = (i < n) ? f * G[i] : -(f * G[i] - ds[i - n]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    sc->d_tau = f * sc->G3;
-    sc->d_kap = affine ? sc->kappa * sc->tau : sc->kappa * sc->tau + sc->dkap_a * sc->dtau_a - sc->sigma_mu;
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  const double f = affine ? 1.0 : (1.0 - sc[pid].sigma);
+  if (!zp) {
+    for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) rhs[i] = f * G[i];
+  } else {
+    for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) rhs[i] = -(f * G[i] - ds[i - g.n]);
   }
-  (void)f_dummy;
+  // the per-problem part, once per problem (every problem has >= 1 chunk and the grid has >= B threads)
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < B) {
+    IterScal& q = sc[t];
+    const double ft = affine ? 1.0 : (1.0 - q.sigma);
+    q.d_tau = ft * q.G3;
+    q.d_kap = affine ? q.kappa * q.tau : q.kappa * q.tau + q.dkap_a * q.dtau_a - q.sigma_mu;
+  }
 }
 
 // ------------------------------------------------------------------ step length
 struct StepParams {
   double backtrack, min_step, beta, step_fraction;
   int nonsym;
-  int64_t nu;
   int hist_cap;
 };
 
-__global__ void k_step_begin(IterScal* sc, const int* skip) {
+__global__ void k_step_begin(IterScal* sc, int64_t B, const int* skip) {
   if (skip && *skip) return;
-  sc->amin_bits = dbits(INFINITY);
+  FOR_PROBLEMS(B) sc[p].amin_bits = dbits(INFINITY);
 }
 
-__global__ void k_fin_step_sym(IterScal* sc, const int* skip) {
+__global__ void k_fin_step_sym(IterScal* sc, int64_t B, const int* skip) {
   if (skip && *skip) return;
-  double a = fmin(1.0, bitsd(sc->amin_bits));
-  if (sc->dtau < 0) a = fmin(a, -sc->tau / sc->dtau);
-  if (sc->dkap < 0) a = fmin(a, -sc->kappa / sc->dkap);
-  sc->alpha_sym = a;
+  FOR_PROBLEMS(B) {
+    IterScal& q = sc[p];
+    double a = fmin(1.0, bitsd(q.amin_bits));
+    if (q.dtau < 0) a = fmin(a, -q.tau / q.dtau);
+    if (q.dkap < 0) a = fmin(a, -q.kappa / q.dkap);
+    q.alpha_sym = a;
+  }
 }
 
-__global__ void k_mu_coef(IterScal* sc, const double* part, int64_t nu, const int* skip) {
+__global__ void k_mu_coef(IterScal* sc, const ProbConst* pc, const double* part, int64_t pst, const int64_t* ckz_ptr,
+                          const int* skip) {
   if (skip && *skip) return;
-  const double sdz = fin_sum(part, S_D0), dsz = fin_sum(part, S_D1), dsdz = fin_sum(part, S_D2);
+  const int64_t p = blockIdx.x;
+  const int64_t c0 = ckz_ptr[p], c1 = ckz_ptr[p + 1];
+  const double sdz = fin_sum(part, S_D0, pst, c0, c1), dsz = fin_sum(part, S_D1, pst, c0, c1),
+               dsdz = fin_sum(part, S_D2, pst, c0, c1);
   if (threadIdx.x != 0) return;
-  const double k = 1.0 / (double)(nu + 1);
-  sc->mu_coef[0] = (sc->sz + sc->tau * sc->kappa) * k;
-  sc->mu_coef[1] = (sdz + dsz + sc->tau * sc->dkap + sc->kappa * sc->dtau) * k;
-  sc->mu_coef[2] = (dsdz + sc->dtau * sc->dkap) * k;
+  IterScal& q = sc[p];
+  const double k = 1.0 / (double)(pc[p].nu + 1);
+  q.mu_coef[0] = (q.sz + q.tau * q.kappa) * k;
+  q.mu_coef[1] = (sdz + dsz + q.tau * q.dkap + q.kappa * q.dtau) * k;
+  q.mu_coef[2] = (dsdz + q.dtau * q.dkap) * k;
 }
 
-__global__ void k_fin_step(IterScal* sc, StepParams sp, int combined, double* hist, const int* skip) {
+__global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined, double* hist, BatchFlags* bf,
+                           const int* skip) {
   if (skip && *skip) return;
-  double a = sc->alpha_sym;
-  if (sp.nonsym) {
-    int j = sc->ns.jint;
-    if (combined && sc->ns.fail) {
-      const unsigned long long m = sc->ns.mask;
-      j = (m == 0ull) ? -1 : j + __ffsll((long long)m);  // first common pass after jint
+  FOR_PROBLEMS(B) {
+    IterScal& q = sc[p];
+    if (q.halt) continue;
+    double a = q.alpha_sym;
+    if (sp.nonsym) {
+      int j = q.ns.jint;
+      if (combined && q.ns.fail) {
+        const unsigned long long m = q.ns.mask;
+        j = (m == 0ull) ? -1 : j + __ffsll((long long)m);  // first common pass after jint
+      }
+      a = (j < 0) ? 0.0 : a * pow(sp.backtrack, (double)j);
     }
-    a = (j < 0) ? 0.0 : a * pow(sp.backtrack, (double)j);
-  }
-  double* h = (sc->iter < sp.hist_cap) ? hist + 12 * sc->iter : nullptr;
-  if (!combined) {
-    sc->alpha_a = a;
-    const double om = 1.0 - a;
-    sc->sigma = om * om * om;
-    sc->sigma_mu = sc->sigma * sc->mu;
-    sc->dtau_a = sc->dtau;
-    sc->dkap_a = sc->dkap;
-    if (h) {
-      h[7] = a;
-      h[8] = sc->sigma;
-    }
-  } else {
-    sc->alpha_c = a;
-    if (h) {
-      h[9] = a;
-      h[10] = sc->ir_total;
-    }
-    if (!(a >= sp.min_step)) {
-      sc->status = CLR_INSUFFICIENT_PROGRESS;
-      sc->halt = 1;
+    double* h = (q.iter < sp.hist_cap) ? hist + (int64_t)12 * sp.hist_cap * p + 12 * q.iter : nullptr;
+    if (!combined) {
+      q.alpha_a = a;
+      const double om = 1.0 - a;
+      q.sigma = om * om * om;
+      q.sigma_mu = q.sigma * q.mu;
+      q.dtau_a = q.dtau;
+      q.dkap_a = q.dkap;
+      if (h) {
+        h[7] = a;
+        h[8] = q.sigma;
+      }
+    } else {
+      q.alpha_c = a;
+      if (h) {
+        h[9] = a;
+        h[10] = q.ir_total;
+      }
+      if (!(a >= sp.min_step)) {
+        q.status = CLR_INSUFFICIENT_PROGRESS;
+        halt_problem(q, bf);
+      }
     }
   }
 }
 
-__global__ void k_update(double* __restrict__ xz, double* __restrict__ s, const double* __restrict__ dir,
-                         const double* __restrict__ ds, int64_t N, int64_t m, const IterScal* sc, double frac,
-                         const int* skip) {
+__global__ void k_update(ChunkGrid g, double* __restrict__ xz, double* __restrict__ s, const double* __restrict__ dir,
+                         const double* __restrict__ ds, const IterScal* sc, double frac, const int* skip) {
   if (skip && *skip) return;
-  const double a = frac * sc->alpha_c;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  if (sc[pid].halt) return;
+  const double a = frac * sc[pid].alpha_c;
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
     xz[i] += a * dir[i];
-    if (i < m) s[i] += a * ds[i];
+    if (zp) s[i - g.n] += a * ds[i - g.n];
   }
 }
 
-__global__ void k_fin_update(IterScal* sc, double frac, const int* dyn_hits, const int* skip) {
+__global__ void k_fin_update(IterScal* sc, int64_t B, double frac, const int* dyn_hits, const int* skip) {
   if (skip && *skip) return;
-  const double a = frac * sc->alpha_c;
-  sc->tau += a * sc->dtau;
-  sc->kappa += a * sc->dkap;
-  sc->iter += 1;
-  sc->dyn_hits = *dyn_hits;
+  FOR_PROBLEMS(B) {
+    IterScal& q = sc[p];
+    if (q.halt) continue;
+    const double a = frac * q.alpha_c;
+    q.tau += a * q.dtau;
+    q.kappa += a * q.dkap;
+    q.iter += 1;
+    q.dyn_hits = *dyn_hits;
+  }
 }
 
 // ------------------------------------------------------------------ init helpers
-__global__ void k_init_scal(IterScal* sc) {
-  memset(sc, 0, sizeof(IterScal));
-  sc->tau = 1.0;
-  sc->kappa = 1.0;
+__global__ void k_init_scal(IterScal* sc, int64_t B, BatchFlags* bf) {
+  FOR_PROBLEMS(B) {
+    memset(&sc[p], 0, sizeof(IterScal));
+    sc[p].tau = 1.0;
+    sc[p].kappa = 1.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    bf->all_halt = 0;
+    bf->n_running = (int)B;
+    bf->ir_none = 0;
+  }
 }
 
-__global__ void k_init_delta(IterScal* sc, double static_reg, double static_reg_dyn, double maxPdiag) {
-  sc->delta = static_reg + static_reg_dyn * fmax(maxPdiag, 1.0);
+__global__ void k_init_delta(IterScal* sc, const ProbConst* pc, int64_t B, double static_reg, double static_reg_dyn) {
+  FOR_PROBLEMS(B) sc[p].delta = static_reg + static_reg_dyn * fmax(pc[p].maxPdiag, 1.0);
 }
 
-__global__ void k_build_rhs_init(double* __restrict__ rhs, const double* __restrict__ q, const double* __restrict__ b,
-                                 int64_t n, int64_t m, int which) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)gridDim.x * blockDim.x)
-    rhs[i] = (which == 0) ? (i < n ? 0.0 : b[i - n]) : (i < n ? -q[i] : 0.0);
+// which 0: [0; b], which 1: [-q; 0], which 2: [-q; b]
+__global__ void k_build_rhs(ChunkGrid g, double* __restrict__ rhs, const double* __restrict__ q,
+                            const double* __restrict__ b, int which, const int* skip) {
+  if (skip && *skip) return;
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x)
+    rhs[i] = zp ? (which == 1 ? 0.0 : b[i - g.n]) : (which == 0 ? 0.0 : -q[i]);
 }
 
-__global__ void k_init_take(double* __restrict__ xz, double* __restrict__ s, const double* __restrict__ sol,
-                            int64_t n, int64_t m, int which) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + m; i += (int64_t)gridDim.x * blockDim.x) {
+// symmetric initial point of the problems with symmetric cones only
+__global__ void k_init_take(ChunkGrid g, double* __restrict__ xz, double* __restrict__ s,
+                            const double* __restrict__ sol, const ProbConst* pc, int which) {
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  if (!pc[pid].sym) return;
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
     if (which == 0) {
-      if (i < n) xz[i] = sol[i];
-      else s[i - n] = -sol[i];
-    } else if (i >= n) {
+      if (!zp) xz[i] = sol[i];
+      else s[i - g.n] = -sol[i];
+    } else if (zp) {
       xz[i] = sol[i];
     }
   }
@@ -485,7 +620,11 @@ void* DeviceArena::alloc(size_t bytes) {
   void* p = nullptr;
   bytes = (bytes + 255) & ~(size_t)255;
   if (g_alloc.a) p = g_alloc.a(bytes, g_alloc.ctx);
-  else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  else if (async_) {
+    if (cudaMallocAsync(&p, bytes, async_) != cudaSuccess) p = nullptr;
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
   if (!p) return nullptr;
   if (nblocks_ == cap_) {
     size_t nc = cap_ ? 2 * cap_ : 64;
@@ -503,11 +642,45 @@ void* DeviceArena::alloc(size_t bytes) {
 void DeviceArena::release() {
   for (size_t i = 0; i < nblocks_; ++i) {
     if (g_alloc.f) g_alloc.f(blocks_[i].p, blocks_[i].n, g_alloc.ctx);
+    else if (async_) cudaFreeAsync(blocks_[i].p, async_);
     else cudaFree(blocks_[i].p);
   }
   delete[] blocks_;
   blocks_ = nullptr;
   nblocks_ = cap_ = total_ = 0;
+}
+
+namespace {
+std::mutex g_pin_mu;
+std::vector<std::pair<size_t, void*>> g_pin_free;  // (size class, block)
+size_t pin_class(size_t bytes) {
+  size_t c = 256;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+}  // namespace
+
+void* pinned_get(size_t bytes) {
+  const size_t c = pin_class(bytes);
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pin_free.size(); ++i)
+      if (g_pin_free[i].first == c) {
+        void* p = g_pin_free[i].second;
+        g_pin_free[i] = g_pin_free.back();
+        g_pin_free.pop_back();
+        return p;
+      }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, c) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.emplace_back(pin_class(bytes), p);
 }
 
 void Solver::drop_graphs() {
@@ -543,13 +716,20 @@ int64_t count_kernel_nodes(cudaGraph_t g) {
   }
   return k;
 }
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 }  // namespace
 
 Solver::~Solver() {
+  if (stream_) cudaStreamSynchronize(stream_);  // nothing of ours in flight before buffers go back
   drop_graphs();
+  ar_.release();
   for (cudaEvent_t e : ev_)
     if (e) cudaEventDestroy(e);
-  if (sc_host_) cudaFreeHost(sc_host_);
+  if (step_ev_) cudaEventDestroy(step_ev_);
+  pinned_put(sc_host_, sizeof(IterScal) * (size_t)lay.B);
+  pinned_put(bf_host_, sizeof(BatchFlags));
   if (own_stream_ && stream_) cudaStreamDestroy(stream_);
   if (body_stream_) cudaStreamDestroy(body_stream_);
 }
@@ -557,30 +737,48 @@ Solver::~Solver() {
 int Solver::analyze(const clr_csc* P, const double* q, const clr_csc* A, const double* b, const clr_cone* cones,
                     int32_t ncones, const clr_settings& s) {
   st = s;
-  auto t0 = std::chrono::steady_clock::now();
-  int rc = build_problem(hp, P, q, A, b, cones, ncones, st, err);
+  const double t0 = now_s();
+  std::vector<HostProblem> ps(1);
+  int rc = build_problem(ps[0], P, q, A, b, cones, ncones, st, err);
   if (rc != CLR_OK) return rc;
-  rc = symbolic_analyze(hp.n + hp.m, hp.kcol_ptr, hp.krow, nullptr, sy);
+  rc = analyze_cohort(std::move(ps), {}, s);
+  setup_s = now_s() - t0;
+  return rc;
+}
+
+int Solver::analyze_cohort(std::vector<HostProblem>&& ps, const std::vector<std::vector<int64_t>>& orders,
+                           const clr_settings& s) {
+  st = s;
+  const double t0 = now_s();
+  probs = std::move(ps);
+  int rc = build_cohort(probs, orders, hp, lay, sy, err);
   if (rc != CLR_OK) return rc;
   build_numeric_maps(sy, hp.kcol_ptr, hp.krow, mp);
-  setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  setup_s += now_s() - t0;
   return CLR_OK;
 }
 
 int Solver::upload() {
-  auto t0 = std::chrono::steady_clock::now();
-  const int64_t n = hp.n, m = hp.m, N = n + m;
+  const double t0 = now_s();
+  const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   if (!stream_) {
     CLR_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
     own_stream_ = true;
   }
-  CLR_CUDA(cudaMallocHost(&sc_host_, sizeof(IterScal)));
+  sc_host_ = static_cast<IterScal*>(pinned_get(sizeof(IterScal) * (size_t)B));
+  bf_host_ = static_cast<BatchFlags*>(pinned_get(sizeof(BatchFlags)));
+  if (!sc_host_ || !bf_host_) return CLR_E_OOM;
   CLR_CUDA(cudaStreamCreateWithFlags(&body_stream_, cudaStreamNonBlocking));
   for (cudaEvent_t& e : ev_) CLR_CUDA(cudaEventCreate(&e));
-  // expected pivot sign by elimination position: + for x, - for z
+  CLR_CUDA(cudaEventCreateWithFlags(&step_ev_, cudaEventDisableTiming));
+  // expected pivot sign and problem by elimination position
   std::vector<int8_t> dsign(N);
-  for (int64_t k = 0; k < N; ++k) dsign[k] = sy.perm[k] < n ? 1 : -1;
-  int rc = ldl_structure_upload(ar_, sy, mp, dsign, st.factor_bits == 64 ? 96 : 128, ls_);
+  std::vector<int32_t> pos_pid(N);
+  for (int64_t k = 0; k < N; ++k) {
+    dsign[k] = sy.perm[k] < n ? 1 : -1;
+    pos_pid[k] = lay.pid[sy.perm[k]];
+  }
+  int rc = ldl_structure_upload(ar_, sy, mp, dsign, st.factor_bits == 64 ? 96 : 128, ls_, &pos_pid);
   if (rc != CLR_OK) return rc;
   rc = (st.factor_bits == 64) ? f64_.alloc(ar_, ls_) : f32_.alloc(ar_, ls_);
   if (rc != CLR_OK) return rc;
@@ -596,8 +794,7 @@ int Solver::upload() {
     for (int64_t i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
     std::vector<int32_t> col(cnt[N]), vi(cnt[N]);
     std::vector<int64_t> next(cnt.begin(), cnt.end() - 1);
-    // fill row by row in increasing column order: rows get entries from columns j (lower part,
-    // row i >= j) visited in increasing j, and their own column's entries (upper part) after
+    // rows get entries from columns j (lower part, row i >= j) and their own column's entries
     for (int64_t j = 0; j < N; ++j)
       for (int64_t p = hp.kcol_ptr[j]; p < hp.kcol_ptr[j + 1]; ++p) {
         const int64_t i = hp.krow[p];
@@ -612,9 +809,10 @@ int Solver::upload() {
         col[next[j]] = (int32_t)i;
         vi[next[j]++] = (int32_t)p;
       }
+    std::vector<std::pair<int32_t, int32_t>> row;
     for (int64_t i = 0; i < N; ++i) {
       // sort each row by column (entries may interleave)
-      std::vector<std::pair<int32_t, int32_t>> row;
+      row.clear();
       for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) row.emplace_back(col[p], vi[p]);
       std::sort(row.begin(), row.end());
       for (int64_t p = cnt[i]; p < cnt[i + 1]; ++p) {
@@ -628,6 +826,20 @@ int Solver::upload() {
     const double avg = N ? (double)cnt[N] / (double)N : 1.0;
     csr_group_ = avg > 24 ? 32 : (avg > 12 ? 16 : (avg > 6 ? 8 : 4));
   }
+  // cohort layout
+  nckx_ = (int64_t)lay.ckx.size();
+  nckz_ = (int64_t)lay.ckz.size();
+  pst_ = std::max<int64_t>(1, std::max(nckx_, nckz_));
+  {
+    std::vector<Chunk> ck(lay.ckx);
+    ck.insert(ck.end(), lay.ckz.begin(), lay.ckz.end());
+    v_.ck = ar_.upload(ck.data(), (int64_t)ck.size());
+  }
+  v_.ckx_ptr = ar_.upload(lay.ckx_ptr.data(), B + 1);
+  v_.ckz_ptr = ar_.upload(lay.ckz_ptr.data(), B + 1);
+  v_.pid = ar_.upload(lay.pid.data(), N);
+  v_.pc = ar_.upload(lay.pc.data(), B);
+  hist_rows_ = st.max_iter + 2;
   v_.kval = ar_.upload(hp.kval.data(), (int64_t)hp.kval.size());
   v_.q = ar_.upload(hp.q.data(), n);
   v_.b = ar_.upload(hp.b.data(), m);
@@ -647,11 +859,13 @@ int Solver::upload() {
   v_.dir = ar_.alloc_n<double>(N);
   v_.ds = ar_.alloc_n<double>(m);
   v_.dsrhs = ar_.alloc_n<double>(m);
-  v_.r = ar_.alloc_n<double>(N + 16);  // also holds 8 residual-stage maxima
+  v_.r = ar_.alloc_n<double>(N);
   v_.solb = ar_.alloc_n<double>(N);
-  v_.part = ar_.alloc_n<double>((int64_t)S_NSLOT * kRedBlocks);
-  v_.hist = ar_.alloc_n<double>(12 * (int64_t)(st.max_iter + 2));
-  sc_ = ar_.alloc_n<IterScal>(1);
+  v_.part = ar_.alloc_n<double>((int64_t)S_NSLOT * pst_);
+  v_.maxb = ar_.alloc_n<unsigned long long>((int64_t)M_NMAX * B);
+  v_.hist = ar_.alloc_n<double>(12 * (int64_t)hist_rows_ * B);
+  sc_ = ar_.alloc_n<IterScal>(B);
+  bf_ = ar_.alloc_n<BatchFlags>(1);
   // cone layout
   const ConeLayout& cl = hp.cl;
   cd_ = ConeDev();
@@ -660,6 +874,9 @@ int Solver::upload() {
   cd_.m_nonneg = cl.m_nonneg;
   cd_.kvz = v_.kval + hp.kval_x;
   cd_.nkz = cl.kval_z;
+  cd_.nprob = B;
+  cd_.row_pid = v_.pid + n;
+  cd_.pc = v_.pc;
   cd_.scratch = ar_.alloc_n<double>(m);
   cd_.nn_w = ar_.alloc_n<double>(cl.m_nonneg);
   cd_.nn_lam = ar_.alloc_n<double>(cl.m_nonneg);
@@ -700,10 +917,20 @@ int Solver::upload() {
   cd_.psd_lam = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k);
   cd_.ep_zt = ar_.alloc_n<double>(3 * (cd_.n_exp + cd_.n_pow));
   exp_central_point_host(cd_.exp_center);
-  if (!v_.kptr || !v_.kcol || !v_.kvi || !v_.kval || !v_.xz || !v_.part || !sc_ || !cd_.scratch) return CLR_E_OOM;
+  if (!v_.kptr || !v_.kcol || !v_.kvi || !v_.kval || !v_.xz || !v_.part || !sc_ || !bf_ || !cd_.scratch || !v_.ck ||
+      !v_.pid || !v_.pc || !v_.hist || !v_.maxb)
+    return CLR_E_OOM;
   CLR_CUDA(cudaStreamSynchronize(stream_));
   device_ready = true;
-  setup_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  setup_s += now_s() - t0;
+  return CLR_OK;
+}
+
+int Solver::use_stream_ordered(cudaStream_t stream) {
+  if (device_ready || !stream) return CLR_E_STATE;
+  stream_ = stream;
+  own_stream_ = false;
+  ar_.set_stream_ordered(stream);
   return CLR_OK;
 }
 
@@ -720,36 +947,34 @@ int Solver::set_stream(void* stream) {
 }
 
 int Solver::factor() {
-  const int* halt = &sc_->halt;
-  if (st.factor_bits == 64)
-    return f64_.factor(stream_, v_.kval, &sc_->delta, st.dyn_reg_eps, st.dyn_reg_delta, halt);
-  return f32_.factor(stream_, v_.kval, &sc_->delta, st.dyn_reg_eps, st.dyn_reg_delta, halt);
+  const int* halt = &bf_->all_halt;
+  if (st.factor_bits == 64) return f64_.factor(stream_, v_.kval, sc_, st.dyn_reg_eps, st.dyn_reg_delta, halt);
+  return f32_.factor(stream_, v_.kval, sc_, st.dyn_reg_eps, st.dyn_reg_delta, halt);
 }
 
-// sol = K^{-1} rhs by the factor plus iterative refinement on the unregularised K (FP64).
-// While a graph is being captured the refinement loop is a conditional WHILE
-// node (its body runs only as often as needed); otherwise it is unrolled to
-// ir_max_steps steps whose kernels return at once after convergence.
+// sol = K^{-1} rhs by the factor plus iterative refinement on the unregularised K (FP64),
+// per problem.  While a graph is being captured the refinement loop is a conditional
+// WHILE node (its body runs only while some problem needs another step); otherwise it
+// is unrolled to ir_max_steps steps whose kernels return at once after convergence.
 int Solver::kkt_solve(const double* rhs, double* sol) {
-  const int64_t N = hp.n + hp.m;
+  const int64_t N = hp.n + hp.m, B = lay.B;
   cudaStream_t s = stream_;
-  const int* halt = &sc_->halt;
-  const int* irs = &sc_->ir_skip;
-  unsigned long long* rmax = &sc_->rnorm_bits;
-  CLR_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s));
-  k_inf_norm<<<grid_for(N, 256, kRedBlocks), 256, 0, s>>>(rhs, N, rmax, halt);
-  k_ir_begin<<<1, 1, 0, s>>>(sc_, rmax);
-  CLR_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s));
-  const int g = grid_for(N, 256);
+  const int* halt = &bf_->all_halt;
+  const int* irs = &bf_->ir_none;
+  const ChunkGrid cg{v_.ck, nckx_, pst_, hp.n};
+  const unsigned nck = (unsigned)(nckx_ + nckz_);
+  const int pg = grid_for(B, 128);
+  k_inf_norm<<<nck, 256, 0, s>>>(cg, rhs, sc_, halt);
+  k_ir_begin<<<pg, 128, 0, s>>>(sc_, B, bf_);
   auto ldl_solve_add = [&](cudaStream_t ss, const double* b, int add) -> int {
     if (st.factor_bits == 64) {
       int rc = f64_.solve(ss, b, irs);
       if (rc) return rc;
-      k_set_from<double><<<g, 256, 0, ss>>>(sol, f64_.xs, N, add, irs);
+      k_set_from<double><<<nck, 256, 0, ss>>>(cg, sol, f64_.xs, add, sc_, irs);
     } else {
       int rc = f32_.solve(ss, b, irs);
       if (rc) return rc;
-      k_set_from<float><<<g, 256, 0, ss>>>(sol, f32_.xs, N, add, irs);
+      k_set_from<float><<<nck, 256, 0, ss>>>(cg, sol, f32_.xs, add, sc_, irs);
     }
     return CLR_OK;
   };
@@ -757,12 +982,13 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   const int kg = grid_for(N * G, 256, 16 * kSMs);
   auto residual = [&](cudaStream_t ss) {
     switch (G) {
-      case 32: k_kmv<32><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
-      case 16: k_kmv<16><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
-      case 8: k_kmv<8><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
-      default: k_kmv<4><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, rmax, irs); break;
+      case 32: k_kmv<32><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      case 16: k_kmv<16><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      case 8: k_kmv<8><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      default: k_kmv<4><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
     }
   };
+  const int cb = (int)std::min<int64_t>(1024, std::max<int64_t>(32, ((B + 31) / 32) * 32));
   int rc = ldl_solve_add(s, rhs, 0);
   if (rc) return rc;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -770,7 +996,7 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   if (cs != cudaStreamCaptureStatusActive || st.ir_max_steps == 0) {
     for (int it = 0; it < st.ir_max_steps; ++it) {
       residual(s);
-      k_ir_check<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio);
+      k_ir_check<<<1, cb, 0, s>>>(sc_, B, bf_, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio, st.ir_max_steps);
       rc = ldl_solve_add(s, v_.r, 1);
       if (rc) return rc;
     }
@@ -778,30 +1004,30 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
     return CLR_OK;
   }
   // graph capture: condition set by the check before the node and at the end of each body pass
-  cudaGraph_t cg = nullptr;
+  cudaGraph_t cgraph = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   const cudaGraphEdgeData* edata = nullptr;
   size_t ndeps = 0;
   cudaGraphConditionalHandle h;
   residual(s);
-  CLR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
-  CLR_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 0, 0));
-  k_ir_check_cond<<<1, 1, 0, s>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio, st.ir_max_steps, h);
+  CLR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cgraph, nullptr, nullptr, nullptr));
+  CLR_CUDA(cudaGraphConditionalHandleCreate(&h, cgraph, 0, 0));
+  k_ir_check_cond<<<1, cb, 0, s>>>(sc_, B, bf_, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio, st.ir_max_steps, h);
   CLR_CHECK_LAUNCH();
-  CLR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, &edata, &ndeps));
+  CLR_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cgraph, &deps, &edata, &ndeps));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t node;
-  CLR_CUDA(cudaGraphAddNode(&node, cg, deps, edata, ndeps, &cp));
+  CLR_CUDA(cudaGraphAddNode(&node, cgraph, deps, edata, ndeps, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   CLR_CUDA(cudaStreamBeginCaptureToGraph(body_stream_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   rc = ldl_solve_add(body_stream_, v_.r, 1);
   residual(body_stream_);
-  k_ir_check_cond<<<1, 1, 0, body_stream_>>>(sc_, rmax, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio,
-                                             st.ir_max_steps, h);
+  k_ir_check_cond<<<1, cb, 0, body_stream_>>>(sc_, B, bf_, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio,
+                                              st.ir_max_steps, h);
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(body_stream_, &out);
   if (rc) return rc;
@@ -818,18 +1044,18 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
 namespace {
 template <int G>
 void launch_kmv_split(cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v, const double* x,
-                      double* lo, double* hi, const double* rhs, double* out, const int* skip) {
+                      double* lo, double* hi, const double* rhs, double* out, IterScal* sc, const int* skip) {
   const int kg = grid_for((r1 - r0) * G, 256, 16 * kSMs);
-  k_kmv<G><<<kg, 256, 0, s>>>(mode, r0, r1, n, v.kptr, v.kcol, v.kvi, v.kval, x, lo, hi, rhs, out, nullptr, skip);
+  k_kmv<G><<<kg, 256, 0, s>>>(mode, r0, r1, n, v.kptr, v.kcol, v.kvi, v.kval, x, lo, hi, rhs, out, v.pid, sc, skip);
 }
 void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v, const double* x,
-         double* lo, double* hi, const double* rhs, double* out, const int* skip) {
+         double* lo, double* hi, const double* rhs, double* out, IterScal* sc, const int* skip) {
   if (r1 <= r0) return;
   switch (G) {
-    case 32: launch_kmv_split<32>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, skip); break;
-    case 16: launch_kmv_split<16>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, skip); break;
-    case 8: launch_kmv_split<8>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, skip); break;
-    default: launch_kmv_split<4>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, skip); break;
+    case 32: launch_kmv_split<32>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
+    case 16: launch_kmv_split<16>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
+    case 8: launch_kmv_split<8>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
+    default: launch_kmv_split<4>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
   }
 }
 }  // namespace
@@ -837,137 +1063,147 @@ void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, con
 // One search direction: solve with the current right-hand side (rhs built by
 // k_rhs), Delta tau, Delta x/z, Delta s = -d_s - H Delta z.
 int Solver::direction(bool affine) {
-  const int64_t n = hp.n, m = hp.m, N = n + m;
+  const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   cudaStream_t s = stream_;
-  const int* halt = &sc_->halt;
+  const int* halt = &bf_->all_halt;
+  const ChunkGrid cg{v_.ck, nckx_, pst_, n};
+  const unsigned nck = (unsigned)(nckx_ + nckz_);
   double* dir = affine ? v_.dir_a : v_.dir;
   double* ds = affine ? v_.dsa : v_.ds;
   int rc = kkt_solve(v_.rhs, v_.sol1);
   if (rc) return rc;
-  k_dots<<<kRedBlocks, kRedThreads, 0, s>>>(v_.qp, v_.sol1, n, v_.b, v_.sol1 + n, m, nullptr, nullptr, 0, v_.part,
-                                            S_D0, halt);
-  k_fin_dtau<<<1, 256, 0, s>>>(sc_, v_.part, halt);
-  k_recover<<<grid_for(N, 256), 256, 0, s>>>(dir, v_.sol1, v_.sol2, N, sc_, halt);
-  kmv(csr_group_, s, 2, n, N, n, v_, dir, nullptr, nullptr, v_.dsrhs, ds, halt);
+  DotArgs da{{v_.qp, v_.b, nullptr}, {v_.sol1, v_.sol1 + n, nullptr}, {1, 0, 0}, 2};
+  k_dots<<<nck, 256, 0, s>>>(cg, da, v_.part, S_D0, halt);
+  k_fin_dtau<<<(unsigned)B, 128, 0, s>>>(sc_, v_.part, pst_, v_.ckx_ptr, v_.ckz_ptr, halt);
+  k_recover<<<nck, 256, 0, s>>>(cg, dir, v_.sol1, v_.sol2, sc_, halt);
+  kmv(csr_group_, s, 2, n, N, n, v_, dir, nullptr, nullptr, v_.dsrhs, ds, sc_, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
 
 int Solver::step_length(bool combined) {
-  const int64_t n = hp.n, m = hp.m;
+  const int64_t n = hp.n, B = lay.B;
   cudaStream_t s = stream_;
-  const int* halt = &sc_->halt;
+  const int* halt = &bf_->all_halt;
+  const ChunkGrid cg{v_.ck, nckx_, pst_, n};
+  const unsigned nck = (unsigned)(nckx_ + nckz_);
+  const int pg = grid_for(B, 128);
   const double* dir = combined ? v_.dir : v_.dir_a;
   const double* ds = combined ? v_.ds : v_.dsa;
-  k_step_begin<<<1, 1, 0, s>>>(sc_, halt);
-  int rc = cones_step_symmetric(s, cd_, v_.s, ds, v_.xz + n, dir + n, &sc_->amin_bits, halt);
+  k_step_begin<<<pg, 128, 0, s>>>(sc_, B, halt);
+  int rc = cones_step_symmetric(s, cd_, v_.s, ds, v_.xz + n, dir + n, sc_, halt);
   if (rc) return rc;
-  k_fin_step_sym<<<1, 1, 0, s>>>(sc_, halt);
+  k_fin_step_sym<<<pg, 128, 0, s>>>(sc_, B, halt);
   const bool nonsym = (cd_.n_exp + cd_.n_pow) > 0;
   if (nonsym) {
     if (combined) {
-      k_dots<<<kRedBlocks, kRedThreads, 0, s>>>(v_.s, dir + n, m, ds, v_.xz + n, m, ds, dir + n, m, v_.part, S_D0,
-                                                halt);
-      k_mu_coef<<<1, 256, 0, s>>>(sc_, v_.part, hp.cl.nu, halt);
+      DotArgs da{{v_.s, ds, ds}, {dir + n, v_.xz + n, dir + n}, {0, 0, 0}, 3};
+      k_dots<<<nck, 256, 0, s>>>(cg, da, v_.part, S_D0, halt);
+      k_mu_coef<<<(unsigned)B, 128, 0, s>>>(sc_, v_.pc, v_.part, pst_, v_.ckz_ptr, halt);
     }
-    rc = cones_step_nonsym(s, cd_, v_.s, ds, v_.xz + n, dir + n, &sc_->alpha_sym, st.backtrack, combined ? 1 : 0,
-                           st.nbhd_beta, sc_->mu_coef, &sc_->ns, halt);
+    rc = cones_step_nonsym(s, cd_, v_.s, ds, v_.xz + n, dir + n, sc_, st.backtrack, combined ? 1 : 0, st.nbhd_beta,
+                           halt);
     if (rc) return rc;
   }
-  StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hp.cl.nu,
-                st.max_iter + 1};
-  k_fin_step<<<1, 1, 0, s>>>(sc_, sp, combined ? 1 : 0, v_.hist, halt);
+  StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hist_rows_};
+  k_fin_step<<<pg, 128, 0, s>>>(sc_, B, sp, combined ? 1 : 0, v_.hist, bf_, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
 
 // Algorithm 1, one pass of steps 12 (residuals, here at the top), 4-11.
 int Solver::iteration() {
-  const int64_t n = hp.n, m = hp.m, N = n + m;
+  const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   cudaStream_t s = stream_;
-  const int* halt = &sc_->halt;
-  unsigned long long* maxb = reinterpret_cast<unsigned long long*>(v_.r);  // r is free here; 8 slots
+  const int* halt = &bf_->all_halt;
+  const ChunkGrid cg{v_.ck, nckx_, pst_, n};
+  const unsigned nck = (unsigned)(nckx_ + nckz_);
+  const int pg = grid_for(B, 128);
   int rc;
   mark(2);
   // ---- residuals, objectives, mu, termination ----
-  kmv(csr_group_, s, 0, 0, N, n, v_, v_.xz, v_.lo, v_.hi, nullptr, nullptr, halt);
-  CLR_CUDA(cudaMemsetAsync(maxb, 0, sizeof(unsigned long long) * M_NMAX, s));
-  k_resid_x<<<kRedBlocks, kRedThreads, 0, s>>>(n, v_.xz, v_.lo, v_.hi, v_.q, v_.D, sc_, v_.G, v_.qp, v_.part, maxb,
-                                               halt);
-  k_resid_z<<<kRedBlocks, kRedThreads, 0, s>>>(n, m, v_.xz, v_.s, v_.lo, v_.b, v_.E, sc_, v_.G, v_.part, maxb, halt);
-  TermParams tp{hp.c, hp.bnorm, hp.qnorm, st.eps_feas, st.eps_inf, hp.cl.nu, st.max_iter, st.max_iter + 1};
-  k_fin_resid<<<1, 256, 0, s>>>(sc_, v_.part, maxb, tp, v_.hist, halt);
+  kmv(csr_group_, s, 0, 0, N, n, v_, v_.xz, v_.lo, v_.hi, nullptr, nullptr, sc_, halt);
+  CLR_CUDA(cudaMemsetAsync(v_.maxb, 0, sizeof(unsigned long long) * M_NMAX * (size_t)B, s));
+  k_resid<<<nck, 256, 0, s>>>(cg, v_.xz, v_.s, v_.lo, v_.hi, v_.q, v_.b, v_.D, v_.E, sc_, v_.G, v_.qp, v_.part,
+                              v_.maxb, halt);
+  TermParams tp{st.eps_feas, st.eps_inf, st.max_iter, hist_rows_};
+  k_fin_resid<<<(unsigned)B, 128, 0, s>>>(sc_, v_.pc, v_.part, pst_, v_.ckx_ptr, v_.ckz_ptr, v_.maxb, tp, v_.hist,
+                                          bf_, halt);
   // ---- step 4: scaling H, KKT values; static + proportional regularisation ----
-  CLR_CUDA(cudaMemsetAsync(&sc_->hmax_bits, 0, sizeof(unsigned long long), s));
-  rc = cones_scaling(s, cd_, v_.s, v_.xz + n, &sc_->mu, &sc_->hmax_bits, halt);
+  k_hmax_reset<<<pg, 128, 0, s>>>(sc_, B, halt);
+  rc = cones_scaling(s, cd_, v_.s, v_.xz + n, sc_, halt);
   if (rc) return rc;
-  k_fin_delta<<<1, 1, 0, s>>>(sc_, st.static_reg, st.static_reg_dyn, hp.maxPdiag, halt);
+  k_fin_delta<<<pg, 128, 0, s>>>(sc_, v_.pc, B, st.static_reg, st.static_reg_dyn, halt);
   // ---- step 5: factor ----
   mark(3);
   rc = factor();
   if (rc) return rc;
   mark(4);
   // ---- constant right-hand side [-q; b] ----
-  k_build_rhs_init<<<grid_for(N, 256), 256, 0, s>>>(v_.rhs, v_.q, v_.b, n, m, 1);
-  // k_build_rhs_init(which=1) gives [-q; 0]; add b on the z part
-  k_set_from<double><<<grid_for(m, 256), 256, 0, s>>>(v_.rhs + n, v_.b, m, 1, halt);
+  k_build_rhs<<<nck, 256, 0, s>>>(cg, v_.rhs, v_.q, v_.b, 2, halt);
   rc = kkt_solve(v_.rhs, v_.sol2);
   if (rc) return rc;
-  k_dots<<<kRedBlocks, kRedThreads, 0, s>>>(v_.qp, v_.sol2, n, v_.b, v_.sol2 + n, m, nullptr, nullptr, 0, v_.part,
-                                            S_D0, halt);
-  k_fin_const<<<1, 256, 0, s>>>(sc_, v_.part, halt);
+  DotArgs da{{v_.qp, v_.b, nullptr}, {v_.sol2, v_.sol2 + n, nullptr}, {1, 0, 0}, 2};
+  k_dots<<<nck, 256, 0, s>>>(cg, da, v_.part, S_D0, halt);
+  k_fin_const<<<(unsigned)B, 128, 0, s>>>(sc_, v_.part, pst_, v_.ckx_ptr, v_.ckz_ptr, halt);
   // ---- step 6: affine direction, d = (G, d_s = s, d_kappa = kappa tau) ----
   CLR_CUDA(cudaMemcpyAsync(v_.dsrhs, v_.s, sizeof(double) * (size_t)m, cudaMemcpyDeviceToDevice, s));
-  k_rhs<<<grid_for(N, 256), 256, 0, s>>>(v_.rhs, v_.G, v_.dsrhs, n, m, 0.0, sc_, 1, halt);
+  k_rhs<<<nck, 256, 0, s>>>(cg, v_.rhs, v_.G, v_.dsrhs, sc_, B, 1, halt);
   rc = direction(true);
   if (rc) return rc;
   // ---- steps 7-8: affine step length, sigma ----
   rc = step_length(false);
   if (rc) return rc;
   // ---- step 9: combined direction ----
-  rc = cones_combined_ds(s, cd_, v_.s, v_.xz + n, v_.dsa, v_.dir_a + n, &sc_->sigma_mu, v_.dsrhs, halt);
+  rc = cones_combined_ds(s, cd_, v_.s, v_.xz + n, v_.dsa, v_.dir_a + n, sc_, v_.dsrhs, halt);
   if (rc) return rc;
-  k_rhs<<<grid_for(N, 256), 256, 0, s>>>(v_.rhs, v_.G, v_.dsrhs, n, m, 0.0, sc_, 0, halt);
+  k_rhs<<<nck, 256, 0, s>>>(cg, v_.rhs, v_.G, v_.dsrhs, sc_, B, 0, halt);
   rc = direction(false);
   if (rc) return rc;
   // ---- step 10: combined step length with the neighbourhood check ----
   rc = step_length(true);
   if (rc) return rc;
   // ---- step 11: update ----
-  k_update<<<grid_for(N, 256), 256, 0, s>>>(v_.xz, v_.s, v_.dir, v_.ds, N, m, sc_, st.step_fraction, halt);
+  k_update<<<nck, 256, 0, s>>>(cg, v_.xz, v_.s, v_.dir, v_.ds, sc_, st.step_fraction, halt);
   const int* dh = (st.factor_bits == 64) ? f64_.dyn_hits : f32_.dyn_hits;
-  k_fin_update<<<1, 1, 0, s>>>(sc_, st.step_fraction, dh, halt);
+  k_fin_update<<<pg, 128, 0, s>>>(sc_, B, st.step_fraction, dh, halt);
   mark(5);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
 
 int Solver::initialise() {
-  const int64_t n = hp.n, m = hp.m, N = n + m;
+  const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   cudaStream_t s = stream_;
+  const ChunkGrid cg{v_.ck, nckx_, pst_, n};
+  const unsigned nck = (unsigned)(nckx_ + nckz_);
+  const int pg = grid_for(B, 128);
+  bool any_sym = false, any_nonsym = false;
+  for (const ProbConst& p : lay.pc) (p.sym ? any_sym : any_nonsym) = true;
   mark(0);
-  k_init_scal<<<1, 1, 0, s>>>(sc_);
+  k_init_scal<<<pg, 128, 0, s>>>(sc_, B, bf_);
   CLR_CUDA(cudaMemsetAsync(v_.xz, 0, sizeof(double) * (size_t)N, s));
   CLR_CUDA(cudaMemsetAsync(v_.s, 0, sizeof(double) * (size_t)m, s));
-  if (hp.cl.symmetric_only) {
+  if (any_sym) {
     int rc = cones_identity_H(s, cd_, nullptr);
     if (rc) return rc;
-    k_init_delta<<<1, 1, 0, s>>>(sc_, st.static_reg, st.static_reg_dyn, hp.maxPdiag);
+    k_init_delta<<<pg, 128, 0, s>>>(sc_, v_.pc, B, st.static_reg, st.static_reg_dyn);
     rc = factor();
     if (rc) return rc;
-    k_build_rhs_init<<<grid_for(N, 256), 256, 0, s>>>(v_.rhs, v_.q, v_.b, n, m, 0);
+    k_build_rhs<<<nck, 256, 0, s>>>(cg, v_.rhs, v_.q, v_.b, 0, nullptr);
     rc = kkt_solve(v_.rhs, v_.sol1);
     if (rc) return rc;
-    k_init_take<<<grid_for(N, 256), 256, 0, s>>>(v_.xz, v_.s, v_.sol1, n, m, 0);
-    k_build_rhs_init<<<grid_for(N, 256), 256, 0, s>>>(v_.rhs, v_.q, v_.b, n, m, 1);
+    k_init_take<<<nck, 256, 0, s>>>(cg, v_.xz, v_.s, v_.sol1, v_.pc, 0);
+    k_build_rhs<<<nck, 256, 0, s>>>(cg, v_.rhs, v_.q, v_.b, 1, nullptr);
     rc = kkt_solve(v_.rhs, v_.sol1);
     if (rc) return rc;
-    k_init_take<<<grid_for(N, 256), 256, 0, s>>>(v_.xz, v_.s, v_.sol1, n, m, 1);
-    rc = cones_shift_init(s, cd_, v_.s, v_.r, nullptr);
+    k_init_take<<<nck, 256, 0, s>>>(cg, v_.xz, v_.s, v_.sol1, v_.pc, 1);
+    rc = cones_shift_init(s, cd_, v_.s, sc_, nullptr);
     if (rc) return rc;
-    rc = cones_shift_init(s, cd_, v_.xz + n, v_.r, nullptr);
+    rc = cones_shift_init(s, cd_, v_.xz + n, sc_, nullptr);
     if (rc) return rc;
-  } else {
+  }
+  if (any_nonsym) {
     int rc = cones_unit_init(s, cd_, v_.s, nullptr);
     if (rc) return rc;
     rc = cones_init_shadow(s, cd_, nullptr);
@@ -975,7 +1211,7 @@ int Solver::initialise() {
     rc = cones_unit_init(s, cd_, v_.xz + n, nullptr);
     if (rc) return rc;
   }
-  k_init_scal<<<1, 1, 0, s>>>(sc_);  // tau = kappa = 1, counters reset (ir_total of the init dropped)
+  k_init_scal<<<pg, 128, 0, s>>>(sc_, B, bf_);  // tau = kappa = 1, counters reset (ir_total of the init dropped)
   mark(1);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -1030,47 +1266,119 @@ int Solver::launch_init() {
   return CLR_OK;
 }
 
-int Solver::solve() {
+int Solver::solve_begin() {
   if (!device_ready) return CLR_E_STATE;
-  auto t0 = std::chrono::steady_clock::now();
+  t_begin_ = now_s();
   perf = clr_perf{};
+  it_ = 0;
+  first_step_ = true;
   int rc = launch_init();
   if (rc) return rc;
   perf.kernel_launches += init_kernels_;
-  perf.factorizations += hp.cl.symmetric_only ? 1 : 0;
-  bool first = true;
-  int status = 0;
-  for (int it = 0; it <= st.max_iter + 1; ++it) {
-    rc = launch_iteration();
-    if (rc) return rc;
-    perf.kernel_launches += iter_kernels_;
-    CLR_CUDA(cudaMemcpyAsync(sc_host_, sc_, sizeof(IterScal), cudaMemcpyDeviceToHost, stream_));
-    CLR_CUDA(cudaStreamSynchronize(stream_));
-    float ms = 0.f;
-    if (first) {
-      if (cudaEventElapsedTime(&ms, ev_[0], ev_[1]) == cudaSuccess) perf.init_ms += ms;
-      first = false;
-    }
-    status = sc_host_->status;
-    if (status == 0 || status == CLR_INSUFFICIENT_PROGRESS) {
-      // a full iteration ran (or stopped at its step-length test, after the factorization)
-      if (cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) perf.resid_cones_ms += ms;
-      if (cudaEventElapsedTime(&ms, ev_[3], ev_[4]) == cudaSuccess) perf.factor_ms += ms;
-      if (cudaEventElapsedTime(&ms, ev_[4], ev_[5]) == cudaSuccess) perf.solve_step_ms += ms;
-      perf.factorizations += 1;
-    } else if (cudaEventElapsedTime(&ms, ev_[2], ev_[5]) == cudaSuccess) {
-      perf.resid_cones_ms += ms;  // the terminating pass only evaluates the residuals
-    }
-    if (status != 0) break;
+  bool any_sym = false;
+  for (const ProbConst& p : lay.pc) any_sym = any_sym || p.sym;
+  perf.factorizations += any_sym ? 1 : 0;
+  return CLR_OK;
+}
+
+int Solver::step_launch() {
+  int rc = launch_iteration();
+  if (rc) return rc;
+  perf.kernel_launches += iter_kernels_;
+  CLR_CUDA(cudaMemcpyAsync(sc_host_, sc_, sizeof(IterScal) * (size_t)lay.B, cudaMemcpyDeviceToHost, stream_));
+  CLR_CUDA(cudaMemcpyAsync(bf_host_, bf_, sizeof(BatchFlags), cudaMemcpyDeviceToHost, stream_));
+  CLR_CUDA(cudaEventRecord(step_ev_, stream_));
+  ++it_;
+  return CLR_OK;
+}
+
+int Solver::step_poll(bool* ready) {
+  cudaError_t e = cudaEventQuery(step_ev_);
+  if (e == cudaErrorNotReady) {
+    *ready = false;
+    return CLR_OK;
   }
-  perf.iterations = sc_host_->iter;
-  if (st.use_graph) perf.kernel_launches += (int64_t)sc_host_->ir_total * body_kernels_;  // executed loop bodies
-  perf.factor_flops = sy.flops;
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "cudaEventQuery");
+    return CLR_E_CUDA;
+  }
+  *ready = true;
+  return finish_step();
+}
+
+// bookkeeping once a launched step has finished
+int Solver::finish_step() {
+  float ms = 0.f;
+  if (first_step_) {
+    if (cudaEventElapsedTime(&ms, ev_[0], ev_[1]) == cudaSuccess) perf.init_ms += ms;
+    first_step_ = false;
+  }
+  // a full iteration ran unless every problem stopped at its residual stage
+  bool full = false;
+  for (int64_t p = 0; p < lay.B && !full; ++p) {
+    const int stt = sc_host_[p].status;
+    full = (stt == 0 || stt == CLR_INSUFFICIENT_PROGRESS);
+  }
+  if (full || !bf_host_->all_halt) {
+    if (cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) perf.resid_cones_ms += ms;
+    if (cudaEventElapsedTime(&ms, ev_[3], ev_[4]) == cudaSuccess) perf.factor_ms += ms;
+    if (cudaEventElapsedTime(&ms, ev_[4], ev_[5]) == cudaSuccess) perf.solve_step_ms += ms;
+    perf.factorizations += 1;
+  } else if (cudaEventElapsedTime(&ms, ev_[2], ev_[5]) == cudaSuccess) {
+    perf.resid_cones_ms += ms;  // the terminating pass only evaluates the residuals
+  }
+  return CLR_OK;
+}
+
+bool Solver::all_halted() const { return bf_host_->all_halt != 0 || it_ > st.max_iter + 1; }
+int Solver::problem_status(int64_t p) const { return sc_host_[p].status; }
+
+int Solver::solve_end() {
   CLR_CUDA(cudaStreamSynchronize(stream_));
-  solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  const IterScal& h = *sc_host_;
-  info = clr_info{};
-  info.status = status;
+  int iters = 0, irt = 0;
+  for (int64_t p = 0; p < lay.B; ++p) {
+    iters = std::max(iters, sc_host_[p].iter);
+    irt += sc_host_[p].ir_total;
+  }
+  perf.iterations = iters;
+  if (st.use_graph) perf.kernel_launches += (int64_t)irt * body_kernels_;  // executed loop bodies (upper bound)
+  perf.factor_flops = sy.flops;
+  solve_s = now_s() - t_begin_;
+  infos.assign(lay.B, clr_info{});
+  history.assign(lay.B, {});
+  std::vector<double> hall(12 * (size_t)hist_rows_ * (size_t)lay.B);
+  CLR_CUDA(cudaMemcpy(hall.data(), v_.hist, sizeof(double) * hall.size(), cudaMemcpyDeviceToHost));
+  for (int64_t p = 0; p < lay.B; ++p) {
+    const IterScal& h = sc_host_[p];
+    infos[p] = info_now(p);
+    infos[p].solve_s = solve_s;
+    const int rows = std::min(h.iter + 1, hist_rows_);
+    const double* src = hall.data() + 12 * (size_t)hist_rows_ * (size_t)p;
+    history[p].assign(src, src + 12 * (size_t)rows);
+  }
+  solved_once = true;
+  return CLR_OK;
+}
+
+int Solver::solve() {
+  int rc = solve_begin();
+  if (rc) return rc;
+  for (int it = 0; it <= st.max_iter + 1; ++it) {
+    rc = step_launch();
+    if (rc) return rc;
+    CLR_CUDA(cudaEventSynchronize(step_ev_));
+    bool ready = false;
+    rc = step_poll(&ready);
+    if (rc) return rc;
+    if (bf_host_->all_halt) break;
+  }
+  return solve_end();
+}
+
+clr_info Solver::info_now(int64_t p) const {
+  const IterScal& h = sc_host_[p];
+  clr_info info{};
+  info.status = h.status;
   info.iterations = h.iter;
   info.ir_steps_total = h.ir_total;
   info.dyn_reg_hits = h.dyn_hits;
@@ -1084,46 +1392,68 @@ int Solver::solve() {
   info.tau = h.tau;
   info.kappa = h.kappa;
   info.setup_s = setup_s;
-  info.solve_s = solve_s;
-  const int rows = std::min(h.iter + 1, st.max_iter + 1);
-  history.assign(12 * (size_t)rows, 0.0);
-  CLR_CUDA(cudaMemcpy(history.data(), v_.hist, sizeof(double) * history.size(), cudaMemcpyDeviceToHost));
-  solved_once = true;
-  last_status = status;
-  return CLR_OK;
+  info.solve_s = now_s() - t_begin_;
+  return info;
 }
 
-int Solver::get_solution(double* x, double* sl, double* z, clr_info* out) {
+int Solver::get_solution_now(int64_t p, double* x, double* sl, double* z, clr_info* out) {
+  if (p < 0 || p >= lay.B) return CLR_E_INVALID;
+  if (infos.size() != (size_t)lay.B) infos.assign(lay.B, clr_info{});
+  infos[p] = info_now(p);
+  return unscale_solution(p, x, sl, z, out);
+}
+
+int Solver::get_solution(int64_t p, double* x, double* sl, double* z, clr_info* out) {
   if (!solved_once) return CLR_E_STATE;
-  const int64_t n = hp.n, m = hp.m;
-  std::vector<double> xz(n + m), s(m);
-  CLR_CUDA(cudaMemcpy(xz.data(), v_.xz, sizeof(double) * (size_t)(n + m), cudaMemcpyDeviceToHost));
-  CLR_CUDA(cudaMemcpy(s.data(), v_.s, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost));
-  const double tau = info.tau, c = hp.c;
+  if (p < 0 || p >= lay.B) return CLR_E_INVALID;
+  return unscale_solution(p, x, sl, z, out);
+}
+
+int Solver::unscale_solution(int64_t p, double* x, double* sl, double* z, clr_info* out) {
+  const HostProblem& pr = probs[p];
+  const int64_t n = pr.n, m = pr.m, N = hp.n + hp.m;
+  (void)N;
+  std::vector<double> xs(n), zs(m), ss(m);
+  if (n) CLR_CUDA(cudaMemcpy(xs.data(), v_.xz + lay.xo[p], sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
+  if (m) {
+    // the problem's rows sit in up to six family runs of the cohort rows
+    const std::vector<int64_t>& zr = lay.zrow[p];
+    int64_t r = 0;
+    while (r < m) {
+      int64_t e = r + 1;
+      while (e < m && zr[e] == zr[e - 1] + 1) ++e;
+      CLR_CUDA(cudaMemcpy(zs.data() + r, v_.xz + hp.n + zr[r], sizeof(double) * (size_t)(e - r),
+                          cudaMemcpyDeviceToHost));
+      CLR_CUDA(cudaMemcpy(ss.data() + r, v_.s + zr[r], sizeof(double) * (size_t)(e - r), cudaMemcpyDeviceToHost));
+      r = e;
+    }
+  }
+  const clr_info& info = infos[p];
+  const double tau = info.tau, c = pr.c;
   // unscale: x = D x^, s = s^ / E, z = E z^ / c
   std::vector<double> xu(n), su(m), zu(m);
-  for (int64_t j = 0; j < n; ++j) xu[j] = hp.D[j] * xz[j];
+  for (int64_t j = 0; j < n; ++j) xu[j] = pr.D[j] * xs[j];
   for (int64_t r = 0; r < m; ++r) {
-    su[r] = s[r] / hp.E[r];
-    zu[r] = hp.E[r] * xz[n + r] / c;
+    su[r] = ss[r] / pr.E[r];
+    zu[r] = pr.E[r] * zs[r] / c;
   }
   double fx = 1.0 / tau, fs = 1.0 / tau, fz = 1.0 / tau;
   const double nan = std::nan("");
-  if (last_status == CLR_PRIMAL_INFEASIBLE) {
+  if (info.status == CLR_PRIMAL_INFEASIBLE) {
     double btz = 0;
-    for (int64_t r = 0; r < m; ++r) btz += (hp.b[r] / hp.E[r]) * zu[r];
+    for (int64_t r = 0; r < m; ++r) btz += (pr.b[r] / pr.E[r]) * zu[r];
     fx = fs = nan;
     fz = -1.0 / btz;
-  } else if (last_status == CLR_DUAL_INFEASIBLE) {
+  } else if (info.status == CLR_DUAL_INFEASIBLE) {
     double qtx = 0;
-    for (int64_t j = 0; j < n; ++j) qtx += (hp.q[j] / (c * hp.D[j])) * xu[j];
+    for (int64_t j = 0; j < n; ++j) qtx += (pr.q[j] / (c * pr.D[j])) * xu[j];
     fx = fs = -1.0 / qtx;
     fz = nan;
   }
   if (x)
     for (int64_t j = 0; j < n; ++j) x[j] = xu[j] * fx;
   for (int64_t r = 0; r < m; ++r) {
-    const int64_t orig = hp.row_perm[r];
+    const int64_t orig = pr.row_perm[r];
     if (sl) sl[orig] = su[r] * fs;
     if (z) z[orig] = zu[r] * fz;
   }
@@ -1131,12 +1461,20 @@ int Solver::get_solution(double* x, double* sl, double* z, clr_info* out) {
   return CLR_OK;
 }
 
-int Solver::update_qb(const double* q, const double* b) {
-  int rc = set_qb(hp, q, b);
+int Solver::update_qb(int64_t p, const double* q, const double* b) {
+  if (p < 0 || p >= lay.B) return CLR_E_INVALID;
+  HostProblem& pr = probs[p];
+  int rc = set_qb(pr, q, b);
   if (rc) return rc;
+  for (int64_t j = 0; j < pr.n; ++j) hp.q[lay.xo[p] + j] = pr.q[j];
+  for (int64_t r = 0; r < pr.m; ++r) hp.b[lay.zrow[p][r]] = pr.b[r];
+  lay.pc[p].bnorm = pr.bnorm;
+  lay.pc[p].qnorm = pr.qnorm;
   if (device_ready) {
     CLR_CUDA(cudaMemcpyAsync(v_.q, hp.q.data(), sizeof(double) * (size_t)hp.n, cudaMemcpyHostToDevice, stream_));
     CLR_CUDA(cudaMemcpyAsync(v_.b, hp.b.data(), sizeof(double) * (size_t)hp.m, cudaMemcpyHostToDevice, stream_));
+    CLR_CUDA(cudaMemcpyAsync(v_.pc, lay.pc.data(), sizeof(ProbConst) * (size_t)lay.B, cudaMemcpyHostToDevice,
+                             stream_));
     CLR_CUDA(cudaStreamSynchronize(stream_));
   }
   return CLR_OK;

@@ -1,5 +1,7 @@
 // The per-iteration device step of Algorithm 1 and the solver object behind
-// the C ABI.
+// the C ABI.  One Solver holds a cohort of B >= 1 independent problems merged
+// block-diagonally: one captured CUDA graph per iteration advances all of
+// them, and every scalar of the method is kept per problem.
 #pragma once
 
 #include <memory>
@@ -10,34 +12,8 @@
 #include "device.cuh"
 #include "internal.h"
 #include "ldl.cuh"
+#include "scal.cuh"
 #include "symbolic.h"
-
-// Scalars shared by the kernels of one iteration (device memory).
-struct IterScal {
-  double tau, kappa;
-  // residual stage (scaled quantities unless noted)
-  double mu, pcost, dcost, res_p, res_d, gap_abs, gap_rel;  // pcost..gap unscaled
-  double xPx, qx, bz, sz, G3;
-  int status, iter, halt, pad0;
-  // regularisation
-  unsigned long long hmax_bits;
-  double delta;
-  // constant-RHS part of Delta tau
-  double qp_dx2, b_dz2;
-  // current direction
-  double d_tau, d_kap, dtau, dkap;
-  double dtau_a, dkap_a;
-  // step length
-  unsigned long long amin_bits;
-  clr::NonsymStep ns;
-  double alpha_sym, alpha_a, alpha_c, sigma, sigma_mu;
-  double mu_coef[3];
-  // iterative refinement
-  int ir_skip, ir_steps, ir_total, ir_cur;
-  double rhs_norm, ir_prev;
-  unsigned long long rnorm_bits;
-  int dyn_hits, pad1;
-};
 
 namespace clr {
 
@@ -51,37 +27,61 @@ struct VecDev {
   double *dir, *ds;          // current / combined direction
   double *dsrhs;             // d_s of the current right-hand side (m)
   double *r, *solb;          // refinement residual and accumulated solution (N)
-  double *part;              // reduction partials
-  double *hist;              // history rows
+  double *part;              // chunk partial sums (S_NSLOT x pst)
+  unsigned long long* maxb;  // residual-stage maxima (8 per problem)
+  double *hist;              // history rows (per problem)
   double *q, *b, *D, *E;     // scaled data and scalings
   double *kval;              // KKT values (x part constant, z part = -H)
   int64_t *kptr;             // full-K CSR (both triangles), values through kvi
   int32_t *kcol, *kvi;
+  int32_t* pid;              // KKT index -> problem
+  Chunk* ck;                 // x chunks then z chunks (z begins are row indices)
+  int64_t *ckx_ptr, *ckz_ptr;
+  ProbConst* pc;
 };
 
 class Solver {
  public:
   clr_settings st{};
-  HostProblem hp;
+  std::vector<HostProblem> probs;  // per problem (small arrays kept: row order, scalings, q, b)
+  HostProblem hp;                  // the cohort problem
+  CohortLayout lay;
   Symbolic sy;
   NumericMaps mp;
   bool device_ready = false;
   bool solved_once = false;
   double setup_s = 0, solve_s = 0;
-  int last_status = 0, last_iters = 0;
-  clr_info info{};
   clr_perf perf{};
-  std::vector<double> history;  // rows of 12
+  std::vector<clr_info> infos;          // per problem, after a solve
+  std::vector<std::vector<double>> history;  // per problem, rows of 12
   std::string err;
 
   ~Solver();
+  // One problem.
   int analyze(const clr_csc* P, const double* q, const clr_csc* A, const double* b, const clr_cone* cones,
               int32_t ncones, const clr_settings& s);
+  // A cohort from problems already through build_problem (moved in) with their orders.
+  int analyze_cohort(std::vector<HostProblem>&& ps, const std::vector<std::vector<int64_t>>& orders,
+                     const clr_settings& s);
   int upload();
   int solve();
-  int get_solution(double* x, double* s, double* z, clr_info* out);
-  int update_qb(const double* q, const double* b);
+  // Asynchronous driving (serving): begin, then step until step_poll says done.
+  int solve_begin();
+  int step_launch();           // one iteration + status copy to pinned memory, no wait
+  int step_poll(bool* ready);  // has the last launched step finished?
+  bool all_halted() const;     // valid after a step finished
+  int problem_status(int64_t p) const;  // from the last finished step
+  int solve_end();
+  int get_solution(int64_t p, double* x, double* s, double* z, clr_info* out);
+  // Problem p as of the last finished step (it must have stopped; used to hand
+  // out results while the rest of the cohort goes on).
+  int get_solution_now(int64_t p, double* x, double* s, double* z, clr_info* out);
+  // Build on caller-owned `stream` with stream-ordered device memory (before upload).
+  int use_stream_ordered(cudaStream_t stream);
+  int update_qb(int64_t p, const double* q, const double* b);
   int set_stream(void* stream);
+  size_t device_bytes() const { return ar_.bytes(); }
+  int64_t nprob() const { return lay.B; }
 
  private:
   DeviceArena ar_;
@@ -92,8 +92,12 @@ class Solver {
   LdlFactor<float> f32_;
   ConeDev cd_;
   VecDev v_{};
-  IterScal* sc_ = nullptr;       // device
-  IterScal* sc_host_ = nullptr;  // pinned
+  IterScal* sc_ = nullptr;        // device, B entries
+  IterScal* sc_host_ = nullptr;   // pinned, B entries
+  BatchFlags* bf_ = nullptr;      // device
+  BatchFlags* bf_host_ = nullptr; // pinned
+  int64_t nckx_ = 0, nckz_ = 0, pst_ = 1;
+  int hist_rows_ = 0;
   int csr_group_ = 32;
   cudaGraph_t graph_ = nullptr;
   cudaGraphExec_t gexec_ = nullptr;
@@ -103,9 +107,17 @@ class Solver {
   cudaStream_t body_stream_ = nullptr;
   std::vector<cudaGraph_t> ir_nodes_;  // refinement loop bodies captured in the current graph
   cudaEvent_t ev_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t step_ev_ = nullptr;
+  // asynchronous solve state
+  int it_ = 0;
+  bool first_step_ = true;
+  double t_begin_ = 0;
   void mark(int i);
   void drop_graphs();
   int launch_init();
+  int finish_step();
+  clr_info info_now(int64_t p) const;
+  int unscale_solution(int64_t p, double* x, double* s, double* z, clr_info* out);
 
   int factor();
   int kkt_solve(const double* rhs, double* sol);

@@ -30,11 +30,10 @@ __global__ void k_scatter_kval(T* __restrict__ F, const double* __restrict__ kva
 
 template <typename T>
 __global__ void k_add_reg(T* __restrict__ F, const int64_t* __restrict__ diag_pos, const int8_t* __restrict__ dsign,
-                          int64_t N, const double* delta, const int* skip) {
+                          const int32_t* __restrict__ pos_pid, int64_t N, const IterScal* sc, const int* skip) {
   if (skip && *skip) return;
-  const double d = *delta;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-    F[diag_pos[k]] += (T)(dsign[k] * d);
+    F[diag_pos[k]] += (T)(dsign[k] * sc[pos_pid[k]].delta);
 }
 
 template <typename T>
@@ -203,7 +202,7 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
 }  // namespace
 
 int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps& mp, const std::vector<int8_t>& dsign,
-                         int small_max, LdlStructure& st) {
+                         int small_max, LdlStructure& st, const std::vector<int32_t>* pos_pid) {
   st.N = sy.N;
   st.nsn = sy.nsn;
   st.nlev = sy.nlev;
@@ -339,6 +338,11 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
   st.rows_kkt = up(ar, mp.rows_kkt);
   st.w_init = up(ar, w_init);
   st.dsign = up(ar, dsign);
+  {
+    std::vector<int32_t> zeros;
+    if (!pos_pid) zeros.assign(sy.N, 0);
+    st.pos_pid = up(ar, pos_pid ? *pos_pid : zeros);
+  }
   st.kdest = up(ar, mp.kdest);
   st.diag_pos = up(ar, mp.diag_pos);
   st.fa_tgt = up(ar, mp.fa_tgt);
@@ -348,7 +352,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
   st.sv_ptr = up(ar, mp.sv_ptr);
   st.sv_src = up(ar, mp.sv_src);
   if (!st.sn_ptr || !st.row_ptr || !st.front_off || !st.upd_off || !st.lev_sn || !st.rows_kkt || !st.w_init ||
-      !st.dsign || !st.kdest || !st.diag_pos || !st.fa_tgt || !st.fa_ptr || !st.fa_src || !st.sv_tgt ||
+      !st.dsign || !st.pos_pid || !st.kdest || !st.diag_pos || !st.fa_tgt || !st.fa_ptr || !st.fa_src || !st.sv_tgt ||
       !st.sv_ptr || !st.sv_src)
     return CLR_E_OOM;
   return CLR_OK;
@@ -376,14 +380,14 @@ int LdlFactor<T>::alloc(DeviceArena& ar, const LdlStructure& st) {
 }
 
 template <typename T>
-int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const double* delta, double dyn_eps, double dyn_delta,
+int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* sc, double dyn_eps, double dyn_delta,
                          const int* skip) const {
   const LdlStructure& S = *s;
   CLR_CUDA(cudaMemsetAsync(dyn_hits, 0, sizeof(int), stm));
   CLR_CUDA(cudaMemsetAsync(F, 0, sizeof(T) * (size_t)S.pool, stm));
   if (S.bfd.epool > 0) CLR_CUDA(cudaMemsetAsync(E, 0, sizeof(T) * (size_t)S.bfd.epool, stm));
   k_scatter_kval<T><<<grid_for(S.nk, 256), 256, 0, stm>>>(F, kval, S.kdest, S.nk, skip);
-  k_add_reg<T><<<grid_for(S.N, 256), 256, 0, stm>>>(F, S.diag_pos, S.dsign, S.N, delta, skip);
+  k_add_reg<T><<<grid_for(S.N, 256), 256, 0, stm>>>(F, S.diag_pos, S.dsign, S.pos_pid, S.N, sc, skip);
   CLR_CHECK_LAUNCH();
   for (int64_t l = 0; l < S.nlev; ++l) {
     const int64_t t0 = S.h_fa_lev_ptr[l], t1 = S.h_fa_lev_ptr[l + 1];

@@ -8,6 +8,7 @@
 #include "bigfront.cuh"
 #include "device.cuh"
 #include "internal.h"
+#include "scal.cuh"
 #include "symbolic.h"
 
 namespace clr {
@@ -20,6 +21,7 @@ struct LdlStructure {
   int32_t* rows_kkt = nullptr;
   int32_t* w_init = nullptr;   // solve slot -> KKT index of the right-hand side, or -1
   int8_t* dsign = nullptr;     // expected pivot sign by position
+  int32_t* pos_pid = nullptr;  // problem of each elimination position (cohorts)
   int64_t *kdest = nullptr, *diag_pos = nullptr;
   int64_t *fa_tgt = nullptr, *fa_ptr = nullptr, *fa_src = nullptr;
   int64_t *sv_tgt = nullptr, *sv_ptr = nullptr, *sv_src = nullptr;
@@ -34,8 +36,9 @@ struct LdlStructure {
   int64_t max_front = 0;
 };
 
+// pos_pid: problem of each elimination position (null: one problem).
 int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps& mp, const std::vector<int8_t>& dsign,
-                         int small_max, LdlStructure& st);
+                         int small_max, LdlStructure& st, const std::vector<int32_t>* pos_pid = nullptr);
 
 template <typename T>
 struct LdlFactor {
@@ -50,8 +53,9 @@ struct LdlFactor {
   int* dyn_hits = nullptr;
   int alloc(DeviceArena& ar, const LdlStructure& st);
   // Factor K: kval (FP64, lower triangle entries in kval order) scattered into
-  // the fronts, +/- (*delta) added on the diagonal (x rows +, z rows -).
-  int factor(cudaStream_t st, const double* kval, const double* delta, double dyn_eps, double dyn_delta,
+  // the fronts, +/- delta added on the diagonal (x rows +, z rows -), with
+  // delta = sc[p].delta of the position's problem p.
+  int factor(cudaStream_t st, const double* kval, const IterScal* sc, double dyn_eps, double dyn_delta,
              const int* skip) const;
   // xs = (L D L^T)^{-1} rhs (rhs FP64 in KKT order).
   int solve(cudaStream_t st, const double* rhs, const int* skip) const;

@@ -25,6 +25,7 @@ struct ConeBench {
   std::vector<int64_t> caller_off;      // caller cone -> first caller row
   int64_t m = 0;
   int rc = CLR_OK;
+  IterScal* sc = nullptr;  // the per-problem scalars of the single problem
 
   ConeBench(const clr_cone* cones, int32_t ncones) {
     int64_t total = 0;
@@ -113,8 +114,16 @@ struct ConeBench {
     cd.psd_lam = ar.alloc_n<double>(cd.n_psd * psd_k);
     cd.ep_zt = ar.alloc_n<double>(3 * (cd.n_exp + cd.n_pow));
     exp_central_point_host(cd.exp_center);
+    // one problem: every row belongs to problem 0
+    std::vector<int32_t> pid(m, 0);
+    ProbConst pc{};
+    pc.sym = (cd.n_exp + cd.n_pow) == 0 ? 1 : 0;
+    cd.nprob = 1;
+    cd.row_pid = ar.upload(pid.data(), m);
+    cd.pc = ar.upload(&pc, 1);
+    sc = ar.alloc_n<IterScal>(1);
     if (cones_init_shadow(nullptr, cd, nullptr) != CLR_OK) rc = CLR_E_CUDA;
-    if (!cd.kvz || !cd.scratch || !cd.soc_wb) rc = CLR_E_OOM;
+    if (!cd.kvz || !cd.scratch || !cd.soc_wb || !cd.row_pid || !cd.pc || !sc) rc = CLR_E_OOM;
   }
 
   double* upload_perm(const double* v) {
@@ -146,10 +155,11 @@ int clr_cones_scaling(const clr_cone* cones, int32_t ncones, const double* s, co
   if (!s || !z) return CLR_E_INVALID;
   double* ds = cb.upload_perm(s);
   double* dz = cb.upload_perm(z);
-  double* dmu = cb.ar.upload(&mu, 1);
-  unsigned long long* hb = cb.ar.alloc_n<unsigned long long>(1);
-  if (!ds || !dz || !dmu || !hb) return CLR_E_OOM;
-  int rc = cones_scaling(nullptr, cb.cd, ds, dz, dmu, hb, nullptr);
+  if (!ds || !dz) return CLR_E_OOM;
+  IterScal h{};
+  h.mu = mu;
+  CLR_CUDA(cudaMemcpy(cb.sc, &h, sizeof(IterScal), cudaMemcpyHostToDevice));
+  int rc = cones_scaling(nullptr, cb.cd, ds, dz, cb.sc, nullptr);
   if (rc) return rc;
   std::vector<double> kv(cb.cd.nkz);
   CLR_CUDA(cudaDeviceSynchronize());
@@ -188,30 +198,24 @@ int clr_cones_step_length(const clr_cone* cones, int32_t ncones, const double* s
     return CLR_OK;
   }
   double *d_s = cb.upload_perm(s), *d_z = cb.upload_perm(z), *d_ds = cb.upload_perm(ds), *d_dz = cb.upload_perm(dz);
-  unsigned long long* amin = cb.ar.alloc_n<unsigned long long>(2);
-  double* a0 = cb.ar.alloc_n<double>(1);
-  double* coef = cb.ar.alloc_n<double>(3);
-  NonsymStep* ns = cb.ar.alloc_n<NonsymStep>(1);
-  if (!d_s || !d_z || !d_ds || !d_dz || !amin || !a0 || !coef || !ns) return CLR_E_OOM;
+  if (!d_s || !d_z || !d_ds || !d_dz) return CLR_E_OOM;
+  IterScal h{};
   const double inf = INFINITY;
-  unsigned long long init[2];
-  std::memcpy(&init[0], &inf, 8);
-  init[1] = ~0ull;
-  CLR_CUDA(cudaMemcpy(amin, init, 16, cudaMemcpyHostToDevice));
-  int rc = cones_step_symmetric(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, amin, nullptr);
+  std::memcpy(&h.amin_bits, &inf, 8);
+  CLR_CUDA(cudaMemcpy(cb.sc, &h, sizeof(IterScal), cudaMemcpyHostToDevice));
+  int rc = cones_step_symmetric(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, cb.sc, nullptr);
   if (rc) return rc;
-  unsigned long long hb[2];
-  CLR_CUDA(cudaMemcpy(hb, amin, 16, cudaMemcpyDeviceToHost));
+  CLR_CUDA(cudaMemcpy(&h, cb.sc, sizeof(IterScal), cudaMemcpyDeviceToHost));
   double amin_v;
-  std::memcpy(&amin_v, &hb[0], 8);
+  std::memcpy(&amin_v, &h.amin_bits, 8);
   double a = std::min(alpha_max, amin_v);
   if (cb.cd.n_exp + cb.cd.n_pow > 0) {
-    CLR_CUDA(cudaMemcpy(a0, &a, 8, cudaMemcpyHostToDevice));
-    rc = cones_step_nonsym(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, a0, 0.8, 0, 1e-6, coef, ns, nullptr);
+    h.alpha_sym = a;
+    CLR_CUDA(cudaMemcpy(cb.sc, &h, sizeof(IterScal), cudaMemcpyHostToDevice));
+    rc = cones_step_nonsym(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, cb.sc, 0.8, 0, 1e-6, nullptr);
     if (rc) return rc;
-    NonsymStep h;
-    CLR_CUDA(cudaMemcpy(&h, ns, sizeof(NonsymStep), cudaMemcpyDeviceToHost));
-    a = a * std::pow(0.8, (double)h.jint);
+    CLR_CUDA(cudaMemcpy(&h, cb.sc, sizeof(IterScal), cudaMemcpyDeviceToHost));
+    a = a * std::pow(0.8, (double)h.ns.jint);
   }
   *alpha_out = a;
   return CLR_OK;
@@ -225,15 +229,15 @@ int clr_cones_combined_ds(const clr_cone* cones, int32_t ncones, const double* s
   if (cb.m == 0) return CLR_OK;
   double *d_s = cb.upload_perm(s), *d_z = cb.upload_perm(z), *d_dsa = cb.upload_perm(ds_a),
          *d_dza = cb.upload_perm(dz_a);
-  double one = 1.0;
-  double* dmu = cb.ar.upload(&one, 1);
-  double* dsm = cb.ar.upload(&sigma_mu, 1);
   double* out = cb.ar.alloc_n<double>(cb.m);
-  unsigned long long* hb = cb.ar.alloc_n<unsigned long long>(1);
-  if (!d_s || !d_z || !d_dsa || !d_dza || !dmu || !dsm || !out || !hb) return CLR_E_OOM;
-  int rc = cones_scaling(nullptr, cb.cd, d_s, d_z, dmu, hb, nullptr);
+  if (!d_s || !d_z || !d_dsa || !d_dza || !out) return CLR_E_OOM;
+  IterScal h{};
+  h.mu = 1.0;
+  h.sigma_mu = sigma_mu;
+  CLR_CUDA(cudaMemcpy(cb.sc, &h, sizeof(IterScal), cudaMemcpyHostToDevice));
+  int rc = cones_scaling(nullptr, cb.cd, d_s, d_z, cb.sc, nullptr);
   if (rc) return rc;
-  rc = cones_combined_ds(nullptr, cb.cd, d_s, d_z, d_dsa, d_dza, dsm, out, nullptr);
+  rc = cones_combined_ds(nullptr, cb.cd, d_s, d_z, d_dsa, d_dza, cb.sc, out, nullptr);
   if (rc) return rc;
   CLR_CUDA(cudaDeviceSynchronize());
   return cb.download_unperm(out, ds_out);
@@ -272,8 +276,8 @@ int clr_ldl_solve(const clr_csc* K, const double* signs, const int64_t* order, i
   if (rc) return rc;
   double* kv = ar.upload(K->val, K->nnz);
   double* drhs = ar.upload(rhs, N);
-  double zero = 0.0;
-  double* ddelta = ar.upload(&zero, 1);
+  IterScal hsc{};  // delta = 0: K is factored as given
+  IterScal* ddelta = ar.upload(&hsc, 1);
   if (!kv || !drhs || !ddelta) return CLR_E_OOM;
   std::vector<double> xs(N), Dpos(N);
   int hits = 0;

@@ -15,11 +15,10 @@
 
 namespace clr {
 
-int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
-                     const std::vector<int64_t>* user_order, Symbolic& sy) {
-  sy = Symbolic();
-  sy.N = N;
-  // ---- symmetric adjacency for the ordering ----
+namespace {
+// Symmetric adjacency (no diagonal) of the matrix whose lower triangle is given as CSC.
+void build_adjacency(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                     std::vector<int64_t>& aptr, std::vector<int64_t>& aidx) {
   std::vector<int64_t> deg(N, 0);
   for (int64_t j = 0; j < N; ++j)
     for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
@@ -28,19 +27,34 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
       deg[i]++;
       deg[j]++;
     }
-  std::vector<int64_t> aptr(N + 1, 0);
+  aptr.assign(N + 1, 0);
   for (int64_t i = 0; i < N; ++i) aptr[i + 1] = aptr[i] + deg[i];
-  std::vector<int64_t> aidx(aptr[N]);
-  {
-    std::vector<int64_t> next(aptr.begin(), aptr.end() - 1);
-    for (int64_t j = 0; j < N; ++j)
-      for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
-        int64_t i = rowidx[p];
-        if (i == j) continue;
-        aidx[next[i]++] = j;
-        aidx[next[j]++] = i;
-      }
-  }
+  aidx.assign(aptr[N], 0);
+  std::vector<int64_t> next(aptr.begin(), aptr.end() - 1);
+  for (int64_t j = 0; j < N; ++j)
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+      int64_t i = rowidx[p];
+      if (i == j) continue;
+      aidx[next[i]++] = j;
+      aidx[next[j]++] = i;
+    }
+}
+}  // namespace
+
+void kkt_amd_order(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                   std::vector<int64_t>& order, int64_t& n_dense) {
+  std::vector<int64_t> aptr, aidx;
+  build_adjacency(N, colptr, rowidx, aptr, aidx);
+  amd_order(N, aptr, aidx, order, n_dense);
+}
+
+int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                     const std::vector<int64_t>* user_order, Symbolic& sy) {
+  sy = Symbolic();
+  sy.N = N;
+  // ---- symmetric adjacency for the ordering ----
+  std::vector<int64_t> aptr, aidx;
+  build_adjacency(N, colptr, rowidx, aptr, aidx);
   std::vector<int64_t> order;
   if (user_order) {
     order = *user_order;

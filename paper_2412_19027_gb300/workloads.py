@@ -250,33 +250,38 @@ def mpc_qp(seed=0, T=None, nx=None, nu=None, x_bound=5.0, u_bound=1.0, u_soc=1.2
     Bd = rng.standard_normal((nx, nu))
     x0 = rng.standard_normal(nx) * x0_scale
     n = T * (nx + nu)
-    xi = lambda t: t * nx                      # x_{t+1} block offset, t = 0..T-1
-    ui = lambda t: T * nx + t * nu              # u_t block offset
-    rows, cols, vals, b = [], [], [], []
-    r = 0
-    for t in range(T):                          # x_{t+1} - A_d x_t - B_d u_t = 0
-        for i in range(nx):
-            rows.append(r); cols.append(xi(t) + i); vals.append(1.0)
-            if t > 0:
-                for k in range(nx):
-                    rows.append(r); cols.append(xi(t - 1) + k); vals.append(-Ad[i, k])
-            for k in range(nu):
-                rows.append(r); cols.append(ui(t) + k); vals.append(-Bd[i, k])
-            b.append(Ad[i] @ x0 if t == 0 else 0.0)
-            r += 1
-    n_zero = r
-    for j in range(n):                          # boxes: v <= ub, -v <= ub
-        ub = x_bound if j < T * nx else u_bound
-        rows += [r, r + 1]; cols += [j, j]; vals += [1.0, -1.0]; b += [ub, ub]
-        r += 2
-    n_nn = r - n_zero
-    for t in range(T):                          # (u_soc, u_t) in SOC
-        b.append(u_soc)
-        r += 1
-        for k in range(nu):
-            rows.append(r); cols.append(ui(t) + k); vals.append(-1.0); b.append(0.0)
-            r += 1
-    m = r
+    n_zero = T * nx
+    # dynamics rows r = t nx + i: x_{t+1,i} - sum_k A_d[i,k] x_{t,k} - sum_k B_d[i,k] u_{t,k} = (A_d x0)_i if t == 0
+    t_i, i_i = np.divmod(np.arange(n_zero), nx)
+    r_id, c_id, v_id = np.arange(n_zero), np.arange(n_zero), np.ones(n_zero)
+    ta = np.repeat(np.arange(1, T), nx * nx)
+    ia = np.tile(np.repeat(np.arange(nx), nx), T - 1)
+    ka = np.tile(np.tile(np.arange(nx), nx), T - 1)
+    r_a, c_a, v_a = ta * nx + ia, (ta - 1) * nx + ka, -Ad[ia, ka]
+    tb = np.repeat(np.arange(T), nx * nu)
+    ib = np.tile(np.repeat(np.arange(nx), nu), T)
+    kb = np.tile(np.tile(np.arange(nu), nx), T)
+    r_b, c_b, v_b = tb * nx + ib, T * nx + tb * nu + kb, -Bd[ib, kb]
+    ax0 = np.array([Ad[i] @ x0 for i in range(nx)])
+    b_dyn = np.where(t_i == 0, ax0[i_i], 0.0)
+    # boxes |v_j| <= ub: rows n_zero + 2j (v_j <= ub) and n_zero + 2j + 1 (-v_j <= ub)
+    j = np.arange(n)
+    ub = np.where(j < T * nx, x_bound, u_bound)
+    r_box, c_box, v_box = n_zero + np.r_[2 * j, 2 * j + 1], np.r_[j, j], np.r_[np.ones(n), -np.ones(n)]
+    b_box = np.repeat(ub, 2)
+    n_nn = 2 * n
+    # one SOC per step: (u_soc, u_t) in SOC(nu + 1)
+    ts = np.repeat(np.arange(T), nu)
+    ks = np.tile(np.arange(nu), T)
+    r0 = n_zero + n_nn
+    r_soc, c_soc, v_soc = r0 + ts * (nu + 1) + 1 + ks, T * nx + ts * nu + ks, -np.ones(T * nu)
+    b_soc = np.zeros(T * (nu + 1))
+    b_soc[:: nu + 1] = u_soc
+    rows = np.r_[r_id, r_a, r_b, r_box, r_soc]
+    cols = np.r_[c_id, c_a, c_b, c_box, c_soc]
+    vals = np.r_[v_id, v_a, v_b, v_box, v_soc]
+    b = np.r_[b_dyn, b_box, b_soc]
+    m = r0 + T * (nu + 1)
     A = sp.csc_matrix((vals, (rows, cols)), shape=(m, n))
     pd = np.r_[np.full(T * nx, 2.0), np.full(T * nu, 0.2)]
     cones = [(ZERO, n_zero, 0.0), (NONNEG, n_nn, 0.0)] + [(SOC, nu + 1, 0.0)] * T

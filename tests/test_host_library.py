@@ -174,3 +174,38 @@ def test_analysis_of_full_size_mixed_cone_problem(clr):
     assert st["max_front"] == 2000
     assert st["n_levels"] <= 8
     assert st["front_pool_entries"] < 10_000_000
+
+
+def _cohort_members():
+    return [W.nonneg_qp(0), W.mpc_qp(1, T=12, nx=5, nu=3),
+            W.mixed_cone(1, n=60, n_zero=10, n_nonneg=80, n_soc=12, n_exp=8, n_pow=8, nnz_per_col=4),
+            W.psd_batch(0, n=60, n_psd=4, psd_k=4, n_nonneg=20, nnz_per_col=4), W.mpc_qp(2, T=20, nx=8, nu=2)]
+
+
+def test_cohort_analysis_is_the_union_of_its_members(clr):
+    """A merged cohort is block diagonal under the concatenated orders: its
+    symbolic factorization is the disjoint union of the members' own (sizes,
+    fill and flops add up, the level count is the largest member's)."""
+    probs = _cohort_members()
+    alone = []
+    for p in probs:
+        s = clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones)
+        alone.append(s.symbolic_stats())
+        s.free()
+    b = clr.clr_batch_analyze([(p.P, p.q, p.A, p.b, p.cones) for p in probs])
+    assert b.size() == len(probs)
+    st = b.symbolic_stats()
+    for key in ("n", "m", "kkt_dim", "kkt_nnz_lower", "l_nnz", "n_supernodes", "front_pool_entries"):
+        assert st[key] == sum(a[key] for a in alone), key
+    assert st["factor_flops"] == pytest.approx(sum(a["factor_flops"] for a in alone), rel=1e-12)
+    assert st["n_levels"] == max(a["n_levels"] for a in alone)
+    assert st["max_front"] == max(a["max_front"] for a in alone)
+    b.free()
+
+
+def test_cohort_rejects_mixed_psd_orders(clr):
+    p4 = W.psd_batch(0, n=60, n_psd=4, psd_k=4, n_nonneg=20, nnz_per_col=4)
+    p5 = W.psd_batch(1, n=60, n_psd=3, psd_k=5, n_nonneg=20, nnz_per_col=4)
+    with pytest.raises(clr.ClrError) as e:
+        clr.clr_batch_analyze([(p.P, p.q, p.A, p.b, p.cones) for p in (p4, p5)])
+    assert e.value.code == -3  # CLR_E_UNSUPPORTED
