@@ -130,12 +130,16 @@ typedef struct {
   int64_t n, m, kkt_dim;   /* N = n + m */
   int64_t kkt_nnz_lower;   /* structural nonzeros of the lower triangle of K */
   int64_t l_nnz;           /* nonzeros of L (supernodal, including the diagonal) */
-  double factor_flops;     /* multiply-adds x 2 of one numeric factorization */
+  double factor_flops;     /* flops of the exact factor (multiply-adds x 2; explicit zeros excluded) */
   int64_t n_supernodes;
   int64_t n_levels;        /* depth of the supernodal elimination tree */
   int64_t max_front;       /* largest frontal matrix order */
   int64_t front_pool_entries; /* entries of the frontal-matrix pool */
   int64_t n_dense_rows;    /* rows treated as dense by the ordering */
+  int64_t ordering;        /* 0: AMD on the KKT pattern; 1: cone rows first, then x by AMD (fewer flops) */
+  int64_t l_nnz_exact;     /* nnz of the exact factor pattern (l_nnz adds the explicit zeros of merged supernodes) */
+  int64_t l_nnz_counted;   /* the same from column counts of the order, without forming the factor */
+  double factor_flops_stored; /* flops the supernodal factorization performs (explicit zeros included) */
 } clr_symbolic_stats;
 
 /* Device-side timing of the last clr_solve, from CUDA events recorded inside

@@ -57,7 +57,8 @@ class clr_symbolic_stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("kkt_dim", C.c_int64), ("kkt_nnz_lower", C.c_int64),
                 ("l_nnz", C.c_int64), ("factor_flops", C.c_double), ("n_supernodes", C.c_int64),
                 ("n_levels", C.c_int64), ("max_front", C.c_int64), ("front_pool_entries", C.c_int64),
-                ("n_dense_rows", C.c_int64)]
+                ("n_dense_rows", C.c_int64), ("ordering", C.c_int64), ("l_nnz_exact", C.c_int64),
+                ("l_nnz_counted", C.c_int64), ("factor_flops_stored", C.c_double)]
 
 
 class clr_problem(C.Structure):

@@ -138,7 +138,8 @@ static int make_batch(clr_solver** out, int32_t nprob, const clr_problem* probs,
         rcs[i] = clr::build_problem(hps[i], pr.P_upper, pr.q, pr.A, pr.b, pr.cones, pr.ncones, s, errs[i]);
         if (rcs[i] == CLR_OK) {
           int64_t nd = 0;
-          clr::kkt_amd_order(hps[i].n + hps[i].m, hps[i].kcol_ptr, hps[i].krow, orders[i], nd);
+          int which = 0;
+          clr::choose_kkt_order(hps[i], orders[i], nd, &which);
         }
       }
     };
@@ -196,6 +197,10 @@ int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out) {
   r.max_front = v.sy.max_front;
   r.front_pool_entries = v.sy.pool;
   r.n_dense_rows = v.sy.n_dense;
+  r.ordering = v.sy.ordering;
+  r.l_nnz_exact = v.sy.l_nnz_exact;
+  r.l_nnz_counted = v.sy.pred_nnz;
+  r.factor_flops_stored = v.sy.flops_stored;
   *out = r;
   return CLR_OK;
 }

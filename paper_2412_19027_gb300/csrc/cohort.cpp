@@ -130,11 +130,26 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     if (lay.ckz.empty()) lay.ckz.push_back(Chunk{0, 0, 0});
     lay.ckx_ptr[1] = (int64_t)lay.ckx.size();
     lay.ckz_ptr[1] = (int64_t)lay.ckz.size();
-    int rc;
-    if (!orders.empty() && !orders[0].empty()) rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, &orders[0], sy);
-    else rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, nullptr, sy);
-    if (rc != CLR_OK) err = "symbolic analysis failed";
-    return rc;
+    std::vector<int64_t> own;
+    int64_t nd = 0;
+    int which = 0;
+    const std::vector<int64_t>* use = nullptr;
+    if (!orders.empty() && !orders[0].empty()) {
+      use = &orders[0];
+      which = -1;
+    } else {
+      choose_kkt_order(hp, own, nd, &which);
+      use = &own;
+    }
+    int rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, use, sy);
+    if (rc != CLR_OK) {
+      err = "symbolic analysis failed";
+      return rc;
+    }
+    sy.n_dense = nd;
+    sy.ordering = which;
+    kkt_factor_counts(N, hp.kcol_ptr, hp.krow, *use, &sy.pred_nnz, &sy.pred_flops);
+    return CLR_OK;
   }
 
   // ---- x segments and family-major rows ----
@@ -283,7 +298,8 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
       use = &orders[p];
     } else {
       int64_t nd = 0;
-      kkt_amd_order(pr.n + pr.m, pr.kcol_ptr, pr.krow, own, nd);
+      int which = 0;
+      choose_kkt_order(pr, own, nd, &which);
       n_dense += nd;
       use = &own;
     }
@@ -306,6 +322,8 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     return rc;
   }
   sy.n_dense = n_dense;
+  sy.ordering = -1;
+  kkt_factor_counts(N, hp.kcol_ptr, hp.krow, order, &sy.pred_nnz, &sy.pred_flops);
   return CLR_OK;
 }
 

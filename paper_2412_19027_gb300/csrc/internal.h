@@ -70,8 +70,13 @@ struct Symbolic {
   int64_t nlev = 0;
   std::vector<int64_t> lev_ptr, lev_sn;    // supernodes of each level
   // statistics
-  int64_t l_nnz = 0;
-  double flops = 0;
+  int64_t l_nnz = 0;        // entries of L as stored (explicit zeros of merged supernodes included)
+  int64_t l_nnz_exact = 0;  // entries of the exact factor pattern
+  double flops = 0;         // flops of the exact factor (algorithmic)
+  double flops_stored = 0;  // flops the supernodal factorization performs (explicit zeros included)
+  int ordering = 0;         // 0 AMD, 1 cone rows first, -1 given by the caller
+  int64_t pred_nnz = 0;     // nnz(L) and flops from column counts of the order (equal to the above)
+  double pred_flops = 0;
   int64_t max_front = 0;
 };
 
@@ -121,10 +126,17 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
 int set_qb(HostProblem& hp, const double* q, const double* b);
 void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx,
                std::vector<int64_t>& perm, int64_t& n_dense);
+// relax: merge supernodes with few explicit zeros (relaxed amalgamation).
 int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
-                     const std::vector<int64_t>* user_order, Symbolic& sy);
+                     const std::vector<int64_t>* user_order, Symbolic& sy, bool relax = true);
 // The fill-reducing order symbolic_analyze uses when given none (AMD on the KKT pattern).
 void kkt_amd_order(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
                    std::vector<int64_t>& order, int64_t& n_dense);
+// nnz(L) (diagonal included) and factor flops of the KKT pattern in `order`, from column counts.
+void kkt_factor_counts(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                       const std::vector<int64_t>& order, int64_t* nnz, double* flops);
+// The order used for a problem: AMD, or cone rows first when that needs fewer flops
+// (*which = 0 or 1).
+int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t& n_dense, int* which);
 
 }  // namespace clr

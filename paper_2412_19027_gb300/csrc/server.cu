@@ -189,7 +189,8 @@ class Server {
                               st_, err);
       if (r->rc == CLR_OK) {
         int64_t nd = 0;
-        kkt_amd_order(r->hp.n + r->hp.m, r->hp.kcol_ptr, r->hp.krow, r->order, nd);
+        int which = 0;
+        choose_kkt_order(r->hp, r->order, nd, &which);
       }
       // inputs no longer needed
       std::vector<int64_t>().swap(r->pcol);

@@ -48,8 +48,206 @@ void kkt_amd_order(int64_t N, const std::vector<int64_t>& colptr, const std::vec
   amd_order(N, aptr, aidx, order, n_dense);
 }
 
+namespace {
+// Column counts of the factor of the symmetric pattern (aptr/aidx) eliminated in
+// `order`, without forming the factor: elimination tree, postorder, then the
+// row-subtree skeleton count of Gilbert, Ng and Peyton -- for every row i the
+// leaves of its row subtree add +1 and the lowest common ancestor of two
+// consecutive leaves -1, so that a subtree sum gives each column's count.
+// Returns nnz(L) (diagonal included) and the flop count used by the symbolic.
+void factor_counts(int64_t N, const std::vector<int64_t>& aptr, const std::vector<int64_t>& aidx,
+                   const std::vector<int64_t>& order, int64_t* nnz, double* flops) {
+  std::vector<int64_t> iorder(N);
+  for (int64_t k = 0; k < N; ++k) iorder[order[k]] = k;
+  std::vector<int64_t> parent(N, -1), anc(N, -1);
+  for (int64_t k = 0; k < N; ++k) {
+    const int64_t v = order[k];
+    for (int64_t p = aptr[v]; p < aptr[v + 1]; ++p) {
+      int64_t i = iorder[aidx[p]];
+      if (i >= k) continue;
+      while (i != -1 && i != k) {
+        const int64_t nxt = anc[i];
+        anc[i] = k;
+        if (nxt == -1) parent[i] = k;
+        i = nxt;
+      }
+    }
+  }
+  // postorder
+  std::vector<int64_t> head(N, -1), nextc(N, -1), post;
+  post.reserve(N);
+  for (int64_t j = N - 1; j >= 0; --j)
+    if (parent[j] >= 0) {
+      nextc[j] = head[parent[j]];
+      head[parent[j]] = j;
+    }
+  std::vector<int64_t> stack;
+  for (int64_t r = 0; r < N; ++r) {
+    if (parent[r] != -1) continue;
+    stack.push_back(r);
+    while (!stack.empty()) {
+      const int64_t top = stack.back();
+      const int64_t c = head[top];
+      if (c != -1) {
+        head[top] = nextc[c];
+        stack.push_back(c);
+      } else {
+        post.push_back(top);
+        stack.pop_back();
+      }
+    }
+  }
+  // first[j]: smallest postorder index in the subtree of j; leaves have first == own index
+  std::vector<int64_t> kpos(N), first(N, -1), delta(N, 0);
+  for (int64_t k = 0; k < N; ++k) kpos[post[k]] = k;
+  for (int64_t k = 0; k < N; ++k) {
+    int64_t j = post[k];
+    delta[j] = (first[j] == -1) ? 1 : 0;  // leaf of the elimination tree
+    for (; j != -1 && first[j] == -1; j = parent[j]) first[j] = k;
+  }
+  std::vector<int64_t> maxfirst(N, -1), prevleaf(N, -1), setp(N);
+  for (int64_t i = 0; i < N; ++i) setp[i] = i;
+  auto find = [&](int64_t x) {
+    int64_t r = x;
+    while (setp[r] != r) r = setp[r];
+    while (setp[x] != r) {
+      const int64_t nx = setp[x];
+      setp[x] = r;
+      x = nx;
+    }
+    return r;
+  };
+  for (int64_t k = 0; k < N; ++k) {
+    const int64_t j = post[k];
+    if (parent[j] != -1) delta[parent[j]] -= 1;
+    const int64_t v = order[j];
+    for (int64_t p = aptr[v]; p < aptr[v + 1]; ++p) {
+      const int64_t i = iorder[aidx[p]];  // entry (i, j) of the lower triangle when i > j
+      if (i <= j) continue;
+      if (first[j] <= maxfirst[i]) continue;  // j is not a leaf of row subtree i
+      maxfirst[i] = first[j];
+      const int64_t jprev = prevleaf[i];
+      prevleaf[i] = j;
+      delta[j] += 1;
+      if (jprev != -1) delta[find(jprev)] -= 1;  // lca of consecutive leaves
+    }
+    if (parent[j] != -1) setp[j] = parent[j];
+  }
+  for (int64_t k = 0; k < N; ++k) {
+    const int64_t j = post[k];
+    if (parent[j] != -1) delta[parent[j]] += delta[j];
+  }
+  int64_t nz = 0;
+  double fl = 0;
+  for (int64_t j = 0; j < N; ++j) {
+    nz += delta[j];
+    const double below = (double)(delta[j] - 1);
+    fl += below * (below + 1.0) + below;
+  }
+  (void)kpos;
+  *nnz = nz;
+  *flops = fl;
+}
+}  // namespace
+
+void kkt_factor_counts(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
+                       const std::vector<int64_t>& order, int64_t* nnz, double* flops) {
+  std::vector<int64_t> aptr, aidx;
+  build_adjacency(N, colptr, rowidx, aptr, aidx);
+  factor_counts(N, aptr, aidx, order, nnz, flops);
+}
+
+// Fill-reducing order of one problem's KKT matrix.  Two candidates, the one
+// whose factor needs fewer flops wins (ties: AMD):
+//   0  AMD on the whole KKT pattern;
+//   1  the constraint rows with a nonzero H block (nonnegative and cone rows)
+//      first, in row order -- H is block diagonal, so they cause no fill among
+//      themselves -- then x and the zero-cone rows in the AMD order of their
+//      Schur-complement pattern (K restricted to them, plus one clique per H
+//      block over the x columns its rows touch).
+// AMD alone eliminates the low-degree x columns of a sparse random A first and
+// fills the whole constraint block; candidate 1 leaves a dense x block instead.
+int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t& n_dense, int* which) {
+  const int64_t n = hp.n, m = hp.m, N = n + m;
+  std::vector<int64_t> aptr, aidx;
+  build_adjacency(N, hp.kcol_ptr, hp.krow, aptr, aidx);
+  amd_order(N, aptr, aidx, order, n_dense);
+  *which = 0;
+  const int64_t mz = hp.cl.m_zero;
+  if (m - mz <= 0 || n == 0) return CLR_OK;
+  // Schur pattern on R = x u zero rows (local ids: x j -> j, zero row r -> n + r)
+  const int64_t R = n + mz;
+  std::vector<std::vector<int64_t>> adj(R);
+  for (int64_t u = 0; u < N; ++u) {
+    const int64_t lu = u < n ? u : (u - n < mz ? u : -1);
+    if (lu < 0) continue;
+    for (int64_t p = aptr[u]; p < aptr[u + 1]; ++p) {
+      const int64_t v = aidx[p];
+      const int64_t lv = v < n ? v : (v - n < mz ? v : -1);
+      if (lv >= 0) adj[lu].push_back(lv);
+    }
+  }
+  // one clique per H block over its x neighbours
+  int64_t pairs = 0;
+  const int64_t pair_cap = 64 * (int64_t)aidx.size() + 50'000'000;
+  std::vector<int64_t> nb;
+  std::vector<int64_t> mark(n, -1);
+  for (size_t ci = 0; ci < hp.cl.cones.size(); ++ci) {
+    const Cone& c = hp.cl.cones[ci];
+    if (c.type == CLR_ZERO) continue;
+    const bool rowwise = c.type == CLR_NONNEG;  // each nonneg row is its own 1x1 block
+    const int64_t nblk = rowwise ? c.dim : 1, bdim = rowwise ? 1 : c.dim;
+    for (int64_t bk = 0; bk < nblk; ++bk) {
+      nb.clear();
+      const int64_t tag = (int64_t)ci * (1LL << 32) + bk;
+      for (int64_t r = c.off + bk * bdim; r < c.off + (bk + 1) * bdim; ++r)
+        for (int64_t p = hp.A.ptr[r]; p < hp.A.ptr[r + 1]; ++p) {
+          const int64_t j = hp.A.idx[p];
+          if (mark[j] != tag) {
+            mark[j] = tag;
+            nb.push_back(j);
+          }
+        }
+      pairs += (int64_t)nb.size() * (int64_t)nb.size();
+      if (pairs > pair_cap) return CLR_OK;  // too dense to be worth it
+      for (int64_t a : nb)
+        for (int64_t b2 : nb)
+          if (a != b2) adj[a].push_back(b2);
+    }
+  }
+  std::vector<int64_t> sptr(R + 1, 0), sidx;
+  for (int64_t u = 0; u < R; ++u) {
+    std::vector<int64_t>& a = adj[u];
+    std::sort(a.begin(), a.end());
+    a.erase(std::unique(a.begin(), a.end()), a.end());
+    sptr[u + 1] = sptr[u] + (int64_t)a.size();
+  }
+  sidx.reserve(sptr[R]);
+  for (int64_t u = 0; u < R; ++u) {
+    sidx.insert(sidx.end(), adj[u].begin(), adj[u].end());
+    std::vector<int64_t>().swap(adj[u]);
+  }
+  std::vector<int64_t> rperm;
+  int64_t nd1 = 0;
+  amd_order(R, sptr, sidx, rperm, nd1);
+  std::vector<int64_t> cand;
+  cand.reserve(N);
+  for (int64_t r = mz; r < m; ++r) cand.push_back(n + r);
+  for (int64_t v : rperm) cand.push_back(v);  // local ids equal KKT indices for x and zero rows
+  int64_t nz0 = 0, nz1 = 0;
+  double f0 = 0, f1 = 0;
+  factor_counts(N, aptr, aidx, order, &nz0, &f0);
+  factor_counts(N, aptr, aidx, cand, &nz1, &f1);
+  if (f1 < f0) {
+    order.swap(cand);
+    n_dense = nd1;
+    *which = 1;
+  }
+  return CLR_OK;
+}
+
 int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
-                     const std::vector<int64_t>* user_order, Symbolic& sy) {
+                     const std::vector<int64_t>* user_order, Symbolic& sy, bool relax_) {
   sy = Symbolic();
   sy.N = N;
   // ---- symmetric adjacency for the ordering ----
@@ -167,8 +365,84 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
     cs[j] = std::move(s);
     if (par[j] < 0) std::vector<int64_t>().swap(cs[j]);
   }
-  sy.nsn = (int64_t)sn_ptr.size();
+  // exact factor statistics (fundamental supernodes hold no explicit zeros)
   sn_ptr.push_back(N);
+  {
+    const int64_t nf = (int64_t)sn_rows.size();
+    sy.flops = 0;
+    sy.l_nnz_exact = 0;
+    for (int64_t J = 0; J < nf; ++J) {
+      const int64_t f = (int64_t)sn_rows[J].size(), c = sn_ptr[J + 1] - sn_ptr[J];
+      sy.l_nnz_exact += c * (c + 1) / 2 + c * (f - c);
+      for (int64_t k = 0; k < c; ++k) {
+        const double below = (double)(f - k - 1);
+        sy.flops += below * (below + 1.0) + below;  // rank-1 update of the lower triangle + scaling
+      }
+    }
+  }
+  // ---- relaxed amalgamation ----
+  // A supernode whose columns end right before its parent's (the last child in
+  // the postorder) is merged into the parent when the explicit zeros this adds
+  // stay small relative to the merged panel -- the relaxed-supernode rule of
+  // Ashcraft and Grimes with the usual thresholds (always up to 4 columns, 80%
+  // zeros up to 16, 10% up to 48, 5% beyond).  The merged rows are the child's
+  // columns followed by the parent's rows (the child's update rows are a subset
+  // of them).  Fewer, wider fronts: less front memory (sum f^2), fewer levels,
+  // more dense work per launch.
+  {
+    const int64_t nf = (int64_t)sn_rows.size();
+    std::vector<int64_t> fpar(nf, -1);
+    for (int64_t J = 0; J < nf; ++J) {
+      const int64_t last = sn_ptr[J + 1] - 1;
+      fpar[J] = (par[last] >= 0) ? sn_of[par[last]] : -1;
+    }
+    std::vector<int64_t> gc(nf), gz(nf, 0), gf(nf);  // merged group ending at J: columns, zeros, rows
+    std::vector<char> absorbed(nf, 0);                // J merged into J + 1
+    for (int64_t J = 0; J < nf; ++J) {
+      gc[J] = sn_ptr[J + 1] - sn_ptr[J];
+      gf[J] = (int64_t)sn_rows[J].size();
+    }
+    for (int64_t J = 0; J + 1 < nf; ++J) {
+      const int64_t P = J + 1;
+      if (fpar[J] != P || !relax_) continue;
+      const int64_t cP = gc[P], fP = gf[P];
+      const int64_t c = gc[J] + cP, f = gc[J] + fP;
+      const int64_t rJ = gf[J] - gc[J];
+      const int64_t z = gz[J] + gz[P] + gc[J] * (fP - rJ);
+      const double tot = (double)c * (double)f - 0.5 * (double)c * (double)(c - 1);
+      const double zr = (double)z / tot;
+      const bool merge = c <= 4 || (c <= 16 && zr < 0.8) || (c <= 48 && zr < 0.1) || zr < 0.05;
+      if (!merge) continue;
+      absorbed[J] = 1;
+      gc[P] = c;
+      gf[P] = f;
+      gz[P] = z;
+    }
+    // rebuild the supernode list: a group is a run of absorbed supernodes ending at a kept one
+    std::vector<int64_t> new_ptr;
+    std::vector<std::vector<int64_t>> new_rows;
+    std::vector<int64_t> old2new(nf);
+    int64_t start = -1;
+    for (int64_t J = 0; J < nf; ++J) {
+      if (start < 0) start = J;
+      if (absorbed[J]) continue;
+      // group [start, J]: columns sn_ptr[start] .. sn_ptr[J+1]-1, rows = own columns + rows of J
+      std::vector<int64_t> rows;
+      rows.reserve((size_t)(sn_ptr[J] - sn_ptr[start]) + sn_rows[J].size());
+      for (int64_t col = sn_ptr[start]; col < sn_ptr[J]; ++col) rows.push_back(col);
+      rows.insert(rows.end(), sn_rows[J].begin(), sn_rows[J].end());
+      for (int64_t K = start; K <= J; ++K) old2new[K] = (int64_t)new_ptr.size();
+      new_ptr.push_back(sn_ptr[start]);
+      new_rows.push_back(std::move(rows));
+      for (int64_t K = start; K <= J; ++K) std::vector<int64_t>().swap(sn_rows[K]);
+      start = -1;
+    }
+    new_ptr.push_back(N);
+    for (int64_t j = 0; j < N; ++j) sn_of[j] = old2new[sn_of[j]];
+    sn_ptr.swap(new_ptr);
+    sn_rows.swap(new_rows);
+  }
+  sy.nsn = (int64_t)sn_rows.size();
   sy.sn_ptr = sn_ptr;
   sy.sn_parent.assign(sy.nsn, -1);
   for (int64_t J = 0; J < sy.nsn; ++J) {
@@ -184,7 +458,7 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
   sy.front_off[0] = 0;
   sy.upd_off[0] = 0;
   sy.l_nnz = 0;
-  sy.flops = 0;
+  sy.flops_stored = 0;
   sy.max_front = 0;
   for (int64_t J = 0; J < sy.nsn; ++J) {
     std::copy(sn_rows[J].begin(), sn_rows[J].end(), sy.rows.begin() + sy.row_ptr[J]);
@@ -194,8 +468,8 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
     sy.upd_off[J + 1] = sy.upd_off[J] + f;
     sy.l_nnz += c * (c + 1) / 2 + c * (f - c);
     for (int64_t k = 0; k < c; ++k) {
-      double below = (double)(f - k - 1);
-      sy.flops += below * (below + 1.0) + below;  // rank-1 update of the lower triangle + scaling
+      const double below = (double)(f - k - 1);
+      sy.flops_stored += below * (below + 1.0) + below;
     }
     sy.max_front = std::max(sy.max_front, f);
   }
