@@ -12,7 +12,7 @@
 namespace clr {
 
 constexpr int kBfNB = 64;
-constexpr int kTrsmRows = 8;  // rows of L21 per CTA of the panel kernel
+constexpr int kTrsmRows = 64;  // rows of L21 per CTA of the panel kernel
 
 // Device arrays indexed by big-front id.
 struct BigFrontDev {
@@ -59,7 +59,7 @@ __host__ __device__ inline int64_t bf_trsm_blocks(int64_t f, int64_t c, int p) {
   const int64_t pw = (c - k0 < kBfNB) ? c - k0 : kBfNB;
   return (f - k0 - pw + kTrsmRows - 1) / kTrsmRows;
 }
-__host__ __device__ inline int64_t bf_fin_blocks(int64_t c, int p) {  // finalisation of the E rows of panel p
+__host__ __device__ inline int64_t bf_fin_blocks(int64_t c, int p) {  // finalisation of the E rows of panel p (same launch)
   if (p < 0 || (int64_t)p * kBfNB >= c) return 0;
   return p + 1;
 }

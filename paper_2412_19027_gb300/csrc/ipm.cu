@@ -56,6 +56,9 @@ __device__ __forceinline__ int64_t chunk_slot(const ChunkGrid& g) {
 // mode 0: lo[i] = sum_{col < n} K_ij v_j, hi[i] = sum_{col >= n} K_ij v_j
 // mode 1: out[i] = rhs[i] - (K v)_i and max |out| of each problem -> sc[p].rnorm_bits
 // mode 2 (rows n..N-1): out[i-n] = -rhs[i-n] + hi   (Delta s = -d_s - H Delta z; K_zz = -H)
+// The sum of a row is formed in one fixed order whatever G is (32 partial sums,
+// entry e of the row going to partial e mod 32, then the pairwise tree t += t+16,
+// t += t+8, ...), so a row gives the same bits in every cohort it belongs to.
 template <int G>
 __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t* __restrict__ kptr,
                       const int32_t* __restrict__ kcol, const int32_t* __restrict__ kvi, const double* __restrict__ kval,
@@ -63,6 +66,7 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
                       const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ pid,
                       IterScal* sc, const int* skip) {
   if (skip && *skip) return;
+  constexpr int NU = 32 / G;  // partial sums per lane: t = lane + G u
   const int lane = threadIdx.x % G;
   // the G lanes of a row group share its trip count: shuffles name only their own group
   const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -70,28 +74,44 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
   const int64_t gstride = ((int64_t)gridDim.x * blockDim.x) / G;
   RunExt<true> mx;
   for (int64_t i = r0 + gid; i < r1; i += gstride) {
-    double a = 0.0, b = 0.0;
-    for (int64_t p = kptr[i] + lane; p < kptr[i + 1]; p += G) {
-      const int32_t c = kcol[p];
-      const double t = kval[kvi[p]] * v[c];
-      if (c < n) a += t;
-      else b += t;
+    double a[NU], b[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) a[u] = b[u] = 0.0;
+    const int64_t p0 = kptr[i], p1 = kptr[i + 1];
+    for (int64_t base = p0; base < p1; base += 32) {
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const int64_t p = base + lane + G * u;
+        if (p < p1) {
+          const int32_t c = kcol[p];
+          const double t = kval[kvi[p]] * v[c];
+          if (c < n) a[u] += t;
+          else b[u] += t;
+        }
+      }
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(gmask, a, o, G);
-      b += __shfl_xor_sync(gmask, b, o, G);
+    for (int off = 16; off >= G; off >>= 1)
+#pragma unroll
+      for (int u = 0; u < off / G; ++u) {
+        a[u] += a[u + off / G];
+        b[u] += b[u + off / G];
+      }
+#pragma unroll
+    for (int off = (G == 32 ? 16 : G / 2); off > 0; off >>= 1) {
+      a[0] += __shfl_xor_sync(gmask, a[0], off, G);
+      b[0] += __shfl_xor_sync(gmask, b[0], off, G);
     }
     if (lane == 0) {
       if (mode == 0) {
-        lo[i] = a;
-        hi[i] = b;
+        lo[i] = a[0];
+        hi[i] = b[0];
       } else if (mode == 1) {
-        const double r = rhs[i] - (a + b);
+        const double r = rhs[i] - (a[0] + b[0]);
         out[i] = r;
         mx.add(sc, &IterScal::rnorm_bits, pid[i], dbits(fabs(r)));
       } else {
-        out[i - n] = -rhs[i - n] + b;
+        out[i - n] = -rhs[i - n] + b[0];
       }
     }
   }

@@ -308,7 +308,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
         for (int64_t b : ids) {
           const int64_t f = bf_f[b], c = bf_c[b];
           ca.push_back((int64_t)p * kBfNB < c ? 1 : 0);
-          cb.push_back(bf_trsm_blocks(f, c, p) + bf_fin_blocks(c, p - 1));
+          cb.push_back(bf_trsm_blocks(f, c, p) + bf_fin_blocks(c, p));
           cc.push_back(bf_update_tiles(f, c, p));
         }
         add_list(pl.A[p], ids, ca);
