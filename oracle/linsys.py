@@ -100,17 +100,27 @@ class KKTSolver:
         return u
 
     def solve(self, rhs):
+        """Refinement on the unregularised K (Sec. 3.6): stop at the tolerance
+        or after ir_max steps; a step that makes ||r||_inf larger is undone and
+        ends the refinement (the regularised factor is no longer a contraction
+        for K there); optionally stop once a step gains less than ir_stop_ratio."""
         x = self._solve_reg(rhs)
         bnorm = float(np.max(np.abs(rhs))) if len(rhs) else 0.0
         prev = np.inf
-        for _ in range(self.ir_max):
+        last = None
+        steps = 0
+        while True:
             r = rhs - self.K @ x
             rn = float(np.max(np.abs(r)))
-            if rn <= self.ir_abs + self.ir_rel * bnorm:
+            if last is not None and rn > prev:
+                x = x - last
                 break
-            if self.ir_stop > 0 and not (rn * self.ir_stop < prev):
-                break  # optional stall test: the last step gained less than ir_stop_ratio
+            stalled = self.ir_stop > 0 and not (rn * self.ir_stop < prev)
+            if not (rn > self.ir_abs + self.ir_rel * bnorm) or stalled or steps >= self.ir_max:
+                break
             prev = rn
-            x = x + self._solve_reg(r)
+            last = self._solve_reg(r)
+            x = x + last
+            steps += 1
             self.ir_steps += 1
         return x

@@ -13,6 +13,8 @@
 // and arithmetic are those it has alone.
 #include <algorithm>
 #include <array>
+#include <chrono>
+#include <cstdio>
 #include <numeric>
 
 #include "internal.h"
@@ -73,7 +75,7 @@ ProbConst prob_const(const HostProblem& p) {
 }  // namespace
 
 int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<int64_t>>& orders, HostProblem& hp,
-                 CohortLayout& lay, Symbolic& sy, std::string& err) {
+                 CohortLayout& lay, Symbolic& sy, std::string& err, int verbose) {
   const int64_t B = (int64_t)probs.size();
   if (B == 0) {
     err = "a cohort needs at least one problem";
@@ -138,10 +140,19 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
       use = &orders[0];
       which = -1;
     } else {
+      const auto t0 = std::chrono::steady_clock::now();
       choose_kkt_order(hp, own, nd, &which);
+      if (verbose)
+        std::fprintf(stderr, "[clr] setup: ordering %.3f s (%s)\n",
+                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(),
+                     which ? "cone rows first" : "AMD");
       use = &own;
     }
+    const auto t1 = std::chrono::steady_clock::now();
     int rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, use, sy);
+    if (verbose)
+      std::fprintf(stderr, "[clr] setup: symbolic %.3f s\n",
+                   std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count());
     if (rc != CLR_OK) {
       err = "symbolic analysis failed";
       return rc;

@@ -118,7 +118,7 @@ struct CohortLayout {
 // fill-reducing order `orders[p]`, or none) into one cohort problem `hp` and
 // its symbolic factorization.  The big per-problem arrays are released.
 int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<int64_t>>& orders, HostProblem& hp,
-                 CohortLayout& lay, Symbolic& sy, std::string& err);
+                 CohortLayout& lay, Symbolic& sy, std::string& err, int verbose = 0);
 
 // ---- host routines (setup.cpp / amd.cpp / symbolic.cpp) ----
 int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_csc* A, const double* b,

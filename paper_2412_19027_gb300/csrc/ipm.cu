@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -340,11 +341,19 @@ __global__ void k_set_from(ChunkGrid g, double* __restrict__ dst, const T* __res
 
 // Refinement test of one problem (Sec. 3.6): stop at the tolerance, or, when
 // stop_ratio > 0, as soon as a step has reduced ||r||_inf by less than
-// stop_ratio (the last correction is kept), or after max_steps steps.
+// stop_ratio (the last correction is kept), or after max_steps steps.  A step
+// that made ||r||_inf larger is undone (k_ir_revert) and ends the refinement:
+// the regularised factor is not a contraction for K there.
 __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double stop_ratio, int max_steps) {
   const double r = bitsd(q.rnorm_bits);
   q.rnorm_bits = 0ull;
+  q.ir_revert = 0;
   if (q.ir_skip) return false;
+  if (r > q.ir_prev) {
+    q.ir_revert = 1;
+    q.ir_skip = 1;
+    return false;
+  }
   const bool stalled = stop_ratio > 0 && !(r * stop_ratio < q.ir_prev);
   q.ir_prev = r;
   if (!(r > abstol + reltol * q.rhs_norm) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
@@ -354,6 +363,19 @@ __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double st
   q.ir_cur += 1;
   q.ir_total += 1;
   return true;
+}
+
+// Undo the last correction of the problems whose residual it made larger.
+template <typename T>
+__global__ void k_ir_revert(ChunkGrid g, double* __restrict__ dst, const T* __restrict__ src, const IterScal* sc,
+                            const int* skip) {
+  if (skip && *skip) return;
+  int64_t i0, len;
+  int pid;
+  bool zp;
+  chunk_range(g, &i0, &len, &pid, &zp);
+  if (!sc[pid].ir_revert) return;
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) dst[i] -= (double)src[i];
 }
 
 // Unrolled loop (no graph): per-problem test, ir_none = no problem continues.
@@ -761,6 +783,7 @@ int Solver::analyze(const clr_csc* P, const double* q, const clr_csc* A, const d
   std::vector<HostProblem> ps(1);
   int rc = build_problem(ps[0], P, q, A, b, cones, ncones, st, err);
   if (rc != CLR_OK) return rc;
+  if (st.verbose) std::fprintf(stderr, "[clr] setup: validate, reorder, equilibrate, KKT layout %.3f s\n", now_s() - t0);
   rc = analyze_cohort(std::move(ps), {}, s);
   setup_s = now_s() - t0;
   return rc;
@@ -771,9 +794,13 @@ int Solver::analyze_cohort(std::vector<HostProblem>&& ps, const std::vector<std:
   st = s;
   const double t0 = now_s();
   probs = std::move(ps);
-  int rc = build_cohort(probs, orders, hp, lay, sy, err);
+  int rc = build_cohort(probs, orders, hp, lay, sy, err, st.verbose);
   if (rc != CLR_OK) return rc;
+  const double t1 = now_s();
   build_numeric_maps(sy, hp.kcol_ptr, hp.krow, mp);
+  if (st.verbose)
+    std::fprintf(stderr, "[clr] setup: ordering + symbolic %.3f s, numeric maps %.3f s (N %lld, nnz(L) %lld, %.3g flops)\n",
+                 t1 - t0, now_s() - t1, (long long)sy.N, (long long)sy.l_nnz, sy.flops);
   setup_s += now_s() - t0;
   return CLR_OK;
 }
@@ -986,6 +1013,10 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   const int pg = grid_for(B, 128);
   k_inf_norm<<<nck, 256, 0, s>>>(cg, rhs, sc_, halt);
   k_ir_begin<<<pg, 128, 0, s>>>(sc_, B, bf_);
+  auto revert = [&](cudaStream_t ss) {
+    if (st.factor_bits == 64) k_ir_revert<double><<<nck, 256, 0, ss>>>(cg, sol, f64_.xs, sc_, halt);
+    else k_ir_revert<float><<<nck, 256, 0, ss>>>(cg, sol, f32_.xs, sc_, halt);
+  };
   auto ldl_solve_add = [&](cudaStream_t ss, const double* b, int add) -> int {
     if (st.factor_bits == 64) {
       int rc = f64_.solve(ss, b, irs);
@@ -1014,9 +1045,11 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CLR_CUDA(cudaStreamIsCapturing(s, &cs));
   if (cs != cudaStreamCaptureStatusActive || st.ir_max_steps == 0) {
-    for (int it = 0; it < st.ir_max_steps; ++it) {
+    for (int it = 0; it <= st.ir_max_steps; ++it) {  // the last pass only checks the last step
       residual(s);
       k_ir_check<<<1, cb, 0, s>>>(sc_, B, bf_, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio, st.ir_max_steps);
+      if (it > 0) revert(s);
+      if (it == st.ir_max_steps) break;
       rc = ldl_solve_add(s, v_.r, 1);
       if (rc) return rc;
     }
@@ -1048,6 +1081,7 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   residual(body_stream_);
   k_ir_check_cond<<<1, cb, 0, body_stream_>>>(sc_, B, bf_, st.ir_abstol, st.ir_reltol, st.ir_stop_ratio,
                                               st.ir_max_steps, h);
+  revert(body_stream_);
   cudaGraph_t out = nullptr;
   cudaError_t e = cudaStreamEndCapture(body_stream_, &out);
   if (rc) return rc;

@@ -47,6 +47,39 @@ __global__ void k_pull(T* __restrict__ X, const int64_t* __restrict__ tgt, const
   }
 }
 
+// Extend-add of large update blocks by relative indices, one child per front per
+// launch: 32 x 32 tiles of the lower update block U_J (rows/cols c_J .. f_J-1 of
+// front J) added into the parent front at (rel[a], rel[b]).
+template <typename T>
+__global__ void k_push(T* __restrict__ F, WorkList wl, const int64_t* __restrict__ sn_ptr,
+                       const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ front_off,
+                       const int64_t* __restrict__ sn_parent, const int64_t* __restrict__ rel_off,
+                       const int32_t* __restrict__ rel, const int* skip) {
+  if (skip && *skip) return;
+  int64_t lo = 0, hi = wl.nfront - 1;
+  const int64_t bid = blockIdx.x;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (wl.pref[mid] <= bid) lo = mid;
+    else hi = mid - 1;
+  }
+  const int64_t J = wl.front[lo], q = bid - wl.pref[lo];
+  const int64_t c = sn_ptr[J + 1] - sn_ptr[J], f = row_ptr[J + 1] - row_ptr[J], r = f - c;
+  int64_t ti = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) / 2.0);
+  while (ti * (ti + 1) / 2 > q) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
+  const int64_t tj = q - ti * (ti + 1) / 2;
+  const int64_t P = sn_parent[J];
+  const int64_t fP = row_ptr[P + 1] - row_ptr[P];
+  const T* U = F + front_off[J];
+  T* FP = F + front_off[P];
+  const int32_t* rl = rel + rel_off[J];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int64_t a = ti * 32 + (e & 31), b = tj * 32 + (e >> 5);
+    if (a < r && b < r && a >= b) FP[rl[a] + (int64_t)rl[b] * fP] += U[(c + a) + (c + b) * f];
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T regularise(T d, int sgn, T eps, T delta, bool* hit) {
   if ((T)sgn * d <= eps) {
@@ -223,6 +256,45 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
     const int64_t c = sy.sn_ptr[J + 1] - sy.sn_ptr[J];
     for (int64_t k = 0; k < c; ++k) w_init[sy.upd_off[J] + k] = mp.rows_kkt[sy.row_ptr[J] + k];
   }
+  // ---- extend-add rounds by relative indices ----
+  {
+    st.rel = up(ar, mp.rel);
+    st.rel_off = up(ar, mp.rel_off);
+    st.sn_parent = up(ar, sy.sn_parent);
+    std::vector<int64_t> buf;
+    std::vector<std::pair<size_t, size_t>> where;  // (front offset, prefix offset) in buf per list
+    st.push_rounds.assign(sy.nlev, {});
+    for (int64_t l = 0; l < sy.nlev; ++l)
+      for (int64_t k = mp.px_lev_ptr[l]; k < mp.px_lev_ptr[l + 1]; ++k) {
+        WorkList wl;
+        const size_t fo = buf.size();
+        for (int64_t t = mp.px_round_ptr[k]; t < mp.px_round_ptr[k + 1]; ++t) buf.push_back(mp.px_child[t]);
+        const size_t po = buf.size();
+        int64_t nb = 0;
+        for (int64_t t = mp.px_round_ptr[k]; t < mp.px_round_ptr[k + 1]; ++t) {
+          const int64_t J = mp.px_child[t];
+          const int64_t r = (sy.row_ptr[J + 1] - sy.row_ptr[J]) - (sy.sn_ptr[J + 1] - sy.sn_ptr[J]);
+          const int64_t T = (r + 31) / 32;
+          buf.push_back(nb);
+          nb += T * (T + 1) / 2;
+        }
+        buf.push_back(nb);
+        wl.nfront = mp.px_round_ptr[k + 1] - mp.px_round_ptr[k];
+        wl.nblocks = nb;
+        st.push_rounds[l].push_back(wl);
+        where.emplace_back(fo, po);
+      }
+    int64_t* dbuf = buf.empty() ? nullptr : ar.upload(buf.data(), (int64_t)buf.size());
+    if (!buf.empty() && !dbuf) return CLR_E_OOM;
+    size_t w = 0;
+    for (int64_t l = 0; l < sy.nlev; ++l)
+      for (WorkList& wl : st.push_rounds[l]) {
+        wl.front = dbuf + where[w].first;
+        wl.pref = dbuf + where[w].second;
+        ++w;
+      }
+    if ((!mp.rel.empty() && !st.rel) || !st.rel_off || !st.sn_parent) return CLR_E_OOM;
+  }
   st.lev_small_maxf.assign(sy.nlev, 0);
   st.lev_big.assign(sy.nlev, {});
   for (int64_t l = 0; l < sy.nlev; ++l)
@@ -392,6 +464,10 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
   for (int64_t l = 0; l < S.nlev; ++l) {
     const int64_t t0 = S.h_fa_lev_ptr[l], t1 = S.h_fa_lev_ptr[l + 1];
     if (t1 > t0) k_pull<T><<<grid_for(t1 - t0, 256), 256, 0, stm>>>(F, S.fa_tgt, S.fa_ptr, S.fa_src, t0, t1, skip);
+    for (const WorkList& wl : S.push_rounds[l])
+      if (wl.nblocks > 0)
+        k_push<T><<<(unsigned)wl.nblocks, 256, 0, stm>>>(F, wl, S.sn_ptr, S.row_ptr, S.front_off, S.sn_parent,
+                                                          S.rel_off, S.rel, skip);
     const int64_t nf = S.h_lev_ptr[l + 1] - S.h_lev_ptr[l];
     if ((int64_t)S.lev_big[l].size() < nf) {
       const int mf = S.lev_small_maxf[l];

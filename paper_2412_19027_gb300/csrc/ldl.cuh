@@ -32,6 +32,12 @@ struct LdlStructure {
   std::vector<std::vector<int64_t>> lev_big;     // big fronts of each level
   BigFrontDev bfd;                               // big-front arrays (device)
   std::vector<BigLevelPlan> bplans;              // per level
+  // extend-add by relative indices: per level, the rounds' work lists (children
+  // and prefix sums of their 32 x 32 tile counts)
+  int32_t* rel = nullptr;
+  int64_t* rel_off = nullptr;
+  int64_t* sn_parent = nullptr;
+  std::vector<std::vector<WorkList>> push_rounds;
   int small_max = 0;
   int64_t max_front = 0;
 };

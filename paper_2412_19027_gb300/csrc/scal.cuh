@@ -40,7 +40,7 @@ struct IterScal {
   int ir_skip, ir_steps, ir_total, ir_cur;
   double rhs_norm, ir_prev;
   unsigned long long rnorm_bits;
-  int dyn_hits, pad1;
+  int dyn_hits, ir_revert;  // ir_revert: the last refinement step is being undone
   // initial point: order-preserving bits of the least nonneg entry
   unsigned long long nn_min_bits;
 };

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <numeric>
+#include <queue>
 
 #include "internal.h"
 #include "symbolic.h"
@@ -381,66 +382,130 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
     }
   }
   // ---- relaxed amalgamation ----
-  // A supernode whose columns end right before its parent's (the last child in
-  // the postorder) is merged into the parent when the explicit zeros this adds
-  // stay small relative to the merged panel -- the relaxed-supernode rule of
-  // Ashcraft and Grimes with the usual thresholds (always up to 4 columns, 80%
-  // zeros up to 16, 10% up to 48, 5% beyond).  The merged rows are the child's
-  // columns followed by the parent's rows (the child's update rows are a subset
-  // of them).  Fewer, wider fronts: less front memory (sum f^2), fewer levels,
-  // more dense work per launch.
-  {
+  // A child supernode is merged into its parent when the explicit zeros this
+  // adds stay small relative to the merged panel -- the relaxed-supernode rule
+  // of Ashcraft and Grimes with the usual thresholds (always up to 4 columns,
+  // 80% zeros up to 16, 10% up to 48, 5% beyond).  Any child may merge, not
+  // only the one whose columns end right before the parent's: its columns are
+  // moved to just before the parent's (a topological reordering of the
+  // elimination tree, so the fill is unchanged), children with the largest
+  // update blocks first.  A merged child's update rows are a subset of the
+  // parent's rows, so the merged front holds the child's columns followed by
+  // the parent's rows.  Fewer, wider fronts: no large extend-adds of thin
+  // supernodes, less front memory, fewer levels, more dense work per launch.
+  if (relax_) {
     const int64_t nf = (int64_t)sn_rows.size();
     std::vector<int64_t> fpar(nf, -1);
     for (int64_t J = 0; J < nf; ++J) {
       const int64_t last = sn_ptr[J + 1] - 1;
       fpar[J] = (par[last] >= 0) ? sn_of[par[last]] : -1;
     }
-    std::vector<int64_t> gc(nf), gz(nf, 0), gf(nf);  // merged group ending at J: columns, zeros, rows
-    std::vector<char> absorbed(nf, 0);                // J merged into J + 1
+    std::vector<std::vector<int64_t>> skids(nf);
+    for (int64_t J = 0; J < nf; ++J)
+      if (fpar[J] >= 0) skids[fpar[J]].push_back(J);
+    std::vector<int64_t> gc(nf), gz(nf, 0), gf(nf);     // merged group of J: columns, zeros, rows
+    std::vector<int64_t> into(nf, -1);                 // J merged into into[J]
+    std::vector<std::vector<int64_t>> group(nf);       // fundamental supernodes of the group, column order
+    std::vector<std::vector<int64_t>> gkids(nf);       // unmerged children of J's group
     for (int64_t J = 0; J < nf; ++J) {
       gc[J] = sn_ptr[J + 1] - sn_ptr[J];
       gf[J] = (int64_t)sn_rows[J].size();
+      group[J].push_back(J);
     }
-    for (int64_t J = 0; J + 1 < nf; ++J) {
-      const int64_t P = J + 1;
-      if (fpar[J] != P || !relax_) continue;
-      const int64_t cP = gc[P], fP = gf[P];
-      const int64_t c = gc[J] + cP, f = gc[J] + fP;
-      const int64_t rJ = gf[J] - gc[J];
-      const int64_t z = gz[J] + gz[P] + gc[J] * (fP - rJ);
-      const double tot = (double)c * (double)f - 0.5 * (double)c * (double)(c - 1);
-      const double zr = (double)z / tot;
-      const bool merge = c <= 4 || (c <= 16 && zr < 0.8) || (c <= 48 && zr < 0.1) || zr < 0.05;
-      if (!merge) continue;
-      absorbed[J] = 1;
-      gc[P] = c;
-      gf[P] = f;
-      gz[P] = z;
+    for (int64_t P = 0; P < nf; ++P) {  // children before parents
+      // candidates: the children of P's group, largest update first; when a
+      // child merges, its own unmerged children become children of the group
+      std::priority_queue<std::pair<int64_t, int64_t>> cand;  // (update rows, -index)
+      for (int64_t J : skids[P]) cand.emplace(gf[J] - gc[J], -J);
+      while (!cand.empty()) {
+        const int64_t J = -cand.top().second;
+        cand.pop();
+        const int64_t rJ = gf[J] - gc[J];
+        const int64_t c = gc[J] + gc[P], f = gc[J] + gf[P];
+        const int64_t z = gz[J] + gz[P] + gc[J] * (gf[P] - rJ);
+        const double tot = (double)c * (double)f - 0.5 * (double)c * (double)(c - 1);
+        const double zr = (double)z / tot;
+        const bool merge = c <= 4 || (c <= 16 && zr < 0.8) || (c <= 48 && zr < 0.1) || zr < 0.05;
+        if (!merge) {
+          gkids[P].push_back(J);  // stays a child of P's group
+          continue;
+        }
+        into[J] = P;
+        gc[P] = c;
+        gf[P] = f;
+        gz[P] = z;
+        std::vector<int64_t> g = std::move(group[J]);  // the child's columns go first
+        g.insert(g.end(), group[P].begin(), group[P].end());
+        group[P] = std::move(g);
+        for (int64_t K : gkids[J]) cand.emplace(gf[K] - gc[K], -K);  // now children of P's group
+        std::vector<int64_t>().swap(gkids[J]);
+      }
     }
-    // rebuild the supernode list: a group is a run of absorbed supernodes ending at a kept one
+    // representatives (groups not merged further), their tree and a postorder of it
+    std::vector<int64_t> rep(nf);
+    for (int64_t J = nf - 1; J >= 0; --J) rep[J] = (into[J] < 0) ? J : rep[into[J]];
+    std::vector<int64_t> rhead(nf, -1), rnext(nf, -1);
+    std::vector<int64_t> roots;
+    for (int64_t J = nf - 1; J >= 0; --J) {
+      if (into[J] >= 0) continue;
+      const int64_t Pr = fpar[J] >= 0 ? rep[fpar[J]] : -1;
+      if (Pr < 0) {
+        roots.push_back(J);
+      } else {
+        rnext[J] = rhead[Pr];
+        rhead[Pr] = J;
+      }
+    }
+    std::reverse(roots.begin(), roots.end());
+    std::vector<int64_t> rpost;
+    std::vector<int64_t> stk;
+    for (int64_t R0 : roots) {
+      stk.push_back(R0);
+      while (!stk.empty()) {
+        const int64_t top = stk.back();
+        const int64_t ch = rhead[top];
+        if (ch != -1) {
+          rhead[top] = rnext[ch];
+          stk.push_back(ch);
+        } else {
+          rpost.push_back(top);
+          stk.pop_back();
+        }
+      }
+    }
+    // new positions: groups in postorder, each group's supernodes in its column order
+    std::vector<int64_t> newpos(N);
     std::vector<int64_t> new_ptr;
-    std::vector<std::vector<int64_t>> new_rows;
-    std::vector<int64_t> old2new(nf);
-    int64_t start = -1;
-    for (int64_t J = 0; J < nf; ++J) {
-      if (start < 0) start = J;
-      if (absorbed[J]) continue;
-      // group [start, J]: columns sn_ptr[start] .. sn_ptr[J+1]-1, rows = own columns + rows of J
-      std::vector<int64_t> rows;
-      rows.reserve((size_t)(sn_ptr[J] - sn_ptr[start]) + sn_rows[J].size());
-      for (int64_t col = sn_ptr[start]; col < sn_ptr[J]; ++col) rows.push_back(col);
-      rows.insert(rows.end(), sn_rows[J].begin(), sn_rows[J].end());
-      for (int64_t K = start; K <= J; ++K) old2new[K] = (int64_t)new_ptr.size();
-      new_ptr.push_back(sn_ptr[start]);
-      new_rows.push_back(std::move(rows));
-      for (int64_t K = start; K <= J; ++K) std::vector<int64_t>().swap(sn_rows[K]);
-      start = -1;
+    new_ptr.reserve(rpost.size() + 1);
+    int64_t next = 0;
+    for (int64_t R : rpost) {
+      new_ptr.push_back(next);
+      for (int64_t J : group[R])
+        for (int64_t col = sn_ptr[J]; col < sn_ptr[J + 1]; ++col) newpos[col] = next++;
     }
     new_ptr.push_back(N);
-    for (int64_t j = 0; j < N; ++j) sn_of[j] = old2new[sn_of[j]];
+    std::vector<std::vector<int64_t>> new_rows(rpost.size());
+    for (size_t t = 0; t < rpost.size(); ++t) {
+      const int64_t R = rpost[t];
+      std::vector<int64_t>& rows = new_rows[t];
+      rows.reserve((size_t)gf[R]);
+      for (int64_t col = new_ptr[t]; col < new_ptr[t + 1]; ++col) rows.push_back(col);
+      const int64_t ownc = sn_ptr[R + 1] - sn_ptr[R];
+      for (size_t k = (size_t)ownc; k < sn_rows[R].size(); ++k) rows.push_back(newpos[sn_rows[R][k]]);
+      std::sort(rows.begin() + (new_ptr[t + 1] - new_ptr[t]), rows.end());
+      std::vector<int64_t>().swap(sn_rows[R]);
+    }
+    // relabel the order and the column tree
+    std::vector<int64_t> perm2(N), par2(N, -1);
+    for (int64_t j = 0; j < N; ++j) perm2[newpos[j]] = sy.perm[j];
+    for (int64_t j = 0; j < N; ++j) par2[newpos[j]] = par[j] >= 0 ? newpos[par[j]] : -1;
+    sy.perm.swap(perm2);
+    for (int64_t t = 0; t < N; ++t) sy.iperm[sy.perm[t]] = t;
+    par.swap(par2);
     sn_ptr.swap(new_ptr);
     sn_rows.swap(new_rows);
+    for (int64_t t = 0; t + 1 < (int64_t)sn_ptr.size(); ++t)
+      for (int64_t col = sn_ptr[t]; col < sn_ptr[t + 1]; ++col) sn_of[col] = t;
   }
   sy.nsn = (int64_t)sn_rows.size();
   sy.sn_ptr = sn_ptr;
@@ -542,16 +607,52 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
     if (sy.sn_parent[J] >= 0) children[sy.sn_parent[J]].push_back(J);
   mp.fa_lev_ptr.assign(sy.nlev + 1, 0);
   mp.sv_lev_ptr.assign(sy.nlev + 1, 0);
+  mp.px_lev_ptr.assign(sy.nlev + 1, 0);
+  mp.px_round_ptr.assign(1, 0);
+  mp.rel_off.assign(sy.nsn, -1);
+  // children pushed by relative indices: the (up to kMaxPush) largest update
+  // blocks of each front with at least kPushRows rows
+  constexpr int64_t kPushRows = 64, kMaxPush = 4;
+  std::vector<std::vector<int64_t>> pushed(sy.nsn);
+  std::vector<char> is_pushed(sy.nsn, 0);
+  auto upd_rows = [&](int64_t J) { return (sy.row_ptr[J + 1] - sy.row_ptr[J]) - (sy.sn_ptr[J + 1] - sy.sn_ptr[J]); };
+  for (int64_t P = 0; P < sy.nsn; ++P) {
+    std::vector<int64_t> big;
+    for (int64_t ch : children[P])
+      if (upd_rows(ch) >= kPushRows) big.push_back(ch);
+    std::stable_sort(big.begin(), big.end(), [&](int64_t a, int64_t b) { return upd_rows(a) > upd_rows(b); });
+    if ((int64_t)big.size() > kMaxPush) big.resize(kMaxPush);
+    for (int64_t ch : big) is_pushed[ch] = 1;
+    pushed[P] = std::move(big);
+  }
   std::vector<std::pair<int64_t, int64_t>> contrib;  // (target, source)
   for (int64_t l = 0; l < sy.nlev; ++l) {
+    int64_t rounds = 0;
+    for (int64_t t = sy.lev_ptr[l]; t < sy.lev_ptr[l + 1]; ++t) rounds = std::max<int64_t>(rounds, (int64_t)pushed[sy.lev_sn[t]].size());
+    for (int64_t k = 0; k < rounds; ++k) {
+      for (int64_t t = sy.lev_ptr[l]; t < sy.lev_ptr[l + 1]; ++t) {
+        const int64_t P = sy.lev_sn[t];
+        if ((int64_t)pushed[P].size() > k) mp.px_child.push_back(pushed[P][k]);
+      }
+      mp.px_round_ptr.push_back((int64_t)mp.px_child.size());
+    }
+    mp.px_lev_ptr[l + 1] = mp.px_lev_ptr[l] + rounds;
     for (int64_t t = sy.lev_ptr[l]; t < sy.lev_ptr[l + 1]; ++t) {
       const int64_t P = sy.lev_sn[t];
       if (children[P].empty()) continue;
       set_loc(P);
       const int64_t fP = sy.row_ptr[P + 1] - sy.row_ptr[P];
-      // factor: U_c entries (a >= b) -> F_P(loc(row a), loc(row b))
+      for (int64_t ch : pushed[P]) {
+        const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+        const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+        const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+        mp.rel_off[ch] = (int64_t)mp.rel.size();
+        for (int64_t a = c; a < f; ++a) mp.rel.push_back((int32_t)loc[rr[a]]);
+      }
+      // factor: U_c entries (a >= b) -> F_P(loc(row a), loc(row b)), for the children not pushed
       contrib.clear();
       for (int64_t ch : children[P]) {
+        if (is_pushed[ch]) continue;
         const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
         const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
         const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];

@@ -1,0 +1,123 @@
+"""Full-size workloads on the GPU, in the configuration the benchmark times.
+
+The dense oracle cannot run at these sizes (the KKT matrices have order 8 600
+to 600 000), so each solve is checked against what holds at any size:
+  * the planted optimum: every problem is built from a chosen complementary
+    (x*, s*, z*), so the optimal value is known -- objective to 1e-6 relative;
+  * the solver's termination tests at eps_feas = 1e-8 (residuals and gap);
+  * the returned s in K and z in K* (cone membership, per family), and
+    complementarity s'z small;
+  * sampled outputs recomputed one by one by the oracle: the scaling matrix
+    H of a random sample of cones at the returned point (Appendix A of the
+    paper: NT for SOC/PSD, the BFGS update for exp/pow), against the
+    library's step-level entry point on the same cones.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import cones as C
+
+pytestmark = pytest.mark.gpu
+
+clr = pytest.importorskip("paper_2412_19027_gb300.clr")
+from paper_2412_19027_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2412_19027_gb300 import build
+    build.build()
+    clr._lib()
+
+
+def _blocks(cones, v):
+    out, off = [], 0
+    for (t, d, a) in cones:
+        out.append((t, d, a, v[off:off + d]))
+        off += d
+    return out
+
+
+def _check_cones(cones, s, z, tol):
+    for (t, d, a, sv), (_, _, _, zv) in zip(_blocks(cones, s), _blocks(cones, z)):
+        if t == C.ZERO:
+            assert np.abs(sv).max() <= tol
+        elif t == C.NONNEG:
+            assert sv.min() >= -tol and zv.min() >= -tol
+        elif t == C.SOC:
+            assert sv[0] - np.linalg.norm(sv[1:]) >= -tol and zv[0] - np.linalg.norm(zv[1:]) >= -tol
+        elif t == C.PSD:
+            assert np.linalg.eigvalsh(C.smat(sv)).min() >= -tol
+            assert np.linalg.eigvalsh(C.smat(zv)).min() >= -tol
+
+
+def _sampled_scalings(cones, s, z, mu, rng, k=40):
+    """H of a random sample of non-zero cones at the final iterate (pushed a
+    little into the interior so that every scaling is defined)."""
+    idx = [i for i, (t, d, a) in enumerate(cones) if t not in (C.ZERO, C.NONNEG)]
+    if not idx:
+        return
+    pick = sorted(rng.choice(idx, min(k, len(idx)), replace=False))
+    blocks_s, blocks_z = _blocks(cones, s), _blocks(cones, z)
+    sub, ss, zz = [], [], []
+    for i in pick:
+        t, d, a, sv = blocks_s[i]
+        zv = blocks_z[i][3]
+        e = C.central_point(t, d, a)  # in the interior of both K and K*
+        sub.append((t, d, a))
+        ss.append(sv + 0.1 * e)
+        zz.append(zv + 0.1 * e)
+    ss, zz = np.concatenate(ss), np.concatenate(zz)
+    H = clr.clr_cones_scaling(sub, ss, zz, mu)
+    off = 0
+    for (t, d, a), Hg in zip(sub, H):
+        sv, zv = ss[off:off + d], zz[off:off + d]
+        off += d
+        if t in (C.EXP, C.POW):
+            Href = C.bfgs_scaling(t, sv, zv, mu, a)
+        else:
+            Href = C.nt_scaling(t, sv, zv)["H"]
+        np.testing.assert_allclose(Hg, Href, rtol=1e-8, atol=1e-10 * np.abs(Href).max())
+
+
+def _solve_full(prob, bits):
+    st = clr.clr_default_settings(bits, ir_stop_ratio=5.0)
+    s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+    s.solve()
+    x, sl, z, info = s.solution()
+    s.free()
+    assert info["status_name"] == "SOLVED", info
+    f_star = prob.objective(prob.x_star)
+    f = prob.objective(x)
+    assert abs(f - f_star) <= 1e-6 * max(1.0, abs(f_star)), (f, f_star)
+    # the termination tests of the solver at eps_feas = 1e-8
+    scale_p = max(1.0, np.abs(prob.b).max() + np.abs(x).max() + np.abs(sl).max())
+    scale_d = max(1.0, np.abs(prob.q).max() + np.abs(x).max() + np.abs(z).max())
+    assert info["res_primal"] <= 1e-8 * scale_p and info["res_dual"] <= 1e-8 * scale_d, info
+    # recomputed on the host from the returned point
+    Pf = prob.P + sp.triu(prob.P, 1).T
+    rp = prob.A @ x + sl - prob.b
+    rd = Pf @ x + prob.A.T @ z + prob.q
+    assert np.abs(rp).max() <= 1e-6 * scale_p and np.abs(rd).max() <= 1e-6 * scale_d
+    _check_cones(prob.cones, sl, z, 1e-7 * max(1.0, np.abs(sl).max(), np.abs(z).max()))
+    assert abs(sl @ z) <= 1e-6 * max(1.0, abs(f_star))
+    return x, sl, z, info
+
+
+@pytest.mark.parametrize("bits", [64, 32])
+def test_mixed_cone_n2000_m6600(bits):
+    prob = W.mixed_cone(0)
+    x, s, z, info = _solve_full(prob, bits)
+    _sampled_scalings(prob.cones, s, z, info["mu"] + 1e-3, np.random.default_rng(0))
+
+
+def test_banded_lp_n200000_m400000_fp32():
+    prob = W.banded_lp(0)
+    _solve_full(prob, 32)
+
+
+def test_psd_batch_2000x10_n20000_fp32():
+    prob = W.psd_batch(0)
+    x, s, z, info = _solve_full(prob, 32)
+    _sampled_scalings(prob.cones, s, z, info["mu"] + 1e-3, np.random.default_rng(1))
