@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--factor-bits", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--factor-bits", type=int, default=32, choices=[16, 32, 64])
     ap.add_argument("--ir-stop-ratio", type=float, default=5.0,
                     help="refinement stall test (0 = the paper's rule only: tolerance or T_max)")
     ap.add_argument("--no-graph", action="store_true",

@@ -88,7 +88,9 @@ typedef struct {
   double eps_feas;        /* termination tolerance (Eq. termination-check); default 1e-8 */
   double eps_inf;         /* infeasibility tolerance (Eq. infeasibility-check); 1e-8 */
   int32_t max_iter;       /* 200 */
-  int32_t factor_bits;    /* LDL^T precision: 64 (FP64) or 32 (FP32) (Sec. 3.6) */
+  int32_t factor_bits;    /* LDL^T precision (Sec. 3.6): 64 (FP64), 32 (FP32), or 16: FP32 factor whose
+                             large-front updates multiply BF16-rounded operands on the tensor cores with
+                             FP32 accumulation (the 16-bit-products variant; defaults as for 32) */
   double static_reg;      /* delta_s: 1e-8 (FP64), sqrt(eps_32) ~ 3.45e-4 (FP32) (Sec. 3.6) */
   double static_reg_dyn;  /* delta_d in delta = delta_s + delta_d max|K_ii|: eps_64^2 */
   double dyn_reg_eps;     /* pivot threshold of dynamic regularisation: 1e-13 (FP64), 1e-6 (FP32) */
@@ -107,6 +109,10 @@ typedef struct {
   double min_step;        /* 1e-10: smaller combined steps end the solve */
   int32_t use_graph;      /* 1: replay each iteration as a captured CUDA graph */
   int32_t verbose;        /* 0 */
+  int32_t fp64_escalation; /* factor_bits 32/16 only, 1 (default): when the refinement of a KKT solve ends with
+                              ||r||_inf > 1e-4 max(1, ||rhs||_inf) (or NaN) the iteration is not taken and the solve
+                              goes on with the FP64 factor and the FP64 regularisation defaults (for every problem
+                              of a cohort); 0: never */
 } clr_settings;
 
 typedef struct {
@@ -123,6 +129,8 @@ typedef struct {
   double mu, tau, kappa;   /* complementarity measure (scaled space) and the embedding scalars */
   double setup_s;          /* host wall time of clr_setup */
   double solve_s;          /* host wall time of the last clr_solve */
+  int32_t fp64_from_iter;  /* iteration from which the FP64 factor was used after an escalation, -1 if none */
+  int32_t pad;
 } clr_info;
 
 /* Statistics of the symbolic KKT analysis done at setup. */
@@ -157,7 +165,7 @@ typedef struct {
 
 typedef struct clr_solver clr_solver;
 
-/* Fill *out with the defaults for a factorization precision (64 or 32).
+/* Fill *out with the defaults for a factorization precision (64, 32 or 16).
  * CLR_E_INVALID for any other factor_bits or a NULL out. */
 int clr_default_settings(clr_settings* out, int32_t factor_bits);
 
@@ -377,7 +385,7 @@ int clr_cones_combined_ds(const clr_cone* cones, int32_t ncones, const double* s
  * of each pivot (dynamic regularisation replaces a pivot d with
  * sign*dyn_reg_delta when sign*d <= dyn_reg_eps).  No static regularisation
  * is added here.  order: NULL for the library's AMD ordering, else a
- * caller permutation (order[k] = index eliminated k-th).  factor_bits 64/32.
+ * caller permutation (order[k] = index eliminated k-th).  factor_bits 64/32/16.
  * x_out = K^{-1} rhs (no refinement); D_out (optional, N): pivots in the
  * caller's numbering. */
 int clr_ldl_solve(const clr_csc* K_lower, const double* signs, const int64_t* order, int32_t factor_bits,

@@ -42,7 +42,8 @@ class clr_settings(C.Structure):
                 ("equilibrate", C.c_int32),
                 ("ruiz_passes", C.c_int32), ("scale_min", C.c_double), ("scale_max", C.c_double),
                 ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
-                ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32)]
+                ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32),
+                ("fp64_escalation", C.c_int32)]
 
 
 class clr_info(C.Structure):
@@ -50,7 +51,8 @@ class clr_info(C.Structure):
                 ("dyn_reg_hits", C.c_int32), ("obj_primal", C.c_double), ("obj_dual", C.c_double),
                 ("res_primal", C.c_double), ("res_dual", C.c_double), ("gap_abs", C.c_double),
                 ("gap_rel", C.c_double), ("mu", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
-                ("setup_s", C.c_double), ("solve_s", C.c_double)]
+                ("setup_s", C.c_double), ("solve_s", C.c_double), ("fp64_from_iter", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class clr_symbolic_stats(C.Structure):

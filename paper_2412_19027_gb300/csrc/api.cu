@@ -22,7 +22,7 @@ using clr::Solver;
 extern "C" {
 
 int clr_default_settings(clr_settings* out, int32_t factor_bits) {
-  if (!out || (factor_bits != 64 && factor_bits != 32)) return CLR_E_INVALID;
+  if (!out || (factor_bits != 64 && factor_bits != 32 && factor_bits != 16)) return CLR_E_INVALID;
   const bool low = factor_bits != 64;
   const double eps64 = 2.220446049250313e-16;
   const double eps32 = 1.1920928955078125e-07;
@@ -49,12 +49,13 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.min_step = 1e-10;
   s.use_graph = 1;
   s.verbose = 0;
+  s.fp64_escalation = 1;
   *out = s;
   return CLR_OK;
 }
 
 static int check_settings(const clr_settings& s) {
-  if (s.factor_bits != 64 && s.factor_bits != 32) return CLR_E_INVALID;
+  if (s.factor_bits != 64 && s.factor_bits != 32 && s.factor_bits != 16) return CLR_E_INVALID;
   if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0 ||
       !(s.ir_stop_ratio >= 0))
     return CLR_E_INVALID;

@@ -2,8 +2,7 @@
 //
 // Panel p covers pivots K = [k0, k0 + pw), k0 = 64 p.  Three launches per panel:
 //   A  (one CTA per front): LDL^T of the pw x pw diagonal block (32 x 32 blocks
-//      factored and inverted by one warp in registers), its pivots, and
-//      Linv = L_KK^{-1};
+//      factored and inverted by one warp), its pivots, and Linv = L_KK^{-1};
 //   B  L_IK = F_IK L_KK^{-T} D_K^{-1} for the rows I below K, as the product
 //      F_IK Linv^T scaled by D^{-1}; the same launch finalises the E rows of
 //      this panel: E_KC <- Linv E_KC (C < K) and E_KK = Linv;
@@ -11,6 +10,10 @@
 //      and the augmented rows E_IC -= L_IK E_KC for C <= K.
 // After the last panel E = L^{-1} [I; 0].  Forward solve: y = E_top w1,
 // u = w2 + E_bottom w1; backward: x1 = E^T [D^{-1} y; x2].
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "bigfront.cuh"
 
 namespace clr {
@@ -44,155 +47,96 @@ __device__ __forceinline__ T reg_pivot(T d, int sgn, T eps, T delta, bool* hit) 
 // ------------------------------------------------------------------ A: diagonal block
 constexpr unsigned FULLMASK = 0xffffffffu;
 
-// LDL^T of a 32 x 32 symmetric block held by one warp in registers: lane i
-// holds row i (r[j], j <= i; zero above).  Right-looking: pivot k is lane k's
-// r[k]; every lane updates its row with the unscaled column k broadcast from
-// the lanes below (S_ij -= L_ik S_jk), then scales its multiplier.  A pivot
-// with the wrong sign or magnitude <= eps is replaced by sign * delta (dynamic
-// regularisation).  Afterwards r[j] = L_ij (j < i) and r[i] = d_i.  Rows >= n
-// are padding (zero rows).
-template <typename T>
-__device__ __forceinline__ void warp_ldl32(T (&r)[32], int n, const int8_t* sgn, T eps, T delta, int* nhit) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < n) {
-      T d = __shfl_sync(FULLMASK, r[k], k);
-      const T sg = (T)sgn[k];
-      if (sg * d <= eps) {
-        d = sg * delta;
-        ++*nhit;
-      }
-      const T lik = (lane > k) ? r[k] / d : (T)0;
-#pragma unroll
-      for (int j = k + 1; j < 32; ++j) {
-        const T sjk = __shfl_sync(FULLMASK, r[k], j);
-        if (lane >= j) r[j] -= lik * sjk;
-      }
-      if (lane > k) r[k] = lik;
-      else if (lane == k) r[k] = d;
-    }
-  }
-}
-
-// Column `lane` of the inverse of the unit lower triangle whose rows are held
-// as above (forward substitution with the rows broadcast from their lanes).
-template <typename T>
-__device__ __forceinline__ void warp_inv_unit32(const T (&r)[32], T (&x)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    T acc = (i == lane) ? (T)1 : (T)0;
-#pragma unroll
-    for (int l = 0; l < i; ++l) acc -= __shfl_sync(FULLMASK, r[l], i) * x[l];
-    x[i] = acc;
-  }
-}
-
-// Diagonal block of panel p (pw <= 64 pivots) as 2 x 2 blocks of 32:
-//   A11 = L11 D1 L11^T by warp 0 in registers, with L11^{-1};
-//   W21 = A21 L11^{-T} (= L21 D1), L21 = W21 D1^{-1};  A22 -= L21 W21^T;
-//   A22 = L22 D2 L22^T by warp 0, with L22^{-1};
-//   (L^{-1})_21 = -L22^{-1} L21 L11^{-1}.
+// Diagonal block of panel p: the pw x pw (<= 64) block by the whole CTA,
+// right-looking with one barrier per pivot.  Each thread owns up to kSlots
+// entries of the lower triangle (registers), and the same entries of
+// X = L^{-1}, built alongside by applying the elimination to the identity:
+// pivot k does S_ij -= L_ik S_jk (i >= j > k, L_ik = S_ik / d_k) and
+// X_ij -= L_ik X_kj (i > k >= j); the pivot column of S and row k of X go
+// through shared memory (double buffered).  A pivot with the wrong sign or
+// magnitude <= eps is replaced by sign * delta (dynamic regularisation).
 // Outputs: L (unit lower, d on the diagonal) into the front, pivots to Dp, and
 // Linv = L^{-1} (64 x 64, column-major, zero padded).
+constexpr int kTri = NB * (NB + 1) / 2;
+constexpr int kSlots = (kTri + 255) / 256;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_bf_diag(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F,
                                                  T* __restrict__ Dp, T* __restrict__ Linv,
                                                  const int8_t* __restrict__ dsign, double eps_d, double delta_d,
                                                  int* hits, const int* skip) {
   if (skip && *skip) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* S = reinterpret_cast<T*>(smraw);  // NB x LD: the block (lower part); rows 0..31 of cols 32..63 as scratch
-  T* Lo = S + NB * LD;                 // NB x LD: L, d on the diagonal
-  T* Li = Lo + NB * LD;                // NB x LD: L^{-1}
+  __shared__ T col[2][NB], xrow[2][NB], dd[NB];
   __shared__ int8_t sgn[NB];
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
   const int64_t f = bf.f[b], c = bf.c[b], k0 = (int64_t)p * NB;
   const int pw = (int)min((int64_t)NB, c - k0);
-  const int cw0 = min(32, pw), cw1 = pw - cw0;
   T* G = F + bf.goff[b];
   const int64_t kp = bf.k0pos[b] + k0;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x;
   const T eps = (T)eps_d, delta = (T)delta_d;
-  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx % NB, j = idx / NB;
-    S[i * LD + j] = (i < pw && j < pw && i >= j) ? G[(k0 + i) + (k0 + j) * f] : (T)0;
-    Lo[i * LD + j] = (T)0;
-    Li[i * LD + j] = (T)0;
+  T v[kSlots], x[kSlots];
+  int ri[kSlots], cj[kSlots];
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m) {
+    const int e = tid + 256 * m;
+    int i = -1, j = -1;
+    if (e < kTri) {  // column-major enumeration of the lower triangle: column j starts at j NB - j (j - 1) / 2
+      const float w = (float)(2 * NB + 1);
+      j = (int)((w - sqrtf(w * w - 8.0f * (float)e)) * 0.5f);
+      while (j > 0 && j * NB - j * (j - 1) / 2 > e) --j;
+      while ((j + 1) * NB - (j + 1) * j / 2 <= e) ++j;
+      i = j + (e - (j * NB - j * (j - 1) / 2));
+    }
+    ri[m] = i;
+    cj[m] = j;
+    v[m] = (i >= 0 && i < pw && j < pw) ? G[(k0 + i) + (k0 + j) * f] : (T)0;
+    x[m] = (i >= 0 && i == j) ? (T)1 : (T)0;
+    if (j == 0) col[0][i] = v[m];
+    if (i == 0) xrow[0][j] = x[m];
   }
   if (tid < NB) sgn[tid] = tid < pw ? dsign[kp + tid] : (int8_t)1;
   __syncthreads();
   int nhit = 0;
-  if (wid == 0) {
-    T r[32], x[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) r[j] = S[lane * LD + j];
-    warp_ldl32(r, cw0, sgn, eps, delta, &nhit);
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j <= lane) Lo[lane * LD + j] = r[j];
-    warp_inv_unit32(r, x);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) Li[i * LD + lane] = x[i];
-  }
-  __syncthreads();
-  if (cw1 > 0) {
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
-      T acc = (T)0;
-      for (int l = 0; l <= j; ++l) acc += S[(32 + i) * LD + l] * Li[j * LD + l];
-      S[i * LD + 32 + j] = acc;                    // W21
-      Lo[(32 + i) * LD + j] = acc / Lo[j * LD + j];  // L21
+  for (int k = 0; k < pw; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    T d = col[cur][k];
+    const T sg = (T)sgn[k];
+    const bool hit = sg * d <= eps;
+    if (hit) d = sg * delta;
+    const T inv = (T)1 / d;
+    if (tid == 0) {
+      dd[k] = d;
+      nhit += hit ? 1 : 0;
     }
-    __syncthreads();
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
-      if (i < j) continue;
-      T acc = (T)0;
-      for (int l = 0; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * S[j * LD + 32 + l];
-      S[(32 + i) * LD + 32 + j] -= acc;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      T r[32], x[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) r[j] = (j <= lane) ? S[(32 + lane) * LD + 32 + j] : (T)0;
-      warp_ldl32(r, cw1, sgn + 32, eps, delta, &nhit);
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j <= lane) Lo[(32 + lane) * LD + 32 + j] = r[j];
-      warp_inv_unit32(r, x);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) Li[(32 + i) * LD + 32 + lane] = x[i];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {  // X = L21 L11^{-1} (scratch in S)
-      const int i = idx % 32, j = idx / 32;
-      T acc = (T)0;
-      for (int l = j; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * Li[l * LD + j];
-      S[i * LD + 32 + j] = acc;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
-      T acc = (T)0;
-      for (int l = 0; l <= i; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + 32 + j];
-      Li[(32 + i) * LD + j] = -acc;
+    for (int m = 0; m < kSlots; ++m) {
+      const int i = ri[m], j = cj[m];
+      if (i < 0) continue;
+      if (j == k) {
+        if (i > k) G[(k0 + i) + (k0 + k) * f] = v[m] * inv;  // L_ik
+      } else if (j > k) {
+        v[m] -= (col[cur][i] * inv) * col[cur][j];
+        if (j == k + 1) col[nxt][i] = v[m];
+      }
+      if (i > k && j <= k) x[m] -= (col[cur][i] * inv) * xrow[cur][j];
+      if (i == k + 1) xrow[nxt][j] = x[m];
     }
     __syncthreads();
   }
   if (tid == 0 && nhit) atomicAdd(hits, nhit);
-  for (int idx = tid; idx < pw * pw; idx += blockDim.x) {
-    const int i = idx % pw, j = idx / pw;
-    if (i >= j) G[(k0 + i) + (k0 + j) * f] = Lo[i * LD + j];
+  for (int i = tid; i < pw; i += blockDim.x) {
+    G[(k0 + i) + (k0 + i) * f] = dd[i];
+    Dp[kp + i] = dd[i];
   }
-  for (int i = tid; i < pw; i += blockDim.x) Dp[kp + i] = Lo[i * LD + i];
   T* LB = Linv + (b * 2 + (p & 1)) * (int64_t)(NB * NB);
-  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx % NB, j = idx / NB;
-    LB[i + j * NB] = (i < pw && j < pw) ? Li[i * LD + j] : (T)0;
+#pragma unroll
+  for (int m = 0; m < kSlots; ++m) {
+    const int i = ri[m], j = cj[m];
+    if (i < 0) continue;
+    LB[i + j * NB] = (i < pw && j < pw) ? x[m] : (T)0;
+    if (i != j) LB[j + i * NB] = (T)0;  // upper triangle
   }
 }
 
@@ -222,7 +166,8 @@ __global__ void __launch_bounds__(256) k_bf_trsm(BigFrontDev bf, WorkList wl, in
     T* G = F + bf.goff[b];
     const int64_t r0 = k0 + pw + (int64_t)kTrsmRows * q;
     const int nr = (int)min((int64_t)kTrsmRows, f - r0);
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+#pragma unroll 8
+    for (int idx = tid; idx < NB * NB; idx += 256) {
       const int i = idx % NB, j = idx / NB;
       Ls[i * LD + j] = LB[i + j * NB];
       Xs[i * LD + j] = (i < nr && j < pw) ? G[(r0 + i) + (k0 + j) * f] : (T)0;
@@ -337,7 +282,8 @@ __global__ void __launch_bounds__(64) k_bf_update(BigFrontDev bf, WorkList wl, i
     const int64_t bj = q - bi * (bi + 1) / 2;
     i0 = t0 + bi * NB;
     j0 = t0 + bj * NB;
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+#pragma unroll 16
+    for (int idx = tid; idx < NB * NB; idx += 64) {
       const int r = idx % NB, l = idx / NB;
       const int64_t ia = i0 + r, ib = j0 + r;
       Ak[l * LDK + r] = (l < pw && ia < f) ? G[ia + (k0 + l) * f] : (T)0;
@@ -349,7 +295,8 @@ __global__ void __launch_bounds__(64) k_bf_update(BigFrontDev bf, WorkList wl, i
     i0 = t0 + bi * NB;
     colbase = cb * NB;
     if (cb == p) ncols = pw;
-    for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+#pragma unroll 16
+    for (int idx = tid; idx < NB * NB; idx += 64) {
       const int r = idx % NB, l = idx / NB;
       const int64_t ia = i0 + r;
       Ak[l * LDK + r] = (l < pw && ia < f) ? G[ia + (k0 + l) * f] : (T)0;
@@ -397,6 +344,165 @@ __global__ void __launch_bounds__(64) k_bf_update(BigFrontDev bf, WorkList wl, i
       }
     }
   }
+}
+
+// ------------------------------------------------------------------ C on the tensor cores
+// The same updates as k_bf_update with 16-bit products: 128 x 64 output tiles,
+// operands rounded to BF16 and staged K-major in shared memory as 8-row x
+// 16-byte core matrices (no swizzle; core matrix (row group g, k group h) at
+// g * 1024 + h * 128 bytes), tcgen05.mma kind::f16 (M = 128, N = 64, 4 x K=16)
+// accumulating in FP32 in tensor memory (64 columns), then F -= acc in FP32.
+// One thread issues the MMAs; completion is signalled on an mbarrier whose
+// wait is bounded (on time-out the tile is skipped and *err set).
+namespace {
+constexpr uint32_t kTcLBO = 128, kTcSBO = 1024;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((kTcLBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((kTcSBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle, base offset 0
+  return d;
+}
+__device__ __forceinline__ uint32_t tc_off(int r, int k) {  // byte offset of element (r, k) of a 16-bit tile
+  return (uint32_t)((r >> 3) * kTcSBO + (k >> 3) * kTcLBO + (r & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint16_t to_bf16(float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&h);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(128) k_bf_update_tc(BigFrontDev bf, WorkList wl, int p, float* __restrict__ F,
+                                                      float* __restrict__ E, const float* __restrict__ Dp, int* err,
+                                                      const int* skip) {
+  if (skip && *skip) return;
+  __shared__ __align__(1024) uint8_t sA[128 * NB * 2];
+  __shared__ __align__(1024) uint8_t sB[64 * NB * 2];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  int64_t b, q;
+  locate(wl, blockIdx.x, &b, &q);
+  const int64_t f = bf.f[b], c = bf.c[b], k0 = (int64_t)p * NB;
+  const int pw = (int)min((int64_t)NB, c - k0);
+  const int64_t t0 = k0 + pw, nr = f - t0;
+  const int64_t n128 = (nr + 127) / 128, n64 = (nr + 63) / 64;
+  float* G = F + bf.goff[b];
+  float* Eb = E + bf.eoff[b];
+  const float* Dk = Dp + bf.k0pos[b] + k0;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  bool etile = true;
+  int64_t bi = 0, bj = 0;
+  for (int64_t j = 0; j < n64; ++j) {
+    const int64_t cnt = n128 - j / 2;
+    if (q < cnt) {
+      bi = j / 2 + q;
+      bj = j;
+      etile = false;
+      break;
+    }
+    q -= cnt;
+  }
+  int64_t cb = 0;
+  if (etile) {
+    bi = q / (p + 1);
+    cb = q % (p + 1);
+  }
+  const int64_t i0 = t0 + 128 * bi;
+  const int64_t j0 = etile ? cb * NB : t0 + 64 * bj;  // first output column
+  const int ncols = etile ? (cb == p ? pw : NB) : (int)min((int64_t)64, f - j0);
+  // stage A = L rows i0 .. i0+127 of the panel, B = D L rows j0.. (trailing) or E_KC (E tile)
+  for (int e = tid; e < 128 * NB; e += blockDim.x) {
+    const int r = e % 128, k = e / 128;
+    const int64_t i = i0 + r;
+    const float v = (k < pw && i < f) ? G[i + (k0 + k) * f] : 0.f;
+    *reinterpret_cast<uint16_t*>(sA + tc_off(r, k)) = to_bf16(v);
+  }
+  if (!etile) {
+    for (int e = tid; e < 64 * NB; e += blockDim.x) {
+      const int r = e % 64, k = e / 64;
+      const int64_t j = j0 + r;
+      const float v = (k < pw && j < f) ? G[j + (k0 + k) * f] * Dk[k] : 0.f;
+      *reinterpret_cast<uint16_t*>(sB + tc_off(r, k)) = to_bf16(v);
+    }
+  } else {
+    for (int e = tid; e < 64 * NB; e += blockDim.x) {
+      const int k = e % 64, r = e / 64;  // consecutive k: consecutive rows of E
+      const float v = (k < pw && r < ncols) ? Eb[(k0 + k) + (j0 + r) * f] : 0.f;
+      *reinterpret_cast<uint16_t*>(sB + tc_off(r, k)) = to_bf16(v);
+    }
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(64));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    // D F32 (bit 4), A and B BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at 17, M >> 4 at 24
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    for (int ks = 0; ks < NB / 16; ++ks) {
+      const uint64_t ad = tc_desc(smem_addr(sA) + ks * 2 * kTcLBO);
+      const uint64_t bd = tc_desc(smem_addr(sB) + ks * 2 * kTcLBO);
+      const uint32_t acc = ks > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_addr(&mbar)));
+  }
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 24) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(&mbar)), "r"(0));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (!done) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    const int64_t i = i0 + 32 * wid + lane;
+    for (int cc = 0; cc < 64; cc += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * wid) << 16) + (uint32_t)cc;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (i < f) {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int col = cc + jj;
+          if (col >= ncols) continue;
+          const int64_t j = j0 + col;
+          if (!etile) {
+            if (i >= j) G[i + j * f] -= __uint_as_float(v[jj]);
+          } else {
+            Eb[i + j * f] -= __uint_as_float(v[jj]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (wid == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
 }
 
 // ------------------------------------------------------------------ solves
@@ -474,7 +580,6 @@ size_t smem_diag() { return 0; }
 
 template <typename T>
 int BigFrontOps<T>::setup_attributes() {
-  CLR_CUDA(cudaFuncSetAttribute(k_bf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LDK * sizeof(T)));
   (void)smem_diag;
@@ -483,14 +588,22 @@ int BigFrontOps<T>::setup_attributes() {
 
 template <typename T>
 int BigFrontOps<T>::factor_level(cudaStream_t st, const BigFrontDev& bf, const BigLevelPlan& plan, T* F, T* E, T* Dp,
-                                 T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip) {
-  const size_t s2 = 2 * NB * LD * sizeof(T), s3 = 3 * NB * LD * sizeof(T), su = 2 * NB * LDK * sizeof(T);
+                                 T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip,
+                                 bool tc16, int* err) {
+  const size_t s2 = 2 * NB * LD * sizeof(T), su = 2 * NB * LDK * sizeof(T);
   for (size_t p = 0; p < plan.A.size(); ++p) {
     if (plan.A[p].nblocks > 0)
-      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, s3, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
+      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, 0, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
                                                                   hits, skip);
     if (plan.B[p].nblocks > 0)
       k_bf_trsm<T><<<(unsigned)plan.B[p].nblocks, 256, s2, st>>>(bf, plan.B[p], (int)p, F, E, Dp, Linv, skip);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc16) {
+        if (plan.Ctc[p].nblocks > 0)
+          k_bf_update_tc<<<(unsigned)plan.Ctc[p].nblocks, 128, 0, st>>>(bf, plan.Ctc[p], (int)p, F, E, Dp, err, skip);
+        continue;
+      }
+    }
     if (plan.C[p].nblocks > 0)
       k_bf_update<T><<<(unsigned)plan.C[p].nblocks, 64, su, st>>>(bf, plan.C[p], (int)p, F, E, Dp, skip);
   }

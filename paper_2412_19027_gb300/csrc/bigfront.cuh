@@ -38,14 +38,18 @@ struct WorkList {
 // Host description of the big-front launches of one level.
 struct BigLevelPlan {
   std::vector<WorkList> A, B, C;  // per panel step p (B/C may be empty lists)
+  std::vector<WorkList> Ctc;      // C as 128 x 64 tensor-core tiles (16-bit products)
   WorkList fwd, bwd;
 };
 
 template <typename T>
 struct BigFrontOps {
   static int setup_attributes();
+  // tc16: trailing and E updates on the tensor cores with BF16 operands and FP32
+  // accumulation (T = float only); err: set to 1 if a tensor-core wait ran out.
   static int factor_level(cudaStream_t st, const BigFrontDev& bf, const BigLevelPlan& plan, T* F, T* E, T* Dp,
-                          T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip);
+                          T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip,
+                          bool tc16 = false, int* err = nullptr);
   static int fwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp, T* w,
                  T* ybuf, const int* skip);
   static int bwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp, const T* ybuf,
@@ -62,6 +66,19 @@ __host__ __device__ inline int64_t bf_trsm_blocks(int64_t f, int64_t c, int p) {
 __host__ __device__ inline int64_t bf_fin_blocks(int64_t c, int p) {  // finalisation of the E rows of panel p (same launch)
   if (p < 0 || (int64_t)p * kBfNB >= c) return 0;
   return p + 1;
+}
+// 128 x 64 tensor-core tiles of panel p: trailing tiles (row block bi of 128,
+// column block bj of 64, bi >= bj / 2 so that the tile meets the lower
+// triangle) and E tiles (row blocks of 128 x the p + 1 column blocks of 64).
+__host__ __device__ inline int64_t bf_tc_tiles(int64_t f, int64_t c, int p) {
+  const int64_t k0 = (int64_t)p * kBfNB;
+  if (k0 >= c) return 0;
+  const int64_t pw = (c - k0 < kBfNB) ? c - k0 : kBfNB;
+  const int64_t nr = f - k0 - pw;
+  const int64_t n128 = (nr + 127) / 128, n64 = (nr + 63) / 64;
+  int64_t t = 0;
+  for (int64_t bj = 0; bj < n64; ++bj) t += n128 - bj / 2;
+  return t + n128 * (p + 1);
 }
 __host__ __device__ inline int64_t bf_update_tiles(int64_t f, int64_t c, int p) {
   const int64_t k0 = (int64_t)p * kBfNB;

@@ -288,7 +288,11 @@ __global__ void k_fin_resid(IterScal* scs, const ProbConst* pcs, const double* p
 
 __global__ void k_hmax_reset(IterScal* sc, int64_t B, const int* skip) {
   if (skip && *skip) return;
-  FOR_PROBLEMS(B) sc[p].hmax_bits = 0ull;
+  FOR_PROBLEMS(B) {
+    sc[p].hmax_bits = 0ull;
+    sc[p].ir_fail = 0;
+    sc[p].escalate = 0;
+  }
 }
 
 // static + proportional regularisation
@@ -344,20 +348,25 @@ __global__ void k_set_from(ChunkGrid g, double* __restrict__ dst, const T* __res
 // stop_ratio (the last correction is kept), or after max_steps steps.  A step
 // that made ||r||_inf larger is undone (k_ir_revert) and ends the refinement:
 // the regularised factor is not a contraction for K there.
+// A refinement that ends with ||r||_inf > 1e-4 max(1, ||rhs||_inf) (or NaN) marks
+// the iteration (ir_fail): with a low-precision factor it is then redone in FP64.
 __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double stop_ratio, int max_steps) {
   const double r = bitsd(q.rnorm_bits);
   q.rnorm_bits = 0ull;
   q.ir_revert = 0;
   if (q.ir_skip) return false;
+  const double fail_tol = 1e-4 * fmax(1.0, q.rhs_norm);
   if (r > q.ir_prev) {
     q.ir_revert = 1;
     q.ir_skip = 1;
+    if (!(q.ir_prev <= fail_tol)) q.ir_fail = 1;
     return false;
   }
   const bool stalled = stop_ratio > 0 && !(r * stop_ratio < q.ir_prev);
   q.ir_prev = r;
   if (!(r > abstol + reltol * q.rhs_norm) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
     q.ir_skip = 1;
+    if (!(r <= fail_tol)) q.ir_fail = 1;
     return false;
   }
   q.ir_cur += 1;
@@ -494,6 +503,7 @@ struct StepParams {
   double backtrack, min_step, beta, step_fraction;
   int nonsym;
   int hist_cap;
+  int escalate_on;  // a failed refinement holds the iteration back for a redo in FP64
 };
 
 __global__ void k_step_begin(IterScal* sc, int64_t B, const int* skip) {
@@ -555,6 +565,11 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
+      if (sp.escalate_on && q.ir_fail) {
+        q.escalate = 1;
+        q.alpha_c = 0.0;
+        continue;
+      }
       q.alpha_c = a;
       if (h) {
         h[9] = a;
@@ -575,7 +590,7 @@ __global__ void k_update(ChunkGrid g, double* __restrict__ xz, double* __restric
   int pid;
   bool zp;
   chunk_range(g, &i0, &len, &pid, &zp);
-  if (sc[pid].halt) return;
+  if (sc[pid].halt || sc[pid].escalate) return;
   const double a = frac * sc[pid].alpha_c;
   for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
     xz[i] += a * dir[i];
@@ -583,11 +598,18 @@ __global__ void k_update(ChunkGrid g, double* __restrict__ xz, double* __restric
   }
 }
 
-__global__ void k_fin_update(IterScal* sc, int64_t B, double frac, const int* dyn_hits, const int* skip) {
+// dyn_hits[1]: a tensor-core wait of the factorization ran out (its result is unusable)
+__global__ void k_fin_update(IterScal* sc, int64_t B, double frac, const int* dyn_hits, BatchFlags* bf,
+                             const int* skip) {
   if (skip && *skip) return;
   FOR_PROBLEMS(B) {
     IterScal& q = sc[p];
-    if (q.halt) continue;
+    if (q.halt || q.escalate) continue;
+    if (dyn_hits[1]) {
+      q.status = CLR_NUMERICAL_ERROR;
+      halt_problem(q, bf);
+      continue;
+    }
     const double a = frac * q.alpha_c;
     q.tau += a * q.dtau;
     q.kappa += a * q.dkap;
@@ -726,12 +748,14 @@ void pinned_put(void* p, size_t bytes) {
 }
 
 void Solver::drop_graphs() {
-  if (gexec_) cudaGraphExecDestroy(gexec_);
-  if (graph_) cudaGraphDestroy(graph_);
+  for (int k = 0; k < 2; ++k) {
+    if (gexec_[k]) cudaGraphExecDestroy(gexec_[k]);
+    if (graph_[k]) cudaGraphDestroy(graph_[k]);
+    gexec_[k] = nullptr;
+    graph_[k] = nullptr;
+  }
   if (igexec_) cudaGraphExecDestroy(igexec_);
   if (igraph_) cudaGraphDestroy(igraph_);
-  gexec_ = nullptr;
-  graph_ = nullptr;
   igexec_ = nullptr;
   igraph_ = nullptr;
 }
@@ -827,6 +851,7 @@ int Solver::upload() {
   }
   int rc = ldl_structure_upload(ar_, sy, mp, dsign, st.factor_bits == 64 ? 96 : 128, ls_, &pos_pid);
   if (rc != CLR_OK) return rc;
+  f32_.tc16 = st.factor_bits == 16;
   rc = (st.factor_bits == 64) ? f64_.alloc(ar_, ls_) : f32_.alloc(ar_, ls_);
   if (rc != CLR_OK) return rc;
   // full-K CSR with value indices
@@ -993,10 +1018,14 @@ int Solver::set_stream(void* stream) {
   return CLR_OK;
 }
 
+double Solver::reg_static() const { return escalated_ ? 1e-8 : st.static_reg; }
+double Solver::reg_dyn_eps() const { return escalated_ ? 1e-13 : st.dyn_reg_eps; }
+double Solver::reg_dyn_delta() const { return escalated_ ? 2e-7 : st.dyn_reg_delta; }
+
 int Solver::factor() {
   const int* halt = &bf_->all_halt;
-  if (st.factor_bits == 64) return f64_.factor(stream_, v_.kval, sc_, st.dyn_reg_eps, st.dyn_reg_delta, halt);
-  return f32_.factor(stream_, v_.kval, sc_, st.dyn_reg_eps, st.dyn_reg_delta, halt);
+  if (use64()) return f64_.factor(stream_, v_.kval, sc_, reg_dyn_eps(), reg_dyn_delta(), halt);
+  return f32_.factor(stream_, v_.kval, sc_, reg_dyn_eps(), reg_dyn_delta(), halt);
 }
 
 // sol = K^{-1} rhs by the factor plus iterative refinement on the unregularised K (FP64),
@@ -1014,11 +1043,11 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   k_inf_norm<<<nck, 256, 0, s>>>(cg, rhs, sc_, halt);
   k_ir_begin<<<pg, 128, 0, s>>>(sc_, B, bf_);
   auto revert = [&](cudaStream_t ss) {
-    if (st.factor_bits == 64) k_ir_revert<double><<<nck, 256, 0, ss>>>(cg, sol, f64_.xs, sc_, halt);
+    if (use64()) k_ir_revert<double><<<nck, 256, 0, ss>>>(cg, sol, f64_.xs, sc_, halt);
     else k_ir_revert<float><<<nck, 256, 0, ss>>>(cg, sol, f32_.xs, sc_, halt);
   };
   auto ldl_solve_add = [&](cudaStream_t ss, const double* b, int add) -> int {
-    if (st.factor_bits == 64) {
+    if (use64()) {
       int rc = f64_.solve(ss, b, irs);
       if (rc) return rc;
       k_set_from<double><<<nck, 256, 0, ss>>>(cg, sol, f64_.xs, add, sc_, irs);
@@ -1159,7 +1188,8 @@ int Solver::step_length(bool combined) {
                            halt);
     if (rc) return rc;
   }
-  StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hist_rows_};
+  StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hist_rows_,
+                (st.fp64_escalation && !use64()) ? 1 : 0};
   k_fin_step<<<pg, 128, 0, s>>>(sc_, B, sp, combined ? 1 : 0, v_.hist, bf_, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -1187,7 +1217,7 @@ int Solver::iteration() {
   k_hmax_reset<<<pg, 128, 0, s>>>(sc_, B, halt);
   rc = cones_scaling(s, cd_, v_.s, v_.xz + n, sc_, halt);
   if (rc) return rc;
-  k_fin_delta<<<pg, 128, 0, s>>>(sc_, v_.pc, B, st.static_reg, st.static_reg_dyn, halt);
+  k_fin_delta<<<pg, 128, 0, s>>>(sc_, v_.pc, B, reg_static(), st.static_reg_dyn, halt);
   // ---- step 5: factor ----
   mark(3);
   rc = factor();
@@ -1219,8 +1249,8 @@ int Solver::iteration() {
   if (rc) return rc;
   // ---- step 11: update ----
   k_update<<<nck, 256, 0, s>>>(cg, v_.xz, v_.s, v_.dir, v_.ds, sc_, st.step_fraction, halt);
-  const int* dh = (st.factor_bits == 64) ? f64_.dyn_hits : f32_.dyn_hits;
-  k_fin_update<<<pg, 128, 0, s>>>(sc_, B, st.step_fraction, dh, halt);
+  const int* dh = use64() ? f64_.dyn_hits : f32_.dyn_hits;
+  k_fin_update<<<pg, 128, 0, s>>>(sc_, B, st.step_fraction, dh, bf_, halt);
   mark(5);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -1273,7 +1303,8 @@ int Solver::initialise() {
 
 int Solver::launch_iteration() {
   if (!st.use_graph) return iteration();
-  if (!gexec_) {
+  const int k = (use64() && st.factor_bits != 64) ? 1 : 0;
+  if (!gexec_[k]) {
     CLR_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
     int rc = iteration();
     cudaGraph_t g = nullptr;
@@ -1286,13 +1317,13 @@ int Solver::launch_iteration() {
       set_cuda_error(e, "cudaStreamEndCapture");
       return CLR_E_CUDA;
     }
-    graph_ = g;
-    iter_kernels_ = count_kernel_nodes(graph_);
-    body_kernels_ = ir_nodes_.empty() ? 0 : count_kernel_nodes(ir_nodes_.back());
+    graph_[k] = g;
+    iter_kernels_[k] = count_kernel_nodes(graph_[k]);
+    body_kernels_[k] = ir_nodes_.empty() ? 0 : count_kernel_nodes(ir_nodes_.back());
     ir_nodes_.clear();
-    CLR_CUDA(cudaGraphInstantiate(&gexec_, graph_, 0));
+    CLR_CUDA(cudaGraphInstantiate(&gexec_[k], graph_[k], 0));
   }
-  CLR_CUDA(cudaGraphLaunch(gexec_, stream_));
+  CLR_CUDA(cudaGraphLaunch(gexec_[k], stream_));
   return CLR_OK;
 }
 
@@ -1326,6 +1357,8 @@ int Solver::solve_begin() {
   perf = clr_perf{};
   it_ = 0;
   first_step_ = true;
+  escalated_ = false;
+  esc_iter_.assign(lay.B, -1);
   int rc = launch_init();
   if (rc) return rc;
   perf.kernel_launches += init_kernels_;
@@ -1338,7 +1371,7 @@ int Solver::solve_begin() {
 int Solver::step_launch() {
   int rc = launch_iteration();
   if (rc) return rc;
-  perf.kernel_launches += iter_kernels_;
+  perf.kernel_launches += iter_kernels_[(use64() && st.factor_bits != 64) ? 1 : 0];
   CLR_CUDA(cudaMemcpyAsync(sc_host_, sc_, sizeof(IterScal) * (size_t)lay.B, cudaMemcpyDeviceToHost, stream_));
   CLR_CUDA(cudaMemcpyAsync(bf_host_, bf_, sizeof(BatchFlags), cudaMemcpyDeviceToHost, stream_));
   CLR_CUDA(cudaEventRecord(step_ev_, stream_));
@@ -1360,8 +1393,32 @@ int Solver::step_poll(bool* ready) {
   return finish_step();
 }
 
+// Switch the rest of this solve to the FP64 factor (allocated on first use).
+int Solver::escalate_to_fp64() {
+  if (!f64_ready_ && st.factor_bits != 64) {
+    int rc = f64_.alloc(ar_, ls_);
+    if (rc != CLR_OK) return rc;
+    f64_ready_ = true;
+  }
+  escalated_ = true;
+  for (int64_t p = 0; p < lay.B; ++p)
+    if (esc_iter_[p] < 0) esc_iter_[p] = sc_host_[p].iter;
+  if (st.verbose)
+    std::fprintf(stderr, "[clr] refinement failed with the low-precision factor: continuing with the FP64 factor "
+                         "and its regularisation\n");
+  return CLR_OK;
+}
+
 // bookkeeping once a launched step has finished
 int Solver::finish_step() {
+  if (!use64() && st.fp64_escalation) {
+    for (int64_t p = 0; p < lay.B; ++p)
+      if (sc_host_[p].escalate) {
+        int rc = escalate_to_fp64();
+        if (rc != CLR_OK) return rc;
+        break;
+      }
+  }
   float ms = 0.f;
   if (first_step_) {
     if (cudaEventElapsedTime(&ms, ev_[0], ev_[1]) == cudaSuccess) perf.init_ms += ms;
@@ -1395,7 +1452,7 @@ int Solver::solve_end() {
     irt += sc_host_[p].ir_total;
   }
   perf.iterations = iters;
-  if (st.use_graph) perf.kernel_launches += (int64_t)irt * body_kernels_;  // executed loop bodies (upper bound)
+  if (st.use_graph) perf.kernel_launches += (int64_t)irt * body_kernels_[escalated_ ? 1 : 0];  // loop bodies (upper bound)
   perf.factor_flops = sy.flops;
   solve_s = now_s() - t_begin_;
   infos.assign(lay.B, clr_info{});
@@ -1432,6 +1489,7 @@ int Solver::solve() {
 clr_info Solver::info_now(int64_t p) const {
   const IterScal& h = sc_host_[p];
   clr_info info{};
+  info.fp64_from_iter = (p < (int64_t)esc_iter_.size()) ? esc_iter_[p] : -1;
   info.status = h.status;
   info.iterations = h.iter;
   info.ir_steps_total = h.ir_total;

@@ -99,11 +99,21 @@ class Solver {
   int64_t nckx_ = 0, nckz_ = 0, pst_ = 1;
   int hist_rows_ = 0;
   int csr_group_ = 32;
-  cudaGraph_t graph_ = nullptr;
-  cudaGraphExec_t gexec_ = nullptr;
+  // iteration graphs per factor precision (0: configured, 1: FP64 after an escalation)
+  cudaGraph_t graph_[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec_[2] = {nullptr, nullptr};
   cudaGraph_t igraph_ = nullptr;
   cudaGraphExec_t igexec_ = nullptr;
-  int64_t iter_kernels_ = 0, init_kernels_ = 0, body_kernels_ = 0;
+  int64_t iter_kernels_[2] = {0, 0}, init_kernels_ = 0, body_kernels_[2] = {0, 0};
+  bool escalated_ = false;       // this solve continues with the FP64 factor
+  bool f64_ready_ = false;       // f64_ allocated
+  std::vector<int> esc_iter_;    // per problem: iteration of the escalation, -1
+  bool use64() const { return st.factor_bits == 64 || escalated_; }
+  // regularisation constants of the factor in use (FP64 defaults after an escalation)
+  double reg_static() const;
+  double reg_dyn_eps() const;
+  double reg_dyn_delta() const;
+  int escalate_to_fp64();
   cudaStream_t body_stream_ = nullptr;
   std::vector<cudaGraph_t> ir_nodes_;  // refinement loop bodies captured in the current graph
   cudaEvent_t ev_[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

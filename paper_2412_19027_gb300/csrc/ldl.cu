@@ -375,17 +375,20 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       pl.A.resize(maxp + 1);
       pl.B.resize(maxp + 1);
       pl.C.resize(maxp + 1);
+      pl.Ctc.resize(maxp + 1);
       for (int p = 0; p <= maxp; ++p) {
-        std::vector<int64_t> ca, cb, cc;
+        std::vector<int64_t> ca, cb, cc, ct;
         for (int64_t b : ids) {
           const int64_t f = bf_f[b], c = bf_c[b];
           ca.push_back((int64_t)p * kBfNB < c ? 1 : 0);
           cb.push_back(bf_trsm_blocks(f, c, p) + bf_fin_blocks(c, p));
           cc.push_back(bf_update_tiles(f, c, p));
+          ct.push_back(bf_tc_tiles(f, c, p));
         }
         add_list(pl.A[p], ids, ca);
         add_list(pl.B[p], ids, cb);
         add_list(pl.C[p], ids, cc);
+        add_list(pl.Ctc[p], ids, ct);
       }
       std::vector<int64_t> cf, cbw;
       for (int64_t b : ids) {
@@ -437,7 +440,8 @@ int LdlFactor<T>::alloc(DeviceArena& ar, const LdlStructure& st) {
   Dp = ar.alloc_n<T>(st.N);
   w = ar.alloc_n<T>(st.wtot);
   xs = ar.alloc_n<T>(st.N);
-  dyn_hits = ar.alloc_n<int>(1);
+  dyn_hits = ar.alloc_n<int>(2);
+  tc_err = dyn_hits ? dyn_hits + 1 : nullptr;
   E = ar.alloc_n<T>(st.bfd.epool);
   ybuf = ar.alloc_n<T>(st.bfd.ypool);
   Linv = ar.alloc_n<T>(st.bfd.n * 2 * kBfNB * kBfNB);
@@ -455,7 +459,7 @@ template <typename T>
 int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* sc, double dyn_eps, double dyn_delta,
                          const int* skip) const {
   const LdlStructure& S = *s;
-  CLR_CUDA(cudaMemsetAsync(dyn_hits, 0, sizeof(int), stm));
+  CLR_CUDA(cudaMemsetAsync(dyn_hits, 0, 2 * sizeof(int), stm));  // dynamic-regularisation hits, tensor-core error
   CLR_CUDA(cudaMemsetAsync(F, 0, sizeof(T) * (size_t)S.pool, stm));
   if (S.bfd.epool > 0) CLR_CUDA(cudaMemsetAsync(E, 0, sizeof(T) * (size_t)S.bfd.epool, stm));
   k_scatter_kval<T><<<grid_for(S.nk, 256), 256, 0, stm>>>(F, kval, S.kdest, S.nk, skip);
@@ -479,7 +483,7 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
     }
     if (!S.lev_big[l].empty()) {
       int rc = BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps, dyn_delta,
-                                            dyn_hits, skip);
+                                            dyn_hits, skip, tc16, tc_err);
       if (rc) return rc;
     }
     CLR_CHECK_LAUNCH();

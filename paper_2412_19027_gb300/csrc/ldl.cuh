@@ -57,6 +57,8 @@ struct LdlFactor {
   T* ybuf = nullptr;  // forward results of the big fronts
   T* Linv = nullptr;  // per big front, two 64 x 64 diagonal-block inverses
   int* dyn_hits = nullptr;
+  int* tc_err = nullptr;  // set if a tensor-core wait of the 16-bit-product updates ran out
+  bool tc16 = false;      // big-front updates with BF16 products on the tensor cores (float only)
   int alloc(DeviceArena& ar, const LdlStructure& st);
   // Factor K: kval (FP64, lower triangle entries in kval order) scattered into
   // the fronts, +/- delta added on the diagonal (x rows +, z rows -), with

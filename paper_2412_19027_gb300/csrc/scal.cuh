@@ -43,6 +43,9 @@ struct IterScal {
   int dyn_hits, ir_revert;  // ir_revert: the last refinement step is being undone
   // initial point: order-preserving bits of the least nonneg entry
   unsigned long long nn_min_bits;
+  // precision escalation: a refinement of this iteration stopped short (ir_fail);
+  // the iteration is not taken (escalate) and is redone with the FP64 factor
+  int ir_fail, escalate;
 };
 
 // Constants of one problem (device memory, written at setup).

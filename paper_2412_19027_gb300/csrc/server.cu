@@ -406,7 +406,7 @@ int clr_server_create(clr_server** out, size_t device_bytes, int32_t max_cohort,
   clr_settings s;
   if (st) s = *st;
   else clr_default_settings(&s, 64);
-  if (s.factor_bits != 64 && s.factor_bits != 32) return CLR_E_INVALID;
+  if (s.factor_bits != 64 && s.factor_bits != 32 && s.factor_bits != 16) return CLR_E_INVALID;
   s.use_graph = 1;
   auto* h = new (std::nothrow) clr_server;
   if (!h) return CLR_E_OOM;

@@ -246,7 +246,8 @@ int clr_cones_combined_ds(const clr_cone* cones, int32_t ncones, const double* s
 int clr_ldl_solve(const clr_csc* K, const double* signs, const int64_t* order, int32_t factor_bits,
                   double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
                   int32_t* dyn_hits_out) {
-  if (!K || !signs || !rhs || !x_out || (factor_bits != 64 && factor_bits != 32)) return CLR_E_INVALID;
+  if (!K || !signs || !rhs || !x_out || (factor_bits != 64 && factor_bits != 32 && factor_bits != 16))
+    return CLR_E_INVALID;
   const int64_t N = K->ncols;
   if (K->nrows != N) return CLR_E_DIM;
   if (N == 0) return CLR_OK;
@@ -292,6 +293,7 @@ int clr_ldl_solve(const clr_csc* K, const double* signs, const int64_t* order, i
     CLR_CUDA(cudaMemcpy(&hits, f.dyn_hits, sizeof(int), cudaMemcpyDeviceToHost));
   } else {
     LdlFactor<float> f;
+    f.tc16 = factor_bits == 16;
     if ((rc = f.alloc(ar, ls))) return rc;
     if ((rc = f.factor(nullptr, kv, ddelta, dyn_reg_eps, dyn_reg_delta, nullptr))) return rc;
     if ((rc = f.solve(nullptr, drhs, nullptr))) return rc;

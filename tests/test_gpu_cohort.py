@@ -4,7 +4,9 @@ Each problem of a cohort must give the result it gives alone -- here bit for
 bit: same status, same iteration count, identical x, s, z (every sum of a
 problem is formed in an order that does not depend on the rest of the cohort,
 and each problem keeps its own equilibration, ordering and supernodes) -- and
-the oracle's answer (status, objective to 1e-6 relative).  Problems of
+the oracle's answer (status, objective to 1e-6 relative).  With a low-precision
+factor a cohort that needs the FP64 escalation takes it as a whole; those
+results are compared at the acceptance bar.  Problems of
 different sizes, cone families and outcomes (solved, infeasible) share one
 cohort; the ones that stop early are frozen while the others go on.
 """
@@ -71,9 +73,14 @@ def test_cohort_matches_alone_and_oracle(bits):
         xb, sb, zb, ib = batch.solution_of(i)
         xa, sa, za, ia = _alone(p, st)
         assert ib["status_name"] == ia["status_name"], (p.name, ib, ia)
-        assert ib["iterations"] == ia["iterations"], (p.name, ib, ia)
-        for u, v in ((xb, xa), (sb, sa), (zb, za)):
-            np.testing.assert_array_equal(u, v, err_msg=p.name)
+        if ib["fp64_from_iter"] < 0 and ia["fp64_from_iter"] < 0:
+            assert ib["iterations"] == ia["iterations"], (p.name, ib, ia)
+            for u, v in ((xb, xa), (sb, sa), (zb, za)):
+                np.testing.assert_array_equal(u, v, err_msg=p.name)
+        elif ib["status_name"] == "SOLVED":
+            # a low-precision cohort goes on in FP64 as a whole once one of its problems needs it
+            f, fa = p.objective(xb), p.objective(xa)
+            assert abs(f - fa) <= 1e-6 * max(1.0, abs(fa)), (p.name, f, fa)
         iters.append(ib["iterations"])
         ref = oracle.solve(p.P, p.q, p.A, p.b, p.cones)
         assert ib["status_name"] == ref.status_name, (p.name, ib["status_name"], ref.status_name)
@@ -100,7 +107,9 @@ def test_cohort_infeasible_member_certificate():
 
 
 def test_cohort_uneven_mpc_fp32():
-    """Uneven MPC problems (the serving workload's shapes), FP32 factor."""
+    """Uneven MPC problems (the serving workload's shapes), FP32 factor: some of
+    them need the FP64 escalation late in the solve (the FP32 factor with the
+    paper's regularisation no longer refines to 1e-6 there)."""
     rng = np.random.default_rng(5)
     probs = [W.mpc_qp(int(s), T=int(rng.integers(10, 31)), nx=int(rng.integers(4, 9)), nu=int(rng.integers(2, 5)))
              for s in range(12)]

@@ -260,3 +260,47 @@ def test_ldl_big_fronts_with_update_rows(bits):
     np.testing.assert_allclose(D, Dref, rtol=tol)
     xref = np.linalg.solve(K, rhs)
     np.testing.assert_allclose(x, xref, rtol=tol, atol=tol * np.abs(xref).max())
+
+
+def test_ldl_big_fronts_bf16_products_refine_to_fp64_accuracy():
+    """factor_bits 16: the big-front updates run on the tensor cores with BF16
+    operands and FP32 accumulation.  The factor is accurate to a few 1e-3, so the
+    pivots match the FP64 factor to 5e-2 and FP64 refinement with it reaches the
+    FP64 solution (what the IPM does with it)."""
+    rng = np.random.default_rng(12)
+    n, m = 300, 260  # fronts of 300 pivots with 260 update rows and a 260-pivot root: several 128-row tiles
+    M = rng.standard_normal((n, n))
+    P = M @ M.T / n + np.eye(n)
+    B = rng.standard_normal((m, m))
+    H = B @ B.T / m + np.eye(m)
+    A = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.2)
+    K = np.block([[P, A.T], [A, -H]])
+    N = n + m
+    signs = np.r_[np.ones(n), -np.ones(m)]
+    rhs = rng.standard_normal(N)
+    order = np.arange(N)
+    x, D, hits = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=16, dyn_reg_eps=1e-6, dyn_reg_delta=1e-4)
+    assert hits == 0
+    L, Dref, _ = ldl_factor(K, signs, 1e-13, 2e-7)
+    np.testing.assert_allclose(D, Dref, rtol=5e-2)
+    xref = np.linalg.solve(K, rhs)
+    assert np.abs(x - xref).max() < 0.1 * np.abs(xref).max()
+    for _ in range(12):  # refinement with the 16-bit-product factor
+        dx, _, _ = clr.clr_ldl_solve(K, signs, rhs - K @ x, order=order, factor_bits=16, dyn_reg_eps=1e-6,
+                                     dyn_reg_delta=1e-4)
+        x = x + dx
+    np.testing.assert_allclose(x, xref, rtol=1e-9, atol=1e-9 * np.abs(xref).max())
+
+
+def test_solve_with_bf16_products_mixed_cone_full_size():
+    """The full mixed-cone QP (root front of ~2050 rows, on the tensor cores)
+    with 16-bit products and FP64 refinement reaches the planted optimum."""
+    prob = W.mixed_cone(0)
+    st = clr.clr_default_settings(16, ir_stop_ratio=5.0)
+    s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+    s.solve()
+    x, sl, z, info = s.solution()
+    s.free()
+    assert info["status_name"] == "SOLVED", info
+    f_star = prob.objective(prob.x_star)
+    assert abs(prob.objective(x) - f_star) <= 1e-6 * max(1.0, abs(f_star))

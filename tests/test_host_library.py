@@ -57,8 +57,12 @@ def test_default_settings_follow_the_paper(clr):
         for key in ("eps_feas", "eps_inf", "max_iter", "static_reg", "static_reg_dyn", "dyn_reg_eps",
                     "dyn_reg_delta", "ruiz_passes", "scale_min", "scale_max", "min_step"):
             assert getattr(s, key) == pytest.approx(o[key], rel=1e-15), key
-    with pytest.raises(clr.ClrError):
-        clr.clr_default_settings(16)
+    # 16: the FP32 factor with BF16 products for the large fronts, otherwise the FP32 defaults
+    s16 = clr.clr_default_settings(16)
+    assert s16.factor_bits == 16 and s16.static_reg == s32.static_reg and s16.dyn_reg_eps == s32.dyn_reg_eps
+    for bad in (8, 0, 128):
+        with pytest.raises(clr.ClrError):
+            clr.clr_default_settings(bad)
 
 
 def test_validation_errors(clr):
