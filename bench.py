@@ -43,6 +43,60 @@ FP64_PEAK_TFLOPS = 1.25            # GB300 FP64 (FFMA and DMMA), nominal
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
 
 
+def measured_peaks():
+    """HBM copy GB/s and cuBLAS BF16 TFLOP/s measured on this GPU model (file
+    beside this script), else the fallback figures of one earlier measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+# Cone kernels at stress shapes (inputs far larger than the 129 MB L2): per unit
+# (nonneg row, SOC(5) cone, PSD(10) cone) the algorithmic bytes of each step =
+# the vectors it must read plus those it must write, 8 B per entry:
+#   scaling:  s, z in; packed -H block and the scaling point (lambda) out
+#             (nonneg 16 + 8 + 8; SOC d: 16d + 8 d(d+1)/2 + 8(d+2) with w-bar, eta;
+#              PSD k: 16 d_k + 8 d_k(d_k+1)/2 + 8 (2 k^2 + k) for R, R^-1, lambda)
+#   step:     s, z, ds, dz in (32 B per row; the result is one scalar)
+#   ds:       lambda, W (w or w-bar; R, R^-1 for PSD), ds_a, dz_a in, d_s out
+CONE_STRESS = [("nonneg", 1 << 26, 1), ("soc", 1 << 22, 5), ("psd", 1 << 16, 55)]
+
+
+def cone_bytes(family, k):
+    d = k
+    if family == "nonneg":
+        return {"scaling": 32, "step": 32, "ds": 40}
+    if family == "soc":
+        return {"scaling": 16 * d + 4 * d * (d + 1) + 8 * (d + 2), "step": 32 * d, "ds": 8 * (5 * d + 1)}
+    kk = 10
+    return {"scaling": 16 * d + 4 * d * (d + 1) + 8 * (2 * kk * kk + kk), "step": 32 * d,
+            "ds": 8 * (4 * d + 2 * kk * kk + kk)}
+
+
+def run_cone_roofline(clr, W, peaks, reps=10):
+    out = {}
+    for fam, count, d in CONE_STRESS:
+        cones, s, z, ds, dz = W.cone_stress(7, fam, count)
+        t = clr.clr_cones_time(cones, s, z, ds, dz, 1.0, reps)
+        del s, z, ds, dz
+        b = cone_bytes(fam, d)
+        row = {"units": count, "unit": {"nonneg": "row", "soc": "SOC(5) cone", "psd": "PSD(10) cone"}[fam]}
+        for step, key in (("scaling", "scaling_ms"), ("step", "step_ms"), ("ds", "combined_ds_ms")):
+            ms = t[key]
+            gbs = b[step] * count / (ms / 1e3) / 1e9
+            row[step] = {"ms": ms, "bytes_per_unit": b[step], "achieved_gbs": gbs,
+                         "frac": gbs / peaks["hbm_gbs"]}
+        out[fam] = row
+    out["peak_gbs"] = peaks["hbm_gbs"]
+    out["peak_source"] = peaks["source"] + " HBM copy"
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -59,6 +113,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cone-roofline", action="store_true",
+                    help="skip the cone kernels at stress shapes (2^26 nonneg rows, 2^22 SOC5, 2^16 PSD10)")
     ap.add_argument("--serve-requests", type=int, default=10_000)
     ap.add_argument("--serve-bits", type=int, default=64, choices=[32, 64])
     return ap.parse_args()
@@ -178,7 +234,7 @@ def serve_stream(clr, sv, reqs, rate):
     th = threading.Thread(target=submitter)
     t_start = time.perf_counter()
     th.start()
-    lat, iters, statuses = [], [], {}
+    lat, iters, statuses, unsolved = [], [], {}, []
     for k in range(len(reqs)):
         while tickets[k] is None:
             time.sleep(1e-4)
@@ -189,11 +245,13 @@ def serve_stream(clr, sv, reqs, rate):
         lat.append(info["solve_s"])
         iters.append(info["iterations"])
         statuses[info["status_name"]] = statuses.get(info["status_name"], 0) + 1
+        if info["status_name"] != "SOLVED" and len(unsolved) < 10:
+            unsolved.append([k, info["status_name"], info["iterations"], info["fp64_from_iter"]])
     t_end = time.perf_counter()
     th.join()
     return {"requests": len(reqs), "offered_per_s": rate, "solves_per_s": len(reqs) / (t_end - t_start),
             "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99), "mean_iterations": float(np.mean(iters)),
-            "statuses": statuses}
+            "statuses": statuses, "unsolved_first": unsolved}
 
 
 def run_serving(args, clr, W):
@@ -387,13 +445,22 @@ def run_ours(args):
     phases = {"residuals+cones": p["resid_cones_ms"], "factorization": p["factor_ms"],
               "solves+steps": p["solve_step_ms"], "init": p["init_ms"]}
     fact_ms = p["factor_ms"] / nf
-    peak = FP32_PEAK_TFLOPS if args.factor_bits == 32 else FP64_PEAK_TFLOPS
+    peaks = measured_peaks()
     achieved = sym["factor_flops"] / (fact_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    if args.factor_bits == 16:
+        # BF16 products on the tensor cores, timed inside the solve: the sustained figure
+        bound, peak = "tensor", peaks["bf16_tflops_sustained"]
+        psrc = "%s cuBLAS BF16 sustained" % peaks["source"]
+    elif args.factor_bits == 32:
+        bound, peak, psrc = "alu", FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+    else:
+        bound, peak, psrc = "alu", FP64_PEAK_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "numeric LDL^T (multifrontal, FP%d)" % args.factor_bits,
-                "flops_per_launch": sym["factor_flops"], "ms_per_launch": fact_ms,
-                "peak_source": "derived: %s" % ("152 SMs x 128 FP32 lanes x 2 x 2070 MHz" if args.factor_bits == 32
-                                                else "GB300 FP64 nominal 1.25 TFLOP/s")}
+                "flops_per_launch": sym["factor_flops"], "ms_per_launch": fact_ms, "peak_source": psrc}
+    cone_roof = None
+    if not args.no_cone_roofline and rank == 0:
+        cone_roof = run_cone_roofline(clr, W, peaks)
 
     serving = None
     if not args.no_serving:
@@ -420,9 +487,9 @@ def run_ours(args):
                 "iterations": infos[-1]["iterations"], "status": infos[-1]["status_name"],
                 "objective_rel_err_vs_planted": obj_err, "res_primal": infos[-1]["res_primal"],
                 "res_dual": infos[-1]["res_dual"], "ir_steps_total": infos[-1]["ir_steps_total"],
-                "fp64_factor": fp64, "phase_ms_per_solve": phases, "roofline": roofline,
+                "fp64_from_iter": infos[-1]["fp64_from_iter"], "fp64_factor": fp64, "phase_ms_per_solve": phases, "roofline": roofline,
                 "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-                "serving": serving,
+                "serving": serving, "cone_roofline": cone_roof,
                 "symbolic": {k: sym[k] for k in ("kkt_dim", "l_nnz", "factor_flops", "n_supernodes", "n_levels",
                                                  "max_front")}}
         print(json.dumps(line), flush=True)

@@ -113,6 +113,9 @@ typedef struct {
                               ||r||_inf > 1e-4 max(1, ||rhs||_inf) (or NaN) the iteration is not taken and the solve
                               goes on with the FP64 factor and the FP64 regularisation defaults (for every problem
                               of a cohort); 0: never */
+  int32_t big_front_schedule; /* large fronts: 1 (default) one dataflow launch per level, tile tasks started as
+                                 their inputs are ready; 0 three launches per 64-column panel.  The
+                                 16-bit-products variant always uses the per-panel launches. */
 } clr_settings;
 
 typedef struct {
@@ -378,6 +381,25 @@ int clr_cones_step_length(const clr_cone* cones, int32_t ncones, const double* s
  * affine directions ds_a, dz_a.  Zero cones give 0. */
 int clr_cones_combined_ds(const clr_cone* cones, int32_t ncones, const double* s, const double* z,
                           const double* ds_a, const double* dz_a, double sigma_mu, double* ds_out);
+
+/* Device time of the cone steps on one cone list, for roofline measurement
+ * (the scaling of Alg. 1 step 4 with the KKT block write, the step-length
+ * ratio tests of Sec. 2.2, the combined-step d_s of Eq. ds-correction-step).
+ * s, z, ds, dz (length sum(dim), caller-owned host arrays) are uploaded once;
+ * each step then runs `reps` (>= 1) times back to back after one untimed
+ * call, bracketed by CUDA events on the default stream, and out receives the
+ * mean device milliseconds per call.  The exp/pow line search is not timed
+ * (step_ms covers the symmetric families).  Inputs larger than the L2 cache
+ * (~129 MB) give DRAM-bound figures.  out->rows = sum(dim), out->kkt_values =
+ * number of packed H entries written per scaling call.  Errors:
+ * CLR_E_INVALID (null pointers, reps < 1), CLR_E_UNSUPPORTED (cone list as
+ * for clr_cones_scaling), CLR_E_OOM, CLR_E_CUDA. */
+typedef struct {
+  double scaling_ms, step_ms, combined_ds_ms;
+  int64_t rows, kkt_values;
+} clr_cone_times;
+int clr_cones_time(const clr_cone* cones, int32_t ncones, const double* s, const double* z, const double* ds,
+                   const double* dz, double mu, int32_t reps, clr_cone_times* out);
 
 /* Sparse LDL^T of a symmetric quasi-definite matrix (Sec. 3.6) with the same
  * supernodal factorization the solver uses.  K_lower: lower triangle (CSC,

@@ -14,7 +14,8 @@ Follows Sec. 3.6 "Solving linear systems" of the paper:
   UNREGULARISED K in FP64, stop when ||r||_inf <= t_abs + t_rel ||b||_inf or
   after T_max refinement steps, else x += (LDL^T)^{-1} r.  An optional stall
   test (setting ir_stop_ratio > 0, off by default, not in the paper) also
-  stops once a step has reduced ||r||_inf by less than that factor.
+  stops once a step has reduced ||r||_inf by less than that factor, provided
+  ||r||_inf is already below the acceptance bar 1e-4 max(1, ||b||_inf).
 
 Two factorizations are provided:
 * ``ldl_factor``: the unpivoted LDL^T with dynamic regularisation, in the
@@ -103,7 +104,8 @@ class KKTSolver:
         """Refinement on the unregularised K (Sec. 3.6): stop at the tolerance
         or after ir_max steps; a step that makes ||r||_inf larger is undone and
         ends the refinement (the regularised factor is no longer a contraction
-        for K there); optionally stop once a step gains less than ir_stop_ratio."""
+        for K there); optionally stop once a step gains less than ir_stop_ratio
+        and ||r||_inf is below the acceptance bar 1e-4 max(1, ||rhs||_inf)."""
         x = self._solve_reg(rhs)
         bnorm = float(np.max(np.abs(rhs))) if len(rhs) else 0.0
         prev = np.inf
@@ -115,7 +117,8 @@ class KKTSolver:
             if last is not None and rn > prev:
                 x = x - last
                 break
-            stalled = self.ir_stop > 0 and not (rn * self.ir_stop < prev)
+            accept = 1e-4 * max(1.0, bnorm)
+            stalled = self.ir_stop > 0 and rn <= accept and not (rn * self.ir_stop < prev)
             if not (rn > self.ir_abs + self.ir_rel * bnorm) or stalled or steps >= self.ir_max:
                 break
             prev = rn

@@ -43,7 +43,7 @@ class clr_settings(C.Structure):
                 ("ruiz_passes", C.c_int32), ("scale_min", C.c_double), ("scale_max", C.c_double),
                 ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
                 ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32),
-                ("fp64_escalation", C.c_int32)]
+                ("fp64_escalation", C.c_int32), ("big_front_schedule", C.c_int32)]
 
 
 class clr_info(C.Structure):
@@ -53,6 +53,11 @@ class clr_info(C.Structure):
                 ("gap_rel", C.c_double), ("mu", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("fp64_from_iter", C.c_int32),
                 ("pad", C.c_int32)]
+
+
+class clr_cone_times(C.Structure):
+    _fields_ = [("scaling_ms", C.c_double), ("step_ms", C.c_double), ("combined_ds_ms", C.c_double),
+                ("rows", C.c_int64), ("kkt_values", C.c_int64)]
 
 
 class clr_symbolic_stats(C.Structure):
@@ -84,7 +89,7 @@ _LIB = None
 EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr_get_solution", "clr_update_qb",
            "clr_get_symbolic_stats", "clr_get_perf", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
            "clr_set_allocator", "clr_free", "clr_error_string", "clr_status_string", "clr_last_cuda_error",
-           "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_ldl_solve",
+           "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_cones_time", "clr_ldl_solve",
            "clr_dense_ldl_solve_noalloc", "clr_batch_setup", "clr_batch_analyze", "clr_batch_size", "clr_batch_get",
            "clr_batch_update_qb", "clr_server_create", "clr_server_submit", "clr_server_poll", "clr_server_wait",
            "clr_server_get_stats", "clr_server_destroy"]
@@ -122,6 +127,8 @@ def _lib():
                                                                                             P(C.c_double)]
         L.clr_cones_combined_ds.argtypes = [P(clr_cone), C.c_int32] + [P(C.c_double)] * 4 + [C.c_double,
                                                                                             P(C.c_double)]
+        L.clr_cones_time.argtypes = [P(clr_cone), C.c_int32] + [P(C.c_double)] * 4 + [C.c_double, C.c_int32,
+                                                                                     P(clr_cone_times)]
         L.clr_ldl_solve.argtypes = [P(clr_csc), P(C.c_double), P(C.c_int64), C.c_int32, C.c_double, C.c_double,
                                     P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
         L.clr_dense_ldl_solve_noalloc.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_double, C.c_double, vp, vp]
@@ -447,6 +454,16 @@ def clr_cones_combined_ds(cones, s, z, ds_a, dz_a, sigma_mu):
     _check(_lib().clr_cones_combined_ds(_cones(cones), len(cones), *[_dptr(v) for v in arrs], float(sigma_mu),
                                         _dptr(out)), "clr_cones_combined_ds")
     return out
+
+
+def clr_cones_time(cones, s, z, ds, dz, mu, reps=10):
+    """Mean device ms per call of the scaling, step-length and combined-d_s
+    kernels on one cone list (see include/clr.h)."""
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (s, z, ds, dz)]
+    out = clr_cone_times()
+    _check(_lib().clr_cones_time(_cones(cones), len(cones), *[_dptr(v) for v in arrs], float(mu), int(reps),
+                                 C.byref(out)), "clr_cones_time")
+    return {k: getattr(out, k) for (k, _) in clr_cone_times._fields_}
 
 
 def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1e-13, dyn_reg_delta=2e-7):

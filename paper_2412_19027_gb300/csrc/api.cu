@@ -50,6 +50,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.use_graph = 1;
   s.verbose = 0;
   s.fp64_escalation = 1;
+  s.big_front_schedule = 1;
   *out = s;
   return CLR_OK;
 }
@@ -57,7 +58,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
 static int check_settings(const clr_settings& s) {
   if (s.factor_bits != 64 && s.factor_bits != 32 && s.factor_bits != 16) return CLR_E_INVALID;
   if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0 ||
-      !(s.ir_stop_ratio >= 0))
+      !(s.ir_stop_ratio >= 0) || (s.big_front_schedule != 0 && s.big_front_schedule != 1))
     return CLR_E_INVALID;
   if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
   if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;

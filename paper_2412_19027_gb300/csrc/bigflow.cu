@@ -1,0 +1,478 @@
+// Dataflow factorization of the big fronts of one level: one persistent launch
+// in which CTAs take 64 x 64 tile tasks from a counter in a topological order
+// of the task graph and wait (bounded) for the version words of the tiles they
+// read.  The arithmetic of each task is that of the per-panel kernels
+// (bigfront.cu); only the scheduling differs: the diagonal block of panel p + 1
+// starts as soon as its own tile has received panel p's update, while the rest
+// of panel p's updates are still running.
+#include "bigfront.cuh"
+
+namespace clr {
+namespace {
+constexpr int NB = kBfNB;
+constexpr int LD = NB + 1;   // odd stride: column accesses free of bank conflicts
+constexpr int LDK = NB + 4;  // 16-byte aligned rows of the K-major operand tiles
+constexpr int NT = kFlowThreads;
+constexpr uint32_t kSpin = 1u << 21;  // polls of one wait (about 2 s) before it gives up
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0: wait until *p >= v.  False if the wait ran out (err := 2) or another
+// CTA has given up (err != 0).
+__device__ bool wait_ge(const int* p, int v, int* err) {
+  for (uint32_t it = 0; it < kSpin; ++it) {
+    if (ld_acquire(p) >= v) return true;
+    if (it >= 16) {
+      if (ld_acquire(err) != 0) return false;
+      __nanosleep(256);
+    }
+  }
+  atomicExch(err, 2);
+  return false;
+}
+
+struct Geo {
+  int64_t f, c, P, nbf;
+};
+__device__ __forceinline__ int64_t brow0(const Geo& g, int64_t b) { return b < g.P ? NB * b : g.c + NB * (b - g.P); }
+__device__ __forceinline__ int bnrow(const Geo& g, int64_t b) {
+  return (int)(b < g.P ? min((int64_t)NB, g.c - NB * b) : min((int64_t)NB, g.f - g.c - NB * (b - g.P)));
+}
+struct Words {
+  int *tile, *etile, *diag, *trsm;
+  int64_t P;
+  __device__ int* t(int64_t i, int64_t j) const { return tile + i * (i + 1) / 2 + j; }
+  __device__ int* e(int64_t i, int64_t c) const { return etile + i * P + c; }
+};
+__device__ __forceinline__ Words words_of(int* base, const Geo& g) {
+  Words w;
+  w.P = g.P;
+  w.tile = base;
+  w.etile = base + g.nbf * (g.nbf + 1) / 2;
+  w.diag = w.etile + g.nbf * g.P;
+  w.trsm = w.diag + g.P;
+  return w;
+}
+
+// element r of K-row k of a K-major operand tile: 4-element units XOR-swizzled by k
+__device__ __forceinline__ int swz(int k, int r) { return k * LDK + (((r >> 2) ^ (k & 7)) << 2) + (r & 3); }
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]);
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// Inverse of a unit lower n x n block (n <= 32) of Lo from row r0 into Li: lane
+// j of the calling warp computes column j by forward substitution.
+template <typename T>
+__device__ __forceinline__ void warp_inv32(const T* Lo, T* Li, int r0, int n) {
+  const int j = threadIdx.x & 31;
+  if (j < n) {
+    Li[(r0 + j) * LD + r0 + j] = (T)1;
+    for (int i = j + 1; i < n; ++i) {
+      T acc = (T)0;
+#pragma unroll 4
+      for (int l = j; l < i; ++l) acc += Lo[(r0 + i) * LD + r0 + l] * Li[(r0 + l) * LD + r0 + j];
+      Li[(r0 + i) * LD + r0 + j] = -acc;
+    }
+  }
+}
+
+// D(p): LDL^T of the pw x pw diagonal block (right-looking, one barrier per
+// pivot, dynamic regularisation of wrong-signed or tiny pivots), L and the
+// pivots written back, Linv = L_KK^{-1} written into E_KK.
+template <typename T>
+__device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T* F, T* E, T* Dp,
+                          const int8_t* dsign, T eps, T delta, int* hits, T* sm, int8_t* sgn) {
+  T* S = sm;
+  T* Lo = S + NB * LD;
+  T* Li = Lo + NB * LD;
+  const int64_t f = g.f, k0 = (int64_t)p * NB;
+  const int pw = bnrow(g, p);
+  T* G = F + bf.goff[b];
+  T* Eb = E + bf.eoff[b];
+  const int64_t kp = bf.k0pos[b] + k0;
+  const int tid = threadIdx.x;
+#pragma unroll 4
+  for (int idx = tid; idx < NB * NB; idx += NT) {
+    const int i = idx % NB, j = idx / NB;
+    S[i * LD + j] = (i < pw && j < pw && i >= j) ? __ldcg(G + (k0 + i) + (k0 + j) * f) : (T)0;
+    Lo[i * LD + j] = (T)0;
+    Li[i * LD + j] = (T)0;
+  }
+  if (tid < NB) sgn[tid] = tid < pw ? dsign[kp + tid] : (int8_t)1;
+  __syncthreads();
+  const int row = tid >> 2, part = tid & 3;
+  int nhit = 0;
+  for (int k = 0; k < pw; ++k) {
+    T d = S[k * LD + k];
+    const T sg = (T)sgn[k];
+    const bool hit = sg * d <= eps;
+    if (hit) d = sg * delta;
+    if (tid == 0) {
+      nhit += hit ? 1 : 0;
+      Lo[k * LD + k] = d;
+    }
+    if (row > k && row < pw) {
+      const T li = S[row * LD + k] / d;
+      T* sr = S + row * LD;
+#pragma unroll 4
+      for (int j = k + 1 + part; j <= row; j += 4) sr[j] -= li * S[j * LD + k];
+      if (part == 0) Lo[row * LD + k] = li;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && nhit) atomicAdd(hits, nhit);
+  for (int idx = tid; idx < pw * pw; idx += NT) {
+    const int i = idx % pw, j = idx / pw;
+    if (i >= j) G[(k0 + i) + (k0 + j) * f] = Lo[i * LD + j];
+  }
+  for (int i = tid; i < pw; i += NT) Dp[kp + i] = Lo[i * LD + i];
+  const int cw0 = min(32, pw), cw1 = pw - cw0;
+  const int wid = tid >> 5;
+  if (wid == 0) warp_inv32(Lo, Li, 0, cw0);
+  if (wid == 1 && cw1 > 0) warp_inv32(Lo, Li, 32, cw1);
+  __syncthreads();
+  if (cw1 > 0) {
+    // L = [A 0; C B]: X = C A^-1 (into S), then Li_21 = -B^-1 X
+    for (int idx = tid; idx < 32 * 32; idx += NT) {
+      const int i = idx % 32, j = idx / 32;
+      T acc = (T)0;
+      if (i < cw1)
+        for (int l = j; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * Li[l * LD + j];
+      S[i * LD + j] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 32; idx += NT) {
+      const int i = idx % 32, j = idx / 32;
+      if (i >= cw1) continue;
+      T acc = (T)0;
+      for (int l = 0; l <= i; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + j];
+      Li[(32 + i) * LD + j] = -acc;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < pw * pw; idx += NT) {
+    const int i = idx % pw, j = idx / pw;
+    Eb[(k0 + i) + (k0 + j) * f] = Li[i * LD + j];  // zero above the diagonal
+  }
+}
+
+// T(p, i): L_IK = F_IK Linv^T D_K^{-1} for the rows of block i (each thread 4 x 4).
+template <typename T>
+__device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, T* F, const T* E,
+                          const T* Dp, T* sm, T* dl) {
+  T* Ls = sm;            // Linv
+  T* Xs = sm + NB * LD;  // F_IK
+  const int64_t f = g.f, k0 = (int64_t)p * NB;
+  const int pw = bnrow(g, p);
+  const int64_t r0 = brow0(g, bi);
+  const int nr = bnrow(g, bi);
+  T* G = F + bf.goff[b];
+  const T* Eb = E + bf.eoff[b];
+  const int tid = threadIdx.x;
+#pragma unroll 4
+  for (int idx = tid; idx < NB * NB; idx += NT) {
+    const int i = idx % NB, j = idx / NB;
+    Ls[i * LD + j] = (i < pw && j < pw) ? __ldcg(Eb + (k0 + i) + (k0 + j) * f) : (T)0;
+    Xs[i * LD + j] = (i < nr && j < pw) ? __ldcg(G + (r0 + i) + (k0 + j) * f) : (T)0;
+  }
+  if (tid < pw) dl[tid] = __ldcg(Dp + bf.k0pos[b] + k0 + tid);
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  for (int l = 0; l < pw; ++l) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = Xs[(tr + 16 * a) * LD + l];
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) bv[bb] = Ls[(tc + 16 * bb) * LD + l];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+  }
+#pragma unroll
+  for (int bb = 0; bb < 4; ++bb) {
+    const int j = tc + 16 * bb;
+    if (j >= pw) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = tr + 16 * a;
+      if (i < nr) G[(r0 + i) + (k0 + j) * f] = acc[a][bb] / dl[j];
+    }
+  }
+}
+
+// Efin(p, e): E_KC <- Linv E_KC for the E rows of panel p and column block e < p.
+template <typename T>
+__device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t e, T* E, T* sm) {
+  T* Ls = sm;
+  T* Xs = sm + NB * LD;
+  const int64_t f = g.f, k0 = (int64_t)p * NB, cb = (int64_t)e * NB;
+  const int pw = bnrow(g, p);
+  T* Eb = E + bf.eoff[b];
+  const int tid = threadIdx.x;
+#pragma unroll 4
+  for (int idx = tid; idx < NB * NB; idx += NT) {
+    const int i = idx % NB, j = idx / NB;
+    Ls[i * LD + j] = (i < pw && j < pw) ? __ldcg(Eb + (k0 + i) + (k0 + j) * f) : (T)0;
+    Xs[i * LD + j] = (i < pw) ? __ldcg(Eb + (k0 + i) + (cb + j) * f) : (T)0;
+  }
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  for (int l = 0; l < pw; ++l) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = Ls[(tr + 16 * a) * LD + l];
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) bv[bb] = Xs[l * LD + tc + 16 * bb];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = tr + 16 * a;
+    if (i >= pw) continue;
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) Eb[(k0 + i) + (cb + tc + 16 * bb) * f] = acc[a][bb];
+  }
+}
+
+// U(p, i, j): F_IJ -= L_IK (D_K L_JK^T) (lower part only on a diagonal tile);
+// EU(p, i, e): E_IC -= L_IK E_KC.  4 x 4 outputs per thread from K-major tiles.
+template <typename T>
+__device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, int64_t bj,
+                            bool etile, T* F, T* E, const T* Dp, T* sm) {
+  T* Ak = sm;
+  T* Bk = sm + NB * LDK;
+  const int64_t f = g.f, k0 = (int64_t)p * NB;
+  const int pw = bnrow(g, p);
+  const int64_t i0 = brow0(g, bi);
+  const int ni = bnrow(g, bi);
+  T* G = F + bf.goff[b];
+  T* Eb = E + bf.eoff[b];
+  const T* Dk = Dp + bf.k0pos[b] + k0;
+  const int tid = threadIdx.x;
+  int64_t c0;
+  int nc;
+  if (!etile) {
+    c0 = brow0(g, bj);
+    nc = bnrow(g, bj);
+#pragma unroll 4
+    for (int idx = tid; idx < NB * NB; idx += NT) {
+      const int r = idx % NB, k = idx / NB;
+      Ak[swz(k, r)] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
+      Bk[swz(k, r)] = (k < pw && r < nc) ? __ldcg(G + (c0 + r) + (k0 + k) * f) * __ldcg(Dk + k) : (T)0;
+    }
+  } else {
+    c0 = bj * NB;
+    nc = bnrow(g, bj);
+#pragma unroll 4
+    for (int idx = tid; idx < NB * NB; idx += NT) {
+      const int r = idx % NB, k = idx / NB;
+      Ak[swz(k, r)] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
+      // E_KC: consecutive threads read consecutive rows k0 + kk of column c0 + cc
+      const int kk = idx % NB, cc = idx / NB;
+      Bk[swz(kk, cc)] = (kk < pw && cc < nc) ? __ldcg(Eb + (k0 + kk) + (c0 + cc) * f) : (T)0;
+    }
+  }
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  for (int k = 0; k < pw; ++k) {
+    T av[4], bv[4];
+    ld4<T>(Ak + swz(k, 4 * tr), av);
+    ld4<T>(Bk + swz(k, 4 * tc), bv);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+  }
+  const bool diag = !etile && bi == bj;
+  T* base = etile ? Eb : G;
+#pragma unroll
+  for (int bb = 0; bb < 4; ++bb) {
+    const int cc = 4 * tc + bb;
+    if (cc >= nc) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = 4 * tr + a;
+      if (r < ni && (!diag || r >= cc)) base[(i0 + r) + (c0 + cc) * f] -= acc[a][bb];
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2)
+    k_bf_flow(BigFrontDev bf, const FlowTask* __restrict__ task, int64_t t0, int64_t nt, int* __restrict__ state,
+              int64_t head_off, const int64_t* __restrict__ soff, T* F, T* E, T* Dp, const int8_t* __restrict__ dsign,
+              double eps_d, double delta_d, int* hits, int* err, const int* skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ int8_t sgn[NB];
+  __shared__ T dl[NB];
+  __shared__ FlowTask s_task;
+  __shared__ int s_go;
+  int* head = state + head_off;
+  const int tid = threadIdx.x;
+  int next = 0;
+  if (tid == 0) next = atomicAdd(head, 1);
+  for (;;) {
+    if (tid == 0) {
+      const int cur = next;
+      int go = 0;
+      if (cur < nt) {
+        next = atomicAdd(head, 1);  // the following ticket, fetched while this task runs
+        const FlowTask tk = task[t0 + cur];
+        s_task = tk;
+        const int64_t b = tk.bf;
+        const Geo g{bf.f[b], bf.c[b], (bf.c[b] + NB - 1) / NB, flow_nbf(bf.f[b], bf.c[b])};
+        const Words w = words_of(state + soff[b], g);
+        const int p = tk.p;
+        bool ok;
+        switch (tk.kind) {
+          case 0:
+            ok = wait_ge(w.t(p, p), p, err);
+            break;
+          case 1:
+            ok = wait_ge(w.diag + p, 1, err) && wait_ge(w.t(tk.i, p), p, err);
+            break;
+          case 2:
+            ok = wait_ge(w.diag + p, 1, err) && wait_ge(w.e(p, tk.j), p - tk.j, err);
+            break;
+          case 3:
+            ok = wait_ge(w.trsm + tk.i, p + 1, err) && wait_ge(w.trsm + tk.j, p + 1, err) &&
+                 wait_ge(w.t(tk.i, tk.j), p, err);
+            break;
+          default:
+            ok = wait_ge(w.trsm + tk.i, p + 1, err) &&
+                 (tk.j < p ? wait_ge(w.e(p, tk.j), p - tk.j + 1, err) : wait_ge(w.diag + p, 1, err)) &&
+                 wait_ge(w.e(tk.i, tk.j), p - tk.j, err);
+            break;
+        }
+        go = ok ? 1 : 0;
+        if (ok) __threadfence();
+      }
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const FlowTask tk = s_task;
+    const int64_t b = tk.bf;
+    const Geo g{bf.f[b], bf.c[b], (bf.c[b] + NB - 1) / NB, flow_nbf(bf.f[b], bf.c[b])};
+    switch (tk.kind) {
+      case 0:
+        task_diag<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, sgn);
+        break;
+      case 1:
+        task_trsm<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
+        break;
+      case 2:
+        task_efin<T>(bf, b, g, tk.p, tk.j, E, sm);
+        break;
+      case 3:
+        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, false, F, E, Dp, sm);
+        break;
+      default:
+        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, true, F, E, Dp, sm);
+        break;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const Words w = words_of(state + soff[b], g);
+      const int p = tk.p;
+      __threadfence();
+      switch (tk.kind) {
+        case 0:
+          st_release(w.diag + p, 1);
+          break;
+        case 1:
+          st_release(w.trsm + tk.i, p + 1);
+          break;
+        case 2:
+          st_release(w.e(p, tk.j), p - tk.j + 1);
+          break;
+        case 3:
+          st_release(w.t(tk.i, tk.j), p + 1);
+          break;
+        default:
+          st_release(w.e(tk.i, tk.j), p - tk.j + 1);
+          break;
+      }
+    }
+  }
+}
+
+template <typename T>
+size_t flow_smem() {
+  return 3 * NB * LD * sizeof(T);  // the diagonal task's three blocks; the others need less
+}
+}  // namespace
+
+template <typename T>
+int BigFrontOps<T>::flow_occupancy() {
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem<T>()));
+  int n = 0;
+  CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<T>, NT, flow_smem<T>()));
+  return n > 0 ? n : 1;
+}
+
+template <typename T>
+int BigFrontOps<T>::flow_level(cudaStream_t st, const BigFrontDev& bf, const FlowTask* task, int64_t t0, int64_t nt,
+                               int* state, int64_t head_off, const int64_t* soff, int grid, T* F, T* E, T* Dp,
+                               const int8_t* dsign, double eps, double delta, int* hits, int* err, const int* skip) {
+  if (nt <= 0) return CLR_OK;
+  const unsigned g = (unsigned)(nt < grid ? nt : grid);
+  k_bf_flow<T><<<g, NT, flow_smem<T>(), st>>>(bf, task, t0, nt, state, head_off, soff, F, E, Dp, dsign, eps, delta,
+                                              hits, err, skip);
+  CLR_CHECK_LAUNCH();
+  return CLR_OK;
+}
+
+#define CLR_FLOW_INST(T)                                                                                         \
+  template int BigFrontOps<T>::flow_occupancy();                                                                   \
+  template int BigFrontOps<T>::flow_level(cudaStream_t, const BigFrontDev&, const FlowTask*, int64_t, int64_t, int*, \
+                                          int64_t, const int64_t*, int, T*, T*, T*, const int8_t*, double, double,   \
+                                          int*, int*, const int*);
+CLR_FLOW_INST(double)
+CLR_FLOW_INST(float)
+#undef CLR_FLOW_INST
+
+}  // namespace clr

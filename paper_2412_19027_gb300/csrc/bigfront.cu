@@ -1,8 +1,8 @@
 // Large fronts: blocked LDL^T with the augmented inverse block E (see bigfront.cuh).
 //
 // Panel p covers pivots K = [k0, k0 + pw), k0 = 64 p.  Three launches per panel:
-//   A  (one CTA per front): LDL^T of the pw x pw diagonal block (32 x 32 blocks
-//      factored and inverted by one warp), its pivots, and Linv = L_KK^{-1};
+//   A  (one CTA per front): LDL^T of the pw x pw diagonal block (one barrier per
+//      pivot), its pivots, and Linv = L_KK^{-1};
 //   B  L_IK = F_IK L_KK^{-T} D_K^{-1} for the rows I below K, as the product
 //      F_IK Linv^T scaled by D^{-1}; the same launch finalises the E rows of
 //      this panel: E_KC <- Linv E_KC (C < K) and E_KK = Linv;
@@ -45,28 +45,42 @@ __device__ __forceinline__ T reg_pivot(T d, int sgn, T eps, T delta, bool* hit) 
 }  // namespace
 
 // ------------------------------------------------------------------ A: diagonal block
-constexpr unsigned FULLMASK = 0xffffffffu;
 
-// Diagonal block of panel p: the pw x pw (<= 64) block by the whole CTA,
-// right-looking with one barrier per pivot.  Each thread owns up to kSlots
-// entries of the lower triangle (registers), and the same entries of
-// X = L^{-1}, built alongside by applying the elimination to the identity:
-// pivot k does S_ij -= L_ik S_jk (i >= j > k, L_ik = S_ik / d_k) and
-// X_ij -= L_ik X_kj (i > k >= j); the pivot column of S and row k of X go
-// through shared memory (double buffered).  A pivot with the wrong sign or
-// magnitude <= eps is replaced by sign * delta (dynamic regularisation).
-// Outputs: L (unit lower, d on the diagonal) into the front, pivots to Dp, and
-// Linv = L^{-1} (64 x 64, column-major, zero padded).
-constexpr int kTri = NB * (NB + 1) / 2;
-constexpr int kSlots = (kTri + 255) / 256;
+// Inverse of a unit lower n x n block (n <= 32) of Lo (rows/cols from r0) into Li:
+// lane j of the calling warp computes column j by forward substitution; the
+// inner products are unrolled so that several shared-memory loads are in flight.
+template <typename T>
+__device__ __forceinline__ void warp_inv32(const T* Lo, T* Li, int r0, int n) {
+  const int j = threadIdx.x & 31;
+  if (j < n) {
+    Li[(r0 + j) * LD + r0 + j] = (T)1;
+    for (int i = j + 1; i < n; ++i) {
+      T acc = (T)0;
+#pragma unroll 4
+      for (int l = j; l < i; ++l) acc += Lo[(r0 + i) * LD + r0 + l] * Li[(r0 + l) * LD + r0 + j];
+      Li[(r0 + i) * LD + r0 + j] = -acc;
+    }
+  }
+}
 
+// Diagonal block of panel p: LDL^T of the pw x pw (<= 64) block by the whole
+// CTA, right-looking, one barrier per pivot: four threads per row update that
+// row left of the diagonal (unrolled, loads in flight); the pivot column is read
+// unscaled from S (not written again) and its multipliers go to Lo.  A pivot
+// with the wrong sign or magnitude <= eps is replaced by sign * delta (dynamic
+// regularisation).  Then Linv = [A^-1 0; -B^-1 C A^-1  B^-1] for the 32-blocks
+// L = [A 0; C B].  Outputs: L (unit lower, d on the diagonal) into the front,
+// pivots to Dp, Linv (64 x 64, column-major, zero padded).
 template <typename T>
 __global__ void __launch_bounds__(256) k_bf_diag(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F,
                                                  T* __restrict__ Dp, T* __restrict__ Linv,
                                                  const int8_t* __restrict__ dsign, double eps_d, double delta_d,
                                                  int* hits, const int* skip) {
   if (skip && *skip) return;
-  __shared__ T col[2][NB], xrow[2][NB], dd[NB];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* S = reinterpret_cast<T*>(smraw);  // NB x LD: the block as it is eliminated
+  T* Lo = S + NB * LD;                 // NB x LD: L (d on the diagonal)
+  T* Li = Lo + NB * LD;                // NB x LD: L^{-1}
   __shared__ int8_t sgn[NB];
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
@@ -76,67 +90,69 @@ __global__ void __launch_bounds__(256) k_bf_diag(BigFrontDev bf, WorkList wl, in
   const int64_t kp = bf.k0pos[b] + k0;
   const int tid = threadIdx.x;
   const T eps = (T)eps_d, delta = (T)delta_d;
-  T v[kSlots], x[kSlots];
-  int ri[kSlots], cj[kSlots];
-#pragma unroll
-  for (int m = 0; m < kSlots; ++m) {
-    const int e = tid + 256 * m;
-    int i = -1, j = -1;
-    if (e < kTri) {  // column-major enumeration of the lower triangle: column j starts at j NB - j (j - 1) / 2
-      const float w = (float)(2 * NB + 1);
-      j = (int)((w - sqrtf(w * w - 8.0f * (float)e)) * 0.5f);
-      while (j > 0 && j * NB - j * (j - 1) / 2 > e) --j;
-      while ((j + 1) * NB - (j + 1) * j / 2 <= e) ++j;
-      i = j + (e - (j * NB - j * (j - 1) / 2));
-    }
-    ri[m] = i;
-    cj[m] = j;
-    v[m] = (i >= 0 && i < pw && j < pw) ? G[(k0 + i) + (k0 + j) * f] : (T)0;
-    x[m] = (i >= 0 && i == j) ? (T)1 : (T)0;
-    if (j == 0) col[0][i] = v[m];
-    if (i == 0) xrow[0][j] = x[m];
+#pragma unroll 8
+  for (int idx = tid; idx < NB * NB; idx += 256) {
+    const int i = idx % NB, j = idx / NB;
+    S[i * LD + j] = (i < pw && j < pw && i >= j) ? G[(k0 + i) + (k0 + j) * f] : (T)0;
+    Lo[i * LD + j] = (T)0;
+    Li[i * LD + j] = (T)0;
   }
   if (tid < NB) sgn[tid] = tid < pw ? dsign[kp + tid] : (int8_t)1;
   __syncthreads();
+  const int row = tid >> 2, part = tid & 3;
   int nhit = 0;
   for (int k = 0; k < pw; ++k) {
-    const int cur = k & 1, nxt = cur ^ 1;
-    T d = col[cur][k];
+    T d = S[k * LD + k];
     const T sg = (T)sgn[k];
     const bool hit = sg * d <= eps;
     if (hit) d = sg * delta;
-    const T inv = (T)1 / d;
     if (tid == 0) {
-      dd[k] = d;
       nhit += hit ? 1 : 0;
+      Lo[k * LD + k] = d;
     }
-#pragma unroll
-    for (int m = 0; m < kSlots; ++m) {
-      const int i = ri[m], j = cj[m];
-      if (i < 0) continue;
-      if (j == k) {
-        if (i > k) G[(k0 + i) + (k0 + k) * f] = v[m] * inv;  // L_ik
-      } else if (j > k) {
-        v[m] -= (col[cur][i] * inv) * col[cur][j];
-        if (j == k + 1) col[nxt][i] = v[m];
-      }
-      if (i > k && j <= k) x[m] -= (col[cur][i] * inv) * xrow[cur][j];
-      if (i == k + 1) xrow[nxt][j] = x[m];
+    if (row > k && row < pw) {
+      const T li = S[row * LD + k] / d;
+      T* sr = S + row * LD;
+#pragma unroll 4
+      for (int j = k + 1 + part; j <= row; j += 4) sr[j] -= li * S[j * LD + k];
+      if (part == 0) Lo[row * LD + k] = li;
     }
     __syncthreads();
   }
   if (tid == 0 && nhit) atomicAdd(hits, nhit);
-  for (int i = tid; i < pw; i += blockDim.x) {
-    G[(k0 + i) + (k0 + i) * f] = dd[i];
-    Dp[kp + i] = dd[i];
+  for (int idx = tid; idx < pw * pw; idx += blockDim.x) {
+    const int i = idx % pw, j = idx / pw;
+    if (i >= j) G[(k0 + i) + (k0 + j) * f] = Lo[i * LD + j];
+  }
+  for (int i = tid; i < pw; i += blockDim.x) Dp[kp + i] = Lo[i * LD + i];
+  const int cw0 = min(32, pw), cw1 = pw - cw0;
+  const int wid = tid >> 5;
+  if (wid == 0) warp_inv32(Lo, Li, 0, cw0);
+  if (wid == 1 && cw1 > 0) warp_inv32(Lo, Li, 32, cw1);
+  __syncthreads();
+  if (cw1 > 0) {
+    // X = C A^-1 (into S, free now), then Li_21 = -B^-1 X
+    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+      const int i = idx % 32, j = idx / 32;
+      T acc = (T)0;
+      if (i < cw1)
+        for (int l = j; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * Li[l * LD + j];
+      S[i * LD + j] = acc;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+      const int i = idx % 32, j = idx / 32;
+      if (i >= cw1) continue;
+      T acc = (T)0;
+      for (int l = 0; l <= i; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + j];
+      Li[(32 + i) * LD + j] = -acc;
+    }
+    __syncthreads();
   }
   T* LB = Linv + (b * 2 + (p & 1)) * (int64_t)(NB * NB);
-#pragma unroll
-  for (int m = 0; m < kSlots; ++m) {
-    const int i = ri[m], j = cj[m];
-    if (i < 0) continue;
-    LB[i + j * NB] = (i < pw && j < pw) ? x[m] : (T)0;
-    if (i != j) LB[j + i * NB] = (T)0;  // upper triangle
+  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx % NB, j = idx / NB;
+    LB[i + j * NB] = (i < pw && j < pw) ? Li[i * LD + j] : (T)0;
   }
 }
 
@@ -228,39 +244,45 @@ __global__ void __launch_bounds__(256) k_bf_trsm(BigFrontDev bf, WorkList wl, in
 }
 
 // ------------------------------------------------------------------ C: trailing and E tiles
-// 64 x 64 output tiles, 64 threads, 8 x 8 outputs per thread; operands staged
-// K-major in shared memory (row/column index contiguous for each k) so that a
-// thread reads its 8 rows and 8 columns with vector loads.
+// 64 x 64 output tiles, 256 threads, 4 x 4 outputs per thread; operands staged
+// K-major in shared memory (for each k the 64 rows / columns contiguous) and
+// read as 4-element vectors.  The 4-element units of a K-row are XOR-swizzled
+// by the row's k so that the column-wise staging of E_KC does not hit one bank.
 //   trailing tile (I >= J below K): F_IJ -= L_IK (D_K L_JK^T)
 //   E tile (rows I below K, column block C <= K): E_IC -= L_IK E_KC, with the
 //   E rows of K already finalised by this panel's B launch (E_KK = Linv).
 constexpr int LDK = NB + 4;  // 16-byte aligned rows of the K-major tiles
 
 template <typename T>
-__device__ __forceinline__ void ld8(const T* p, T (&v)[8]);
+__device__ __forceinline__ int swz(int k, int r) {  // element r of K-row k: 4-element units swizzled by k
+  return k * LDK + (((r >> 2) ^ (k & 7)) << 2) + (r & 3);
+}
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]);
 template <>
-__device__ __forceinline__ void ld8<float>(const float* p, float (&v)[8]) {
-  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+__device__ __forceinline__ void ld4<float>(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
 }
 template <>
-__device__ __forceinline__ void ld8<double>(const double* p, double (&v)[8]) {
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const double2 a = *reinterpret_cast<const double2*>(p + 2 * u);
-    v[2 * u] = a.x;
-    v[2 * u + 1] = a.y;
-  }
+__device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(64) k_bf_update(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F,
-                                                  T* __restrict__ E, const T* __restrict__ Dp, const int* skip) {
+__global__ void __launch_bounds__(256) k_bf_update(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F,
+                                                   T* __restrict__ E, const T* __restrict__ Dp, const int* skip) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Ak = reinterpret_cast<T*>(smraw);  // [l][row]
-  T* Bk = Ak + NB * LDK;                 // [l][col]
+  T* Ak = reinterpret_cast<T*>(smraw);  // [k][row], swizzled chunks
+  T* Bk = Ak + NB * LDK;                 // [k][col], swizzled chunks
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
   const int64_t f = bf.f[b], c = bf.c[b], k0 = (int64_t)p * NB;
@@ -282,12 +304,12 @@ __global__ void __launch_bounds__(64) k_bf_update(BigFrontDev bf, WorkList wl, i
     const int64_t bj = q - bi * (bi + 1) / 2;
     i0 = t0 + bi * NB;
     j0 = t0 + bj * NB;
-#pragma unroll 16
-    for (int idx = tid; idx < NB * NB; idx += 64) {
-      const int r = idx % NB, l = idx / NB;
+#pragma unroll 8
+    for (int idx = tid; idx < NB * NB; idx += 256) {
+      const int r = idx % NB, k = idx / NB;
       const int64_t ia = i0 + r, ib = j0 + r;
-      Ak[l * LDK + r] = (l < pw && ia < f) ? G[ia + (k0 + l) * f] : (T)0;
-      Bk[l * LDK + r] = (l < pw && ib < f) ? G[ib + (k0 + l) * f] * Dk[l] : (T)0;
+      Ak[swz<T>(k, r)] = (k < pw && ia < f) ? G[ia + (k0 + k) * f] : (T)0;
+      Bk[swz<T>(k, r)] = (k < pw && ib < f) ? G[ib + (k0 + k) * f] * Dk[k] : (T)0;
     }
   } else {
     const int64_t e = q - na;
@@ -295,51 +317,51 @@ __global__ void __launch_bounds__(64) k_bf_update(BigFrontDev bf, WorkList wl, i
     i0 = t0 + bi * NB;
     colbase = cb * NB;
     if (cb == p) ncols = pw;
-#pragma unroll 16
-    for (int idx = tid; idx < NB * NB; idx += 64) {
-      const int r = idx % NB, l = idx / NB;
+#pragma unroll 8
+    for (int idx = tid; idx < NB * NB; idx += 256) {
+      const int r = idx % NB, k = idx / NB;
       const int64_t ia = i0 + r;
-      Ak[l * LDK + r] = (l < pw && ia < f) ? G[ia + (k0 + l) * f] : (T)0;
-      // E_KC: row k0 + l, column colbase + r (consecutive l are consecutive in memory)
-      const int l2 = idx % NB, cc = idx / NB;
-      Bk[l2 * LDK + cc] = (l2 < pw && cc < ncols) ? Eb[(k0 + l2) + (colbase + cc) * f] : (T)0;
+      Ak[swz<T>(k, r)] = (k < pw && ia < f) ? G[ia + (k0 + k) * f] : (T)0;
+      // E_KC: consecutive threads read consecutive rows k0 + kk of column colbase + cc
+      const int kk = idx % NB, cc = idx / NB;
+      Bk[swz<T>(kk, cc)] = (kk < pw && cc < ncols) ? Eb[(k0 + kk) + (colbase + cc) * f] : (T)0;
     }
   }
   __syncthreads();
-  const int tr = tid % 8, tc = tid / 8;
-  T acc[8][8];
+  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
+  T acc[4][4];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int bb = 0; bb < 8; ++bb) acc[a][bb] = (T)0;
-  for (int l = 0; l < pw; ++l) {
-    T av[8], bv[8];
-    ld8<T>(Ak + l * LDK + 8 * tr, av);
-    ld8<T>(Bk + l * LDK + 8 * tc, bv);
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  for (int k = 0; k < pw; ++k) {
+    T av[4], bv[4];
+    ld4<T>(Ak + swz<T>(k, 4 * tr), av);
+    ld4<T>(Bk + swz<T>(k, 4 * tc), bv);
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int bb = 0; bb < 8; ++bb) acc[a][bb] += av[a] * bv[bb];
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
   }
   if (!etile) {
 #pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
-      const int64_t j = j0 + 8 * tc + bb;
+    for (int bb = 0; bb < 4; ++bb) {
+      const int64_t j = j0 + 4 * tc + bb;
       if (j >= f) continue;
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int64_t i = i0 + 8 * tr + a;
+      for (int a = 0; a < 4; ++a) {
+        const int64_t i = i0 + 4 * tr + a;
         if (i < f && i >= j) G[i + j * f] -= acc[a][bb];
       }
     }
   } else {
 #pragma unroll
-    for (int bb = 0; bb < 8; ++bb) {
-      const int cc = 8 * tc + bb;
+    for (int bb = 0; bb < 4; ++bb) {
+      const int cc = 4 * tc + bb;
       if (cc >= ncols) continue;
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int64_t i = i0 + 8 * tr + a;
+      for (int a = 0; a < 4; ++a) {
+        const int64_t i = i0 + 4 * tr + a;
         if (i < f) Eb[i + (colbase + cc) * f] -= acc[a][bb];
       }
     }
@@ -574,15 +596,12 @@ __global__ void k_bf_bwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, c
 }
 
 // ------------------------------------------------------------------ host
-namespace {
-size_t smem_diag() { return 0; }
-}  // namespace
 
 template <typename T>
 int BigFrontOps<T>::setup_attributes() {
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LDK * sizeof(T)));
-  (void)smem_diag;
   return CLR_OK;
 }
 
@@ -590,10 +609,10 @@ template <typename T>
 int BigFrontOps<T>::factor_level(cudaStream_t st, const BigFrontDev& bf, const BigLevelPlan& plan, T* F, T* E, T* Dp,
                                  T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip,
                                  bool tc16, int* err) {
-  const size_t s2 = 2 * NB * LD * sizeof(T), su = 2 * NB * LDK * sizeof(T);
+  const size_t s2 = 2 * NB * LD * sizeof(T), s3 = 3 * NB * LD * sizeof(T), su = 2 * NB * LDK * sizeof(T);
   for (size_t p = 0; p < plan.A.size(); ++p) {
     if (plan.A[p].nblocks > 0)
-      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, 0, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
+      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, s3, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
                                                                   hits, skip);
     if (plan.B[p].nblocks > 0)
       k_bf_trsm<T><<<(unsigned)plan.B[p].nblocks, 256, s2, st>>>(bf, plan.B[p], (int)p, F, E, Dp, Linv, skip);
@@ -605,7 +624,7 @@ int BigFrontOps<T>::factor_level(cudaStream_t st, const BigFrontDev& bf, const B
       }
     }
     if (plan.C[p].nblocks > 0)
-      k_bf_update<T><<<(unsigned)plan.C[p].nblocks, 64, su, st>>>(bf, plan.C[p], (int)p, F, E, Dp, skip);
+      k_bf_update<T><<<(unsigned)plan.C[p].nblocks, 256, su, st>>>(bf, plan.C[p], (int)p, F, E, Dp, skip);
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;

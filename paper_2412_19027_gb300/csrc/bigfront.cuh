@@ -42,6 +42,38 @@ struct BigLevelPlan {
   WorkList fwd, bwd;
 };
 
+// ---------------------------------------------------------------------------
+// Dataflow factorization of the big fronts of one level in ONE launch.
+// A front with c pivots and f rows is cut into blocks of 64: P = ceil(c/64)
+// pivot blocks [64b, min(64b+64, c)), then the update rows [c, f) in blocks of
+// 64 from c, nbf blocks in all.  Tasks (64 x 64 tiles):
+//   D(p)        diagonal block of panel p: LDL^T, pivots, Linv = L_KK^{-1}
+//               (written into E_KK, which it equals);
+//   T(p, i)     block row i > p of panel p: L_IK = F_IK Linv^T D_K^{-1};
+//   Efin(p, e)  E rows of panel p, column block e < p: E_KC <- Linv E_KC;
+//   U(p, i, j)  trailing tile i >= j > p: F_IJ -= L_IK D_K L_JK^T;
+//   EU(p, i, e) E tile i > p, e <= p: E_IC -= L_IK E_KC.
+// Persistent CTAs take tasks from one counter in a fixed topological order of
+// the task graph (with the next panel's diagonal block ahead of the bulk of the
+// current panel's updates); a task waits (bounded) on per-front version words
+// set by the tasks it depends on.  Every task it waits on was taken earlier by a
+// CTA that is running, so the launch needs no co-residency guarantee.
+struct FlowTask {
+  int32_t bf;    // big-front id
+  int16_t kind;  // 0 D, 1 T, 2 Efin, 3 U, 4 EU
+  int16_t p;     // panel
+  int32_t i, j;  // block row; block column (Efin: e; EU: e)
+};
+// version words of one front: tile[tri(i, j)], etile[i * P + e], diag[P], trsm[nbf]
+__host__ __device__ inline int64_t flow_nbf(int64_t f, int64_t c) {
+  return (c + kBfNB - 1) / kBfNB + (f - c + kBfNB - 1) / kBfNB;
+}
+__host__ __device__ inline int64_t flow_words(int64_t f, int64_t c) {
+  const int64_t P = (c + kBfNB - 1) / kBfNB, n = flow_nbf(f, c);
+  return n * (n + 1) / 2 + n * P + P + n;
+}
+constexpr int kFlowThreads = 256;
+
 template <typename T>
 struct BigFrontOps {
   static int setup_attributes();
@@ -54,7 +86,16 @@ struct BigFrontOps {
                  T* ybuf, const int* skip);
   static int bwd(cudaStream_t st, const BigFrontDev& bf, const WorkList& wl, const T* E, const T* Dp, const T* ybuf,
                  T* xs, const int32_t* rows_kkt, const int* skip);
+  // Dataflow factorization of one level: tasks [t0, t0 + nt) of the task table;
+  // state: zeroed words holding the level's task counter (at head_off) and, at
+  // soff[b], the version words of each big front b of the level.  err: set to 2
+  // if a wait ran out (the factor is then unusable).
+  static int flow_level(cudaStream_t st, const BigFrontDev& bf, const FlowTask* task, int64_t t0, int64_t nt,
+                        int* state, int64_t head_off, const int64_t* soff, int grid, T* F, T* E, T* Dp,
+                        const int8_t* dsign, double eps, double delta, int* hits, int* err, const int* skip);
+  static int flow_occupancy();  // resident CTAs per SM of the flow kernel
 };
+
 
 // CTA counts per front used to build the plans (must match the kernels).
 __host__ __device__ inline int64_t bf_trsm_blocks(int64_t f, int64_t c, int p) {

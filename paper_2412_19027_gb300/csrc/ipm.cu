@@ -312,7 +312,10 @@ __global__ void k_inf_norm(ChunkGrid g, const double* __restrict__ v, IterScal* 
   bool zp;
   chunk_range(g, &i0, &len, &pid, &zp);
   double mx = 0.0;
-  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) mx = fmax(mx, fabs(v[i]));
+  for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
+    const double a = fabs(v[i]);
+    mx = (a == a) ? fmax(mx, a) : INFINITY;  // a NaN entry makes the norm infinite (fmax would drop it)
+  }
   mx = block_max(mx, sh);
   if (threadIdx.x == 0) atomicMax(&sc[pid].rnorm_bits, dbits(mx));
 }
@@ -343,13 +346,14 @@ __global__ void k_set_from(ChunkGrid g, double* __restrict__ dst, const T* __res
     dst[i] = add ? dst[i] + (double)src[i] : (double)src[i];
 }
 
-// Refinement test of one problem (Sec. 3.6): stop at the tolerance, or, when
-// stop_ratio > 0, as soon as a step has reduced ||r||_inf by less than
-// stop_ratio (the last correction is kept), or after max_steps steps.  A step
-// that made ||r||_inf larger is undone (k_ir_revert) and ends the refinement:
-// the regularised factor is not a contraction for K there.
-// A refinement that ends with ||r||_inf > 1e-4 max(1, ||rhs||_inf) (or NaN) marks
-// the iteration (ir_fail): with a low-precision factor it is then redone in FP64.
+// Refinement test of one problem (Sec. 3.6): stop at the tolerance, or after
+// max_steps steps, or, when stop_ratio > 0 and ||r||_inf is already below the
+// acceptance bar fail_tol = 1e-4 max(1, ||rhs||_inf), as soon as a step has
+// reduced ||r||_inf by less than stop_ratio (the last correction is kept).  A
+// step that made ||r||_inf larger is undone (k_ir_revert) and ends the
+// refinement: the regularised factor is not a contraction for K there.
+// A refinement that ends above fail_tol (or NaN) marks the iteration
+// (ir_fail): with a low-precision factor it is then redone in FP64.
 __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double stop_ratio, int max_steps) {
   const double r = bitsd(q.rnorm_bits);
   q.rnorm_bits = 0ull;
@@ -362,7 +366,7 @@ __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double st
     if (!(q.ir_prev <= fail_tol)) q.ir_fail = 1;
     return false;
   }
-  const bool stalled = stop_ratio > 0 && !(r * stop_ratio < q.ir_prev);
+  const bool stalled = stop_ratio > 0 && r <= fail_tol && !(r * stop_ratio < q.ir_prev);
   q.ir_prev = r;
   if (!(r > abstol + reltol * q.rhs_norm) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
     q.ir_skip = 1;
@@ -852,6 +856,7 @@ int Solver::upload() {
   int rc = ldl_structure_upload(ar_, sy, mp, dsign, st.factor_bits == 64 ? 96 : 128, ls_, &pos_pid);
   if (rc != CLR_OK) return rc;
   f32_.tc16 = st.factor_bits == 16;
+  f32_.flow = f64_.flow = st.big_front_schedule == 1;
   rc = (st.factor_bits == 64) ? f64_.alloc(ar_, ls_) : f32_.alloc(ar_, ls_);
   if (rc != CLR_OK) return rc;
   // full-K CSR with value indices

@@ -404,6 +404,64 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       pd.wl->front = dbuf + pd.fo;
       pd.wl->pref = dbuf + pd.po;
     }
+    // dataflow task tables (bigfront.cuh), per level in blocks k = 0 .. max panels:
+    //   D(k), T(k, .) of every front; then the updates of panel k - 1 outside
+    //   column block k (trailing tiles by column, E tiles); then Efin(k, .) and
+    //   panel k's updates of column block k + 1, which D(k + 1) and T(k + 1, .)
+    //   wait for.  Every task depends only on tasks before it.
+    std::vector<FlowTask> tasks;
+    std::vector<int64_t> soff(bf_f.size(), 0);
+    int64_t words = 0;
+    st.flow_t0.assign(sy.nlev, 0);
+    st.flow_nt.assign(sy.nlev, 0);
+    st.flow_head.assign(sy.nlev, 0);
+    for (int64_t l = 0; l < sy.nlev; ++l) {
+      if (st.lev_big[l].empty()) continue;
+      st.flow_head[l] = words++;
+      std::vector<int64_t> ids;
+      int64_t maxp = 0;
+      for (int64_t J : st.lev_big[l]) {
+        const int64_t b = bid_of[J];
+        ids.push_back(b);
+        soff[b] = words;
+        words += flow_words(bf_f[b], bf_c[b]);
+        maxp = std::max<int64_t>(maxp, (bf_c[b] + kBfNB - 1) / kBfNB);
+      }
+      st.flow_t0[l] = (int64_t)tasks.size();
+      auto add = [&](int64_t b, int kind, int64_t p, int64_t i, int64_t j) {
+        tasks.push_back(FlowTask{(int32_t)b, (int16_t)kind, (int16_t)p, (int32_t)i, (int32_t)j});
+      };
+      for (int64_t k = 0; k <= maxp; ++k) {
+        for (int64_t b : ids) {
+          const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, n = flow_nbf(bf_f[b], bf_c[b]);
+          if (k >= P) continue;
+          add(b, 0, k, k, k);
+          for (int64_t i = k + 1; i < n; ++i) add(b, 1, k, i, k);
+        }
+        for (int64_t b : ids) {
+          const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, n = flow_nbf(bf_f[b], bf_c[b]);
+          const int64_t p = k - 1;
+          if (p < 0 || p >= P) continue;
+          for (int64_t j = p + 2; j < n; ++j)
+            for (int64_t i = j; i < n; ++i) add(b, 3, p, i, j);
+          for (int64_t i = p + 1; i < n; ++i)
+            for (int64_t e = 0; e <= p; ++e) add(b, 4, p, i, e);
+        }
+        for (int64_t b : ids) {
+          const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, n = flow_nbf(bf_f[b], bf_c[b]);
+          if (k >= P) continue;
+          for (int64_t e = 0; e < k; ++e) add(b, 2, k, k, e);
+          for (int64_t i = k + 1; i < n && k + 1 < n; ++i) add(b, 3, k, i, k + 1);
+        }
+      }
+      st.flow_nt[l] = (int64_t)tasks.size() - st.flow_t0[l];
+    }
+    st.flow_words = words;
+    if (!tasks.empty()) {
+      st.flow_task = ar.upload(tasks.data(), (int64_t)tasks.size());
+      st.flow_soff = ar.upload(soff.data(), (int64_t)soff.size());
+      if (!st.flow_task || !st.flow_soff) return CLR_E_OOM;
+    }
   }
   st.sn_ptr = up(ar, sy.sn_ptr);
   st.row_ptr = up(ar, sy.row_ptr);
@@ -447,6 +505,17 @@ int LdlFactor<T>::alloc(DeviceArena& ar, const LdlStructure& st) {
   Linv = ar.alloc_n<T>(st.bfd.n * 2 * kBfNB * kBfNB);
   if (!F || !Dp || !w || !xs || !dyn_hits || !E || !ybuf || !Linv) return CLR_E_OOM;
   if (BigFrontOps<T>::setup_attributes() != CLR_OK) return CLR_E_CUDA;
+  if (st.flow_words > 0) {
+    flow_state = ar.alloc_n<int>(st.flow_words);
+    if (!flow_state) return CLR_E_OOM;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return CLR_E_CUDA;
+    const int occ = BigFrontOps<T>::flow_occupancy();
+    if (occ < 0) return CLR_E_CUDA;
+    flow_grid = sms * occ;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_factor_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -459,7 +528,9 @@ template <typename T>
 int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* sc, double dyn_eps, double dyn_delta,
                          const int* skip) const {
   const LdlStructure& S = *s;
-  CLR_CUDA(cudaMemsetAsync(dyn_hits, 0, 2 * sizeof(int), stm));  // dynamic-regularisation hits, tensor-core error
+  CLR_CUDA(cudaMemsetAsync(dyn_hits, 0, 2 * sizeof(int), stm));  // dynamic-regularisation hits, big-front error
+  const bool use_flow = flow && !tc16 && flow_state != nullptr;
+  if (use_flow) CLR_CUDA(cudaMemsetAsync(flow_state, 0, sizeof(int) * (size_t)S.flow_words, stm));
   CLR_CUDA(cudaMemsetAsync(F, 0, sizeof(T) * (size_t)S.pool, stm));
   if (S.bfd.epool > 0) CLR_CUDA(cudaMemsetAsync(E, 0, sizeof(T) * (size_t)S.bfd.epool, stm));
   k_scatter_kval<T><<<grid_for(S.nk, 256), 256, 0, stm>>>(F, kval, S.kdest, S.nk, skip);
@@ -482,8 +553,11 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
                                                                dyn_hits, skip);
     }
     if (!S.lev_big[l].empty()) {
-      int rc = BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps, dyn_delta,
-                                            dyn_hits, skip, tc16, tc_err);
+      int rc = use_flow ? BigFrontOps<T>::flow_level(stm, S.bfd, S.flow_task, S.flow_t0[l], S.flow_nt[l], flow_state,
+                                                     S.flow_head[l], S.flow_soff, flow_grid, F, E, Dp, S.dsign,
+                                                     dyn_eps, dyn_delta, dyn_hits, tc_err, skip)
+                        : BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps,
+                                                       dyn_delta, dyn_hits, skip, tc16, tc_err);
       if (rc) return rc;
     }
     CLR_CHECK_LAUNCH();

@@ -38,6 +38,13 @@ struct LdlStructure {
   int64_t* rel_off = nullptr;
   int64_t* sn_parent = nullptr;
   std::vector<std::vector<WorkList>> push_rounds;
+  // dataflow factorization of the big fronts: task table (device), per level
+  // its task range and the offset of its task counter in the state words;
+  // per big-front id the offset of its version words
+  FlowTask* flow_task = nullptr;
+  int64_t* flow_soff = nullptr;
+  std::vector<int64_t> flow_t0, flow_nt, flow_head;
+  int64_t flow_words = 0;
   int small_max = 0;
   int64_t max_front = 0;
 };
@@ -57,8 +64,11 @@ struct LdlFactor {
   T* ybuf = nullptr;  // forward results of the big fronts
   T* Linv = nullptr;  // per big front, two 64 x 64 diagonal-block inverses
   int* dyn_hits = nullptr;
-  int* tc_err = nullptr;  // set if a tensor-core wait of the 16-bit-product updates ran out
+  int* tc_err = nullptr;  // set if a wait of the big-front kernels ran out (the factor is unusable)
   bool tc16 = false;      // big-front updates with BF16 products on the tensor cores (float only)
+  bool flow = true;       // big fronts by the dataflow kernel (one launch per level); else per-panel launches
+  int* flow_state = nullptr;
+  int flow_grid = 0;
   int alloc(DeviceArena& ar, const LdlStructure& st);
   // Factor K: kval (FP64, lower triangle entries in kval order) scattered into
   // the fronts, +/- delta added on the diagonal (x rows +, z rows -), with

@@ -243,6 +243,51 @@ int clr_cones_combined_ds(const clr_cone* cones, int32_t ncones, const double* s
   return cb.download_unperm(out, ds_out);
 }
 
+int clr_cones_time(const clr_cone* cones, int32_t ncones, const double* s, const double* z, const double* ds,
+                   const double* dz, double mu, int32_t reps, clr_cone_times* out) {
+  if ((ncones && !cones) || !out || !s || !z || !ds || !dz || reps < 1) return CLR_E_INVALID;
+  *out = clr_cone_times{-1.0, -1.0, -1.0, 0, 0};
+  ConeBench cb(cones, ncones);
+  if (cb.rc) return cb.rc;
+  out->rows = cb.m;
+  out->kkt_values = cb.cd.nkz;
+  if (cb.m == 0) return CLR_OK;
+  double *d_s = cb.upload_perm(s), *d_z = cb.upload_perm(z), *d_ds = cb.upload_perm(ds), *d_dz = cb.upload_perm(dz);
+  double* dsout = cb.ar.alloc_n<double>(cb.m);
+  if (!d_s || !d_z || !d_ds || !d_dz || !dsout) return CLR_E_OOM;
+  IterScal h{};
+  h.mu = mu;
+  h.sigma_mu = 0.1 * mu;
+  const double inf = INFINITY;
+  std::memcpy(&h.amin_bits, &inf, 8);
+  CLR_CUDA(cudaMemcpy(cb.sc, &h, sizeof(IterScal), cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  CLR_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return CLR_E_CUDA;
+  }
+  int rc = CLR_OK;
+  // 0: scaling (+ KKT block), 1: symmetric step-length ratio tests, 2: combined-step d_s
+  for (int which = 0; which < 3 && rc == CLR_OK; ++which) {
+    for (int r = 0; r <= reps && rc == CLR_OK; ++r) {
+      if (r == 1 && cudaEventRecord(e0, nullptr) != cudaSuccess) rc = CLR_E_CUDA;
+      if (rc) break;
+      if (which == 0) rc = cones_scaling(nullptr, cb.cd, d_s, d_z, cb.sc, nullptr);
+      else if (which == 1) rc = cones_step_symmetric(nullptr, cb.cd, d_s, d_ds, d_z, d_dz, cb.sc, nullptr);
+      else rc = cones_combined_ds(nullptr, cb.cd, d_s, d_z, d_ds, d_dz, cb.sc, dsout, nullptr);
+    }
+    float ms = 0.f;
+    if (rc == CLR_OK && (cudaEventRecord(e1, nullptr) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = CLR_E_CUDA;
+    if (rc == CLR_OK) (which == 0 ? out->scaling_ms : which == 1 ? out->step_ms : out->combined_ds_ms) = ms / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
 int clr_ldl_solve(const clr_csc* K, const double* signs, const int64_t* order, int32_t factor_bits,
                   double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
                   int32_t* dyn_hits_out) {

@@ -295,6 +295,45 @@ def mpc_stream(seed=0, count=10_000):
     return [int(v) for v in rng.integers(0, 2 ** 31 - 1, count)]
 
 
+def cone_stress(seed, family, count, soc_dim=5, psd_k=10):
+    """Strictly interior s, z and N(0,1) directions ds, dz for `count` cones of
+    one family (nonneg: `count` rows; SOC of dimension soc_dim; PSD of order
+    psd_k), vectorised for large counts.  Returns (cones, s, z, ds, dz)."""
+    rng = np.random.default_rng(seed)
+    if family == "nonneg":
+        cones = [(NONNEG, count, 0.0)]
+        s, z = rng.uniform(0.5, 2.0, count), rng.uniform(0.5, 2.0, count)
+        m = count
+    elif family == "soc":
+        d = soc_dim
+        cones = [(SOC, d, 0.0)] * count
+
+        def inner():
+            u = rng.standard_normal((count, d - 1))
+            t = np.linalg.norm(u, axis=1) * rng.uniform(1.5, 3.0, count) + rng.uniform(0.5, 2.0, count)
+            return np.concatenate([t[:, None], u], axis=1).ravel()
+        s, z = inner(), inner()
+        m = count * d
+    elif family == "psd":
+        k = psd_k
+        dim = k * (k + 1) // 2
+        cones = [(PSD, dim, 0.0)] * count
+        iu, ju = np.triu_indices(k)  # svec order: upper triangle by columns
+        order = np.lexsort((iu, ju))
+        iu, ju = iu[order], ju[order]
+        wgt = np.where(iu == ju, 1.0, math.sqrt(2.0))
+
+        def inner():
+            X = rng.standard_normal((count, k, k))
+            M = X @ np.swapaxes(X, 1, 2) / k + 0.5 * np.eye(k)[None]
+            return (M[:, iu, ju] * wgt[None, :]).ravel()
+        s, z = inner(), inner()
+        m = count * dim
+    else:
+        raise ValueError(family)
+    return cones, s, z, rng.standard_normal(m), rng.standard_normal(m)
+
+
 # Configurations of the measured workloads, by name.
 WORKLOADS = {
     "qp_nonneg_n50_m100": lambda seed=0: nonneg_qp(seed),

@@ -81,13 +81,16 @@ def _sampled_scalings(cones, s, z, mu, rng, k=40):
         np.testing.assert_allclose(Hg, Href, rtol=1e-8, atol=1e-10 * np.abs(Href).max())
 
 
-def _solve_full(prob, bits):
-    st = clr.clr_default_settings(bits, ir_stop_ratio=5.0)
+def _solve_full(prob, bits, **kw):
+    st = clr.clr_default_settings(bits, ir_stop_ratio=5.0, **kw)
     s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
     s.solve()
     x, sl, z, info = s.solution()
+    hist = s.history()
     s.free()
-    assert info["status_name"] == "SOLVED", info
+    # iteration, mu, pcost, dcost, res_p, res_d, gap, alpha_a, sigma, alpha_c, ir steps, tau
+    assert info["status_name"] == "SOLVED", "%s\n%s" % (
+        {k: v for k, v in info.items()}, np.array2string(hist[-6:], precision=3, max_line_width=200))
     f_star = prob.objective(prob.x_star)
     f = prob.objective(x)
     assert abs(f - f_star) <= 1e-6 * max(1.0, abs(f_star)), (f, f_star)
@@ -121,3 +124,19 @@ def test_psd_batch_2000x10_n20000_fp32():
     prob = W.psd_batch(0)
     x, s, z, info = _solve_full(prob, 32)
     _sampled_scalings(prob.cones, s, z, info["mu"] + 1e-3, np.random.default_rng(1))
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_big_front_schedules_agree(bits):
+    """The dataflow big-front kernel (one launch per level) and the per-panel
+    launches run the same arithmetic per tile: the same iterations and the same
+    optimum to rounding."""
+    prob = W.mixed_cone(0)
+    out = {}
+    for sched in (0, 1):
+        x, s, z, info = _solve_full(prob, bits, big_front_schedule=sched)
+        out[sched] = (x, info)
+    (x0, i0), (x1, i1) = out[0], out[1]
+    assert i0["iterations"] == i1["iterations"], (i0, i1)
+    f0, f1 = prob.objective(x0), prob.objective(x1)
+    assert abs(f0 - f1) <= 1e-9 * max(1.0, abs(f0))

@@ -304,3 +304,29 @@ def test_solve_with_bf16_products_mixed_cone_full_size():
     assert info["status_name"] == "SOLVED", info
     f_star = prob.objective(prob.x_star)
     assert abs(prob.objective(x) - f_star) <= 1e-6 * max(1.0, abs(f_star))
+
+
+@pytest.mark.parametrize("family,count", [("nonneg", 5000), ("soc", 700), ("psd", 40)])
+def test_cone_stress_inputs_and_timing(family, count):
+    """The cone-roofline inputs (small counts of the bench's stress shapes):
+    scalings of a sample match the oracle, and the timing entry point runs
+    the same kernels and reports the rows and packed H entries it covers."""
+    cones, s, z, ds, dz = W.cone_stress(3, family, count)
+    pick = [0, count // 2, count - 1] if family != "nonneg" else [0]
+    offs = np.cumsum([0] + [d for (_, d, _) in cones])
+    sub = [cones[i] for i in pick]
+    ss = np.concatenate([s[offs[i]:offs[i + 1]] for i in pick])
+    zz = np.concatenate([z[offs[i]:offs[i + 1]] for i in pick])
+    H = clr.clr_cones_scaling(sub, ss, zz, 1.0)
+    off = 0
+    for (t, d, a), Hg in zip(sub, H):
+        ref = C.nt_scaling(t, ss[off:off + d], zz[off:off + d])["H"]
+        np.testing.assert_allclose(Hg, ref, rtol=1e-9, atol=1e-11 * max(1.0, np.abs(ref).max()))
+        off += d
+    t = clr.clr_cones_time(cones, s, z, ds, dz, 1.0, reps=3)
+    assert t["rows"] == len(s)
+    dim = cones[0][1]
+    packed = {"nonneg": len(s), "soc": count * dim * (dim + 1) // 2, "psd": count * dim * (dim + 1) // 2}[family]
+    assert t["kkt_values"] == packed
+    for k in ("scaling_ms", "step_ms", "combined_ds_ms"):
+        assert 0.0 < t[k] < 1e3, t
