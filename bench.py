@@ -262,6 +262,13 @@ def run_serving(args, clr, W):
     reqs = [clr.Request(p.P, p.q, p.A, p.b, p.cones) for p in probs]
     t_gen = time.perf_counter() - t_gen
     st = clr.clr_default_settings(args.serve_bits)
+    # blocking parameters for the stream's cohorts, picked by the autotuner on a
+    # 64-problem cohort of the stream's shapes (3 IPM iterations per candidate)
+    t_tune = time.perf_counter()
+    tune = clr.clr_autotune([(p.P, p.q, p.A, p.b, p.cones) for p in probs[-64:]], st, iters=3)
+    tune["seconds"] = time.perf_counter() - t_tune
+    st = clr.clr_default_settings(args.serve_bits, small_front_max=tune["small_front_max"],
+                                  amalgamation=tune["amalgamation"], big_front_schedule=tune["big_front_schedule"])
     # one at a time: the whole public call sequence per problem
     k1 = min(200, len(probs))
     lat1 = []
@@ -295,7 +302,8 @@ def run_serving(args, clr, W):
             "server": {"max_cohort": 256, "max_active": 4, "device_budget_bytes": 16 << 30,
                        "cohorts": stats["cohorts"], "max_cohort_seen": stats["max_cohort_seen"],
                        "peak_device_bytes": stats["peak_bytes"]},
-            "one_at_a_time": one, "saturation": sat, "poisson": pois, "sweep_vs_one_at_a_time": sweep,
+            "autotune": tune, "one_at_a_time": one, "saturation": sat, "poisson": pois,
+            "sweep_vs_one_at_a_time": sweep,
             "speedup_solves_per_s": sat["solves_per_s"] / rate1, "generation_s": t_gen}
 
 

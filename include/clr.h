@@ -116,6 +116,11 @@ typedef struct {
   int32_t big_front_schedule; /* large fronts: 1 (default) one dataflow launch per level, tile tasks started as
                                  their inputs are ready; 0 three launches per 64-column panel.  The
                                  16-bit-products variant always uses the per-panel launches. */
+  int32_t small_front_max;    /* fronts of at most this order are factored by one CTA each in shared memory,
+                                 larger ones by the big-front kernels; 0 (default): 128 (FP32 / 16-bit
+                                 products), 96 (FP64); at most 224 (FP32) / 160 (FP64) */
+  int32_t amalgamation;       /* relaxed supernode amalgamation: 0 off, 1 (default) column thresholds
+                                 4 / 16 / 48, 2 thresholds 8 / 32 / 96 (same zero ratios) */
 } clr_settings;
 
 typedef struct {
@@ -277,6 +282,29 @@ int clr_batch_update_qb(clr_solver* s, int32_t i, const double* q, const double*
  * of clr_setup + clr_solve on the same problem up to the rounding of the K
  * products.  All host threads are owned by the server.
  * ------------------------------------------------------------------------ */
+/* Autotuner of the factorization's blocking parameters (small_front_max,
+ * amalgamation, big_front_schedule) for a cohort of problems: every candidate
+ * (small_front_max in {64, 96, 128, 160} plus 192 for FP32 factors, amalgamation
+ * 0..2, both schedules) is set up as a cohort of `probs` with the other fields
+ * of *base and solved for `iters` (>= 1) IPM iterations; the device time per
+ * iteration (CUDA events: residuals, scaling, factorization, solves, steps)
+ * picks the winner.  With cache_path non-NULL the result is looked up first
+ * in that text file under a key made of the factor precision, the cohort size,
+ * total n, m, nnz(P), nnz(A) and cone counts per family, and appended to it
+ * after a run (one line per key).  out: the chosen fields, its ms per
+ * iteration and that of *base's own fields.  Host-side analysis is repeated
+ * per candidate, so the call takes seconds for large problems.  Errors: as
+ * clr_batch_setup; CLR_E_INVALID for iters < 1. */
+typedef struct {
+  int32_t small_front_max, amalgamation, big_front_schedule;
+  int32_t candidates;        /* candidates timed (0 when read from the cache) */
+  double ms_per_iter;        /* chosen fields */
+  double base_ms_per_iter;   /* *base's fields (-1 when read from the cache) */
+  int32_t from_cache, pad;
+} clr_tune_result;
+int clr_autotune(int32_t nprob, const clr_problem* probs, const clr_settings* base, int32_t iters,
+                 const char* cache_path, clr_tune_result* out);
+
 typedef struct clr_server clr_server;
 
 typedef struct {

@@ -43,7 +43,8 @@ class clr_settings(C.Structure):
                 ("ruiz_passes", C.c_int32), ("scale_min", C.c_double), ("scale_max", C.c_double),
                 ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
                 ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32),
-                ("fp64_escalation", C.c_int32), ("big_front_schedule", C.c_int32)]
+                ("fp64_escalation", C.c_int32), ("big_front_schedule", C.c_int32),
+                ("small_front_max", C.c_int32), ("amalgamation", C.c_int32)]
 
 
 class clr_info(C.Structure):
@@ -58,6 +59,12 @@ class clr_info(C.Structure):
 class clr_cone_times(C.Structure):
     _fields_ = [("scaling_ms", C.c_double), ("step_ms", C.c_double), ("combined_ds_ms", C.c_double),
                 ("rows", C.c_int64), ("kkt_values", C.c_int64)]
+
+
+class clr_tune_result(C.Structure):
+    _fields_ = [("small_front_max", C.c_int32), ("amalgamation", C.c_int32), ("big_front_schedule", C.c_int32),
+                ("candidates", C.c_int32), ("ms_per_iter", C.c_double), ("base_ms_per_iter", C.c_double),
+                ("from_cache", C.c_int32), ("pad", C.c_int32)]
 
 
 class clr_symbolic_stats(C.Structure):
@@ -92,7 +99,7 @@ EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr
            "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_cones_time", "clr_ldl_solve",
            "clr_dense_ldl_solve_noalloc", "clr_batch_setup", "clr_batch_analyze", "clr_batch_size", "clr_batch_get",
            "clr_batch_update_qb", "clr_server_create", "clr_server_submit", "clr_server_poll", "clr_server_wait",
-           "clr_server_get_stats", "clr_server_destroy"]
+           "clr_server_get_stats", "clr_server_destroy", "clr_autotune"]
 
 
 def _lib():
@@ -145,6 +152,8 @@ def _lib():
                                       P(clr_info)]
         L.clr_server_get_stats.argtypes = [vp, P(clr_server_stats)]
         L.clr_server_destroy.argtypes = [vp]
+        L.clr_autotune.argtypes = [C.c_int32, P(clr_problem), P(clr_settings), C.c_int32, C.c_char_p,
+                                   P(clr_tune_result)]
         _LIB = L
     return _LIB
 
@@ -348,6 +357,19 @@ def clr_batch_setup(problems, settings=None):
 
 def clr_batch_analyze(problems, settings=None):
     return Batch(problems, settings, device=False)
+
+
+def clr_autotune(problems, settings=None, iters=3, cache_path=None):
+    """Pick small_front_max, amalgamation and big_front_schedule for a cohort of
+    problems (sequence of (P_upper, q, A, b, cones)) by timing candidate settings
+    on the device (see include/clr.h).  Returns a dict of the result."""
+    reqs = [Request(*p) for p in problems]
+    arr = (clr_problem * len(reqs))(*[r.prob for r in reqs])
+    st = _settings(settings)
+    out = clr_tune_result()
+    path = cache_path.encode() if cache_path else None
+    _check(_lib().clr_autotune(len(reqs), arr, C.byref(st), int(iters), path, C.byref(out)), "clr_autotune")
+    return {k: getattr(out, k) for (k, _) in clr_tune_result._fields_ if k != "pad"}
 
 
 class Request:

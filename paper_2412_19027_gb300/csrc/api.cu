@@ -2,8 +2,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <thread>
 
 #include "ipm.cuh"
@@ -51,6 +53,8 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.verbose = 0;
   s.fp64_escalation = 1;
   s.big_front_schedule = 1;
+  s.small_front_max = 0;
+  s.amalgamation = 1;
   *out = s;
   return CLR_OK;
 }
@@ -59,6 +63,9 @@ static int check_settings(const clr_settings& s) {
   if (s.factor_bits != 64 && s.factor_bits != 32 && s.factor_bits != 16) return CLR_E_INVALID;
   if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0 ||
       !(s.ir_stop_ratio >= 0) || (s.big_front_schedule != 0 && s.big_front_schedule != 1))
+    return CLR_E_INVALID;
+  if (s.small_front_max < 0 || s.small_front_max > (s.factor_bits == 64 ? 160 : 224) || s.amalgamation < 0 ||
+      s.amalgamation > 2)
     return CLR_E_INVALID;
   if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
   if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;
@@ -170,6 +177,112 @@ int clr_batch_setup(clr_solver** out, int32_t nprob, const clr_problem* probs, c
 
 int clr_batch_analyze(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st) {
   return make_batch(out, nprob, probs, st, false);
+}
+
+// ---- autotuner ----
+static std::string tune_key(int32_t nprob, const clr_problem* probs, const clr_settings& st) {
+  int64_t n = 0, m = 0, nnzp = 0, nnza = 0, cnt[6] = {0, 0, 0, 0, 0, 0};
+  for (int32_t i = 0; i < nprob; ++i) {
+    const clr_problem& p = probs[i];
+    if (p.A) {
+      n += p.A->ncols;
+      m += p.A->nrows;
+      nnza += p.A->nnz;
+    }
+    if (p.P_upper) nnzp += p.P_upper->nnz;
+    for (int32_t c = 0; c < p.ncones && p.cones; ++c)
+      if (p.cones[c].type >= 0 && p.cones[c].type < 6) cnt[p.cones[c].type] += p.cones[c].type <= 1 ? p.cones[c].dim : 1;
+  }
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "bits=%d;B=%d;n=%lld;m=%lld;nnzP=%lld;nnzA=%lld;cones=%lld,%lld,%lld,%lld,%lld,%lld",
+                st.factor_bits, nprob, (long long)n, (long long)m, (long long)nnzp, (long long)nnza, (long long)cnt[0],
+                (long long)cnt[1], (long long)cnt[2], (long long)cnt[3], (long long)cnt[4], (long long)cnt[5]);
+  return buf;
+}
+
+// device ms per IPM iteration of a cohort with settings s (iters iterations)
+static int tune_time(int32_t nprob, const clr_problem* probs, const clr_settings& s, double* ms) {
+  clr_solver* h = nullptr;
+  int rc = make_batch(&h, nprob, probs, &s, true);
+  if (rc) return rc;
+  rc = h->impl.solve();
+  if (rc == CLR_OK) {
+    const clr_perf& p = h->impl.perf;
+    const double tot = p.resid_cones_ms + p.factor_ms + p.solve_step_ms;
+    *ms = tot / std::max(1, p.iterations);
+  }
+  clr_free(h);
+  return rc;
+}
+
+int clr_autotune(int32_t nprob, const clr_problem* probs, const clr_settings* base, int32_t iters,
+                 const char* cache_path, clr_tune_result* out) {
+  if (!out || !base || iters < 1 || nprob < 1 || !probs) return CLR_E_INVALID;
+  int rc = check_settings(*base);
+  if (rc) return rc;
+  *out = clr_tune_result{};
+  const std::string key = tune_key(nprob, probs, *base);
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[512];
+      while (std::fgets(line, sizeof(line), f)) {
+        char k[300];
+        int sm = 0, am = 0, sc = 0;
+        double ms = 0;
+        if (std::sscanf(line, "%299s %d %d %d %lf", k, &sm, &am, &sc, &ms) == 5 && key == k) {
+          out->small_front_max = sm;
+          out->amalgamation = am;
+          out->big_front_schedule = sc;
+          out->ms_per_iter = ms;
+          out->base_ms_per_iter = -1;
+          out->from_cache = 1;
+        }
+      }
+      std::fclose(f);
+      if (out->from_cache) return CLR_OK;
+    }
+  }
+  clr_settings s = *base;
+  s.max_iter = iters;
+  s.verbose = 0;
+  double ms = 0;
+  rc = tune_time(nprob, probs, s, &ms);  // warm-up (module load, allocator pools)
+  if (rc) return rc;
+  rc = tune_time(nprob, probs, s, &ms);
+  if (rc) return rc;
+  out->base_ms_per_iter = ms;
+  out->small_front_max = s.small_front_max;
+  out->amalgamation = s.amalgamation;
+  out->big_front_schedule = s.big_front_schedule;
+  out->ms_per_iter = ms;
+  const int fronts64[] = {64, 96, 128, 160};
+  const int fronts32[] = {64, 96, 128, 160, 192};
+  const bool f64 = base->factor_bits == 64;
+  const int* fr = f64 ? fronts64 : fronts32;
+  const int nfr = f64 ? 4 : 5;
+  for (int a = 0; a <= 2; ++a)
+    for (int i = 0; i < nfr; ++i)
+      for (int sc = 0; sc <= 1; ++sc) {
+        s.small_front_max = fr[i];
+        s.amalgamation = a;
+        s.big_front_schedule = sc;
+        rc = tune_time(nprob, probs, s, &ms);
+        if (rc) return rc;
+        out->candidates += 1;
+        if (ms < out->ms_per_iter) {
+          out->ms_per_iter = ms;
+          out->small_front_max = fr[i];
+          out->amalgamation = a;
+          out->big_front_schedule = sc;
+        }
+      }
+  if (cache_path)
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), out->small_front_max, out->amalgamation,
+                   out->big_front_schedule, out->ms_per_iter);
+      std::fclose(f);
+    }
+  return CLR_OK;
 }
 
 int32_t clr_batch_size(const clr_solver* s) { return s ? (int32_t)s->impl.nprob() : 0; }

@@ -5,6 +5,7 @@
 // (bigfront.cu); only the scheduling differs: the diagonal block of panel p + 1
 // starts as soon as its own tile has received panel p's update, while the rest
 // of panel p's updates are still running.
+#include "bfdiag.cuh"
 #include "bigfront.cuh"
 
 namespace clr {
@@ -31,7 +32,7 @@ __device__ bool wait_ge(const int* p, int v, int* err) {
     if (ld_acquire(p) >= v) return true;
     if (it >= 16) {
       if (ld_acquire(err) != 0) return false;
-      __nanosleep(256);
+      __nanosleep(64);
     }
   }
   atomicExch(err, 2);
@@ -82,100 +83,19 @@ __device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
   v[3] = b.y;
 }
 
-// Inverse of a unit lower n x n block (n <= 32) of Lo from row r0 into Li: lane
-// j of the calling warp computes column j by forward substitution.
-template <typename T>
-__device__ __forceinline__ void warp_inv32(const T* Lo, T* Li, int r0, int n) {
-  const int j = threadIdx.x & 31;
-  if (j < n) {
-    Li[(r0 + j) * LD + r0 + j] = (T)1;
-    for (int i = j + 1; i < n; ++i) {
-      T acc = (T)0;
-#pragma unroll 4
-      for (int l = j; l < i; ++l) acc += Lo[(r0 + i) * LD + r0 + l] * Li[(r0 + l) * LD + r0 + j];
-      Li[(r0 + i) * LD + r0 + j] = -acc;
-    }
-  }
-}
-
-// D(p): LDL^T of the pw x pw diagonal block (right-looking, one barrier per
-// pivot, dynamic regularisation of wrong-signed or tiny pivots), L and the
-// pivots written back, Linv = L_KK^{-1} written into E_KK.
+// D(p): LDL^T of the pw x pw diagonal block with dynamic regularisation (see
+// bfdiag.cuh); L and the pivots written back, Linv = L_KK^{-1} written into
+// E_KK, which it equals (the zeros above its diagonal are the E pool's).
 template <typename T>
 __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T* F, T* E, T* Dp,
-                          const int8_t* dsign, T eps, T delta, int* hits, T* sm, int8_t* sgn) {
-  T* S = sm;
-  T* Lo = S + NB * LD;
-  T* Li = Lo + NB * LD;
+                          const int8_t* dsign, T eps, T delta, int* hits, T* sm, DiagScratch<T>& sh) {
   const int64_t f = g.f, k0 = (int64_t)p * NB;
   const int pw = bnrow(g, p);
-  T* G = F + bf.goff[b];
-  T* Eb = E + bf.eoff[b];
   const int64_t kp = bf.k0pos[b] + k0;
-  const int tid = threadIdx.x;
-#pragma unroll 4
-  for (int idx = tid; idx < NB * NB; idx += NT) {
-    const int i = idx % NB, j = idx / NB;
-    S[i * LD + j] = (i < pw && j < pw && i >= j) ? __ldcg(G + (k0 + i) + (k0 + j) * f) : (T)0;
-    Lo[i * LD + j] = (T)0;
-    Li[i * LD + j] = (T)0;
-  }
-  if (tid < NB) sgn[tid] = tid < pw ? dsign[kp + tid] : (int8_t)1;
-  __syncthreads();
-  const int row = tid >> 2, part = tid & 3;
-  int nhit = 0;
-  for (int k = 0; k < pw; ++k) {
-    T d = S[k * LD + k];
-    const T sg = (T)sgn[k];
-    const bool hit = sg * d <= eps;
-    if (hit) d = sg * delta;
-    if (tid == 0) {
-      nhit += hit ? 1 : 0;
-      Lo[k * LD + k] = d;
-    }
-    if (row > k && row < pw) {
-      const T li = S[row * LD + k] / d;
-      T* sr = S + row * LD;
-#pragma unroll 4
-      for (int j = k + 1 + part; j <= row; j += 4) sr[j] -= li * S[j * LD + k];
-      if (part == 0) Lo[row * LD + k] = li;
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && nhit) atomicAdd(hits, nhit);
-  for (int idx = tid; idx < pw * pw; idx += NT) {
-    const int i = idx % pw, j = idx / pw;
-    if (i >= j) G[(k0 + i) + (k0 + j) * f] = Lo[i * LD + j];
-  }
-  for (int i = tid; i < pw; i += NT) Dp[kp + i] = Lo[i * LD + i];
-  const int cw0 = min(32, pw), cw1 = pw - cw0;
-  const int wid = tid >> 5;
-  if (wid == 0) warp_inv32(Lo, Li, 0, cw0);
-  if (wid == 1 && cw1 > 0) warp_inv32(Lo, Li, 32, cw1);
-  __syncthreads();
-  if (cw1 > 0) {
-    // L = [A 0; C B]: X = C A^-1 (into S), then Li_21 = -B^-1 X
-    for (int idx = tid; idx < 32 * 32; idx += NT) {
-      const int i = idx % 32, j = idx / 32;
-      T acc = (T)0;
-      if (i < cw1)
-        for (int l = j; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * Li[l * LD + j];
-      S[i * LD + j] = acc;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 32 * 32; idx += NT) {
-      const int i = idx % 32, j = idx / 32;
-      if (i >= cw1) continue;
-      T acc = (T)0;
-      for (int l = 0; l <= i; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + j];
-      Li[(32 + i) * LD + j] = -acc;
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < pw * pw; idx += NT) {
-    const int i = idx % pw, j = idx / pw;
-    Eb[(k0 + i) + (k0 + j) * f] = Li[i * LD + j];  // zero above the diagonal
-  }
+  T* G = F + bf.goff[b] + k0 + k0 * f;
+  T* Li = E + bf.eoff[b] + k0 + k0 * f;
+  const int nhit = bf_diag_block<T>(G, f, pw, Dp + kp, Li, f, false, dsign + kp, eps, delta, sm, sh);
+  if (threadIdx.x == 0 && nhit) atomicAdd(hits, nhit);
 }
 
 // T(p, i): L_IK = F_IK Linv^T D_K^{-1} for the rows of block i (each thread 4 x 4).
@@ -191,7 +111,7 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
   T* G = F + bf.goff[b];
   const T* Eb = E + bf.eoff[b];
   const int tid = threadIdx.x;
-#pragma unroll 4
+#pragma unroll
   for (int idx = tid; idx < NB * NB; idx += NT) {
     const int i = idx % NB, j = idx / NB;
     Ls[i * LD + j] = (i < pw && j < pw) ? __ldcg(Eb + (k0 + i) + (k0 + j) * f) : (T)0;
@@ -237,7 +157,7 @@ __device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
   const int pw = bnrow(g, p);
   T* Eb = E + bf.eoff[b];
   const int tid = threadIdx.x;
-#pragma unroll 4
+#pragma unroll
   for (int idx = tid; idx < NB * NB; idx += NT) {
     const int i = idx % NB, j = idx / NB;
     Ls[i * LD + j] = (i < pw && j < pw) ? __ldcg(Eb + (k0 + i) + (k0 + j) * f) : (T)0;
@@ -290,7 +210,7 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
   if (!etile) {
     c0 = brow0(g, bj);
     nc = bnrow(g, bj);
-#pragma unroll 4
+#pragma unroll
     for (int idx = tid; idx < NB * NB; idx += NT) {
       const int r = idx % NB, k = idx / NB;
       Ak[swz(k, r)] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
@@ -299,7 +219,7 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
   } else {
     c0 = bj * NB;
     nc = bnrow(g, bj);
-#pragma unroll 4
+#pragma unroll
     for (int idx = tid; idx < NB * NB; idx += NT) {
       const int r = idx % NB, k = idx / NB;
       Ak[swz(k, r)] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
@@ -346,7 +266,7 @@ __global__ void __launch_bounds__(NT, 2)
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  __shared__ int8_t sgn[NB];
+  __shared__ DiagScratch<T> dsh;
   __shared__ T dl[NB];
   __shared__ FlowTask s_task;
   __shared__ int s_go;
@@ -399,7 +319,7 @@ __global__ void __launch_bounds__(NT, 2)
     const Geo g{bf.f[b], bf.c[b], (bf.c[b] + NB - 1) / NB, flow_nbf(bf.f[b], bf.c[b])};
     switch (tk.kind) {
       case 0:
-        task_diag<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, sgn);
+        task_diag<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, dsh);
         break;
       case 1:
         task_trsm<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
@@ -441,8 +361,9 @@ __global__ void __launch_bounds__(NT, 2)
 }
 
 template <typename T>
-size_t flow_smem() {
-  return 3 * NB * LD * sizeof(T);  // the diagonal task's three blocks; the others need less
+size_t flow_smem() {  // the update task's two operand tiles; the diagonal task needs less
+  static_assert(2 * NB * LDK >= kDiagSmem && 2 * NB * LDK >= 2 * NB * LD, "shared memory of the flow tasks");
+  return 2 * NB * LDK * sizeof(T);
 }
 }  // namespace
 

@@ -2,7 +2,7 @@
 //
 // Panel p covers pivots K = [k0, k0 + pw), k0 = 64 p.  Three launches per panel:
 //   A  (one CTA per front): LDL^T of the pw x pw diagonal block (one barrier per
-//      pivot), its pivots, and Linv = L_KK^{-1};
+//      pivot, bfdiag.cuh), its pivots, and Linv = L_KK^{-1};
 //   B  L_IK = F_IK L_KK^{-T} D_K^{-1} for the rows I below K, as the product
 //      F_IK Linv^T scaled by D^{-1}; the same launch finalises the E rows of
 //      this panel: E_KC <- Linv E_KC (C < K) and E_KK = Linv;
@@ -14,6 +14,7 @@
 
 #include <type_traits>
 
+#include "bfdiag.cuh"
 #include "bigfront.cuh"
 
 namespace clr {
@@ -46,31 +47,10 @@ __device__ __forceinline__ T reg_pivot(T d, int sgn, T eps, T delta, bool* hit) 
 
 // ------------------------------------------------------------------ A: diagonal block
 
-// Inverse of a unit lower n x n block (n <= 32) of Lo (rows/cols from r0) into Li:
-// lane j of the calling warp computes column j by forward substitution; the
-// inner products are unrolled so that several shared-memory loads are in flight.
-template <typename T>
-__device__ __forceinline__ void warp_inv32(const T* Lo, T* Li, int r0, int n) {
-  const int j = threadIdx.x & 31;
-  if (j < n) {
-    Li[(r0 + j) * LD + r0 + j] = (T)1;
-    for (int i = j + 1; i < n; ++i) {
-      T acc = (T)0;
-#pragma unroll 4
-      for (int l = j; l < i; ++l) acc += Lo[(r0 + i) * LD + r0 + l] * Li[(r0 + l) * LD + r0 + j];
-      Li[(r0 + i) * LD + r0 + j] = -acc;
-    }
-  }
-}
-
-// Diagonal block of panel p: LDL^T of the pw x pw (<= 64) block by the whole
-// CTA, right-looking, one barrier per pivot: four threads per row update that
-// row left of the diagonal (unrolled, loads in flight); the pivot column is read
-// unscaled from S (not written again) and its multipliers go to Lo.  A pivot
-// with the wrong sign or magnitude <= eps is replaced by sign * delta (dynamic
-// regularisation).  Then Linv = [A^-1 0; -B^-1 C A^-1  B^-1] for the 32-blocks
-// L = [A 0; C B].  Outputs: L (unit lower, d on the diagonal) into the front,
-// pivots to Dp, Linv (64 x 64, column-major, zero padded).
+// Diagonal block of panel p (one CTA per front): LDL^T with dynamic
+// regularisation and Linv = L_KK^{-1} (bfdiag.cuh).  Outputs: L (unit lower, d
+// on the diagonal) into the front, pivots to Dp, Linv (64 x 64, column-major,
+// zero padded) into the front's slot of the panel's parity.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bf_diag(BigFrontDev bf, WorkList wl, int p, T* __restrict__ F,
                                                  T* __restrict__ Dp, T* __restrict__ Linv,
@@ -78,82 +58,16 @@ __global__ void __launch_bounds__(256) k_bf_diag(BigFrontDev bf, WorkList wl, in
                                                  int* hits, const int* skip) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* S = reinterpret_cast<T*>(smraw);  // NB x LD: the block as it is eliminated
-  T* Lo = S + NB * LD;                 // NB x LD: L (d on the diagonal)
-  T* Li = Lo + NB * LD;                // NB x LD: L^{-1}
-  __shared__ int8_t sgn[NB];
+  __shared__ DiagScratch<T> sh;
   int64_t b, q;
   locate(wl, blockIdx.x, &b, &q);
   const int64_t f = bf.f[b], c = bf.c[b], k0 = (int64_t)p * NB;
   const int pw = (int)min((int64_t)NB, c - k0);
-  T* G = F + bf.goff[b];
   const int64_t kp = bf.k0pos[b] + k0;
-  const int tid = threadIdx.x;
-  const T eps = (T)eps_d, delta = (T)delta_d;
-#pragma unroll 8
-  for (int idx = tid; idx < NB * NB; idx += 256) {
-    const int i = idx % NB, j = idx / NB;
-    S[i * LD + j] = (i < pw && j < pw && i >= j) ? G[(k0 + i) + (k0 + j) * f] : (T)0;
-    Lo[i * LD + j] = (T)0;
-    Li[i * LD + j] = (T)0;
-  }
-  if (tid < NB) sgn[tid] = tid < pw ? dsign[kp + tid] : (int8_t)1;
-  __syncthreads();
-  const int row = tid >> 2, part = tid & 3;
-  int nhit = 0;
-  for (int k = 0; k < pw; ++k) {
-    T d = S[k * LD + k];
-    const T sg = (T)sgn[k];
-    const bool hit = sg * d <= eps;
-    if (hit) d = sg * delta;
-    if (tid == 0) {
-      nhit += hit ? 1 : 0;
-      Lo[k * LD + k] = d;
-    }
-    if (row > k && row < pw) {
-      const T li = S[row * LD + k] / d;
-      T* sr = S + row * LD;
-#pragma unroll 4
-      for (int j = k + 1 + part; j <= row; j += 4) sr[j] -= li * S[j * LD + k];
-      if (part == 0) Lo[row * LD + k] = li;
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && nhit) atomicAdd(hits, nhit);
-  for (int idx = tid; idx < pw * pw; idx += blockDim.x) {
-    const int i = idx % pw, j = idx / pw;
-    if (i >= j) G[(k0 + i) + (k0 + j) * f] = Lo[i * LD + j];
-  }
-  for (int i = tid; i < pw; i += blockDim.x) Dp[kp + i] = Lo[i * LD + i];
-  const int cw0 = min(32, pw), cw1 = pw - cw0;
-  const int wid = tid >> 5;
-  if (wid == 0) warp_inv32(Lo, Li, 0, cw0);
-  if (wid == 1 && cw1 > 0) warp_inv32(Lo, Li, 32, cw1);
-  __syncthreads();
-  if (cw1 > 0) {
-    // X = C A^-1 (into S, free now), then Li_21 = -B^-1 X
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
-      T acc = (T)0;
-      if (i < cw1)
-        for (int l = j; l < 32; ++l) acc += Lo[(32 + i) * LD + l] * Li[l * LD + j];
-      S[i * LD + j] = acc;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
-      const int i = idx % 32, j = idx / 32;
-      if (i >= cw1) continue;
-      T acc = (T)0;
-      for (int l = 0; l <= i; ++l) acc += Li[(32 + i) * LD + 32 + l] * S[l * LD + j];
-      Li[(32 + i) * LD + j] = -acc;
-    }
-    __syncthreads();
-  }
   T* LB = Linv + (b * 2 + (p & 1)) * (int64_t)(NB * NB);
-  for (int idx = tid; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx % NB, j = idx / NB;
-    LB[i + j * NB] = (i < pw && j < pw) ? Li[i * LD + j] : (T)0;
-  }
+  const int nhit = bf_diag_block<T>(F + bf.goff[b] + k0 + k0 * f, f, pw, Dp + kp, LB, NB, true, dsign + kp,
+                                    (T)eps_d, (T)delta_d, reinterpret_cast<T*>(smraw), sh);
+  if (threadIdx.x == 0 && nhit) atomicAdd(hits, nhit);
 }
 
 // ------------------------------------------------------------------ B: panel rows + E finalisation
@@ -370,10 +284,12 @@ __global__ void __launch_bounds__(256) k_bf_update(BigFrontDev bf, WorkList wl, 
 
 // ------------------------------------------------------------------ C on the tensor cores
 // The same updates as k_bf_update with 16-bit products: 128 x 64 output tiles,
-// operands rounded to BF16 and staged K-major in shared memory as 8-row x
-// 16-byte core matrices (no swizzle; core matrix (row group g, k group h) at
-// g * 1024 + h * 128 bytes), tcgen05.mma kind::f16 (M = 128, N = 64, 4 x K=16)
-// accumulating in FP32 in tensor memory (64 columns), then F -= acc in FP32.
+// each FP32 operand split into two BF16 parts (hi = bf16(v), lo = bf16(v - hi))
+// and the product formed as hi*hi + hi*lo + lo*hi (the lo*lo term, ~2^-16
+// relative, is dropped), accumulated in FP32 in tensor memory by tcgen05.mma
+// kind::f16 (M = 128, N = 64, K = 16, 12 instructions per panel).  Operands are
+// staged K-major in shared memory as 8-row x 16-byte core matrices (no
+// swizzle; core matrix (row group g, k group h) at g * 1024 + h * 128 bytes).
 // One thread issues the MMAs; completion is signalled on an mbarrier whose
 // wait is bounded (on time-out the tile is skipped and *err set).
 namespace {
@@ -392,18 +308,27 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
 __device__ __forceinline__ uint32_t tc_off(int r, int k) {  // byte offset of element (r, k) of a 16-bit tile
   return (uint32_t)((r >> 3) * kTcSBO + (k >> 3) * kTcLBO + (r & 7) * 16 + (k & 7) * 2);
 }
-__device__ __forceinline__ uint16_t to_bf16(float v) {
+// v = hi + lo + O(2^-16 |v|), hi and lo BF16 (round to nearest)
+__device__ __forceinline__ void split_bf16(float v, uint16_t* hi, uint16_t* lo) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  return *reinterpret_cast<const uint16_t*>(&h);
+  const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+  *hi = *reinterpret_cast<const uint16_t*>(&h);
+  *lo = *reinterpret_cast<const uint16_t*>(&l);
 }
+constexpr int kTcA = 128 * kBfNB * 2, kTcB = 64 * kBfNB * 2;  // bytes of one BF16 operand tile
+constexpr size_t kTcSmem = 2 * (size_t)kTcA + 2 * (size_t)kTcB + 1024;  // hi and lo of A and B, alignment slack
 }  // namespace
 
 __global__ void __launch_bounds__(128) k_bf_update_tc(BigFrontDev bf, WorkList wl, int p, float* __restrict__ F,
                                                       float* __restrict__ E, const float* __restrict__ Dp, int* err,
                                                       const int* skip) {
   if (skip && *skip) return;
-  __shared__ __align__(1024) uint8_t sA[128 * NB * 2];
-  __shared__ __align__(1024) uint8_t sB[64 * NB * 2];
+  extern __shared__ __align__(16) uint8_t tcraw[];
+  // operand tiles from a 1024-byte aligned base: A hi, A lo, B hi, B lo
+  uint8_t* sA = tcraw + ((1024 - (smem_addr(tcraw) & 1023)) & 1023);
+  uint8_t* sAl = sA + kTcA;
+  uint8_t* sB = sAl + kTcA;
+  uint8_t* sBl = sB + kTcB;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   int64_t b, q;
@@ -441,20 +366,20 @@ __global__ void __launch_bounds__(128) k_bf_update_tc(BigFrontDev bf, WorkList w
     const int r = e % 128, k = e / 128;
     const int64_t i = i0 + r;
     const float v = (k < pw && i < f) ? G[i + (k0 + k) * f] : 0.f;
-    *reinterpret_cast<uint16_t*>(sA + tc_off(r, k)) = to_bf16(v);
+    split_bf16(v, reinterpret_cast<uint16_t*>(sA + tc_off(r, k)), reinterpret_cast<uint16_t*>(sAl + tc_off(r, k)));
   }
   if (!etile) {
     for (int e = tid; e < 64 * NB; e += blockDim.x) {
       const int r = e % 64, k = e / 64;
       const int64_t j = j0 + r;
       const float v = (k < pw && j < f) ? G[j + (k0 + k) * f] * Dk[k] : 0.f;
-      *reinterpret_cast<uint16_t*>(sB + tc_off(r, k)) = to_bf16(v);
+      split_bf16(v, reinterpret_cast<uint16_t*>(sB + tc_off(r, k)), reinterpret_cast<uint16_t*>(sBl + tc_off(r, k)));
     }
   } else {
     for (int e = tid; e < 64 * NB; e += blockDim.x) {
       const int k = e % 64, r = e / 64;  // consecutive k: consecutive rows of E
       const float v = (k < pw && r < ncols) ? Eb[(k0 + k) + (j0 + r) * f] : 0.f;
-      *reinterpret_cast<uint16_t*>(sB + tc_off(r, k)) = to_bf16(v);
+      split_bf16(v, reinterpret_cast<uint16_t*>(sB + tc_off(r, k)), reinterpret_cast<uint16_t*>(sBl + tc_off(r, k)));
     }
   }
   if (tid == 0) {
@@ -474,15 +399,18 @@ __global__ void __launch_bounds__(128) k_bf_update_tc(BigFrontDev bf, WorkList w
   if (tid == 0) {
     // D F32 (bit 4), A and B BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at 17, M >> 4 at 24
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    for (int ks = 0; ks < NB / 16; ++ks) {
-      const uint64_t ad = tc_desc(smem_addr(sA) + ks * 2 * kTcLBO);
-      const uint64_t bd = tc_desc(smem_addr(sB) + ks * 2 * kTcLBO);
-      const uint32_t acc = ks > 0 ? 1u : 0u;
-      asm volatile(
-          "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-          " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-    }
+    const uint8_t* As[3] = {sA, sA, sAl};
+    const uint8_t* Bs[3] = {sB, sBl, sB};
+    for (int ks = 0; ks < NB / 16; ++ks)
+      for (int t = 0; t < 3; ++t) {  // hi*hi, hi*lo, lo*hi
+        const uint64_t ad = tc_desc(smem_addr(As[t]) + ks * 2 * kTcLBO);
+        const uint64_t bd = tc_desc(smem_addr(Bs[t]) + ks * 2 * kTcLBO);
+        const uint32_t acc = (ks > 0 || t > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
         smem_addr(&mbar)));
   }
@@ -599,9 +527,11 @@ __global__ void k_bf_bwd(BigFrontDev bf, WorkList wl, const T* __restrict__ E, c
 
 template <typename T>
 int BigFrontOps<T>::setup_attributes() {
-  CLR_CUDA(cudaFuncSetAttribute(k_bf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * NB * LD * sizeof(T)));
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kDiagSmem * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LD * sizeof(T)));
   CLR_CUDA(cudaFuncSetAttribute(k_bf_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NB * LDK * sizeof(T)));
+  if (std::is_same<T, float>::value)
+    CLR_CUDA(cudaFuncSetAttribute(k_bf_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   return CLR_OK;
 }
 
@@ -609,17 +539,18 @@ template <typename T>
 int BigFrontOps<T>::factor_level(cudaStream_t st, const BigFrontDev& bf, const BigLevelPlan& plan, T* F, T* E, T* Dp,
                                  T* Linv, const int8_t* dsign, double eps, double delta, int* hits, const int* skip,
                                  bool tc16, int* err) {
-  const size_t s2 = 2 * NB * LD * sizeof(T), s3 = 3 * NB * LD * sizeof(T), su = 2 * NB * LDK * sizeof(T);
+  const size_t s2 = 2 * NB * LD * sizeof(T), su = 2 * NB * LDK * sizeof(T);
   for (size_t p = 0; p < plan.A.size(); ++p) {
     if (plan.A[p].nblocks > 0)
-      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, s3, st>>>(bf, plan.A[p], (int)p, F, Dp, Linv, dsign, eps, delta,
-                                                                  hits, skip);
+      k_bf_diag<T><<<(unsigned)plan.A[p].nblocks, 256, kDiagSmem * sizeof(T), st>>>(bf, plan.A[p], (int)p, F, Dp, Linv,
+                                                                                  dsign, eps, delta, hits, skip);
     if (plan.B[p].nblocks > 0)
       k_bf_trsm<T><<<(unsigned)plan.B[p].nblocks, 256, s2, st>>>(bf, plan.B[p], (int)p, F, E, Dp, Linv, skip);
     if constexpr (std::is_same<T, float>::value) {
       if (tc16) {
         if (plan.Ctc[p].nblocks > 0)
-          k_bf_update_tc<<<(unsigned)plan.Ctc[p].nblocks, 128, 0, st>>>(bf, plan.Ctc[p], (int)p, F, E, Dp, err, skip);
+          k_bf_update_tc<<<(unsigned)plan.Ctc[p].nblocks, 128, kTcSmem, st>>>(bf, plan.Ctc[p], (int)p, F, E, Dp, err,
+                                                                          skip);
         continue;
       }
     }

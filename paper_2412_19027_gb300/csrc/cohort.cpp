@@ -75,7 +75,7 @@ ProbConst prob_const(const HostProblem& p) {
 }  // namespace
 
 int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<int64_t>>& orders, HostProblem& hp,
-                 CohortLayout& lay, Symbolic& sy, std::string& err, int verbose) {
+                 CohortLayout& lay, Symbolic& sy, std::string& err, int verbose, int relax) {
   const int64_t B = (int64_t)probs.size();
   if (B == 0) {
     err = "a cohort needs at least one problem";
@@ -149,7 +149,7 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
       use = &own;
     }
     const auto t1 = std::chrono::steady_clock::now();
-    int rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, use, sy);
+    int rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, use, sy, relax);
     if (verbose)
       std::fprintf(stderr, "[clr] setup: symbolic %.3f s\n",
                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t1).count());
@@ -327,7 +327,7 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     }
   }
   for (HostProblem& pr : probs) release_big(pr);
-  int rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, &order, sy);
+  int rc = symbolic_analyze(N, hp.kcol_ptr, hp.krow, &order, sy, relax);
   if (rc != CLR_OK) {
     err = "symbolic analysis failed";
     return rc;

@@ -250,82 +250,122 @@ __global__ void k_scale_nonneg(ConeDev cd, const double* __restrict__ s, const d
       cd.kvz[i] = 0.0;  // zero cone: H = 0
       continue;
     }
+    // lambda = sqrt(s z), w = s / lambda = sqrt(s / z), H = w^2 (one square root and
+    // one division: FP64 division and square root dominate this pass on GB300)
     const double si = s[i], zi = z[i];
-    const double h = si / zi;
+    const double lam = sqrt(si * zi);
+    const double wi = si / lam;
+    const double h = wi * wi;
     cd.kvz[i] = -h;
-    cd.nn_w[i - nz] = sqrt(h);
-    cd.nn_lam[i - nz] = sqrt(si * zi);
+    cd.nn_w[i - nz] = wi;
+    cd.nn_lam[i - nz] = lam;
     if (h > 0) mx.add(sc, &IterScal::hmax_bits, cd.row_pid[i], dbits(h));
   }
   mx.flush(sc, &IterScal::hmax_bits);
 }
 
+// Lanes per SOC: groups of G lanes of a warp (G = 8 when every SOC has at most 8
+// rows, else 32) each take one cone at a time; reductions are G-lane butterflies.
+template <int G>
+__device__ __forceinline__ double gsum(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ double gmax(double v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// The cones of a warp in pass k: (w + k nw) 32/G + g, g the lane group.  Every
+// lane of a warp runs the same passes (shuffles need the whole warp); a group
+// past the last cone works on an empty cone (d = 0) and writes nothing.
+#define SOC_GROUP_LOOP(G)                                                                \
+  constexpr int PG = 32 / (G);                                                           \
+  const int lane = threadIdx.x & ((G) - 1);                                              \
+  const int64_t w_ = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;              \
+  const int64_t nw_ = ((int64_t)gridDim.x * blockDim.x) >> 5;                            \
+  for (int64_t base = w_ * PG; base < cd.n_soc; base += nw_ * PG)
+
+// blocks of 256 threads for the SOC kernels: one pass over the cones when that
+// takes at most 16 blocks per SM, else grid-stride passes
+inline unsigned soc_grid(const ConeDev& cd, int G) {
+  const int64_t warps = (cd.n_soc * G + 31) / 32;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 16 * kSMs));
+}
+
+template <int G>
 __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
                             const int* skip) {
   if (skip && *skip) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t cone = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (cone >= cd.n_soc) return;
-  const int64_t off = cd.soc_off[cone];
-  const int d = cd.soc_dim[cone];
-  const double* sv = s + off;
-  const double* zc = z + off;
-  double s1 = 0, z1 = 0, sz = 0;
-  for (int j = lane; j < d; j += 32) {
-    const double a = sv[j], b = zc[j];
-    if (j > 0) {
-      s1 += a * a;
-      z1 += b * b;
-    }
-    sz += a * b;
-  }
-  s1 = warp_sum(s1);
-  z1 = warp_sum(z1);
-  sz = warp_sum(sz);
-  const double s0 = sv[0], z0 = zc[0];
-  const double ns1 = sqrt(s1), nz1 = sqrt(z1);
-  const double ns = sqrt((s0 - ns1) * (s0 + ns1)), nzj = sqrt((z0 - nz1) * (z0 + nz1));
-  const double sbzb = sz / (ns * nzj);
-  const double gamma = sqrt(0.5 * (1.0 + sbzb));
-  const double eta = sqrt(ns / nzj);
-  const double inv2g = 1.0 / (2.0 * gamma);
-  // w-bar and the products needed for lambda = eta W-bar z
-  double wz = 0, w1z1 = 0;
-  for (int j = lane; j < d; j += 32) {
-    const double wb = (j == 0) ? (s0 / ns + z0 / nzj) * inv2g : (sv[j] / ns - zc[j] / nzj) * inv2g;
-    cd.soc_wb[off + j] = wb;
-    wz += wb * zc[j];
-    if (j > 0) w1z1 += wb * zc[j];
-  }
-  wz = warp_sum(wz);
-  w1z1 = warp_sum(w1z1);
-  __syncwarp();
-  const double wb0 = cd.soc_wb[off];
-  const double coef = z0 + w1z1 / (1.0 + wb0);
-  for (int j = lane; j < d; j += 32) {
-    const double lam = (j == 0) ? eta * wz : eta * (zc[j] + coef * cd.soc_wb[off + j]);
-    cd.soc_lam[off + j] = lam;
-  }
-  if (lane == 0) cd.soc_eta[cone] = eta;
-  // H = eta^2 (2 wb wb' - J), packed lower, column-major; KKT value is -H
-  const double e2 = eta * eta;
-  double* kb = cd.kvz + cd.soc_kb[cone];
-  double mx = 0.0;
-  int64_t base = 0;
-  for (int c = 0; c < d; ++c) {
-    const double wc = cd.soc_wb[off + c];
-    for (int r = c + lane; r < d; r += 32) {
-      double h = 2.0 * e2 * cd.soc_wb[off + r] * wc;
-      if (r == c) {
-        h += (c == 0) ? -e2 : e2;
-        mx = fmax(mx, fabs(h));
+  RunExt<true> run;
+  SOC_GROUP_LOOP(G) {
+    const int64_t cone = base + (threadIdx.x & 31) / G;
+    const bool valid = cone < cd.n_soc;
+    const int64_t off = valid ? cd.soc_off[cone] : 0;
+    const int d = valid ? cd.soc_dim[cone] : 0;
+    const double* sv = s + off;
+    const double* zc = z + off;
+    double s1 = 0, z1 = 0, sz = 0;
+    for (int j = lane; j < d; j += G) {
+      const double a = sv[j], b = zc[j];
+      if (j > 0) {
+        s1 += a * a;
+        z1 += b * b;
       }
-      kb[base + (r - c)] = -h;
+      sz += a * b;
     }
-    base += d - c;
+    s1 = gsum<G>(s1);
+    z1 = gsum<G>(z1);
+    sz = gsum<G>(sz);
+    const double s0 = valid ? sv[0] : 1.0, z0 = valid ? zc[0] : 1.0;
+    const double ns1 = sqrt(s1), nz1 = sqrt(z1);
+    const double ns = sqrt((s0 - ns1) * (s0 + ns1)), nzj = sqrt((z0 - nz1) * (z0 + nz1));
+    const double sbzb = sz / (ns * nzj);
+    const double gamma = sqrt(0.5 * (1.0 + sbzb));
+    const double eta = sqrt(ns / nzj);
+    const double inv2g = 1.0 / (2.0 * gamma);
+    // w-bar and the products needed for lambda = eta W-bar z
+    double wz = 0, w1z1 = 0;
+    for (int j = lane; j < d; j += G) {
+      const double wb = (j == 0) ? (s0 / ns + z0 / nzj) * inv2g : (sv[j] / ns - zc[j] / nzj) * inv2g;
+      cd.soc_wb[off + j] = wb;
+      wz += wb * zc[j];
+      if (j > 0) w1z1 += wb * zc[j];
+    }
+    wz = gsum<G>(wz);
+    w1z1 = gsum<G>(w1z1);
+    __syncwarp();
+    const double wb0 = valid ? cd.soc_wb[off] : 1.0;
+    const double coef = z0 + w1z1 / (1.0 + wb0);
+    for (int j = lane; j < d; j += G) {
+      const double lam = (j == 0) ? eta * wz : eta * (zc[j] + coef * cd.soc_wb[off + j]);
+      cd.soc_lam[off + j] = lam;
+    }
+    if (lane == 0 && valid) cd.soc_eta[cone] = eta;
+    // H = eta^2 (2 wb wb' - J), packed lower, column-major; KKT value is -H
+    const double e2 = eta * eta;
+    double* kb = cd.kvz + (valid ? cd.soc_kb[cone] : 0);
+    double mx = 0.0;
+    int64_t kbase = 0;
+    for (int c = 0; c < d; ++c) {
+      const double wc = cd.soc_wb[off + c];
+      for (int r = c + lane; r < d; r += G) {
+        double h = 2.0 * e2 * cd.soc_wb[off + r] * wc;
+        if (r == c) {
+          h += (c == 0) ? -e2 : e2;
+          mx = fmax(mx, fabs(h));
+        }
+        kb[kbase + (r - c)] = -h;
+      }
+      kbase += d - c;
+    }
+    mx = gmax<G>(mx);
+    if (lane == 0 && valid) run.add(sc, &IterScal::hmax_bits, cd.row_pid[off], dbits(mx));
+    __syncwarp();
   }
-  mx = warp_max(mx);
-  if (lane == 0) atomicMax(&sc[cd.row_pid[off]].hmax_bits, dbits(mx));
+  run.flush(sc, &IterScal::hmax_bits);
 }
 
 __global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
@@ -616,7 +656,10 @@ int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const dou
                   const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0)
     k_scale_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, s, z, sc, skip);
-  if (cd.n_soc > 0) k_scale_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, s, z, sc, skip);
+  if (cd.n_soc > 0) {
+    if (cd.soc_dmax <= 8) k_scale_soc<8><<<soc_grid(cd, 8), 256, 0, st>>>(cd, s, z, sc, skip);
+    else k_scale_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, z, sc, skip);
+  }
   if (cd.n_exp + cd.n_pow > 0)
     k_scale_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, sc, skip);
   if (cd.n_psd > 0) {
@@ -694,19 +737,22 @@ __global__ void k_step_nonneg(ConeDev cd, const double* __restrict__ s, const do
 
 namespace {
 // Largest alpha with x + alpha dx in the closed SOC (smallest positive root of
-// the J-norm quadratic, and t + alpha dt >= 0); warp-cooperative, result in all lanes.
+// the J-norm quadratic, and t + alpha dt >= 0); G-lane cooperative, result in all
+// lanes of the group (d = 0: no limit).
+template <int G>
 __device__ double soc_step(const double* x, const double* dx, int d) {
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & (G - 1);
   double a2 = 0, b2 = 0, c2 = 0;
-  for (int j = lane; j < d; j += 32) {
+  for (int j = lane; j < d; j += G) {
     if (j == 0) continue;
     a2 += dx[j] * dx[j];
     b2 += x[j] * dx[j];
     c2 += x[j] * x[j];
   }
-  a2 = warp_sum(a2);
-  b2 = warp_sum(b2);
-  c2 = warp_sum(c2);
+  a2 = gsum<G>(a2);
+  b2 = gsum<G>(b2);
+  c2 = gsum<G>(c2);
+  if (d == 0) return INFINITY;
   const double A = dx[0] * dx[0] - a2;
   const double B = x[0] * dx[0] - b2;
   const double C = x[0] * x[0] - c2;
@@ -727,16 +773,21 @@ __device__ double soc_step(const double* x, const double* dx, int d) {
 }
 }  // namespace
 
+template <int G>
 __global__ void k_step_soc(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
                            const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
                            const int* skip) {
   if (skip && *skip) return;
-  const int64_t cone = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (cone >= cd.n_soc) return;
-  const int64_t off = cd.soc_off[cone];
-  const int d = cd.soc_dim[cone];
-  const double a = fmin(soc_step(s + off, ds + off, d), soc_step(z + off, dz + off, d));
-  if ((threadIdx.x & 31) == 0 && a < INFINITY) atomicMin(&sc[cd.row_pid[off]].amin_bits, dbits(a));
+  RunExt<false> run;
+  SOC_GROUP_LOOP(G) {
+    const int64_t cone = base + (threadIdx.x & 31) / G;
+    const bool valid = cone < cd.n_soc;
+    const int64_t off = valid ? cd.soc_off[cone] : 0;
+    const int d = valid ? cd.soc_dim[cone] : 0;
+    const double a = fmin(soc_step<G>(s + off, ds + off, d), soc_step<G>(z + off, dz + off, d));
+    if (lane == 0 && valid && a < INFINITY) run.add(sc, &IterScal::amin_bits, cd.row_pid[off], dbits(a));
+  }
+  run.flush(sc, &IterScal::amin_bits);
 }
 
 __global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
@@ -782,6 +833,7 @@ __global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const doubl
     __syncthreads();
     const double lmin = jacobi_eigmin(X, k, csb, &flag);
     if (lmin < 0) amax = fmin(amax, -1.0 / lmin);
+    if (bad || !(lmin == lmin)) amax = 0.0;  // not positive definite in floating point, or NaN: no step
     __syncthreads();
   }
   if (threadIdx.x == 0 && amax < INFINITY) atomicMin(&sc[cd.row_pid[row]].amin_bits, dbits(amax));
@@ -790,8 +842,10 @@ __global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const doubl
 int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, const double* ds, const double* z,
                          const double* dz, IterScal* sc, const int* skip) {
   if (cd.m_nonneg > 0) k_step_nonneg<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
-  if (cd.n_soc > 0)
-    k_step_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+  if (cd.n_soc > 0) {
+    if (cd.soc_dmax <= 8) k_step_soc<8><<<soc_grid(cd, 8), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+    else k_step_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+  }
   if (cd.n_psd > 0) {
     const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));
     k_step_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, s, ds, z, dz, sc, skip);
@@ -954,21 +1008,22 @@ __global__ void k_ds_nonneg(ConeDev cd, const double* __restrict__ dsa, const do
 
 namespace {
 // y = W-bar x (warp), x, y of length d indexed by lane stride; wb in global.
+template <int G>
 __device__ void soc_wbar(const double* wb, const double* x, double* y, int d, bool jconj) {
   // jconj: y = J W-bar J x
-  const int lane = threadIdx.x & 31;
-  double w1x1 = 0, w0 = wb[0];
-  for (int j = lane; j < d; j += 32)
+  const int lane = threadIdx.x & (G - 1);
+  double w1x1 = 0, w0 = d > 0 ? wb[0] : 1.0;
+  for (int j = lane; j < d; j += G)
     if (j > 0) w1x1 += wb[j] * x[j];
-  w1x1 = warp_sum(w1x1);
-  const double x0 = x[0];
+  w1x1 = gsum<G>(w1x1);
+  const double x0 = d > 0 ? x[0] : 0.0;
   __syncwarp();
   if (!jconj) {
     const double coef = x0 + w1x1 / (1.0 + w0);
-    for (int j = lane; j < d; j += 32) y[j] = (j == 0) ? w0 * x0 + w1x1 : x[j] + coef * wb[j];
+    for (int j = lane; j < d; j += G) y[j] = (j == 0) ? w0 * x0 + w1x1 : x[j] + coef * wb[j];
   } else {
     const double coef = x0 - w1x1 / (1.0 + w0);
-    for (int j = lane; j < d; j += 32) y[j] = (j == 0) ? w0 * x0 - w1x1 : x[j] - coef * wb[j];
+    for (int j = lane; j < d; j += G) y[j] = (j == 0) ? w0 * x0 - w1x1 : x[j] - coef * wb[j];
   }
   __syncwarp();
 }
@@ -976,59 +1031,62 @@ __device__ void soc_wbar(const double* wb, const double* x, double* y, int d, bo
 
 // SOC: d_s = W (lambda \ (lambda o lambda + (W^{-1} ds_a) o (W dz_a) - sigma mu e)); W symmetric.
 // Uses `out` on the cone's rows as scratch.
+template <int G>
 __global__ void k_ds_soc(ConeDev cd, const double* __restrict__ dsa, const double* __restrict__ dza,
                          const IterScal* sc, double* __restrict__ out, double* __restrict__ scratch,
                          const int* skip) {
   if (skip && *skip) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t cone = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (cone >= cd.n_soc) return;
-  const int64_t off = cd.soc_off[cone];
-  const int d = cd.soc_dim[cone];
-  const double eta = cd.soc_eta[cone];
-  const double* wb = cd.soc_wb + off;
-  const double* lam = cd.soc_lam + off;
-  double* u = scratch + off;       // W^{-1} ds_a
-  double* v = out + off;           // W dz_a, then the Jordan quotient
-  soc_wbar(wb, dsa + off, u, d, true);
-  soc_wbar(wb, dza + off, v, d, false);
-  for (int j = lane; j < d; j += 32) {
-    u[j] /= eta;
-    v[j] *= eta;
-  }
-  __syncwarp();
-  // eta_c = u o v = (u'v, u0 v1 + v0 u1);  lambda o lambda = (|lam|^2, 2 lam0 lam1)
-  double uv = 0, ll = 0, l1v = 0, l1sq = 0;
-  for (int j = lane; j < d; j += 32) {
-    uv += u[j] * v[j];
-    ll += lam[j] * lam[j];
-  }
-  uv = warp_sum(uv);
-  ll = warp_sum(ll);
-  const double u0 = u[0], v0 = v[0], l0 = lam[0];
-  const double smu = sc[cd.row_pid[off]].sigma_mu;
-  __syncwarp();
-  // w = lam o lam + eta_c - sigma mu e
-  for (int j = lane; j < d; j += 32) {
-    const double wj = (j == 0) ? ll + uv - smu : 2.0 * l0 * lam[j] + u0 * v[j] + v0 * u[j];
-    u[j] = wj;  // reuse u for w
-  }
-  __syncwarp();
-  for (int j = lane; j < d; j += 32)
-    if (j > 0) {
-      l1v += lam[j] * u[j];
-      l1sq += lam[j] * lam[j];
+  SOC_GROUP_LOOP(G) {
+    const int64_t cone = base + (threadIdx.x & 31) / G;
+    const bool valid = cone < cd.n_soc;
+    const int64_t off = valid ? cd.soc_off[cone] : 0;
+    const int d = valid ? cd.soc_dim[cone] : 0;
+    const double eta = valid ? cd.soc_eta[cone] : 1.0;
+    const double* wb = cd.soc_wb + off;
+    const double* lam = cd.soc_lam + off;
+    double* u = scratch + off;  // W^{-1} ds_a
+    double* v = out + off;      // W dz_a, then the Jordan quotient
+    soc_wbar<G>(wb, dsa + off, u, d, true);
+    soc_wbar<G>(wb, dza + off, v, d, false);
+    for (int j = lane; j < d; j += G) {
+      u[j] /= eta;
+      v[j] *= eta;
     }
-  l1v = warp_sum(l1v);
-  l1sq = warp_sum(l1sq);
-  const double w0 = u[0];
-  const double x0 = (l0 * w0 - l1v) / (l0 * l0 - l1sq);
-  __syncwarp();
-  for (int j = lane; j < d; j += 32) v[j] = (j == 0) ? x0 : (u[j] - x0 * lam[j]) / l0;
-  __syncwarp();
-  // out = W x = eta W-bar x (write through u as scratch)
-  soc_wbar(wb, v, u, d, false);
-  for (int j = lane; j < d; j += 32) out[off + j] = eta * u[j];
+    __syncwarp();
+    // eta_c = u o v = (u'v, u0 v1 + v0 u1);  lambda o lambda = (|lam|^2, 2 lam0 lam1)
+    double uv = 0, ll = 0, l1v = 0, l1sq = 0;
+    for (int j = lane; j < d; j += G) {
+      uv += u[j] * v[j];
+      ll += lam[j] * lam[j];
+    }
+    uv = gsum<G>(uv);
+    ll = gsum<G>(ll);
+    const double u0 = valid ? u[0] : 0.0, v0 = valid ? v[0] : 0.0, l0 = valid ? lam[0] : 1.0;
+    const double smu = valid ? sc[cd.row_pid[off]].sigma_mu : 0.0;
+    __syncwarp();
+    // w = lam o lam + eta_c - sigma mu e
+    for (int j = lane; j < d; j += G) {
+      const double wj = (j == 0) ? ll + uv - smu : 2.0 * l0 * lam[j] + u0 * v[j] + v0 * u[j];
+      u[j] = wj;  // reuse u for w
+    }
+    __syncwarp();
+    for (int j = lane; j < d; j += G)
+      if (j > 0) {
+        l1v += lam[j] * u[j];
+        l1sq += lam[j] * lam[j];
+      }
+    l1v = gsum<G>(l1v);
+    l1sq = gsum<G>(l1sq);
+    const double w0 = valid ? u[0] : 0.0;
+    const double x0 = (l0 * w0 - l1v) / (l0 * l0 - l1sq);
+    __syncwarp();
+    for (int j = lane; j < d; j += G) v[j] = (j == 0) ? x0 : (u[j] - x0 * lam[j]) / l0;
+    __syncwarp();
+    // out = W x = eta W-bar x (write through u as scratch)
+    soc_wbar<G>(wb, v, u, d, false);
+    for (int j = lane; j < d; j += G) out[off + j] = eta * u[j];
+    __syncwarp();
+  }
 }
 
 __global__ void k_ds_exppow(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z,
@@ -1149,8 +1207,10 @@ int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const
                       const double* dza, IterScal* sc, double* ds_out, const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0)
     k_ds_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
-  if (cd.n_soc > 0)
-    k_ds_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
+  if (cd.n_soc > 0) {
+    if (cd.soc_dmax <= 8) k_ds_soc<8><<<soc_grid(cd, 8), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
+    else k_ds_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
+  }
   if (cd.n_exp + cd.n_pow > 0)
     k_ds_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, dsa, dza, sc, ds_out,
                                                                                skip);

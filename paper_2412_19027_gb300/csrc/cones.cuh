@@ -18,6 +18,7 @@ struct ConeDev {
   const int64_t* soc_off = nullptr;
   const int32_t* soc_dim = nullptr;
   const int64_t* soc_kb = nullptr;
+  int soc_dmax = 0;  // largest SOC dimension (picks 8 or 32 lanes per cone)
   // exp / pow cones: rows row0 + 3 i, packed H at kb0 + 6 i
   int64_t n_exp = 0, exp_row0 = 0, exp_kb0 = 0;
   int64_t n_pow = 0, pow_row0 = 0, pow_kb0 = 0;

@@ -118,7 +118,7 @@ struct CohortLayout {
 // fill-reducing order `orders[p]`, or none) into one cohort problem `hp` and
 // its symbolic factorization.  The big per-problem arrays are released.
 int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<int64_t>>& orders, HostProblem& hp,
-                 CohortLayout& lay, Symbolic& sy, std::string& err, int verbose = 0);
+                 CohortLayout& lay, Symbolic& sy, std::string& err, int verbose = 0, int relax = 1);
 
 // ---- host routines (setup.cpp / amd.cpp / symbolic.cpp) ----
 int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_csc* A, const double* b,
@@ -126,9 +126,10 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
 int set_qb(HostProblem& hp, const double* q, const double* b);
 void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx,
                std::vector<int64_t>& perm, int64_t& n_dense);
-// relax: merge supernodes with few explicit zeros (relaxed amalgamation).
+// relax: merge supernodes with few explicit zeros (relaxed amalgamation):
+// 0 off, 1 column thresholds 4 / 16 / 48, 2 thresholds 8 / 32 / 96.
 int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
-                     const std::vector<int64_t>* user_order, Symbolic& sy, bool relax = true);
+                     const std::vector<int64_t>* user_order, Symbolic& sy, int relax = 1);
 // The fill-reducing order symbolic_analyze uses when given none (AMD on the KKT pattern).
 void kkt_amd_order(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
                    std::vector<int64_t>& order, int64_t& n_dense);

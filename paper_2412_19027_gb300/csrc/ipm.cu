@@ -79,17 +79,33 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
 #pragma unroll
     for (int u = 0; u < NU; ++u) a[u] = b[u] = 0.0;
     const int64_t p0 = kptr[i], p1 = kptr[i + 1];
-    for (int64_t base = p0; base < p1; base += 32) {
+    // four 32-entry steps per pass: all loads of the pass issued before the adds,
+    // which keep the order of the plain one-step loop (partial t sums entries
+    // p = p0 + t (mod 32) in increasing p)
+    for (int64_t base = p0; base < p1; base += 128) {
+      double tv[4][NU];
+      bool tx[4][NU];
 #pragma unroll
-      for (int u = 0; u < NU; ++u) {
-        const int64_t p = base + lane + G * u;
-        if (p < p1) {
-          const int32_t c = kcol[p];
-          const double t = kval[kvi[p]] * v[c];
-          if (c < n) a[u] += t;
-          else b[u] += t;
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const int64_t p = base + 32 * k + lane + G * u;
+          tv[k][u] = 0.0;
+          tx[k][u] = true;
+          if (p < p1) {
+            const int32_t c = kcol[p];
+            tv[k][u] = kval[kvi[p]] * v[c];
+            tx[k][u] = c < n;
+          }
         }
-      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          if (base + 32 * k + lane + G * u >= p1) continue;
+          if (tx[k][u]) a[u] += tv[k][u];
+          else b[u] += tv[k][u];
+        }
     }
 #pragma unroll
     for (int off = 16; off >= G; off >>= 1)
@@ -569,9 +585,16 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
-      if (sp.escalate_on && q.ir_fail) {
-        q.escalate = 1;
+      if (q.ir_fail) {
         q.alpha_c = 0.0;
+        if (sp.escalate_on) {
+          q.escalate = 1;  // redo the iteration with the FP64 factor
+        } else {
+          // a KKT solve of this iteration stayed above the acceptance bar (or gave a
+          // NaN) even in FP64: stop at the current, finite iterate
+          q.status = CLR_NUMERICAL_ERROR;
+          halt_problem(q, bf);
+        }
         continue;
       }
       q.alpha_c = a;
@@ -822,7 +845,7 @@ int Solver::analyze_cohort(std::vector<HostProblem>&& ps, const std::vector<std:
   st = s;
   const double t0 = now_s();
   probs = std::move(ps);
-  int rc = build_cohort(probs, orders, hp, lay, sy, err, st.verbose);
+  int rc = build_cohort(probs, orders, hp, lay, sy, err, st.verbose, st.amalgamation);
   if (rc != CLR_OK) return rc;
   const double t1 = now_s();
   build_numeric_maps(sy, hp.kcol_ptr, hp.krow, mp);
@@ -853,7 +876,8 @@ int Solver::upload() {
     dsign[k] = sy.perm[k] < n ? 1 : -1;
     pos_pid[k] = lay.pid[sy.perm[k]];
   }
-  int rc = ldl_structure_upload(ar_, sy, mp, dsign, st.factor_bits == 64 ? 96 : 128, ls_, &pos_pid);
+  const int small_max = st.small_front_max > 0 ? st.small_front_max : (st.factor_bits == 64 ? 96 : 128);
+  int rc = ldl_structure_upload(ar_, sy, mp, dsign, small_max, ls_, &pos_pid);
   if (rc != CLR_OK) return rc;
   f32_.tc16 = st.factor_bits == 16;
   f32_.flow = f64_.flow = st.big_front_schedule == 1;
@@ -964,6 +988,7 @@ int Solver::upload() {
     for (int64_t c = cl.soc_begin; c < cl.soc_end; ++c) {
       off.push_back(cl.cones[c].off);
       dim.push_back((int32_t)cl.cones[c].dim);
+      cd_.soc_dmax = std::max<int>(cd_.soc_dmax, (int)cl.cones[c].dim);
       kb.push_back(cl.cones[c].kbase);
     }
     cd_.soc_off = ar_.upload(off.data(), (int64_t)off.size());

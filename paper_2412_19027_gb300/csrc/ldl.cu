@@ -14,6 +14,8 @@
 // below-diagonal rows), backward sweep root -> leaves (D^{-1}, then L^T with
 // the ancestors' solution gathered by KKT index).
 #include <algorithm>
+#include <queue>
+#include <unordered_map>
 
 #include "ldl.cuh"
 
@@ -233,6 +235,78 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
   return ar.upload(v.data(), (int64_t)v.size());
 }
 }  // namespace
+
+// Reorder the tasks [t0, end) of one level (generated in a topological order of
+// the graph whose edges are the waits of k_bf_flow) into the order of list
+// scheduling by longest path to the end: Kahn's algorithm taking, among the
+// tasks whose predecessors are all placed, the one with the largest bottom
+// level (the diagonal tasks weigh 4, the others 1).  The counter hands tasks out
+// in this order, so the chain D(p) -> T(p, p+1) -> U(p, p+1, p+1) -> D(p+1) is
+// taken early and the bulk of the updates fills the CTAs around it.
+static void flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0) {
+  const int64_t n = (int64_t)tasks.size() - t0;
+  if (n <= 1) return;
+  auto key = [](int64_t b, int kind, int64_t p, int64_t i, int64_t j) -> uint64_t {
+    return ((uint64_t)b << 43) ^ ((uint64_t)kind << 40) ^ ((uint64_t)p << 28) ^ ((uint64_t)i << 14) ^ (uint64_t)j;
+  };
+  std::unordered_map<uint64_t, int64_t> idx;
+  idx.reserve((size_t)n * 2);
+  for (int64_t t = 0; t < n; ++t) {
+    const FlowTask& k = tasks[t0 + t];
+    idx[key(k.bf, k.kind, k.p, k.i, k.j)] = t;
+  }
+  auto find = [&](int64_t b, int kind, int64_t p, int64_t i, int64_t j) -> int64_t {
+    auto it = idx.find(key(b, kind, p, i, j));
+    return it == idx.end() ? -1 : it->second;
+  };
+  std::vector<std::vector<int64_t>> succ(n);
+  std::vector<int> indeg(n, 0);
+  for (int64_t t = 0; t < n; ++t) {
+    const FlowTask& k = tasks[t0 + t];
+    int64_t d[3] = {-1, -1, -1};
+    const int64_t p = k.p, i = k.i, j = k.j, b = k.bf;
+    switch (k.kind) {
+      case 0: d[0] = p > 0 ? find(b, 3, p - 1, p, p) : -1; break;
+      case 1: d[0] = find(b, 0, p, p, p); d[1] = p > 0 ? find(b, 3, p - 1, i, p) : -1; break;
+      case 2: d[0] = find(b, 0, p, p, p); d[1] = p - 1 >= j ? find(b, 4, p - 1, p, j) : -1; break;
+      case 3:
+        d[0] = find(b, 1, p, i, p);
+        d[1] = find(b, 1, p, j, p);
+        d[2] = p > 0 ? find(b, 3, p - 1, i, j) : -1;
+        break;
+      default:
+        d[0] = find(b, 1, p, i, p);
+        d[1] = j < p ? find(b, 2, p, p, j) : find(b, 0, p, p, p);
+        d[2] = p - 1 >= j ? find(b, 4, p - 1, i, j) : -1;
+        break;
+    }
+    for (int q = 0; q < 3; ++q)
+      if (d[q] >= 0 && (q == 0 || d[q] != d[q - 1])) {
+        succ[d[q]].push_back(t);
+        ++indeg[t];
+      }
+  }
+  // bottom levels: the generated order is topological, so go backwards
+  std::vector<int64_t> bl(n, 0);
+  for (int64_t t = n - 1; t >= 0; --t) {
+    int64_t m = 0;
+    for (int64_t u : succ[t]) m = std::max(m, bl[u]);
+    bl[t] = m + (tasks[t0 + t].kind == 0 ? 4 : 1);
+  }
+  std::priority_queue<std::pair<int64_t, int64_t>> ready;  // (bottom level, -index)
+  for (int64_t t = 0; t < n; ++t)
+    if (indeg[t] == 0) ready.emplace(bl[t], -t);
+  std::vector<FlowTask> out;
+  out.reserve((size_t)n);
+  while (!ready.empty()) {
+    const int64_t t = -ready.top().second;
+    ready.pop();
+    out.push_back(tasks[t0 + t]);
+    for (int64_t u : succ[t])
+      if (--indeg[u] == 0) ready.emplace(bl[u], -u);
+  }
+  if ((int64_t)out.size() == n) std::copy(out.begin(), out.end(), tasks.begin() + t0);
+}
 
 int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps& mp, const std::vector<int8_t>& dsign,
                          int small_max, LdlStructure& st, const std::vector<int32_t>* pos_pid) {
@@ -455,6 +529,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
         }
       }
       st.flow_nt[l] = (int64_t)tasks.size() - st.flow_t0[l];
+      flow_priority_order(tasks, st.flow_t0[l]);
     }
     st.flow_words = words;
     if (!tasks.empty()) {

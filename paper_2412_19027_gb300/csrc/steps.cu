@@ -75,6 +75,7 @@ struct ConeBench {
         if (f == CLR_SOC) {
           soc_off.push_back((int64_t)perm.size());
           soc_dim.push_back((int32_t)d);
+          cd.soc_dmax = std::max<int>(cd.soc_dmax, (int)d);
           soc_kb.push_back(kz);
         }
         if (f == CLR_POW) alpha.push_back(cones[i].alpha);

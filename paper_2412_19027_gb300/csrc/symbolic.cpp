@@ -248,7 +248,7 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
 }
 
 int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::vector<int64_t>& rowidx,
-                     const std::vector<int64_t>* user_order, Symbolic& sy, bool relax_) {
+                     const std::vector<int64_t>* user_order, Symbolic& sy, int relax_) {
   sy = Symbolic();
   sy.N = N;
   // ---- symmetric adjacency for the ordering ----
@@ -385,7 +385,8 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
   // A child supernode is merged into its parent when the explicit zeros this
   // adds stay small relative to the merged panel -- the relaxed-supernode rule
   // of Ashcraft and Grimes with the usual thresholds (always up to 4 columns,
-  // 80% zeros up to 16, 10% up to 48, 5% beyond).  Any child may merge, not
+  // 80% zeros up to 16, 10% up to 48, 5% beyond; level 2 doubles the column
+  // thresholds to 8 / 32 / 96).  Any child may merge, not
   // only the one whose columns end right before the parent's: its columns are
   // moved to just before the parent's (a topological reordering of the
   // elimination tree, so the fill is unchanged), children with the largest
@@ -393,7 +394,8 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
   // parent's rows, so the merged front holds the child's columns followed by
   // the parent's rows.  Fewer, wider fronts: no large extend-adds of thin
   // supernodes, less front memory, fewer levels, more dense work per launch.
-  if (relax_) {
+  if (relax_ > 0) {
+    const int64_t c1 = relax_ >= 2 ? 8 : 4, c2 = 4 * c1, c3 = 12 * c1;
     const int64_t nf = (int64_t)sn_rows.size();
     std::vector<int64_t> fpar(nf, -1);
     for (int64_t J = 0; J < nf; ++J) {
@@ -425,7 +427,7 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
         const int64_t z = gz[J] + gz[P] + gc[J] * (gf[P] - rJ);
         const double tot = (double)c * (double)f - 0.5 * (double)c * (double)(c - 1);
         const double zr = (double)z / tot;
-        const bool merge = c <= 4 || (c <= 16 && zr < 0.8) || (c <= 48 && zr < 0.1) || zr < 0.05;
+        const bool merge = c <= c1 || (c <= c2 && zr < 0.8) || (c <= c3 && zr < 0.1) || zr < 0.05;
         if (!merge) {
           gkids[P].push_back(J);  // stays a child of P's group
           continue;

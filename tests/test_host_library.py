@@ -242,3 +242,25 @@ def test_cone_rows_first_order_for_sparse_random_A(clr):
     assert st["ordering"] == 1
     assert st["max_front"] <= p.n  # the x block, not the constraint block
     assert st["factor_flops"] < 2 * p.n ** 3 / 3.0 * 1.5
+
+
+def test_blocking_settings_validated_and_applied(clr):
+    """small_front_max and amalgamation: range checks, and the amalgamation level
+    changes only the supernode partition (same fill, fewer and wider fronts)."""
+    p = W.mixed_cone(3, n=300, n_zero=40, n_nonneg=300, n_soc=40, n_exp=10, n_pow=10, nnz_per_col=5)
+    for bad in ({"small_front_max": 300}, {"small_front_max": -1}, {"amalgamation": 3},
+                {"big_front_schedule": 2}):
+        with pytest.raises(clr.ClrError):
+            clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, **bad))
+    with pytest.raises(clr.ClrError):  # the FP64 small-front kernel holds at most 160 x 160 in shared memory
+        clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, small_front_max=200))
+    clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(32, small_front_max=200)).free()
+    stats = []
+    for level in (0, 1, 2):
+        s = clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, amalgamation=level))
+        stats.append(s.symbolic_stats())
+        s.free()
+    assert len({st["l_nnz_exact"] for st in stats}) == 1
+    assert stats[0]["l_nnz"] == stats[0]["l_nnz_exact"]  # no amalgamation: no explicit zeros
+    assert stats[0]["n_supernodes"] >= stats[1]["n_supernodes"] >= stats[2]["n_supernodes"]
+    assert stats[2]["l_nnz"] >= stats[1]["l_nnz"] >= stats[0]["l_nnz"]
