@@ -78,9 +78,10 @@ def cone_bytes(family, k):
             "ds": 8 * (4 * d + 2 * kk * kk + kk)}
 
 
-def run_cone_roofline(clr, W, peaks, reps=10):
+def run_cone_roofline(clr, W, peaks, reps=10, shift=0):
     out = {}
     for fam, count, d in CONE_STRESS:
+        count >>= shift
         cones, s, z, ds, dz = W.cone_stress(7, fam, count)
         t = clr.clr_cones_time(cones, s, z, ds, dz, 1.0, reps)
         del s, z, ds, dz
@@ -115,6 +116,11 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cone-roofline", action="store_true",
                     help="skip the cone kernels at stress shapes (2^26 nonneg rows, 2^22 SOC5, 2^16 PSD10)")
+    ap.add_argument("--configs", action="store_true",
+                    help="solve each synthetic configuration once (absolute times, statuses, errors) and exit")
+    ap.add_argument("--cone-only", action="store_true",
+                    help="run only the cone kernels at the stress shapes and print their JSON (for profiling)")
+    ap.add_argument("--cone-shift", type=int, default=0, help="divide the stress shapes by 2^shift")
     ap.add_argument("--serve-requests", type=int, default=10_000)
     ap.add_argument("--serve-bits", type=int, default=64, choices=[32, 64])
     return ap.parse_args()
@@ -307,6 +313,63 @@ def run_serving(args, clr, W):
             "speedup_solves_per_s": sat["solves_per_s"] / rate1, "generation_s": t_gen}
 
 
+def run_configs(args, clr, W):
+    """One timed solve of each configuration (setup reported apart), FP64 and the
+    low-precision factors where the configuration asks for them."""
+    import torch
+
+    def one(prob, bits, **kw):
+        st = clr.clr_default_settings(bits, **kw)
+        t0 = time.perf_counter()
+        s_ = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+        t1 = time.perf_counter()
+        s_.solve()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        x, _, _, info = s_.solution()
+        pf = s_.perf()
+        sym = s_.symbolic_stats()
+        s_.free()
+        rec = {"factor_bits": bits, "status": info["status_name"], "iterations": info["iterations"],
+               "setup_s": t1 - t0, "solve_ms": 1e3 * (t2 - t1),
+               "device_ms": pf["init_ms"] + pf["resid_cones_ms"] + pf["factor_ms"] + pf["solve_step_ms"],
+               "factor_ms_per_factorization": pf["factor_ms"] / max(1, pf["factorizations"]),
+               "ir_steps_total": info["ir_steps_total"], "fp64_from_iter": info["fp64_from_iter"],
+               "res_primal": info["res_primal"], "res_dual": info["res_dual"], "gap_rel": info["gap_rel"],
+               "kkt_dim": sym["kkt_dim"], "l_nnz": sym["l_nnz"], "factor_flops": sym["factor_flops"],
+               "max_front": sym["max_front"]}
+        if getattr(prob, "x_star", None) is not None:
+            f_star = prob.objective(prob.x_star)
+            rec["objective_rel_err_vs_planted"] = abs(prob.objective(x) - f_star) / max(1.0, abs(f_star))
+        return rec
+
+    out = {}
+    p0 = W.nonneg_qp(args.seed)
+    out["qp_nonneg_n50_m100"] = [one(p0, 64)]
+    # throughput: a cohort of 4096 seeds of the same shape in one solver
+    probs = [W.nonneg_qp(args.seed + k) for k in range(4096)]
+    st = clr.clr_default_settings(64)
+    t0 = time.perf_counter()
+    bt = clr.clr_batch_setup([(p.P, p.q, p.A, p.b, p.cones) for p in probs], st)
+    t1 = time.perf_counter()
+    bt.solve()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    stats = {}
+    for k in range(len(probs)):
+        nm = bt.info_of(k)["status_name"]
+        stats[nm] = stats.get(nm, 0) + 1
+    bt.free()
+    out["qp_nonneg_n50_m100_cohort4096"] = {"setup_s": t1 - t0, "solve_ms": 1e3 * (t2 - t1),
+                                            "solves_per_s": len(probs) / (t2 - t1), "statuses": stats}
+    out["mixed_n2000_m6600"] = [one(W.mixed_cone(args.seed), b, ir_stop_ratio=5.0) for b in (64, 32, 16)]
+    pc2 = W.banded_lp(args.seed)
+    out["banded_n200000_m400000"] = [one(pc2, b, ir_stop_ratio=5.0) for b in (64, 32, 16)]
+    pc3 = W.psd_batch(args.seed)
+    out["psd2000x10_n20000"] = [one(pc3, b, ir_stop_ratio=5.0) for b in (32, 64)]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -356,6 +419,15 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     from paper_2412_19027_gb300 import clr, workloads as W
+    if args.configs:
+        if rank == 0:
+            print(json.dumps({"configs": run_configs(args, clr, W)}), flush=True)
+        return
+    if args.cone_only:
+        if rank == 0:
+            print(json.dumps({"cone_roofline": run_cone_roofline(clr, W, measured_peaks(), 3, args.cone_shift)}),
+                  flush=True)
+        return
     prob = W.mixed_cone(args.seed + rank)
     n, m = prob.n, prob.m
     stream = torch.cuda.Stream()

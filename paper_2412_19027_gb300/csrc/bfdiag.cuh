@@ -7,7 +7,7 @@
 //      -- dynamic regularisation of a pivot of the wrong sign or too small;
 //      l_rk = a_rk / d; a_rc -= l_rk a_ck) and, with the same row operations on
 //      the identity, the inverse of its unit lower factor;
-//   2. the rows below: L_RQ = A_RQ L_QQ^{-T} D_Q^{-1};
+//   2. the rows below, by substitution along each row: L_RQ D_Q L_QQ^T = A_RQ;
 //   3. the trailing block: A_RR' -= L_RQ D_Q L_R'Q^T;
 // then the off-diagonal blocks of L^{-1} by block rows:
 //   Linv_QP = -Linv_QQ sum_{P <= M < Q} L_QM Linv_MP.
@@ -83,18 +83,15 @@ __device__ __forceinline__ void diag_sub16(T* A, T* V, int c0, int w, DiagScratc
 // Li (leading dimension ldi); with zero_rest, also zeros in the rest of the
 // 64 x 64 Li block.  smem: kDiagSmem elements.  Returns the number of
 // regularised pivots (in thread 0).
+// The factorization proper: A (64 x 65 in shared memory) holds the lower triangle
+// of the block, zeros elsewhere; V (64 x 65) is work space.  Outputs as for
+// bf_diag_block.
 template <typename T>
-__device__ int bf_diag_block(T* G, int64_t f, int pw, T* D, T* Li, int64_t ldi, bool zero_rest, const int8_t* dsign,
-                             T eps, T delta, T* smem, DiagScratch<T>& sh) {
+__device__ int bf_diag_factor(T* A, T* V, T* G, int64_t f, int pw, T* D, T* Li, int64_t ldi, bool zero_rest,
+                              const int8_t* dsign, T eps, T delta, DiagScratch<T>& sh) {
   constexpr int LDD = kDiagLD;
-  T* A = smem;             // the block as it is eliminated; L and the pivots at the end
-  T* V = smem + 64 * LDD;  // L^{-1}
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nth = blockDim.x;
-  for (int idx = tid; idx < 64 * 64; idx += nth) {
-    const int i = idx % 64, j = idx / 64;
-    A[i * LDD + j] = (i < pw && j < pw && i >= j) ? __ldcg(G + i + (int64_t)j * f) : (T)0;
-    V[i * LDD + j] = (T)0;
-  }
+  const int tid = threadIdx.x, wid = tid >> 5, nth = blockDim.x;
+  for (int idx = tid; idx < 64 * 64; idx += nth) V[(idx % 64) * LDD + idx / 64] = (T)0;
   if (tid < 64) sh.sgn[tid] = tid < pw ? dsign[tid] : (int8_t)1;
   __syncthreads();
   int nhit = 0;
@@ -104,30 +101,18 @@ __device__ int bf_diag_block(T* G, int64_t f, int pw, T* D, T* Li, int64_t ldi, 
     __syncthreads();
     const int r0 = c0 + w, nr = pw - r0;
     if (nr > 0) {
-      // rows below: l_rc = (sum_{m <= c} a_rm Linv_cm) / d_c
-      T out[3];
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int idx = tid + nth * t;
-        out[t] = (T)0;
-        if (idx < nr * 16) {
-          const int rr = r0 + idx / 16, c = idx % 16;
+      // rows below, by substitution along each row (one thread per row, as the
+      // elimination computes them): l_rc = (a_rc - sum_{m<c} l_rm d_m l_cm) / d_c
+      for (int rr = r0 + tid; rr < pw; rr += nth) {
+        T* Arow = A + rr * LDD + c0;
+#pragma unroll 16
+        for (int c = 0; c < 16; ++c) {
           if (c < w) {
-            T acc = (T)0;
-#pragma unroll
-            for (int m = 0; m < 16; ++m)
-              if (m <= c) acc += A[rr * LDD + c0 + m] * V[(c0 + c) * LDD + c0 + m];
-            out[t] = acc / sh.dv[c0 + c];
+            const T* Lc = A + (c0 + c) * LDD + c0;
+            T v = Arow[c];
+            for (int m = 0; m < c; ++m) v -= Arow[m] * (sh.dv[c0 + m] * Lc[m]);
+            Arow[c] = v / sh.dv[c0 + c];
           }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int idx = tid + nth * t;
-        if (idx < nr * 16) {
-          const int rr = r0 + idx / 16, c = idx % 16;
-          if (c < w) A[rr * LDD + c0 + c] = out[t];
         }
       }
       __syncthreads();
@@ -209,6 +194,19 @@ __device__ int bf_diag_block(T* G, int64_t f, int pw, T* D, T* Li, int64_t ldi, 
       if (i < j || i >= pw) Li[i + (int64_t)j * ldi] = (T)0;
     }
   return nhit;
+}
+
+template <typename T>
+__device__ int bf_diag_block(T* G, int64_t f, int pw, T* D, T* Li, int64_t ldi, bool zero_rest, const int8_t* dsign,
+                             T eps, T delta, T* smem, DiagScratch<T>& sh) {
+  constexpr int LDD = kDiagLD;
+  T* A = smem;             // the block as it is eliminated; L and the pivots at the end
+  T* V = smem + 64 * LDD;  // L^{-1}
+  for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+    const int i = idx % 64, j = idx / 64;
+    A[i * LDD + j] = (i < pw && j < pw && i >= j) ? __ldcg(G + i + (int64_t)j * f) : (T)0;
+  }
+  return bf_diag_factor<T>(A, V, G, f, pw, D, Li, ldi, zero_rest, dsign, eps, delta, sh);
 }
 
 }  // namespace clr

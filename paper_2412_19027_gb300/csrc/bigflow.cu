@@ -98,6 +98,96 @@ __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
   if (threadIdx.x == 0 && nhit) atomicAdd(hits, nhit);
 }
 
+// DX(p), 1 <= p < P: the three links of the critical chain in one task, kept in
+// shared memory between them -- the panel row T(p-1, p) (its L rows stored and
+// published through the trsm word of block p as soon as they are written), the
+// update of the diagonal tile (p, p) by panel p-1, and D(p).  Same arithmetic,
+// in the same order, as the three separate tasks.
+template <typename T>
+__device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T* F, T* E, T* Dp, const int8_t* dsign,
+                       T eps, T delta, T* sm, DiagScratch<T>& sh, T* dl, int* trsm_word) {
+  T* Ls = sm;               // Linv of panel p - 1; work space of the factorization afterwards
+  T* Xs = sm + NB * LD;     // F_{p,p-1}, then L_{p,p-1}
+  T* A = sm + 2 * NB * LD;  // the diagonal tile (p, p), lower triangle
+  const int64_t f = g.f, kq = (int64_t)(p - 1) * NB, k0 = (int64_t)p * NB;
+  const int pw = bnrow(g, p);  // panel p - 1 is a full 64-column panel (p - 1 < P - 1)
+  T* G = F + bf.goff[b];
+  T* Eb = E + bf.eoff[b];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int idx = tid; idx < NB * NB; idx += NT) {
+    const int i = idx % NB, j = idx / NB;
+    Ls[i * LD + j] = __ldcg(Eb + (kq + i) + (kq + j) * f);
+    Xs[i * LD + j] = (i < pw) ? __ldcg(G + (k0 + i) + (kq + j) * f) : (T)0;
+    A[i * LD + j] = (i < pw && j < pw && i >= j) ? __ldcg(G + (k0 + i) + (k0 + j) * f) : (T)0;
+  }
+  if (tid < NB) dl[tid] = __ldcg(Dp + bf.k0pos[b] + kq + tid);
+  __syncthreads();
+  const int tr = tid % 16, tc = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  for (int l = 0; l < NB; ++l) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = Xs[(tr + 16 * a) * LD + l];
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) bv[bb] = Ls[(tc + 16 * bb) * LD + l];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+  }
+  __syncthreads();  // every thread has read F_{p,p-1}
+#pragma unroll
+  for (int bb = 0; bb < 4; ++bb) {
+    const int j = tc + 16 * bb;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = tr + 16 * a;
+      const T v = (i < pw) ? acc[a][bb] / dl[j] : (T)0;
+      Xs[i * LD + j] = v;
+      if (i < pw) G[(k0 + i) + (kq + j) * f] = v;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    st_release(trsm_word, p);
+  }
+  // A_ij -= sum_l L_il (L_jl d_l), i >= j
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+  for (int l = 0; l < NB; ++l) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = Xs[(tr + 16 * a) * LD + l];
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) bv[bb] = Xs[(tc + 16 * bb) * LD + l] * dl[l];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+  }
+#pragma unroll
+  for (int bb = 0; bb < 4; ++bb) {
+    const int j = tc + 16 * bb;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = tr + 16 * a;
+      if (i < pw && i >= j) A[i * LD + j] -= acc[a][bb];
+    }
+  }
+  __syncthreads();
+  const int64_t kp = bf.k0pos[b] + k0;
+  return bf_diag_factor<T>(A, Ls, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp, eps, delta,
+                           sh);
+}
+
 // T(p, i): L_IK = F_IK Linv^T D_K^{-1} for the rows of block i (each thread 4 x 4).
 template <typename T>
 __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, T* F, const T* E,
@@ -291,6 +381,10 @@ __global__ void __launch_bounds__(NT, 2)
           case 0:
             ok = wait_ge(w.t(p, p), p, err);
             break;
+          case 5:
+            ok = wait_ge(w.diag + p - 1, 1, err) && wait_ge(w.t(p, p - 1), p - 1, err) &&
+                 wait_ge(w.t(p, p), p - 1, err);
+            break;
           case 1:
             ok = wait_ge(w.diag + p, 1, err) && wait_ge(w.t(tk.i, p), p, err);
             break;
@@ -321,6 +415,12 @@ __global__ void __launch_bounds__(NT, 2)
       case 0:
         task_diag<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, dsh);
         break;
+      case 5: {
+        const Words w = words_of(state + soff[b], g);
+        const int nhit = task_dx<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, sm, dsh, dl, w.trsm + tk.p);
+        if (tid == 0 && nhit) atomicAdd(hits, nhit);
+        break;
+      }
       case 1:
         task_trsm<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
         break;
@@ -343,6 +443,10 @@ __global__ void __launch_bounds__(NT, 2)
         case 0:
           st_release(w.diag + p, 1);
           break;
+        case 5:
+          st_release(w.t(p, p), p);
+          st_release(w.diag + p, 1);
+          break;
         case 1:
           st_release(w.trsm + tk.i, p + 1);
           break;
@@ -361,9 +465,10 @@ __global__ void __launch_bounds__(NT, 2)
 }
 
 template <typename T>
-size_t flow_smem() {  // the update task's two operand tiles; the diagonal task needs less
-  static_assert(2 * NB * LDK >= kDiagSmem && 2 * NB * LDK >= 2 * NB * LD, "shared memory of the flow tasks");
-  return 2 * NB * LDK * sizeof(T);
+size_t flow_smem() {  // the fused chain task's three blocks; the others need less
+  static_assert(3 * NB * LD >= kDiagSmem && 3 * NB * LD >= 2 * NB * LDK && LD == kDiagLD,
+                "shared memory of the flow tasks");
+  return 3 * NB * LD * sizeof(T);
 }
 }  // namespace
 

@@ -48,7 +48,8 @@ struct BigLevelPlan {
 // pivot blocks [64b, min(64b+64, c)), then the update rows [c, f) in blocks of
 // 64 from c, nbf blocks in all.  Tasks (64 x 64 tiles):
 //   D(p)        diagonal block of panel p: LDL^T, pivots, Linv = L_KK^{-1}
-//               (written into E_KK, which it equals);
+//               (written into E_KK, which it equals); for 1 <= p < P the task
+//               DX(p) does T(p-1, p), U(p-1, p, p) and D(p) in one, in shared memory;
 //   T(p, i)     block row i > p of panel p: L_IK = F_IK Linv^T D_K^{-1};
 //   Efin(p, e)  E rows of panel p, column block e < p: E_KC <- Linv E_KC;
 //   U(p, i, j)  trailing tile i >= j > p: F_IJ -= L_IK D_K L_JK^T;
@@ -60,7 +61,7 @@ struct BigLevelPlan {
 // CTA that is running, so the launch needs no co-residency guarantee.
 struct FlowTask {
   int32_t bf;    // big-front id
-  int16_t kind;  // 0 D, 1 T, 2 Efin, 3 U, 4 EU
+  int16_t kind;  // 0 D, 1 T, 2 Efin, 3 U, 4 EU, 5 DX
   int16_t p;     // panel
   int32_t i, j;  // block row; block column (Efin: e; EU: e)
 };

@@ -295,6 +295,19 @@ inline unsigned soc_grid(const ConeDev& cd, int G) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, 16 * kSMs));
 }
 
+// Launch shape of the thread-per-cone exp/pow kernels: their FP64 transcendental
+// work (logs, exponentials, Newton steps) is bound by the SM's FP64 pipe (~2 DFMA
+// per clock on a GB300), so few cones are spread over as many SMs as possible
+// (blocks of ceil(n / 152) threads, at most 128) rather than packed into few.
+struct EpLaunch {
+  unsigned blocks;
+  int threads;
+};
+inline EpLaunch ep_launch(int64_t nc) {
+  const int64_t t = std::min<int64_t>(128, std::max<int64_t>(1, (nc + kSMs - 1) / kSMs));
+  return EpLaunch{(unsigned)((nc + t - 1) / t), (int)t};
+}
+
 template <int G>
 __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
                             const int* skip) {
@@ -661,7 +674,8 @@ int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const dou
     else k_scale_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, z, sc, skip);
   }
   if (cd.n_exp + cd.n_pow > 0)
-    k_scale_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, sc, skip);
+    k_scale_exppow<<<ep_launch(cd.n_exp + cd.n_pow).blocks, ep_launch(cd.n_exp + cd.n_pow).threads, 0, st>>>(
+        cd, s, z, sc, skip);
   if (cd.n_psd > 0) {
     const int threads = 32 * ((cd.psd_k + 1) / 2 > 0 ? (cd.psd_k + 1) / 2 : 1);
     k_scale_psd<<<(unsigned)cd.n_psd, threads < 64 ? 64 : threads, 0, st>>>(cd, s, z, sc, skip);
@@ -723,14 +737,37 @@ __global__ void k_step_nonneg(ConeDev cd, const double* __restrict__ s, const do
                               const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
                               const int* skip) {
   if (skip && *skip) return;
+  // a ratio -x / dx is divided out only when it can beat the thread's running
+  // minimum (x <= best (-dx) (1 + 1e-15) covers every quotient that rounds to at
+  // most best): the FP64 divisions, not the loads, bounded this pass
   RunExt<false> mn;
   const int64_t b0 = cd.m_zero, b1 = cd.m_zero + cd.m_nonneg;
+  double best = INFINITY;
+  int bpid = -1;
   for (int64_t i = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b1; i += (int64_t)gridDim.x * blockDim.x) {
     const double dsi = ds[i], dzi = dz[i];
-    double a = INFINITY;
-    if (dsi < 0) a = fmin(a, -s[i] / dsi);
-    if (dzi < 0) a = fmin(a, -z[i] / dzi);
-    if (a < INFINITY) mn.add(sc, &IterScal::amin_bits, cd.row_pid[i], dbits(a));
+    if (!(dsi < 0) && !(dzi < 0)) continue;
+    const int pid = cd.row_pid[i];
+    if (pid != bpid) {
+      best = INFINITY;
+      bpid = pid;
+    }
+    if (dsi < 0) {
+      const double num = s[i], den = -dsi;
+      if (num <= best * den * (1.0 + 1e-15)) {
+        const double a = num / den;
+        best = fmin(best, a);
+        mn.add(sc, &IterScal::amin_bits, pid, dbits(a));
+      }
+    }
+    if (dzi < 0) {
+      const double num = z[i], den = -dzi;
+      if (num <= best * den * (1.0 + 1e-15)) {
+        const double a = num / den;
+        best = fmin(best, a);
+        mn.add(sc, &IterScal::amin_bits, pid, dbits(a));
+      }
+    }
   }
   mn.flush(sc, &IterScal::amin_bits);
 }
@@ -962,11 +999,11 @@ int cones_step_nonsym(cudaStream_t st, const ConeDev& cd, const double* s, const
   k_ns_reset<<<grid_for(cd.nprob, 128), 128, 0, st>>>(sc, cd.nprob, skip);
   const int64_t nc = cd.n_exp + cd.n_pow;
   if (nc == 0) return CLR_OK;
-  const unsigned g = (unsigned)((nc + 63) / 64);
-  k_ns_interior<<<g, 64, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, skip);
+  const EpLaunch el = ep_launch(nc);
+  k_ns_interior<<<el.blocks, el.threads, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, skip);
   if (nbhd) {
-    k_ns_first<<<g, 64, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, beta, skip);
-    k_ns_window<<<g, 64, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, beta, skip);
+    k_ns_first<<<el.blocks, el.threads, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, beta, skip);
+    k_ns_window<<<el.blocks, el.threads, 0, st>>>(cd, s, ds, z, dz, sc, backtrack, beta, skip);
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -1212,7 +1249,8 @@ int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const
     else k_ds_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
   }
   if (cd.n_exp + cd.n_pow > 0)
-    k_ds_exppow<<<(unsigned)((cd.n_exp + cd.n_pow + 127) / 128), 128, 0, st>>>(cd, s, z, dsa, dza, sc, ds_out,
+    k_ds_exppow<<<ep_launch(cd.n_exp + cd.n_pow).blocks, ep_launch(cd.n_exp + cd.n_pow).threads, 0, st>>>(
+        cd, s, z, dsa, dza, sc, ds_out,
                                                                                skip);
   if (cd.n_psd > 0) {
     const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));

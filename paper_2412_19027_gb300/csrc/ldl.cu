@@ -236,16 +236,23 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
 }
 }  // namespace
 
-// Reorder the tasks [t0, end) of one level (generated in a topological order of
-// the graph whose edges are the waits of k_bf_flow) into the order of list
-// scheduling by longest path to the end: Kahn's algorithm taking, among the
-// tasks whose predecessors are all placed, the one with the largest bottom
-// level (the diagonal tasks weigh 4, the others 1).  The counter hands tasks out
-// in this order, so the chain D(p) -> T(p, p+1) -> U(p, p+1, p+1) -> D(p+1) is
-// taken early and the bulk of the updates fills the CTAs around it.
-static void flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0) {
+// Order the tasks [t0, end) of one level for the counter of k_bf_flow: the
+// dependency graph has the edges of the kernel's waits; Kahn's algorithm takes,
+// among the tasks whose predecessors are all placed, the one with the largest
+// bottom level (longest path to the end, each task weighted by its typical
+// duration), so the chains that bound the factorization -- the diagonal tasks
+// and the successive updates of one tile -- are handed out early and the bulk of
+// the updates fills the CTAs around them.  Returns false if the graph has a
+// cycle (a bug: the caller then fails the setup).
+//   deps: D(0) -; DX(p) D/DX(p-1), U(p-2, p, p-1), U(p-2, p, p);
+//   T(p, i) D/DX(p), U(p-1, i, p); Efin(p, e) D/DX(p), EU(p-1, p, e);
+//   U(p, i, j) T~(p, i), T~(p, j), U(p-1, i, j);
+//   EU(p, i, e) T~(p, i), Efin(p, e) or D/DX(p) (e = p), EU(p-1, i, e);
+// T~(p, i) is DX(p+1) when i = p + 1 is a pivot block (folded), else T(p, i).
+static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0,
+                                const std::vector<int64_t>& P_of) {
   const int64_t n = (int64_t)tasks.size() - t0;
-  if (n <= 1) return;
+  if (n <= 1) return true;
   auto key = [](int64_t b, int kind, int64_t p, int64_t i, int64_t j) -> uint64_t {
     return ((uint64_t)b << 43) ^ ((uint64_t)kind << 40) ^ ((uint64_t)p << 28) ^ ((uint64_t)i << 14) ^ (uint64_t)j;
   };
@@ -259,6 +266,10 @@ static void flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0) {
     auto it = idx.find(key(b, kind, p, i, j));
     return it == idx.end() ? -1 : it->second;
   };
+  auto dd = [&](int64_t b, int64_t p) { return p == 0 ? find(b, 0, 0, 0, 0) : find(b, 5, p, p, p); };
+  auto tt = [&](int64_t b, int64_t p, int64_t i) {
+    return (i == p + 1 && i < P_of[b]) ? find(b, 5, i, i, i) : find(b, 1, p, i, p);
+  };
   std::vector<std::vector<int64_t>> succ(n);
   std::vector<int> indeg(n, 0);
   for (int64_t t = 0; t < n; ++t) {
@@ -266,32 +277,54 @@ static void flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0) {
     int64_t d[3] = {-1, -1, -1};
     const int64_t p = k.p, i = k.i, j = k.j, b = k.bf;
     switch (k.kind) {
-      case 0: d[0] = p > 0 ? find(b, 3, p - 1, p, p) : -1; break;
-      case 1: d[0] = find(b, 0, p, p, p); d[1] = p > 0 ? find(b, 3, p - 1, i, p) : -1; break;
-      case 2: d[0] = find(b, 0, p, p, p); d[1] = p - 1 >= j ? find(b, 4, p - 1, p, j) : -1; break;
+      case 0: break;
+      case 5:
+        d[0] = dd(b, p - 1);
+        d[1] = p >= 2 ? find(b, 3, p - 2, p, p - 1) : -1;
+        d[2] = p >= 2 ? find(b, 3, p - 2, p, p) : -1;
+        break;
+      case 1: d[0] = dd(b, p); d[1] = p > 0 ? find(b, 3, p - 1, i, p) : -1; break;
+      case 2: d[0] = dd(b, p); d[1] = p - 1 >= j ? find(b, 4, p - 1, p, j) : -1; break;
       case 3:
-        d[0] = find(b, 1, p, i, p);
-        d[1] = find(b, 1, p, j, p);
+        d[0] = tt(b, p, i);
+        d[1] = tt(b, p, j);
         d[2] = p > 0 ? find(b, 3, p - 1, i, j) : -1;
         break;
       default:
-        d[0] = find(b, 1, p, i, p);
-        d[1] = j < p ? find(b, 2, p, p, j) : find(b, 0, p, p, p);
+        d[0] = tt(b, p, i);
+        d[1] = j < p ? find(b, 2, p, p, j) : dd(b, p);
         d[2] = p - 1 >= j ? find(b, 4, p - 1, i, j) : -1;
         break;
     }
-    for (int q = 0; q < 3; ++q)
-      if (d[q] >= 0 && (q == 0 || d[q] != d[q - 1])) {
-        succ[d[q]].push_back(t);
-        ++indeg[t];
-      }
+    for (int q = 0; q < 3; ++q) {
+      if (d[q] < 0) continue;
+      bool dup = false;
+      for (int r = 0; r < q; ++r) dup = dup || d[r] == d[q];
+      if (dup) continue;
+      succ[d[q]].push_back(t);
+      ++indeg[t];
+    }
   }
-  // bottom levels: the generated order is topological, so go backwards
+  // a topological order (FIFO Kahn), then bottom levels in its reverse
+  std::vector<int64_t> topo;
+  topo.reserve((size_t)n);
+  {
+    std::vector<int> deg = indeg;
+    for (int64_t t = 0; t < n; ++t)
+      if (deg[t] == 0) topo.push_back(t);
+    for (size_t h = 0; h < topo.size(); ++h)
+      for (int64_t u : succ[topo[h]])
+        if (--deg[u] == 0) topo.push_back(u);
+  }
+  if ((int64_t)topo.size() != n) return false;
   std::vector<int64_t> bl(n, 0);
-  for (int64_t t = n - 1; t >= 0; --t) {
+  for (int64_t h = n - 1; h >= 0; --h) {
+    const int64_t t = topo[h];
     int64_t m = 0;
     for (int64_t u : succ[t]) m = std::max(m, bl[u]);
-    bl[t] = m + (tasks[t0 + t].kind == 0 ? 4 : 1);
+    // weights: typical task times in microseconds on a GB300 (FP32, 64 x 64 tiles)
+    static const int64_t wt[6] = {30, 7, 6, 11, 11, 40};
+    bl[t] = m + wt[tasks[t0 + t].kind];
   }
   std::priority_queue<std::pair<int64_t, int64_t>> ready;  // (bottom level, -index)
   for (int64_t t = 0; t < n; ++t)
@@ -305,7 +338,9 @@ static void flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0) {
     for (int64_t u : succ[t])
       if (--indeg[u] == 0) ready.emplace(bl[u], -u);
   }
-  if ((int64_t)out.size() == n) std::copy(out.begin(), out.end(), tasks.begin() + t0);
+  if ((int64_t)out.size() != n) return false;
+  std::copy(out.begin(), out.end(), tasks.begin() + t0);
+  return true;
 }
 
 int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps& mp, const std::vector<int8_t>& dsign,
@@ -478,13 +513,11 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       pd.wl->front = dbuf + pd.fo;
       pd.wl->pref = dbuf + pd.po;
     }
-    // dataflow task tables (bigfront.cuh), per level in blocks k = 0 .. max panels:
-    //   D(k), T(k, .) of every front; then the updates of panel k - 1 outside
-    //   column block k (trailing tiles by column, E tiles); then Efin(k, .) and
-    //   panel k's updates of column block k + 1, which D(k + 1) and T(k + 1, .)
-    //   wait for.  Every task depends only on tasks before it.
+    // dataflow task tables (bigfront.cuh), per level: every task of every big front
+    // of the level, then ordered by flow_priority_order.  A pivot block p >= 1
+    // has the fused task DX(p) instead of D(p), T(p-1, p) and U(p-1, p, p).
     std::vector<FlowTask> tasks;
-    std::vector<int64_t> soff(bf_f.size(), 0);
+    std::vector<int64_t> soff(bf_f.size(), 0), P_of(bf_f.size(), 0);
     int64_t words = 0;
     st.flow_t0.assign(sy.nlev, 0);
     st.flow_nt.assign(sy.nlev, 0);
@@ -492,44 +525,30 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
     for (int64_t l = 0; l < sy.nlev; ++l) {
       if (st.lev_big[l].empty()) continue;
       st.flow_head[l] = words++;
-      std::vector<int64_t> ids;
-      int64_t maxp = 0;
-      for (int64_t J : st.lev_big[l]) {
-        const int64_t b = bid_of[J];
-        ids.push_back(b);
-        soff[b] = words;
-        words += flow_words(bf_f[b], bf_c[b]);
-        maxp = std::max<int64_t>(maxp, (bf_c[b] + kBfNB - 1) / kBfNB);
-      }
       st.flow_t0[l] = (int64_t)tasks.size();
       auto add = [&](int64_t b, int kind, int64_t p, int64_t i, int64_t j) {
         tasks.push_back(FlowTask{(int32_t)b, (int16_t)kind, (int16_t)p, (int32_t)i, (int32_t)j});
       };
-      for (int64_t k = 0; k <= maxp; ++k) {
-        for (int64_t b : ids) {
-          const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, n = flow_nbf(bf_f[b], bf_c[b]);
-          if (k >= P) continue;
-          add(b, 0, k, k, k);
-          for (int64_t i = k + 1; i < n; ++i) add(b, 1, k, i, k);
-        }
-        for (int64_t b : ids) {
-          const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, n = flow_nbf(bf_f[b], bf_c[b]);
-          const int64_t p = k - 1;
-          if (p < 0 || p >= P) continue;
-          for (int64_t j = p + 2; j < n; ++j)
-            for (int64_t i = j; i < n; ++i) add(b, 3, p, i, j);
-          for (int64_t i = p + 1; i < n; ++i)
+      for (int64_t J : st.lev_big[l]) {
+        const int64_t b = bid_of[J];
+        soff[b] = words;
+        words += flow_words(bf_f[b], bf_c[b]);
+        const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, nb = flow_nbf(bf_f[b], bf_c[b]);
+        P_of[b] = P;
+        for (int64_t p = 0; p < P; ++p) {
+          add(b, p == 0 ? 0 : 5, p, p, p);
+          for (int64_t i = p + 1; i < nb; ++i)
+            if (!(i == p + 1 && i < P)) add(b, 1, p, i, p);
+          for (int64_t e = 0; e < p; ++e) add(b, 2, p, p, e);
+          for (int64_t j = p + 1; j < nb; ++j)
+            for (int64_t i = j; i < nb; ++i)
+              if (!(i == p + 1 && j == p + 1 && i < P)) add(b, 3, p, i, j);
+          for (int64_t i = p + 1; i < nb; ++i)
             for (int64_t e = 0; e <= p; ++e) add(b, 4, p, i, e);
-        }
-        for (int64_t b : ids) {
-          const int64_t P = (bf_c[b] + kBfNB - 1) / kBfNB, n = flow_nbf(bf_f[b], bf_c[b]);
-          if (k >= P) continue;
-          for (int64_t e = 0; e < k; ++e) add(b, 2, k, k, e);
-          for (int64_t i = k + 1; i < n && k + 1 < n; ++i) add(b, 3, k, i, k + 1);
         }
       }
       st.flow_nt[l] = (int64_t)tasks.size() - st.flow_t0[l];
-      flow_priority_order(tasks, st.flow_t0[l]);
+      if (!flow_priority_order(tasks, st.flow_t0[l], P_of)) return CLR_E_INVALID;
     }
     st.flow_words = words;
     if (!tasks.empty()) {
