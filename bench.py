@@ -41,6 +41,7 @@ UNIT = "iter/s"
 WORKLOAD = "mixed-cone QP n=2000 m=6600 (500 zero, 3000 nonneg, 500 SOC5, 100 exp, 100 pow0.3), P=diag+rank10"
 FP64_PEAK_TFLOPS = 1.25            # GB300 FP64 (FFMA and DMMA), nominal
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
+FLOW_DRAM_BYTES_FP32 = 17.867008e6 + 2.787840e6    # k_bf_flow<float>, mixed-cone QP (profiles/k_bf_flow_*)
 
 
 def measured_peaks():
@@ -535,9 +536,15 @@ def run_ours(args):
         bound, peak, psrc = "alu", FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
     else:
         bound, peak, psrc = "alu", FP64_PEAK_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s"
+    # DRAM bytes of the factorization's dominant launch (k_bf_flow, one per factorization
+    # of this workload) from one ncu capture of this kernel version (profiles/); other
+    # precisions were not captured
+    traffic = FLOW_DRAM_BYTES_FP32 if (args.factor_bits == 32 and not args.no_graph) else None
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "numeric LDL^T (multifrontal, FP%d)" % args.factor_bits,
-                "flops_per_launch": sym["factor_flops"], "ms_per_launch": fact_ms, "peak_source": psrc}
+                "traffic": traffic, "kernel": "numeric LDL^T (multifrontal, FP%d)" % args.factor_bits,
+                "flops_per_launch": sym["factor_flops"], "ms_per_launch": fact_ms, "peak_source": psrc,
+                "traffic_source": "ncu dram__bytes_read+write of k_bf_flow<float> (dominant launch)" if traffic
+                else None}
     cone_roof = None
     if not args.no_cone_roofline and rank == 0:
         cone_roof = run_cone_roofline(clr, W, peaks)
