@@ -60,6 +60,11 @@ __device__ __forceinline__ int64_t chunk_slot(const ChunkGrid& g) {
 // The sum of a row is formed in one fixed order whatever G is (32 partial sums,
 // entry e of the row going to partial e mod 32, then the pairwise tree t += t+16,
 // t += t+8, ...), so a row gives the same bits in every cohort it belongs to.
+// Rows longer than this go to k_kmv_long (a CTA per row); each row's sum is taken
+// in an order fixed by its length alone, so a problem's K products are the same
+// alone and in a cohort.
+constexpr int64_t kLongRow = 512;
+
 template <int G>
 __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t* __restrict__ kptr,
                       const int32_t* __restrict__ kcol, const int32_t* __restrict__ kvi, const double* __restrict__ kval,
@@ -79,6 +84,7 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
 #pragma unroll
     for (int u = 0; u < NU; ++u) a[u] = b[u] = 0.0;
     const int64_t p0 = kptr[i], p1 = kptr[i + 1];
+    if (p1 - p0 > kLongRow) continue;  // k_kmv_long (the whole G-lane group skips)
     // four 32-entry steps per pass: all loads of the pass issued before the adds,
     // which keep the order of the plain one-step loop (partial t sums entries
     // p = p0 + t (mod 32) in increasing p)
@@ -133,6 +139,94 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
     }
   }
   if (mode == 1) mx.flush(sc, &IterScal::rnorm_bits);
+}
+
+// The long rows: 8 warps per row, warp w sums the w-th of 8 contiguous segments of
+// 32-entry steps (lane t: entries p = p0 + t (mod 32)), the 8 partials of a lane are
+// added in warp order, then the 32 lanes by the same butterfly as k_kmv.  Outputs
+// as k_kmv for the modes.
+__global__ void __launch_bounds__(256)
+    k_kmv_long(int mode, const int64_t* __restrict__ rows, int64_t nrows, int64_t n, const int64_t* __restrict__ kptr,
+               const int32_t* __restrict__ kcol, const int32_t* __restrict__ kvi, const double* __restrict__ kval,
+               const double* __restrict__ v, double* __restrict__ lo, double* __restrict__ hi,
+               const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ pid,
+               IterScal* sc, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double pa[8][32], pb[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  RunExt<true> mx;
+  for (int64_t t = blockIdx.x; t < nrows; t += gridDim.x) {
+    const int64_t i = rows[t];
+    const int64_t p0 = kptr[i], p1 = kptr[i + 1];
+    const int64_t S = ((p1 - p0 + 255) / 256) * 32;  // segment length, a multiple of 32
+    const int64_t s0 = p0 + w * S, s1 = min(p1, s0 + S);
+    double a = 0.0, b = 0.0;
+    for (int64_t base = s0; base < s1; base += 128) {
+      double tv[4];
+      bool tx[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t p = base + 32 * k + lane;
+        tv[k] = 0.0;
+        tx[k] = true;
+        if (p < s1) {
+          const int32_t c = kcol[p];
+          tv[k] = kval[kvi[p]] * v[c];
+          tx[k] = c < n;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (base + 32 * k + lane >= s1) continue;
+        if (tx[k]) a += tv[k];
+        else b += tv[k];
+      }
+    }
+    pa[w][lane] = a;
+    pb[w][lane] = b;
+    __syncthreads();
+    if (w == 0) {
+      a = pa[0][lane];
+      b = pb[0][lane];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) {
+        a += pa[q][lane];
+        b += pb[q][lane];
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+      }
+      if (lane == 0) {
+        if (mode == 0) {
+          lo[i] = a;
+          hi[i] = b;
+        } else if (mode == 1) {
+          const double r = rhs[i] - (a + b);
+          out[i] = r;
+          mx.add(sc, &IterScal::rnorm_bits, pid[i], dbits(fabs(r)));
+        } else {
+          out[i - n] = -rhs[i - n] + b;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (mode == 1 && w == 0) mx.flush(sc, &IterScal::rnorm_bits);
+}
+
+// launch k_kmv_long for the long rows in [r0, r1)
+void kmv_long(cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v,
+              const std::vector<int64_t>& h_long, const double* x, double* lo, double* hi, const double* rhs,
+              double* out, IterScal* sc, const int* skip) {
+  if (h_long.empty()) return;
+  const int64_t a = std::lower_bound(h_long.begin(), h_long.end(), r0) - h_long.begin();
+  const int64_t b = std::lower_bound(h_long.begin(), h_long.end(), r1) - h_long.begin();
+  if (b <= a) return;
+  const unsigned g = (unsigned)std::min<int64_t>(b - a, 2 * kSMs);
+  k_kmv_long<<<g, 256, 0, s>>>(mode, v.long_rows + a, b - a, n, v.kptr, v.kcol, v.kvi, v.kval, x, lo, hi, rhs, out,
+                               v.pid, sc, skip);
 }
 
 // ------------------------------------------------------------------ residuals
@@ -921,6 +1015,12 @@ int Solver::upload() {
         vi[p] = row[p - cnt[i]].second;
       }
     }
+    h_long_.clear();
+    for (int64_t i = 0; i < N; ++i)
+      if (cnt[i + 1] - cnt[i] > kLongRow) h_long_.push_back(i);
+    v_.nlong = (int64_t)h_long_.size();
+    v_.long_rows = h_long_.empty() ? nullptr : ar_.upload(h_long_.data(), v_.nlong);
+    if (!h_long_.empty() && !v_.long_rows) return CLR_E_OOM;
     v_.kptr = ar_.upload(cnt.data(), N + 1);
     v_.kcol = ar_.upload(col.data(), (int64_t)col.size());
     v_.kvi = ar_.upload(vi.data(), (int64_t)vi.size());
@@ -1097,6 +1197,7 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
       case 8: k_kmv<8><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
       default: k_kmv<4><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
     }
+    kmv_long(ss, 1, 0, N, hp.n, v_, h_long_, sol, nullptr, nullptr, rhs, v_.r, sc_, irs);
   };
   const int cb = (int)std::min<int64_t>(1024, std::max<int64_t>(32, ((B + 31) / 32) * 32));
   int rc = ldl_solve_add(s, rhs, 0);
@@ -1161,8 +1262,9 @@ void launch_kmv_split(cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t 
   const int kg = grid_for((r1 - r0) * G, 256, 16 * kSMs);
   k_kmv<G><<<kg, 256, 0, s>>>(mode, r0, r1, n, v.kptr, v.kcol, v.kvi, v.kval, x, lo, hi, rhs, out, v.pid, sc, skip);
 }
-void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v, const double* x,
-         double* lo, double* hi, const double* rhs, double* out, IterScal* sc, const int* skip) {
+void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v,
+         const std::vector<int64_t>& h_long, const double* x, double* lo, double* hi, const double* rhs, double* out,
+         IterScal* sc, const int* skip) {
   if (r1 <= r0) return;
   switch (G) {
     case 32: launch_kmv_split<32>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
@@ -1170,6 +1272,7 @@ void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, con
     case 8: launch_kmv_split<8>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
     default: launch_kmv_split<4>(s, mode, r0, r1, n, v, x, lo, hi, rhs, out, sc, skip); break;
   }
+  kmv_long(s, mode, r0, r1, n, v, h_long, x, lo, hi, rhs, out, sc, skip);
 }
 }  // namespace
 
@@ -1189,7 +1292,7 @@ int Solver::direction(bool affine) {
   k_dots<<<nck, 256, 0, s>>>(cg, da, v_.part, S_D0, halt);
   k_fin_dtau<<<(unsigned)B, 128, 0, s>>>(sc_, v_.part, pst_, v_.ckx_ptr, v_.ckz_ptr, halt);
   k_recover<<<nck, 256, 0, s>>>(cg, dir, v_.sol1, v_.sol2, sc_, halt);
-  kmv(csr_group_, s, 2, n, N, n, v_, dir, nullptr, nullptr, v_.dsrhs, ds, sc_, halt);
+  kmv(csr_group_, s, 2, n, N, n, v_, h_long_, dir, nullptr, nullptr, v_.dsrhs, ds, sc_, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -1236,7 +1339,7 @@ int Solver::iteration() {
   int rc;
   mark(2);
   // ---- residuals, objectives, mu, termination ----
-  kmv(csr_group_, s, 0, 0, N, n, v_, v_.xz, v_.lo, v_.hi, nullptr, nullptr, sc_, halt);
+  kmv(csr_group_, s, 0, 0, N, n, v_, h_long_, v_.xz, v_.lo, v_.hi, nullptr, nullptr, sc_, halt);
   CLR_CUDA(cudaMemsetAsync(v_.maxb, 0, sizeof(unsigned long long) * M_NMAX * (size_t)B, s));
   k_resid<<<nck, 256, 0, s>>>(cg, v_.xz, v_.s, v_.lo, v_.hi, v_.q, v_.b, v_.D, v_.E, sc_, v_.G, v_.qp, v_.part,
                               v_.maxb, halt);

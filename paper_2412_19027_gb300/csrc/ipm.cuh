@@ -18,6 +18,8 @@
 namespace clr {
 
 struct VecDev {
+  const int64_t* long_rows = nullptr;  // KKT rows with more than kLongRow entries (sorted)
+  int64_t nlong = 0;
   double *xz, *s;            // iterate: [x; z] (N), s (m)
   double *lo, *hi;           // split K products (N each)
   double *G;                 // [G1; G2] (N)
@@ -99,6 +101,7 @@ class Solver {
   int64_t nckx_ = 0, nckz_ = 0, pst_ = 1;
   int hist_rows_ = 0;
   int csr_group_ = 32;
+  std::vector<int64_t> h_long_;  // KKT rows handled by k_kmv_long
   // iteration graphs per factor precision (0: configured, 1: FP64 after an escalation)
   cudaGraph_t graph_[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec_[2] = {nullptr, nullptr};
