@@ -68,6 +68,7 @@ constexpr int64_t kLongRow = 512;
 template <int G>
 __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t* __restrict__ kptr,
                       const int32_t* __restrict__ kcol, const int32_t* __restrict__ kvi, const double* __restrict__ kval,
+                      const double* __restrict__ kfv,
                       const double* __restrict__ v, double* __restrict__ lo, double* __restrict__ hi,
                       const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ pid,
                       IterScal* sc, const int* skip) {
@@ -100,7 +101,7 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
           tx[k][u] = true;
           if (p < p1) {
             const int32_t c = kcol[p];
-            tv[k][u] = kval[kvi[p]] * v[c];
+            tv[k][u] = (i < n ? kfv[p] : kval[kvi[p]]) * v[c];
             tx[k][u] = c < n;
           }
         }
@@ -148,6 +149,7 @@ __global__ void k_kmv(int mode, int64_t r0, int64_t r1, int64_t n, const int64_t
 __global__ void __launch_bounds__(256)
     k_kmv_long(int mode, const int64_t* __restrict__ rows, int64_t nrows, int64_t n, const int64_t* __restrict__ kptr,
                const int32_t* __restrict__ kcol, const int32_t* __restrict__ kvi, const double* __restrict__ kval,
+               const double* __restrict__ kfv,
                const double* __restrict__ v, double* __restrict__ lo, double* __restrict__ hi,
                const double* __restrict__ rhs, double* __restrict__ out, const int32_t* __restrict__ pid,
                IterScal* sc, const int* skip) {
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256)
         tx[k] = true;
         if (p < s1) {
           const int32_t c = kcol[p];
-          tv[k] = kval[kvi[p]] * v[c];
+          tv[k] = (i < n ? kfv[p] : kval[kvi[p]]) * v[c];
           tx[k] = c < n;
         }
       }
@@ -224,9 +226,9 @@ void kmv_long(cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const
   const int64_t a = std::lower_bound(h_long.begin(), h_long.end(), r0) - h_long.begin();
   const int64_t b = std::lower_bound(h_long.begin(), h_long.end(), r1) - h_long.begin();
   if (b <= a) return;
-  const unsigned g = (unsigned)std::min<int64_t>(b - a, 2 * kSMs);
-  k_kmv_long<<<g, 256, 0, s>>>(mode, v.long_rows + a, b - a, n, v.kptr, v.kcol, v.kvi, v.kval, x, lo, hi, rhs, out,
-                               v.pid, sc, skip);
+  const unsigned g = (unsigned)std::min<int64_t>(b - a, 16 * kSMs);  // a row per CTA, up to 16 CTAs per SM
+  k_kmv_long<<<g, 256, 0, s>>>(mode, v.long_rows + a, b - a, n, v.kptr, v.kcol, v.kvi, v.kval, v.kfv, x, lo, hi, rhs,
+                               out, v.pid, sc, skip);
 }
 
 // ------------------------------------------------------------------ residuals
@@ -462,8 +464,9 @@ __global__ void k_set_from(ChunkGrid g, double* __restrict__ dst, const T* __res
 // reduced ||r||_inf by less than stop_ratio (the last correction is kept).  A
 // step that made ||r||_inf larger is undone (k_ir_revert) and ends the
 // refinement: the regularised factor is not a contraction for K there.
-// A refinement that ends above fail_tol (or NaN) marks the iteration
-// (ir_fail): with a low-precision factor it is then redone in FP64.
+// A refinement that ends above fail_tol marks the iteration (ir_fail = 1; 2 if
+// the residual is not finite): with a low-precision factor it is then redone in
+// FP64; in FP64 a non-finite solve stops the solve at the current iterate.
 __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double stop_ratio, int max_steps) {
   const double r = bitsd(q.rnorm_bits);
   q.rnorm_bits = 0ull;
@@ -473,14 +476,14 @@ __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double st
   if (r > q.ir_prev) {
     q.ir_revert = 1;
     q.ir_skip = 1;
-    if (!(q.ir_prev <= fail_tol)) q.ir_fail = 1;
+    if (!(q.ir_prev <= fail_tol)) q.ir_fail = max(q.ir_fail, isfinite(q.ir_prev) ? 1 : 2);
     return false;
   }
   const bool stalled = stop_ratio > 0 && r <= fail_tol && !(r * stop_ratio < q.ir_prev);
   q.ir_prev = r;
   if (!(r > abstol + reltol * q.rhs_norm) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
     q.ir_skip = 1;
-    if (!(r <= fail_tol)) q.ir_fail = 1;
+    if (!(r <= fail_tol)) q.ir_fail = max(q.ir_fail, isfinite(r) ? 1 : 2);  // 2: a non-finite solve
     return false;
   }
   q.ir_cur += 1;
@@ -679,16 +682,17 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
-      if (q.ir_fail) {
+      if (q.ir_fail && sp.escalate_on) {
         q.alpha_c = 0.0;
-        if (sp.escalate_on) {
-          q.escalate = 1;  // redo the iteration with the FP64 factor
-        } else {
-          // a KKT solve of this iteration stayed above the acceptance bar (or gave a
-          // NaN) even in FP64: stop at the current, finite iterate
-          q.status = CLR_NUMERICAL_ERROR;
-          halt_problem(q, bf);
-        }
+        q.escalate = 1;  // redo the iteration with the FP64 factor
+        continue;
+      }
+      if (q.ir_fail == 2) {
+        // a KKT solve of this iteration gave a non-finite value even in FP64: stop at
+        // the current, finite iterate
+        q.alpha_c = 0.0;
+        q.status = CLR_NUMERICAL_ERROR;
+        halt_problem(q, bf);
         continue;
       }
       q.alpha_c = a;
@@ -1024,6 +1028,14 @@ int Solver::upload() {
     v_.kptr = ar_.upload(cnt.data(), N + 1);
     v_.kcol = ar_.upload(col.data(), (int64_t)col.size());
     v_.kvi = ar_.upload(vi.data(), (int64_t)vi.size());
+    {
+      // the x rows' values in full-CSR order (P and A are constant through the solve):
+      // contiguous loads instead of gathers through the value index
+      std::vector<double> fv(cnt[hp.n], 0.0);
+      for (int64_t p = 0; p < cnt[hp.n]; ++p) fv[p] = hp.kval[vi[p]];
+      v_.kfv = fv.empty() ? nullptr : ar_.upload(fv.data(), (int64_t)fv.size());
+      if (!fv.empty() && !v_.kfv) return CLR_E_OOM;
+    }
     const double avg = N ? (double)cnt[N] / (double)N : 1.0;
     csr_group_ = avg > 24 ? 32 : (avg > 12 ? 16 : (avg > 6 ? 8 : 4));
   }
@@ -1192,10 +1204,10 @@ int Solver::kkt_solve(const double* rhs, double* sol) {
   const int kg = grid_for(N * G, 256, 16 * kSMs);
   auto residual = [&](cudaStream_t ss) {
     switch (G) {
-      case 32: k_kmv<32><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
-      case 16: k_kmv<16><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
-      case 8: k_kmv<8><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
-      default: k_kmv<4><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      case 32: k_kmv<32><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, v_.kfv, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      case 16: k_kmv<16><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, v_.kfv, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      case 8: k_kmv<8><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, v_.kfv, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
+      default: k_kmv<4><<<kg, 256, 0, ss>>>(1, 0, N, hp.n, v_.kptr, v_.kcol, v_.kvi, v_.kval, v_.kfv, sol, nullptr, nullptr, rhs, v_.r, v_.pid, sc_, irs); break;
     }
     kmv_long(ss, 1, 0, N, hp.n, v_, h_long_, sol, nullptr, nullptr, rhs, v_.r, sc_, irs);
   };
@@ -1260,7 +1272,8 @@ template <int G>
 void launch_kmv_split(cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v, const double* x,
                       double* lo, double* hi, const double* rhs, double* out, IterScal* sc, const int* skip) {
   const int kg = grid_for((r1 - r0) * G, 256, 16 * kSMs);
-  k_kmv<G><<<kg, 256, 0, s>>>(mode, r0, r1, n, v.kptr, v.kcol, v.kvi, v.kval, x, lo, hi, rhs, out, v.pid, sc, skip);
+  k_kmv<G><<<kg, 256, 0, s>>>(mode, r0, r1, n, v.kptr, v.kcol, v.kvi, v.kval, v.kfv, x, lo, hi, rhs, out, v.pid, sc,
+                              skip);
 }
 void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, const VecDev& v,
          const std::vector<int64_t>& h_long, const double* x, double* lo, double* hi, const double* rhs, double* out,

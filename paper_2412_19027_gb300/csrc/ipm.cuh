@@ -19,6 +19,7 @@ namespace clr {
 
 struct VecDev {
   const int64_t* long_rows = nullptr;  // KKT rows with more than kLongRow entries (sorted)
+  const double* kfv = nullptr;         // values of the x rows of the full KKT CSR (constant), CSR order
   int64_t nlong = 0;
   double *xz, *s;            // iterate: [x; z] (N), s (m)
   double *lo, *hi;           // split K products (N each)

@@ -72,7 +72,11 @@ MIXED_CONES = ([(C.NONNEG, 7, 0.0), (C.SOC, 5, 0.0), (C.EXP, 3, 0.0), (C.ZERO, 2
 PSD_CONES = [(C.PSD, 55, 0.0)] * 3 + [(C.NONNEG, 4, 0.0)]
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4], ids=["mixed", "psd10", "psd3"])
+PSD32_CONES = [(C.PSD, 528, 0.0)] * 2 + [(C.NONNEG, 3, 0.0)]
+
+
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4, PSD32_CONES],
+                         ids=["mixed", "psd10", "psd3", "psd32"])
 def test_cone_scaling_matches_oracle(cones):
     rng = np.random.default_rng(0)
     s, z = _rand_cone_points(rng, cones)
@@ -91,7 +95,7 @@ def test_cone_scaling_matches_oracle(cones):
         off += d
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES], ids=["mixed", "psd10"])
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, PSD32_CONES], ids=["mixed", "psd10", "psd32"])
 def test_step_length_matches_oracle(cones):
     rng = np.random.default_rng(1)
     for trial in range(5):
@@ -122,7 +126,7 @@ def test_step_length_matches_oracle(cones):
         assert got == pytest.approx(alpha, rel=1e-9)
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES], ids=["mixed", "psd10"])
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, PSD32_CONES], ids=["mixed", "psd10", "psd32"])
 def test_combined_ds_matches_oracle(cones):
     rng = np.random.default_rng(2)
     s, z = _rand_cone_points(rng, cones)
