@@ -362,14 +362,14 @@ __global__ void __launch_bounds__(NT, 2)
   __shared__ int s_go;
   int* head = state + head_off;
   const int tid = threadIdx.x;
-  int next = 0;
-  if (tid == 0) next = atomicAdd(head, 1);
   for (;;) {
     if (tid == 0) {
-      const int cur = next;
+      // The next ticket is taken only once this CTA is free: a ticket reserved
+      // while the current task still waits for its inputs would be held back
+      // for the whole wait, although another CTA could run it at once.
+      const int cur = atomicAdd(head, 1);
       int go = 0;
       if (cur < nt) {
-        next = atomicAdd(head, 1);  // the following ticket, fetched while this task runs
         const FlowTask tk = task[t0 + cur];
         s_task = tk;
         const int64_t b = tk.bf;
