@@ -38,47 +38,51 @@ __device__ __forceinline__ double diag_rcp(double x) { return __drcp_rn(x); }
 // Warp-level LDL^T of the w x w (w <= 16) diagonal sub-block at (c0, c0) of A:
 // lane r keeps row r in registers; column k comes by shuffles.  Writes L (pivots
 // on the diagonal) back into A, the pivots and their reciprocals to sh, and the
-// scaled rows l_rc d_c (c < r) into the same place of W.
+// scaled rows l_rc d_c (c < r) into the same place of W.  The pivot loop has no
+// branches: rows and pivots past w are padded with the identity (pivot 1, no
+// multipliers), so the whole loop is one block the compiler can schedule across
+// pivots; the expected signs come in as one bit mask.
 template <typename T>
 __device__ __forceinline__ void diag_sub16(T* A, T* W, int c0, int w, DiagScratch<T>& sh, T eps, T delta,
                                            int& nhit) {
   constexpr int LDD = kDiagLD;
   constexpr unsigned FULL = 0xffffffffu;
   const int r = threadIdx.x & 31;
-  T v[16], dd[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) v[c] = (r < w && c <= r) ? A[(c0 + r) * LDD + c0 + c] : (T)0;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    dd[k] = (T)1;
-    if (k < w) {
-      T col[16];
-#pragma unroll
-      for (int c = k; c < 16; ++c) col[c] = __shfl_sync(FULL, v[k], c);  // a_ck, held by lane c
-      T d = col[k];
-      const T sg = (T)sh.sgn[c0 + k];
-      if (sg * d <= eps) {
-        d = sg * delta;
-        ++nhit;
-      }
-      const T inv = diag_rcp(d);
-      const T lik = (r > k && r < w) ? v[k] * inv : (T)0;
-#pragma unroll
-      for (int c = k + 1; c < 16; ++c) v[c] = (c <= r) ? v[c] - lik * col[c] : v[c];
-      v[k] = (r == k) ? d : ((r > k) ? lik : v[k]);
-      dd[k] = d;
-      if (r == 0) {
-        sh.dv[c0 + k] = d;
-        sh.dinv[c0 + k] = inv;
-      }
-    }
-  }
+  const unsigned neg = __ballot_sync(FULL, r < 16 && sh.sgn[c0 + r] < 0);
+  T v[16], dd[16], di[16];
 #pragma unroll
   for (int c = 0; c < 16; ++c)
+    v[c] = (r < w && c <= r) ? A[(c0 + r) * LDD + c0 + c] : ((c == r) ? (T)1 : (T)0);
+  int hits = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    T col[16];
+#pragma unroll
+    for (int c = k; c < 16; ++c) col[c] = __shfl_sync(FULL, v[k], c);  // a_ck, held by lane c
+    const T sg = ((neg >> k) & 1u) ? (T)-1 : (T)1;
+    const bool bad = sg * col[k] <= eps;
+    const T d = bad ? sg * delta : col[k];
+    hits += bad ? 1 : 0;
+    const T inv = diag_rcp(d);
+    const T lik = (r > k) ? v[k] * inv : (T)0;
+#pragma unroll
+    for (int c = k + 1; c < 16; ++c) v[c] = (c <= r) ? v[c] - lik * col[c] : v[c];
+    v[k] = (r == k) ? d : ((r > k) ? lik : v[k]);
+    dd[k] = d;
+    di[k] = inv;
+  }
+  nhit += hits;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
     if (r < w && c <= r) {
       A[(c0 + r) * LDD + c0 + c] = v[c];
       if (c < r) W[(c0 + r) * LDD + c0 + c] = v[c] * dd[c];
     }
+    if (r == 0 && c < w) {
+      sh.dv[c0 + c] = dd[c];
+      sh.dinv[c0 + c] = di[c];
+    }
+  }
 }
 
 // G: the block (column-major, leading dimension f, lower triangle read).

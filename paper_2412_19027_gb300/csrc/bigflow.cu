@@ -21,6 +21,11 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -106,24 +111,36 @@ __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
 template <typename T>
 __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T* F, T* E, T* Dp, const int8_t* dsign,
                        T eps, T delta, T* sm, DiagScratch<T>& sh, T* dl, int* trsm_word) {
-  T* Ls = sm;               // Linv of panel p - 1; work space of the factorization afterwards
-  T* Xs = sm + NB * LD;     // F_{p,p-1}, then L_{p,p-1}
-  T* A = sm + 2 * NB * LD;  // the diagonal tile (p, p), lower triangle
+  T* Bk = sm;                // K-major Linv of panel p - 1 (row j, k = l); work space of the factorization afterwards
+  T* Xk = sm + NB * LDK;     // K-major F_{p,p-1} (row i, k = l), then L_{p,p-1}
+  T* A = sm + 2 * NB * LDK;  // the diagonal tile (p, p), lower triangle, row stride LD
   const int64_t f = g.f, kq = (int64_t)(p - 1) * NB, k0 = (int64_t)p * NB;
   const int pw = bnrow(g, p);  // panel p - 1 is a full 64-column panel (p - 1 < P - 1)
   T* G = F + bf.goff[b];
   T* Eb = E + bf.eoff[b];
   const int tid = threadIdx.x;
+  {  // all loads in one batch, then into shared memory
+    T ra[16], rb[16], rc[16];
 #pragma unroll
-  for (int idx = tid; idx < NB * NB; idx += NT) {
-    const int i = idx % NB, j = idx / NB;
-    Ls[i * LD + j] = __ldcg(Eb + (kq + i) + (kq + j) * f);
-    Xs[i * LD + j] = (i < pw) ? __ldcg(G + (k0 + i) + (kq + j) * f) : (T)0;
-    A[i * LD + j] = (i < pw && j < pw && i >= j) ? __ldcg(G + (k0 + i) + (k0 + j) * f) : (T)0;
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      const int i = idx % NB, l = idx / NB;
+      ra[it] = __ldcg(Eb + (kq + i) + (kq + l) * f);
+      rb[it] = (i < pw) ? __ldcg(G + (k0 + i) + (kq + l) * f) : (T)0;
+      rc[it] = (i < pw && l < pw && i >= l) ? __ldcg(G + (k0 + i) + (k0 + l) * f) : (T)0;
+    }
+    if (tid < NB) dl[tid] = __ldcg(Dp + bf.k0pos[b] + kq + tid);
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      const int i = idx % NB, l = idx / NB;
+      Bk[swz(l, i)] = ra[it];
+      Xk[swz(l, i)] = rb[it];
+      A[i * LD + l] = rc[it];
+    }
   }
-  if (tid < NB) dl[tid] = __ldcg(Dp + bf.k0pos[b] + kq + tid);
   __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;
+  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -131,10 +148,8 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
   for (int l = 0; l < NB; ++l) {
     T av[4], bv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = Xs[(tr + 16 * a) * LD + l];
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) bv[bb] = Ls[(tc + 16 * bb) * LD + l];
+    ld4<T>(Xk + swz(l, 4 * tr), av);
+    ld4<T>(Bk + swz(l, 4 * tc), bv);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -143,14 +158,18 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
   __syncthreads();  // every thread has read F_{p,p-1}
 #pragma unroll
   for (int bb = 0; bb < 4; ++bb) {
-    const int j = tc + 16 * bb;
+    const int j = 4 * tc + bb;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const int i = tr + 16 * a;
-      const T v = (i < pw) ? acc[a][bb] / dl[j] : (T)0;
-      Xs[i * LD + j] = v;
-      if (i < pw) G[(k0 + i) + (kq + j) * f] = v;
+      const int i = 4 * tr + a;
+      Xk[swz(j, i)] = (i < pw) ? acc[a][bb] / dl[j] : (T)0;
     }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int idx = tid; idx < NB * NB; idx += NT) {
+    const int i = idx % NB, j = idx / NB;
+    if (i < pw) G[(k0 + i) + (kq + j) * f] = Xk[swz(j, i)];
   }
   __syncthreads();
   if (tid == 0) {
@@ -164,10 +183,11 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
   for (int l = 0; l < NB; ++l) {
     T av[4], bv[4];
+    ld4<T>(Xk + swz(l, 4 * tr), av);
+    ld4<T>(Xk + swz(l, 4 * tc), bv);
+    const T dlv = dl[l];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = Xs[(tr + 16 * a) * LD + l];
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) bv[bb] = Xs[(tc + 16 * bb) * LD + l] * dl[l];
+    for (int bb = 0; bb < 4; ++bb) bv[bb] *= dlv;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -175,16 +195,16 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
   }
 #pragma unroll
   for (int bb = 0; bb < 4; ++bb) {
-    const int j = tc + 16 * bb;
+    const int j = 4 * tc + bb;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const int i = tr + 16 * a;
+      const int i = 4 * tr + a;
       if (i < pw && i >= j) A[i * LD + j] -= acc[a][bb];
     }
   }
   __syncthreads();
   const int64_t kp = bf.k0pos[b] + k0;
-  return bf_diag_factor<T>(A, Ls, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp, eps, delta,
+  return bf_diag_factor<T>(A, Bk, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp, eps, delta,
                            sh);
 }
 
@@ -192,8 +212,8 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
 template <typename T>
 __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, T* F, const T* E,
                           const T* Dp, T* sm, T* dl) {
-  T* Ls = sm;            // Linv
-  T* Xs = sm + NB * LD;  // F_IK
+  T* Bk = sm;             // K-major Linv (row j, k = l)
+  T* Xk = sm + NB * LDK;  // K-major F_IK (row i, k = l), then L_IK (row i, k = j)
   const int64_t f = g.f, k0 = (int64_t)p * NB;
   const int pw = bnrow(g, p);
   const int64_t r0 = brow0(g, bi);
@@ -201,15 +221,26 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
   T* G = F + bf.goff[b];
   const T* Eb = E + bf.eoff[b];
   const int tid = threadIdx.x;
+  {  // all loads in one batch, then into shared memory
+    T ra[16], rb[16];
 #pragma unroll
-  for (int idx = tid; idx < NB * NB; idx += NT) {
-    const int i = idx % NB, j = idx / NB;
-    Ls[i * LD + j] = (i < pw && j < pw) ? __ldcg(Eb + (k0 + i) + (k0 + j) * f) : (T)0;
-    Xs[i * LD + j] = (i < nr && j < pw) ? __ldcg(G + (r0 + i) + (k0 + j) * f) : (T)0;
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      const int i = idx % NB, l = idx / NB;
+      ra[it] = (i < pw && l < pw) ? __ldcg(Eb + (k0 + i) + (k0 + l) * f) : (T)0;
+      rb[it] = (i < nr && l < pw) ? __ldcg(G + (r0 + i) + (k0 + l) * f) : (T)0;
+    }
+    if (tid < pw) dl[tid] = __ldcg(Dp + bf.k0pos[b] + k0 + tid);
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      const int i = idx % NB, l = idx / NB;
+      Bk[swz(l, i)] = ra[it];
+      Xk[swz(l, i)] = rb[it];
+    }
   }
-  if (tid < pw) dl[tid] = __ldcg(Dp + bf.k0pos[b] + k0 + tid);
   __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;
+  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -217,24 +248,28 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
     for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
   for (int l = 0; l < pw; ++l) {
     T av[4], bv[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) av[a] = Xs[(tr + 16 * a) * LD + l];
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) bv[bb] = Ls[(tc + 16 * bb) * LD + l];
+    ld4<T>(Xk + swz(l, 4 * tr), av);
+    ld4<T>(Bk + swz(l, 4 * tc), bv);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
   }
+  __syncthreads();  // every thread has read F_IK
 #pragma unroll
   for (int bb = 0; bb < 4; ++bb) {
-    const int j = tc + 16 * bb;
-    if (j >= pw) continue;
+    const int j = 4 * tc + bb;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      const int i = tr + 16 * a;
-      if (i < nr) G[(r0 + i) + (k0 + j) * f] = acc[a][bb] / dl[j];
+      const int i = 4 * tr + a;
+      if (j < pw) Xk[swz(j, i)] = acc[a][bb] / dl[j];
     }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int idx = tid; idx < NB * NB; idx += NT) {
+    const int i = idx % NB, j = idx / NB;
+    if (i < nr && j < pw) G[(r0 + i) + (k0 + j) * f] = Xk[swz(j, i)];
   }
 }
 
@@ -284,7 +319,7 @@ __device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
 // EU(p, i, e): E_IC -= L_IK E_KC.  4 x 4 outputs per thread from K-major tiles.
 template <typename T>
 __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, int64_t bj,
-                            bool etile, T* F, T* E, const T* Dp, T* sm) {
+                            bool etile, T* F, T* E, const T* Dp, T* sm, T* dl) {
   T* Ak = sm;
   T* Bk = sm + NB * LDK;
   const int64_t f = g.f, k0 = (int64_t)p * NB;
@@ -293,33 +328,48 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
   const int ni = bnrow(g, bi);
   T* G = F + bf.goff[b];
   T* Eb = E + bf.eoff[b];
-  const T* Dk = Dp + bf.k0pos[b] + k0;
   const int tid = threadIdx.x;
-  int64_t c0;
-  int nc;
-  if (!etile) {
-    c0 = brow0(g, bj);
-    nc = bnrow(g, bj);
+  const int64_t c0 = etile ? bj * NB : brow0(g, bj);
+  const int nc = bnrow(g, bj);
+  const bool diag = !etile && bi == bj;
+  T* base = etile ? Eb : G;
+  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
+  // every global load of the task in one batch: both operand tiles, the pivots
+  // and this thread's 4 x 4 outputs of the target tile (its inputs are complete
+  // once the task runs), so the task pays one round trip to L2
+  T ra[16], rb[16], tv[4][4];
 #pragma unroll
-    for (int idx = tid; idx < NB * NB; idx += NT) {
-      const int r = idx % NB, k = idx / NB;
-      Ak[swz(k, r)] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
-      Bk[swz(k, r)] = (k < pw && r < nc) ? __ldcg(G + (c0 + r) + (k0 + k) * f) * __ldcg(Dk + k) : (T)0;
-    }
-  } else {
-    c0 = bj * NB;
-    nc = bnrow(g, bj);
+  for (int it = 0; it < 16; ++it) {
+    const int idx = tid + NT * it;
+    const int r = idx % NB, k = idx / NB;
+    ra[it] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
+    if (!etile)
+      rb[it] = (k < pw && r < nc) ? __ldcg(G + (c0 + r) + (k0 + k) * f) : (T)0;
+    else  // E_KC: consecutive threads read consecutive rows k0 + kk of column c0 + cc
+      rb[it] = (r < pw && k < nc) ? __ldcg(Eb + (k0 + r) + (c0 + k) * f) : (T)0;
+  }
 #pragma unroll
-    for (int idx = tid; idx < NB * NB; idx += NT) {
-      const int r = idx % NB, k = idx / NB;
-      Ak[swz(k, r)] = (k < pw && r < ni) ? __ldcg(G + (i0 + r) + (k0 + k) * f) : (T)0;
-      // E_KC: consecutive threads read consecutive rows k0 + kk of column c0 + cc
-      const int kk = idx % NB, cc = idx / NB;
-      Bk[swz(kk, cc)] = (kk < pw && cc < nc) ? __ldcg(Eb + (k0 + kk) + (c0 + cc) * f) : (T)0;
+  for (int bb = 0; bb < 4; ++bb) {
+    const int cc = 4 * tc + bb;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = 4 * tr + a;
+      tv[a][bb] = (r < ni && cc < nc && (!diag || r >= cc)) ? __ldcg(base + (i0 + r) + (c0 + cc) * f) : (T)0;
     }
   }
+  if (!etile && tid < NB) dl[tid] = tid < pw ? __ldcg(Dp + bf.k0pos[b] + k0 + tid) : (T)0;
+  if (!etile) __syncthreads();
+#pragma unroll
+  for (int it = 0; it < 16; ++it) {
+    const int idx = tid + NT * it;
+    const int r = idx % NB, k = idx / NB;
+    Ak[swz(k, r)] = ra[it];
+    if (!etile)
+      Bk[swz(k, r)] = rb[it] * dl[k];
+    else
+      Bk[swz(r, k)] = rb[it];
+  }
   __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -334,8 +384,6 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
 #pragma unroll
       for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
   }
-  const bool diag = !etile && bi == bj;
-  T* base = etile ? Eb : G;
 #pragma unroll
   for (int bb = 0; bb < 4; ++bb) {
     const int cc = 4 * tc + bb;
@@ -343,7 +391,7 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int r = 4 * tr + a;
-      if (r < ni && (!diag || r >= cc)) base[(i0 + r) + (c0 + cc) * f] -= acc[a][bb];
+      if (r < ni && (!diag || r >= cc)) base[(i0 + r) + (c0 + cc) * f] = tv[a][bb] - acc[a][bb];
     }
   }
 }
@@ -376,31 +424,58 @@ __global__ void __launch_bounds__(NT, 2)
         const Geo g{bf.f[b], bf.c[b], (bf.c[b] + NB - 1) / NB, flow_nbf(bf.f[b], bf.c[b])};
         const Words w = words_of(state + soff[b], g);
         const int p = tk.p;
-        bool ok;
+        // the version words this task reads and the versions it needs
+        const int* wp[3];
+        int wv[3];
+        int nw;
         switch (tk.kind) {
           case 0:
-            ok = wait_ge(w.t(p, p), p, err);
+            wp[0] = w.t(p, p), wv[0] = p;
+            nw = 1;
             break;
           case 5:
-            ok = wait_ge(w.diag + p - 1, 1, err) && wait_ge(w.t(p, p - 1), p - 1, err) &&
-                 wait_ge(w.t(p, p), p - 1, err);
+            wp[0] = w.diag + p - 1, wv[0] = 1;
+            wp[1] = w.t(p, p - 1), wv[1] = p - 1;
+            wp[2] = w.t(p, p), wv[2] = p - 1;
+            nw = 3;
             break;
           case 1:
-            ok = wait_ge(w.diag + p, 1, err) && wait_ge(w.t(tk.i, p), p, err);
+            wp[0] = w.diag + p, wv[0] = 1;
+            wp[1] = w.t(tk.i, p), wv[1] = p;
+            nw = 2;
             break;
           case 2:
-            ok = wait_ge(w.diag + p, 1, err) && wait_ge(w.e(p, tk.j), p - tk.j, err);
+            wp[0] = w.diag + p, wv[0] = 1;
+            wp[1] = w.e(p, tk.j), wv[1] = p - tk.j;
+            nw = 2;
             break;
           case 3:
-            ok = wait_ge(w.trsm + tk.i, p + 1, err) && wait_ge(w.trsm + tk.j, p + 1, err) &&
-                 wait_ge(w.t(tk.i, tk.j), p, err);
+            wp[0] = w.trsm + tk.i, wv[0] = p + 1;
+            wp[1] = w.trsm + tk.j, wv[1] = p + 1;
+            wp[2] = w.t(tk.i, tk.j), wv[2] = p;
+            nw = 3;
             break;
           default:
-            ok = wait_ge(w.trsm + tk.i, p + 1, err) &&
-                 (tk.j < p ? wait_ge(w.e(p, tk.j), p - tk.j + 1, err) : wait_ge(w.diag + p, 1, err)) &&
-                 wait_ge(w.e(tk.i, tk.j), p - tk.j, err);
+            wp[0] = w.trsm + tk.i, wv[0] = p + 1;
+            if (tk.j < p)
+              wp[1] = w.e(p, tk.j), wv[1] = p - tk.j + 1;
+            else
+              wp[1] = w.diag + p, wv[1] = 1;
+            wp[2] = w.e(tk.i, tk.j), wv[2] = p - tk.j;
+            nw = 3;
             break;
         }
+        // one round trip when the inputs are already there (the loads are issued
+        // together; the fence below orders them before the task's reads), else
+        // bounded waits word by word
+        int got[3] = {0, 0, 0};
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (q < nw) got[q] = ld_relaxed(wp[q]);
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (q < nw && got[q] < wv[q]) ok = ok && wait_ge(wp[q], wv[q], err);
         go = ok ? 1 : 0;
         if (ok) __threadfence();
       }
@@ -428,10 +503,10 @@ __global__ void __launch_bounds__(NT, 2)
         task_efin<T>(bf, b, g, tk.p, tk.j, E, sm);
         break;
       case 3:
-        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, false, F, E, Dp, sm);
+        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, false, F, E, Dp, sm, dl);
         break;
       default:
-        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, true, F, E, Dp, sm);
+        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, true, F, E, Dp, sm, dl);
         break;
     }
     __syncthreads();
@@ -466,9 +541,9 @@ __global__ void __launch_bounds__(NT, 2)
 
 template <typename T>
 size_t flow_smem() {  // the fused chain task's three blocks; the others need less
-  static_assert(3 * NB * LD >= kDiagSmem && 3 * NB * LD >= 2 * NB * LDK && LD == kDiagLD,
-                "shared memory of the flow tasks");
-  return 3 * NB * LD * sizeof(T);
+  constexpr int n = 2 * NB * LDK + NB * LD;
+  static_assert(n >= kDiagSmem && NB * LDK >= NB * kDiagLD && LD == kDiagLD, "shared memory of the flow tasks");
+  return n * sizeof(T);
 }
 }  // namespace
 

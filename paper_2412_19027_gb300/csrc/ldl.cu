@@ -236,23 +236,33 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
 }
 }  // namespace
 
-// Order the tasks [t0, end) of one level for the counter of k_bf_flow: the
-// dependency graph has the edges of the kernel's waits; Kahn's algorithm takes,
-// among the tasks whose predecessors are all placed, the one with the largest
-// bottom level (longest path to the end, each task weighted by its typical
-// duration), so the chains that bound the factorization -- the diagonal tasks
-// and the successive updates of one tile -- are handed out early and the bulk of
-// the updates fills the CTAs around them.  Returns false if the graph has a
-// cycle (a bug: the caller then fails the setup).
+// Order the tasks [t0, end) of one level for the counter of k_bf_flow.  A CTA
+// takes the next ticket as soon as it is free and then waits until the task's
+// inputs are there, so a ticket handed out long before its task can run keeps a
+// CTA idle.  The order is therefore that of a list schedule simulated on the
+// host: `workers` CTAs, each task taking its typical duration (FP32 times per
+// kind measured on a GB300, 64 x 64 tiles) plus a notification delay after each
+// input; a free CTA starts, among the tasks whose inputs are done, the one with
+// the largest bottom level (longest weighted path to the end), and the tickets
+// follow the simulated start times.  The fused chain task DX(p) publishes the L
+// rows of block p early (its trsm word), so the updates that only read those
+// rows count from that point.  Start times never decrease along the order and
+// each task starts after its inputs finish, so the order is topological: every
+// wait is for a smaller ticket.  Returns false if the graph has a cycle (a bug:
+// the caller then fails the setup).
 //   deps: D(0) -; DX(p) D/DX(p-1), U(p-2, p, p-1), U(p-2, p, p);
 //   T(p, i) D/DX(p), U(p-1, i, p); Efin(p, e) D/DX(p), EU(p-1, p, e);
 //   U(p, i, j) T~(p, i), T~(p, j), U(p-1, i, j);
 //   EU(p, i, e) T~(p, i), Efin(p, e) or D/DX(p) (e = p), EU(p-1, i, e);
 // T~(p, i) is DX(p+1) when i = p + 1 is a pivot block (folded), else T(p, i).
-static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0,
-                                const std::vector<int64_t>& P_of) {
+static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0, const std::vector<int64_t>& P_of,
+                                int workers) {
   const int64_t n = (int64_t)tasks.size() - t0;
   if (n <= 1) return true;
+  // typical durations (microseconds) by kind: D, T, Efin, U, EU, DX; DX
+  // publishes its L rows this long after it starts; delay of a notification
+  static const double dur[6] = {25.0, 7.5, 6.0, 12.0, 10.0, 31.0};
+  const double kMid = 6.0, kLat = 2.5;
   auto key = [](int64_t b, int kind, int64_t p, int64_t i, int64_t j) -> uint64_t {
     return ((uint64_t)b << 43) ^ ((uint64_t)kind << 40) ^ ((uint64_t)p << 28) ^ ((uint64_t)i << 14) ^ (uint64_t)j;
   };
@@ -267,14 +277,18 @@ static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0,
     return it == idx.end() ? -1 : it->second;
   };
   auto dd = [&](int64_t b, int64_t p) { return p == 0 ? find(b, 0, 0, 0, 0) : find(b, 5, p, p, p); };
-  auto tt = [&](int64_t b, int64_t p, int64_t i) {
-    return (i == p + 1 && i < P_of[b]) ? find(b, 5, i, i, i) : find(b, 1, p, i, p);
+  auto folded = [&](int64_t b, int64_t p, int64_t i) { return i == p + 1 && i < P_of[b]; };
+  auto tt = [&](int64_t b, int64_t p, int64_t i) { return folded(b, p, i) ? find(b, 5, i, i, i) : find(b, 1, p, i, p); };
+  struct Edge {
+    int64_t to;
+    bool mid;  // the successor needs only the early-published rows of a DX task
   };
-  std::vector<std::vector<int64_t>> succ(n);
+  std::vector<std::vector<Edge>> succ(n);
   std::vector<int> indeg(n, 0);
   for (int64_t t = 0; t < n; ++t) {
     const FlowTask& k = tasks[t0 + t];
     int64_t d[3] = {-1, -1, -1};
+    bool mid[3] = {false, false, false};
     const int64_t p = k.p, i = k.i, j = k.j, b = k.bf;
     switch (k.kind) {
       case 0: break;
@@ -286,12 +300,12 @@ static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0,
       case 1: d[0] = dd(b, p); d[1] = p > 0 ? find(b, 3, p - 1, i, p) : -1; break;
       case 2: d[0] = dd(b, p); d[1] = p - 1 >= j ? find(b, 4, p - 1, p, j) : -1; break;
       case 3:
-        d[0] = tt(b, p, i);
-        d[1] = tt(b, p, j);
+        d[0] = tt(b, p, i), mid[0] = folded(b, p, i);
+        d[1] = tt(b, p, j), mid[1] = folded(b, p, j);
         d[2] = p > 0 ? find(b, 3, p - 1, i, j) : -1;
         break;
       default:
-        d[0] = tt(b, p, i);
+        d[0] = tt(b, p, i), mid[0] = folded(b, p, i);
         d[1] = j < p ? find(b, 2, p, p, j) : dd(b, p);
         d[2] = p - 1 >= j ? find(b, 4, p - 1, i, j) : -1;
         break;
@@ -301,7 +315,7 @@ static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0,
       bool dup = false;
       for (int r = 0; r < q; ++r) dup = dup || d[r] == d[q];
       if (dup) continue;
-      succ[d[q]].push_back(t);
+      succ[d[q]].push_back(Edge{t, mid[q]});
       ++indeg[t];
     }
   }
@@ -313,32 +327,50 @@ static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0,
     for (int64_t t = 0; t < n; ++t)
       if (deg[t] == 0) topo.push_back(t);
     for (size_t h = 0; h < topo.size(); ++h)
-      for (int64_t u : succ[topo[h]])
-        if (--deg[u] == 0) topo.push_back(u);
+      for (const Edge& e : succ[topo[h]])
+        if (--deg[e.to] == 0) topo.push_back(e.to);
   }
   if ((int64_t)topo.size() != n) return false;
-  std::vector<int64_t> bl(n, 0);
+  std::vector<double> bl(n, 0.0);
   for (int64_t h = n - 1; h >= 0; --h) {
     const int64_t t = topo[h];
-    int64_t m = 0;
-    for (int64_t u : succ[t]) m = std::max(m, bl[u]);
-    // weights: typical task times in microseconds on a GB300 (FP32, 64 x 64 tiles)
-    static const int64_t wt[6] = {30, 7, 6, 11, 11, 40};
-    bl[t] = m + wt[tasks[t0 + t].kind];
+    double m = 0.0;
+    for (const Edge& e : succ[t]) m = std::max(m, bl[e.to]);
+    bl[t] = m + dur[tasks[t0 + t].kind];
   }
-  std::priority_queue<std::pair<int64_t, int64_t>> ready;  // (bottom level, -index)
+  // the list schedule
+  using TimeTask = std::pair<double, int64_t>;
+  std::priority_queue<TimeTask, std::vector<TimeTask>, std::greater<TimeTask>> pending;  // (ready time, task)
+  std::priority_queue<std::pair<double, int64_t>> avail;                                 // (bottom level, -task)
+  std::priority_queue<double, std::vector<double>, std::greater<double>> cta;           // free times
+  for (int w = 0; w < std::max(1, workers); ++w) cta.push(0.0);
+  std::vector<double> ready(n, 0.0);
   for (int64_t t = 0; t < n; ++t)
-    if (indeg[t] == 0) ready.emplace(bl[t], -t);
+    if (indeg[t] == 0) pending.emplace(0.0, t);
   std::vector<FlowTask> out;
   out.reserve((size_t)n);
-  while (!ready.empty()) {
-    const int64_t t = -ready.top().second;
-    ready.pop();
+  while ((int64_t)out.size() < n) {
+    const double now = cta.top();
+    cta.pop();
+    while (!pending.empty() && pending.top().first <= now) {
+      avail.emplace(bl[pending.top().second], -pending.top().second);
+      pending.pop();
+    }
+    if (avail.empty()) {
+      if (pending.empty()) return false;
+      cta.push(pending.top().first);  // idle until the next task is ready
+      continue;
+    }
+    const int64_t t = -avail.top().second;
+    avail.pop();
     out.push_back(tasks[t0 + t]);
-    for (int64_t u : succ[t])
-      if (--indeg[u] == 0) ready.emplace(bl[u], -u);
+    const double fin = now + dur[tasks[t0 + t].kind];
+    cta.push(fin);
+    for (const Edge& e : succ[t]) {
+      ready[e.to] = std::max(ready[e.to], (e.mid ? now + kMid : fin) + kLat);
+      if (--indeg[e.to] == 0) pending.emplace(ready[e.to], e.to);
+    }
   }
-  if ((int64_t)out.size() != n) return false;
   std::copy(out.begin(), out.end(), tasks.begin() + t0);
   return true;
 }
@@ -518,6 +550,11 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
     // has the fused task DX(p) instead of D(p), T(p-1, p) and U(p-1, p, p).
     std::vector<FlowTask> tasks;
     std::vector<int64_t> soff(bf_f.size(), 0), P_of(bf_f.size(), 0);
+    // CTAs of one launch of k_bf_flow: two per SM (its occupancy for both precisions)
+    int flow_workers = 2 * 152, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        sms > 0)
+      flow_workers = 2 * sms;
     int64_t words = 0;
     st.flow_t0.assign(sy.nlev, 0);
     st.flow_nt.assign(sy.nlev, 0);
@@ -548,7 +585,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
         }
       }
       st.flow_nt[l] = (int64_t)tasks.size() - st.flow_t0[l];
-      if (!flow_priority_order(tasks, st.flow_t0[l], P_of)) return CLR_E_INVALID;
+      if (!flow_priority_order(tasks, st.flow_t0[l], P_of, flow_workers)) return CLR_E_INVALID;
     }
     st.flow_words = words;
     if (!tasks.empty()) {
