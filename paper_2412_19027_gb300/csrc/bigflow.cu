@@ -547,9 +547,15 @@ size_t flow_smem() {  // the fused chain task's three blocks; the others need le
 }
 }  // namespace
 
+// dynamic shared memory of a launch with one CTA per SM (more than half an SM's)
+template <typename T>
+size_t flow_smem_one() {
+  return flow_smem<T>() > (size_t)120 * 1024 ? flow_smem<T>() : (size_t)120 * 1024;
+}
+
 template <typename T>
 int BigFrontOps<T>::flow_occupancy() {
-  CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem<T>()));
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem_one<T>()));
   int n = 0;
   CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<T>, NT, flow_smem<T>()));
   return n > 0 ? n : 1;
@@ -557,12 +563,14 @@ int BigFrontOps<T>::flow_occupancy() {
 
 template <typename T>
 int BigFrontOps<T>::flow_level(cudaStream_t st, const BigFrontDev& bf, const FlowTask* task, int64_t t0, int64_t nt,
-                               int* state, int64_t head_off, const int64_t* soff, int grid, T* F, T* E, T* Dp,
-                               const int8_t* dsign, double eps, double delta, int* hits, int* err, const int* skip) {
+                               int* state, int64_t head_off, const int64_t* soff, int grid, bool one_per_sm, T* F,
+                               T* E, T* Dp, const int8_t* dsign, double eps, double delta, int* hits, int* err,
+                               const int* skip) {
   if (nt <= 0) return CLR_OK;
   const unsigned g = (unsigned)(nt < grid ? nt : grid);
-  k_bf_flow<T><<<g, NT, flow_smem<T>(), st>>>(bf, task, t0, nt, state, head_off, soff, F, E, Dp, dsign, eps, delta,
-                                              hits, err, skip);
+  const size_t smem = one_per_sm ? flow_smem_one<T>() : flow_smem<T>();
+  k_bf_flow<T><<<g, NT, smem, st>>>(bf, task, t0, nt, state, head_off, soff, F, E, Dp, dsign, eps, delta, hits, err,
+                                    skip);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -570,7 +578,8 @@ int BigFrontOps<T>::flow_level(cudaStream_t st, const BigFrontDev& bf, const Flo
 #define CLR_FLOW_INST(T)                                                                                         \
   template int BigFrontOps<T>::flow_occupancy();                                                                   \
   template int BigFrontOps<T>::flow_level(cudaStream_t, const BigFrontDev&, const FlowTask*, int64_t, int64_t, int*, \
-                                          int64_t, const int64_t*, int, T*, T*, T*, const int8_t*, double, double,   \
+                                          int64_t, const int64_t*, int, bool, T*, T*, T*, const int8_t*, double,     \
+                                          double,                                                                    \
                                           int*, int*, const int*);
 CLR_FLOW_INST(double)
 CLR_FLOW_INST(float)

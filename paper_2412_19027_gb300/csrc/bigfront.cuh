@@ -90,9 +90,10 @@ struct BigFrontOps {
   // Dataflow factorization of one level: tasks [t0, t0 + nt) of the task table;
   // state: zeroed words holding the level's task counter (at head_off) and, at
   // soff[b], the version words of each big front b of the level.  err: set to 2
-  // if a wait ran out (the factor is then unusable).
+  // if a wait ran out (the factor is then unusable).  one_per_sm: enough shared
+  // memory is requested that a single CTA fits on an SM.
   static int flow_level(cudaStream_t st, const BigFrontDev& bf, const FlowTask* task, int64_t t0, int64_t nt,
-                        int* state, int64_t head_off, const int64_t* soff, int grid, T* F, T* E, T* Dp,
+                        int* state, int64_t head_off, const int64_t* soff, int grid, bool one_per_sm, T* F, T* E, T* Dp,
                         const int8_t* dsign, double eps, double delta, int* hits, int* err, const int* skip);
   static int flow_occupancy();  // resident CTAs per SM of the flow kernel
 };

@@ -249,19 +249,22 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
 // rows count from that point.  Start times never decrease along the order and
 // each task starts after its inputs finish, so the order is topological: every
 // wait is for a smaller ticket.  Returns false if the graph has a cycle (a bug:
-// the caller then fails the setup).
+// the caller then fails the setup).  The caller schedules each level twice --
+// two CTAs per SM, or one CTA per SM whose tasks run faster without a second
+// CTA beside them -- and keeps the shorter.
 //   deps: D(0) -; DX(p) D/DX(p-1), U(p-2, p, p-1), U(p-2, p, p);
 //   T(p, i) D/DX(p), U(p-1, i, p); Efin(p, e) D/DX(p), EU(p-1, p, e);
 //   U(p, i, j) T~(p, i), T~(p, j), U(p-1, i, j);
 //   EU(p, i, e) T~(p, i), Efin(p, e) or D/DX(p) (e = p), EU(p-1, i, e);
 // T~(p, i) is DX(p+1) when i = p + 1 is a pivot block (folded), else T(p, i).
+// dur: typical durations (microseconds) by kind D, T, Efin, U, EU, DX; span: the
+// simulated duration of the level.
 static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0, const std::vector<int64_t>& P_of,
-                                int workers) {
+                                int workers, const double* dur, double* span) {
   const int64_t n = (int64_t)tasks.size() - t0;
+  *span = 0.0;
   if (n <= 1) return true;
-  // typical durations (microseconds) by kind: D, T, Efin, U, EU, DX; DX
-  // publishes its L rows this long after it starts; delay of a notification
-  static const double dur[6] = {25.0, 7.5, 6.0, 12.0, 10.0, 31.0};
+  // DX publishes its L rows this long after it starts; delay of a notification
   const double kMid = 6.0, kLat = 2.5;
   auto key = [](int64_t b, int kind, int64_t p, int64_t i, int64_t j) -> uint64_t {
     return ((uint64_t)b << 43) ^ ((uint64_t)kind << 40) ^ ((uint64_t)p << 28) ^ ((uint64_t)i << 14) ^ (uint64_t)j;
@@ -365,6 +368,7 @@ static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0, const 
     avail.pop();
     out.push_back(tasks[t0 + t]);
     const double fin = now + dur[tasks[t0 + t].kind];
+    *span = std::max(*span, fin);
     cta.push(fin);
     for (const Edge& e : succ[t]) {
       ready[e.to] = std::max(ready[e.to], (e.mid ? now + kMid : fin) + kLat);
@@ -550,11 +554,12 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
     // has the fused task DX(p) instead of D(p), T(p-1, p) and U(p-1, p, p).
     std::vector<FlowTask> tasks;
     std::vector<int64_t> soff(bf_f.size(), 0), P_of(bf_f.size(), 0);
-    // CTAs of one launch of k_bf_flow: two per SM (its occupancy for both precisions)
-    int flow_workers = 2 * 152, dev = 0, sms = 0;
+    // SMs of the device: a launch of k_bf_flow runs one or two CTAs on each
+    int flow_sms = 152, dev = 0, sms = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         sms > 0)
-      flow_workers = 2 * sms;
+      flow_sms = sms;
+    st.flow_one.assign(sy.nlev, 0);
     int64_t words = 0;
     st.flow_t0.assign(sy.nlev, 0);
     st.flow_nt.assign(sy.nlev, 0);
@@ -585,7 +590,17 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
         }
       }
       st.flow_nt[l] = (int64_t)tasks.size() - st.flow_t0[l];
-      if (!flow_priority_order(tasks, st.flow_t0[l], P_of, flow_workers)) return CLR_E_INVALID;
+      // FP32 task times (microseconds; D, T, Efin, U, EU, DX) measured on a GB300
+      // with two CTAs per SM and with one (no second CTA competing for the SM)
+      static const double dur2[6] = {22.0, 7.0, 5.5, 8.0, 8.0, 27.0};
+      static const double dur1[6] = {20.0, 6.5, 5.3, 5.8, 6.1, 25.0};
+      std::vector<FlowTask> one(tasks.begin() + st.flow_t0[l], tasks.end());
+      double span2 = 0.0, span1 = 0.0;
+      if (!flow_priority_order(tasks, st.flow_t0[l], P_of, 2 * flow_sms, dur2, &span2) ||
+          !flow_priority_order(one, 0, P_of, flow_sms, dur1, &span1))
+        return CLR_E_INVALID;
+      st.flow_one[l] = span1 < 0.97 * span2 ? 1 : 0;
+      if (st.flow_one[l]) std::copy(one.begin(), one.end(), tasks.begin() + st.flow_t0[l]);
     }
     st.flow_words = words;
     if (!tasks.empty()) {
@@ -645,7 +660,8 @@ int LdlFactor<T>::alloc(DeviceArena& ar, const LdlStructure& st) {
       return CLR_E_CUDA;
     const int occ = BigFrontOps<T>::flow_occupancy();
     if (occ < 0) return CLR_E_CUDA;
-    flow_grid = sms * occ;
+    flow_sms = sms;
+    flow_occ = occ;
   }
   static bool attr_set = false;
   if (!attr_set) {
@@ -685,7 +701,9 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
     }
     if (!S.lev_big[l].empty()) {
       int rc = use_flow ? BigFrontOps<T>::flow_level(stm, S.bfd, S.flow_task, S.flow_t0[l], S.flow_nt[l], flow_state,
-                                                     S.flow_head[l], S.flow_soff, flow_grid, F, E, Dp, S.dsign,
+                                                     S.flow_head[l], S.flow_soff,
+                                                     S.flow_one[l] ? flow_sms : flow_sms * flow_occ, S.flow_one[l] != 0,
+                                                     F, E, Dp, S.dsign,
                                                      dyn_eps, dyn_delta, dyn_hits, tc_err, skip)
                         : BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps,
                                                        dyn_delta, dyn_hits, skip, tc16, tc_err);

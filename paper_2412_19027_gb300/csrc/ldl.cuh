@@ -44,6 +44,7 @@ struct LdlStructure {
   FlowTask* flow_task = nullptr;
   int64_t* flow_soff = nullptr;
   std::vector<int64_t> flow_t0, flow_nt, flow_head;
+  std::vector<int8_t> flow_one;  // per level: launch one CTA per SM (else two)
   int64_t flow_words = 0;
   int small_max = 0;
   int64_t max_front = 0;
@@ -68,7 +69,7 @@ struct LdlFactor {
   bool tc16 = false;      // big-front updates with BF16 products on the tensor cores (float only)
   bool flow = true;       // big fronts by the dataflow kernel (one launch per level); else per-panel launches
   int* flow_state = nullptr;
-  int flow_grid = 0;
+  int flow_sms = 0, flow_occ = 0;  // SMs of the device, resident flow CTAs per SM
   int alloc(DeviceArena& ar, const LdlStructure& st);
   // Factor K: kval (FP64, lower triangle entries in kval order) scattered into
   // the fronts, +/- delta added on the diagonal (x rows +, z rows -), with
