@@ -203,7 +203,7 @@ int clr_analyze(clr_solver** out, const clr_csc* P_upper, const double* q, const
 /* Solve phase of Algorithm 1: initial point, then iterations until the
  * termination or infeasibility tests pass, max_iter is reached, or the step
  * length falls below min_step.  Blocking.  Each call starts from scratch
- * (data as set up, or as replaced by clr_update_qb). */
+ * (data as set up, or as replaced by clr_update_qb / clr_update_PA). */
 int clr_solve(clr_solver* s);
 
 /* Copy the result to host buffers (any may be NULL): x (n), s (m), z (m) in
@@ -217,6 +217,17 @@ int clr_get_solution(const clr_solver* s, double* x, double* sl, double* z, clr_
  * the cones and the symbolic analysis (parametric re-solve, Sec. 4.6).  The
  * equilibration computed at setup is kept.  CLR_E_INVALID on NaN/Inf. */
 int clr_update_qb(clr_solver* s, const double* q, const double* b);
+
+/* Replace the values of P and/or A, same sparsity patterns as at setup
+ * (parametric programming, Sec. 4.6: the coefficients change, the solver and
+ * its symbolic factorization are reused).  Px (host): nnz(P_upper) values in
+ * the CSC order of the P_upper given to setup; Ax (host): nnz(A) values in the
+ * CSC order of A.  Either may be NULL (kept).  An entry set to 0 stays in the
+ * pattern.  The equilibration computed at setup is kept and applied to the new
+ * values; the fill-reducing order, the supernodes and every device buffer are
+ * reused.  The next clr_solve starts from scratch on the new data.
+ * CLR_E_INVALID on NaN/Inf (nothing is changed then). */
+int clr_update_PA(clr_solver* s, const double* Px, const double* Ax);
 
 int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out);
 
@@ -266,6 +277,9 @@ int clr_batch_get(const clr_solver* s, int32_t i, double* x, double* sl, double*
 
 /* clr_update_qb for problem i of the cohort. */
 int clr_batch_update_qb(clr_solver* s, int32_t i, const double* q, const double* b);
+
+/* clr_update_PA for problem i of the cohort (its own P and A patterns). */
+int clr_batch_update_PA(clr_solver* s, int32_t i, const double* Px, const double* Ax);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  The paper has no

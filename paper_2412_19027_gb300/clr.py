@@ -94,6 +94,7 @@ class clr_perf(C.Structure):
 
 _LIB = None
 EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr_get_solution", "clr_update_qb",
+           "clr_update_PA", "clr_batch_update_PA",
            "clr_get_symbolic_stats", "clr_get_perf", "clr_get_symbolic", "clr_get_scaling", "clr_get_history", "clr_set_stream",
            "clr_set_allocator", "clr_free", "clr_error_string", "clr_status_string", "clr_last_cuda_error",
            "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_cones_time", "clr_ldl_solve",
@@ -117,6 +118,8 @@ def _lib():
         L.clr_solve.argtypes = [vp]
         L.clr_get_solution.argtypes = [vp, P(C.c_double), P(C.c_double), P(C.c_double), P(clr_info)]
         L.clr_update_qb.argtypes = [vp, P(C.c_double), P(C.c_double)]
+        L.clr_update_PA.argtypes = [vp, P(C.c_double), P(C.c_double)]
+        L.clr_batch_update_PA.argtypes = [vp, C.c_int32, P(C.c_double), P(C.c_double)]
         L.clr_get_symbolic_stats.argtypes = [vp, P(clr_symbolic_stats)]
         L.clr_get_perf.argtypes = [vp, P(clr_perf)]
         L.clr_get_symbolic.argtypes = [vp] + [P(C.c_int64)] * 7
@@ -185,6 +188,33 @@ def _csc(M, keep):
                    rowind.ctypes.data_as(C.POINTER(C.c_int32)), val.ctypes.data_as(C.POINTER(C.c_double)))
 
 
+def _values_on(M, pattern, upper, name):
+    """Values of M in the CSC order of `pattern` (indptr, indices) given to setup:
+    M is a 1-D array of nnz values, or a matrix with exactly that pattern."""
+    if M is None:
+        return None
+    if isinstance(M, np.ndarray) and M.ndim == 1:
+        v = np.ascontiguousarray(M, dtype=np.float64)
+    else:
+        M = sp.csc_matrix(M)
+        if upper and not _is_upper(M):
+            M = sp.csc_matrix(sp.triu(M))
+        M.sort_indices()
+        if not (np.array_equal(M.indptr, pattern[0]) and np.array_equal(M.indices, pattern[1])):
+            raise ValueError("%s: the sparsity pattern differs from the one given at setup" % name)
+        v = np.ascontiguousarray(M.data, dtype=np.float64)
+    if len(v) != len(pattern[1]):
+        raise ValueError("%s: %d values for a pattern of %d entries" % (name, len(v), len(pattern[1])))
+    return v
+
+
+def _pattern(c):
+    n = c.ncols
+    ptr = np.ctypeslib.as_array(c.colptr, shape=(n + 1,)).copy()
+    idx = np.ctypeslib.as_array(c.rowind, shape=(c.nnz,)).copy() if c.nnz else np.zeros(0, np.int32)
+    return ptr, idx
+
+
 def _cones(cones):
     arr = (clr_cone * max(len(cones), 1))()
     for i, (t, d, a) in enumerate(cones):
@@ -222,6 +252,7 @@ class Solver:
         _check(fn(C.byref(h), C.byref(Pc), _dptr(q), C.byref(Ac), _dptr(b), cz, len(cones), C.byref(st)),
                "clr_setup" if device else "clr_analyze")
         self.h = h
+        self.patterns = [(_pattern(Pc), _pattern(Ac))]
 
     def __del__(self):
         self.free()
@@ -254,6 +285,21 @@ class Solver:
         q = np.ascontiguousarray(q, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         _check(_lib().clr_update_qb(self.h, _dptr(q), _dptr(b)), "clr_update_qb")
+
+    def update_PA(self, P=None, A=None):
+        """New values of P (upper triangle) and/or A with the patterns given at
+        setup: each a matrix of that pattern or a 1-D array of its values in
+        CSC order; None keeps the current values."""
+        self._update_PA(0, P, A)
+
+    def _update_PA(self, i, P, A):
+        (pp, ap) = self.patterns[i]
+        Pv, Av = _values_on(P, pp, True, "P"), _values_on(A, ap, False, "A")
+        ptr = lambda v: None if v is None else _dptr(v)
+        if i == 0 and not isinstance(self, Batch):
+            _check(_lib().clr_update_PA(self.h, ptr(Pv), ptr(Av)), "clr_update_PA")
+        else:
+            _check(_lib().clr_batch_update_PA(self.h, i, ptr(Pv), ptr(Av)), "clr_batch_update_PA")
 
     def set_stream(self, stream_ptr):
         _check(_lib().clr_set_stream(self.h, C.c_void_p(stream_ptr)), "clr_set_stream")
@@ -313,6 +359,7 @@ class Batch(Solver):
         keep = []
         arr = (clr_problem * len(problems))()
         self.sizes = []
+        pats = []
         for i, (P, q, A, b, cones) in enumerate(problems):
             Pc = _csc(sp.triu(sp.csc_matrix(P)) if not _is_upper(P) else P, keep)
             Ac = _csc(A, keep)
@@ -322,6 +369,7 @@ class Batch(Solver):
             keep += [Pc, Ac, q, b, cz]
             arr[i] = clr_problem(C.pointer(Pc), _dptr(q), C.pointer(Ac), _dptr(b), cz, len(cones))
             self.sizes.append((len(q), len(b)))
+            pats.append((_pattern(Pc), _pattern(Ac)))
         self.n, self.m = self.sizes[0]
         st = _settings(settings)
         self.settings = st
@@ -329,6 +377,7 @@ class Batch(Solver):
         fn = _lib().clr_batch_setup if device else _lib().clr_batch_analyze
         _check(fn(C.byref(h), len(problems), arr, C.byref(st)), "clr_batch_setup" if device else "clr_batch_analyze")
         self.h = h
+        self.patterns = pats
 
     def size(self):
         return _lib().clr_batch_size(self.h)
@@ -349,6 +398,9 @@ class Batch(Solver):
         q = np.ascontiguousarray(q, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         _check(_lib().clr_batch_update_qb(self.h, i, _dptr(q), _dptr(b)), "clr_batch_update_qb")
+
+    def update_PA_of(self, i, P=None, A=None):
+        self._update_PA(i, P, A)
 
 
 def clr_batch_setup(problems, settings=None):

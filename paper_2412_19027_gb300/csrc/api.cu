@@ -122,6 +122,11 @@ int clr_update_qb(clr_solver* s, const double* q, const double* b) {
   return s->impl.update_qb(0, q, b);
 }
 
+int clr_update_PA(clr_solver* s, const double* Px, const double* Ax) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.update_PA(0, Px, Ax);
+}
+
 // ---- cohorts ----
 static int make_batch(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st,
                       bool device) {
@@ -295,6 +300,11 @@ int clr_batch_get(const clr_solver* s, int32_t i, double* x, double* sl, double*
 int clr_batch_update_qb(clr_solver* s, int32_t i, const double* q, const double* b) {
   if (!s) return CLR_E_INVALID;
   return s->impl.update_qb(i, q, b);
+}
+
+int clr_batch_update_PA(clr_solver* s, int32_t i, const double* Px, const double* Ax) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.update_PA(i, Px, Ax);
 }
 
 int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out) {

@@ -118,6 +118,14 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     p.bnorm = hp.bnorm;
     p.qnorm = hp.qnorm;
     p.maxPdiag = hp.maxPdiag;
+    p.nnzP = hp.nnzP;
+    p.nnzA = hp.nnzA;
+    p.p_kv = std::move(hp.p_kv);
+    p.a_kv = std::move(hp.a_kv);
+    p.p_diag = std::move(hp.p_diag);
+    p.p_scale = std::move(hp.p_scale);
+    p.a_scale = std::move(hp.a_scale);
+    p.kx_off = 0;
     const int64_t n = hp.n, m = hp.m, N = n + m;
     lay.xo = {0, n};
     lay.zrow[0].resize(m);
@@ -255,8 +263,10 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     }
     hp.kcol_ptr[col + 1] = (int64_t)hp.kval.size();
   };
-  for (int64_t p = 0; p < B; ++p)
+  for (int64_t p = 0; p < B; ++p) {
+    probs[p].kx_off = (int64_t)hp.kval.size();  // the problem's x columns are copied whole, in order
     for (int64_t j = 0; j < probs[p].n; ++j) copy_col(p, j, lay.xo[p] + j);
+  }
   hp.kval_x = (int64_t)hp.kval.size();
   std::vector<int64_t> zcol_start(m);  // kval z-part offset of each merged z column
   for (int64_t R = 0; R < m; ++R) {

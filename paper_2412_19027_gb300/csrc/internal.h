@@ -101,6 +101,15 @@ struct HostProblem {
   std::vector<int64_t> krow;       // row KKT index of each kval entry
   std::vector<int64_t> kdiag;      // kval index of the diagonal of each KKT column
   int64_t kval_x = 0;              // entries of the x part of kval
+  // value updates of P and A (clr_update_PA): for each stored value of the
+  // caller's P (upper triangle) and A, in their CSC order, its kval index (x
+  // part of this problem) and equilibration factor (c D_i D_j for P, E_r D_j
+  // for A); the caller indices of P's diagonal entries; the offset of this
+  // problem's x part in the cohort's kval (set by build_cohort)
+  int64_t nnzP = 0, nnzA = 0;
+  std::vector<int64_t> p_kv, a_kv, p_diag;
+  std::vector<double> p_scale, a_scale;
+  int64_t kx_off = 0;
 };
 
 // Where the problems of a cohort live in the merged vectors (host side).
@@ -124,6 +133,10 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
 int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_csc* A, const double* b,
                   const clr_cone* cones, int32_t ncones, const clr_settings& st, std::string& err);
 int set_qb(HostProblem& hp, const double* q, const double* b);
+// New values of P (upper, nnzP entries) and/or A (nnzA entries) in the caller's
+// CSC order (either may be NULL): written, scaled by the setup's equilibration,
+// into kval (at kx_off + the problem's index); maxPdiag updated.
+int set_PA(HostProblem& pr, const double* Px, const double* Ax, std::vector<double>& kval);
 void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int64_t>& idx,
                std::vector<int64_t>& perm, int64_t& n_dense);
 // relax: merge supernodes with few explicit zeros (relaxed amalgamation):

@@ -378,6 +378,19 @@ __global__ void k_fin_resid(IterScal* scs, const ProbConst* pcs, const double* p
       status = CLR_MAX_ITER;
   }
   sc.status = status;
+  if (status == 0) {
+    // the complementarity gap still falls while the residuals stay: with a
+    // low-precision factor, the accuracy of the KKT solves is what holds them up
+    const double feas = fmax(nrp / (tp.eps_feas * fmax(1.0, pc.bnorm + nx + ns)),
+                             nrd / (tp.eps_feas * fmax(1.0, pc.qnorm + nx + nz)));
+    if (sc.feas_best == 0.0 || feas < 0.5 * sc.feas_best) {
+      sc.feas_best = feas;
+      sc.mu_at_best = mu;
+      sc.feas_stall = 0;
+    } else if (feas < 1e6 && mu < 0.1 * sc.mu_at_best) {
+      sc.feas_stall += 1;
+    }
+  }
   if (sc.iter < tp.hist_cap) {
     double* h = hist + (int64_t)12 * tp.hist_cap * p + 12 * sc.iter;
     h[0] = sc.iter;
@@ -682,7 +695,7 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
-      if (q.ir_fail && sp.escalate_on) {
+      if ((q.ir_fail || q.feas_stall >= 3) && sp.escalate_on) {
         q.alpha_c = 0.0;
         q.escalate = 1;  // redo the iteration with the FP64 factor
         continue;
@@ -1033,6 +1046,7 @@ int Solver::upload() {
       // contiguous loads instead of gathers through the value index
       std::vector<double> fv(cnt[hp.n], 0.0);
       for (int64_t p = 0; p < cnt[hp.n]; ++p) fv[p] = hp.kval[vi[p]];
+      h_kfv_src_.assign(vi.begin(), vi.begin() + cnt[hp.n]);
       v_.kfv = fv.empty() ? nullptr : ar_.upload(fv.data(), (int64_t)fv.size());
       if (!fv.empty() && !v_.kfv) return CLR_E_OOM;
     }
@@ -1731,6 +1745,31 @@ int Solver::update_qb(int64_t p, const double* q, const double* b) {
   if (device_ready) {
     CLR_CUDA(cudaMemcpyAsync(v_.q, hp.q.data(), sizeof(double) * (size_t)hp.n, cudaMemcpyHostToDevice, stream_));
     CLR_CUDA(cudaMemcpyAsync(v_.b, hp.b.data(), sizeof(double) * (size_t)hp.m, cudaMemcpyHostToDevice, stream_));
+    CLR_CUDA(cudaMemcpyAsync(v_.pc, lay.pc.data(), sizeof(ProbConst) * (size_t)lay.B, cudaMemcpyHostToDevice,
+                             stream_));
+    CLR_CUDA(cudaStreamSynchronize(stream_));
+  }
+  return CLR_OK;
+}
+
+// New values of P and/or A for problem p (same pattern): the x part of the KKT
+// values and its full-CSR copy are rewritten; the symbolic analysis, the order
+// and every device buffer are kept (parametric programming, Sec. 4.6).
+int Solver::update_PA(int64_t p, const double* Px, const double* Ax) {
+  if (p < 0 || p >= lay.B) return CLR_E_INVALID;
+  if (!Px && !Ax) return CLR_OK;
+  HostProblem& pr = probs[p];
+  int rc = set_PA(pr, Px, Ax, hp.kval);
+  if (rc) return rc;
+  lay.pc[p].maxPdiag = pr.maxPdiag;
+  if (device_ready) {
+    std::vector<double> fv(h_kfv_src_.size());
+    for (size_t k = 0; k < fv.size(); ++k) fv[k] = hp.kval[h_kfv_src_[k]];
+    CLR_CUDA(cudaMemcpyAsync(v_.kval, hp.kval.data(), sizeof(double) * (size_t)hp.kval_x, cudaMemcpyHostToDevice,
+                             stream_));
+    if (!fv.empty())
+      CLR_CUDA(cudaMemcpyAsync(const_cast<double*>(v_.kfv), fv.data(), sizeof(double) * fv.size(),
+                               cudaMemcpyHostToDevice, stream_));
     CLR_CUDA(cudaMemcpyAsync(v_.pc, lay.pc.data(), sizeof(ProbConst) * (size_t)lay.B, cudaMemcpyHostToDevice,
                              stream_));
     CLR_CUDA(cudaStreamSynchronize(stream_));

@@ -82,6 +82,7 @@ class Solver {
   // Build on caller-owned `stream` with stream-ordered device memory (before upload).
   int use_stream_ordered(cudaStream_t stream);
   int update_qb(int64_t p, const double* q, const double* b);
+  int update_PA(int64_t p, const double* Px, const double* Ax);
   int set_stream(void* stream);
   size_t device_bytes() const { return ar_.bytes(); }
   int64_t nprob() const { return lay.B; }
@@ -103,6 +104,7 @@ class Solver {
   int hist_rows_ = 0;
   int csr_group_ = 32;
   std::vector<int64_t> h_long_;  // KKT rows handled by k_kmv_long
+  std::vector<int32_t> h_kfv_src_;  // kval index of each entry of the x rows' full-CSR values (kfv)
   // iteration graphs per factor precision (0: configured, 1: FP64 after an escalation)
   cudaGraph_t graph_[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec_[2] = {nullptr, nullptr};

@@ -46,6 +46,11 @@ struct IterScal {
   // precision escalation: a refinement of this iteration stopped short (ir_fail);
   // the iteration is not taken (escalate) and is redone with the FP64 factor
   int ir_fail, escalate;
+  // feasibility stall (low-precision factor): the best termination ratio of the
+  // residuals so far, mu when it was reached, and the iterations since then in
+  // which mu stood ten times lower; three of them also escalate
+  double feas_best, mu_at_best;
+  int feas_stall, pad1;
 };
 
 // Constants of one problem (device memory, written at setup).

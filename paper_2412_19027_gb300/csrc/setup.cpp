@@ -195,12 +195,14 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
   for (int64_t r = 0; r < m; ++r) Ar.ptr[r + 1] += Ar.ptr[r];
   Ar.idx.resize(A->nnz);
   Ar.val.resize(A->nnz);
+  std::vector<int64_t> ar_src(A->nnz);  // caller index of each Ar entry
   {
     std::vector<int64_t> next(Ar.ptr.begin(), Ar.ptr.end() - 1);
     for (int64_t j = 0; j < n; ++j)
       for (int64_t p = A->colptr[j]; p < A->colptr[j + 1]; ++p) {
         int64_t r = inv_row[A->rowind[p]];
         Ar.idx[next[r]] = (int32_t)j;
+        ar_src[next[r]] = p;
         Ar.val[next[r]++] = A->val[p];
       }
   }
@@ -218,6 +220,7 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
   for (int64_t j = 0; j < n; ++j) Pf.ptr[j + 1] += Pf.ptr[j];
   Pf.idx.resize(Pf.ptr[n]);
   Pf.val.resize(Pf.ptr[n]);
+  std::vector<int64_t> pf_src(Pf.ptr[n]);  // caller index of each Pf entry
   {
     // row j of the full matrix: entries (j, i) for i < j come from column j's upper part mirrored
     // (P(i, j) stored in column j gives row i col j and row j col i).  Fill rows in column order so
@@ -228,11 +231,13 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
         int64_t i = P->rowind[p];  // i <= j
         // row i gets column j (j >= i: appended in increasing j order)
         Pf.idx[next[i]] = (int32_t)j;
+        pf_src[next[i]] = p;
         Pf.val[next[i]++] = P->val[p];
         if (i != j) {
           // row j gets column i; columns i < j arrive in increasing i order for fixed j, and
           // before any entry (j, j') with j' >= j is appended, since those come from column j' >= j.
           Pf.idx[next[j]] = (int32_t)i;
+          pf_src[next[j]] = p;
           Pf.val[next[j]++] = P->val[p];
         }
       }
@@ -302,12 +307,14 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
   for (int64_t j = 0; j < n; ++j) At.ptr[j + 1] += At.ptr[j];
   At.idx.resize(Ar.nnz());
   At.val.resize(Ar.nnz());
+  std::vector<int64_t> at_src(Ar.nnz());  // caller index of each At entry
   {
     std::vector<int64_t> next(At.ptr.begin(), At.ptr.end() - 1);
     for (int64_t r = 0; r < m; ++r)
       for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) {
         int64_t j = Ar.idx[p];
         At.idx[next[j]] = (int32_t)r;
+        at_src[next[j]] = ar_src[p];
         At.val[next[j]++] = Ar.val[p];
       }
   }
@@ -318,6 +325,24 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
   // x column j: P(i, j) for i >= j with an explicit diagonal, then A(:, j) as rows n + r.
   // z block of each cone: packed lower triangle of its H block (column-major).
   const int64_t N = n + m;
+  // value-update maps: equilibration factor of each caller value, P's diagonal
+  hp.nnzP = P->nnz;
+  hp.nnzA = A->nnz;
+  hp.p_kv.assign(P->nnz, -1);
+  hp.a_kv.assign(A->nnz, -1);
+  hp.p_scale.resize(P->nnz);
+  hp.a_scale.resize(A->nnz);
+  hp.p_diag.clear();
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = P->colptr[j]; p < P->colptr[j + 1]; ++p) {
+      const int64_t i = P->rowind[p];
+      hp.p_scale[p] = hp.c * hp.D[i] * hp.D[j];
+      if (i == j) hp.p_diag.push_back(p);
+    }
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = A->colptr[j]; p < A->colptr[j + 1]; ++p)
+      hp.a_scale[p] = hp.E[inv_row[A->rowind[p]]] * hp.D[j];
+  hp.kx_off = 0;
   hp.kcol_ptr.assign(N + 1, 0);
   hp.krow.clear();
   hp.kval.clear();
@@ -336,10 +361,12 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
       int64_t i = Pf.idx[p];
       if (i < j) continue;
       if (i == j) hp.kdiag[j] = (int64_t)hp.kval.size();
+      hp.p_kv[pf_src[p]] = (int64_t)hp.kval.size();
       hp.krow.push_back(i);
       hp.kval.push_back(Pf.val[p]);
     }
     for (int64_t p = At.ptr[j]; p < At.ptr[j + 1]; ++p) {
+      hp.a_kv[at_src[p]] = (int64_t)hp.kval.size();
       hp.krow.push_back(n + At.idx[p]);
       hp.kval.push_back(At.val[p]);
     }
@@ -383,6 +410,21 @@ int set_qb(HostProblem& hp, const double* q, const double* b) {
     hp.b[r] = hp.E[r] * v;
     hp.bnorm = std::max(hp.bnorm, std::fabs(v));
   }
+  return CLR_OK;
+}
+
+// New values of P and/or A in the caller's CSC order, scaled with the setup's
+// equilibration (the parametric update keeps D, E and c, as clr_update_qb does).
+int set_PA(HostProblem& pr, const double* Px, const double* Ax, std::vector<double>& kval) {
+  if ((Px && !finite_all(Px, pr.nnzP)) || (Ax && !finite_all(Ax, pr.nnzA))) return CLR_E_INVALID;
+  if ((Px && (int64_t)pr.p_kv.size() != pr.nnzP) || (Ax && (int64_t)pr.a_kv.size() != pr.nnzA)) return CLR_E_STATE;
+  if (Px) {
+    for (int64_t k = 0; k < pr.nnzP; ++k) kval[pr.kx_off + pr.p_kv[k]] = Px[k] * pr.p_scale[k];
+    pr.maxPdiag = 0.0;
+    for (int64_t k : pr.p_diag) pr.maxPdiag = std::max(pr.maxPdiag, std::fabs(Px[k] * pr.p_scale[k]));
+  }
+  if (Ax)
+    for (int64_t k = 0; k < pr.nnzA; ++k) kval[pr.kx_off + pr.a_kv[k]] = Ax[k] * pr.a_scale[k];
   return CLR_OK;
 }
 

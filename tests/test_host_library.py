@@ -28,7 +28,7 @@ def clr():
 def _declared_functions():
     text = open(os.path.join(ROOT, "include", "clr.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(clr_[a-z_0-9]+)\s*\(", text)) - {"clr_alloc_fn", "clr_free_fn"})
+    return sorted(set(re.findall(r"\b(clr_[A-Za-z_0-9]+)\s*\(", text)) - {"clr_alloc_fn", "clr_free_fn"})
 
 
 def test_library_exports_every_declared_symbol(clr):
@@ -264,3 +264,32 @@ def test_blocking_settings_validated_and_applied(clr):
     assert stats[0]["l_nnz"] == stats[0]["l_nnz_exact"]  # no amalgamation: no explicit zeros
     assert stats[0]["n_supernodes"] >= stats[1]["n_supernodes"] >= stats[2]["n_supernodes"]
     assert stats[2]["l_nnz"] >= stats[1]["l_nnz"] >= stats[0]["l_nnz"]
+
+
+def test_update_PA_validation(clr):
+    """clr_update_PA on a host-analysed solver: values on the setup's patterns are
+    accepted (as a matrix of that pattern or as a CSC-ordered array), a changed
+    pattern or a wrong count is refused in the binding, NaN by the library."""
+    prob = W.nonneg_qp(0)
+    s = clr.clr_analyze(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    A2 = prob.A.copy()
+    A2.data = A2.data * 1.5
+    s.update_PA(A=A2)
+    s.update_PA(P=sp.triu(prob.P * 2.0))
+    s.update_PA(P=None, A=None)
+    s.update_PA(A=np.ones(prob.A.nnz))
+    with pytest.raises(ValueError):
+        s.update_PA(A=np.ones(prob.A.nnz - 1))
+    A3 = prob.A.tolil()
+    A3[0, :] = 0.0
+    A3[0, 0] = 1.0
+    A3 = sp.csc_matrix(A3)
+    A3.eliminate_zeros()
+    with pytest.raises(ValueError):
+        s.update_PA(A=A3)
+    bad = np.ones(prob.A.nnz)
+    bad[3] = np.nan
+    with pytest.raises(clr.ClrError) as e:
+        s.update_PA(A=bad)
+    assert e.value.code == -1
+    s.free()
