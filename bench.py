@@ -41,7 +41,7 @@ UNIT = "iter/s"
 WORKLOAD = "mixed-cone QP n=2000 m=6600 (500 zero, 3000 nonneg, 500 SOC5, 100 exp, 100 pow0.3), P=diag+rank10"
 FP64_PEAK_TFLOPS = 1.25            # GB300 FP64 (FFMA and DMMA), nominal
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
-FLOW_DRAM_BYTES_FP32 = 17.867008e6 + 2.787840e6    # k_bf_flow<float>, mixed-cone QP (profiles/k_bf_flow_*)
+FLOW_DRAM_BYTES_FP32 = 17.800448e6 + 1.957632e6    # k_bf_flow<float>, mixed-cone QP (profiles/k_bf_flow_*)
 
 
 def measured_peaks():
