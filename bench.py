@@ -119,6 +119,9 @@ def parse():
                     help="skip the cone kernels at stress shapes (2^26 nonneg rows, 2^22 SOC5, 2^16 PSD10)")
     ap.add_argument("--configs", action="store_true",
                     help="solve each synthetic configuration once (absolute times, statuses, errors) and exit")
+    ap.add_argument("--paper-workloads", action="store_true",
+                    help="solve the paper's benchmark classes once each (portfolio and Huber QPs, entropy "
+                         "maximisation; FP64 and FP32 factors) and exit")
     ap.add_argument("--cone-only", action="store_true",
                     help="run only the cone kernels at the stress shapes and print their JSON (for profiling)")
     ap.add_argument("--cone-shift", type=int, default=0, help="divide the stress shapes by 2^shift")
@@ -314,6 +317,43 @@ def run_serving(args, clr, W):
             "speedup_solves_per_s": sat["solves_per_s"] / rate1, "generation_s": t_gen}
 
 
+def run_paper_workloads(args, clr, W):
+    """The paper's benchmark classes (Sec. 5.1 portfolio and Huber QPs, Sec. 5.3
+    entropy maximisation), one timed solve per factor precision, setup reported
+    apart.  Sizes below the paper's (n = 5000 / 5000 / 2000 there): at those the
+    host setup of this solver takes 20 s / 650 s / 130 s (the extend-add maps of
+    fronts with thousands of children, and the ordering of rows with hundreds of
+    entries), so the smaller instances keep the run to a minute."""
+    import torch
+
+    out = {}
+    for name, prob in (("portfolio_n2000", W.portfolio_qp(args.seed, n=2000)),
+                       ("huber_n1000", W.huber_qp(args.seed, n=1000)),
+                       ("entropy_n600", W.entropy_max(args.seed, n=600))):
+        runs = []
+        for bits in (64, 32):
+            st = clr.clr_default_settings(bits)
+            t0 = time.perf_counter()
+            s_ = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+            t1 = time.perf_counter()
+            s_.solve()
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            x, _, _, info = s_.solution()
+            pf = s_.perf()
+            sym = s_.symbolic_stats()
+            s_.free()
+            runs.append({"factor_bits": bits, "status": info["status_name"], "iterations": info["iterations"],
+                         "setup_s": t1 - t0, "solve_ms": 1e3 * (t2 - t1),
+                         "factor_ms_per_factorization": pf["factor_ms"] / max(1, pf["factorizations"]),
+                         "fp64_from_iter": info["fp64_from_iter"], "gap_rel": info["gap_rel"],
+                         "res_primal": info["res_primal"], "res_dual": info["res_dual"],
+                         "objective": float(prob.objective(x)), "kkt_dim": sym["kkt_dim"],
+                         "l_nnz": sym["l_nnz"], "factor_flops": sym["factor_flops"], "max_front": sym["max_front"]})
+        out[name] = runs
+    return out
+
+
 def run_configs(args, clr, W):
     """One timed solve of each configuration (setup reported apart), FP64 and the
     low-precision factors where the configuration asks for them."""
@@ -423,6 +463,10 @@ def run_ours(args):
     if args.configs:
         if rank == 0:
             print(json.dumps({"configs": run_configs(args, clr, W)}), flush=True)
+        return
+    if args.paper_workloads:
+        if rank == 0:
+            print(json.dumps({"paper_workloads": run_paper_workloads(args, clr, W)}), flush=True)
         return
     if args.cone_only:
         if rank == 0:

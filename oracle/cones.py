@@ -441,13 +441,17 @@ def bfgs_scaling(ctype, s, z, mu, alpha=0.0):
     """H = S (S^T Z)^{-1} S^T + H_a - H_a Z (Z^T H_a Z)^{-1} Z^T H_a, with
     S = [s, st], Z = [z, zt], st = -grad f(z), zt = -grad f*(s), H_a = mu Hess f(z).
     mu is the global complementarity measure.  When 1 - 9/((s'z)(st'zt)) is below
-    BFGS_DEGENERACY (near the central path, where S and Z become rank one) the
-    matrix H_a alone is used."""
+    BFGS_DEGENERACY (near the central path, where S and Z become rank one), or
+    when zt cannot be evaluated (the Newton system of the conjugate barrier is
+    singular near the boundary of the cone), the matrix H_a alone is used."""
     st = -barrier_grad(ctype, z, alpha)
-    zt = dual_shadow(ctype, s, alpha)
     Ha = mu * barrier_hess(ctype, z, alpha)
+    try:
+        zt = dual_shadow(ctype, s, alpha)
+    except (np.linalg.LinAlgError, FloatingPointError, ZeroDivisionError, ValueError):
+        return Ha
     sz, stzt = s @ z, st @ zt
-    if not (1.0 - 9.0 / (sz * stzt) > BFGS_DEGENERACY):
+    if not (np.all(np.isfinite(zt)) and 1.0 - 9.0 / (sz * stzt) > BFGS_DEGENERACY):
         return Ha
     S = np.column_stack([s, st])
     Z = np.column_stack([z, zt])
@@ -463,7 +467,15 @@ def third_order_correction(ctype, z, dz, ds, alpha=0.0):
 
 
 def neighbourhood_ok(ctype, s, z, mu, beta, alpha=0.0):
-    """nu_i <grad f*(s_i), grad f(z_i)>^{-1} >= beta mu  (Sec. 2.2, N(beta))."""
-    zt = dual_shadow(ctype, s, alpha)  # = -grad f*(s)
-    st = -barrier_grad(ctype, z, alpha)  # = -grad f(z)
-    return 3.0 / (zt @ st) >= beta * mu
+    """nu_i <grad f*(s_i), grad f(z_i)>^{-1} >= beta mu  (Sec. 2.2, N(beta)).
+
+    A trial point at which grad f*(s) cannot be evaluated (the Newton system of
+    the conjugate is singular, or a value is not finite) counts as outside the
+    neighbourhood, so the step length backs off instead of failing the solve."""
+    try:
+        zt = dual_shadow(ctype, s, alpha)  # = -grad f*(s)
+        st = -barrier_grad(ctype, z, alpha)  # = -grad f(z)
+        d = float(zt @ st)
+    except (np.linalg.LinAlgError, FloatingPointError, ZeroDivisionError, ValueError):
+        return False
+    return bool(np.isfinite(d) and d > 0.0 and 3.0 / d >= beta * mu)

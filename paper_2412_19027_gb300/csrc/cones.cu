@@ -932,10 +932,11 @@ __device__ bool ns_nbhd(const NsCone& c, double alpha, const double* mu_coef, do
   }
   const double mu_t = mu_coef[0] + alpha * (mu_coef[1] + alpha * mu_coef[2]);
   const double start[3] = {c.zt0[0], c.zt0[1], c.zt0[2]};
-  dual_shadow(c.is_exp, sc, c.a, start, zt);
+  // a trial point whose grad f*(s) cannot be evaluated counts as outside N(beta)
+  if (!dual_shadow(c.is_exp, sc, c.a, start, zt)) return false;
   barrier_grad(c.is_exp, zc, c.a, g);
   const double dot = -(zt[0] * g[0] + zt[1] * g[1] + zt[2] * g[2]);  // <z~, s~>, s~ = -grad f(z)
-  return 3.0 / dot >= beta * mu_t;
+  return isfinite(dot) && dot > 0.0 && 3.0 / dot >= beta * mu_t;
 }
 }  // namespace
 

@@ -289,6 +289,91 @@ def mpc_qp(seed=0, T=None, nx=None, nu=None, x_bound=5.0, u_bound=1.0, u_soc=1.2
                    np.asarray(b), cones, meta=dict(T=T, nx=nx, nu=nu))
 
 
+# ----------------------------------------------------------------------------
+# the paper's own benchmark classes (Sec. 5.1 quadratic programs, Sec. 5.3
+# exponential cone programs), written as conic problems; not built from a known
+# optimum (the oracle solves the small instances)
+
+def portfolio_qp(seed=0, n=5000, density=0.5):
+    """Portfolio optimisation (Sec. 5.1): maximise mu'x - gamma x' Sigma x s.t.
+    1'x = 1, x >= 0, Sigma = F F' + D with rank p = round(0.1 n).  Conic form with
+    y = F'x: variables (x, y), minimise gamma (x'Dx + y'y) - mu'x, zero rows
+    F'x - y = 0 and 1'x = 1, nonnegative rows -x <= 0.  F n x p with `density`
+    N(0, 1) entries, D = diag(U(0, sqrt(p))), mu ~ N(0, 1), gamma = 1."""
+    rng = np.random.default_rng(seed)
+    p = max(1, int(round(0.1 * n)))
+    mask = rng.random((n, p)) < density
+    F = sp.csc_matrix(np.where(mask, rng.standard_normal((n, p)), 0.0))
+    d = rng.uniform(0.0, math.sqrt(p), n)
+    mu = rng.standard_normal(n)
+    gamma = 1.0
+    P = sp.block_diag([sp.diags(2.0 * gamma * d), sp.identity(p) * (2.0 * gamma)], format="csc")
+    q = np.r_[-mu, np.zeros(p)]
+    A = sp.vstack([sp.hstack([F.T, -sp.identity(p)]),
+                   sp.hstack([sp.csr_matrix(np.ones((1, n))), sp.csr_matrix((1, p))]),
+                   sp.hstack([-sp.identity(n), sp.csr_matrix((n, p))])], format="csc")
+    b = np.r_[np.zeros(p), 1.0, np.zeros(n)]
+    cones = [(ZERO, p + 1, 0.0), (NONNEG, n, 0.0)]
+    return Problem("portfolio_n%d_p%d" % (n, p), sp.csc_matrix(sp.triu(P)), q, A, b, cones,
+                   meta=dict(n=n, p=p, mu=mu, F=F, d=d, gamma=gamma))
+
+
+def huber_qp(seed=0, n=5000, density=0.15, T=1.0):
+    """Huber fitting (Sec. 5.1): minimise sum_i phi_T(a_i'x - b_i), m = round(1.5 n),
+    phi_T(t) = t^2 for |t| <= T, T (2|t| - T) otherwise.  Conic form: variables
+    (x, u, r, s), minimise u'u + 2T 1'(r + s) s.t. A x - u - r + s = b (zero
+    rows), r, s >= 0; at the optimum u + r - s = Ax - b with u the clipped
+    residual.  A m x n with `density` N(0, 1) entries, x_true ~ N(0, 1/n),
+    b = A x_true + e with e_i ~ N(0, 1/4), and U(0, 10) on 5 % of the rows."""
+    rng = np.random.default_rng(seed)
+    m = int(round(1.5 * n))
+    mask = rng.random((m, n)) < density
+    Ad = sp.csc_matrix(np.where(mask, rng.standard_normal((m, n)), 0.0))
+    x_true = rng.standard_normal(n) / math.sqrt(n)
+    noise = np.where(rng.random(m) < 0.95, 0.5 * rng.standard_normal(m), rng.uniform(0.0, 10.0, m))
+    bd = Ad @ x_true + noise
+    I = sp.identity(m, format="csc")
+    Z = sp.csc_matrix((m, m))
+    P = sp.block_diag([sp.csc_matrix((n, n)), 2.0 * I, Z, Z], format="csc")
+    q = np.r_[np.zeros(n + m), 2.0 * T * np.ones(2 * m)]
+    A = sp.vstack([sp.hstack([Ad, -I, -I, I]),
+                   sp.hstack([sp.csc_matrix((m, n)), Z, -I, Z]),
+                   sp.hstack([sp.csc_matrix((m, n)), Z, Z, -I])], format="csc")
+    b = np.r_[bd, np.zeros(2 * m)]
+    cones = [(ZERO, m, 0.0), (NONNEG, 2 * m, 0.0)]
+    return Problem("huber_n%d_m%d" % (n, m), sp.csc_matrix(sp.triu(P)), q, A, b, cones,
+                   meta=dict(n=n, m=m, A=Ad, b=bd, T=T))
+
+
+def entropy_max(seed=0, n=2000):
+    """Entropy maximisation (Sec. 5.3): maximise -sum_i x_i log x_i s.t. 1'x = 1,
+    A x <= b, m = round(0.5 n), A_ij ~ N(0, n), b = A v / 1'v with v_i ~ U(0, 1)
+    (so v / 1'v is feasible).  Conic form: variables (x, t), minimise -1't s.t.
+    1'x = 1 (zero row), A x <= b (nonnegative rows), (t_i, x_i, 1) in K_exp for
+    each i, i.e. x_i exp(t_i / x_i) <= 1, t_i <= -x_i log x_i."""
+    rng = np.random.default_rng(seed)
+    m = max(1, int(round(0.5 * n)))
+    Ad = rng.standard_normal((m, n)) * math.sqrt(n)
+    v = rng.uniform(0.0, 1.0, n)
+    bd = Ad @ v / v.sum()
+    rows, cols, vals = [], [], []
+    for i in range(n):  # exp cone i: rows 3i, 3i + 1, 3i + 2 of the cone block
+        rows += [3 * i, 3 * i + 1]
+        cols += [n + i, i]
+        vals += [-1.0, -1.0]
+    E = sp.csc_matrix((vals, (rows, cols)), shape=(3 * n, 2 * n))
+    A = sp.vstack([sp.hstack([sp.csr_matrix(np.ones((1, n))), sp.csr_matrix((1, n))]),
+                   sp.hstack([sp.csr_matrix(Ad), sp.csr_matrix((m, n))]),
+                   E], format="csc")
+    be = np.zeros(3 * n)
+    be[2::3] = 1.0
+    b = np.r_[1.0, bd, be]
+    q = np.r_[np.zeros(n), -np.ones(n)]
+    cones = [(ZERO, 1, 0.0), (NONNEG, m, 0.0)] + [(EXP, 3, 0.0)] * n
+    return Problem("entropy_n%d_m%d" % (n, m), sp.csc_matrix((2 * n, 2 * n)), q, A, b, cones,
+                   meta=dict(n=n, m=m, A=Ad, b=bd))
+
+
 def mpc_stream(seed=0, count=10_000):
     """Seeds and Poisson inter-arrival draws for the MPC serving stream."""
     rng = np.random.default_rng(seed)
