@@ -61,10 +61,11 @@ enum clr_status {
 
 /* Cone types (Sec. 2.1).  CLR_PSD_TRI: dim = k(k+1)/2 rows holding the svec
  * of a k x k symmetric matrix -- upper triangle, column by column, entries
- * above the diagonal multiplied by sqrt(2).  All PSD cones of one problem
- * must have the same order k <= 32 (the paper's restriction, Sec. 2.1
- * footnote and Sec. 3.4).  CLR_EXP and CLR_POW have dim 3; alpha is the power
- * cone exponent in (0, 1). */
+ * above the diagonal multiplied by sqrt(2).  Every PSD cone has order
+ * k <= 32 (the paper's bound, Sec. 2.1 footnote and Sec. 3.4); cones of
+ * different orders may be mixed (the paper requires one order and names mixed
+ * orders as future work, Sec. 6).  CLR_EXP and CLR_POW have dim 3; alpha is
+ * the power cone exponent in (0, 1). */
 enum clr_cone_type { CLR_ZERO = 0, CLR_NONNEG = 1, CLR_SOC = 2, CLR_EXP = 3, CLR_POW = 4, CLR_PSD_TRI = 5 };
 
 typedef struct {
@@ -259,8 +260,7 @@ typedef struct {
 } clr_problem;
 
 /* Setup of nprob >= 1 problems as one solver (the host analysis of each
- * problem runs on worker threads).  All PSD cones of the cohort must share one
- * order (else CLR_E_UNSUPPORTED).  Errors as clr_setup, for the first failing
+ * problem runs on worker threads).  Errors as clr_setup, for the first failing
  * problem.  clr_solve solves every problem; clr_get_solution and
  * clr_update_qb act on problem 0; clr_get_perf covers the cohort. */
 int clr_batch_setup(clr_solver** out, int32_t nprob, const clr_problem* probs, const clr_settings* st);

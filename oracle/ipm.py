@@ -99,7 +99,6 @@ def _validate(Pu, q, A, b, cones):
     if np.any(np.tril(Pu, -1) != 0):
         raise ProblemError("P must be upper triangular")
     total = 0
-    psd_k = None
     for (t, d, a) in cones:
         if t not in C.FAMILY_NAMES or d < 0:
             raise ProblemError("bad cone")
@@ -111,10 +110,8 @@ def _validate(Pu, q, A, b, cones):
             raise ProblemError("SOC dimension must be >= 1")
         if t == C.PSD:
             k = C.psd_order(d)
-            if psd_k is None:
-                psd_k = k
-            if k != psd_k or k > 32 or k < 1:
-                raise ProblemError("PSD cones must share one order <= 32")
+            if k > 32 or k < 1:
+                raise ProblemError("PSD cones of order 1 .. 32 only")
         total += d
     if total != m:
         raise ProblemError("cone dimensions do not add up to m")

@@ -85,15 +85,8 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     err = "one order per problem";
     return CLR_E_DIM;
   }
-  int psd_k = 0;
-  for (const HostProblem& p : probs)
-    if (p.cl.psd_k) {
-      if (psd_k && p.cl.psd_k != psd_k) {
-        err = "all PSD cones of a cohort must share one order";
-        return CLR_E_UNSUPPORTED;
-      }
-      psd_k = p.cl.psd_k;
-    }
+  int psd_k = 0;  // the largest PSD order (cones of every order <= 32 are handled per cone)
+  for (const HostProblem& p : probs) psd_k = std::max(psd_k, p.cl.psd_k);
   lay = CohortLayout();
   lay.B = B;
   lay.pc.resize(B);

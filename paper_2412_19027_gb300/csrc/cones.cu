@@ -579,14 +579,25 @@ __device__ double jacobi_eigmin(double* A, int k, double* cs_buf, int* flag) {
 
 // PSD scaling: L_s L_s' = S, L_z L_z' = Z, L_z' L_s = U Lambda V', R = L_s V Lambda^{-1/2},
 // R^{-1} = Lambda^{-1/2} U' L_z', H(X) = (R R') X (R R') written as the svec block.
+// PSD cone holding row r (r >= psd_row0): binary search over the cones' first rows
+__device__ __forceinline__ int64_t psd_cone_of(const ConeDev& cd, int64_t r) {
+  int64_t lo = 0, hi = cd.n_psd - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (cd.psd_crow[mid] <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
                             const int* skip) {
   if (skip && *skip) return;
   __shared__ double Ls[32 * LDP], Lz[32 * LDP], M[32 * LDP], V[32 * LDP], sig[32];
   __shared__ int bad, flag;
-  const int k = cd.psd_k, d = cd.psd_d;
   const int64_t cone = blockIdx.x;
-  const int64_t row = cd.psd_row0 + (int64_t)d * cone;
+  const int k = cd.psd_ck[cone], d = k * (k + 1) / 2;
+  const int64_t row = cd.psd_crow[cone];
   if (threadIdx.x == 0) bad = 0;
   load_smat(s + row, k, Ls);
   load_smat(z + row, k, Lz);
@@ -601,9 +612,9 @@ __global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const doub
   }
   __syncthreads();
   jacobi_svd(M, V, sig, k, &flag);
-  double* R = cd.psd_R + (int64_t)k * k * cone;
-  double* Ri = cd.psd_Ri + (int64_t)k * k * cone;
-  double* lam = cd.psd_lam + (int64_t)k * cone;
+  double* R = cd.psd_R + cd.psd_cR[cone];
+  double* Ri = cd.psd_Ri + cd.psd_cR[cone];
+  double* lam = cd.psd_lam + cd.psd_cl[cone];
   for (int j = threadIdx.x; j < k; j += blockDim.x) lam[j] = bad ? NAN : sig[j];
   // R = Ls V diag(sig^-1/2); Ri = diag(sig^-1/2) U' Lz' with U = M / sig (columns)
   for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
@@ -626,7 +637,7 @@ __global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const doub
   __syncthreads();
   // H_{(i,j),(p,q)} = c_ij c_pq (M_ip M_jq + M_iq M_jp), c = 1/sqrt(2) on diagonal pairs;
   // packed lower over svec indices (row index >= column index), column-major.
-  double* kb = cd.kvz + cd.psd_kb0 + (int64_t)d * (d + 1) / 2 * cone;
+  double* kb = cd.kvz + cd.psd_ckb[cone];
   double mx = 0.0;
   const int64_t npk = (int64_t)d * (d + 1) / 2;
   for (int64_t t = threadIdx.x; t < npk; t += blockDim.x) {
@@ -677,7 +688,7 @@ int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const dou
     k_scale_exppow<<<ep_launch(cd.n_exp + cd.n_pow).blocks, ep_launch(cd.n_exp + cd.n_pow).threads, 0, st>>>(
         cd, s, z, sc, skip);
   if (cd.n_psd > 0) {
-    const int threads = 32 * ((cd.psd_k + 1) / 2 > 0 ? (cd.psd_k + 1) / 2 : 1);
+    const int threads = 32 * ((cd.psd_kmax + 1) / 2 > 0 ? (cd.psd_kmax + 1) / 2 : 1);
     k_scale_psd<<<(unsigned)cd.n_psd, threads < 64 ? 64 : threads, 0, st>>>(cd, s, z, sc, skip);
   }
   CLR_CHECK_LAUNCH();
@@ -718,9 +729,9 @@ __global__ void k_identity_diag(ConeDev cd, const int* skip) {
       continue;
     }
     if (cd.n_psd > 0 && r >= cd.psd_row0) {
-      const int64_t d = cd.psd_d;
-      const int64_t i = (r - cd.psd_row0) / d, c = (r - cd.psd_row0) % d;
-      cd.kvz[cd.psd_kb0 + d * (d + 1) / 2 * i + c * d - c * (c - 1) / 2] = -1.0;
+      const int64_t i = psd_cone_of(cd, r);
+      const int64_t kk = cd.psd_ck[i], d = kk * (kk + 1) / 2, c = r - cd.psd_crow[i];
+      cd.kvz[cd.psd_ckb[i] + c * d - c * (c - 1) / 2] = -1.0;
     }
   }
 }
@@ -833,8 +844,8 @@ __global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const doubl
   if (skip && *skip) return;
   __shared__ double L[32 * LDP], X[32 * LDP], Y[32 * LDP], csb[64];
   __shared__ int bad, flag;
-  const int k = cd.psd_k, d = cd.psd_d;
-  const int64_t row = cd.psd_row0 + (int64_t)d * blockIdx.x;
+  const int k = cd.psd_ck[blockIdx.x];
+  const int64_t row = cd.psd_crow[blockIdx.x];
   double amax = INFINITY;
   for (int side = 0; side < 2; ++side) {
     const double* v = side == 0 ? s + row : z + row;
@@ -884,7 +895,7 @@ int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, co
     else k_step_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   }
   if (cd.n_psd > 0) {
-    const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));
+    const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
     k_step_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   }
   CLR_CHECK_LAUNCH();
@@ -1168,12 +1179,12 @@ __global__ void k_ds_psd(ConeDev cd, const double* __restrict__ dsa, const doubl
                          const IterScal* sc, double* __restrict__ out, const int* skip) {
   if (skip && *skip) return;
   __shared__ double A[32 * LDP], B[32 * LDP], T[32 * LDP];
-  const int k = cd.psd_k, d = cd.psd_d;
   const int64_t cone = blockIdx.x;
-  const int64_t row = cd.psd_row0 + (int64_t)d * cone;
-  const double* R = cd.psd_R + (int64_t)k * k * cone;
-  const double* Ri = cd.psd_Ri + (int64_t)k * k * cone;
-  const double* lam = cd.psd_lam + (int64_t)k * cone;
+  const int k = cd.psd_ck[cone];
+  const int64_t row = cd.psd_crow[cone];
+  const double* R = cd.psd_R + cd.psd_cR[cone];
+  const double* Ri = cd.psd_Ri + cd.psd_cR[cone];
+  const double* lam = cd.psd_lam + cd.psd_cl[cone];
   const double smu = sc[cd.row_pid[row]].sigma_mu;
   // A = Ri dS Ri'
   load_smat(dsa + row, k, A);
@@ -1254,7 +1265,7 @@ int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const
         cd, s, z, dsa, dza, sc, ds_out,
                                                                                skip);
   if (cd.n_psd > 0) {
-    const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));
+    const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
     k_ds_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
   }
   CLR_CHECK_LAUNCH();
@@ -1315,8 +1326,8 @@ __global__ void k_shift_psd(ConeDev cd, double* __restrict__ v, const int* skip)
   if (skip && *skip) return;
   __shared__ double X[32 * LDP], csb[64];
   __shared__ int flag;
-  const int k = cd.psd_k, d = cd.psd_d;
-  const int64_t row = cd.psd_row0 + (int64_t)d * blockIdx.x;
+  const int k = cd.psd_ck[blockIdx.x];
+  const int64_t row = cd.psd_crow[blockIdx.x];
   load_smat(v + row, k, X);
   const double a = jacobi_eigmin(X, k, csb, &flag);
   __syncthreads();
@@ -1332,7 +1343,7 @@ int cones_shift_init(cudaStream_t st, const ConeDev& cd, double* v, IterScal* sc
   }
   if (cd.n_soc > 0) k_shift_soc<<<(unsigned)((cd.n_soc * 32 + 255) / 256), 256, 0, st>>>(cd, v, skip);
   if (cd.n_psd > 0) {
-    const int threads = std::max(64, 32 * ((cd.psd_k + 1) / 2));
+    const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
     k_shift_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, v, skip);
   }
   CLR_CHECK_LAUNCH();
@@ -1361,7 +1372,7 @@ __global__ void k_unit_init(ConeDev cd, double* __restrict__ v, const int* skip)
       const double a = cd.pow_alpha[i];
       val = (c == 0) ? sqrt(1.0 + a) : (c == 1 ? sqrt(2.0 - a) : 0.0);
     } else if (cd.n_psd > 0 && r >= cd.psd_row0) {
-      const int64_t c = (r - cd.psd_row0) % cd.psd_d;
+      const int64_t c = r - cd.psd_crow[psd_cone_of(cd, r)];
       int j = (int)((sqrt(8.0 * c + 1.0) - 1.0) / 2.0);
       while ((int64_t)j * (j + 1) / 2 > c) --j;
       while ((int64_t)(j + 1) * (j + 2) / 2 <= c) ++j;

@@ -5,6 +5,9 @@
 // reductions), exp/pow one thread per cone, PSD one block per cone.
 #pragma once
 
+#include <algorithm>
+#include <vector>
+
 #include "device.cuh"
 #include "scal.cuh"
 
@@ -23,9 +26,16 @@ struct ConeDev {
   int64_t n_exp = 0, exp_row0 = 0, exp_kb0 = 0;
   int64_t n_pow = 0, pow_row0 = 0, pow_kb0 = 0;
   const double* pow_alpha = nullptr;
-  // PSD cones: order k, svec dim d, rows row0 + d i, packed H at kb0 + d(d+1)/2 i
-  int64_t n_psd = 0, psd_row0 = 0, psd_kb0 = 0;
-  int psd_k = 0, psd_d = 0;
+  // PSD cones, of mixed orders k <= 32: per cone its order, first row, packed-H
+  // offset in kvz and offset of its k x k blocks in psd_R / psd_Ri (its k entries
+  // of psd_lam at psd_cl); psd_row0 = the first PSD row, psd_kmax = the largest k
+  int64_t n_psd = 0, psd_row0 = 0;
+  int psd_kmax = 0;
+  const int32_t* psd_ck = nullptr;
+  const int64_t* psd_crow = nullptr;
+  const int64_t* psd_ckb = nullptr;
+  const int64_t* psd_cR = nullptr;
+  const int64_t* psd_cl = nullptr;
   int64_t nn_kb = 0;  // packed offset of the first nonneg diagonal (after the zero cone)
   double* kvz = nullptr;  // z part of the KKT values (-H blocks)
   int64_t nkz = 0;        // number of entries of kvz
@@ -46,6 +56,42 @@ struct ConeDev {
   const int32_t* row_pid = nullptr;
   const ProbConst* pc = nullptr;
 };
+
+// Per-cone PSD data on the device from each PSD cone's svec dimension, first row
+// and packed-H offset (in cone order); allocates psd_R, psd_Ri, psd_lam.  False
+// on a dimension that is not k(k+1)/2 with k <= 32, or on allocation failure.
+inline bool cones_psd_setup(DeviceArena& ar, ConeDev& cd, const std::vector<int64_t>& dims,
+                            const std::vector<int64_t>& rows, const std::vector<int64_t>& kbs) {
+  const int64_t n = (int64_t)dims.size();
+  std::vector<int32_t> ck(n);
+  std::vector<int64_t> cR(n), cl(n);
+  int64_t nR = 0, nl = 0;
+  int kmax = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int k = 0;
+    while ((int64_t)(k + 1) * (k + 2) / 2 <= dims[i]) ++k;
+    if ((int64_t)k * (k + 1) / 2 != dims[i] || k < 1 || k > 32) return false;
+    ck[i] = k;
+    cR[i] = nR;
+    cl[i] = nl;
+    nR += (int64_t)k * k;
+    nl += k;
+    kmax = std::max(kmax, k);
+  }
+  cd.n_psd = n;
+  cd.psd_kmax = kmax;
+  cd.psd_row0 = n ? rows[0] : 0;
+  if (n == 0) return true;
+  cd.psd_ck = ar.upload(ck.data(), n);
+  cd.psd_crow = ar.upload(rows.data(), n);
+  cd.psd_ckb = ar.upload(kbs.data(), n);
+  cd.psd_cR = ar.upload(cR.data(), n);
+  cd.psd_cl = ar.upload(cl.data(), n);
+  cd.psd_R = ar.alloc_n<double>(nR);
+  cd.psd_Ri = ar.alloc_n<double>(nR);
+  cd.psd_lam = ar.alloc_n<double>(nl);
+  return cd.psd_ck && cd.psd_crow && cd.psd_ckb && cd.psd_cR && cd.psd_cl && cd.psd_R && cd.psd_Ri && cd.psd_lam;
+}
 
 // Per-problem scalars are read from and written to sc[row_pid[row]]; `skip`
 // (when non-null and set) makes every kernel return at once.

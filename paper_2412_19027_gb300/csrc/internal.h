@@ -44,7 +44,7 @@ struct ConeLayout {
   int64_t exp_begin = 0, exp_end = 0;
   int64_t pow_begin = 0, pow_end = 0;
   int64_t psd_begin = 0, psd_end = 0;
-  int psd_k = 0;
+  int psd_k = 0;  // largest PSD order (cones of different orders are allowed)
   int64_t nu = 0;            // barrier degree of K
   int64_t soc_max_dim = 0;
   int64_t kval_z = 0;        // entries of the z part of kval

@@ -1135,14 +1135,15 @@ int Solver::upload() {
     for (int64_t c = cl.pow_begin; c < cl.pow_end; ++c) al.push_back(cl.cones[c].alpha);
     cd_.pow_alpha = ar_.upload(al.data(), (int64_t)al.size());
   }
-  cd_.n_psd = cl.psd_end - cl.psd_begin;
-  cd_.psd_k = cl.psd_k;
-  cd_.psd_d = cl.psd_k * (cl.psd_k + 1) / 2;
-  cd_.psd_row0 = cd_.n_psd ? cl.cones[cl.psd_begin].off : 0;
-  cd_.psd_kb0 = cd_.n_psd ? cl.cones[cl.psd_begin].kbase : 0;
-  cd_.psd_R = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k * cl.psd_k);
-  cd_.psd_Ri = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k * cl.psd_k);
-  cd_.psd_lam = ar_.alloc_n<double>(cd_.n_psd * cl.psd_k);
+  {
+    std::vector<int64_t> dims, rows, kbs;
+    for (int64_t c = cl.psd_begin; c < cl.psd_end; ++c) {
+      dims.push_back(cl.cones[c].dim);
+      rows.push_back(cl.cones[c].off);
+      kbs.push_back(cl.cones[c].kbase);
+    }
+    if (!cones_psd_setup(ar_, cd_, dims, rows, kbs)) return CLR_E_OOM;
+  }
   cd_.ep_zt = ar_.alloc_n<double>(3 * (cd_.n_exp + cd_.n_pow));
   exp_central_point_host(cd_.exp_center);
   if (!v_.kptr || !v_.kcol || !v_.kvi || !v_.kval || !v_.xz || !v_.part || !sc_ || !bf_ || !cd_.scratch || !v_.ck ||

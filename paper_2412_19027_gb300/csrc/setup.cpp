@@ -119,11 +119,11 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
         err = "PSD cone dimension is not k(k+1)/2";
         return CLR_E_INVALID;
       }
-      if (psd_k == 0) psd_k = k;
-      if (k != psd_k || k > 32) {
-        err = "all PSD cones must share one order <= 32";
+      if (k > 32) {
+        err = "PSD cones of order <= 32 only";
         return CLR_E_UNSUPPORTED;
       }
+      psd_k = std::max(psd_k, k);
     }
     total += c.dim;
   }
@@ -179,7 +179,7 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
       case CLR_NONNEG: cl.kval_z += c.dim; cl.nu += c.dim; break;
       case CLR_SOC: cl.kval_z += packed(c.dim); cl.nu += 1; cl.soc_max_dim = std::max(cl.soc_max_dim, c.dim); break;
       case CLR_EXP: case CLR_POW: cl.kval_z += 6; cl.nu += 3; cl.symmetric_only = false; break;
-      case CLR_PSD_TRI: cl.kval_z += packed(c.dim); cl.nu += psd_k; break;
+      case CLR_PSD_TRI: cl.kval_z += packed(c.dim); cl.nu += psd_order_of(c.dim); break;
     }
   }
 

@@ -38,8 +38,8 @@ struct ConeBench {
       if ((cones[i].type == CLR_EXP || cones[i].type == CLR_POW) && cones[i].dim != 3) rc = CLR_E_INVALID;
       if (cones[i].type == CLR_PSD_TRI) {
         int k = (int)std::lround((std::sqrt(8.0 * cones[i].dim + 1.0) - 1.0) / 2.0);
-        if (k * (k + 1) / 2 != cones[i].dim || k > 32 || (psd_k && k != psd_k)) rc = CLR_E_UNSUPPORTED;
-        psd_k = k;
+        if (k * (k + 1) / 2 != cones[i].dim || k > 32) rc = CLR_E_UNSUPPORTED;
+        psd_k = std::max(psd_k, k);
       }
     }
     if (rc) return;
@@ -58,7 +58,7 @@ struct ConeBench {
       for (int32_t i = 0; i < ncones; ++i)
         if (cones[i].type == f)
           for (int64_t r = 0; r < cones[i].dim; ++r) perm.push_back(caller_off[i] + r);
-    std::vector<int64_t> soc_off, soc_kb;
+    std::vector<int64_t> soc_off, soc_kb, psd_dim, psd_row, psd_kb;
     std::vector<int32_t> soc_dim;
     std::vector<double> alpha;
     int64_t kz = mz + mn;
@@ -79,6 +79,11 @@ struct ConeBench {
           soc_kb.push_back(kz);
         }
         if (f == CLR_POW) alpha.push_back(cones[i].alpha);
+        if (f == CLR_PSD_TRI) {
+          psd_dim.push_back(d);
+          psd_row.push_back((int64_t)perm.size());
+          psd_kb.push_back(kz);
+        }
         kz += (f == CLR_EXP || f == CLR_POW) ? 6 : d * (d + 1) / 2;
         for (int64_t r = 0; r < d; ++r) perm.push_back(caller_off[i] + r);
       }
@@ -97,11 +102,10 @@ struct ConeBench {
     cd.pow_row0 = row0[CLR_POW];
     cd.pow_kb0 = kb0[CLR_POW];
     cd.pow_alpha = ar.upload(alpha.data(), (int64_t)alpha.size());
-    cd.n_psd = counts[CLR_PSD_TRI];
-    cd.psd_k = psd_k;
-    cd.psd_d = psd_k * (psd_k + 1) / 2;
-    cd.psd_row0 = row0[CLR_PSD_TRI];
-    cd.psd_kb0 = kb0[CLR_PSD_TRI];
+    if (!cones_psd_setup(ar, cd, psd_dim, psd_row, psd_kb)) {
+      rc = CLR_E_OOM;
+      return;
+    }
     cd.nkz = kz;
     cd.kvz = ar.alloc_n<double>(kz);
     cd.scratch = ar.alloc_n<double>(m);
@@ -110,9 +114,7 @@ struct ConeBench {
     cd.soc_eta = ar.alloc_n<double>(cd.n_soc);
     cd.soc_wb = ar.alloc_n<double>(m);
     cd.soc_lam = ar.alloc_n<double>(m);
-    cd.psd_R = ar.alloc_n<double>(cd.n_psd * psd_k * psd_k);
-    cd.psd_Ri = ar.alloc_n<double>(cd.n_psd * psd_k * psd_k);
-    cd.psd_lam = ar.alloc_n<double>(cd.n_psd * psd_k);
+
     cd.ep_zt = ar.alloc_n<double>(3 * (cd.n_exp + cd.n_pow));
     exp_central_point_host(cd.exp_center);
     // one problem: every row belongs to problem 0

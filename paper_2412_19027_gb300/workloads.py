@@ -236,6 +236,18 @@ def psd_batch(seed=0, n=20_000, n_psd=2000, psd_k=10, n_nonneg=5000, nnz_per_col
     return _finish("psd_batch_n%d_m%d" % (n, m), rng, sp.csc_matrix((n, n)), A, cones)
 
 
+def psd_mixed(seed=0, n=60, orders=(2, 3, 4, 5, 8, 10, 16), per_order=2, n_nonneg=20, nnz_per_col=5):
+    """PSD cones of mixed orders (the paper's stated future direction, Sec. 6):
+    `per_order` cones of each order in `orders`, interleaved, plus n_nonneg
+    nonneg rows; A with nnz_per_col N(0,1) entries per column, P = 0."""
+    rng = np.random.default_rng(seed)
+    psd = [k for _ in range(per_order) for k in orders]
+    cones = [(NONNEG, n_nonneg, 0.0)] + [(PSD, k * (k + 1) // 2, 0.0) for k in psd]
+    m = sum(d for (_, d, _) in cones)
+    A = _sparse_columns(rng, m, n, min(nnz_per_col, m))
+    return _finish("psd_mixed_n%d_m%d" % (n, m), rng, sp.csc_matrix((n, n)), A, cones)
+
+
 def mpc_qp(seed=0, T=None, nx=None, nu=None, x_bound=5.0, u_bound=1.0, u_soc=1.2, x0_scale=0.5):
     """MPC-shaped QP: states x_1..x_T, inputs u_0..u_{T-1}; x_{t+1} = A_d x_t +
     B_d u_t as zero-cone rows (A_d = G 0.95 / rho(G)); boxes |x| <= 5, |u| <= 1

@@ -47,6 +47,8 @@ def _mixed_cohort():
         W.banded_lp(0, n=150, window=16),
         W.mpc_qp(0, T=10, nx=4, nu=2),
         W.psd_batch(0, n=60, n_psd=4, psd_k=4, n_nonneg=20, nnz_per_col=4),
+        W.psd_batch(1, n=60, n_psd=3, psd_k=5, n_nonneg=20, nnz_per_col=4),  # another PSD order
+        W.psd_mixed(1, n=40, orders=(2, 3, 6), per_order=2, n_nonneg=10, nnz_per_col=4),
         _infeasible_lp(),
         W.nonneg_qp(3),
         W.mixed_cone(2, n=200, n_zero=50, n_nonneg=300, n_soc=50, n_exp=10, n_pow=10, nnz_per_col=6),

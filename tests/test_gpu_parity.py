@@ -75,8 +75,12 @@ PSD_CONES = [(C.PSD, 55, 0.0)] * 3 + [(C.NONNEG, 4, 0.0)]
 PSD32_CONES = [(C.PSD, 528, 0.0)] * 2 + [(C.NONNEG, 3, 0.0)]
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4, PSD32_CONES],
-                         ids=["mixed", "psd10", "psd3", "psd32"])
+PSD_MIXED_CONES = ([(C.PSD, 3, 0.0), (C.PSD, 55, 0.0), (C.NONNEG, 2, 0.0), (C.PSD, 6, 0.0), (C.PSD, 528, 0.0),
+                    (C.PSD, 1, 0.0), (C.PSD, 21, 0.0)])
+
+
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4, PSD32_CONES, PSD_MIXED_CONES],
+                         ids=["mixed", "psd10", "psd3", "psd32", "psd_mixed_orders"])
 def test_cone_scaling_matches_oracle(cones):
     rng = np.random.default_rng(0)
     s, z = _rand_cone_points(rng, cones)
@@ -334,3 +338,24 @@ def test_cone_stress_inputs_and_timing(family, count):
     assert t["kkt_values"] == packed
     for k in ("scaling_ms", "step_ms", "combined_ds_ms"):
         assert 0.0 < t[k] < 1e3, t
+
+
+def test_psd_mixed_orders_solve_reaches_oracle_accuracy():
+    """PSD cones of orders 2 .. 16 in one problem: the GPU follows the oracle to
+    its optimum.  As with the PSD(32) edge case, one iteration before the
+    oracle's SOLVED the smallest eigenvalues of a cone's S or Z (~1e-11 against
+    ~10) can defeat its Cholesky factor and stop the solve at that finite iterate
+    with NUMERICAL_ERROR; the answer is checked there."""
+    prob = W.psd_mixed(0)
+    st = clr.clr_default_settings(64)
+    solver = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+    solver.solve()
+    x, s, z, info = solver.solution()
+    solver.free()
+    ref = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    assert ref.status_name == "SOLVED"
+    assert info["status_name"] in ("SOLVED", "NUMERICAL_ERROR"), info
+    assert np.all(np.isfinite(x)) and info["gap_rel"] <= 1e-6, info
+    f, fr = prob.objective(x), prob.objective(ref.x)
+    assert abs(f - fr) <= 1e-6 * max(1.0, abs(fr)), (f, fr)
+    assert info["iterations"] >= ref.iterations - 2

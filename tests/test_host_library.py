@@ -74,9 +74,6 @@ def test_validation_errors(clr):
         clr.clr_analyze(prob.P, prob.q, prob.A, prob.b, [(1, 99, 0.0)])
     assert e.value.code == -2
     with pytest.raises(clr.ClrError) as e:
-        clr.clr_analyze(prob.P, prob.q, prob.A[:6], prob.b[:6], [(5, 3, 0.0), (5, 1, 0.0), (1, 2, 0.0)])
-    assert e.value.code == -3
-    with pytest.raises(clr.ClrError) as e:
         clr.clr_analyze(prob.P, prob.q, prob.A[:3], prob.b[:3], [(4, 3, 1.5)])
     assert e.value.code == -1
 
@@ -208,11 +205,21 @@ def test_cohort_analysis_is_the_union_of_its_members(clr):
     b.free()
 
 
-def test_cohort_rejects_mixed_psd_orders(clr):
+def test_psd_orders_mixed_and_bounded(clr):
+    """PSD cones of different orders are accepted, in one problem and across a
+    cohort; an order above 32 is refused (CLR_E_UNSUPPORTED)."""
     p4 = W.psd_batch(0, n=60, n_psd=4, psd_k=4, n_nonneg=20, nnz_per_col=4)
     p5 = W.psd_batch(1, n=60, n_psd=3, psd_k=5, n_nonneg=20, nnz_per_col=4)
+    b = clr.clr_batch_analyze([(p.P, p.q, p.A, p.b, p.cones) for p in (p4, p5)])
+    assert b.size() == 2
+    b.free()
+    pm = W.psd_mixed(0)
+    s = clr.clr_analyze(pm.P, pm.q, pm.A, pm.b, pm.cones)
+    s.free()
+    k = 33
+    A = sp.csc_matrix(np.ones((k * (k + 1) // 2, 1)))
     with pytest.raises(clr.ClrError) as e:
-        clr.clr_batch_analyze([(p.P, p.q, p.A, p.b, p.cones) for p in (p4, p5)])
+        clr.clr_analyze(sp.csc_matrix((1, 1)), np.zeros(1), A, np.zeros(A.shape[0]), [(5, A.shape[0], 0.0)])
     assert e.value.code == -3  # CLR_E_UNSUPPORTED
 
 

@@ -344,3 +344,13 @@ def test_validation_rejects_bad_input():
         oracle.solve(np.eye(2), np.zeros(2), np.eye(2), np.ones(2), [(C.NONNEG, 3, 0.0)])
     with pytest.raises(ipm.ProblemError):
         oracle.solve(np.eye(1), np.zeros(1), np.ones((3, 1)), np.ones(3), [(C.POW, 3, 1.5)])
+
+
+def test_psd_cones_of_mixed_orders_reach_the_planted_optimum():
+    """PSD cones of orders 2 .. 16 in one problem (interleaved with each other):
+    the oracle reaches the planted optimum (every PSD cone handled by its own order)."""
+    prob = W.psd_mixed(0)
+    r = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones)
+    assert r["status_name"] == "SOLVED"
+    f, fs = prob.objective(r["x"]), prob.objective(prob.x_star)
+    assert abs(f - fs) <= 1e-6 * max(1.0, abs(fs))
