@@ -259,7 +259,7 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
 // T~(p, i) is DX(p+1) when i = p + 1 is a pivot block (folded), else T(p, i).
 // dur: typical durations (microseconds) by kind D, T, Efin, U, EU, DX; span: the
 // simulated duration of the level.
-static bool flow_priority_order(std::vector<FlowTask>& tasks, int64_t t0, const std::vector<int64_t>& P_of,
+static bool flow_schedule_order(std::vector<FlowTask>& tasks, int64_t t0, const std::vector<int64_t>& P_of,
                                 int workers, const double* dur, double* span) {
   const int64_t n = (int64_t)tasks.size() - t0;
   *span = 0.0;
@@ -550,7 +550,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       pd.wl->pref = dbuf + pd.po;
     }
     // dataflow task tables (bigfront.cuh), per level: every task of every big front
-    // of the level, then ordered by flow_priority_order.  A pivot block p >= 1
+    // of the level, then ordered by flow_schedule_order.  A pivot block p >= 1
     // has the fused task DX(p) instead of D(p), T(p-1, p) and U(p-1, p, p).
     std::vector<FlowTask> tasks;
     std::vector<int64_t> soff(bf_f.size(), 0), P_of(bf_f.size(), 0);
@@ -596,8 +596,8 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       static const double dur1[6] = {20.0, 6.5, 5.3, 5.8, 6.1, 25.0};
       std::vector<FlowTask> one(tasks.begin() + st.flow_t0[l], tasks.end());
       double span2 = 0.0, span1 = 0.0;
-      if (!flow_priority_order(tasks, st.flow_t0[l], P_of, 2 * flow_sms, dur2, &span2) ||
-          !flow_priority_order(one, 0, P_of, flow_sms, dur1, &span1))
+      if (!flow_schedule_order(tasks, st.flow_t0[l], P_of, 2 * flow_sms, dur2, &span2) ||
+          !flow_schedule_order(one, 0, P_of, flow_sms, dur1, &span1))
         return CLR_E_INVALID;
       st.flow_one[l] = span1 < 0.97 * span2 ? 1 : 0;
       if (st.flow_one[l]) std::copy(one.begin(), one.end(), tasks.begin() + st.flow_t0[l]);

@@ -29,7 +29,6 @@ struct ConeBench {
 
   ConeBench(const clr_cone* cones, int32_t ncones) {
     int64_t total = 0;
-    int psd_k = 0;
     caller_off.resize(ncones);
     for (int32_t i = 0; i < ncones; ++i) {
       caller_off[i] = total;
@@ -39,7 +38,6 @@ struct ConeBench {
       if (cones[i].type == CLR_PSD_TRI) {
         int k = (int)std::lround((std::sqrt(8.0 * cones[i].dim + 1.0) - 1.0) / 2.0);
         if (k * (k + 1) / 2 != cones[i].dim || k > 32) rc = CLR_E_UNSUPPORTED;
-        psd_k = std::max(psd_k, k);
       }
     }
     if (rc) return;

@@ -346,3 +346,24 @@ def test_third_order_correction_identity(t, a):
         e1 = C.third_order_correction(t, z, dz, ds, a)
         e2 = C.third_order_correction(t, z, 2.0 * dz, ds, a)
         np.testing.assert_allclose(e2, 2.0 * e1, rtol=1e-10, atol=1e-12)
+
+
+def test_failed_shadow_falls_back_and_leaves_the_neighbourhood(monkeypatch):
+    """Where z~ = -grad f*(s) cannot be evaluated (a singular Newton system near the
+    boundary of the cone), the BFGS scaling is H_a = mu grad^2 f(z) and the trial
+    point counts as outside N(beta) -- exercised by making the Newton solve fail."""
+    s = np.array([-0.5, 1.0, 2.0])          # interior of the exponential cone
+    z = np.array([-1.0, 0.3, 1.5])          # interior of its dual
+    assert C.in_int_primal(C.EXP, s) and C.in_int_dual(C.EXP, z)
+    mu = 0.7
+    H_ok = C.bfgs_scaling(C.EXP, s, z, mu)
+    assert C.neighbourhood_ok(C.EXP, s, z, mu, 1e-6)
+
+    def singular(*args, **kwargs):
+        raise np.linalg.LinAlgError("Singular matrix")
+
+    monkeypatch.setattr(C, "dual_shadow", singular)
+    H_fb = C.bfgs_scaling(C.EXP, s, z, mu)
+    np.testing.assert_allclose(H_fb, mu * C.barrier_hess(C.EXP, z), rtol=1e-14)
+    assert not np.allclose(H_fb, H_ok)      # the fallback is a different matrix here
+    assert C.neighbourhood_ok(C.EXP, s, z, mu, 1e-6) is False
