@@ -627,7 +627,40 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
     for (int64_t ch : big) is_pushed[ch] = 1;
     pushed[P] = std::move(big);
   }
-  std::vector<std::pair<int64_t, int64_t>> contrib;  // (target, source)
+  std::vector<std::pair<int64_t, int64_t>> contrib, ctmp;  // (target, source)
+  std::vector<int64_t> cnt;
+  // counting pass: stable reorder of v by key(target) in [0, nb)
+  auto count_pass = [&](std::vector<std::pair<int64_t, int64_t>>& from, std::vector<std::pair<int64_t, int64_t>>& to,
+                        int64_t nb, auto key) {
+    cnt.assign(nb + 1, 0);
+    for (const auto& x : from) ++cnt[key(x.first) + 1];
+    for (int64_t k = 0; k < nb; ++k) cnt[k + 1] += cnt[k];
+    to.resize(from.size());
+    for (const auto& x : from) to[cnt[key(x.first)]++] = x;
+  };
+  // stable sort by target of targets base + la + lb fP (2-D) or base + la (1-D)
+  auto sort_by_target = [&](std::vector<std::pair<int64_t, int64_t>>& v, int64_t base, int64_t fP, bool two_d) {
+    if (v.size() < 2) return;
+    if (!two_d) {
+      count_pass(v, ctmp, fP, [&](int64_t t) { return t - base; });
+      v.swap(ctmp);
+      return;
+    }
+    count_pass(v, ctmp, fP, [&](int64_t t) { return (t - base) % fP; });
+    count_pass(ctmp, v, fP, [&](int64_t t) { return (t - base) / fP; });
+  };
+  {
+    // exact sizes of the source lists (the pulls), so they are filled without regrowth
+    int64_t nfa = 0, nsv = 0;
+    for (int64_t J = 0; J < sy.nsn; ++J) {
+      if (sy.sn_parent[J] < 0) continue;
+      const int64_t u = upd_rows(J);
+      nsv += u;
+      if (!is_pushed[J]) nfa += u * (u + 1) / 2;
+    }
+    mp.fa_src.reserve(nfa);
+    mp.sv_src.reserve(nsv);
+  }
   for (int64_t l = 0; l < sy.nlev; ++l) {
     int64_t rounds = 0;
     for (int64_t t = sy.lev_ptr[l]; t < sy.lev_ptr[l + 1]; ++t) rounds = std::max<int64_t>(rounds, (int64_t)pushed[sy.lev_sn[t]].size());
@@ -653,6 +686,12 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
       }
       // factor: U_c entries (a >= b) -> F_P(loc(row a), loc(row b)), for the children not pushed
       contrib.clear();
+      {
+        int64_t ne = 0;
+        for (int64_t ch : children[P])
+          if (!is_pushed[ch]) ne += upd_rows(ch) * (upd_rows(ch) + 1) / 2;
+        contrib.reserve(ne);
+      }
       for (int64_t ch : children[P]) {
         if (is_pushed[ch]) continue;
         const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
@@ -666,10 +705,10 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
           }
         }
       }
-      std::stable_sort(contrib.begin(), contrib.end(),
-                       [](const std::pair<int64_t, int64_t>& x, const std::pair<int64_t, int64_t>& y) {
-                         return x.first < y.first;
-                       });
+      // stable sort by target: targets are positions (row la, column lb) of P's
+      // fP x fP front, so two stable counting passes -- by row, then by column --
+      // order them as a comparison sort would, equal targets in insertion order
+      sort_by_target(contrib, sy.front_off[P], fP, true);
       for (size_t q = 0; q < contrib.size(); ++q) {
         if (q == 0 || contrib[q].first != contrib[q - 1].first) {
           mp.fa_tgt.push_back(contrib[q].first);
@@ -685,10 +724,7 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
         const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
         for (int64_t a = c; a < f; ++a) contrib.emplace_back(sy.upd_off[P] + loc[rr[a]], sy.upd_off[ch] + a);
       }
-      std::stable_sort(contrib.begin(), contrib.end(),
-                       [](const std::pair<int64_t, int64_t>& x, const std::pair<int64_t, int64_t>& y) {
-                         return x.first < y.first;
-                       });
+      sort_by_target(contrib, sy.upd_off[P], fP, false);  // targets: P's fP work slots
       for (size_t q = 0; q < contrib.size(); ++q) {
         if (q == 0 || contrib[q].first != contrib[q - 1].first) {
           mp.sv_tgt.push_back(contrib[q].first);
