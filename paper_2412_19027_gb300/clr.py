@@ -263,10 +263,14 @@ class Solver:
             self.h = C.c_void_p()
 
     def solve(self):
+        """clr_solve: run Algorithm 1 from its initial point to a stopping status;
+        returns the status code (STATUS maps it to a name)."""
         _check(_lib().clr_solve(self.h), "clr_solve")
         return self.info()["status"]
 
     def info(self):
+        """The clr_info of the last solve as a dict (status, status_name,
+        iterations, residuals, gap, refinement and escalation counters)."""
         inf = clr_info()
         _check(_lib().clr_get_solution(self.h, None, None, None, C.byref(inf)), "clr_get_solution")
         d = {name: getattr(inf, name) for name, _ in clr_info._fields_}
@@ -274,6 +278,7 @@ class Solver:
         return d
 
     def solution(self):
+        """(x, s, z, info) of the last solve, unscaled, in the caller's row order."""
         x, s, z = np.empty(self.n), np.empty(self.m), np.empty(self.m)
         inf = clr_info()
         _check(_lib().clr_get_solution(self.h, _dptr(x), _dptr(s), _dptr(z), C.byref(inf)), "clr_get_solution")
@@ -282,6 +287,7 @@ class Solver:
         return x, s, z, d
 
     def update_qb(self, q, b):
+        """New q (n) and b (m, caller's row order); the next solve uses them."""
         q = np.ascontiguousarray(q, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         _check(_lib().clr_update_qb(self.h, _dptr(q), _dptr(b)), "clr_update_qb")
@@ -302,19 +308,26 @@ class Solver:
             _check(_lib().clr_batch_update_PA(self.h, i, ptr(Pv), ptr(Av)), "clr_batch_update_PA")
 
     def set_stream(self, stream_ptr):
+        """Run the solver's work on the given CUDA stream (a cudaStream_t as an int)."""
         _check(_lib().clr_set_stream(self.h, C.c_void_p(stream_ptr)), "clr_set_stream")
 
     def symbolic_stats(self):
+        """Sizes of the symbolic factorization (KKT order, nnz(L), factor flops,
+        supernodes, levels, largest front, chosen ordering) as a dict."""
         s = clr_symbolic_stats()
         _check(_lib().clr_get_symbolic_stats(self.h, C.byref(s)), "clr_get_symbolic_stats")
         return {name: getattr(s, name) for name, _ in clr_symbolic_stats._fields_}
 
     def perf(self):
+        """Device time by phase (init, residuals+cones, factorization, solves+steps,
+        ms) and counts (factorizations, kernel launches, factor flops) as a dict."""
         s = clr_perf()
         _check(_lib().clr_get_perf(self.h, C.byref(s)), "clr_get_perf")
         return {name: getattr(s, name) for name, _ in clr_perf._fields_}
 
     def symbolic(self):
+        """The symbolic factorization: elimination order, supernode column ranges,
+        parents, front row lists and the constraint-row permutation (numpy arrays)."""
         st = self.symbolic_stats()
         N, nsn = st["kkt_dim"], st["n_supernodes"]
         L = C.POINTER(C.c_int64)
@@ -328,11 +341,14 @@ class Solver:
         return dict(perm=perm, sn_ptr=snp, sn_parent=par, row_ptr=rp, rows=rows, row_perm=rowperm)
 
     def scaling(self):
+        """Equilibration of the setup: D (n), E (m, reordered rows) and the cost scale c."""
         D, E, c = np.empty(self.n), np.empty(self.m), C.c_double()
         _check(_lib().clr_get_scaling(self.h, _dptr(D), _dptr(E), C.byref(c)), "clr_get_scaling")
         return D, E, c.value
 
     def history(self):
+        """Per-iteration log of the last solve, rows of (iter, mu, pcost, dcost, res_p,
+        res_d, gap, alpha_a, sigma, alpha_c, ir_steps, tau)."""
         cap = self.settings.max_iter + 2
         out = np.zeros((cap, 12))
         rows = C.c_int32()
@@ -380,14 +396,17 @@ class Batch(Solver):
         self.patterns = pats
 
     def size(self):
+        """Number of problems in the cohort."""
         return _lib().clr_batch_size(self.h)
 
     def info_of(self, i):
+        """info of problem i after a solve."""
         inf = clr_info()
         _check(_lib().clr_batch_get(self.h, i, None, None, None, C.byref(inf)), "clr_batch_get")
         return _info_dict(inf)
 
     def solution_of(self, i):
+        """(x, s, z, info) of problem i, as Solver.solution for a single problem."""
         n, m = self.sizes[i]
         x, s, z = np.empty(n), np.empty(m), np.empty(m)
         inf = clr_info()
@@ -395,11 +414,13 @@ class Batch(Solver):
         return x, s, z, _info_dict(inf)
 
     def update_qb_of(self, i, q, b):
+        """New q and b for problem i of the cohort."""
         q = np.ascontiguousarray(q, dtype=np.float64)
         b = np.ascontiguousarray(b, dtype=np.float64)
         _check(_lib().clr_batch_update_qb(self.h, i, _dptr(q), _dptr(b)), "clr_batch_update_qb")
 
     def update_PA_of(self, i, P=None, A=None):
+        """New values of P and/or A for problem i (the patterns it was set up with)."""
         self._update_PA(i, P, A)
 
 
@@ -452,6 +473,7 @@ class Server:
         self.sizes = {}
 
     def submit(self, req):
+        """Queue a Request (deep-copied by the server); returns its ticket."""
         t = C.c_uint64()
         _check(_lib().clr_server_submit(self.h, C.byref(req.prob), C.byref(t)), "clr_server_submit")
         self.sizes[t.value] = (req.n, req.m)
@@ -469,17 +491,21 @@ class Server:
         return x, s, z, _info_dict(inf)
 
     def poll(self, ticket):
+        """(x, s, z, info) of a finished request, or None while it runs."""
         return self._result(_lib().clr_server_poll, ticket)
 
     def wait(self, ticket, timeout_s=60.0):
+        """Block until the request finishes (None after timeout_s seconds)."""
         return self._result(_lib().clr_server_wait, ticket, C.c_double(timeout_s))
 
     def stats(self):
+        """Server counters (requests, cohorts, device memory in use and peak) as a dict."""
         s = clr_server_stats()
         _check(_lib().clr_server_get_stats(self.h, C.byref(s)), "clr_server_get_stats")
         return {name: getattr(s, name) for name, _ in clr_server_stats._fields_}
 
     def close(self):
+        """Finish the requests in flight and release the server."""
         if getattr(self, "h", None) and self.h.value:
             _lib().clr_server_destroy(self.h)
             self.h = C.c_void_p()
@@ -494,10 +520,13 @@ def _is_upper(P):
 
 
 def clr_setup(P_upper, q, A, b, cones, settings=None):
+    """Set up a solver on the current GPU (host analysis, then device buffers)."""
     return Solver(P_upper, q, A, b, cones, settings, device=True)
 
 
 def clr_analyze(P_upper, q, A, b, cones, settings=None):
+    """The host analysis only (validation, equilibration, ordering, symbolic
+    factorization); no device memory, usable without a GPU."""
     return Solver(P_upper, q, A, b, cones, settings, device=False)
 
 
