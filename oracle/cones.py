@@ -255,12 +255,51 @@ def barrier_third(ctype, z, alpha=0.0):
     return T
 
 
+def _exp_dual_shadow(s):
+    """z_tilde = (r, v, t) in int K*_exp with -grad f(z_tilde) = s = (x, y, z), for the
+    dual barrier f = -log(psi) - log(-r) - log(t), psi = v - r - r log(t / (-r)).
+
+    The three equations reduce to one in rho = -r > 0 (derived from the gradient):
+        y: 1/psi = y;   z: (1 + rho y) / t = z;   x: y log(rho z / (1 + rho y)) - 1/rho = x,
+    whose left side increases in rho from -inf to y log(z/y) > x (s interior), so the
+    root is unique; it is bracketed by doubling and found by bisection on log(rho),
+    which stays accurate when s nears the boundary (rho ~ 2 / (y log(z/y) - x))."""
+    x, y, z = (float(v) for v in s)
+    gap = y * math.log(z / y) - x
+    if not (y > 0.0 and z > 0.0 and gap > 0.0):
+        raise ValueError("s is not in the interior of the exponential cone")
+
+    def g(rho):
+        return y * (math.log(rho * z) - math.log1p(rho * y)) - 1.0 / rho - x
+
+    lo, hi = 1.0, 1.0
+    while g(lo) > 0.0:
+        lo *= 0.5
+    while g(hi) < 0.0:
+        hi *= 2.0
+    for _ in range(200):
+        mid = math.sqrt(lo * hi)
+        if g(mid) < 0.0:
+            lo = mid
+        else:
+            hi = mid
+        if hi <= lo * (1.0 + 1e-15):
+            break
+    rho = math.sqrt(lo * hi)
+    t = (1.0 + rho * y) / z
+    v = 1.0 / y - rho - rho * math.log(t / rho)
+    return np.array([-rho, v, t])
+
+
 def dual_shadow(ctype, s, alpha=0.0, tol=1e-28, max_iter=100):
     """z_tilde = -grad f*(s): the point of int K* with -grad f(z_tilde) = s.
 
-    Damped Newton on phi(u) = f(u) + <s, u>, whose minimiser satisfies
-    grad f(u) = -s.  The step 1/(1 + lambda) (lambda = Newton decrement) keeps
+    Exponential cone: the one-dimensional reduction of _exp_dual_shadow.  Power
+    cone: damped Newton on phi(u) = f(u) + <s, u>, whose minimiser satisfies
+    grad f(u) = -s; the step 1/(1 + lambda) (lambda = Newton decrement) keeps
     u inside int K* for a self-concordant f.  Starts at the central point."""
+    if ctype == EXP:
+        return _exp_dual_shadow(s)
     u = central_point(ctype, 3, alpha)
     for _ in range(max_iter):
         g = barrier_grad(ctype, u, alpha) + s
@@ -460,9 +499,15 @@ def bfgs_scaling(ctype, s, z, mu, alpha=0.0):
 
 
 def third_order_correction(ctype, z, dz, ds, alpha=0.0):
-    """eta = -1/2 grad^3 f(z)[dz, (grad^2 f(z))^{-1} ds]  (Eq. higher-order-correction)."""
+    """eta = -1/2 grad^3 f(z)[dz, (grad^2 f(z))^{-1} ds]  (Eq. higher-order-correction).
+
+    Where grad^2 f(z) is singular in floating point (z at the boundary of the dual
+    cone to rounding) the term is dropped: eta = 0 for that cone."""
     T = barrier_third(ctype, z, alpha)
-    u = np.linalg.solve(barrier_hess(ctype, z, alpha), ds)
+    try:
+        u = np.linalg.solve(barrier_hess(ctype, z, alpha), ds)
+    except np.linalg.LinAlgError:
+        return np.zeros(3)
     return -0.5 * np.einsum("ijk,j,k->i", T, dz, u)
 
 

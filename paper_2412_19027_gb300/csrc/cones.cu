@@ -1149,10 +1149,12 @@ __global__ void k_ds_exppow(ConeDev cd, const double* __restrict__ s, const doub
   const int64_t row = is_exp ? cd.exp_row0 + 3 * i : cd.pow_row0 + 3 * i;
   const double a = is_exp ? 0.0 : cd.pow_alpha[i];
   const double zv[3] = {z[row], z[row + 1], z[row + 2]};
-  double g[3], H[3][3], u[3];
+  double g[3], H[3][3], u[3] = {0.0, 0.0, 0.0};
   barrier_grad(is_exp, zv, a, g);
   barrier_hess(is_exp, zv, a, H);
   const double dsv[3] = {dsa[row], dsa[row + 1], dsa[row + 2]}, dzv[3] = {dza[row], dza[row + 1], dza[row + 2]};
+  // a Hessian that is not positive definite in floating point (z at the boundary of
+  // the dual cone to rounding) leaves u = 0: the third-order term is dropped
   spd3_solve(H, dsv, u);
   // eta = -1/2 sum_jk T_ijk dz_j u_k with T the third derivative of f
   Psi P;

@@ -367,3 +367,29 @@ def test_failed_shadow_falls_back_and_leaves_the_neighbourhood(monkeypatch):
     np.testing.assert_allclose(H_fb, mu * C.barrier_hess(C.EXP, z), rtol=1e-14)
     assert not np.allclose(H_fb, H_ok)      # the fallback is a different matrix here
     assert C.neighbourhood_ok(C.EXP, s, z, mu, 1e-6) is False
+
+
+def test_exp_dual_shadow_near_the_boundary():
+    """The one-dimensional reduction keeps -grad f(z_tilde) = s as s approaches the
+    boundary of the exponential cone (where z_tilde grows like 2 / (y log(z/y) - x))."""
+    y, x = 0.05, 0.15
+    for rel in (1e-2, 1e-5, 1e-8, 1e-10):
+        s = np.array([x, y, y * math.exp(x / y) * (1.0 + rel)])
+        u = C.dual_shadow(C.EXP, s)
+        assert C.in_int_dual(C.EXP, u)
+        np.testing.assert_allclose(-C.barrier_grad(C.EXP, u), s, rtol=1e-9, atol=1e-12)
+        gap = y * math.log(s[2] / y) - x
+        assert -u[0] == pytest.approx(2.0 / gap, rel=0.05 + 10 * gap)
+
+
+def test_third_order_correction_dropped_on_singular_hessian(monkeypatch):
+    z = np.array([-1.0, 0.3, 1.5])
+    dz, ds = np.array([0.1, -0.2, 0.3]), np.array([0.2, 0.1, -0.1])
+    eta = C.third_order_correction(C.EXP, z, dz, ds)
+    assert np.abs(eta).max() > 0
+
+    def singular(*args, **kwargs):
+        raise np.linalg.LinAlgError("Singular matrix")
+
+    monkeypatch.setattr(C.np.linalg, "solve", singular)
+    np.testing.assert_array_equal(C.third_order_correction(C.EXP, z, dz, ds), np.zeros(3))
