@@ -181,8 +181,10 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
     if (Lp.size() > 1) {
       std::unordered_map<uint64_t, std::vector<int64_t>> buckets;
       for (int64_t i : Lp) {
-        std::sort(E[i].begin(), E[i].end());
-        std::sort(A[i].begin(), A[i].end());
+        // E[i] is sorted but for the element p just appended, A[i] is sorted (compaction
+        // keeps the order): one insertion instead of a sort
+        std::vector<int64_t>& Ei = E[i];
+        if (!Ei.empty()) std::rotate(std::upper_bound(Ei.begin(), Ei.end() - 1, Ei.back()), Ei.end() - 1, Ei.end());
         uint64_t h = 1469598103934665603ull;
         for (int64_t e : E[i]) h = (h ^ (uint64_t)e) * 1099511628211ull;
         h = (h ^ 0x9e3779b97f4a7c15ull) * 1099511628211ull;
@@ -197,11 +199,9 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
           for (size_t b2 = a + 1; b2 < g.size(); ++b2) {
             int64_t j = g[b2];
             if (status[j] != VAR) continue;
-            // i and j are adjacent to each other only through elements (A lists exclude L_p)
-            std::vector<int64_t> Ai = A[i], Aj = A[j];
-            Ai.erase(std::remove(Ai.begin(), Ai.end(), j), Ai.end());
-            Aj.erase(std::remove(Aj.begin(), Aj.end(), i), Aj.end());
-            if (E[i] == E[j] && Ai == Aj) {
+            // i and j are adjacent to each other only through elements (the A lists
+            // exclude L_p, to which both belong), so their lists compare as they are
+            if (E[i] == E[j] && A[i] == A[j]) {
               nv[i] += nv[j];
               deg[i] = std::max<int64_t>(deg[i] - nv[j], 0);
               nv[j] = 0;
