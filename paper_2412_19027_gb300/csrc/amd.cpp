@@ -83,7 +83,7 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
   for (int64_t i = 0; i < N; ++i)
     if (status[i] == VAR) dl.insert(i, deg[i]);
 
-  std::vector<int64_t> mark(N, -1), wtag(N, -1), wval(N, 0);
+  std::vector<int64_t> mark(N, -1), wtag(N, -1), wval(N, 0), ew(N, 0);
   int64_t tag = 0;
   int64_t nleft = N - n_dense;  // weighted count of uneliminated variables
   std::vector<int64_t> Lp;
@@ -121,24 +121,17 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
     std::vector<int64_t>().swap(members[p]);
     nleft -= nv[p];
     Le[p] = Lp;
+    ew[p] = wLp;
 
     // ---- |L_e \ L_p| for every element e adjacent to L_p ----
     for (int64_t i : Lp) {
       for (int64_t e : E[i]) {
         if (status[e] != ELEM || e == p) continue;
         if (wtag[e] != tag) {
+          // |L_e| (weighted) is fixed for the life of e: a variable of L_e that is
+          // eliminated absorbs e, and a merge moves weight between two members
           wtag[e] = tag;
-          // prune L_e to live variables and take its weight
-          std::vector<int64_t>& le = Le[e];
-          int64_t w = 0;
-          size_t o = 0;
-          for (size_t t = 0; t < le.size(); ++t)
-            if (status[le[t]] == VAR) {
-              le[o++] = le[t];
-              w += nv[le[t]];
-            }
-          le.resize(o);
-          wval[e] = w;
+          wval[e] = ew[e];
         }
         wval[e] -= nv[i];
       }
