@@ -17,7 +17,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
-#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
@@ -27,6 +26,14 @@ namespace clr {
 namespace {
 
 enum { VAR = 0, ELEM = 1, MERGED = 2, DEAD = 3, DENSE = 4 };
+
+// splitmix64 finaliser: spreads an index over 64 bits for the order-free list hash
+inline uint64_t mix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ull;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+  return x ^ (x >> 31);
+}
 
 struct DegreeLists {
   std::vector<int64_t> head, next, prev;
@@ -86,7 +93,9 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
   std::vector<int64_t> mark(N, -1), wtag(N, -1), wval(N, 0), ew(N, 0);
   int64_t tag = 0;
   int64_t nleft = N - n_dense;  // weighted count of uneliminated variables
-  std::vector<int64_t> Lp;
+  std::vector<int64_t> Lp, group;
+  std::vector<uint64_t> hv(N, 0);
+  std::vector<std::pair<uint64_t, int64_t>> hashed;
   while (nleft > 0) {
     // ---- select pivot of minimum approximate degree ----
     while (dl.mindeg <= N && dl.head[dl.mindeg] < 0) ++dl.mindeg;
@@ -142,6 +151,7 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
       std::vector<int64_t>& Ei = E[i];
       int64_t ext = 0;
       size_t o = 0;
+      uint64_t h = 0;  // order-free hash of E[i] and A[i] for the supervariable test
       for (size_t t = 0; t < Ei.size(); ++t) {
         int64_t e = Ei[t];
         if (status[e] != ELEM || e == p) continue;
@@ -152,9 +162,11 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
         }
         Ei[o++] = e;
         ext += (wtag[e] == tag) ? wval[e] : 0;
+        h += mix64((uint64_t)e);
       }
       Ei.resize(o);
       Ei.push_back(p);
+      h += mix64((uint64_t)p);
       std::vector<int64_t>& Ai = A[i];
       int64_t wA = 0;
       o = 0;
@@ -163,8 +175,10 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
         if (status[v] != VAR || mark[v] == tag || v == i) continue;  // covered by element p
         Ai[o++] = v;
         wA += nv[v];
+        h += mix64((uint64_t)v ^ 0x9e3779b97f4a7c15ull);
       }
       Ai.resize(o);
+      hv[i] = h;
       const int64_t lp_i = wLp - nv[i];
       int64_t d = std::min(nleft - nv[i], deg[i] + lp_i);
       d = std::min(d, wA + lp_i + ext);
@@ -172,20 +186,24 @@ void amd_order(int64_t N, const std::vector<int64_t>& ptr, const std::vector<int
     }
     // ---- supervariables: merge variables of L_p with identical adjacency ----
     if (Lp.size() > 1) {
-      std::unordered_map<uint64_t, std::vector<int64_t>> buckets;
-      for (int64_t i : Lp) {
+      // candidates grouped by the hash taken in the update above (a group keeps the
+      // order of L_p; equal lists always share a group, and only equal lists merge)
+      hashed.clear();
+      for (size_t t = 0; t < Lp.size(); ++t) {
         // E[i] is sorted but for the element p just appended, A[i] is sorted (compaction
         // keeps the order): one insertion instead of a sort
-        std::vector<int64_t>& Ei = E[i];
+        std::vector<int64_t>& Ei = E[Lp[t]];
         if (!Ei.empty()) std::rotate(std::upper_bound(Ei.begin(), Ei.end() - 1, Ei.back()), Ei.end() - 1, Ei.end());
-        uint64_t h = 1469598103934665603ull;
-        for (int64_t e : E[i]) h = (h ^ (uint64_t)e) * 1099511628211ull;
-        h = (h ^ 0x9e3779b97f4a7c15ull) * 1099511628211ull;
-        for (int64_t v : A[i]) h = (h ^ (uint64_t)v) * 1099511628211ull;
-        buckets[h].push_back(i);
+        hashed.emplace_back(hv[Lp[t]], (int64_t)t);
       }
-      for (auto& kv : buckets) {
-        std::vector<int64_t>& g = kv.second;
+      std::sort(hashed.begin(), hashed.end());
+      for (size_t g0 = 0; g0 < hashed.size();) {
+        size_t g1 = g0 + 1;
+        while (g1 < hashed.size() && hashed[g1].first == hashed[g0].first) ++g1;
+        group.clear();
+        for (size_t t = g0; t < g1; ++t) group.push_back(Lp[hashed[t].second]);
+        g0 = g1;
+        const std::vector<int64_t>& g = group;
         for (size_t a = 0; a < g.size(); ++a) {
           int64_t i = g[a];
           if (status[i] != VAR) continue;
