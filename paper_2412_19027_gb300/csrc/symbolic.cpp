@@ -628,7 +628,9 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
     pushed[P] = std::move(big);
   }
   std::vector<std::pair<int64_t, int64_t>> contrib, ctmp;  // (target, source)
-  std::vector<int64_t> cnt;
+  std::vector<int64_t> cnt, tcount;
+  // fronts up to this many entries get their pull lists by direct placement
+  constexpr int64_t kDirectTargets = (int64_t)1 << 26;
   // counting pass: stable reorder of v by key(target) in [0, nb)
   auto count_pass = [&](std::vector<std::pair<int64_t, int64_t>>& from, std::vector<std::pair<int64_t, int64_t>>& to,
                         int64_t nb, auto key) {
@@ -685,36 +687,68 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
         for (int64_t a = c; a < f; ++a) mp.rel.push_back((int32_t)loc[rr[a]]);
       }
       // factor: U_c entries (a >= b) -> F_P(loc(row a), loc(row b)), for the children not pushed
-      contrib.clear();
-      {
-        int64_t ne = 0;
-        for (int64_t ch : children[P])
-          if (!is_pushed[ch]) ne += upd_rows(ch) * (upd_rows(ch) + 1) / 2;
+      int64_t ne = 0;
+      for (int64_t ch : children[P])
+        if (!is_pushed[ch]) ne += upd_rows(ch) * (upd_rows(ch) + 1) / 2;
+      if (ne > 0 && fP * fP <= kDirectTargets) {
+        // two passes straight into the lists: count the sources of every target of
+        // P's front, then place each source at its target's next slot -- targets in
+        // increasing order, each target's sources in child / column / row order, as
+        // the sorted pairs below give them
+        std::vector<int64_t>& cntT = tcount;
+        cntT.assign((size_t)(fP * fP), 0);
+        auto each = [&](auto&& fn) {
+          for (int64_t ch : children[P]) {
+            if (is_pushed[ch]) continue;
+            const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+            const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+            const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+            for (int64_t b = c; b < f; ++b) {
+              const int64_t lb = loc[rr[b]];
+              for (int64_t a = b; a < f; ++a) fn(loc[rr[a]] + lb * fP, sy.front_off[ch] + a + b * f);
+            }
+          }
+        };
+        each([&](int64_t t, int64_t) { ++cntT[t]; });
+        const int64_t s0 = (int64_t)mp.fa_src.size();
+        int64_t pos = s0;
+        for (int64_t t = 0; t < fP * fP; ++t) {
+          if (!cntT[t]) continue;
+          mp.fa_tgt.push_back(sy.front_off[P] + t);
+          mp.fa_ptr.push_back(pos);
+          const int64_t k = cntT[t];
+          cntT[t] = pos;
+          pos += k;
+        }
+        mp.fa_src.resize(pos);
+        each([&](int64_t t, int64_t src) { mp.fa_src[cntT[t]++] = src; });
+      } else if (ne > 0) {
+        contrib.clear();
         contrib.reserve(ne);
-      }
-      for (int64_t ch : children[P]) {
-        if (is_pushed[ch]) continue;
-        const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
-        const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
-        const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
-        for (int64_t b = c; b < f; ++b) {
-          int64_t lb = loc[rr[b]];
-          for (int64_t a = b; a < f; ++a) {
-            int64_t la = loc[rr[a]];
-            contrib.emplace_back(sy.front_off[P] + la + lb * fP, sy.front_off[ch] + a + b * f);
+        for (int64_t ch : children[P]) {
+          if (is_pushed[ch]) continue;
+          const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+          const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+          const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+          for (int64_t b = c; b < f; ++b) {
+            int64_t lb = loc[rr[b]];
+            for (int64_t a = b; a < f; ++a) {
+              int64_t la = loc[rr[a]];
+              contrib.emplace_back(sy.front_off[P] + la + lb * fP, sy.front_off[ch] + a + b * f);
+            }
           }
         }
-      }
-      // stable sort by target: targets are positions (row la, column lb) of P's
-      // fP x fP front, so two stable counting passes -- by row, then by column --
-      // order them as a comparison sort would, equal targets in insertion order
-      sort_by_target(contrib, sy.front_off[P], fP, true);
-      for (size_t q = 0; q < contrib.size(); ++q) {
-        if (q == 0 || contrib[q].first != contrib[q - 1].first) {
-          mp.fa_tgt.push_back(contrib[q].first);
-          mp.fa_ptr.push_back((int64_t)mp.fa_src.size());
+        // stable sort by target: targets are positions (row la, column lb) of P's
+        // fP x fP front, so two stable counting passes -- by row, then by column --
+        // order them as a comparison sort would, equal targets in insertion order
+        sort_by_target(contrib, sy.front_off[P], fP, true);
+        for (size_t q = 0; q < contrib.size(); ++q) {
+          if (q == 0 || contrib[q].first != contrib[q - 1].first) {
+            mp.fa_tgt.push_back(contrib[q].first);
+            mp.fa_ptr.push_back((int64_t)mp.fa_src.size());
+          }
+          mp.fa_src.push_back(contrib[q].second);
         }
-        mp.fa_src.push_back(contrib[q].second);
       }
       // solve: update vector entries of child c (w slots c_c .. f_c-1) -> w slot loc(row) of P
       contrib.clear();
