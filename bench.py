@@ -321,9 +321,9 @@ def run_paper_workloads(args, clr, W):
     """The paper's benchmark classes (Sec. 5.1 portfolio and Huber QPs, Sec. 5.3
     entropy maximisation), one timed solve per factor precision, setup reported
     apart.  Sizes below the paper's (n = 5000 / 5000 / 2000 there): at those the
-    host setup of this solver takes 8 s (portfolio), 47 s (entropy) and, for Huber,
-    more host memory than a node has (the per-entry extend-add lists of fronts with
-    thousands of children), so the smaller instances keep the run to a minute."""
+    host setup of this solver takes 2.6 s (portfolio), 40 s (entropy) and 163 s
+    (Huber: the ordering and the per-entry extend-add lists of fronts with thousands
+    of children), so the smaller instances keep the run to a minute."""
     import torch
 
     out = {}
