@@ -369,6 +369,19 @@ def nt_scaling(ctype, s, z):
     raise ValueError(ctype)
 
 
+def psd_apply_H(R, v):
+    """H v for a PSD cone with NT scaling matrix R, in factored form:
+    H = W^T W with W(X) = R^T X R (Appendix A), so H v = svec(R (R^T V R) R^T),
+    V = smat(v).  Equal to nt_scaling(...)["H"] @ v in exact arithmetic; in
+    floating point each factor only carries the square root of H's range.  The
+    product is symmetrised by averaging it with its transpose (its rounding is
+    not symmetric, and keeping one triangle would mix the large eigen-block's
+    rounding into the small one)."""
+    Y = R.T @ smat(v) @ R
+    X = R @ Y @ R.T
+    return svec(0.5 * (X + X.T))
+
+
 # --------------------------------------------------------------------------
 # Jordan algebra (Eq. ds-correction-step, symmetric branch)
 # --------------------------------------------------------------------------

@@ -37,6 +37,10 @@ independently, by the CUDA path):
   the symmetric cones (capped at 1), multiply by 0.8 until every exp/pow cone
   is interior (and, for the combined step, inside N(beta) with the trial mu);
 * N(beta) is checked on exp/pow cones only; beta = 1e-6;
+* H Delta z in Delta s = -d_s - H Delta z is applied per PSD cone as
+  W^T (W Delta z) = svec(R (R^T Delta Z R) R^T) (Appendix A, H = W^T W), not
+  through the assembled svec block: near convergence that block has entries
+  up to ~1/mu and its product loses the small eigen-directions of S;
 * dual infeasibility uses q^T x in the first test (printed b^T z);
 * infeasibility tests use the unnormalised (homogeneous) iterates.
 """
@@ -181,12 +185,14 @@ def equilibrate(P, A, q, cones, st):
 # --------------------------------------------------------------------------
 # the IPM
 # --------------------------------------------------------------------------
-def reduced_direction(ks, Ph, qh, Ah, bh, Hblk, x, tau, kappa, dx2, dz2, d):
+def reduced_direction(ks, Ph, qh, Ah, bh, Hblk, x, tau, kappa, dx2, dz2, d, hmul=None):
     """Search direction from the reduced system (Eq. linsys_2x2) and the
     recovery formulas (Eq. step-direction, first form of Delta tau).
 
     ks solves K u = r with K = [P A^T; A -H]; (dx2, dz2) solve K u = [-q; b];
-    d = (d_x, d_z, d_tau, d_s, d_kappa).  Returns (Dx, Dz, Dtau, Ds, Dkappa)."""
+    d = (d_x, d_z, d_tau, d_s, d_kappa).  Delta s = -d_s - H Delta z, with
+    H Delta z formed by hmul (default: the assembled Hblk times Delta z).
+    Returns (Dx, Dz, Dtau, Ds, Dkappa)."""
     d_x, d_z, d_tau, d_s, d_kap = d
     n = len(x)
     sol1 = ks.solve(np.r_[d_x, -(d_z - d_s)])
@@ -199,7 +205,7 @@ def reduced_direction(ks, Ph, qh, Ah, bh, Hblk, x, tau, kappa, dx2, dz2, d):
     Dtau = num / den
     Dx = dx1 + Dtau * dx2
     Dz = dz1 + Dtau * dz2
-    Ds = -d_s - Hblk @ Dz
+    Ds = -d_s - (hmul(Dz) if hmul is not None else Hblk @ Dz)
     Dkap = -(d_kap + kappa * Dtau) / tau
     return Dx, Dz, Dtau, Ds, Dkap
 
@@ -340,9 +346,21 @@ def solve(P, q, A, b, cones, settings=None, record=False):
                 G2 = s + Ah @ x - bh * tau
                 G3 = kappa + qh @ x + bh @ z + (x @ Px) / tau
 
+                def hmul(v):
+                    # H Delta z for Delta s (Eq. step-direction): the assembled blocks,
+                    # except that a PSD cone applies H = W^T W in factored form,
+                    # R (R^T V R) R^T (Appendix A), which keeps the small
+                    # eigen-directions of S accurate once H is ill-conditioned
+                    out = Hblk @ v
+                    for (t, d, a, off) in K:
+                        if t == C.PSD:
+                            sl = slice(off, off + d)
+                            out[sl] = C.psd_apply_H(scal[off]["R"], v[sl])
+                    return out
+
                 def direction(dx_, dz_, dtau_, ds_, dkap_):
                     return reduced_direction(ks, Ph, qh, Ah, bh, Hblk, x, tau, kappa, dx2, dz2,
-                                             (dx_, dz_, dtau_, ds_, dkap_))
+                                             (dx_, dz_, dtau_, ds_, dkap_), hmul)
 
                 def step_length(Ds, Dz, Dtau, Dkap, neighbourhood):
                     amax = 1.0

@@ -1254,6 +1254,70 @@ __global__ void k_ds_psd(ConeDev cd, const double* __restrict__ dsa, const doubl
   }
 }
 
+// Delta s = -d_s - H Delta z on the rows of each PSD cone, with H = W^T W applied
+// in factored form: Delta S = -D_s - R (R^T Delta Z R) R^T (Appendix A, W(X) = R^T X R).
+// Near convergence the assembled svec block of H has entries up to ~1/mu, and its
+// product with Delta z loses the small eigen-directions of S to cancellation; each
+// factor R carries only the square root of that range.  R (R^T dZ R) R^T is
+// symmetrised by averaging the (i, j) and (j, i) entries.  Overwrites the PSD rows
+// of out (written before by the K product of the assembled blocks).
+__global__ void k_psd_ds_from_dz(ConeDev cd, const double* __restrict__ dz, const double* __restrict__ dsrhs,
+                                 double* __restrict__ out, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double B[32 * LDP], T[32 * LDP];
+  const int64_t cone = blockIdx.x;
+  const int k = cd.psd_ck[cone];
+  const int64_t row = cd.psd_crow[cone];
+  const double* R = cd.psd_R + cd.psd_cR[cone];
+  load_smat(dz + row, k, B);
+  // T = R' dZ
+  for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+    const int i = q % k, j = q / k;
+    double acc = 0;
+    for (int l = 0; l < k; ++l) acc += R[l + i * k] * B[l + j * LDP];
+    T[i + j * LDP] = acc;
+  }
+  __syncthreads();
+  // B = T R = R' dZ R
+  for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+    const int i = q % k, j = q / k;
+    double acc = 0;
+    for (int l = 0; l < k; ++l) acc += T[i + l * LDP] * R[l + j * k];
+    B[i + j * LDP] = acc;
+  }
+  __syncthreads();
+  // T = R B
+  for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+    const int i = q % k, j = q / k;
+    double acc = 0;
+    for (int l = 0; l < k; ++l) acc += R[i + l * k] * B[l + j * LDP];
+    T[i + j * LDP] = acc;
+  }
+  __syncthreads();
+  // (T R')_{ij} and (T R')_{ji}, averaged; out = -d_s - svec
+  for (int q = threadIdx.x; q < k * k; q += blockDim.x) {
+    const int i = q % k, j = q / k;
+    if (i > j) continue;
+    double acc = 0, acc2 = 0;
+    for (int l = 0; l < k; ++l) {
+      acc += T[i + l * LDP] * R[j + l * k];
+      acc2 += T[j + l * LDP] * R[i + l * k];
+    }
+    const double val = 0.5 * (acc + acc2);
+    const int64_t r = row + smat_index(i, j);
+    out[r] = -dsrhs[r] - ((i == j) ? val : val * kSqrt2);
+  }
+}
+
+int cones_psd_ds_from_dz(cudaStream_t st, const ConeDev& cd, const double* dz, const double* dsrhs, double* ds_out,
+                         const int* skip) {
+  if (cd.n_psd == 0) return CLR_OK;
+  const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
+  k_psd_ds_from_dz<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, dz, dsrhs, ds_out, skip);
+  CLR_CHECK_LAUNCH();
+  return CLR_OK;
+}
+
 int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* dsa,
                       const double* dza, IterScal* sc, double* ds_out, const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0)

@@ -119,6 +119,10 @@ int cones_init_shadow(cudaStream_t st, const ConeDev& cd, const int* skip);
 // Combined-step d_s (Eq. ds-correction-step) for every cone, with the problem's sigma mu.
 int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, const double* dsa,
                       const double* dza, IterScal* sc, double* ds_out, const int* skip);
+// Delta s = -d_s - H Delta z on the PSD rows with H applied in factored form
+// (R (R^T Delta Z R) R^T); overwrites those rows of ds_out (z-row indexing).
+int cones_psd_ds_from_dz(cudaStream_t st, const ConeDev& cd, const double* dz, const double* dsrhs, double* ds_out,
+                         const int* skip);
 // Initial point shift (symmetric init): v += (1 - a) e where a = least Jordan eigenvalue < sqrt(eps).
 // Zero-cone entries are set to 0; the merged nonneg cone of each problem shifts by its own
 // minimum (sc[p].nn_min_bits is scratch).

@@ -424,7 +424,8 @@ __global__ void k_hmax_reset(IterScal* sc, int64_t B, const int* skip) {
 __global__ void k_fin_delta(IterScal* sc, const ProbConst* pc, int64_t B, double static_reg, double static_reg_dyn,
                             const int* skip) {
   if (skip && *skip) return;
-  FOR_PROBLEMS(B) sc[p].delta = static_reg + static_reg_dyn * fmax(pc[p].maxPdiag, bitsd(sc[p].hmax_bits));
+  FOR_PROBLEMS(B)
+  sc[p].delta = static_reg * fmax(1.0, sc[p].reg_boost) + static_reg_dyn * fmax(pc[p].maxPdiag, bitsd(sc[p].hmax_bits));
 }
 
 // ------------------------------------------------------------------ solves / refinement
@@ -634,7 +635,10 @@ struct StepParams {
   int nonsym;
   int hist_cap;
   int escalate_on;  // a failed refinement holds the iteration back for a redo in FP64
+  int boost_on;     // FP64 factor: a non-finite solve holds the iteration back for a redo
+                    // with a larger static regularisation
 };
+constexpr double kRegBoostStep = 100.0, kRegBoostMax = 1e4;
 
 __global__ void k_step_begin(IterScal* sc, int64_t B, const int* skip) {
   if (skip && *skip) return;
@@ -700,9 +704,18 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         q.escalate = 1;  // redo the iteration with the FP64 factor
         continue;
       }
+      if (q.ir_fail == 2 && sp.boost_on && fmax(1.0, q.reg_boost) < kRegBoostMax) {
+        // the unpivoted FP64 factor broke down (a pivot near zero made it overflow):
+        // redo the iteration with the static regularisation raised; refinement on
+        // the unregularised K recovers the solution of K
+        q.reg_boost = fmax(1.0, q.reg_boost) * kRegBoostStep;
+        q.alpha_c = 0.0;
+        q.escalate = 1;
+        continue;
+      }
       if (q.ir_fail == 2) {
-        // a KKT solve of this iteration gave a non-finite value even in FP64: stop at
-        // the current, finite iterate
+        // a KKT solve of this iteration gave a non-finite value even in FP64 with
+        // the largest regularisation: stop at the current, finite iterate
         q.alpha_c = 0.0;
         q.status = CLR_NUMERICAL_ERROR;
         halt_problem(q, bf);
@@ -762,6 +775,7 @@ __global__ void k_init_scal(IterScal* sc, int64_t B, BatchFlags* bf) {
     memset(&sc[p], 0, sizeof(IterScal));
     sc[p].tau = 1.0;
     sc[p].kappa = 1.0;
+    sc[p].reg_boost = 1.0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     bf->all_halt = 0;
@@ -1305,7 +1319,8 @@ void kmv(int G, cudaStream_t s, int mode, int64_t r0, int64_t r1, int64_t n, con
 }  // namespace
 
 // One search direction: solve with the current right-hand side (rhs built by
-// k_rhs), Delta tau, Delta x/z, Delta s = -d_s - H Delta z.
+// k_rhs), Delta tau, Delta x/z, Delta s = -d_s - H Delta z (PSD blocks of H in
+// factored form).
 int Solver::direction(bool affine) {
   const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   cudaStream_t s = stream_;
@@ -1321,6 +1336,9 @@ int Solver::direction(bool affine) {
   k_fin_dtau<<<(unsigned)B, 128, 0, s>>>(sc_, v_.part, pst_, v_.ckx_ptr, v_.ckz_ptr, halt);
   k_recover<<<nck, 256, 0, s>>>(cg, dir, v_.sol1, v_.sol2, sc_, halt);
   kmv(csr_group_, s, 2, n, N, n, v_, h_long_, dir, nullptr, nullptr, v_.dsrhs, ds, sc_, halt);
+  // PSD rows again, with H in factored form (the assembled block loses the small
+  // eigen-directions of S near convergence)
+  cones_psd_ds_from_dz(s, cd_, dir + n, v_.dsrhs, ds, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
@@ -1350,7 +1368,7 @@ int Solver::step_length(bool combined) {
     if (rc) return rc;
   }
   StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hist_rows_,
-                (st.fp64_escalation && !use64()) ? 1 : 0};
+                (st.fp64_escalation && !use64()) ? 1 : 0, use64() ? 1 : 0};
   k_fin_step<<<pg, 128, 0, s>>>(sc_, B, sp, combined ? 1 : 0, v_.hist, bf_, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;

@@ -51,6 +51,10 @@ struct IterScal {
   // which mu stood ten times lower; three of them also escalate
   double feas_best, mu_at_best;
   int feas_stall, pad1;
+  // FP64 factor breakdown: a KKT solve of the iteration gave a non-finite value
+  // (the unpivoted factor overflowed); the iteration is redone (escalate) with the
+  // static regularisation multiplied by reg_boost (x100 per breakdown, at most 1e4)
+  double reg_boost;
 };
 
 // Constants of one problem (device memory, written at setup).

@@ -120,37 +120,16 @@ def test_banded_lp_n200000_m400000_fp32():
     _solve_full(prob, 32)
 
 
-def test_psd_batch_2000x10_n20000_fp32_accuracy_reached():
-    """The PSD batch: near mu ~ 1e-9 the scaling matrices H of the PSD cones reach
-    condition numbers ~1e18 and the steps stall just short of the 1e-8 gap test
-    (the oracle stalls the same way at a tenth of the size).  What is checked here
-    is the answer at the point where the solve stops: objective against the
-    planted optimum, residuals recomputed on the host, cone membership, and the
-    sampled scalings; the status is one of SOLVED or the two stall statuses,
-    never a NaN iterate."""
+@pytest.mark.parametrize("bits", [32, 64])
+def test_psd_batch_2000x10_n20000(bits):
+    """The PSD batch (2000 PSD(10) cones of complementary rank 5 + 5, 5000 nonneg
+    rows): SOLVED at eps_feas = 1e-8 against the planted optimum, in FP32 (with
+    the FP64 escalation) and in FP64.  Near mu ~ 1e-9 the PSD blocks of H reach
+    condition numbers ~1e19: Delta s uses H in factored form, and a breakdown of
+    the unpivoted FP64 factor is redone with a larger static regularisation."""
     prob = W.psd_batch(0)
-    st = clr.clr_default_settings(32, ir_stop_ratio=5.0)
-    s_ = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
-    s_.solve()
-    x, sl, z, info = s_.solution()
-    s_.free()
-    assert info["status_name"] in ("SOLVED", "INSUFFICIENT_PROGRESS", "NUMERICAL_ERROR"), info
-    assert np.all(np.isfinite(x)) and np.all(np.isfinite(sl)) and np.all(np.isfinite(z)), info
-    f_star = prob.objective(prob.x_star)
-    assert abs(prob.objective(x) - f_star) <= 1e-6 * max(1.0, abs(f_star)), (prob.objective(x), f_star, info)
-    scale_p = max(1.0, np.abs(prob.b).max() + np.abs(x).max() + np.abs(sl).max())
-    scale_d = max(1.0, np.abs(prob.q).max() + np.abs(x).max() + np.abs(z).max())
-    rp = prob.A @ x + sl - prob.b
-    rd = prob.A.T @ z + prob.q
-    assert np.abs(rp).max() <= 1e-6 * scale_p and np.abs(rd).max() <= 1e-6 * scale_d, info
-    _check_cones(prob.cones, sl, z, 1e-7 * max(1.0, np.abs(sl).max(), np.abs(z).max()))
+    x, sl, z, info = _solve_full(prob, bits)
     _sampled_scalings(prob.cones, sl, z, info["mu"] + 1e-3, np.random.default_rng(1))
-
-
-@pytest.mark.xfail(reason="the PSD batch stalls at a relative gap of ~1e-7 (the oracle too)", strict=False)
-def test_psd_batch_2000x10_n20000_fp32_solved_to_1e8():
-    prob = W.psd_batch(0)
-    _solve_full(prob, 32)
 
 
 @pytest.mark.parametrize("bits", [32, 64])

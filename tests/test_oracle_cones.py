@@ -393,3 +393,64 @@ def test_third_order_correction_dropped_on_singular_hessian(monkeypatch):
 
     monkeypatch.setattr(C.np.linalg, "solve", singular)
     np.testing.assert_array_equal(C.third_order_correction(C.EXP, z, dz, ds), np.zeros(3))
+
+
+def _near_complementary_psd_pair(rng, k, small):
+    """S, Z sharing one orthogonal basis Q, S with k//2 eigenvalues ~small and
+    Z with the others ~small (a strictly complementary PSD pair near the end of
+    an interior-point solve).  Returns S, Z, Q and Z's eigenvalues."""
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    h = k // 2
+    es = np.r_[rng.uniform(0.5, 2.0, k - h), small * rng.uniform(0.5, 2.0, h)]
+    ez = np.r_[small * rng.uniform(0.5, 2.0, k - h), rng.uniform(0.5, 2.0, h)]
+    return (Q * es) @ Q.T, (Q * ez) @ Q.T, Q, ez
+
+
+@pytest.mark.parametrize("k", [2, 4, 6])
+def test_psd_factored_H_equals_assembled_H(k):
+    """H v in factored form, R (R^T V R) R^T, is the assembled svec block of
+    nt_scaling times v (both are H = W^T W of Appendix A)."""
+    rng = np.random.default_rng(40 + k)
+    M1, M2 = rng.standard_normal((k, k)), rng.standard_normal((k, k))
+    s, z = C.svec(M1 @ M1.T + 0.3 * np.eye(k)), C.svec(M2 @ M2.T + 0.3 * np.eye(k))
+    sc = C.nt_scaling(C.PSD, s, z)
+    v = rng.standard_normal(len(s))
+    Hv = sc["H"] @ v
+    np.testing.assert_allclose(C.psd_apply_H(sc["R"], v), Hv, rtol=1e-12, atol=1e-12 * np.abs(Hv).max())
+    # and it maps z to s (H z = s)
+    np.testing.assert_allclose(C.psd_apply_H(sc["R"], z), s, rtol=1e-10, atol=1e-12)
+
+
+def test_psd_factored_H_keeps_the_small_eigenspace_of_S():
+    """Near convergence (S, Z of complementary rank, small eigenvalues 1e-9) a
+    search direction Delta Z has the scale of Z on each eigen-direction, and the
+    exact H Delta Z -- evaluated in 60-digit arithmetic from the same FP64 R --
+    has the scale of S: ~1e-9 on the small eigenspace of S.  The factored
+    product R (R^T Delta Z R) R^T keeps that block to many digits; the
+    assembled svec block (entries up to ~1e9) loses it to cancellation.  This
+    is why Delta s of a PSD cone is formed in factored form."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 60
+    rng = np.random.default_rng(7)
+    k = 6
+    S, Z, Q, ez = _near_complementary_psd_pair(rng, k, 1e-9)
+    sc = C.nt_scaling(C.PSD, C.svec(S), C.svec(Z))
+    R = sc["R"]
+    G = rng.standard_normal((k, k))
+    dZ = Q @ ((G + G.T) * np.sqrt(np.outer(ez, ez))) @ Q.T  # entries scaled like Z's
+    v = C.svec(dZ)
+    Rm = mpmath.matrix(R.tolist())
+    Qm = mpmath.matrix(Q[:, k - k // 2:].tolist())
+
+    def small_block(Xm):
+        # the block on the small eigenspace of S, projected in 60-digit arithmetic
+        B = Qm.T * Xm * Qm
+        return np.array([[float(B[i, j]) for j in range(B.cols)] for i in range(B.rows)])
+
+    ref = small_block(Rm * (Rm.T * mpmath.matrix(C.smat(v).tolist()) * Rm) * Rm.T)
+    err_fact = np.abs(small_block(mpmath.matrix(C.smat(C.psd_apply_H(R, v)).tolist())) - ref).max()
+    err_asm = np.abs(small_block(mpmath.matrix(C.smat(sc["H"] @ v).tolist())) - ref).max()
+    scale = np.abs(ref).max()
+    assert scale < 1e-7  # the exact product is tiny there
+    assert err_fact <= 1e-4 * scale, (err_fact, scale)
+    assert err_asm > 100 * err_fact, (err_asm, err_fact)
