@@ -456,6 +456,24 @@ int clr_ldl_solve(const clr_csc* K_lower, const double* signs, const int64_t* or
                   double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
                   int32_t* dyn_hits_out);
 
+/* Arithmetic peaks of the current GPU measured by the library's own kernels,
+ * the denominators of the benchmark's roofline fractions (the paper reports
+ * none): FP64 and FP32 FMA throughput of the CUDA cores, and tcgen05 tensor
+ * throughput for kind::tf32 and kind::f16 with BF16 operands (FP32
+ * accumulation; M = 128, N = 256 MMAs issued back to back from shared-memory
+ * operands, one CTA per SM).  Each figure is the best of `reps` (>= 1)
+ * launches timed with CUDA events on `stream` (cudaStream_t as void*, NULL:
+ * legacy default stream); *_ms are those launches' durations.  Allocates and
+ * frees a few MB of scratch.  tc_timeouts != 0 means a tensor-core wait ran out
+ * (the tensor figures are then invalid).  Errors: CLR_E_INVALID (out NULL,
+ * reps < 1), CLR_E_CUDA.  Changes no clock or other GPU setting. */
+typedef struct {
+  double fp64_fma_tflops, fp32_fma_tflops, tf32_tc_tflops, bf16_tc_tflops;
+  double fp64_ms, fp32_ms, tf32_ms, bf16_ms;
+  int32_t sms, tc_timeouts;
+} clr_peaks;
+int clr_probe_peaks(int32_t reps, void* stream, clr_peaks* out);
+
 /* ------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a
  * service for callers that cannot allocate device memory where they need a
@@ -472,7 +490,8 @@ int clr_ldl_solve(const clr_csc* K_lower, const double* signs, const int64_t* or
  * clr_ldl_solve) and solve of one quasi-definite system, on DEVICE pointers:
  *   K      N x N column-major, lower triangle read (upper ignored)
  *   signs  N expected pivot signs (> 0: +1, else -1)
- *   rhs    N;  x (output) N;  D (output, may be NULL) N pivots
+ *   rhs    N;  x (output) N, may be the same buffer as rhs (in-place solve);
+ *          D (output, may be NULL) N pivots; K must not overlap x or D
  *   dyn_hits (output, device int, may be NULL): pivots replaced
  *   stream cudaStream_t as void* (NULL: legacy default stream)
  * No device memory is allocated or freed: the working matrix lives in one

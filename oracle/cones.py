@@ -382,6 +382,27 @@ def psd_apply_H(R, v):
     return svec(0.5 * (X + X.T))
 
 
+def apply_scaling(ctype, sc, which, v):
+    """W v, W^{-T} v or W^T v ('W', 'WinvT', 'WT') for the NT scaling sc of a
+    symmetric cone.  PSD cones apply W(X) = R^T X R, W^{-T}(X) = R^{-1} X R^{-T}
+    and W^T(X) = R X R^T as congruences with R (Appendix A), symmetrised by
+    averaging with the transpose, rather than through the assembled svec
+    matrices, whose entries grow like the square root of H's condition number;
+    the other cones multiply by the matrices."""
+    if ctype == PSD:
+        R, Ri = sc["R"], sc["Rinv"]
+        V = smat(v)
+        if which == "W":
+            X = R.T @ V @ R
+        elif which == "WinvT":
+            X = Ri @ V @ Ri.T
+        else:
+            X = R @ V @ R.T
+        return svec(0.5 * (X + X.T))
+    M = {"W": sc["W"], "WinvT": sc["WinvT"], "WT": sc["W"].T}[which]
+    return M @ v
+
+
 # --------------------------------------------------------------------------
 # Jordan algebra (Eq. ds-correction-step, symmetric branch)
 # --------------------------------------------------------------------------

@@ -40,7 +40,10 @@ independently, by the CUDA path):
 * H Delta z in Delta s = -d_s - H Delta z is applied per PSD cone as
   W^T (W Delta z) = svec(R (R^T Delta Z R) R^T) (Appendix A, H = W^T W), not
   through the assembled svec block: near convergence that block has entries
-  up to ~1/mu and its product loses the small eigen-directions of S;
+  up to ~1/mu and its product loses the small eigen-directions of S; for the
+  same reason W, W^{-T} and W^T in the combined-step d_s of a PSD cone are
+  congruences with R and R^{-1} (the KKT matrix and its refinement residual
+  keep the assembled block);
 * dual infeasibility uses q^T x in the first test (printed b^T z);
 * infeasibility tests use the unnormalised (homogeneous) iterates.
 """
@@ -412,9 +415,10 @@ def solve(P, q, A, b, cones, settings=None, record=False):
                     if t in (C.NONNEG, C.SOC, C.PSD):
                         sc = scal[off]
                         lam = C.lam_vec(t, sc["lam"], d)
-                        eta = C.jordan_prod(t, sc["WinvT"] @ Dsa[sl], sc["W"] @ Dza[sl])
+                        eta = C.jordan_prod(t, C.apply_scaling(t, sc, "WinvT", Dsa[sl]),
+                                            C.apply_scaling(t, sc, "W", Dza[sl]))
                         v = C.jordan_prod(t, lam, lam) + eta - sigma * mu * C.identity(t, d)
-                        ds_c[sl] = sc["W"].T @ C.jordan_div(t, sc["lam"], v)
+                        ds_c[sl] = C.apply_scaling(t, sc, "WT", C.jordan_div(t, sc["lam"], v))
                     else:
                         eta = C.third_order_correction(t, z[sl], Dza[sl], Dsa[sl], a)
                         ds_c[sl] = s[sl] + sigma * mu * C.barrier_grad(t, z[sl], a) + eta

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libclr.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["setup.cpp", "amd.cpp", "symbolic.cpp", "cohort.cpp", "ldl.cu", "bigfront.cu", "bigflow.cu", "cones.cu", "ipm.cu", "server.cu", "api.cu", "steps.cu", "noalloc.cu"]
+SOURCES = ["setup.cpp", "amd.cpp", "symbolic.cpp", "cohort.cpp", "ldl.cu", "bigfront.cu", "bigflow.cu", "cones.cu", "ipm.cu", "server.cu", "api.cu", "steps.cu", "noalloc.cu", "probe.cu"]
 
 
 def _nvcc():

@@ -100,7 +100,7 @@ EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr
            "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_cones_time", "clr_ldl_solve",
            "clr_dense_ldl_solve_noalloc", "clr_batch_setup", "clr_batch_analyze", "clr_batch_size", "clr_batch_get",
            "clr_batch_update_qb", "clr_server_create", "clr_server_submit", "clr_server_poll", "clr_server_wait",
-           "clr_server_get_stats", "clr_server_destroy", "clr_autotune"]
+           "clr_server_get_stats", "clr_server_destroy", "clr_autotune", "clr_probe_peaks"]
 
 
 def _lib():
@@ -142,6 +142,7 @@ def _lib():
         L.clr_ldl_solve.argtypes = [P(clr_csc), P(C.c_double), P(C.c_int64), C.c_int32, C.c_double, C.c_double,
                                     P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
         L.clr_dense_ldl_solve_noalloc.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_double, C.c_double, vp, vp]
+        L.clr_probe_peaks.argtypes = [C.c_int32, vp, P(clr_peaks)]
         L.clr_batch_setup.argtypes = [P(vp), C.c_int32, P(clr_problem), P(clr_settings)]
         L.clr_batch_analyze.argtypes = [P(vp), C.c_int32, P(clr_problem), P(clr_settings)]
         L.clr_batch_size.argtypes = [vp]
@@ -584,6 +585,20 @@ def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1
     _check(_lib().clr_ldl_solve(C.byref(Kc), _dptr(signs), ordp, factor_bits, dyn_reg_eps, dyn_reg_delta, _dptr(rhs),
                                 _dptr(x), _dptr(D), C.byref(hits)), "clr_ldl_solve")
     return x, D, hits.value
+
+
+class clr_peaks(C.Structure):
+    _fields_ = [("fp64_fma_tflops", C.c_double), ("fp32_fma_tflops", C.c_double), ("tf32_tc_tflops", C.c_double),
+                ("bf16_tc_tflops", C.c_double), ("fp64_ms", C.c_double), ("fp32_ms", C.c_double),
+                ("tf32_ms", C.c_double), ("bf16_ms", C.c_double), ("sms", C.c_int32), ("tc_timeouts", C.c_int32)]
+
+
+def clr_probe_peaks(reps=5, stream_ptr=None):
+    """FP64 / FP32 FMA and tcgen05 TF32 / BF16 tensor throughput (TFLOP/s) of
+    the current GPU, measured by the library's probe kernels (see include/clr.h)."""
+    out = clr_peaks()
+    _check(_lib().clr_probe_peaks(int(reps), C.c_void_p(stream_ptr), C.byref(out)), "clr_probe_peaks")
+    return {k: getattr(out, k) for (k, _) in clr_peaks._fields_}
 
 
 def clr_dense_ldl_solve_noalloc(K_ptr, signs_ptr, N, rhs_ptr, x_ptr, D_ptr=None, dyn_reg_eps=1e-13,

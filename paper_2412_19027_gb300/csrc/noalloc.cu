@@ -27,9 +27,10 @@ constexpr int kNoAllocMaxN = CLR_NOALLOC_MAX_N;
 // on a device; held by each GPU that loads the library until the process exits.
 static __device__ __align__(256) double g_noalloc_work[kNoAllocMaxN * kNoAllocMaxN];
 
-__global__ void k_noalloc_ldl(double* __restrict__ W, const double* __restrict__ K, const double* __restrict__ signs,
-                              int N, const double* __restrict__ rhs, double* __restrict__ x, double* __restrict__ D,
-                              double eps, double delta, int* hits) {
+// The caller's buffers carry no __restrict__: rhs and x may be the same buffer
+// (an in-place solve reads every rhs entry into x before anything else is written).
+__global__ void k_noalloc_ldl(double* __restrict__ W, const double* K, const double* signs, int N, const double* rhs,
+                              double* x, double* D, double eps, double delta, int* hits) {
   __shared__ double dsh;
   __shared__ int nhit;
   const int tid = threadIdx.x;

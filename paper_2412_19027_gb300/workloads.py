@@ -175,6 +175,30 @@ def nonneg_qp(seed=0, n=50, m=100, density=0.1, rank=5):
     return _finish("nonneg_qp_n%d_m%d" % (n, m), rng, M @ M.T, A, [(NONNEG, m, 0.0)])
 
 
+def unique_qp(seed=0, n=40, n_eq=8, n_inactive=30, rank=5):
+    """QP (LP when rank = 0) with a unique, nondegenerate primal-dual optimum:
+    n_eq zero rows and n - n_eq active nonneg rows (s* = 0, z* > 0) make a
+    square dense Gaussian active block A_B (nonsingular with probability one),
+    plus n_inactive inactive nonneg rows (s* > 0, z* = 0).  x* and z* are then
+    the only optimum, so two solvers' answers can be compared entry by entry."""
+    rng = np.random.default_rng(seed)
+    m = n + n_inactive
+    A = rng.standard_normal((m, n))
+    M = rng.standard_normal((n, rank)) if rank > 0 else np.zeros((n, 1))
+    x = rng.standard_normal(n)
+    s = np.zeros(m)
+    z = np.zeros(m)
+    z[:n_eq] = rng.standard_normal(n_eq)
+    z[n_eq:n] = rng.uniform(0.5, 2.0, n - n_eq)
+    s[n:] = rng.uniform(0.5, 2.0, n_inactive)
+    P_full = sp.csc_matrix(M @ M.T)
+    b = A @ x + s
+    q = -(P_full @ x) - A.T @ z
+    cones = [(ZERO, n_eq, 0.0), (NONNEG, m - n_eq, 0.0)]
+    return Problem("unique_qp_n%d_m%d" % (n, m), sp.csc_matrix(sp.triu(P_full)), np.asarray(q), sp.csc_matrix(A),
+                   np.asarray(b), cones, x, s, z, {"active_rows": n})
+
+
 def mixed_cone(seed=0, n=2000, n_zero=500, n_nonneg=3000, n_soc=500, soc_dim=5, n_exp=100, n_pow=100,
                pow_alpha=0.3, nnz_per_col=10, p_rank=10):
     """Mixed-cone QP.  Full size: n=2000, m=6600 = 500 zero + 3000 nonneg +

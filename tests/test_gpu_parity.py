@@ -23,6 +23,8 @@ import oracle
 from oracle import cones as C
 from oracle.linsys import ldl_factor
 
+import kkt_checks as KC
+
 pytestmark = pytest.mark.gpu
 
 clr = pytest.importorskip("paper_2412_19027_gb300.clr")
@@ -196,25 +198,64 @@ def test_ldl_amd_order_solves():
     assert np.all(D * signs > 0)
 
 
+def _cone_membership(cones, s, z, tol):
+    off = 0
+    for (t, d, a) in cones:
+        sv, zv = s[off:off + d], z[off:off + d]
+        off += d
+        if t == C.ZERO:
+            assert np.abs(sv).max() <= tol
+        elif t == C.NONNEG:
+            assert sv.min() >= -tol and zv.min() >= -tol
+        elif t == C.SOC:
+            assert sv[0] - np.linalg.norm(sv[1:]) >= -tol and zv[0] - np.linalg.norm(zv[1:]) >= -tol
+        elif t == C.PSD:
+            assert np.linalg.eigvalsh(C.smat(sv)).min() >= -tol
+            assert np.linalg.eigvalsh(C.smat(zv)).min() >= -tol
+        else:  # exp / pow: the closed cones, checked on a point pushed inward by tol
+            e = C.central_point(t, d, a)
+            assert C.in_int_primal(t, sv + tol * e, a) and C.in_int_dual(t, zv + tol * e, a)
+
+
 def _compare_solve(prob, factor_bits=64, iters_tol=2, obj_rtol=1e-6):
+    """GPU solve against oracle.solve on the same problem:
+    * status SOLVED on both sides, iterations within iters_tol, objective within
+      obj_rtol relative;
+    * the termination test of the paper at eps_feas = 1e-8 (primal and dual
+      residuals, gap) recomputed on the host in FP64 from the returned x, s, z --
+      for the GPU's answer and for the oracle's;
+    * s in K and z in K* (to 1e-9 of the iterate's size) and s'z small;
+    * entry by entry, where the optimum is unique and nondegenerate (zero and
+      nonneg cones; kkt_checks.distance_bound): |x_gpu - x_oracle| and
+      |z_gpu - z_oracle| within the sum of the two answers' a-posteriori
+      distance bounds (x2 for rounding), and s through s = b - A x."""
     st = clr.clr_default_settings(factor_bits)
     solver = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
-    status = solver.solve()
+    solver.solve()
     x, s, z, info = solver.solution()
+    solver.free()
     ref = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones)
     assert ref.status == 1
     assert info["status_name"] == "SOLVED", info
     f, fr = prob.objective(x), prob.objective(ref.x)
     assert abs(f - fr) <= obj_rtol * max(1.0, abs(fr)), (f, fr)
-    assert info["res_primal"] <= 1e-8 * max(1.0, np.abs(prob.b).max() + np.abs(x).max() + np.abs(s).max())
     assert abs(info["iterations"] - ref.iterations) <= iters_tol, (info["iterations"], ref.iterations)
-    # the returned point satisfies the KKT conditions of the unscaled problem
-    Pf = (prob.P + sp.triu(prob.P, 1).T)
-    rp = prob.A @ x + s - prob.b
-    rd = Pf @ x + prob.A.T @ z + prob.q
-    scale = 1.0 + max(np.abs(x).max(), np.abs(z).max(), np.abs(s).max())
-    assert np.abs(rp).max() < 1e-6 * scale and np.abs(rd).max() < 1e-6 * scale
-    solver.free()
+    for (xx, ss, zz), who in (((x, s, z), "gpu"), ((ref.x, ref.s, ref.z), "oracle")):
+        ok, d = KC.termination(prob.P, prob.q, prob.A, prob.b, xx, ss, zz, 1e-8 * (1 + 1e-6))
+        assert ok, (who, d)
+        size = max(1.0, np.abs(ss).max(), np.abs(zz).max())
+        _cone_membership(prob.cones, ss, zz, 1e-9 * size)
+        assert abs(ss @ zz) <= 1e-7 * d["scale_g"], (who, ss @ zz)
+    bg = KC.distance_bound(prob.P, prob.q, prob.A, prob.b, prob.cones, x, s, z)
+    bo = KC.distance_bound(prob.P, prob.q, prob.A, prob.b, prob.cones, ref.x, ref.s, ref.z)
+    if bg is not None and bo is not None:
+        slack = 1e-12 * (1.0 + np.abs(ref.x).max() + np.abs(ref.z).max())
+        ex, ez = 2.0 * (bg[0] + bo[0]) + slack, 2.0 * (bg[1] + bo[1]) + slack
+        assert np.all(np.abs(x - ref.x) <= ex), np.max(np.abs(x - ref.x) - ex)
+        assert np.all(np.abs(z - ref.z) <= ez), np.max(np.abs(z - ref.z) - ez)
+        As = sp.csc_matrix(prob.A)
+        rs = np.abs(prob.A @ x + s - prob.b) + np.abs(prob.A @ ref.x + ref.s - prob.b)
+        assert np.all(np.abs(s - ref.s) <= abs(As) @ ex + rs + slack)
     return info, ref
 
 
@@ -231,6 +272,9 @@ SOLVE_CASES = [
     ("psd10_small", lambda: W.psd_batch(1, n=200, n_psd=6, psd_k=10, n_nonneg=40, nnz_per_col=4)),
     ("banded_small", lambda: W.banded_lp(0, n=150, window=16)),
     ("mpc_small", lambda: W.mpc_qp(0, T=10, nx=4, nu=2)),
+    ("unique_lp", lambda: W.unique_qp(0, rank=0)),
+    ("unique_qp", lambda: W.unique_qp(1, rank=5)),
+    ("unique_qp_large", lambda: W.unique_qp(2, n=120, n_eq=20, n_inactive=200, rank=10)),
 ]
 
 
@@ -239,7 +283,10 @@ def test_solve_matches_oracle_fp64(name, make):
     _compare_solve(make(), 64)
 
 
-@pytest.mark.parametrize("name,make", SOLVE_CASES[:4] + SOLVE_CASES[7:8], ids=[c[0] for c in SOLVE_CASES[:4] + SOLVE_CASES[7:8]])
+FP32_CASES = SOLVE_CASES[:4] + SOLVE_CASES[7:8] + SOLVE_CASES[9:]
+
+
+@pytest.mark.parametrize("name,make", FP32_CASES, ids=[c[0] for c in FP32_CASES])
 def test_solve_matches_oracle_fp32_factor(name, make):
     """FP32 factorization + FP64 refinement reaches the FP64 oracle's answer."""
     _compare_solve(make(), 32, iters_tol=4)

@@ -454,3 +454,27 @@ def test_psd_factored_H_keeps_the_small_eigenspace_of_S():
     assert scale < 1e-7  # the exact product is tiny there
     assert err_fact <= 1e-4 * scale, (err_fact, scale)
     assert err_asm > 100 * err_fact, (err_asm, err_fact)
+
+
+@pytest.mark.parametrize("t,d", [(C.NONNEG, 4), (C.SOC, 5), (C.PSD, 10)])
+def test_apply_scaling_matches_the_matrices(t, d):
+    """W v, W^{-T} v and W^T v of apply_scaling equal the assembled NT matrices
+    times v (PSD in factored form, the others through the matrices)."""
+    rng = np.random.default_rng(60 + d)
+    if t == C.PSD:
+        k = C.psd_order(d)
+        M1, M2 = rng.standard_normal((k, k)), rng.standard_normal((k, k))
+        s, z = C.svec(M1 @ M1.T + 0.3 * np.eye(k)), C.svec(M2 @ M2.T + 0.3 * np.eye(k))
+    elif t == C.SOC:
+        s = np.r_[3.0, rng.standard_normal(d - 1)]
+        z = np.r_[3.5, rng.standard_normal(d - 1)]
+    else:
+        s, z = rng.uniform(0.5, 2, d), rng.uniform(0.5, 2, d)
+    sc = C.nt_scaling(t, s, z)
+    v = rng.standard_normal(d)
+    for which, M in (("W", sc["W"]), ("WinvT", sc["WinvT"]), ("WT", sc["W"].T)):
+        ref = M @ v
+        np.testing.assert_allclose(C.apply_scaling(t, sc, which, v), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # W^{-T} s = W z = lambda
+    np.testing.assert_allclose(C.apply_scaling(t, sc, "WinvT", s), C.lam_vec(t, sc["lam"], d), atol=1e-10)
+    np.testing.assert_allclose(C.apply_scaling(t, sc, "W", z), C.lam_vec(t, sc["lam"], d), atol=1e-10)

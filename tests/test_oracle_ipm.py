@@ -354,3 +354,26 @@ def test_psd_cones_of_mixed_orders_reach_the_planted_optimum():
     assert r["status_name"] == "SOLVED"
     f, fs = prob.objective(r["x"]), prob.objective(prob.x_star)
     assert abs(f - fs) <= 1e-6 * max(1.0, abs(fs))
+
+
+@pytest.mark.parametrize("seed,rank", [(0, 0), (1, 5), (2, 3)])
+def test_unique_qp_solution_within_posterior_bound(seed, rank):
+    """On a QP with a unique nondegenerate optimum (planted), the oracle's answer
+    passes the host-recomputed termination test at 1e-8, and its distance to the
+    planted (x*, z*) is within the first-order a-posteriori bound that the GPU
+    parity tests use to compare two answers entry by entry."""
+    from paper_2412_19027_gb300 import workloads as W
+    import kkt_checks as KC
+    p = W.unique_qp(seed, rank=rank)
+    r = oracle.solve(p.P, p.q, p.A, p.b, p.cones)
+    assert r.status_name == "SOLVED"
+    ok, d = KC.termination(p.P, p.q, p.A, p.b, r.x, r.s, r.z)
+    assert ok, d
+    bnd = KC.distance_bound(p.P, p.q, p.A, p.b, p.cones, r.x, r.s, r.z)
+    assert bnd is not None
+    e_x, e_z = bnd
+    slack = 1e-12 * (1.0 + np.abs(p.x_star).max())
+    assert np.all(np.abs(r.x - p.x_star) <= 2.0 * e_x + slack), np.max(np.abs(r.x - p.x_star) - e_x)
+    assert np.all(np.abs(r.z - p.z_star) <= 2.0 * e_z + slack)
+    # the bound is informative: far below the size of the solution
+    assert e_x.max() < 1e-5 * max(1.0, np.abs(p.x_star).max())
