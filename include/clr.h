@@ -122,6 +122,11 @@ typedef struct {
                                  products), 96 (FP64); at most 224 (FP32) / 160 (FP64) */
   int32_t amalgamation;       /* relaxed supernode amalgamation: 0 off, 1 (default) column thresholds
                                  4 / 16 / 48, 2 thresholds 8 / 32 / 96 (same zero ratios) */
+  double escalate_ratio;      /* factor_bits 32/16 with fp64_escalation: also escalate when a KKT solve of an
+                                 iteration ends its refinement above t_abs + t_rel ||rhs|| with ||r||_inf larger
+                                 than escalate_ratio times the largest entry of the iterate's scaled residual G
+                                 (the direction is then too inexact to reduce the feasibility residuals);
+                                 default 0.1, 0 = off */
 } clr_settings;
 
 typedef struct {
@@ -206,6 +211,23 @@ int clr_analyze(clr_solver** out, const clr_csc* P_upper, const double* q, const
  * length falls below min_step.  Blocking.  Each call starts from scratch
  * (data as set up, or as replaced by clr_update_qb / clr_update_PA). */
 int clr_solve(clr_solver* s);
+
+/* clr_solve in parts, for callers that interleave iterations with other work or
+ * time them (the same kernels and graphs as clr_solve):
+ *   clr_solve_begin    starts a solve from scratch: the initial point (Alg. 1
+ *                      step 2), queued on the solver's stream;
+ *   clr_solve_iterate  runs up to k (>= 0) passes of the iteration (Alg. 1 steps
+ *                      3-11; blocking), stopping early once every problem has
+ *                      stopped (then *done = 1, else 0); *iters_run = the
+ *                      iterations completed (a pass that only finds the
+ *                      termination test satisfied completes none);
+ *   clr_solve_end      finishes the solve (results readable with
+ *                      clr_get_solution).
+ * done and iters_run may be NULL.  CLR_E_STATE if the solver holds no device
+ * data (clr_analyze), CLR_E_INVALID on k < 0. */
+int clr_solve_begin(clr_solver* s);
+int clr_solve_iterate(clr_solver* s, int32_t k, int32_t* done, int32_t* iters_run);
+int clr_solve_end(clr_solver* s);
 
 /* Copy the result to host buffers (any may be NULL): x (n), s (m), z (m) in
  * the caller's original row order, un-scaled.  SOLVED: x/tau, s/tau, z/tau.

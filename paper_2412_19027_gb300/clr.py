@@ -44,7 +44,7 @@ class clr_settings(C.Structure):
                 ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
                 ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32),
                 ("fp64_escalation", C.c_int32), ("big_front_schedule", C.c_int32),
-                ("small_front_max", C.c_int32), ("amalgamation", C.c_int32)]
+                ("small_front_max", C.c_int32), ("amalgamation", C.c_int32), ("escalate_ratio", C.c_double)]
 
 
 class clr_info(C.Structure):
@@ -100,7 +100,8 @@ EXPORTS = ["clr_default_settings", "clr_setup", "clr_analyze", "clr_solve", "clr
            "clr_cones_scaling", "clr_cones_step_length", "clr_cones_combined_ds", "clr_cones_time", "clr_ldl_solve",
            "clr_dense_ldl_solve_noalloc", "clr_batch_setup", "clr_batch_analyze", "clr_batch_size", "clr_batch_get",
            "clr_batch_update_qb", "clr_server_create", "clr_server_submit", "clr_server_poll", "clr_server_wait",
-           "clr_server_get_stats", "clr_server_destroy", "clr_autotune", "clr_probe_peaks"]
+           "clr_server_get_stats", "clr_server_destroy", "clr_autotune", "clr_probe_peaks", "clr_solve_begin",
+           "clr_solve_iterate", "clr_solve_end"]
 
 
 def _lib():
@@ -143,6 +144,9 @@ def _lib():
                                     P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
         L.clr_dense_ldl_solve_noalloc.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_double, C.c_double, vp, vp]
         L.clr_probe_peaks.argtypes = [C.c_int32, vp, P(clr_peaks)]
+        L.clr_solve_begin.argtypes = [vp]
+        L.clr_solve_iterate.argtypes = [vp, C.c_int32, P(C.c_int32), P(C.c_int32)]
+        L.clr_solve_end.argtypes = [vp]
         L.clr_batch_setup.argtypes = [P(vp), C.c_int32, P(clr_problem), P(clr_settings)]
         L.clr_batch_analyze.argtypes = [P(vp), C.c_int32, P(clr_problem), P(clr_settings)]
         L.clr_batch_size.argtypes = [vp]
@@ -268,6 +272,20 @@ class Solver:
         returns the status code (STATUS maps it to a name)."""
         _check(_lib().clr_solve(self.h), "clr_solve")
         return self.info()["status"]
+
+    def solve_begin(self):
+        """clr_solve_begin: start a solve (initial point) on the solver's stream."""
+        _check(_lib().clr_solve_begin(self.h), "clr_solve_begin")
+
+    def solve_iterate(self, k=1):
+        """clr_solve_iterate: up to k IPM iterations; returns (done, iterations run)."""
+        done, ran = C.c_int32(), C.c_int32()
+        _check(_lib().clr_solve_iterate(self.h, int(k), C.byref(done), C.byref(ran)), "clr_solve_iterate")
+        return bool(done.value), ran.value
+
+    def solve_end(self):
+        """clr_solve_end: finish the solve started by solve_begin."""
+        _check(_lib().clr_solve_end(self.h), "clr_solve_end")
 
     def info(self):
         """The clr_info of the last solve as a dict (status, status_name,

@@ -55,6 +55,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.big_front_schedule = 1;
   s.small_front_max = 0;
   s.amalgamation = 1;
+  s.escalate_ratio = 0.1;
   *out = s;
   return CLR_OK;
 }
@@ -68,6 +69,7 @@ static int check_settings(const clr_settings& s) {
       s.amalgamation > 2)
     return CLR_E_INVALID;
   if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
+  if (!(s.escalate_ratio >= 0)) return CLR_E_INVALID;
   if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;
   return CLR_OK;
 }
@@ -110,6 +112,41 @@ int clr_analyze(clr_solver** out, const clr_csc* P_upper, const double* q, const
 int clr_solve(clr_solver* s) {
   if (!s) return CLR_E_INVALID;
   return s->impl.solve();
+}
+
+int clr_solve_begin(clr_solver* s) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.solve_begin();
+}
+
+int clr_solve_iterate(clr_solver* s, int32_t k, int32_t* done, int32_t* iters_run) {
+  if (!s || k < 0) return CLR_E_INVALID;
+  clr::Solver& v = s->impl;
+  if (!v.device_ready) return CLR_E_STATE;
+  int64_t before = 0;
+  for (int64_t p = 0; p < v.lay.B; ++p) before = std::max<int64_t>(before, v.problem_iter(p));
+  int32_t finished = 0;
+  for (int32_t i = 0; i < k; ++i) {
+    int rc = v.step_launch();
+    if (rc) return rc;
+    bool ready = false;
+    rc = v.step_wait(&ready);
+    if (rc) return rc;
+    if (v.all_halted()) {
+      finished = 1;
+      break;
+    }
+  }
+  int64_t after = 0;
+  for (int64_t p = 0; p < v.lay.B; ++p) after = std::max<int64_t>(after, v.problem_iter(p));
+  if (done) *done = finished;
+  if (iters_run) *iters_run = (int32_t)(after - before);
+  return CLR_OK;
+}
+
+int clr_solve_end(clr_solver* s) {
+  if (!s) return CLR_E_INVALID;
+  return s->impl.solve_end();
 }
 
 int clr_get_solution(const clr_solver* s, double* x, double* sl, double* z, clr_info* info) {

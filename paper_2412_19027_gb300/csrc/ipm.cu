@@ -29,7 +29,7 @@ namespace clr {
 
 // ------------------------------------------------------------------ slots
 enum SumSlot { S_XPX = 0, S_QX, S_BZ, S_SZ, S_D0, S_D1, S_D2, S_NSLOT };
-enum MaxSlot { M_RD = 0, M_X, M_RP, M_S, M_Z, M_ATZ, M_PX, M_AXS, M_NMAX };
+enum MaxSlot { M_RD = 0, M_X, M_RP, M_S, M_Z, M_ATZ, M_PX, M_AXS, M_GS, M_NMAX };
 
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
@@ -248,7 +248,7 @@ __global__ void k_resid(ChunkGrid g, const double* __restrict__ xz, const double
   const int64_t slot = chunk_slot(g);
   const double tau = sc[pid].tau;
   unsigned long long* mb = maxb + (int64_t)M_NMAX * pid;
-  double s0 = 0, s1 = 0, m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  double s0 = 0, s1 = 0, m0 = 0, m1 = 0, m2 = 0, m3 = 0, m4 = 0;
   if (!zp) {
     for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
       const double x = xz[i], px = lo[i], atz = hi[i], qi = q[i], di = D[i];
@@ -261,6 +261,7 @@ __global__ void k_resid(ChunkGrid g, const double* __restrict__ xz, const double
       m1 = fmax(m1, fabs(di * x));
       m2 = fmax(m2, fabs(atz) / di);
       m3 = fmax(m3, fabs(px) / di);
+      m4 = fmax(m4, fabs(g1));
     }
   } else {
     const int64_t n = g.n;
@@ -275,6 +276,7 @@ __global__ void k_resid(ChunkGrid g, const double* __restrict__ xz, const double
       m1 = fmax(m1, fabs(si) / ei);
       m2 = fmax(m2, fabs(ei * zi));
       m3 = fmax(m3, fabs(ax + si) / ei);
+      m4 = fmax(m4, fabs(g2));
     }
   }
   s0 = block_sum(s0, sh);
@@ -283,7 +285,9 @@ __global__ void k_resid(ChunkGrid g, const double* __restrict__ xz, const double
   m1 = block_max(m1, sh);
   m2 = block_max(m2, sh);
   m3 = block_max(m3, sh);
+  m4 = block_max(m4, sh);
   if (threadIdx.x == 0) {
+    atomicMax(mb + M_GS, dbits(m4));
     part[(zp ? S_BZ : S_XPX) * g.pst + slot] = s0;
     part[(zp ? S_SZ : S_QX) * g.pst + slot] = s1;
     if (!zp) {
@@ -347,6 +351,7 @@ __global__ void k_fin_resid(IterScal* scs, const ProbConst* pcs, const double* p
   const double gd = (-0.5 * xpx / (tau * tau) - bz / tau) / c;
   const double gap = fabs(gp - gd);
   sc.mu = mu;
+  sc.g_scaled = bitsd(mb[M_GS]);
   sc.xPx = xpx;
   sc.qx = qx;
   sc.bz = bz;
@@ -417,6 +422,7 @@ __global__ void k_hmax_reset(IterScal* sc, int64_t B, const int* skip) {
     sc[p].hmax_bits = 0ull;
     sc[p].ir_fail = 0;
     sc[p].escalate = 0;
+    sc[p].ir_worst = 0.0;
   }
 }
 
@@ -487,17 +493,20 @@ __device__ bool ir_step_due(IterScal& q, double abstol, double reltol, double st
   q.ir_revert = 0;
   if (q.ir_skip) return false;
   const double fail_tol = 1e-4 * fmax(1.0, q.rhs_norm);
+  const double tol = abstol + reltol * q.rhs_norm;
   if (r > q.ir_prev) {
     q.ir_revert = 1;
     q.ir_skip = 1;
     if (!(q.ir_prev <= fail_tol)) q.ir_fail = max(q.ir_fail, isfinite(q.ir_prev) ? 1 : 2);
+    if (q.ir_prev > tol) q.ir_worst = fmax(q.ir_worst, q.ir_prev);
     return false;
   }
   const bool stalled = stop_ratio > 0 && r <= fail_tol && !(r * stop_ratio < q.ir_prev);
   q.ir_prev = r;
-  if (!(r > abstol + reltol * q.rhs_norm) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
+  if (!(r > tol) || stalled || q.ir_cur >= max_steps) {  // NaN also stops
     q.ir_skip = 1;
     if (!(r <= fail_tol)) q.ir_fail = max(q.ir_fail, isfinite(r) ? 1 : 2);  // 2: a non-finite solve
+    if (r > tol) q.ir_worst = fmax(q.ir_worst, r);
     return false;
   }
   q.ir_cur += 1;
@@ -637,6 +646,8 @@ struct StepParams {
   int escalate_on;  // a failed refinement holds the iteration back for a redo in FP64
   int boost_on;     // FP64 factor: a non-finite solve holds the iteration back for a redo
                     // with a larger static regularisation
+  double escalate_ratio;  // escalate when a refinement ended above its tolerance with
+                          // ||r|| > escalate_ratio max|G| (0: off)
 };
 constexpr double kRegBoostStep = 100.0, kRegBoostMax = 1e4;
 
@@ -699,7 +710,8 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
-      if ((q.ir_fail || q.feas_stall >= 3) && sp.escalate_on) {
+      const bool inexact = sp.escalate_ratio > 0 && q.ir_worst > sp.escalate_ratio * q.g_scaled;
+      if ((q.ir_fail || q.feas_stall >= 3 || inexact) && sp.escalate_on) {
         q.alpha_c = 0.0;
         q.escalate = 1;  // redo the iteration with the FP64 factor
         continue;
@@ -1368,7 +1380,7 @@ int Solver::step_length(bool combined) {
     if (rc) return rc;
   }
   StepParams sp{st.backtrack, st.min_step, st.nbhd_beta, st.step_fraction, nonsym ? 1 : 0, hist_rows_,
-                (st.fp64_escalation && !use64()) ? 1 : 0, use64() ? 1 : 0};
+                (st.fp64_escalation && !use64()) ? 1 : 0, use64() ? 1 : 0, st.escalate_ratio};
   k_fin_step<<<pg, 128, 0, s>>>(sc_, B, sp, combined ? 1 : 0, v_.hist, bf_, halt);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
@@ -1650,15 +1662,19 @@ int Solver::solve_end() {
   return CLR_OK;
 }
 
+int Solver::step_wait(bool* ready) {
+  CLR_CUDA(cudaEventSynchronize(step_ev_));
+  return step_poll(ready);
+}
+
 int Solver::solve() {
   int rc = solve_begin();
   if (rc) return rc;
   for (int it = 0; it <= st.max_iter + 1; ++it) {
     rc = step_launch();
     if (rc) return rc;
-    CLR_CUDA(cudaEventSynchronize(step_ev_));
     bool ready = false;
-    rc = step_poll(&ready);
+    rc = step_wait(&ready);
     if (rc) return rc;
     if (bf_host_->all_halt) break;
   }

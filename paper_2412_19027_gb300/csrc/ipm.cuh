@@ -72,6 +72,8 @@ class Solver {
   int solve_begin();
   int step_launch();           // one iteration + status copy to pinned memory, no wait
   int step_poll(bool* ready);  // has the last launched step finished?
+  int step_wait(bool* ready);  // wait for the last launched step, then as step_poll
+  int problem_iter(int64_t p) const { return sc_host_[p].iter; }  // valid after a step finished
   bool all_halted() const;     // valid after a step finished
   int problem_status(int64_t p) const;  // from the last finished step
   int solve_end();

@@ -55,6 +55,9 @@ struct IterScal {
   // (the unpivoted factor overflowed); the iteration is redone (escalate) with the
   // static regularisation multiplied by reg_boost (x100 per breakdown, at most 1e4)
   double reg_boost;
+  // largest scaled residual |G| of the iterate, and the largest final refinement
+  // residual of this iteration's KKT solves that ended above the tolerance
+  double g_scaled, ir_worst;
 };
 
 // Constants of one problem (device memory, written at setup).

@@ -171,3 +171,28 @@ def test_single_variable():
     assert info["status_name"] == "SOLVED"
     assert x[0] == pytest.approx(1.0, abs=1e-7)
     assert z @ s == pytest.approx(0.0, abs=1e-7)
+
+
+def test_incremental_solve_matches_clr_solve():
+    """clr_solve_begin / clr_solve_iterate / clr_solve_end run the same kernels
+    and graphs as clr_solve: the same iterates bit for bit, and the iteration
+    counts of the parts add up to the solve's."""
+    prob = W.mixed_cone(3, n=80, n_zero=10, n_nonneg=100, n_soc=15, n_exp=5, n_pow=5, nnz_per_col=4)
+    st = clr.clr_default_settings(64)
+    s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+    s.solve()
+    x1, s1, z1, info1 = s.solution()
+    s.solve_begin()
+    total, done, calls = 0, False, 0
+    while not done:
+        done, ran = s.solve_iterate(3)
+        total += ran
+        calls += 1
+        assert calls < 100
+    s.solve_end()
+    x2, s2, z2, info2 = s.solution()
+    s.free()
+    assert info1["status_name"] == info2["status_name"] == "SOLVED"
+    assert info1["iterations"] == info2["iterations"] == total
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(z1, z2)
