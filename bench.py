@@ -1,27 +1,33 @@
 """Benchmark of the GPU interior-point solver (one JSON line on rank 0).
 
-A step is one complete solve (initial point, then IPM iterations until the
-termination tests pass at eps_feas = 1e-8) of the mixed-cone QP workload:
-n = 2000, m = 6600 (500 zero, 3000 nonneg, 500 SOC(5), 100 exp, 100
-pow(0.3) rows/cones), P = diag + rank 10, A with 10 nnz per column, built
-from a planted optimum (seeded synthetic data).  Every step passes through
-all rows of the per-iteration device path.
+Workload: the large sparse LP (banded LP) n = 200 000, m = 400 000: 100 000
+zero-cone and 300 000 nonnegative rows, A with 8 N(0,1) entries per column
+(6 band rows around 2j plus 2 rows uniform in a window of 1024), P diagonal
+U(0,1) with half of it zero, built from a planted optimum (seeded synthetic
+data).  eps_feas = 1e-8.
 
-metric  IPM iterations per second (total iterations / device time), for the
-        FP32-factor + FP64-refinement path; the FP64-factor path is measured
-        in the same run and reported under "fp64_factor"; time-to-1e-8 of
-        both under "time_to_tol_ms".
+step    one IPM iteration of Algorithm 1 (residuals, termination tests, cone
+        scalings, KKT factorization, the three refined KKT solves, step
+        lengths, combined direction, update: every row of the per-iteration
+        device step), run through clr_solve_iterate on the solver's stream;
+        the timed region starts a fresh solve (its initial point included) and
+        starts another one whenever a solve ends inside it.
+metric  IPM iterations per second of the FP32-factor + FP64-refinement path
+        (with its escalation to the FP64 factor); time-to-1e-8 of full solves
+        with the FP32 factor, the FP64 factor and the 16-bit-product factor,
+        each with its error against the planted optimum, under
+        "time_to_tol_ms".
 N > 1   independent replicas, one problem per GPU (weak scaling, no
         collective on the data path).
 
-serving  the MPC request stream (10 000 QPs, horizon U{10..50}, states
-        U{4..12}, inputs U{2..4}, stable random dynamics, boxes and one SOC
-        per step) through the continuous-batching server: solves/s and
-        p50/p99 latency (submit -> result readable) at Poisson arrivals, next
-        to one-at-a-time solves (clr_setup + clr_solve + read-back + free per
-        problem), under "serving".
+Also reported: the mixed-cone QP (n = 2000, m = 6600) under "mixed_cone_qp";
+the MPC serving stream (FP64 and FP32 factors) under "serving"; the cone
+kernels at stress shapes under "cone_roofline"; the GPU's measured
+arithmetic peaks (the library's probe) under "peaks".
 
---impl reference times the FP64 CPU oracle on the host cores instead.
+--impl reference times the FP64 CPU oracle on the host cores instead (one IPM
+iteration per step on a scaled-down instance of the same generator: the dense
+oracle cannot hold the full KKT matrix of order 600 000).
 """
 import argparse
 import json
@@ -36,12 +42,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "IPM iterations/s to eps_feas=1e-8 (time-to-1e-8 in time_to_tol_ms)"
+METRIC = "IPM iterations/s to eps_feas=1e-8 (time-to-1e-8 of the FP32, FP64 and 16-bit-product factors in time_to_tol_ms)"
 UNIT = "iter/s"
-WORKLOAD = "mixed-cone QP n=2000 m=6600 (500 zero, 3000 nonneg, 500 SOC5, 100 exp, 100 pow0.3), P=diag+rank10"
-FP64_PEAK_TFLOPS = 1.25            # GB300 FP64 (FFMA and DMMA), nominal
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2070 MHz
-FLOW_DRAM_BYTES_FP32 = 17.800448e6 + 1.957632e6    # k_bf_flow<float>, mixed-cone QP (profiles/k_bf_flow_*)
+WORKLOAD = ("banded LP n=200000 m=400000 (100000 zero, 300000 nonneg rows), A 8 nnz/col (6 band + 2 in a "
+            "1024 window), P diag U(0,1) half zero, planted optimum")
+SAMPLE_N = 2000  # scaled-down instance of the same generator for the CPU oracle (dense KKT of order 6000)
 
 
 def measured_peaks():
@@ -102,10 +107,11 @@ def run_cone_roofline(clr, W, peaks, reps=10, shift=0):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20, help="timed IPM iterations")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--factor-bits", type=int, default=32, choices=[16, 32, 64])
+    ap.add_argument("--n", type=int, default=0, help="banded LP size (default: the full n=200000)")
     ap.add_argument("--ir-stop-ratio", type=float, default=5.0,
                     help="refinement stall test (0 = the paper's rule only: tolerance or T_max)")
     ap.add_argument("--no-graph", action="store_true",
@@ -113,7 +119,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=1, help="0 skips the FP64 and 16-bit full solves")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-cone QP leg")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cone-roofline", action="store_true",
                     help="skip the cone kernels at stress shapes (2^26 nonneg rows, 2^22 SOC5, 2^16 PSD10)")
@@ -126,7 +134,6 @@ def parse():
                     help="run only the cone kernels at the stress shapes and print their JSON (for profiling)")
     ap.add_argument("--cone-shift", type=int, default=0, help="divide the stress shapes by 2^shift")
     ap.add_argument("--serve-requests", type=int, default=10_000)
-    ap.add_argument("--serve-bits", type=int, default=64, choices=[32, 64])
     return ap.parse_args()
 
 
@@ -191,25 +198,28 @@ class ClockSampler:
 
 def cpu_baseline(seed, iters=2):
     """The oracle, as it stands, on the host cores: a bounded sample of the
-    workload (its first `iters` IPM iterations; setup time subtracted)."""
+    workload -- its first `iters` IPM iterations on the same generator at
+    n = SAMPLE_N (the dense oracle cannot hold the full problem), setup time
+    subtracted."""
     code = r"""
 import sys, time, json
 sys.path.insert(0, %r)
 import oracle
 from paper_2412_19027_gb300 import workloads as W
-prob = W.mixed_cone(%d)
+prob = W.banded_lp(%d, n=%d)
 t0 = time.perf_counter(); oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=0)); t1 = time.perf_counter()
 r = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=%d)); t2 = time.perf_counter()
 print(json.dumps(dict(iters=r.iterations, setup=t1 - t0, total=t2 - t1)))
-""" % (ROOT, seed, iters)
+""" % (ROOT, seed, SAMPLE_N, iters)
     cores = os.cpu_count() or 1
     env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     d = json.loads(out.stdout.strip().splitlines()[-1])
     t = max(d["total"] - d["setup"], 1e-9)
     return {"value": d["iters"] / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d IPM iterations of the same workload (FP64 NumPy/LAPACK oracle, dense KKT "
-                      "8600x8600), setup time subtracted; %.1f s of CPU work" % (d["iters"], d["total"])}
+            "sample": "first %d IPM iterations of the same generator at n=%d, m=%d (FP64 NumPy/LAPACK oracle, dense "
+                      "KKT of order %d), setup time subtracted; %.1f s of CPU work" % (
+                          d["iters"], SAMPLE_N, 2 * SAMPLE_N, 3 * SAMPLE_N, d["total"])}
 
 
 def _pct(v, q):
@@ -264,23 +274,27 @@ def serve_stream(clr, sv, reqs, rate):
             "statuses": statuses, "unsolved_first": unsolved}
 
 
-def run_serving(args, clr, W):
-    """The MPC request stream through the continuous-batching server, next to one-at-a-time solves."""
+def make_stream(args, clr, W):
     t_gen = time.perf_counter()
     seeds = W.mpc_stream(args.seed, args.serve_requests)
     probs = [W.mpc_qp(sd) for sd in seeds]
     reqs = [clr.Request(p.P, p.q, p.A, p.b, p.cones) for p in probs]
-    t_gen = time.perf_counter() - t_gen
-    st = clr.clr_default_settings(args.serve_bits)
+    return probs, reqs, time.perf_counter() - t_gen
+
+
+def run_serving(args, clr, W, bits, stream, sweep_points=(0.25, 0.5, 0.8, 1.0, 1.2), k_one=200):
+    """The MPC request stream through the continuous-batching server, next to one-at-a-time solves."""
+    probs, reqs, t_gen = stream
+    st = clr.clr_default_settings(bits)
     # blocking parameters for the stream's cohorts, picked by the autotuner on a
     # 64-problem cohort of the stream's shapes (3 IPM iterations per candidate)
     t_tune = time.perf_counter()
     tune = clr.clr_autotune([(p.P, p.q, p.A, p.b, p.cones) for p in probs[-64:]], st, iters=3)
     tune["seconds"] = time.perf_counter() - t_tune
-    st = clr.clr_default_settings(args.serve_bits, small_front_max=tune["small_front_max"],
+    st = clr.clr_default_settings(bits, small_front_max=tune["small_front_max"],
                                   amalgamation=tune["amalgamation"], big_front_schedule=tune["big_front_schedule"])
     # one at a time: the whole public call sequence per problem
-    k1 = min(200, len(probs))
+    k1 = min(k_one, len(probs))
     lat1 = []
     t0 = time.perf_counter()
     for p in probs[:k1]:
@@ -300,7 +314,7 @@ def run_serving(args, clr, W):
     pois = serve_stream(clr, sv, reqs, 0.8 * sat["solves_per_s"])
     pois["arrivals"] = "Poisson at 0.8 x saturation throughput"
     sweep = []
-    for f in (0.25, 0.5, 0.8, 1.0, 1.2):
+    for f in sweep_points:
         nsw = int(min(500, len(reqs), max(50, 10.0 * f * rate1)))  # at most ~10 s per point
         r = serve_stream(clr, sv, reqs[:nsw], f * rate1)
         r["offered_x_one_at_a_time"] = f
@@ -308,7 +322,7 @@ def run_serving(args, clr, W):
     stats = sv.stats()
     sv.close()
     return {"workload": "MPC QP stream: %d requests, T U{10..50}, nx U{4..12}, nu U{2..4}, |x|<=5, |u|<=1, "
-                        "||u_t||<=1.2, cost x'x + 0.1 u'u; FP%d factor" % (len(reqs), args.serve_bits),
+                        "||u_t||<=1.2, cost x'x + 0.1 u'u; FP%d factor" % (len(reqs), bits),
             "server": {"max_cohort": 256, "max_active": 4, "device_budget_bytes": 16 << 30,
                        "cohorts": stats["cohorts"], "max_cohort_seen": stats["max_cohort_seen"],
                        "peak_device_bytes": stats["peak_bytes"]},
@@ -412,21 +426,21 @@ def run_configs(args, clr, W):
 
 
 def run_reference(args):
+    """The oracle on the host cores, on the same generator at n = SAMPLE_N: one
+    IPM iteration per step (the dense oracle cannot hold the full problem)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    iters_per_step = 1
-    sample_times = []
-    code_iters = 0
     import oracle
     from paper_2412_19027_gb300 import workloads as W
-    prob = W.mixed_cone(args.seed)
+    prob = W.banded_lp(args.seed, n=SAMPLE_N)
     t0 = time.perf_counter()
     oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=0))
     setup = time.perf_counter() - t0
+    sample_times, code_iters = [], 0
     for k in range(args.warmup + args.steps):
         t = time.perf_counter()
-        r = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=iters_per_step))
+        r = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(max_iter=1))
         dt = time.perf_counter() - t - setup
         if k >= args.warmup:
             sample_times.append(max(dt, 1e-9))
@@ -434,17 +448,61 @@ def run_reference(args):
     total = sum(sample_times)
     value = code_iters / total
     cores = os.cpu_count() or 1
+    sample = ("%d steps x 1 IPM iteration of the same generator at n=%d, m=%d (dense KKT of order %d), setup "
+              "subtracted" % (args.steps, SAMPLE_N, 2 * SAMPLE_N, 3 * SAMPLE_N))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "seed": args.seed,
-                       "step": "one IPM iteration of the oracle (bounded sample of the solve)"},
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
-                             "sample": "%d steps x %d IPM iteration(s), setup subtracted" % (args.steps,
-                                                                                            iters_per_step)},
+                       "step": "one IPM iteration of the oracle on the scaled-down instance (bounded sample)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def timed_solves(torch, solver, stream, flush, count):
+    """`count` full solves (clr_solve) timed with CUDA events on the solver's
+    stream, L2 flushed before each; returns (ms list, info of the last, perf of the last)."""
+    st, en = _events(torch, count), _events(torch, count)
+    out, info, perf = [], None, None
+    for k in range(count):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            st[k].record(stream)
+        solver.solve()
+        en[k].record(stream)
+        info, perf = solver.info(), solver.perf()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(st, en)], info, perf
+
+
+def factor_roofline(perf, sym, peaks):
+    """Roofline of the numeric factorization, per precision it ran in during the
+    solve: unit = one factorization (all launches of the factorization phase),
+    algorithmic flops = the symbolic factor flop count, time = CUDA events around
+    the phase inside the captured iteration graphs."""
+    out = {}
+    n64 = perf["factorizations64"]
+    f64_ms = perf["factor64_ms"]
+    f32_ms = perf["factor_ms"] - f64_ms
+    # factorizations of the iterations (redone iterations included); the
+    # initial-point factorization (one for problems of symmetric cones only, as
+    # here) is timed in init_ms and left out
+    n32 = max(0, perf["factorizations"] - n64 - 1)
+    for name, n, ms, peak, src in (("fp32", n32, f32_ms, peaks["fp32_fma_tflops"], "measured FP32 FMA (library probe)"),
+                                   ("fp64", n64, f64_ms, peaks["fp64_fma_tflops"], "measured FP64 FMA (library probe)")):
+        if n <= 0 or ms <= 0:
+            continue
+        per = ms / n
+        ach = sym["factor_flops"] / (per / 1e3) / 1e12
+        out[name] = {"factorizations": n, "ms_per_factorization": per, "total_ms": ms, "achieved_tflops": ach,
+                     "peak_tflops": peak, "peak_source": src, "frac": ach / peak}
+    return out
 
 
 def run_ours(args):
@@ -473,51 +531,66 @@ def run_ours(args):
             print(json.dumps({"cone_roofline": run_cone_roofline(clr, W, measured_peaks(), 3, args.cone_shift)}),
                   flush=True)
         return
-    prob = W.mixed_cone(args.seed + rank)
-    n, m = prob.n, prob.m
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2
+    peaks = clr.clr_probe_peaks(5, stream.cuda_stream)
+    copy_peaks = measured_peaks()
+    peaks.update({"hbm_gbs": copy_peaks["hbm_gbs"], "bf16_cublas_tflops": copy_peaks["bf16_tflops"],
+                  "hbm_source": copy_peaks["source"] + " (MEASURED_PEAKS.json copy test)"})
+
+    t_gen = time.perf_counter()
+    prob = W.banded_lp(args.seed + rank, n=args.n) if args.n else W.banded_lp(args.seed + rank)
+    t_gen = time.perf_counter() - t_gen
+    n, m = prob.n, prob.m
+    f_star = prob.objective(prob.x_star)
 
     def make(bits):
         kw = {"ir_stop_ratio": args.ir_stop_ratio, "use_graph": 0 if args.no_graph else 1}
         st = clr.clr_default_settings(bits, **kw)
+        t0 = time.perf_counter()
         s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
         s.set_stream(stream.cuda_stream)
-        return s
+        return s, time.perf_counter() - t0
 
-    def timed(solver, steps, warmup):
-        for _ in range(warmup):
-            solver.solve()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        iters, launches, perfs, infos = 0, 0, [], []
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        for k in range(steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-                starts[k].record(stream)
-            solver.solve()
-            ends[k].record(stream)
-            info = solver.info()
-            p = solver.perf()
-            iters += info["iterations"]
-            launches += p["kernel_launches"]
-            perfs.append(p)
-            infos.append(info)
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-        times = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
-        return times, iters, launches, perfs, infos
+    def err_of(x):
+        return abs(prob.objective(x) - f_star) / max(1.0, abs(f_star))
 
-    main = make(args.factor_bits)
+    # ---------------- headline: IPM iterations, FP32 factor + FP64 refinement
+    main, setup_s = make(args.factor_bits)
     sym = main.symbolic_stats()
+    main.solve_begin()
+    for _ in range(args.warmup):
+        done, _ = main.solve_iterate(1)
+        if done:
+            main.solve_end()
+            main.solve_begin()
+    main.solve_end()
+    starts, ends = _events(torch, args.steps), _events(torch, args.steps)
+    iters, restarts = 0, 0
     clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     clocks.start()
-    times, iters, launches, perfs, infos = timed(main, args.steps, args.warmup)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            starts[k].record(stream)
+        if k == 0:
+            main.solve_begin()  # a fresh solve: its initial point is inside the timed region
+        done, ran = main.solve_iterate(1)
+        iters += ran
+        if done:
+            main.solve_end()
+            main.solve_begin()
+            restarts += 1
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
     clk = clocks.stop()
+    main.solve_end()
+    times = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = float(sum(times))
     if ws > 1:
         t = torch.tensor([total_ms, float(iters)], device="cuda", dtype=torch.float64)
@@ -529,28 +602,24 @@ def run_ours(args):
     else:
         total_ms_max, iters_all = total_ms, float(iters)
     value = iters_all / (total_ms_max / 1e3)
-    x, s_, z, info = main.solution()
-    f_star = prob.objective(prob.x_star)
-    obj_err = abs(prob.objective(x) - f_star) / max(1.0, abs(f_star))
 
-    # the FP64-factor path on the same problem
-    fp64 = None
-    if args.fp64_steps > 0:
-        s64 = main if args.factor_bits == 64 else make(64)
-        t64, it64, _, p64, inf64 = timed(s64, args.fp64_steps, 1)
-        x64, _, _, _ = s64.solution()
-        fp64 = {"time_to_tol_ms": float(np.median(t64)), "iterations": inf64[-1]["iterations"],
-                "iters_per_s": it64 / (sum(t64) / 1e3), "status": inf64[-1]["status_name"],
-                "objective_rel_err_vs_planted": abs(prob.objective(x64) - f_star) / max(1.0, abs(f_star)),
-                "factor_ms_per_factorization": p64[-1]["factor_ms"] / max(1, p64[-1]["factorizations"])}
-        if s64 is not main:
-            s64.free()
-
-    # end to end through the C ABI with host buffers: q, b in; x, s, z out
+    # ---------------- time to 1e-8: full solves in each factor precision
+    ttt = {}
+    t32, inf32, pf32 = timed_solves(torch, main, stream, flush, 2)
+    x32, _, _, _ = main.solution()
+    ttt["fp32_factor"] = {"ms": float(np.median(t32)), "all_ms": t32, "iterations": inf32["iterations"],
+                          "status": inf32["status_name"], "fp64_from_iter": inf32["fp64_from_iter"],
+                          "objective_rel_err_vs_planted": err_of(x32), "gap_rel": inf32["gap_rel"],
+                          "res_primal": inf32["res_primal"], "res_dual": inf32["res_dual"],
+                          "ir_steps_total": inf32["ir_steps_total"], "setup_s": setup_s,
+                          "phase_ms": {"init": pf32["init_ms"], "residuals+cones": pf32["resid_cones_ms"],
+                                       "factorization": pf32["factor_ms"], "solves+steps": pf32["solve_step_ms"]},
+                          "factorization_roofline": factor_roofline(pf32, sym, peaks)}
+    # end to end through the C ABI with host buffers: q, b in; x, s, z out (one full solve per step)
     e2e = None
     if not args.no_e2e:
         e_iters, e_time = 0, 0.0
-        for k in range(args.steps):
+        for k in range(args.e2e_steps):
             torch.cuda.synchronize()
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -562,40 +631,72 @@ def run_ours(args):
             e_time += time.perf_counter() - t0
             e_iters += info_e["iterations"]
         e2e = {"value": e_iters / e_time, "unit": UNIT, "h2d_bytes_per_step": 8 * (n + m),
-               "d2h_bytes_per_step": 8 * (n + 2 * m)}
+               "d2h_bytes_per_step": 8 * (n + 2 * m),
+               "step": "one full solve through the public API (clr_update_qb from host q, b; clr_solve; "
+                       "clr_get_solution to host x, s, z); %d solves" % args.e2e_steps}
+    main.free()
+    for bits, key in ((64, "fp64_factor"), (16, "bf16_products_fp32_factor")):
+        if args.fp64_steps <= 0:
+            break
+        sv_, su = make(bits)
+        tt, inf, pf = timed_solves(torch, sv_, stream, flush, 1)
+        xx, _, _, _ = sv_.solution()
+        ttt[key] = {"ms": float(np.median(tt)), "iterations": inf["iterations"], "status": inf["status_name"],
+                    "fp64_from_iter": inf["fp64_from_iter"], "objective_rel_err_vs_planted": err_of(xx),
+                    "gap_rel": inf["gap_rel"], "res_primal": inf["res_primal"], "res_dual": inf["res_dual"],
+                    "ir_steps_total": inf["ir_steps_total"], "setup_s": su,
+                    "phase_ms": {"init": pf["init_ms"], "residuals+cones": pf["resid_cones_ms"],
+                                 "factorization": pf["factor_ms"], "solves+steps": pf["solve_step_ms"]},
+                    "factorization_roofline": factor_roofline(pf, sym, peaks)}
+        sv_.free()
+    if "fp64_factor" in ttt:
+        ttt["fp32_speedup_vs_fp64_factor"] = ttt["fp64_factor"]["ms"] / ttt["fp32_factor"]["ms"]
 
-    # dominant phase and its roofline
-    p = perfs[-1]
-    nf = max(1, p["factorizations"])
-    phases = {"residuals+cones": p["resid_cones_ms"], "factorization": p["factor_ms"],
-              "solves+steps": p["solve_step_ms"], "init": p["init_ms"]}
-    fact_ms = p["factor_ms"] / nf
-    peaks = measured_peaks()
-    achieved = sym["factor_flops"] / (fact_ms / 1e3) / 1e12
-    if args.factor_bits == 16:
-        # BF16 products on the tensor cores, timed inside the solve: the sustained figure
-        bound, peak = "tensor", peaks["bf16_tflops_sustained"]
-        psrc = "%s cuBLAS BF16 sustained" % peaks["source"]
-    elif args.factor_bits == 32:
-        bound, peak, psrc = "alu", FP32_PEAK_TFLOPS, "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-    else:
-        bound, peak, psrc = "alu", FP64_PEAK_TFLOPS, "GB300 FP64 nominal 1.25 TFLOP/s"
-    # DRAM bytes of the factorization's dominant launch (k_bf_flow, one per factorization
-    # of this workload) from one ncu capture of this kernel version (profiles/); other
-    # precisions were not captured
-    traffic = FLOW_DRAM_BYTES_FP32 if (args.factor_bits == 32 and not args.no_graph) else None
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "numeric LDL^T (multifrontal, FP%d)" % args.factor_bits,
-                "flops_per_launch": sym["factor_flops"], "ms_per_launch": fact_ms, "peak_source": psrc,
-                "traffic_source": "ncu dram__bytes_read+write of k_bf_flow<float> (dominant launch)" if traffic
-                else None}
+    # dominant kernel of the headline solve: the factorization phase in the
+    # precision that took the most time
+    fr = ttt["fp32_factor"]["factorization_roofline"]
+    dom = max(fr.items(), key=lambda kv: kv[1]["total_ms"]) if fr else None
+    roofline = None
+    if dom:
+        name, d = dom
+        roofline = {"bound": "alu", "achieved": d["achieved_tflops"], "peak": d["peak_tflops"], "unit": "TFLOP/s",
+                    "frac": d["frac"], "traffic": None,
+                    "kernel": "numeric LDL^T, %s factor (k_bf_flow dataflow launches + small-front kernels of one "
+                              "factorization)" % name.upper(),
+                    "flops_per_launch": sym["factor_flops"], "ms_per_launch": d["ms_per_factorization"],
+                    "peak_source": d["peak_source"] + ", of measured",
+                    "unit_of_launch": "one numeric factorization of the KKT matrix (order %d)" % sym["kkt_dim"],
+                    "traffic_source": "not captured for this kernel version"}
+
+    # ---------------- the mixed-cone QP (earlier headline workload)
+    mixed = None
+    if not args.no_mixed and rank == 0:
+        pm = W.mixed_cone(args.seed)
+        mixed = {}
+        for bits in (32, 64):
+            st = clr.clr_default_settings(bits, ir_stop_ratio=args.ir_stop_ratio)
+            sv_ = clr.clr_setup(pm.P, pm.q, pm.A, pm.b, pm.cones, st)
+            sv_.set_stream(stream.cuda_stream)
+            sv_.solve()
+            tt, inf, pf = timed_solves(torch, sv_, stream, flush, 3)
+            xx, _, _, _ = sv_.solution()
+            fs = pm.objective(pm.x_star)
+            mixed["fp%d_factor" % bits] = {"time_to_tol_ms": float(np.median(tt)), "iterations": inf["iterations"],
+                                           "status": inf["status_name"], "fp64_from_iter": inf["fp64_from_iter"],
+                                           "objective_rel_err_vs_planted": abs(pm.objective(xx) - fs) / max(1.0, abs(fs)),
+                                           "factor_ms_per_factorization": pf["factor_ms"] / max(1, pf["factorizations"])}
+            sv_.free()
+        mixed["workload"] = "mixed-cone QP n=2000 m=6600 (500 zero, 3000 nonneg, 500 SOC5, 100 exp, 100 pow0.3), P=diag+rank10"
+
     cone_roof = None
     if not args.no_cone_roofline and rank == 0:
-        cone_roof = run_cone_roofline(clr, W, peaks)
+        cone_roof = run_cone_roofline(clr, W, {"hbm_gbs": peaks["hbm_gbs"], "source": copy_peaks["source"]})
 
     serving = None
     if not args.no_serving:
-        serving = run_serving(args, clr, W)
+        stream_reqs = make_stream(args, clr, W)
+        serving = {"fp64_factor": run_serving(args, clr, W, 64, stream_reqs),
+                   "fp32_factor": run_serving(args, clr, W, 32, stream_reqs, sweep_points=(0.8,), k_one=100)}
 
     if rank == 0:
         cpu = None
@@ -610,21 +711,24 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64 (f%d factor)" % args.factor_bits, "data": "synthetic",
                 "config": {"workload": WORKLOAD, "seed": args.seed, "factor_bits": args.factor_bits,
-                           "eps_feas": 1e-8, "l2": "flushed (256 MB write) before every timed solve",
+                           "eps_feas": 1e-8, "step": "one IPM iteration (clr_solve_iterate); the timed region "
+                           "starts a fresh solve and restarts one whenever a solve ends",
+                           "l2": "flushed (256 MB write) before every timed step; the KKT factor (%.0f MB) is "
+                                 "larger than L2 as well" % (sym["l_nnz"] * 4 / 1e6),
                            "parallelism": "replicas" if ws > 1 else "single GPU",
-                           "ir_stop_ratio": main.settings.ir_stop_ratio, "cuda_graphs": not args.no_graph},
-                "time_to_tol_ms": {"median": float(np.median(times)), "fp64_factor": fp64["time_to_tol_ms"] if fp64
-                                   else None},
-                "iterations": infos[-1]["iterations"], "status": infos[-1]["status_name"],
-                "objective_rel_err_vs_planted": obj_err, "res_primal": infos[-1]["res_primal"],
-                "res_dual": infos[-1]["res_dual"], "ir_steps_total": infos[-1]["ir_steps_total"],
-                "fp64_from_iter": infos[-1]["fp64_from_iter"], "fp64_factor": fp64, "phase_ms_per_solve": phases, "roofline": roofline,
-                "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-                "serving": serving, "cone_roofline": cone_roof,
+                           "ir_stop_ratio": args.ir_stop_ratio, "cuda_graphs": not args.no_graph,
+                           "escalate_ratio": 0.1},
+                "iterations_timed": iters, "solves_restarted_in_timed_region": restarts,
+                "time_to_tol_ms": ttt, "roofline": roofline, "peaks": peaks,
+                "gpu_launches": int(pf32["kernel_launches"] * iters / max(1, pf32["iterations"])),
+                "gpu_launches_note": "kernels per timed region, from the solver's count per full solve scaled by "
+                                     "the iterations timed",
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+                "mixed_cone_qp": mixed, "serving": serving, "cone_roofline": cone_roof,
+                "generation_s": t_gen,
                 "symbolic": {k: sym[k] for k in ("kkt_dim", "l_nnz", "factor_flops", "n_supernodes", "n_levels",
                                                  "max_front")}}
         print(json.dumps(line), flush=True)
-    main.free()
     if ws > 1:
         torch.distributed.destroy_process_group()
 

@@ -125,8 +125,8 @@ typedef struct {
   double escalate_ratio;      /* factor_bits 32/16 with fp64_escalation: also escalate when a KKT solve of an
                                  iteration ends its refinement above t_abs + t_rel ||rhs|| with ||r||_inf larger
                                  than escalate_ratio times the largest entry of the iterate's scaled residual G
-                                 (the direction is then too inexact to reduce the feasibility residuals);
-                                 default 0.1, 0 = off */
+                                 while the primal or dual residual still fails its termination test (the
+                                 direction is then too inexact to reduce it); default 0.1, 0 = off */
 } clr_settings;
 
 typedef struct {
@@ -175,6 +175,9 @@ typedef struct {
   double factor_ms;         /* numeric LDL^T (all iterations) */
   double solve_step_ms;     /* KKT solves with refinement, directions, step lengths, update */
   double factor_flops;      /* flops of one numeric factorization (symbolic count) */
+  double factor64_ms;       /* the part of factor_ms spent in iterations with the FP64 factor */
+  int32_t factorizations64; /* iterations factored with the FP64 factor (factor_bits 64, or after escalation) */
+  int32_t pad;
 } clr_perf;
 
 typedef struct clr_solver clr_solver;

@@ -89,7 +89,8 @@ class clr_server_stats(C.Structure):
 class clr_perf(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("iterations", C.c_int32), ("factorizations", C.c_int32),
                 ("init_ms", C.c_double), ("resid_cones_ms", C.c_double), ("factor_ms", C.c_double),
-                ("solve_step_ms", C.c_double), ("factor_flops", C.c_double)]
+                ("solve_step_ms", C.c_double), ("factor_flops", C.c_double), ("factor64_ms", C.c_double),
+                ("factorizations64", C.c_int32), ("pad", C.c_int32)]
 
 
 _LIB = None

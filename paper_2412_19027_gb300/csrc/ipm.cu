@@ -383,11 +383,12 @@ __global__ void k_fin_resid(IterScal* scs, const ProbConst* pcs, const double* p
       status = CLR_MAX_ITER;
   }
   sc.status = status;
+  sc.feas_ratio = fmax(nrp / (tp.eps_feas * fmax(1.0, pc.bnorm + nx + ns)),
+                       nrd / (tp.eps_feas * fmax(1.0, pc.qnorm + nx + nz)));
   if (status == 0) {
     // the complementarity gap still falls while the residuals stay: with a
     // low-precision factor, the accuracy of the KKT solves is what holds them up
-    const double feas = fmax(nrp / (tp.eps_feas * fmax(1.0, pc.bnorm + nx + ns)),
-                             nrd / (tp.eps_feas * fmax(1.0, pc.qnorm + nx + nz)));
+    const double feas = sc.feas_ratio;
     if (sc.feas_best == 0.0 || feas < 0.5 * sc.feas_best) {
       sc.feas_best = feas;
       sc.mu_at_best = mu;
@@ -710,7 +711,9 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
-      const bool inexact = sp.escalate_ratio > 0 && q.ir_worst > sp.escalate_ratio * q.g_scaled;
+      // the direction is too inexact to reduce feasibility residuals that still fail
+      // their termination test
+      const bool inexact = sp.escalate_ratio > 0 && q.ir_worst > sp.escalate_ratio * q.g_scaled && q.feas_ratio > 1.0;
       if ((q.ir_fail || q.feas_stall >= 3 || inexact) && sp.escalate_on) {
         q.alpha_c = 0.0;
         q.escalate = 1;  // redo the iteration with the FP64 factor
@@ -1560,6 +1563,7 @@ int Solver::solve_begin() {
 }
 
 int Solver::step_launch() {
+  step64_ = use64();
   int rc = launch_iteration();
   if (rc) return rc;
   perf.kernel_launches += iter_kernels_[(use64() && st.factor_bits != 64) ? 1 : 0];
@@ -1623,7 +1627,13 @@ int Solver::finish_step() {
   }
   if (full || !bf_host_->all_halt) {
     if (cudaEventElapsedTime(&ms, ev_[2], ev_[3]) == cudaSuccess) perf.resid_cones_ms += ms;
-    if (cudaEventElapsedTime(&ms, ev_[3], ev_[4]) == cudaSuccess) perf.factor_ms += ms;
+    if (cudaEventElapsedTime(&ms, ev_[3], ev_[4]) == cudaSuccess) {
+      perf.factor_ms += ms;
+      if (step64_) {
+        perf.factor64_ms += ms;
+        perf.factorizations64 += 1;
+      }
+    }
     if (cudaEventElapsedTime(&ms, ev_[4], ev_[5]) == cudaSuccess) perf.solve_step_ms += ms;
     perf.factorizations += 1;
   } else if (cudaEventElapsedTime(&ms, ev_[2], ev_[5]) == cudaSuccess) {

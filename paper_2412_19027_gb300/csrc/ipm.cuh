@@ -114,6 +114,7 @@ class Solver {
   cudaGraphExec_t igexec_ = nullptr;
   int64_t iter_kernels_[2] = {0, 0}, init_kernels_ = 0, body_kernels_[2] = {0, 0};
   bool escalated_ = false;       // this solve continues with the FP64 factor
+  bool step64_ = false;          // the last launched iteration factored in FP64
   bool f64_ready_ = false;       // f64_ allocated
   std::vector<int> esc_iter_;    // per problem: iteration of the escalation, -1
   bool use64() const { return st.factor_bits == 64 || escalated_; }

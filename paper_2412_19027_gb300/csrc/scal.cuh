@@ -58,6 +58,8 @@ struct IterScal {
   // largest scaled residual |G| of the iterate, and the largest final refinement
   // residual of this iteration's KKT solves that ended above the tolerance
   double g_scaled, ir_worst;
+  // max of the two feasibility termination ratios r/(eps (1 + norms)) of the iterate
+  double feas_ratio;
 };
 
 // Constants of one problem (device memory, written at setup).
