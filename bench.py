@@ -134,6 +134,9 @@ def parse():
                     help="run only the cone kernels at the stress shapes and print their JSON (for profiling)")
     ap.add_argument("--cone-shift", type=int, default=0, help="divide the stress shapes by 2^shift")
     ap.add_argument("--serve-requests", type=int, default=10_000)
+    ap.add_argument("--init-only", action="store_true",
+                    help="set up the workload (--n, --factor-bits, --no-graph) and run only the initial point "
+                         "(one factorization and its solves), then exit: the case the factorization profiles use")
     return ap.parse_args()
 
 
@@ -530,6 +533,18 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"cone_roofline": run_cone_roofline(clr, W, measured_peaks(), 3, args.cone_shift)}),
                   flush=True)
+        return
+    if args.init_only:
+        if rank == 0:
+            prob = W.banded_lp(args.seed, n=args.n) if args.n else W.banded_lp(args.seed)
+            st = clr.clr_default_settings(args.factor_bits, ir_stop_ratio=args.ir_stop_ratio, max_iter=0,
+                                          use_graph=0 if args.no_graph else 1)
+            s_ = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+            s_.solve()
+            info, sym = s_.info(), s_.symbolic_stats()
+            s_.free()
+            print(json.dumps({"init_only": {"status": info["status_name"], "kkt_dim": sym["kkt_dim"],
+                                            "l_nnz": sym["l_nnz"], "n_levels": sym["n_levels"]}}), flush=True)
         return
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 256 MB > 129 MB L2

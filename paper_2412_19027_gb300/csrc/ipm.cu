@@ -1553,6 +1553,7 @@ int Solver::solve_begin() {
   first_step_ = true;
   escalated_ = false;
   esc_iter_.assign(lay.B, -1);
+  for (int64_t p = 0; p < lay.B; ++p) sc_host_[p].iter = 0;  // host mirror: no iteration of this solve yet
   int rc = launch_init();
   if (rc) return rc;
   perf.kernel_launches += init_kernels_;
