@@ -381,6 +381,204 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
   run.flush(sc, &IterScal::hmax_bits);
 }
 
+// ---------------------------------------------------------------- small SOCs, a thread per cone
+// When every SOC has at most kSocT rows (the common case: SOC(3..8) in MPC, portfolio
+// and the mixed-cone QP) one thread holds a cone's rows in registers.  The per-cone
+// scalars -- J-norms, gamma, eta and their square roots and divisions -- are then
+// computed once per cone, where a lane group computed them once per lane; these passes
+// are bound by the FP64 pipe (~2 DFMA per clock per SM), so the redundant work was
+// what they spent their time on.  The formulas are those of the lane-group kernels.
+constexpr int kSocT = 8;
+inline unsigned soc_t_grid(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16 * kSMs));
+}
+#define SOC_THREAD_LOOP \
+  for (int64_t cone = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cone < cd.n_soc; \
+       cone += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void __launch_bounds__(256) k_scale_soc_t(ConeDev cd, const double* __restrict__ s,
+                                                     const double* __restrict__ z, IterScal* sc, const int* skip) {
+  if (skip && *skip) return;
+  RunExt<true> run;
+  SOC_THREAD_LOOP {
+    const int64_t off = cd.soc_off[cone];
+    const int d = cd.soc_dim[cone];
+    double sv[kSocT], zv[kSocT], wb[kSocT];
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j) {
+      sv[j] = j < d ? s[off + j] : 0.0;
+      zv[j] = j < d ? z[off + j] : 0.0;
+    }
+    double s1 = 0, z1 = 0, sz = sv[0] * zv[0];
+#pragma unroll
+    for (int j = 1; j < kSocT; ++j) {
+      s1 += sv[j] * sv[j];
+      z1 += zv[j] * zv[j];
+      sz += sv[j] * zv[j];
+    }
+    const double ns1 = sqrt(s1), nz1 = sqrt(z1);
+    const double ns = sqrt((sv[0] - ns1) * (sv[0] + ns1)), nzj = sqrt((zv[0] - nz1) * (zv[0] + nz1));
+    const double sbzb = sz / (ns * nzj);
+    const double gamma = sqrt(0.5 * (1.0 + sbzb));
+    const double eta = sqrt(ns / nzj);
+    const double inv2g = 1.0 / (2.0 * gamma);
+    const double rs = 1.0 / ns, rz = 1.0 / nzj;
+    double wz = 0, w1z1 = 0;
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j) {
+      wb[j] = (j == 0) ? (sv[0] * rs + zv[0] * rz) * inv2g : (sv[j] * rs - zv[j] * rz) * inv2g;
+      wz += wb[j] * zv[j];
+      if (j > 0) w1z1 += wb[j] * zv[j];
+    }
+    const double coef = zv[0] + w1z1 / (1.0 + wb[0]);
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j) {
+      if (j >= d) continue;
+      cd.soc_wb[off + j] = wb[j];
+      cd.soc_lam[off + j] = (j == 0) ? eta * wz : eta * (zv[j] + coef * wb[j]);
+    }
+    cd.soc_eta[cone] = eta;
+    // H = eta^2 (2 wb wb' - J), packed lower, column-major; KKT value is -H
+    const double e2 = eta * eta;
+    double* kb = cd.kvz + cd.soc_kb[cone];
+    double mx = 0.0;
+    int q = 0;
+#pragma unroll
+    for (int c = 0; c < kSocT; ++c) {
+#pragma unroll
+      for (int r = c; r < kSocT; ++r) {
+        if (r >= d || c >= d) continue;
+        double h = 2.0 * e2 * wb[r] * wb[c];
+        if (r == c) {
+          h += (c == 0) ? -e2 : e2;
+          mx = fmax(mx, fabs(h));
+        }
+        kb[q++] = -h;
+      }
+    }
+    run.add(sc, &IterScal::hmax_bits, cd.row_pid[off], dbits(mx));
+  }
+  run.flush(sc, &IterScal::hmax_bits);
+}
+
+__device__ __forceinline__ double soc_step_t(const double* x, const double* dx) {
+  double a2 = 0, b2 = 0, c2 = 0;
+#pragma unroll
+  for (int j = 1; j < kSocT; ++j) {
+    a2 += dx[j] * dx[j];
+    b2 += x[j] * dx[j];
+    c2 += x[j] * x[j];
+  }
+  const double A = dx[0] * dx[0] - a2;
+  const double B = x[0] * dx[0] - b2;
+  const double C = x[0] * x[0] - c2;
+  double r = INFINITY;
+  if (A == 0.0) {
+    if (B < 0) r = -C / (2.0 * B);
+  } else {
+    const double disc = B * B - A * C;
+    if (disc >= 0) {
+      const double sq = sqrt(disc);
+      const double r1 = (-B - sq) / A, r2 = (-B + sq) / A;
+      if (r1 > 0) r = fmin(r, r1);
+      if (r2 > 0) r = fmin(r, r2);
+    }
+  }
+  if (dx[0] < 0) r = fmin(r, -x[0] / dx[0]);
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_step_soc_t(ConeDev cd, const double* __restrict__ s,
+                                                    const double* __restrict__ ds, const double* __restrict__ z,
+                                                    const double* __restrict__ dz, IterScal* sc, const int* skip) {
+  if (skip && *skip) return;
+  RunExt<false> run;
+  SOC_THREAD_LOOP {
+    const int64_t off = cd.soc_off[cone];
+    const int d = cd.soc_dim[cone];
+    double x[kSocT], dx[kSocT], y[kSocT], dy[kSocT];
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j) {
+      x[j] = j < d ? s[off + j] : 0.0;
+      dx[j] = j < d ? ds[off + j] : 0.0;
+      y[j] = j < d ? z[off + j] : 0.0;
+      dy[j] = j < d ? dz[off + j] : 0.0;
+    }
+    const double a = d > 0 ? fmin(soc_step_t(x, dx), soc_step_t(y, dy)) : INFINITY;
+    if (a < INFINITY) run.add(sc, &IterScal::amin_bits, cd.row_pid[off], dbits(a));
+  }
+  run.flush(sc, &IterScal::amin_bits);
+}
+
+// y = W-bar x, or J W-bar J x (jconj), for one cone in registers
+__device__ __forceinline__ void soc_wbar_t(const double* wb, const double* x, double* y, bool jconj) {
+  double w1x1 = 0;
+#pragma unroll
+  for (int j = 1; j < kSocT; ++j) w1x1 += wb[j] * x[j];
+  const double w0 = wb[0], x0 = x[0];
+  if (!jconj) {
+    const double coef = x0 + w1x1 / (1.0 + w0);
+    y[0] = w0 * x0 + w1x1;
+#pragma unroll
+    for (int j = 1; j < kSocT; ++j) y[j] = x[j] + coef * wb[j];
+  } else {
+    const double coef = x0 - w1x1 / (1.0 + w0);
+    y[0] = w0 * x0 - w1x1;
+#pragma unroll
+    for (int j = 1; j < kSocT; ++j) y[j] = x[j] - coef * wb[j];
+  }
+}
+
+// d_s = W (lambda \ (lambda o lambda + (W^{-1} ds_a) o (W dz_a) - sigma mu e)), W = eta W-bar
+__global__ void __launch_bounds__(256) k_ds_soc_t(ConeDev cd, const double* __restrict__ dsa,
+                                                  const double* __restrict__ dza, const IterScal* sc,
+                                                  double* __restrict__ out, const int* skip) {
+  if (skip && *skip) return;
+  SOC_THREAD_LOOP {
+    const int64_t off = cd.soc_off[cone];
+    const int d = cd.soc_dim[cone];
+    const double eta = cd.soc_eta[cone];
+    double wb[kSocT], lam[kSocT], a[kSocT], b[kSocT], u[kSocT], v[kSocT];
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j) {
+      wb[j] = j < d ? cd.soc_wb[off + j] : 0.0;
+      lam[j] = j < d ? cd.soc_lam[off + j] : 0.0;
+      a[j] = j < d ? dsa[off + j] : 0.0;
+      b[j] = j < d ? dza[off + j] : 0.0;
+    }
+    soc_wbar_t(wb, a, u, true);   // W-bar^{-1} ds_a = J W-bar J ds_a
+    soc_wbar_t(wb, b, v, false);  // W-bar dz_a
+    double uv = 0, ll = 0;
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j) {
+      u[j] /= eta;
+      v[j] *= eta;
+      uv += u[j] * v[j];
+      ll += lam[j] * lam[j];
+    }
+    const double smu = sc[cd.row_pid[off]].sigma_mu;
+    // w = lam o lam + u o v - sigma mu e  (into a)
+    a[0] = ll + uv - smu;
+#pragma unroll
+    for (int j = 1; j < kSocT; ++j) a[j] = 2.0 * lam[0] * lam[j] + u[0] * v[j] + v[0] * u[j];
+    double l1v = 0, l1sq = 0;
+#pragma unroll
+    for (int j = 1; j < kSocT; ++j) {
+      l1v += lam[j] * a[j];
+      l1sq += lam[j] * lam[j];
+    }
+    const double l0 = lam[0];
+    const double x0 = (l0 * a[0] - l1v) / (l0 * l0 - l1sq);
+    b[0] = x0;
+#pragma unroll
+    for (int j = 1; j < kSocT; ++j) b[j] = (a[j] - x0 * lam[j]) / l0;
+    soc_wbar_t(wb, b, u, false);
+#pragma unroll
+    for (int j = 0; j < kSocT; ++j)
+      if (j < d) out[off + j] = eta * u[j];
+  }
+}
+
 __global__ void k_scale_exppow(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
                                const int* skip) {
   if (skip && *skip) return;
@@ -681,7 +879,7 @@ int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const dou
   if (cd.m_zero + cd.m_nonneg > 0)
     k_scale_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, s, z, sc, skip);
   if (cd.n_soc > 0) {
-    if (cd.soc_dmax <= 8) k_scale_soc<8><<<soc_grid(cd, 8), 256, 0, st>>>(cd, s, z, sc, skip);
+    if (cd.soc_dmax <= kSocT) k_scale_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, s, z, sc, skip);
     else k_scale_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, z, sc, skip);
   }
   if (cd.n_exp + cd.n_pow > 0)
@@ -891,7 +1089,7 @@ int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, co
                          const double* dz, IterScal* sc, const int* skip) {
   if (cd.m_nonneg > 0) k_step_nonneg<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   if (cd.n_soc > 0) {
-    if (cd.soc_dmax <= 8) k_step_soc<8><<<soc_grid(cd, 8), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+    if (cd.soc_dmax <= kSocT) k_step_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
     else k_step_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   }
   if (cd.n_psd > 0) {
@@ -1323,7 +1521,7 @@ int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const
   if (cd.m_zero + cd.m_nonneg > 0)
     k_ds_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
   if (cd.n_soc > 0) {
-    if (cd.soc_dmax <= 8) k_ds_soc<8><<<soc_grid(cd, 8), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
+    if (cd.soc_dmax <= kSocT) k_ds_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
     else k_ds_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
   }
   if (cd.n_exp + cd.n_pow > 0)

@@ -71,13 +71,15 @@ class Server {
     streams_.resize(max_active_, nullptr);
     slot_free_.assign(max_active_, 1);
     for (cudaStream_t& s : streams_) CLR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    // keep freed device memory in the pool: cohorts come and go
+    // keep freed device memory in the pool while the server runs (cohorts come and
+    // go); the pool's previous release threshold is restored by stop()
     int dev = 0;
     CLR_CUDA(cudaGetDevice(&dev));
-    cudaMemPool_t pool;
-    CLR_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    CLR_CUDA(cudaDeviceGetDefaultMemPool(&pool_, dev));
+    CLR_CUDA(cudaMemPoolGetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &pool_thr_old_));
     uint64_t thr = UINT64_MAX;
-    CLR_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    CLR_CUDA(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &thr));
+    pool_set_ = true;
     const int nw = (int)std::max<unsigned>(1, std::min<unsigned>(std::thread::hardware_concurrency(), 8));
     for (int i = 0; i < nw; ++i) workers_.emplace_back([this] { worker(); });
     builder_ = std::thread([this] { build_loop(); });
@@ -103,6 +105,10 @@ class Server {
     for (cudaStream_t s : streams_)
       if (s) cudaStreamDestroy(s);
     streams_.clear();
+    if (pool_set_) {
+      cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &pool_thr_old_);
+      pool_set_ = false;
+    }
   }
 
   int submit(const clr_problem* p, uint64_t* ticket) {
@@ -372,6 +378,9 @@ class Server {
     }
   }
 
+  cudaMemPool_t pool_ = nullptr;  // the device's default pool (stream-ordered allocations)
+  uint64_t pool_thr_old_ = 0;      // its release threshold before start()
+  bool pool_set_ = false;
   size_t budget_;
   int max_cohort_, max_active_;
   clr_settings st_;

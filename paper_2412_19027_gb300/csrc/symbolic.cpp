@@ -690,7 +690,9 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
       int64_t ne = 0;
       for (int64_t ch : children[P])
         if (!is_pushed[ch]) ne += upd_rows(ch) * (upd_rows(ch) + 1) / 2;
-      if (ne > 0 && fP * fP <= kDirectTargets) {
+      // the direct path scans all fP^2 targets of the parent: taken when the
+      // children's contributions are comparable to that (else the sorted pairs)
+      if (ne > 0 && fP * fP <= kDirectTargets && fP * fP <= 4 * ne) {
         // two passes straight into the lists: count the sources of every target of
         // P's front, then place each source at its target's next slot -- targets in
         // increasing order, each target's sources in child / column / row order, as
