@@ -508,6 +508,27 @@ def factor_roofline(perf, sym, peaks):
     return out
 
 
+def solve_roofline(perf, info, sym, peaks):
+    """The solve phase (refined KKT solves, direction recovery, step lengths,
+    update): unit = one KKT solve (a forward and a backward sweep over the factor);
+    algorithmic bytes = 2 nnz(L) x the factor's element size (each sweep reads the
+    factor once; vectors are O(N) and left out); solves = 3 per iteration + the
+    refinement steps (the initial point's are in init_ms); time = the phase's CUDA
+    events, so the other work of the phase is charged to the solves."""
+    n64 = perf["factorizations64"]
+    n_all = max(1, perf["factorizations"] - 1)
+    w = (8.0 * n64 + 4.0 * (n_all - n64)) / n_all if n_all else 8.0
+    solves = 3 * info["iterations"] + info["ir_steps_total"]
+    if solves <= 0 or perf["solve_step_ms"] <= 0:
+        return None
+    per = perf["solve_step_ms"] / solves
+    byts = 2.0 * sym["l_nnz"] * w
+    gbs = byts / (per / 1e3) / 1e9
+    return {"solves": solves, "ms_per_solve": per, "bytes_per_solve": byts, "achieved_gbs": gbs,
+            "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"], "bound": "hbm",
+            "note": "factor element size averaged over the iterations' FP32 / FP64 factors"}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -629,7 +650,8 @@ def run_ours(args):
                           "ir_steps_total": inf32["ir_steps_total"], "setup_s": setup_s,
                           "phase_ms": {"init": pf32["init_ms"], "residuals+cones": pf32["resid_cones_ms"],
                                        "factorization": pf32["factor_ms"], "solves+steps": pf32["solve_step_ms"]},
-                          "factorization_roofline": factor_roofline(pf32, sym, peaks)}
+                          "factorization_roofline": factor_roofline(pf32, sym, peaks),
+                          "solve_roofline": solve_roofline(pf32, inf32, sym, peaks)}
     # end to end through the C ABI with host buffers: q, b in; x, s, z out (one full solve per step)
     e2e = None
     if not args.no_e2e:
@@ -662,7 +684,8 @@ def run_ours(args):
                     "ir_steps_total": inf["ir_steps_total"], "setup_s": su,
                     "phase_ms": {"init": pf["init_ms"], "residuals+cones": pf["resid_cones_ms"],
                                  "factorization": pf["factor_ms"], "solves+steps": pf["solve_step_ms"]},
-                    "factorization_roofline": factor_roofline(pf, sym, peaks)}
+                    "factorization_roofline": factor_roofline(pf, sym, peaks),
+                    "solve_roofline": solve_roofline(pf, inf, sym, peaks)}
         sv_.free()
     if "fp64_factor" in ttt:
         ttt["fp32_speedup_vs_fp64_factor"] = ttt["fp64_factor"]["ms"] / ttt["fp32_factor"]["ms"]
