@@ -125,8 +125,8 @@ typedef struct {
   double escalate_ratio;      /* factor_bits 32/16 with fp64_escalation: also escalate when a KKT solve of an
                                  iteration ends its refinement above t_abs + t_rel ||rhs|| with ||r||_inf larger
                                  than escalate_ratio times the largest entry of the iterate's scaled residual G
-                                 while the primal or dual residual still fails its termination test (the
-                                 direction is then too inexact to reduce it); default 0.1, 0 = off */
+                                 while the primal or dual residual is still more than 100 times its termination
+                                 tolerance (the direction is then too inexact to reduce it); default 0.1, 0 = off */
 } clr_settings;
 
 typedef struct {

@@ -711,9 +711,9 @@ __global__ void k_fin_step(IterScal* sc, int64_t B, StepParams sp, int combined,
         h[8] = q.sigma;
       }
     } else {
-      // the direction is too inexact to reduce feasibility residuals that still fail
-      // their termination test
-      const bool inexact = sp.escalate_ratio > 0 && q.ir_worst > sp.escalate_ratio * q.g_scaled && q.feas_ratio > 1.0;
+      // the direction is too inexact to reduce feasibility residuals still far (100x)
+      // above their termination tolerance
+      const bool inexact = sp.escalate_ratio > 0 && q.ir_worst > sp.escalate_ratio * q.g_scaled && q.feas_ratio > 100.0;
       if ((q.ir_fail || q.feas_stall >= 3 || inexact) && sp.escalate_on) {
         q.alpha_c = 0.0;
         q.escalate = 1;  // redo the iteration with the FP64 factor
