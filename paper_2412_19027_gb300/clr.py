@@ -142,7 +142,7 @@ def _lib():
         L.clr_cones_time.argtypes = [P(clr_cone), C.c_int32] + [P(C.c_double)] * 4 + [C.c_double, C.c_int32,
                                                                                      P(clr_cone_times)]
         L.clr_ldl_solve.argtypes = [P(clr_csc), P(C.c_double), P(C.c_int64), C.c_int32, C.c_double, C.c_double,
-                                    P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32)]
+                                    P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int32), C.c_int32]
         L.clr_dense_ldl_solve_noalloc.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_double, C.c_double, vp, vp]
         L.clr_probe_peaks.argtypes = [C.c_int32, vp, P(clr_peaks)]
         L.clr_solve_begin.argtypes = [vp]
@@ -589,7 +589,8 @@ def clr_cones_time(cones, s, z, ds, dz, mu, reps=10):
     return {k: getattr(out, k) for (k, _) in clr_cone_times._fields_}
 
 
-def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1e-13, dyn_reg_delta=2e-7):
+def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1e-13, dyn_reg_delta=2e-7,
+                  big_front_schedule=1):
     keep = []
     Kc = _csc(sp.tril(sp.csc_matrix(K_lower)), keep)
     signs = np.ascontiguousarray(signs, dtype=np.float64)
@@ -602,7 +603,7 @@ def clr_ldl_solve(K_lower, signs, rhs, order=None, factor_bits=64, dyn_reg_eps=1
         order = np.ascontiguousarray(order, dtype=np.int64)
         ordp = order.ctypes.data_as(C.POINTER(C.c_int64))
     _check(_lib().clr_ldl_solve(C.byref(Kc), _dptr(signs), ordp, factor_bits, dyn_reg_eps, dyn_reg_delta, _dptr(rhs),
-                                _dptr(x), _dptr(D), C.byref(hits)), "clr_ldl_solve")
+                                _dptr(x), _dptr(D), C.byref(hits), int(big_front_schedule)), "clr_ldl_solve")
     return x, D, hits.value
 
 

@@ -5,6 +5,20 @@
 // (bigfront.cu); only the scheduling differs: the diagonal block of panel p + 1
 // starts as soon as its own tile has received panel p's update, while the rest
 // of panel p's updates are still running.
+//
+// FP32 factor, tensor-core variant (TC): the producers of L, L D and E_KC tiles
+// also store packed TF32 hi/lo operand tiles (bigfront.cuh, FlowTc); the U and
+// EU tasks load their two operand tiles with one TMA tensor copy each
+// (cp.async.bulk.tensor, completion on an mbarrier) and issue 16 tcgen05.mma
+// kind::tf32 (M = 128, N = 64, K = 8) into a 128 x 64 FP32 accumulator in
+// tensor memory: A = [L_hi; L_lo] (128 rows), B = the high then the low part of
+// the other operand, so that lanes 0-63 hold L_hi B and lanes 64-127 L_lo B;
+// their sum is the FP32 product to ~2^-21 relative (every partial product of
+// two TF32 parts is exact in FP32).
+#include <cuda.h>
+
+#include <cstring>
+
 #include "bfdiag.cuh"
 #include "bigfront.cuh"
 
@@ -88,12 +102,105 @@ __device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
   v[3] = b.y;
 }
 
+// ---------------------------------------------------------------- tensor-core helpers
+// Packed operand tile: element (row, k) at word (k / 4) * 512 + row * 4 + k % 4 --
+// K-major core matrices of 8 rows x 16 bytes, adjacent in K 2048 bytes apart and
+// in rows 128 bytes apart; rows 0-63 the high TF32 parts, 64-127 the low parts.
+__device__ __forceinline__ int pk_word(int row, int k) { return ((k >> 2) << 9) + (row << 2) + (k & 3); }
+// v = hi + lo + O(2^-22 |v|): hi = v with its 13 low mantissa bits cleared (a TF32
+// value, so the tensor core reads it unchanged), lo = v - hi (exact) rounded to TF32.
+__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+  uint32_t l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hi));
+  lo = __uint_as_float(l);
+}
+// All threads: store the 64 x 64 tile val(row, k) as a packed operand tile at dst;
+// each pass of the CTA writes 1 KB of high and 1 KB of low parts, contiguous.
+template <typename V>
+__device__ __forceinline__ void pk_write(float* dst, V val) {
+#pragma unroll 4
+  for (int it = 0; it < 16; ++it) {
+    const int idx = threadIdx.x + NT * it;
+    const int q = idx & 3, r = (idx >> 2) & 63, kg = idx >> 8;
+    float hi, lo;
+    split_tf32(val(r, 4 * kg + q), hi, lo);
+    const int w = (kg << 9) + (r << 2) + q;
+    dst[w] = hi;
+    dst[w + 256] = lo;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// Tile indices within a front's packed tiles: PL(p, i), i > p; PLD = PL + nL; PE(p, e), e <= p.
+__device__ __forceinline__ int64_t pk_l(int64_t nbf, int p, int64_t i) {
+  return (int64_t)p * (nbf - 1) - (int64_t)p * (p - 1) / 2 + (i - p - 1);
+}
+__device__ __forceinline__ int64_t pk_e(int64_t nL, int p, int64_t e) { return 2 * nL + (int64_t)p * (p + 1) / 2 + e; }
+struct PkRef {  // the packed tiles of the front a task works on
+  float* pk = nullptr;  // the level's tiles
+  int64_t base = 0;     // first tile of the front
+  int64_t nL = 0;
+  __device__ float* tile(int64_t t) const { return pk + kPkWords * (base + t); }
+};
+__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// shared-memory descriptor of a packed tile (K-major, no swizzle; LBO 2048, SBO 128 bytes)
+__device__ __forceinline__ uint64_t pk_desc(uint32_t a) {
+  uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)(2048 >> 4) << 16;
+  d |= (uint64_t)(128 >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // tcgen05 descriptor version; base offset 0, no swizzle
+  return d;
+}
+// bounded wait on an mbarrier phase (false: it ran out)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// one TMA tensor copy of packed tile `tile` (32 rows of 256 floats of the map) to dst
+__device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap* map, int64_t tile, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"((int)(tile * 32)), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+constexpr int kTcTileBytes = 128 * NB * 4;                  // one packed tile in shared memory (32 KB)
+constexpr size_t kTcSmemFlow = 2 * (size_t)kTcTileBytes + 1024;  // A, B and the 1024-byte alignment slack
+// M = 128, N = 64, D FP32 (bit 4), A and B TF32 (format 2 at bits 7 and 10), both K-major
+constexpr uint32_t kTf32Idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                                ((uint32_t)(128 >> 4) << 24);
+
 // D(p): LDL^T of the pw x pw diagonal block with dynamic regularisation (see
 // bfdiag.cuh); L and the pivots written back, Linv = L_KK^{-1} written into
 // E_KK, which it equals (the zeros above its diagonal are the E pool's).
-template <typename T>
+template <typename T, bool TC>
 __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T* F, T* E, T* Dp,
-                          const int8_t* dsign, T eps, T delta, int* hits, T* sm, DiagScratch<T>& sh) {
+                          const int8_t* dsign, T eps, T delta, int* hits, T* sm, DiagScratch<T>& sh, const PkRef& pkr) {
   const int64_t f = g.f, k0 = (int64_t)p * NB;
   const int pw = bnrow(g, p);
   const int64_t kp = bf.k0pos[b] + k0;
@@ -101,6 +208,13 @@ __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
   T* Li = E + bf.eoff[b] + k0 + k0 * f;
   const int nhit = bf_diag_block<T>(G, f, pw, Dp + kp, Li, f, false, dsign + kp, eps, delta, sm, sh);
   if (threadIdx.x == 0 && nhit) atomicAdd(hits, nhit);
+  if constexpr (TC) {  // PE(p, p): E_KK = Linv (unit lower), rows = its columns
+    const T* V = sm + 64 * kDiagLD;
+    pk_write(pkr.tile(pk_e(pkr.nL, p, p)), [&](int n, int k) -> float {
+      return (k < pw && n < pw && k >= n) ? (k == n ? 1.f : (float)V[k * kDiagLD + n]) : 0.f;
+    });
+    fence_proxy_async_global();
+  }
 }
 
 // DX(p), 1 <= p < P: the three links of the critical chain in one task, kept in
@@ -108,9 +222,9 @@ __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
 // published through the trsm word of block p as soon as they are written), the
 // update of the diagonal tile (p, p) by panel p-1, and D(p).  Same arithmetic,
 // in the same order, as the three separate tasks.
-template <typename T>
+template <typename T, bool TC>
 __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T* F, T* E, T* Dp, const int8_t* dsign,
-                       T eps, T delta, T* sm, DiagScratch<T>& sh, T* dl, int* trsm_word) {
+                       T eps, T delta, T* sm, DiagScratch<T>& sh, T* dl, int* trsm_word, const PkRef& pkr) {
   T* Bk = sm;                // K-major Linv of panel p - 1 (row j, k = l); work space of the factorization afterwards
   T* Xk = sm + NB * LDK;     // K-major F_{p,p-1} (row i, k = l), then L_{p,p-1}
   T* A = sm + 2 * NB * LDK;  // the diagonal tile (p, p), lower triangle, row stride LD
@@ -171,6 +285,12 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     const int i = idx % NB, j = idx / NB;
     if (i < pw) G[(k0 + i) + (kq + j) * f] = Xk[swz(j, i)];
   }
+  if constexpr (TC) {  // PL(p-1, p) and PLD(p-1, p) before the L rows are published
+    pk_write(pkr.tile(pk_l(g.nbf, p - 1, p)), [&](int r, int k) -> float { return r < pw ? (float)Xk[swz(k, r)] : 0.f; });
+    pk_write(pkr.tile(pkr.nL + pk_l(g.nbf, p - 1, p)),
+             [&](int r, int k) -> float { return r < pw ? (float)(Xk[swz(k, r)] * dl[k]) : 0.f; });
+    fence_proxy_async_global();
+  }
   __syncthreads();
   if (tid == 0) {
     __threadfence();
@@ -204,14 +324,21 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
   }
   __syncthreads();
   const int64_t kp = bf.k0pos[b] + k0;
-  return bf_diag_factor<T>(A, Bk, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp, eps, delta,
-                           sh);
+  const int nhit = bf_diag_factor<T>(A, Bk, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp,
+                                     eps, delta, sh);
+  if constexpr (TC) {  // PE(p, p) from Linv (in Bk, row stride kDiagLD)
+    pk_write(pkr.tile(pk_e(pkr.nL, p, p)), [&](int n, int k) -> float {
+      return (k < pw && n < pw && k >= n) ? (k == n ? 1.f : (float)Bk[k * kDiagLD + n]) : 0.f;
+    });
+    fence_proxy_async_global();
+  }
+  return nhit;
 }
 
 // T(p, i): L_IK = F_IK Linv^T D_K^{-1} for the rows of block i (each thread 4 x 4).
-template <typename T>
+template <typename T, bool TC>
 __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, T* F, const T* E,
-                          const T* Dp, T* sm, T* dl) {
+                          const T* Dp, T* sm, T* dl, const PkRef& pkr) {
   T* Bk = sm;             // K-major Linv (row j, k = l)
   T* Xk = sm + NB * LDK;  // K-major F_IK (row i, k = l), then L_IK (row i, k = j)
   const int64_t f = g.f, k0 = (int64_t)p * NB;
@@ -271,11 +398,19 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
     const int i = idx % NB, j = idx / NB;
     if (i < nr && j < pw) G[(r0 + i) + (k0 + j) * f] = Xk[swz(j, i)];
   }
+  if constexpr (TC) {  // PL(p, i) and PLD(p, i)
+    pk_write(pkr.tile(pk_l(g.nbf, p, bi)),
+             [&](int r, int k) -> float { return (r < nr && k < pw) ? (float)Xk[swz(k, r)] : 0.f; });
+    pk_write(pkr.tile(pkr.nL + pk_l(g.nbf, p, bi)),
+             [&](int r, int k) -> float { return (r < nr && k < pw) ? (float)(Xk[swz(k, r)] * dl[k]) : 0.f; });
+    fence_proxy_async_global();
+  }
 }
 
 // Efin(p, e): E_KC <- Linv E_KC for the E rows of panel p and column block e < p.
-template <typename T>
-__device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t e, T* E, T* sm) {
+template <typename T, bool TC>
+__device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t e, T* E, T* sm,
+                          const PkRef& pkr) {
   T* Ls = sm;
   T* Xs = sm + NB * LD;
   const int64_t f = g.f, k0 = (int64_t)p * NB, cb = (int64_t)e * NB;
@@ -312,6 +447,20 @@ __device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
     if (i >= pw) continue;
 #pragma unroll
     for (int bb = 0; bb < 4; ++bb) Eb[(k0 + i) + (cb + tc + 16 * bb) * f] = acc[a][bb];
+  }
+  if constexpr (TC) {  // PE(p, e): row n = E column cb + n, k = E row k0 + i
+    float* dst = pkr.tile(pk_e(pkr.nL, p, e));
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) {
+        const int i = tr + 16 * a, n = tc + 16 * bb;
+        float hi, lo;
+        split_tf32(i < pw ? (float)acc[a][bb] : 0.f, hi, lo);
+        dst[pk_word(n, i)] = hi;
+        dst[pk_word(n, i) + 256] = lo;
+      }
+    fence_proxy_async_global();
   }
 }
 
@@ -396,20 +545,135 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
   }
 }
 
-template <typename T>
+
+// U(p, i, j) / EU(p, i, e) on the tensor cores (FP32 factor): thread 0 copies
+// the packed operand tiles A = PL(p, i) and B = PLD(p, j) (U) or PE(p, e) (EU)
+// into shared memory with two TMA tensor copies and issues the 16 MMAs; the
+// other threads meanwhile load the target tile.  Lanes 0-63 of the accumulator
+// hold L_hi B, lanes 64-127 L_lo B; warps 2, 3, 6, 7 pass the low halves through
+// shared memory, warps 0, 1, 4, 5 form target - (high + low) and store it
+// (rows 32 (w % 4) + lane, columns 32 (w / 4) ...).  Returns false, with *err = 2,
+// if a wait ran out (the caller then stops; copies and MMAs in flight were
+// waited for once more, with the same bound).
+__device__ bool task_update_tc(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, int64_t bj,
+                               bool etile, float* F, float* E, const CUtensorMap* tmap, const PkRef& pkr,
+                               unsigned char* smtc, uint32_t bar_ld, uint32_t bar_mma, uint32_t parity,
+                               uint32_t tmem, int* err, int* s_flag) {
+  const int64_t f = g.f;
+  const int64_t i0 = brow0(g, bi);
+  const int ni = bnrow(g, bi);
+  const int64_t c0 = etile ? bj * NB : brow0(g, bj);
+  const int nc = bnrow(g, bj);
+  const bool diag = !etile && bi == bj;
+  float* base = etile ? E + bf.eoff[b] : F + bf.goff[b];
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const uint32_t sA = s_addr(smtc), sB = sA + kTcTileBytes;
+  if (tid == 0) {
+    const int64_t ta = pkr.base + pk_l(g.nbf, p, bi);
+    const int64_t tb = pkr.base + (etile ? pk_e(pkr.nL, p, bj) : pkr.nL + pk_l(g.nbf, p, bj));
+    fence_proxy_async_global();  // the tiles were released by generic stores (acquired above)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld), "r"(2 * kTcTileBytes)
+                 : "memory");
+    tma_tile(sA, tmap, ta, bar_ld);
+    tma_tile(sB, tmap, tb, bar_ld);
+  }
+  const int q = wid & 3, h = wid >> 2;
+  const int r = 32 * q + lane;  // output row of the top warps (q < 2)
+  float tv[32];
+  if (q < 2) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int cc = 32 * h + jj;
+      tv[jj] = (r < ni && cc < nc && (!diag || r >= cc)) ? __ldcg(base + (i0 + r) + (c0 + cc) * f) : 0.f;
+    }
+  }
+  if (tid == 0) {
+    if (mbar_wait(bar_ld, parity)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < NB / 8; ++ks) {
+        const uint32_t ko = (uint32_t)ks * 4096u;  // K = 8: two core matrices along K
+        mma_tf32(tmem, pk_desc(sA + ko), pk_desc(sB + ko), kTf32Idesc, ks > 0 ? 1u : 0u);
+        mma_tf32(tmem, pk_desc(sA + ko), pk_desc(sB + 1024u + ko), kTf32Idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                   : "memory");
+    } else {
+      atomicExch(err, 2);
+      *s_flag = 1;
+      mbar_wait(bar_ld, parity);  // once more for the copies in flight
+    }
+  }
+  __syncthreads();
+  if (*s_flag) return false;
+  if (!mbar_wait(bar_mma, parity)) atomicExch(s_flag, 1);
+  __syncthreads();
+  if (*s_flag) {
+    if (tid == 0) {
+      atomicExch(err, 2);
+      mbar_wait(bar_mma, parity);
+    }
+    return false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t v[32];
+  tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
+  float* X = reinterpret_cast<float*>(smtc);  // the low halves (the operands are consumed)
+  if (q >= 2) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) X[(32 * h + jj) * 64 + 32 * (q - 2) + lane] = __uint_as_float(v[jj]);
+  }
+  __syncthreads();
+  if (q < 2) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int cc = 32 * h + jj;
+      if (r < ni && cc < nc && (!diag || r >= cc))
+        base[(i0 + r) + (c0 + cc) * f] = tv[jj] - (__uint_as_float(v[jj]) + X[(32 * h + jj) * 64 + r]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  return true;
+}
+
+template <typename T, bool TC>
 __global__ void __launch_bounds__(NT, 2)
     k_bf_flow(BigFrontDev bf, const FlowTask* __restrict__ task, int64_t t0, int64_t nt, int* __restrict__ state,
               int64_t head_off, const int64_t* __restrict__ soff, T* F, T* E, T* Dp, const int8_t* __restrict__ dsign,
-              double eps_d, double delta_d, int* hits, int* err, const int* skip) {
+              double eps_d, double delta_d, int* hits, int* err, const int* skip, const __grid_constant__ CUtensorMap tmap,
+              float* pk) {
+  static_assert(!TC || sizeof(T) == 4, "tensor-core products: FP32 factor only");
   if (skip && *skip) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
+  // TC: packed tiles need a 1024-byte aligned base (the other tasks use the same space)
+  unsigned char* smtc = smraw + (TC ? ((1024u - (s_addr(smraw) & 1023u)) & 1023u) : 0u);
+  T* sm = reinterpret_cast<T*>(smtc);
   __shared__ DiagScratch<T> dsh;
   __shared__ T dl[NB];
   __shared__ FlowTask s_task;
   __shared__ int s_go;
+  __shared__ __align__(8) uint64_t s_bar[2];  // TC: TMA and MMA completion
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_flag;
   int* head = state + head_off;
   const int tid = threadIdx.x;
+  uint32_t tmem = 0, parity = 0;
+  if constexpr (TC) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(&s_bar[0])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(&s_bar[1])), "r"(1));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_flag = 0;
+    }
+    if ((tid >> 5) == 0) {  // 64 columns: the 128 x 64 FP32 accumulator
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&s_tmem)), "r"(64));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = s_tmem;
+  }
   for (;;) {
     if (tid == 0) {
       // The next ticket is taken only once this CTA is free: a ticket reserved
@@ -486,30 +750,45 @@ __global__ void __launch_bounds__(NT, 2)
     const FlowTask tk = s_task;
     const int64_t b = tk.bf;
     const Geo g{bf.f[b], bf.c[b], (bf.c[b] + NB - 1) / NB, flow_nbf(bf.f[b], bf.c[b])};
+    PkRef pkr;
+    if constexpr (TC) {
+      pkr.pk = pk;
+      pkr.base = bf.pkoff[b];
+      pkr.nL = flow_pk_nl(g.f, g.c);
+    }
+    bool stop = false;
     switch (tk.kind) {
       case 0:
-        task_diag<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, dsh);
+        task_diag<T, TC>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, dsh, pkr);
         break;
       case 5: {
         const Words w = words_of(state + soff[b], g);
-        const int nhit = task_dx<T>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, sm, dsh, dl, w.trsm + tk.p);
+        const int nhit =
+            task_dx<T, TC>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, sm, dsh, dl, w.trsm + tk.p, pkr);
         if (tid == 0 && nhit) atomicAdd(hits, nhit);
         break;
       }
       case 1:
-        task_trsm<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
+        task_trsm<T, TC>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl, pkr);
         break;
       case 2:
-        task_efin<T>(bf, b, g, tk.p, tk.j, E, sm);
-        break;
-      case 3:
-        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, false, F, E, Dp, sm, dl);
+        task_efin<T, TC>(bf, b, g, tk.p, tk.j, E, sm, pkr);
         break;
       default:
-        task_update<T>(bf, b, g, tk.p, tk.i, tk.j, true, F, E, Dp, sm, dl);
+        if constexpr (TC) {
+          stop = !task_update_tc(bf, b, g, tk.p, tk.i, tk.j, tk.kind != 3, F, E, &tmap, pkr, smtc,
+                                 s_addr(&s_bar[0]), s_addr(&s_bar[1]), parity, tmem, err, &s_flag);
+          parity ^= 1u;
+        } else {
+          task_update<T>(bf, b, g, tk.p, tk.i, tk.j, tk.kind != 3, F, E, Dp, sm, dl);
+        }
         break;
     }
+    // TC: the generic accesses to shared memory of this task come before the
+    // next task's TMA writes to it
+    if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (stop) break;
     if (tid == 0) {
       const Words w = words_of(state + soff[b], g);
       const int p = tk.p;
@@ -537,6 +816,11 @@ __global__ void __launch_bounds__(NT, 2)
       }
     }
   }
+  if constexpr (TC) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((tid >> 5) == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+  }
 }
 
 template <typename T>
@@ -544,6 +828,12 @@ size_t flow_smem() {  // the fused chain task's three blocks; the others need le
   constexpr int n = 2 * NB * LDK + NB * LD;
   static_assert(n >= kDiagSmem && NB * LDK >= NB * kDiagLD && LD == kDiagLD, "shared memory of the flow tasks");
   return n * sizeof(T);
+}
+// TC launch: the two packed operand tiles of a U / EU task (the other tasks
+// fit in the same space) from a 1024-byte aligned base
+size_t flow_smem_tc() {
+  static_assert(2 * (size_t)NB * LDK * 4 + (size_t)NB * LD * 4 + 1024 <= kTcSmemFlow, "shared memory of the TC flow");
+  return kTcSmemFlow;
 }
 }  // namespace
 
@@ -553,11 +843,45 @@ size_t flow_smem_one() {
   return flow_smem<T>() > (size_t)120 * 1024 ? flow_smem<T>() : (size_t)120 * 1024;
 }
 
+int flow_tc_encode(FlowTc* tc) {
+  if (!tc || !tc->pk || tc->tiles <= 0 || (reinterpret_cast<uintptr_t>(tc->pk) & 15) != 0) return CLR_E_INVALID;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q{};
+  CLR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess) return CLR_E_CUDA;
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  // rows of 256 floats (1 KB), 32 rows per packed tile; one box = one tile
+  const cuuint64_t dims[2] = {256, (cuuint64_t)tc->tiles * 32};
+  const cuuint64_t strides[1] = {256 * sizeof(float)};
+  const cuuint32_t box[2] = {256, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  CUtensorMap m;
+  const CUresult r = reinterpret_cast<Encode>(fn)(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tc->pk, dims, strides, box,
+                                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_cuda_error(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+    return CLR_E_CUDA;
+  }
+  static_assert(sizeof(CUtensorMap) == sizeof(tc->tmap), "tensor map size");
+  std::memcpy(tc->tmap, &m, sizeof(m));
+  return CLR_OK;
+}
+
 template <typename T>
-int BigFrontOps<T>::flow_occupancy() {
-  CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem_one<T>()));
+int BigFrontOps<T>::flow_occupancy(bool tc) {
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)flow_smem_one<T>()));
   int n = 0;
-  CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<T>, NT, flow_smem<T>()));
+  if (tc && sizeof(T) == 4) {
+    CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)flow_smem_one<float>()));
+    CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<float, true>, NT, flow_smem_tc()));
+  } else {
+    CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<T, false>, NT, flow_smem<T>()));
+  }
   return n > 0 ? n : 1;
 }
 
@@ -565,22 +889,33 @@ template <typename T>
 int BigFrontOps<T>::flow_level(cudaStream_t st, const BigFrontDev& bf, const FlowTask* task, int64_t t0, int64_t nt,
                                int* state, int64_t head_off, const int64_t* soff, int grid, bool one_per_sm, T* F,
                                T* E, T* Dp, const int8_t* dsign, double eps, double delta, int* hits, int* err,
-                               const int* skip) {
+                               const int* skip, const FlowTc* tc) {
   if (nt <= 0) return CLR_OK;
   const unsigned g = (unsigned)(nt < grid ? nt : grid);
+  CUtensorMap m;
+  if constexpr (sizeof(T) == 4) {
+    if (tc) {
+      std::memcpy(&m, tc->tmap, sizeof(m));
+      const size_t smem = one_per_sm ? flow_smem_one<float>() : flow_smem_tc();
+      k_bf_flow<float, true><<<g, NT, smem, st>>>(bf, task, t0, nt, state, head_off, soff, F, E, Dp, dsign, eps,
+                                                  delta, hits, err, skip, m, tc->pk);
+      CLR_CHECK_LAUNCH();
+      return CLR_OK;
+    }
+  }
+  std::memset(&m, 0, sizeof(m));
   const size_t smem = one_per_sm ? flow_smem_one<T>() : flow_smem<T>();
-  k_bf_flow<T><<<g, NT, smem, st>>>(bf, task, t0, nt, state, head_off, soff, F, E, Dp, dsign, eps, delta, hits, err,
-                                    skip);
+  k_bf_flow<T, false><<<g, NT, smem, st>>>(bf, task, t0, nt, state, head_off, soff, F, E, Dp, dsign, eps, delta, hits,
+                                           err, skip, m, nullptr);
   CLR_CHECK_LAUNCH();
   return CLR_OK;
 }
 
 #define CLR_FLOW_INST(T)                                                                                         \
-  template int BigFrontOps<T>::flow_occupancy();                                                                   \
+  template int BigFrontOps<T>::flow_occupancy(bool);                                                               \
   template int BigFrontOps<T>::flow_level(cudaStream_t, const BigFrontDev&, const FlowTask*, int64_t, int64_t, int*, \
                                           int64_t, const int64_t*, int, bool, T*, T*, T*, const int8_t*, double,     \
-                                          double,                                                                    \
-                                          int*, int*, const int*);
+                                          double, int*, int*, const int*, const FlowTc*);
 CLR_FLOW_INST(double)
 CLR_FLOW_INST(float)
 #undef CLR_FLOW_INST

@@ -25,6 +25,7 @@ struct BigFrontDev {
   const int64_t* woff = nullptr;  // offset of the front's solve slots
   const int64_t* yoff = nullptr;  // offset of its forward result y (c entries)
   const int64_t* rk = nullptr;    // offset of its rows in rows_kkt
+  const int64_t* pkoff = nullptr; // first packed operand tile of the front in its level's tiles (tensor-core flow)
   int64_t epool = 0, ypool = 0;
 };
 
@@ -75,6 +76,36 @@ __host__ __device__ inline int64_t flow_words(int64_t f, int64_t c) {
 }
 constexpr int kFlowThreads = 256;
 
+// Tensor-core products of the dataflow factorization (FP32 factor).  The tasks
+// that produce an L tile (T, DX), a D-scaled L tile or an E_KC tile (D, DX,
+// Efin) also store it, split into two TF32 parts, as a packed operand tile:
+// the exact shared-memory image that tcgen05.mma kind::tf32 reads (128 rows:
+// rows 0-63 the high parts, 64-127 the low parts; 64 k; K-major 8-row x
+// 16-byte core matrices, no swizzle).  The U and EU tasks copy their two
+// operand tiles into shared memory with one TMA tensor copy each and multiply
+// them on the tensor cores with FP32 accumulation in tensor memory.
+// Per front (P pivot blocks, nbf blocks): PL(p, i), i > p (L_IK), PLD(p, i)
+// (L_IK D_K), PE(p, e), e <= p (E_KC, stored with rows = the C columns).
+constexpr int64_t kPkWords = 128 * kBfNB;  // floats of one packed tile (32 KB)
+__host__ __device__ inline int64_t flow_pk_nl(int64_t f, int64_t c) {
+  const int64_t P = (c + kBfNB - 1) / kBfNB, n = flow_nbf(f, c);
+  return P * (n - 1) - P * (P - 1) / 2;
+}
+__host__ __device__ inline int64_t flow_pk_tiles(int64_t f, int64_t c) {
+  const int64_t P = (c + kBfNB - 1) / kBfNB;
+  return 2 * flow_pk_nl(f, c) + P * (P + 1) / 2;
+}
+// The packed tiles of one level and the TMA tensor map over them (a
+// CUtensorMap, kept opaque here): rows of 256 floats, a tile is 32 rows.
+struct FlowTc {
+  float* pk = nullptr;
+  int64_t tiles = 0;
+  unsigned char tmap[128] = {};
+};
+// Host: encode the tensor map over tc->pk (tc->tiles packed tiles).  CLR_E_CUDA
+// if the driver entry point is missing or rejects the map.
+int flow_tc_encode(FlowTc* tc);
+
 template <typename T>
 struct BigFrontOps {
   static int setup_attributes();
@@ -92,10 +123,13 @@ struct BigFrontOps {
   // soff[b], the version words of each big front b of the level.  err: set to 2
   // if a wait ran out (the factor is then unusable).  one_per_sm: enough shared
   // memory is requested that a single CTA fits on an SM.
+  // tc (T = float only; null: CUDA-core products): trailing and E updates on
+  // the tensor cores from packed operand tiles (see FlowTc).
   static int flow_level(cudaStream_t st, const BigFrontDev& bf, const FlowTask* task, int64_t t0, int64_t nt,
                         int* state, int64_t head_off, const int64_t* soff, int grid, bool one_per_sm, T* F, T* E, T* Dp,
-                        const int8_t* dsign, double eps, double delta, int* hits, int* err, const int* skip);
-  static int flow_occupancy();  // resident CTAs per SM of the flow kernel
+                        const int8_t* dsign, double eps, double delta, int* hits, int* err, const int* skip,
+                        const FlowTc* tc = nullptr);
+  static int flow_occupancy(bool tc = false);  // resident CTAs per SM of the flow kernel
 };
 
 

@@ -451,10 +451,12 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
     }
   // ---- big fronts: arrays, E / y pools, launch plans per level ----
   {
-    std::vector<int64_t> bf_f, bf_c, bf_goff, bf_eoff, bf_k0, bf_woff, bf_yoff, bf_rk;
+    std::vector<int64_t> bf_f, bf_c, bf_goff, bf_eoff, bf_k0, bf_woff, bf_yoff, bf_rk, bf_pk;
     std::vector<int64_t> bid_of(sy.nsn, -1);
     int64_t epool = 0, ypool = 0;
-    for (int64_t l = 0; l < sy.nlev; ++l)
+    st.pk_tiles = 0;
+    for (int64_t l = 0; l < sy.nlev; ++l) {
+      int64_t pk_level = 0;  // packed tiles are scratch of one level's launch: offsets restart per level
       for (int64_t J : st.lev_big[l]) {
         const int64_t f = sy.row_ptr[J + 1] - sy.row_ptr[J], c = sy.sn_ptr[J + 1] - sy.sn_ptr[J];
         bid_of[J] = (int64_t)bf_f.size();
@@ -466,9 +468,13 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
         bf_woff.push_back(sy.upd_off[J]);
         bf_yoff.push_back(ypool);
         bf_rk.push_back(sy.row_ptr[J]);
+        bf_pk.push_back(pk_level);
+        pk_level += flow_pk_tiles(f, c);
         epool += f * c;
         ypool += c;
       }
+      st.pk_tiles = std::max(st.pk_tiles, pk_level);
+    }
     BigFrontDev& bd = st.bfd;
     bd.n = (int64_t)bf_f.size();
     bd.epool = epool;
@@ -481,6 +487,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
     bd.woff = up(ar, bf_woff);
     bd.yoff = up(ar, bf_yoff);
     bd.rk = up(ar, bf_rk);
+    bd.pkoff = up(ar, bf_pk);
     // work lists: host-built (front ids, prefix sums), uploaded in one buffer
     std::vector<int64_t> buf;
     struct Pending {
@@ -658,7 +665,15 @@ int LdlFactor<T>::alloc(DeviceArena& ar, const LdlStructure& st) {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return CLR_E_CUDA;
-    const int occ = BigFrontOps<T>::flow_occupancy();
+    const bool tc = use_flow_tc();
+    if (tc) {
+      tcs.tiles = st.pk_tiles;
+      tcs.pk = ar.alloc_n<float>(st.pk_tiles * kPkWords);
+      if (!tcs.pk) return CLR_E_OOM;
+      const int rc = flow_tc_encode(&tcs);
+      if (rc != CLR_OK) return rc;
+    }
+    const int occ = BigFrontOps<T>::flow_occupancy(tc);
     if (occ < 0) return CLR_E_CUDA;
     flow_sms = sms;
     flow_occ = occ;
@@ -703,8 +718,8 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
       int rc = use_flow ? BigFrontOps<T>::flow_level(stm, S.bfd, S.flow_task, S.flow_t0[l], S.flow_nt[l], flow_state,
                                                      S.flow_head[l], S.flow_soff,
                                                      S.flow_one[l] ? flow_sms : flow_sms * flow_occ, S.flow_one[l] != 0,
-                                                     F, E, Dp, S.dsign,
-                                                     dyn_eps, dyn_delta, dyn_hits, tc_err, skip)
+                                                     F, E, Dp, S.dsign, dyn_eps, dyn_delta, dyn_hits, tc_err, skip,
+                                                     (use_flow_tc() && tcs.pk) ? &tcs : nullptr)
                         : BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps,
                                                        dyn_delta, dyn_hits, skip, tc16, tc_err);
       if (rc) return rc;

@@ -317,6 +317,40 @@ def test_ldl_big_fronts_with_update_rows(bits):
     np.testing.assert_allclose(x, xref, rtol=tol, atol=tol * np.abs(xref).max())
 
 
+@pytest.mark.parametrize("n,m", [(180, 160), (300, 260), (700, 500)])
+def test_ldl_big_fronts_tensor_core_updates(n, m):
+    """FP32 dataflow factorization whose trailing and E updates run on the
+    tensor cores (big_front_schedule 1: TF32 high and low parts, FP32
+    accumulation in tensor memory, operand tiles staged by TMA) against the same
+    schedule with CUDA-core products (2) and against the oracle's LDL^T: fronts
+    of 3 to 11 panels of 64 columns, ragged last pivot and update blocks."""
+    rng = np.random.default_rng(n + m)
+    M = rng.standard_normal((n, n))
+    P = M @ M.T / n + np.eye(n)
+    B = rng.standard_normal((m, m))
+    H = B @ B.T / m + np.eye(m)
+    A = rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.2)
+    K = np.block([[P, A.T], [A, -H]])
+    N = n + m
+    signs = np.r_[np.ones(n), -np.ones(m)]
+    rhs = rng.standard_normal(N)
+    order = np.arange(N)
+    x1, D1, h1 = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=32, big_front_schedule=1)
+    x2, D2, h2 = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=32, big_front_schedule=2)
+    assert h1 == 0 and h2 == 0
+    L, Dref, _ = ldl_factor(K, signs, 1e-13, 2e-7)
+    np.testing.assert_allclose(D1, Dref, rtol=1e-4)
+    np.testing.assert_allclose(D2, Dref, rtol=1e-4)
+    # both are FP32 factors of the same matrix in the same order: their pivot
+    # errors are of the same size (the split products are exact to ~2^-21)
+    e1 = np.max(np.abs(D1 - Dref) / np.abs(Dref))
+    e2 = np.max(np.abs(D2 - Dref) / np.abs(Dref))
+    assert e1 <= 8 * e2 + 1e-6, (e1, e2)
+    xref = np.linalg.solve(K, rhs)
+    for x in (x1, x2):
+        np.testing.assert_allclose(x, xref, rtol=1e-4, atol=1e-4 * np.abs(xref).max())
+
+
 def test_ldl_big_fronts_bf16_products_refine_to_fp64_accuracy():
     """factor_bits 16: the big-front updates run on the tensor cores with BF16
     operands and FP32 accumulation.  The factor is accurate to a few 1e-3, so the
