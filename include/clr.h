@@ -115,11 +115,13 @@ typedef struct {
                               goes on with the FP64 factor and the FP64 regularisation defaults (for every problem
                               of a cohort); 0: never */
   int32_t big_front_schedule; /* large fronts: 1 (default) one dataflow launch per level, tile tasks started as
-                                 their inputs are ready; with the FP32 factor its trailing and E updates run
-                                 on the tensor cores (tcgen05 kind::tf32, each operand split into high and
-                                 low TF32 parts, FP32 accumulation; operand tiles staged by TMA); 2 the same
-                                 schedule with CUDA-core products only; 0 three launches per 64-column panel.
-                                 The 16-bit-products variant always uses the per-panel launches. */
+                                 their inputs are ready; with the FP32 factor, on the levels where a schedule
+                                 simulated at setup from measured task times is shorter that way, its
+                                 trailing and E updates run on the tensor cores (tcgen05 kind::tf32, each
+                                 operand split into high and low TF32 parts, FP32 accumulation; operand tiles
+                                 staged by TMA); 3 the tensor-core launch on every level; 2 CUDA-core
+                                 products only; 0 three launches per 64-column panel.  The 16-bit-products
+                                 variant always uses the per-panel launches. */
   int32_t small_front_max;    /* fronts of at most this order are factored by one CTA each in shared memory,
                                  larger ones by the big-front kernels; 0 (default): 128 (FP32 / 16-bit
                                  products), 96 (FP64); at most 224 (FP32) / 160 (FP64) */
@@ -480,8 +482,9 @@ int clr_cones_time(const clr_cone* cones, int32_t ncones, const double* s, const
  * caller permutation (order[k] = index eliminated k-th).  factor_bits 64/32/16.
  * x_out = K^{-1} rhs (no refinement); D_out (optional, N): pivots in the
  * caller's numbering.  big_front_schedule: the large fronts' schedule, as the
- * setting of the same name (0 per-panel launches, 1 dataflow with tensor-core
- * updates for factor_bits 32, 2 dataflow with CUDA-core products). */
+ * setting of the same name (0 per-panel launches; dataflow: 1 tensor-core
+ * updates for factor_bits 32 on the levels chosen at setup, 2 CUDA-core
+ * products, 3 tensor-core updates on every level). */
 int clr_ldl_solve(const clr_csc* K_lower, const double* signs, const int64_t* order, int32_t factor_bits,
                   double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
                   int32_t* dyn_hits_out, int32_t big_front_schedule);

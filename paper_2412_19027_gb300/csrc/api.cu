@@ -63,7 +63,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
 static int check_settings(const clr_settings& s) {
   if (s.factor_bits != 64 && s.factor_bits != 32 && s.factor_bits != 16) return CLR_E_INVALID;
   if (!(s.eps_feas > 0) || !(s.eps_inf > 0) || s.max_iter < 0 || s.ir_max_steps < 0 || s.ruiz_passes < 0 ||
-      !(s.ir_stop_ratio >= 0) || s.big_front_schedule < 0 || s.big_front_schedule > 2)
+      !(s.ir_stop_ratio >= 0) || s.big_front_schedule < 0 || s.big_front_schedule > 3)
     return CLR_E_INVALID;
   if (s.small_front_max < 0 || s.small_front_max > (s.factor_bits == 64 ? 160 : 224) || s.amalgamation < 0 ||
       s.amalgamation > 2)

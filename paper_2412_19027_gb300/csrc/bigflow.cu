@@ -6,17 +6,19 @@
 // starts as soon as its own tile has received panel p's update, while the rest
 // of panel p's updates are still running.
 //
-// FP32 factor, tensor-core variant (TC): the producers of L, L D and E_KC tiles
-// also store packed TF32 hi/lo operand tiles (bigfront.cuh, FlowTc); the U and
-// EU tasks load their two operand tiles with one TMA tensor copy each
-// (cp.async.bulk.tensor, completion on an mbarrier) and issue 16 tcgen05.mma
-// kind::tf32 (M = 128, N = 64, K = 8) into a 128 x 64 FP32 accumulator in
-// tensor memory: A = [L_hi; L_lo] (128 rows), B = the high then the low part of
-// the other operand, so that lanes 0-63 hold L_hi B and lanes 64-127 L_lo B;
-// their sum is the FP32 product to ~2^-21 relative (every partial product of
-// two TF32 parts is exact in FP32).
+// FP32 factor, tensor-core variant (TC): the producers of L and E_KC tiles also
+// store them as packed FP32 operand tiles (bigfront.cuh, FlowTc); the U and EU
+// tasks load their two operand tiles with one TMA tensor copy each
+// (cp.async.bulk.tensor, completion on an mbarrier), split them in shared
+// memory into high and low TF32 parts and issue 16 tcgen05.mma kind::tf32
+// (M = 128, N = 64, K = 8) into a 128 x 64 FP32 accumulator in tensor memory:
+// A = [L_hi; L_lo] (128 rows), B = the high then the low part of the other
+// operand, so that lanes 0-63 hold L_hi B and lanes 64-127 L_lo B; their sum is
+// the FP32 product to ~2^-21 relative (every partial product of two TF32 parts
+// is exact in FP32).
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "bfdiag.cuh"
@@ -66,7 +68,7 @@ __device__ __forceinline__ int bnrow(const Geo& g, int64_t b) {
   return (int)(b < g.P ? min((int64_t)NB, g.c - NB * b) : min((int64_t)NB, g.f - g.c - NB * (b - g.P)));
 }
 struct Words {
-  int *tile, *etile, *diag, *trsm;
+  int *tile, *etile, *diag, *trsm, *pe;
   int64_t P;
   __device__ int* t(int64_t i, int64_t j) const { return tile + i * (i + 1) / 2 + j; }
   __device__ int* e(int64_t i, int64_t c) const { return etile + i * P + c; }
@@ -78,6 +80,7 @@ __device__ __forceinline__ Words words_of(int* base, const Geo& g) {
   w.etile = base + g.nbf * (g.nbf + 1) / 2;
   w.diag = w.etile + g.nbf * g.P;
   w.trsm = w.diag + g.P;
+  w.pe = w.trsm + g.nbf;
   return w;
 }
 
@@ -103,10 +106,12 @@ __device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
 }
 
 // ---------------------------------------------------------------- tensor-core helpers
-// Packed operand tile: element (row, k) at word (k / 4) * 512 + row * 4 + k % 4 --
-// K-major core matrices of 8 rows x 16 bytes, adjacent in K 2048 bytes apart and
-// in rows 128 bytes apart; rows 0-63 the high TF32 parts, 64-127 the low parts.
-__device__ __forceinline__ int pk_word(int row, int k) { return ((k >> 2) << 9) + (row << 2) + (k & 3); }
+// Packed FP32 operand tile (global memory, and the TMA staging copy): element
+// (row, k) at word (k / 4) * 256 + row * 4 + k % 4.  The split operand the MMA
+// reads: 128 rows (0-63 the high TF32 parts, 64-127 the low parts), element
+// (row, k) at word (k / 4) * 512 + row * 4 + k % 4 -- K-major core matrices of 8
+// rows x 16 bytes, adjacent in K 2048 bytes apart and in rows 128 bytes apart.
+__device__ __forceinline__ int pk_word(int row, int k) { return ((k >> 2) << 8) + (row << 2) + (k & 3); }
 // v = hi + lo + O(2^-22 |v|): hi = v with its 13 low mantissa bits cleared (a TF32
 // value, so the tensor core reads it unchanged), lo = v - hi (exact) rounded to TF32.
 __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
@@ -115,27 +120,46 @@ __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hi));
   lo = __uint_as_float(l);
 }
-// All threads: store the 64 x 64 tile val(row, k) as a packed operand tile at dst;
-// each pass of the CTA writes 1 KB of high and 1 KB of low parts, contiguous.
+// All threads: store the 64 x 64 tile val(row, k) as a packed operand tile at
+// dst (each pass of the CTA writes 1 KB, contiguous).
 template <typename V>
 __device__ __forceinline__ void pk_write(float* dst, V val) {
 #pragma unroll 4
   for (int it = 0; it < 16; ++it) {
     const int idx = threadIdx.x + NT * it;
     const int q = idx & 3, r = (idx >> 2) & 63, kg = idx >> 8;
-    float hi, lo;
-    split_tf32(val(r, 4 * kg + q), hi, lo);
-    const int w = (kg << 9) + (r << 2) + q;
-    dst[w] = hi;
-    dst[w + 256] = lo;
+    dst[(kg << 8) + (r << 2) + q] = val(r, 4 * kg + q);
+  }
+}
+// All threads: split the staged packed tile src into its high and low parts in
+// the MMA's layout at dst, each k-column scaled by sc[k] first (sc null: 1).
+__device__ __forceinline__ void pk_split(const float* src, float* dst, const float* sc) {
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int ch = threadIdx.x + NT * it;  // 16-byte chunk (k group kg, row r)
+    const int kg = ch >> 6, r = ch & 63;
+    float4 v = reinterpret_cast<const float4*>(src)[ch];
+    if (sc) {
+      v.x *= sc[4 * kg];
+      v.y *= sc[4 * kg + 1];
+      v.z *= sc[4 * kg + 2];
+      v.w *= sc[4 * kg + 3];
+    }
+    float4 h, l;
+    split_tf32(v.x, h.x, l.x);
+    split_tf32(v.y, h.y, l.y);
+    split_tf32(v.z, h.z, l.z);
+    split_tf32(v.w, h.w, l.w);
+    reinterpret_cast<float4*>(dst)[kg * 128 + r] = h;
+    reinterpret_cast<float4*>(dst)[kg * 128 + 64 + r] = l;
   }
 }
 __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-// Tile indices within a front's packed tiles: PL(p, i), i > p; PLD = PL + nL; PE(p, e), e <= p.
+// Tile indices within a front's packed tiles: PL(p, i), i > p; PE(p, e), e <= p.
 __device__ __forceinline__ int64_t pk_l(int64_t nbf, int p, int64_t i) {
   return (int64_t)p * (nbf - 1) - (int64_t)p * (p - 1) / 2 + (i - p - 1);
 }
-__device__ __forceinline__ int64_t pk_e(int64_t nL, int p, int64_t e) { return 2 * nL + (int64_t)p * (p + 1) / 2 + e; }
+__device__ __forceinline__ int64_t pk_e(int64_t nL, int p, int64_t e) { return nL + (int64_t)p * (p + 1) / 2 + e; }
 struct PkRef {  // the packed tiles of the front a task works on
   float* pk = nullptr;  // the level's tiles
   int64_t base = 0;     // first tile of the front
@@ -164,12 +188,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   }
   return false;
 }
-// one TMA tensor copy of packed tile `tile` (32 rows of 256 floats of the map) to dst
+// one TMA tensor copy of packed tile `tile` (16 rows of 256 floats of the map) to dst
 __device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap* map, int64_t tile, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"((int)(tile * 32)), "r"(bar)
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"((int)(tile * 16)), "r"(bar)
       : "memory");
 }
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
@@ -189,8 +213,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-constexpr int kTcTileBytes = 128 * NB * 4;                  // one packed tile in shared memory (32 KB)
-constexpr size_t kTcSmemFlow = 2 * (size_t)kTcTileBytes + 1024;  // A, B and the 1024-byte alignment slack
+constexpr int kTcOpBytes = 128 * NB * 4;   // one split operand (high and low parts, 32 KB)
+constexpr int kTcPkBytes = NB * NB * 4;    // one packed FP32 tile (16 KB)
+// split A, split B, staged A, staged B and the 1024-byte alignment slack
+constexpr size_t kTcSmemFlow = 2 * (size_t)kTcOpBytes + 2 * (size_t)kTcPkBytes + 1024;
 // M = 128, N = 64, D FP32 (bit 4), A and B TF32 (format 2 at bits 7 and 10), both K-major
 constexpr uint32_t kTf32Idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
                                 ((uint32_t)(128 >> 4) << 24);
@@ -208,13 +234,6 @@ __device__ void task_diag(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
   T* Li = E + bf.eoff[b] + k0 + k0 * f;
   const int nhit = bf_diag_block<T>(G, f, pw, Dp + kp, Li, f, false, dsign + kp, eps, delta, sm, sh);
   if (threadIdx.x == 0 && nhit) atomicAdd(hits, nhit);
-  if constexpr (TC) {  // PE(p, p): E_KK = Linv (unit lower), rows = its columns
-    const T* V = sm + 64 * kDiagLD;
-    pk_write(pkr.tile(pk_e(pkr.nL, p, p)), [&](int n, int k) -> float {
-      return (k < pw && n < pw && k >= n) ? (k == n ? 1.f : (float)V[k * kDiagLD + n]) : 0.f;
-    });
-    fence_proxy_async_global();
-  }
 }
 
 // DX(p), 1 <= p < P: the three links of the critical chain in one task, kept in
@@ -285,10 +304,8 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     const int i = idx % NB, j = idx / NB;
     if (i < pw) G[(k0 + i) + (kq + j) * f] = Xk[swz(j, i)];
   }
-  if constexpr (TC) {  // PL(p-1, p) and PLD(p-1, p) before the L rows are published
+  if constexpr (TC) {  // PL(p-1, p) before the L rows are published
     pk_write(pkr.tile(pk_l(g.nbf, p - 1, p)), [&](int r, int k) -> float { return r < pw ? (float)Xk[swz(k, r)] : 0.f; });
-    pk_write(pkr.tile(pkr.nL + pk_l(g.nbf, p - 1, p)),
-             [&](int r, int k) -> float { return r < pw ? (float)(Xk[swz(k, r)] * dl[k]) : 0.f; });
     fence_proxy_async_global();
   }
   __syncthreads();
@@ -326,12 +343,6 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
   const int64_t kp = bf.k0pos[b] + k0;
   const int nhit = bf_diag_factor<T>(A, Bk, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp,
                                      eps, delta, sh);
-  if constexpr (TC) {  // PE(p, p) from Linv (in Bk, row stride kDiagLD)
-    pk_write(pkr.tile(pk_e(pkr.nL, p, p)), [&](int n, int k) -> float {
-      return (k < pw && n < pw && k >= n) ? (k == n ? 1.f : (float)Bk[k * kDiagLD + n]) : 0.f;
-    });
-    fence_proxy_async_global();
-  }
   return nhit;
 }
 
@@ -398,11 +409,9 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
     const int i = idx % NB, j = idx / NB;
     if (i < nr && j < pw) G[(r0 + i) + (k0 + j) * f] = Xk[swz(j, i)];
   }
-  if constexpr (TC) {  // PL(p, i) and PLD(p, i)
+  if constexpr (TC) {  // PL(p, i)
     pk_write(pkr.tile(pk_l(g.nbf, p, bi)),
              [&](int r, int k) -> float { return (r < nr && k < pw) ? (float)Xk[swz(k, r)] : 0.f; });
-    pk_write(pkr.tile(pkr.nL + pk_l(g.nbf, p, bi)),
-             [&](int r, int k) -> float { return (r < nr && k < pw) ? (float)(Xk[swz(k, r)] * dl[k]) : 0.f; });
     fence_proxy_async_global();
   }
 }
@@ -455,10 +464,7 @@ __device__ void task_efin(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
 #pragma unroll
       for (int bb = 0; bb < 4; ++bb) {
         const int i = tr + 16 * a, n = tc + 16 * bb;
-        float hi, lo;
-        split_tf32(i < pw ? (float)acc[a][bb] : 0.f, hi, lo);
-        dst[pk_word(n, i)] = hi;
-        dst[pk_word(n, i) + 256] = lo;
+        dst[pk_word(n, i)] = i < pw ? (float)acc[a][bb] : 0.f;
       }
     fence_proxy_async_global();
   }
@@ -547,36 +553,44 @@ __device__ void task_update(const BigFrontDev& bf, int64_t b, const Geo& g, int 
 
 
 // U(p, i, j) / EU(p, i, e) on the tensor cores (FP32 factor): thread 0 copies
-// the packed operand tiles A = PL(p, i) and B = PLD(p, j) (U) or PE(p, e) (EU)
-// into shared memory with two TMA tensor copies and issues the 16 MMAs; the
-// other threads meanwhile load the target tile.  Lanes 0-63 of the accumulator
-// hold L_hi B, lanes 64-127 L_lo B; warps 2, 3, 6, 7 pass the low halves through
-// shared memory, warps 0, 1, 4, 5 form target - (high + low) and store it
-// (rows 32 (w % 4) + lane, columns 32 (w / 4) ...).  Returns false, with *err = 2,
-// if a wait ran out (the caller then stops; copies and MMAs in flight were
-// waited for once more, with the same bound).
-__device__ bool task_update_tc(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, int64_t bj,
-                               bool etile, float* F, float* E, const CUtensorMap* tmap, const PkRef& pkr,
-                               unsigned char* smtc, uint32_t bar_ld, uint32_t bar_mma, uint32_t parity,
-                               uint32_t tmem, int* err, int* s_flag) {
+// the packed operand tiles A = PL(p, i) and B = PL(p, j) (U) or PE(p, e) (EU)
+// into shared memory with two TMA tensor copies while the other threads load
+// the target tile and (U) the pivots D_K; all threads split A and B into high
+// and low TF32 parts (B scaled by D_K for U), thread 0 issues the 16 MMAs.
+// Lanes 0-63 of the accumulator hold L_hi B, lanes 64-127 L_lo B; warps 2, 3,
+// 6, 7 pass the low halves through shared memory, warps 0, 1, 4, 5 form
+// target - (high + low) and store it (rows 32 (w % 4) + lane, columns 32 (w / 4)
+// ...).  Returns false, with *err = 2, if a wait ran out (the caller then stops;
+// copies and MMAs in flight were waited for once more, with the same bound).
+__device__ __noinline__ bool task_update_tc(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int64_t bi, int64_t bj,
+                               bool etile, float* F, float* E, const float* Dp, const CUtensorMap* tmap,
+                               const PkRef& pkr, unsigned char* smtc, float* dl, uint32_t bar_ld, uint32_t bar_mma,
+                               uint32_t parity, uint32_t tmem, int* err, int* s_flag) {
   const int64_t f = g.f;
   const int64_t i0 = brow0(g, bi);
   const int ni = bnrow(g, bi);
   const int64_t c0 = etile ? bj * NB : brow0(g, bj);
   const int nc = bnrow(g, bj);
+  const int pw = bnrow(g, p);
   const bool diag = !etile && bi == bj;
   float* base = etile ? E + bf.eoff[b] : F + bf.goff[b];
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-  const uint32_t sA = s_addr(smtc), sB = sA + kTcTileBytes;
+  // split A and B (32 KB each; the other tasks' scratch lies in the same 64 KB),
+  // then the staged tiles (16 KB each; written only by the TMA)
+  float* opA = reinterpret_cast<float*>(smtc);
+  float* opB = reinterpret_cast<float*>(smtc + kTcOpBytes);
+  float* stA = reinterpret_cast<float*>(smtc + 2 * kTcOpBytes);
+  float* stB = stA + NB * NB;
   if (tid == 0) {
     const int64_t ta = pkr.base + pk_l(g.nbf, p, bi);
-    const int64_t tb = pkr.base + (etile ? pk_e(pkr.nL, p, bj) : pkr.nL + pk_l(g.nbf, p, bj));
+    const int64_t tb = pkr.base + (etile ? pk_e(pkr.nL, p, bj) : pk_l(g.nbf, p, bj));
     fence_proxy_async_global();  // the tiles were released by generic stores (acquired above)
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld), "r"(2 * kTcTileBytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_ld), "r"(2 * kTcPkBytes)
                  : "memory");
-    tma_tile(sA, tmap, ta, bar_ld);
-    tma_tile(sB, tmap, tb, bar_ld);
+    tma_tile(s_addr(stA), tmap, ta, bar_ld);
+    tma_tile(s_addr(stB), tmap, tb, bar_ld);
   }
+  if (!etile && tid < NB) dl[tid] = tid < pw ? __ldcg(Dp + bf.k0pos[b] + (int64_t)p * NB + tid) : 0.f;
   const int q = wid & 3, h = wid >> 2;
   const int r = 32 * q + lane;  // output row of the top warps (q < 2)
   float tv[32];
@@ -587,25 +601,31 @@ __device__ bool task_update_tc(const BigFrontDev& bf, int64_t b, const Geo& g, i
       tv[jj] = (r < ni && cc < nc && (!diag || r >= cc)) ? __ldcg(base + (i0 + r) + (c0 + cc) * f) : 0.f;
     }
   }
-  if (tid == 0) {
-    if (mbar_wait(bar_ld, parity)) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int ks = 0; ks < NB / 8; ++ks) {
-        const uint32_t ko = (uint32_t)ks * 4096u;  // K = 8: two core matrices along K
-        mma_tf32(tmem, pk_desc(sA + ko), pk_desc(sB + ko), kTf32Idesc, ks > 0 ? 1u : 0u);
-        mma_tf32(tmem, pk_desc(sA + ko), pk_desc(sB + 1024u + ko), kTf32Idesc, 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
-                   : "memory");
-    } else {
+  if (!mbar_wait(bar_ld, parity)) atomicExch(s_flag, 1);
+  __syncthreads();
+  if (*s_flag) {
+    if (tid == 0) {
       atomicExch(err, 2);
-      *s_flag = 1;
       mbar_wait(bar_ld, parity);  // once more for the copies in flight
     }
+    return false;
   }
+  pk_split(stA, opA, nullptr);
+  pk_split(stB, opB, etile ? nullptr : dl);  // U: B = L_JK D_K
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the split operands are read by the MMAs
   __syncthreads();
-  if (*s_flag) return false;
+  if (tid == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t sA = s_addr(opA), sB = s_addr(opB);
+#pragma unroll
+    for (int ks = 0; ks < NB / 8; ++ks) {
+      const uint32_t ko = (uint32_t)ks * 4096u;  // K = 8: two core matrices along K
+      mma_tf32(tmem, pk_desc(sA + ko), pk_desc(sB + ko), kTf32Idesc, ks > 0 ? 1u : 0u);
+      mma_tf32(tmem, pk_desc(sA + ko), pk_desc(sB + 1024u + ko), kTf32Idesc, 1u);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                 : "memory");
+  }
   if (!mbar_wait(bar_mma, parity)) atomicExch(s_flag, 1);
   __syncthreads();
   if (*s_flag) {
@@ -618,7 +638,7 @@ __device__ bool task_update_tc(const BigFrontDev& bf, int64_t b, const Geo& g, i
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   uint32_t v[32];
   tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), v);
-  float* X = reinterpret_cast<float*>(smtc);  // the low halves (the operands are consumed)
+  float* X = opA;  // the low halves (16 KB; the MMAs have read the operands)
   if (q >= 2) {
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) X[(32 * h + jj) * 64 + 32 * (q - 2) + lane] = __uint_as_float(v[jj]);
@@ -673,6 +693,7 @@ __global__ void __launch_bounds__(NT, 2)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     tmem = s_tmem;
+    if (tid == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
   }
   for (;;) {
     if (tid == 0) {
@@ -723,6 +744,8 @@ __global__ void __launch_bounds__(NT, 2)
             wp[0] = w.trsm + tk.i, wv[0] = p + 1;
             if (tk.j < p)
               wp[1] = w.e(p, tk.j), wv[1] = p - tk.j + 1;
+            else if (TC)  // the packed E_KK, stored after the diagonal task's release
+              wp[1] = w.pe + p, wv[1] = 1;
             else
               wp[1] = w.diag + p, wv[1] = 1;
             wp[2] = w.e(tk.i, tk.j), wv[2] = p - tk.j;
@@ -776,7 +799,7 @@ __global__ void __launch_bounds__(NT, 2)
         break;
       default:
         if constexpr (TC) {
-          stop = !task_update_tc(bf, b, g, tk.p, tk.i, tk.j, tk.kind != 3, F, E, &tmap, pkr, smtc,
+          stop = !task_update_tc(bf, b, g, tk.p, tk.i, tk.j, tk.kind != 3, F, E, Dp, &tmap, pkr, smtc, dl,
                                  s_addr(&s_bar[0]), s_addr(&s_bar[1]), parity, tmem, err, &s_flag);
           parity ^= 1u;
         } else {
@@ -784,9 +807,9 @@ __global__ void __launch_bounds__(NT, 2)
         }
         break;
     }
-    // TC: the generic accesses to shared memory of this task come before the
-    // next task's TMA writes to it
-    if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // (TC: only the TMA writes the staging tiles, and generic code only reads
+    // them; the generic writes to the split operands and the other tasks'
+    // scratch are ordered before the MMAs by the proxy fence in task_update_tc)
     __syncthreads();
     if (stop) break;
     if (tid == 0) {
@@ -815,6 +838,25 @@ __global__ void __launch_bounds__(NT, 2)
           break;
       }
     }
+    if constexpr (TC) {
+      if (tk.kind == 0 || tk.kind == 5) {
+        // PE(p, p) = E_KK (Linv, unit lower; rows = its columns) from the diagonal
+        // task's copy in shared memory, after the release above so that the
+        // chain of diagonal tasks does not wait for it; EU(p, i, p) waits for
+        // the pe word instead
+        const int p = tk.p, pw = bnrow(g, p);
+        const T* V = tk.kind == 0 ? sm + 64 * kDiagLD : sm;
+        pk_write(pkr.tile(pk_e(pkr.nL, p, p)), [&](int n, int k) -> float {
+          return (k < pw && n < pw && k >= n) ? (k == n ? 1.f : (float)V[k * kDiagLD + n]) : 0.f;
+        });
+        fence_proxy_async_global();
+        __syncthreads();
+        if (tid == 0) {
+          __threadfence();
+          st_release(words_of(state + soff[b], g).pe + p, 1);
+        }
+      }
+    }
   }
   if constexpr (TC) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -832,7 +874,9 @@ size_t flow_smem() {  // the fused chain task's three blocks; the others need le
 // TC launch: the two packed operand tiles of a U / EU task (the other tasks
 // fit in the same space) from a 1024-byte aligned base
 size_t flow_smem_tc() {
-  static_assert(2 * (size_t)NB * LDK * 4 + (size_t)NB * LD * 4 + 1024 <= kTcSmemFlow, "shared memory of the TC flow");
+  static_assert(2 * (size_t)NB * LDK * 4 + (size_t)NB * LD * 4 <= 2 * (size_t)kTcOpBytes,
+                "the other tasks' scratch stays clear of the TMA staging tiles");
+  static_assert(kTcSmemFlow <= 120 * 1024, "the one-CTA-per-SM launch covers the TC tiles");
   return kTcSmemFlow;
 }
 }  // namespace
@@ -852,10 +896,10 @@ int flow_tc_encode(FlowTc* tc) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  // rows of 256 floats (1 KB), 32 rows per packed tile; one box = one tile
-  const cuuint64_t dims[2] = {256, (cuuint64_t)tc->tiles * 32};
+  // rows of 256 floats (1 KB), 16 rows per packed tile; one box = one tile
+  const cuuint64_t dims[2] = {256, (cuuint64_t)tc->tiles * 16};
   const cuuint64_t strides[1] = {256 * sizeof(float)};
-  const cuuint32_t box[2] = {256, 32};
+  const cuuint32_t box[2] = {256, 16};
   const cuuint32_t estr[2] = {1, 1};
   CUtensorMap m;
   const CUresult r = reinterpret_cast<Encode>(fn)(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, tc->pk, dims, strides, box,
@@ -872,13 +916,32 @@ int flow_tc_encode(FlowTc* tc) {
 
 template <typename T>
 int BigFrontOps<T>::flow_occupancy(bool tc) {
+  // the whole unified L1 / shared memory as shared memory, so that two CTAs of
+  // the TC launch (97 KB each) fit on an SM
   CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)flow_smem_one<T>()));
+  CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<T, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
   int n = 0;
   if (tc && sizeof(T) == 4) {
     CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)flow_smem_one<float>()));
-    CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<float, true>, NT, flow_smem_tc()));
+    CLR_CUDA(cudaFuncSetAttribute(k_bf_flow<float, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+    // from the kernel's resources: the occupancy calculator reports one CTA per
+    // SM for this launch although two are resident (measured with per-task
+    // timestamps: SM ids and overlapping task intervals)
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, regs_sm = 0, resv = 0;
+    CLR_CUDA(cudaFuncGetAttributes(&fa, k_bf_flow<float, true>));
+    CLR_CUDA(cudaGetDevice(&dev));
+    CLR_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    CLR_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    CLR_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    const size_t per_cta = flow_smem_tc() + fa.sharedSizeBytes + (size_t)resv;
+    const int by_smem = (int)((size_t)smem_sm / per_cta);
+    const int by_regs = fa.numRegs > 0 ? regs_sm / (fa.numRegs * NT) : 1;
+    n = std::min(2, std::min(by_smem, by_regs));
   } else {
     CLR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bf_flow<T, false>, NT, flow_smem<T>()));
   }

@@ -66,37 +66,38 @@ struct FlowTask {
   int16_t p;     // panel
   int32_t i, j;  // block row; block column (Efin: e; EU: e)
 };
-// version words of one front: tile[tri(i, j)], etile[i * P + e], diag[P], trsm[nbf]
+// version words of one front: tile[tri(i, j)], etile[i * P + e], diag[P], trsm[nbf],
+// pe[P] (tensor-core flow: the packed E_KK tile of panel p is stored)
 __host__ __device__ inline int64_t flow_nbf(int64_t f, int64_t c) {
   return (c + kBfNB - 1) / kBfNB + (f - c + kBfNB - 1) / kBfNB;
 }
 __host__ __device__ inline int64_t flow_words(int64_t f, int64_t c) {
   const int64_t P = (c + kBfNB - 1) / kBfNB, n = flow_nbf(f, c);
-  return n * (n + 1) / 2 + n * P + P + n;
+  return n * (n + 1) / 2 + n * P + P + n + P;
 }
 constexpr int kFlowThreads = 256;
 
 // Tensor-core products of the dataflow factorization (FP32 factor).  The tasks
-// that produce an L tile (T, DX), a D-scaled L tile or an E_KC tile (D, DX,
-// Efin) also store it, split into two TF32 parts, as a packed operand tile:
-// the exact shared-memory image that tcgen05.mma kind::tf32 reads (128 rows:
-// rows 0-63 the high parts, 64-127 the low parts; 64 k; K-major 8-row x
-// 16-byte core matrices, no swizzle).  The U and EU tasks copy their two
-// operand tiles into shared memory with one TMA tensor copy each and multiply
-// them on the tensor cores with FP32 accumulation in tensor memory.
-// Per front (P pivot blocks, nbf blocks): PL(p, i), i > p (L_IK), PLD(p, i)
-// (L_IK D_K), PE(p, e), e <= p (E_KC, stored with rows = the C columns).
-constexpr int64_t kPkWords = 128 * kBfNB;  // floats of one packed tile (32 KB)
+// that produce an L tile (T, DX) or an E_KC tile (D, DX, Efin) also store it as
+// a packed FP32 operand tile: 64 rows x 64 k in K-major core matrices of 8 rows
+// x 16 bytes without swizzle (element (row, k) at word (k / 4) * 256 + row * 4
+// + k % 4), the layout one TMA tensor copy lands in shared memory.  The U and EU
+// tasks copy their two operand tiles into shared memory with TMA, split them
+// there into high and low TF32 parts (the U task's B operand scaled by D_K on
+// the way) and multiply them on the tensor cores with FP32 accumulation in
+// tensor memory.  Per front (P pivot blocks, nbf blocks): PL(p, i), i > p
+// (L_IK), then PE(p, e), e <= p (E_KC, stored with rows = the C columns).
+constexpr int64_t kPkWords = kBfNB * kBfNB;  // floats of one packed tile (16 KB)
 __host__ __device__ inline int64_t flow_pk_nl(int64_t f, int64_t c) {
   const int64_t P = (c + kBfNB - 1) / kBfNB, n = flow_nbf(f, c);
   return P * (n - 1) - P * (P - 1) / 2;
 }
 __host__ __device__ inline int64_t flow_pk_tiles(int64_t f, int64_t c) {
   const int64_t P = (c + kBfNB - 1) / kBfNB;
-  return 2 * flow_pk_nl(f, c) + P * (P + 1) / 2;
+  return flow_pk_nl(f, c) + P * (P + 1) / 2;
 }
 // The packed tiles of one level and the TMA tensor map over them (a
-// CUtensorMap, kept opaque here): rows of 256 floats, a tile is 32 rows.
+// CUtensorMap, kept opaque here): rows of 256 floats, a tile is 16 rows.
 struct FlowTc {
   float* pk = nullptr;
   int64_t tiles = 0;

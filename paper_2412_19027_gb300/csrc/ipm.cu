@@ -1021,7 +1021,7 @@ int Solver::upload() {
   if (rc != CLR_OK) return rc;
   f32_.tc16 = st.factor_bits == 16;
   f32_.flow = f64_.flow = st.big_front_schedule != 0;
-  f32_.flow_tc = st.big_front_schedule == 1;
+  f32_.flow_tc = st.big_front_schedule == 1 ? 1 : (st.big_front_schedule == 3 ? 2 : 0);
   rc = (st.factor_bits == 64) ? f64_.alloc(ar_, ls_) : f32_.alloc(ar_, ls_);
   if (rc != CLR_OK) return rc;
   // full-K CSR with value indices

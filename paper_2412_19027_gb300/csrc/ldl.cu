@@ -567,6 +567,7 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
         sms > 0)
       flow_sms = sms;
     st.flow_one.assign(sy.nlev, 0);
+    st.flow_tc.assign(sy.nlev, 0);
     int64_t words = 0;
     st.flow_t0.assign(sy.nlev, 0);
     st.flow_nt.assign(sy.nlev, 0);
@@ -598,16 +599,28 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       }
       st.flow_nt[l] = (int64_t)tasks.size() - st.flow_t0[l];
       // FP32 task times (microseconds; D, T, Efin, U, EU, DX) measured on a GB300
-      // with two CTAs per SM and with one (no second CTA competing for the SM)
+      // with two CTAs per SM and with one (no second CTA competing for the SM),
+      // and of the tensor-core launch (two CTAs per SM; per-task timestamps on the
+      // mixed-cone QP's root front: U and EU ~0.8x, the diagonal tasks ~1.1x and
+      // the panel tasks ~1.08x those of the CUDA-core launch)
       static const double dur2[6] = {22.0, 7.0, 5.5, 8.0, 8.0, 27.0};
       static const double dur1[6] = {20.0, 6.5, 5.3, 5.8, 6.1, 25.0};
-      std::vector<FlowTask> one(tasks.begin() + st.flow_t0[l], tasks.end());
-      double span2 = 0.0, span1 = 0.0;
+      static const double dur2tc[6] = {25.2, 7.6, 5.9, 6.5, 5.9, 29.8};
+      std::vector<FlowTask> one(tasks.begin() + st.flow_t0[l], tasks.end()), tco(one);
+      double span2 = 0.0, span1 = 0.0, spantc = 0.0;
       if (!flow_schedule_order(tasks, st.flow_t0[l], P_of, 2 * flow_sms, dur2, &span2) ||
-          !flow_schedule_order(one, 0, P_of, flow_sms, dur1, &span1))
+          !flow_schedule_order(one, 0, P_of, flow_sms, dur1, &span1) ||
+          !flow_schedule_order(tco, 0, P_of, 2 * flow_sms, dur2tc, &spantc))
         return CLR_E_INVALID;
-      st.flow_one[l] = span1 < 0.97 * span2 ? 1 : 0;
-      if (st.flow_one[l]) std::copy(one.begin(), one.end(), tasks.begin() + st.flow_t0[l]);
+      // the launch of the level: the shortest simulated schedule (the one-CTA and
+      // tensor-core launches only when at least 3 % shorter); the tensor-core
+      // launch applies to FP32 factors only -- an FP64 factor runs its CUDA-core
+      // launch in the order simulated for that choice (any of the orders is valid)
+      const double best_cc = std::min(span2, span1 < 0.97 * span2 ? span1 : span2);
+      st.flow_tc[l] = spantc < 0.97 * best_cc ? 1 : 0;
+      st.flow_one[l] = (!st.flow_tc[l] && span1 < 0.97 * span2) ? 1 : 0;
+      if (st.flow_tc[l]) std::copy(tco.begin(), tco.end(), tasks.begin() + st.flow_t0[l]);
+      else if (st.flow_one[l]) std::copy(one.begin(), one.end(), tasks.begin() + st.flow_t0[l]);
     }
     st.flow_words = words;
     if (!tasks.empty()) {
@@ -719,7 +732,7 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
                                                      S.flow_head[l], S.flow_soff,
                                                      S.flow_one[l] ? flow_sms : flow_sms * flow_occ, S.flow_one[l] != 0,
                                                      F, E, Dp, S.dsign, dyn_eps, dyn_delta, dyn_hits, tc_err, skip,
-                                                     (use_flow_tc() && tcs.pk) ? &tcs : nullptr)
+                                                     (use_flow_tc() && tcs.pk && (S.flow_tc[l] || flow_tc == 2)) ? &tcs : nullptr)
                         : BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps,
                                                        dyn_delta, dyn_hits, skip, tc16, tc_err);
       if (rc) return rc;

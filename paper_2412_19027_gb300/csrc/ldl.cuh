@@ -45,6 +45,7 @@ struct LdlStructure {
   int64_t* flow_soff = nullptr;
   std::vector<int64_t> flow_t0, flow_nt, flow_head;
   std::vector<int8_t> flow_one;  // per level: launch one CTA per SM (else two)
+  std::vector<int8_t> flow_tc;   // per level: FP32 factors use the tensor-core launch
   int64_t flow_words = 0;
   int64_t pk_tiles = 0;  // packed operand tiles of the largest level (tensor-core flow, FP32 factor)
   int small_max = 0;
@@ -69,13 +70,14 @@ struct LdlFactor {
   int* tc_err = nullptr;  // set if a wait of the big-front kernels ran out (the factor is unusable)
   bool tc16 = false;      // big-front updates with BF16 products on the tensor cores (float only)
   bool flow = true;       // big fronts by the dataflow kernel (one launch per level); else per-panel launches
-  bool flow_tc = true;    // FP32 dataflow: trailing and E updates on the tensor cores (TF32 hi/lo parts)
+  int flow_tc = 1;        // FP32 dataflow, trailing and E updates on the tensor cores (TF32 hi/lo parts):
+                          // 0 never, 1 on the levels whose simulated schedule is shorter that way, 2 always
   FlowTc tcs;             // its packed operand tiles and their tensor map (allocated when used)
   int* flow_state = nullptr;
   int flow_sms = 0, flow_occ = 0;  // SMs of the device, resident flow CTAs per SM
   int alloc(DeviceArena& ar, const LdlStructure& st);
   // the FP32 dataflow factorization with tensor-core updates is in use
-  bool use_flow_tc() const { return sizeof(T) == 4 && flow && flow_tc && !tc16 && s && s->pk_tiles > 0; }
+  bool use_flow_tc() const { return sizeof(T) == 4 && flow && flow_tc != 0 && !tc16 && s && s->pk_tiles > 0; }
   // Factor K: kval (FP64, lower triangle entries in kval order) scattered into
   // the fronts, +/- delta added on the diagonal (x rows +, z rows -), with
   // delta = sc[p].delta of the position's problem p.

@@ -293,7 +293,7 @@ int clr_ldl_solve(const clr_csc* K, const double* signs, const int64_t* order, i
                   double dyn_reg_eps, double dyn_reg_delta, const double* rhs, double* x_out, double* D_out,
                   int32_t* dyn_hits_out, int32_t big_front_schedule) {
   if (!K || !signs || !rhs || !x_out || (factor_bits != 64 && factor_bits != 32 && factor_bits != 16) ||
-      big_front_schedule < 0 || big_front_schedule > 2)
+      big_front_schedule < 0 || big_front_schedule > 3)
     return CLR_E_INVALID;
   const int64_t N = K->ncols;
   if (K->nrows != N) return CLR_E_DIM;
@@ -343,7 +343,7 @@ int clr_ldl_solve(const clr_csc* K, const double* signs, const int64_t* order, i
     LdlFactor<float> f;
     f.tc16 = factor_bits == 16;
     f.flow = big_front_schedule != 0;
-    f.flow_tc = big_front_schedule == 1;
+    f.flow_tc = big_front_schedule == 1 ? 1 : (big_front_schedule == 3 ? 2 : 0);
     if ((rc = f.alloc(ar, ls))) return rc;
     if ((rc = f.factor(nullptr, kv, ddelta, dyn_reg_eps, dyn_reg_delta, nullptr))) return rc;
     if ((rc = f.solve(nullptr, drhs, nullptr))) return rc;

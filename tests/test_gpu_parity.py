@@ -320,10 +320,11 @@ def test_ldl_big_fronts_with_update_rows(bits):
 @pytest.mark.parametrize("n,m", [(180, 160), (300, 260), (700, 500)])
 def test_ldl_big_fronts_tensor_core_updates(n, m):
     """FP32 dataflow factorization whose trailing and E updates run on the
-    tensor cores (big_front_schedule 1: TF32 high and low parts, FP32
+    tensor cores (big_front_schedule 3: TF32 high and low parts, FP32
     accumulation in tensor memory, operand tiles staged by TMA) against the same
     schedule with CUDA-core products (2) and against the oracle's LDL^T: fronts
-    of 3 to 11 panels of 64 columns, ragged last pivot and update blocks."""
+    of 3 to 11 panels of 64 columns, ragged last pivot and update blocks.
+    Schedule 3 puts every level on the tensor cores (1 chooses per level)."""
     rng = np.random.default_rng(n + m)
     M = rng.standard_normal((n, n))
     P = M @ M.T / n + np.eye(n)
@@ -335,7 +336,7 @@ def test_ldl_big_fronts_tensor_core_updates(n, m):
     signs = np.r_[np.ones(n), -np.ones(m)]
     rhs = rng.standard_normal(N)
     order = np.arange(N)
-    x1, D1, h1 = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=32, big_front_schedule=1)
+    x1, D1, h1 = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=32, big_front_schedule=3)
     x2, D2, h2 = clr.clr_ldl_solve(K, signs, rhs, order=order, factor_bits=32, big_front_schedule=2)
     assert h1 == 0 and h2 == 0
     L, Dref, _ = ldl_factor(K, signs, 1e-13, 2e-7)

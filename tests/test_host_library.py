@@ -256,7 +256,7 @@ def test_blocking_settings_validated_and_applied(clr):
     changes only the supernode partition (same fill, fewer and wider fronts)."""
     p = W.mixed_cone(3, n=300, n_zero=40, n_nonneg=300, n_soc=40, n_exp=10, n_pow=10, nnz_per_col=5)
     for bad in ({"small_front_max": 300}, {"small_front_max": -1}, {"amalgamation": 3},
-                {"big_front_schedule": 3}, {"big_front_schedule": -1}):
+                {"big_front_schedule": 4}, {"big_front_schedule": -1}):
         with pytest.raises(clr.ClrError):
             clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, **bad))
     with pytest.raises(clr.ClrError):  # the FP64 small-front kernel holds at most 160 x 160 in shared memory
