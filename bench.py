@@ -123,6 +123,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=1, help="0 skips the FP64 and 16-bit full solves")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-cone QP leg")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-tc-factor", action="store_true",
+                    help="skip the FP32 factorization of the batched PSD problem with and without tensor cores")
     ap.add_argument("--no-cone-roofline", action="store_true",
                     help="skip the cone kernels at stress shapes (2^26 nonneg rows, 2^22 SOC5, 2^16 PSD10)")
     ap.add_argument("--configs", action="store_true",
@@ -137,6 +139,11 @@ def parse():
     ap.add_argument("--init-only", action="store_true",
                     help="set up the workload (--n, --factor-bits, --no-graph) and run only the initial point "
                          "(one factorization and its solves), then exit: the case the factorization profiles use")
+    ap.add_argument("--init-workload", default="banded_lp", choices=["banded_lp", "psd_batch"],
+                    help="--init-only: the banded LP of order --n, or the PSD batch with n = --n variables, "
+                         "n/10 PSD(10) cones and n/4 nonnegative rows")
+    ap.add_argument("--big-front-schedule", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="large-front schedule of every solve (the setting of that name)")
     return ap.parse_args()
 
 
@@ -557,9 +564,14 @@ def run_ours(args):
         return
     if args.init_only:
         if rank == 0:
-            prob = W.banded_lp(args.seed, n=args.n) if args.n else W.banded_lp(args.seed)
+            if args.init_workload == "psd_batch":
+                nn = args.n or 20000
+                prob = W.psd_batch(args.seed, n=nn, n_psd=nn // 10, n_nonneg=nn // 4)
+            else:
+                prob = W.banded_lp(args.seed, n=args.n) if args.n else W.banded_lp(args.seed)
             st = clr.clr_default_settings(args.factor_bits, ir_stop_ratio=args.ir_stop_ratio, max_iter=0,
-                                          use_graph=0 if args.no_graph else 1)
+                                          use_graph=0 if args.no_graph else 1,
+                                          big_front_schedule=args.big_front_schedule)
             s_ = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
             s_.solve()
             info, sym = s_.info(), s_.symbolic_stats()
@@ -581,7 +593,8 @@ def run_ours(args):
     f_star = prob.objective(prob.x_star)
 
     def make(bits):
-        kw = {"ir_stop_ratio": args.ir_stop_ratio, "use_graph": 0 if args.no_graph else 1}
+        kw = {"ir_stop_ratio": args.ir_stop_ratio, "use_graph": 0 if args.no_graph else 1,
+              "big_front_schedule": args.big_front_schedule}
         st = clr.clr_default_settings(bits, **kw)
         t0 = time.perf_counter()
         s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
@@ -726,6 +739,34 @@ def run_ours(args):
             sv_.free()
         mixed["workload"] = "mixed-cone QP n=2000 m=6600 (500 zero, 3000 nonneg, 500 SOC5, 100 exp, 100 pow0.3), P=diag+rank10"
 
+    # ---------------- the FP32 factorization with tensor-core updates: the batched
+    # PSD problem (its large fronts are throughput-bound, so the per-level choice
+    # puts them on the tensor cores) against the CUDA-core launch
+    tcf = None
+    if not args.no_tc_factor and rank == 0:
+        pp = W.psd_batch(args.seed)
+        tcf = {"workload": "batched PSD problem n=20000: 2000 PSD(10) cones + 5000 nonneg rows, P=0 (FP32 factor)"}
+        for sched, key in ((1, "tensor_cores_where_chosen"), (2, "cuda_cores")):
+            st = clr.clr_default_settings(32, ir_stop_ratio=args.ir_stop_ratio, max_iter=2, big_front_schedule=sched)
+            t0 = time.perf_counter()
+            sv_ = clr.clr_setup(pp.P, pp.q, pp.A, pp.b, pp.cones, st)
+            su = time.perf_counter() - t0
+            sv_.set_stream(stream.cuda_stream)
+            sv_.solve()
+            _, _, pf = timed_solves(torch, sv_, stream, flush, 2)
+            sy_ = sv_.symbolic_stats()
+            sv_.free()
+            ms = pf["factor_ms"] / max(1, pf["factorizations"])
+            tf = sy_["factor_flops"] / (ms * 1e-3) / 1e12
+            tcf[key] = {"ms_per_factorization": ms, "factorizations": pf["factorizations"],
+                        "achieved_tflops": tf, "factor_flops": sy_["factor_flops"], "setup_s": su,
+                        "frac_of_tf32_tensor_peak": tf / peaks["tf32_tc_tflops"],
+                        "frac_of_fp32_fma_peak": tf / peaks["fp32_fma_tflops"]}
+        tcf["speedup"] = tcf["cuda_cores"]["ms_per_factorization"] / tcf["tensor_cores_where_chosen"]["ms_per_factorization"]
+        tcf["note"] = ("flops = the LDL^T's exact symbolic count per factorization; each 64 x 64 x 64 tile update "
+                       "issues 4x its flops as TF32 MMAs (high and low parts of both operands), so the algorithmic "
+                       "rate is bounded by 1/4 of the TF32 peak")
+
     cone_roof = None
     if not args.no_cone_roofline and rank == 0:
         cone_roof = run_cone_roofline(clr, W, {"hbm_gbs": peaks["hbm_gbs"], "source": copy_peaks["source"]})
@@ -763,6 +804,7 @@ def run_ours(args):
                                      "the iterations timed",
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                 "mixed_cone_qp": mixed, "serving": serving, "cone_roofline": cone_roof,
+                "tensor_core_factorization": tcf,
                 "generation_s": t_gen,
                 "symbolic": {k: sym[k] for k in ("kkt_dim", "l_nnz", "factor_flops", "n_supernodes", "n_levels",
                                                  "max_front")}}
