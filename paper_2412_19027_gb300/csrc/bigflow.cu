@@ -273,13 +273,16 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     }
   }
   __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
+  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3.  Linv is unit lower
+  // triangular, so columns 4 tc .. need only l <= 4 tc + 3 (the terms skipped are
+  // exact zeros); warp w takes column blocks w and 15 - w, which balances them
+  const int tr = tid % 16, tcw = tid / 16, tc = (tcw & 1) ? 15 - (tcw >> 1) : (tcw >> 1);
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
-  for (int l = 0; l < NB; ++l) {
+  for (int l = 0; l < 4 * tc + 4; ++l) {
     T av[4], bv[4];
     ld4<T>(Xk + swz(l, 4 * tr), av);
     ld4<T>(Bk + swz(l, 4 * tc), bv);
@@ -313,30 +316,37 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     __threadfence();
     st_release(trsm_word, p);
   }
-  // A_ij -= sum_l L_il (L_jl d_l), i >= j
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
-  for (int l = 0; l < NB; ++l) {
-    T av[4], bv[4];
-    ld4<T>(Xk + swz(l, 4 * tr), av);
-    ld4<T>(Xk + swz(l, 4 * tc), bv);
-    const T dlv = dl[l];
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) bv[bb] *= dlv;
+  // A_ij -= sum_l L_il (L_jl d_l), i >= j: only the 136 4 x 4 blocks on or below
+  // the diagonal, one per thread (threads 136 .. 255 idle), each summed in the
+  // same order as a full-tile product would
+  if (tid < 136) {
+    int lr = 0;
+    while ((lr + 1) * (lr + 2) / 2 <= tid) ++lr;  // block row; tid = lr (lr + 1) / 2 + lc
+    const int lc = tid - lr * (lr + 1) / 2;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
-  }
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+    for (int l = 0; l < NB; ++l) {
+      T av[4], bv[4];
+      ld4<T>(Xk + swz(l, 4 * lr), av);
+      ld4<T>(Xk + swz(l, 4 * lc), bv);
+      const T dlv = dl[l];
 #pragma unroll
-  for (int bb = 0; bb < 4; ++bb) {
-    const int j = 4 * tc + bb;
+      for (int bb = 0; bb < 4; ++bb) bv[bb] *= dlv;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = 4 * tr + a;
-      if (i < pw && i >= j) A[i * LD + j] -= acc[a][bb];
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+    }
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      const int j = 4 * lc + bb;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = 4 * lr + a;
+        if (i < pw && i >= j) A[i * LD + j] -= acc[a][bb];
+      }
     }
   }
   __syncthreads();
@@ -378,13 +388,16 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
     }
   }
   __syncthreads();
-  const int tr = tid % 16, tc = tid / 16;  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3
+  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3; Linv lower triangular: only
+  // l <= 4 tc + 3 (as in the fused chain task)
+  const int tr = tid % 16, tcw = tid / 16, tc = (tcw & 1) ? 15 - (tcw >> 1) : (tcw >> 1);
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
-  for (int l = 0; l < pw; ++l) {
+  const int lend = min(pw, 4 * tc + 4);
+  for (int l = 0; l < lend; ++l) {
     T av[4], bv[4];
     ld4<T>(Xk + swz(l, 4 * tr), av);
     ld4<T>(Bk + swz(l, 4 * tc), bv);
