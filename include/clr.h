@@ -132,6 +132,10 @@ typedef struct {
                                  than escalate_ratio times the largest entry of the iterate's scaled residual G
                                  while the primal or dual residual is still more than 100 times its termination
                                  tolerance (the direction is then too inexact to reduce it); default 0.1, 0 = off */
+  int32_t soc_expand_dim;     /* second-order cones of at least this many rows enter the KKT matrix in sparse
+                                 form (Sec. 3.3: H = eta^2 (I + u u' - v v') as its diagonal plus two extra
+                                 rows and columns per cone, [-eta^2 I, eta u, eta v; eta u', 1, 0;
+                                 eta v', 0, -1]) instead of a dense d x d block; default 33, 0 = never */
 } clr_settings;
 
 typedef struct {
@@ -154,7 +158,9 @@ typedef struct {
 
 /* Statistics of the symbolic KKT analysis done at setup. */
 typedef struct {
-  int64_t n, m, kkt_dim;   /* N = n + m */
+  int64_t n, m, kkt_dim;   /* N = n + m; m counts the two auxiliary rows of each expanded SOC (the last
+                              rows of the reordered constraint block; clr_get_symbolic's row_perm and
+                              clr_get_scaling's E cover the caller's rows only) */
   int64_t kkt_nnz_lower;   /* structural nonzeros of the lower triangle of K */
   int64_t l_nnz;           /* nonzeros of L (supernodal, including the diagonal) */
   double factor_flops;     /* flops of the exact factor (multiply-adds x 2; explicit zeros excluded) */
@@ -396,13 +402,13 @@ int clr_get_perf(const clr_solver* s, clr_perf* out);
  * + 1): columns of supernode J are perm-positions sn_ptr[J] .. sn_ptr[J+1]-1.
  * sn_parent (n_supernodes): parent supernode or -1.  row_ptr (n_supernodes+1)
  * and rows (row_ptr[n_supernodes]): perm-positions of the rows of each front,
- * its own columns first.  row_perm (m): reordered constraint row i is caller
+ * its own columns first.  row_perm (the caller's m): reordered constraint row i is caller
  * row row_perm[i].  Any output may be NULL; sizes from clr_get_symbolic_stats
  * (rows total: query with rows == NULL and read *rows_len). */
 int clr_get_symbolic(const clr_solver* s, int64_t* perm, int64_t* sn_ptr, int64_t* sn_parent, int64_t* row_ptr,
                      int64_t* rows, int64_t* rows_len, int64_t* row_perm);
 
-/* Equilibration scalings: D (n), E (m, reordered rows), c (1 value). */
+/* Equilibration scalings: D (n), E (the caller's m, reordered rows), c (1 value). */
 int clr_get_scaling(const clr_solver* s, double* D, double* E, double* c);
 
 /* Per-iteration log of the last solve, up to cap rows of 12 doubles:

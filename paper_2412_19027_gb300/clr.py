@@ -44,7 +44,8 @@ class clr_settings(C.Structure):
                 ("step_fraction", C.c_double), ("backtrack", C.c_double), ("nbhd_beta", C.c_double),
                 ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32),
                 ("fp64_escalation", C.c_int32), ("big_front_schedule", C.c_int32),
-                ("small_front_max", C.c_int32), ("amalgamation", C.c_int32), ("escalate_ratio", C.c_double)]
+                ("small_front_max", C.c_int32), ("amalgamation", C.c_int32), ("escalate_ratio", C.c_double),
+                ("soc_expand_dim", C.c_int32)]
 
 
 class clr_info(C.Structure):

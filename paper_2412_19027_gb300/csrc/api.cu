@@ -56,6 +56,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.small_front_max = 0;
   s.amalgamation = 1;
   s.escalate_ratio = 0.1;
+  s.soc_expand_dim = 33;
   *out = s;
   return CLR_OK;
 }
@@ -69,7 +70,7 @@ static int check_settings(const clr_settings& s) {
       s.amalgamation > 2)
     return CLR_E_INVALID;
   if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
-  if (!(s.escalate_ratio >= 0)) return CLR_E_INVALID;
+  if (!(s.escalate_ratio >= 0) || s.soc_expand_dim < 0) return CLR_E_INVALID;
   if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;
   return CLR_OK;
 }
@@ -384,7 +385,8 @@ int clr_get_symbolic(const clr_solver* s, int64_t* perm, int64_t* sn_ptr, int64_
   if (row_ptr) std::copy(v.sy.row_ptr.begin(), v.sy.row_ptr.end(), row_ptr);
   if (rows) std::copy(v.sy.rows.begin(), v.sy.rows.end(), rows);
   if (rows_len) *rows_len = (int64_t)v.sy.rows.size();
-  if (row_perm) std::copy(v.hp.row_perm.begin(), v.hp.row_perm.end(), row_perm);
+  // the caller's rows (the auxiliary rows of expanded SOCs come last and have none)
+  if (row_perm) std::copy(v.hp.row_perm.begin(), v.hp.row_perm.end() - v.hp.cl.n_aux, row_perm);
   return CLR_OK;
 }
 
@@ -392,7 +394,7 @@ int clr_get_scaling(const clr_solver* s, double* D, double* E, double* c) {
   if (!s) return CLR_E_INVALID;
   const Solver& v = s->impl;
   if (D) std::copy(v.hp.D.begin(), v.hp.D.end(), D);
-  if (E) std::copy(v.hp.E.begin(), v.hp.E.end(), E);
+  if (E) std::copy(v.hp.E.begin(), v.hp.E.end() - v.hp.cl.n_aux, E);
   if (c) *c = v.hp.c;
   return CLR_OK;
 }

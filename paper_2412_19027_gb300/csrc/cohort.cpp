@@ -28,7 +28,7 @@ void chunk_run(std::vector<Chunk>& out, int64_t begin, int64_t len, int32_t pid)
 }
 
 // rows of family f (0 zero, 1 nonneg, 2 SOC, 3 exp, 4 pow, 5 PSD) in a problem's reordered rows
-void family_ranges(const HostProblem& p, int64_t start[6], int64_t size[6]) {
+void family_ranges(const HostProblem& p, int64_t start[7], int64_t size[7]) {
   const ConeLayout& cl = p.cl;
   auto rows_of = [&](int64_t c0, int64_t c1, int64_t* st, int64_t* sz) {
     *sz = 0;
@@ -43,6 +43,8 @@ void family_ranges(const HostProblem& p, int64_t start[6], int64_t size[6]) {
   rows_of(cl.exp_begin, cl.exp_end, &start[3], &size[3]);
   rows_of(cl.pow_begin, cl.pow_end, &start[4], &size[4]);
   rows_of(cl.psd_begin, cl.psd_end, &start[5], &size[5]);
+  start[6] = cl.aux_begin;  // the auxiliary rows of the expanded SOCs
+  size[6] = cl.n_aux;
 }
 
 void release_big(HostProblem& p) {
@@ -127,9 +129,9 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     lay.pc[0] = prob_const(hp);
     chunk_run(lay.ckx, 0, n, 0);
     if (lay.ckx.empty()) lay.ckx.push_back(Chunk{0, 0, 0});
-    int64_t fs[6], fz[6];
+    int64_t fs[7], fz[7];
     family_ranges(hp, fs, fz);
-    for (int f = 0; f < 6; ++f) chunk_run(lay.ckz, fs[f], fz[f], 0);
+    for (int f = 0; f < 7; ++f) chunk_run(lay.ckz, fs[f], fz[f], 0);
     if (lay.ckz.empty()) lay.ckz.push_back(Chunk{0, 0, 0});
     lay.ckx_ptr[1] = (int64_t)lay.ckx.size();
     lay.ckz_ptr[1] = (int64_t)lay.ckz.size();
@@ -168,22 +170,23 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
   lay.xo.assign(B + 1, 0);
   for (int64_t p = 0; p < B; ++p) lay.xo[p + 1] = lay.xo[p] + probs[p].n;
   const int64_t n = lay.xo[B];
-  std::vector<std::array<int64_t, 6>> fstart(B), fsize(B);
-  int64_t ftot[6] = {0, 0, 0, 0, 0, 0};
+  constexpr int NF = 7;  // zero, nonneg, SOC, exp, pow, PSD, auxiliary rows
+  std::vector<std::array<int64_t, NF>> fstart(B), fsize(B);
+  int64_t ftot[NF] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t p = 0; p < B; ++p) {
     family_ranges(probs[p], fstart[p].data(), fsize[p].data());
-    for (int f = 0; f < 6; ++f) ftot[f] += fsize[p][f];
+    for (int f = 0; f < NF; ++f) ftot[f] += fsize[p][f];
   }
-  int64_t cstart[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int f = 0; f < 6; ++f) cstart[f + 1] = cstart[f] + ftot[f];
-  const int64_t m = cstart[6];
+  int64_t cstart[NF + 1] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int f = 0; f < NF; ++f) cstart[f + 1] = cstart[f] + ftot[f];
+  const int64_t m = cstart[NF];
   const int64_t N = n + m;
-  std::vector<std::array<int64_t, 6>> pref(B);  // start of problem p's run inside family f
+  std::vector<std::array<int64_t, NF>> pref(B);  // start of problem p's run inside family f
   {
-    int64_t run[6];
-    for (int f = 0; f < 6; ++f) run[f] = cstart[f];
+    int64_t run[NF];
+    for (int f = 0; f < NF; ++f) run[f] = cstart[f];
     for (int64_t p = 0; p < B; ++p)
-      for (int f = 0; f < 6; ++f) {
+      for (int f = 0; f < NF; ++f) {
         pref[p][f] = run[f];
         run[f] += fsize[p][f];
       }
@@ -192,7 +195,7 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
   std::vector<int64_t> zinv_r(m);
   for (int64_t p = 0; p < B; ++p) {
     lay.zrow[p].assign(probs[p].m, -1);
-    for (int f = 0; f < 6; ++f)
+    for (int f = 0; f < NF; ++f)
       for (int64_t k = 0; k < fsize[p][f]; ++k) {
         const int64_t r = fstart[p][f] + k, R = pref[p][f] + k;
         lay.zrow[p][r] = R;
@@ -211,7 +214,7 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
     const size_t x0 = lay.ckx.size(), z0 = lay.ckz.size();
     chunk_run(lay.ckx, lay.xo[p], probs[p].n, (int32_t)p);
     if (lay.ckx.size() == x0) lay.ckx.push_back(Chunk{lay.xo[p], 0, (int32_t)p});
-    for (int f = 0; f < 6; ++f) chunk_run(lay.ckz, pref[p][f], fsize[p][f], (int32_t)p);
+    for (int f = 0; f < NF; ++f) chunk_run(lay.ckz, pref[p][f], fsize[p][f], (int32_t)p);
     if (lay.ckz.size() == z0) lay.ckz.push_back(Chunk{0, 0, (int32_t)p});
     lay.ckx_ptr[p + 1] = (int64_t)lay.ckx.size();
     lay.ckz_ptr[p + 1] = (int64_t)lay.ckz.size();
@@ -283,6 +286,7 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
         Cone k = pl.cones[c];
         k.off = lay.zrow[p][k.off];
         k.kbase = zcol_start[k.off];
+        if (k.aux >= 0) k.aux = lay.zrow[p][k.aux];
         cl.cones.push_back(k);
         if (k.type == CLR_SOC) cl.soc_max_dim = std::max(cl.soc_max_dim, k.dim);
       }
@@ -293,6 +297,8 @@ int build_cohort(std::vector<HostProblem>& probs, const std::vector<std::vector<
   add_family(&ConeLayout::exp_begin, &ConeLayout::exp_end, &cl.exp_begin, &cl.exp_end);
   add_family(&ConeLayout::pow_begin, &ConeLayout::pow_end, &cl.pow_begin, &cl.pow_end);
   add_family(&ConeLayout::psd_begin, &ConeLayout::psd_end, &cl.psd_begin, &cl.psd_end);
+  cl.aux_begin = cstart[6];
+  cl.n_aux = ftot[6];
   cl.kval_z = (int64_t)hp.kval.size() - hp.kval_x;
   cl.nu = 0;
   cl.symmetric_only = true;

@@ -278,6 +278,14 @@ __device__ __forceinline__ double gmax(double v) {
   for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+// A SOC of at most kSocT rows in dense form: the thread-per-cone kernels take it.
+// In a cohort that also holds larger (or expanded) SOCs each kernel family takes
+// its own cones (ConeDev::soc_split), so that a cone's arithmetic does not depend
+// on which other problems share the launch.
+constexpr int kSocT = 8;
+__device__ __forceinline__ bool soc_small(const ConeDev& cd, int64_t c) {
+  return cd.soc_dim[c] <= kSocT && !(cd.soc_aux && cd.soc_aux[c] >= 0);
+}
 // The cones of a warp in pass k: (w + k nw) 32/G + g, g the lane group.  Every
 // lane of a warp runs the same passes (shuffles need the whole warp); a group
 // past the last cone works on an empty cone (d = 0) and writes nothing.
@@ -315,7 +323,7 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
   RunExt<true> run;
   SOC_GROUP_LOOP(G) {
     const int64_t cone = base + (threadIdx.x & 31) / G;
-    const bool valid = cone < cd.n_soc;
+    const bool valid = cone < cd.n_soc && !(cd.soc_split && soc_small(cd, cone));
     const int64_t off = valid ? cd.soc_off[cone] : 0;
     const int d = valid ? cd.soc_dim[cone] : 0;
     const double* sv = s + off;
@@ -361,18 +369,44 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
     const double e2 = eta * eta;
     double* kb = cd.kvz + (valid ? cd.soc_kb[cone] : 0);
     double mx = 0.0;
-    int64_t kbase = 0;
-    for (int c = 0; c < d; ++c) {
-      const double wc = cd.soc_wb[off + c];
-      for (int r = c + lane; r < d; r += G) {
-        double h = 2.0 * e2 * cd.soc_wb[off + r] * wc;
-        if (r == c) {
-          h += (c == 0) ? -e2 : e2;
-          mx = fmax(mx, fabs(h));
-        }
-        kb[kbase + (r - c)] = -h;
+    const int64_t aux = (valid && cd.soc_aux) ? cd.soc_aux[cone] : -1;  // uniform over the group
+    if (aux >= 0) {
+      // sparse form (the large-SOC expansion of Sec. 3.3): 2 wb wb' - J = I + 2 (wb wb' - e0 e0'),
+      // and the rank-two part has, in the basis e0, w^ = (0, wb_1) / r (r = ||wb_1||, wb0^2 - r^2 = 1),
+      // the matrix 2 [r^2, wb0 r; wb0 r, r^2]: eigenvectors (e0 +- w^) / sqrt 2, eigenvalues
+      // 2 r (r +- wb0).  So H = eta^2 (I + u u' - v v') with u = sqrt(r (r + wb0)) (e0 + w^) and
+      // v = sqrt(r / (r + wb0)) (e0 - w^), v'v = 2 r / (r + wb0) < 1 (the matrix with the two
+      // extra rows stays quasi-definite).  Column i: -eta^2 on the diagonal, eta u_i and
+      // eta v_i in the two auxiliary rows.
+      double r2 = 0.0;
+      for (int j = lane; j < d; j += G)
+        if (j > 0) r2 += cd.soc_wb[off + j] * cd.soc_wb[off + j];
+      r2 = gsum<G>(r2);
+      const double r = sqrt(r2);
+      const double cu = r > 0.0 ? sqrt(r * (r + wb0)) : 0.0, cv = r > 0.0 ? sqrt(r / (r + wb0)) : 0.0;
+      const double ir = r > 0.0 ? 1.0 / r : 0.0;
+      for (int j = lane; j < d; j += G) {
+        const double wj = cd.soc_wb[off + j];
+        const double uj = (j == 0) ? cu : cu * wj * ir, vj = (j == 0) ? cv : -cv * wj * ir;
+        kb[3 * j] = -e2;
+        kb[3 * j + 1] = eta * uj;
+        kb[3 * j + 2] = eta * vj;
+        mx = fmax(mx, fabs(e2 * (2.0 * wj * wj + ((j == 0) ? -1.0 : 1.0))));  // H_jj
       }
-      kbase += d - c;
+    } else {
+      int64_t kbase = 0;
+      for (int c = 0; c < d; ++c) {
+        const double wc = cd.soc_wb[off + c];
+        for (int r = c + lane; r < d; r += G) {
+          double h = 2.0 * e2 * cd.soc_wb[off + r] * wc;
+          if (r == c) {
+            h += (c == 0) ? -e2 : e2;
+            mx = fmax(mx, fabs(h));
+          }
+          kb[kbase + (r - c)] = -h;
+        }
+        kbase += d - c;
+      }
     }
     mx = gmax<G>(mx);
     if (lane == 0 && valid) run.add(sc, &IterScal::hmax_bits, cd.row_pid[off], dbits(mx));
@@ -388,13 +422,13 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
 // computed once per cone, where a lane group computed them once per lane; these passes
 // are bound by the FP64 pipe (~2 DFMA per clock per SM), so the redundant work was
 // what they spent their time on.  The formulas are those of the lane-group kernels.
-constexpr int kSocT = 8;
 inline unsigned soc_t_grid(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16 * kSMs));
 }
 #define SOC_THREAD_LOOP \
   for (int64_t cone = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cone < cd.n_soc; \
-       cone += (int64_t)gridDim.x * blockDim.x)
+       cone += (int64_t)gridDim.x * blockDim.x) \
+    if (!cd.soc_split || soc_small(cd, cone))
 
 __global__ void __launch_bounds__(256) k_scale_soc_t(ConeDev cd, const double* __restrict__ s,
                                                      const double* __restrict__ z, IterScal* sc, const int* skip) {
@@ -879,8 +913,9 @@ int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const dou
   if (cd.m_zero + cd.m_nonneg > 0)
     k_scale_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, s, z, sc, skip);
   if (cd.n_soc > 0) {
-    if (cd.soc_dmax <= kSocT) k_scale_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, s, z, sc, skip);
-    else k_scale_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, z, sc, skip);
+    // small dense SOCs a thread per cone; larger and expanded ones (sparse KKT form) a warp per cone
+    if (cd.soc_nsmall > 0) k_scale_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, s, z, sc, skip);
+    if (cd.soc_nsmall < cd.n_soc) k_scale_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, z, sc, skip);
   }
   if (cd.n_exp + cd.n_pow > 0)
     k_scale_exppow<<<ep_launch(cd.n_exp + cd.n_pow).blocks, ep_launch(cd.n_exp + cd.n_pow).threads, 0, st>>>(
@@ -913,7 +948,13 @@ __global__ void k_identity_diag(ConeDev cd, const int* skip) {
       }
       const int64_t c = r - cd.soc_off[lo];
       const int64_t d = cd.soc_dim[lo];
-      cd.kvz[cd.soc_kb[lo] + c * d - c * (c - 1) / 2] = -1.0;
+      const bool expanded = cd.soc_aux && cd.soc_aux[lo] >= 0;  // its couplings stay 0 (u = v = 0)
+      cd.kvz[cd.soc_kb[lo] + (expanded ? 3 * c : c * d - c * (c - 1) / 2)] = -1.0;
+      continue;
+    }
+    if (cd.n_aux > 0 && r >= cd.aux_begin) {  // auxiliary rows: their constant diagonals
+      const int64_t k = r - cd.aux_begin;
+      cd.kvz[cd.nkz - cd.n_aux + k] = (k % 2 == 0) ? 1.0 : -1.0;
       continue;
     }
     if (r >= cd.exp_row0 && r < cd.exp_row0 + 3 * cd.n_exp) {
@@ -1027,7 +1068,7 @@ __global__ void k_step_soc(ConeDev cd, const double* __restrict__ s, const doubl
   RunExt<false> run;
   SOC_GROUP_LOOP(G) {
     const int64_t cone = base + (threadIdx.x & 31) / G;
-    const bool valid = cone < cd.n_soc;
+    const bool valid = cone < cd.n_soc && !(cd.soc_split && soc_small(cd, cone));
     const int64_t off = valid ? cd.soc_off[cone] : 0;
     const int d = valid ? cd.soc_dim[cone] : 0;
     const double a = fmin(soc_step<G>(s + off, ds + off, d), soc_step<G>(z + off, dz + off, d));
@@ -1089,8 +1130,8 @@ int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, co
                          const double* dz, IterScal* sc, const int* skip) {
   if (cd.m_nonneg > 0) k_step_nonneg<<<grid_for(cd.m_nonneg, 256), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   if (cd.n_soc > 0) {
-    if (cd.soc_dmax <= kSocT) k_step_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
-    else k_step_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+    if (cd.soc_nsmall > 0) k_step_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+    if (cd.soc_nsmall < cd.n_soc) k_step_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   }
   if (cd.n_psd > 0) {
     const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
@@ -1285,7 +1326,7 @@ __global__ void k_ds_soc(ConeDev cd, const double* __restrict__ dsa, const doubl
   if (skip && *skip) return;
   SOC_GROUP_LOOP(G) {
     const int64_t cone = base + (threadIdx.x & 31) / G;
-    const bool valid = cone < cd.n_soc;
+    const bool valid = cone < cd.n_soc && !(cd.soc_split && soc_small(cd, cone));
     const int64_t off = valid ? cd.soc_off[cone] : 0;
     const int d = valid ? cd.soc_dim[cone] : 0;
     const double eta = valid ? cd.soc_eta[cone] : 1.0;
@@ -1521,8 +1562,9 @@ int cones_combined_ds(cudaStream_t st, const ConeDev& cd, const double* s, const
   if (cd.m_zero + cd.m_nonneg > 0)
     k_ds_nonneg<<<grid_for(cd.m_zero + cd.m_nonneg, 256), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
   if (cd.n_soc > 0) {
-    if (cd.soc_dmax <= kSocT) k_ds_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
-    else k_ds_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
+    if (cd.soc_nsmall > 0) k_ds_soc_t<<<soc_t_grid(cd.n_soc), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, skip);
+    if (cd.soc_nsmall < cd.n_soc)
+      k_ds_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, dsa, dza, sc, ds_out, cd.scratch, skip);
   }
   if (cd.n_exp + cd.n_pow > 0)
     k_ds_exppow<<<ep_launch(cd.n_exp + cd.n_pow).blocks, ep_launch(cd.n_exp + cd.n_pow).threads, 0, st>>>(
@@ -1619,7 +1661,7 @@ __global__ void k_unit_init(ConeDev cd, double* __restrict__ v, const int* skip)
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < cd.m; r += (int64_t)gridDim.x * blockDim.x) {
     if (cd.pc[cd.row_pid[r]].sym) continue;  // symmetric problems keep their symmetric initial point
     double val = 0.0;
-    if (r < cd.m_zero) val = 0.0;
+    if (r < cd.m_zero || (cd.n_aux > 0 && r >= cd.aux_begin)) val = 0.0;  // zero cone, auxiliary rows
     else if (r < cd.m_zero + cd.m_nonneg) val = 1.0;
     else if (cd.n_soc > 0 && r < cd.soc_off[cd.n_soc - 1] + cd.soc_dim[cd.n_soc - 1]) {
       int64_t lo = 0, hi = cd.n_soc - 1;

@@ -21,7 +21,18 @@ struct ConeDev {
   const int64_t* soc_off = nullptr;
   const int32_t* soc_dim = nullptr;
   const int64_t* soc_kb = nullptr;
-  int soc_dmax = 0;  // largest SOC dimension (picks 8 or 32 lanes per cone)
+  // expanded SOCs (null: none): per cone its first auxiliary row, or -1 for a dense
+  // block.  An expanded cone's kval holds 3 values per row from soc_kb on (the
+  // diagonal -eta^2, then eta u_i and eta v_i in its two auxiliary rows); the
+  // auxiliary rows [aux_begin, aux_begin + n_aux) are the last rows, their
+  // diagonals (+1, -1 alternating) the last n_aux entries of kvz
+  const int64_t* soc_aux = nullptr;
+  int64_t aux_begin = 0, n_aux = 0;
+  int soc_dmax = 0;  // largest SOC dimension
+  // dense SOCs of at most 8 rows (a thread per cone; the others a warp per cone);
+  // soc_split: both kinds are present, each kernel family skips the other's cones
+  int64_t soc_nsmall = 0;
+  int soc_split = 0;
   // exp / pow cones: rows row0 + 3 i, packed H at kb0 + 6 i
   int64_t n_exp = 0, exp_row0 = 0, exp_kb0 = 0;
   int64_t n_pow = 0, pow_row0 = 0, pow_kb0 = 0;

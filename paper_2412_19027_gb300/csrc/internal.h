@@ -3,8 +3,10 @@
 // Numbering used throughout:
 //   KKT index i in [0, N), N = n + m:  i < n is x_i, i = n + r is constraint
 //   row r of the REORDERED constraint block (zero, nonneg, SOC, exp, pow, PSD;
-//   Sec. 3.3 and 3.5 of the paper).  The KKT matrix is Eq. linsys_2x2:
-//   K = [P A^T; A -H].
+//   Sec. 3.3 and 3.5 of the paper), then the auxiliary rows of the expanded
+//   SOCs (two per cone, p then q; no caller row, empty A row, b = 0, s = z = 0
+//   throughout; their KKT rows carry the low-rank part of the cone's H).  The
+//   KKT matrix is Eq. linsys_2x2: K = [P A^T; A -H].
 //   Elimination position k in [0, N): perm[k] = KKT index eliminated k-th.
 #pragma once
 
@@ -25,6 +27,8 @@ struct Cone {
   double alpha;
   int64_t off;    // first reordered constraint row
   int64_t kbase;  // offset of its packed lower H block in the z part of kval
+  int64_t aux = -1;  // expanded SOC: its first auxiliary row (q = aux + 1); its z columns then
+                     // hold 3 values each (diagonal -eta^2, eta u_i, eta v_i) from kbase on
 };
 
 // Compressed sparse row (or column) matrix with int64 pointers.
@@ -49,6 +53,8 @@ struct ConeLayout {
   int64_t soc_max_dim = 0;
   int64_t kval_z = 0;        // entries of the z part of kval
   bool symmetric_only = true;
+  int64_t aux_begin = 0, n_aux = 0;  // auxiliary rows of the expanded SOCs: [aux_begin, aux_begin + n_aux),
+                                     // the last rows; p rows at even offsets (KKT diagonal +1), q rows -1
 };
 
 // Symbolic supernodal factorization of the permuted KKT matrix.

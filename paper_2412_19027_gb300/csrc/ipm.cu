@@ -38,6 +38,7 @@ __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlon
 struct ChunkGrid {
   const Chunk* ck;
   int64_t nckx, pst, n;  // pst: stride of a partial-sum slot
+  int64_t zaux = INT64_MAX;  // first auxiliary row of the expanded SOCs (kernels that keep them at 0)
 };
 // KKT index range of block b's chunk: [i0, i0 + len); z chunks start at n.
 __device__ __forceinline__ void chunk_range(const ChunkGrid& g, int64_t* i0, int64_t* len, int* pid, bool* zpart) {
@@ -759,6 +760,7 @@ __global__ void k_update(ChunkGrid g, double* __restrict__ xz, double* __restric
   if (sc[pid].halt || sc[pid].escalate) return;
   const double a = frac * sc[pid].alpha_c;
   for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
+    if (zp && i - g.n >= g.zaux) continue;  // auxiliary rows: s = z = 0
     xz[i] += a * dir[i];
     if (zp) s[i - g.n] += a * ds[i - g.n];
   }
@@ -824,11 +826,12 @@ __global__ void k_init_take(ChunkGrid g, double* __restrict__ xz, double* __rest
   chunk_range(g, &i0, &len, &pid, &zp);
   if (!pc[pid].sym) return;
   for (int64_t i = i0 + threadIdx.x; i < i0 + len; i += blockDim.x) {
+    const bool aux = zp && i - g.n >= g.zaux;  // auxiliary rows: s = z = 0
     if (which == 0) {
       if (!zp) xz[i] = sol[i];
-      else s[i - g.n] = -sol[i];
+      else s[i - g.n] = aux ? 0.0 : -sol[i];
     } else if (zp) {
-      xz[i] = sol[i];
+      xz[i] = aux ? 0.0 : sol[i];
     }
   }
 }
@@ -1013,7 +1016,10 @@ int Solver::upload() {
   std::vector<int8_t> dsign(N);
   std::vector<int32_t> pos_pid(N);
   for (int64_t k = 0; k < N; ++k) {
-    dsign[k] = sy.perm[k] < n ? 1 : -1;
+    const int64_t v = sy.perm[k], r = v - n;
+    // x rows +1, constraint rows -1, except the first auxiliary row (p) of each expanded SOC: +1
+    const bool aux_p = r >= hp.cl.aux_begin && r < hp.cl.aux_begin + hp.cl.n_aux && (r - hp.cl.aux_begin) % 2 == 0;
+    dsign[k] = (v < n || aux_p) ? 1 : -1;
     pos_pid[k] = lay.pid[sy.perm[k]];
   }
   const int small_max = st.small_front_max > 0 ? st.small_front_max : (st.factor_bits == 64 ? 96 : 128);
@@ -1115,6 +1121,11 @@ int Solver::upload() {
   v_.dsa = ar_.alloc_n<double>(m);
   v_.dir = ar_.alloc_n<double>(N);
   v_.ds = ar_.alloc_n<double>(m);
+  // Delta s of the auxiliary rows is never written: zero for good
+  if (v_.dsa && v_.ds) {
+    CLR_CUDA(cudaMemsetAsync(v_.dsa, 0, sizeof(double) * (size_t)std::max<int64_t>(m, 1), stream_));
+    CLR_CUDA(cudaMemsetAsync(v_.ds, 0, sizeof(double) * (size_t)std::max<int64_t>(m, 1), stream_));
+  }
   v_.dsrhs = ar_.alloc_n<double>(m);
   v_.r = ar_.alloc_n<double>(N);
   v_.solb = ar_.alloc_n<double>(N);
@@ -1139,17 +1150,23 @@ int Solver::upload() {
   cd_.nn_lam = ar_.alloc_n<double>(cl.m_nonneg);
   cd_.n_soc = cl.soc_end - cl.soc_begin;
   {
-    std::vector<int64_t> off, kb;
+    std::vector<int64_t> off, kb, aux;
     std::vector<int32_t> dim;
     for (int64_t c = cl.soc_begin; c < cl.soc_end; ++c) {
       off.push_back(cl.cones[c].off);
       dim.push_back((int32_t)cl.cones[c].dim);
       cd_.soc_dmax = std::max<int>(cd_.soc_dmax, (int)cl.cones[c].dim);
       kb.push_back(cl.cones[c].kbase);
+      aux.push_back(cl.cones[c].aux);
+      if (cl.cones[c].dim <= 8 && cl.cones[c].aux < 0) cd_.soc_nsmall++;  // a thread per cone
     }
+    cd_.soc_split = (cd_.soc_nsmall > 0 && cd_.soc_nsmall < cd_.n_soc) ? 1 : 0;
     cd_.soc_off = ar_.upload(off.data(), (int64_t)off.size());
     cd_.soc_dim = ar_.upload(dim.data(), (int64_t)dim.size());
     cd_.soc_kb = ar_.upload(kb.data(), (int64_t)kb.size());
+    if (cl.n_aux > 0) cd_.soc_aux = ar_.upload(aux.data(), (int64_t)aux.size());
+    cd_.aux_begin = cl.aux_begin;
+    cd_.n_aux = cl.n_aux;
   }
   cd_.soc_eta = ar_.alloc_n<double>(cd_.n_soc);
   cd_.soc_wb = ar_.alloc_n<double>(m);
@@ -1351,7 +1368,8 @@ int Solver::direction(bool affine) {
   k_dots<<<nck, 256, 0, s>>>(cg, da, v_.part, S_D0, halt);
   k_fin_dtau<<<(unsigned)B, 128, 0, s>>>(sc_, v_.part, pst_, v_.ckx_ptr, v_.ckz_ptr, halt);
   k_recover<<<nck, 256, 0, s>>>(cg, dir, v_.sol1, v_.sol2, sc_, halt);
-  kmv(csr_group_, s, 2, n, N, n, v_, h_long_, dir, nullptr, nullptr, v_.dsrhs, ds, sc_, halt);
+  // (the auxiliary rows of expanded SOCs, the last rows, keep Delta s = 0)
+  kmv(csr_group_, s, 2, n, N - hp.cl.n_aux, n, v_, h_long_, dir, nullptr, nullptr, v_.dsrhs, ds, sc_, halt);
   // PSD rows again, with H in factored form (the assembled block loses the small
   // eigen-directions of S near convergence)
   cones_psd_ds_from_dz(s, cd_, dir + n, v_.dsrhs, ds, halt);
@@ -1395,7 +1413,7 @@ int Solver::iteration() {
   const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   cudaStream_t s = stream_;
   const int* halt = &bf_->all_halt;
-  const ChunkGrid cg{v_.ck, nckx_, pst_, n};
+  const ChunkGrid cg{v_.ck, nckx_, pst_, n, hp.cl.n_aux ? hp.cl.aux_begin : INT64_MAX};
   const unsigned nck = (unsigned)(nckx_ + nckz_);
   const int pg = grid_for(B, 128);
   int rc;
@@ -1454,7 +1472,7 @@ int Solver::iteration() {
 int Solver::initialise() {
   const int64_t n = hp.n, m = hp.m, N = n + m, B = lay.B;
   cudaStream_t s = stream_;
-  const ChunkGrid cg{v_.ck, nckx_, pst_, n};
+  const ChunkGrid cg{v_.ck, nckx_, pst_, n, hp.cl.n_aux ? hp.cl.aux_begin : INT64_MAX};
   const unsigned nck = (unsigned)(nckx_ + nckz_);
   const int pg = grid_for(B, 128);
   bool any_sym = false, any_nonsym = false;
@@ -1773,6 +1791,7 @@ int Solver::unscale_solution(int64_t p, double* x, double* sl, double* z, clr_in
     for (int64_t j = 0; j < n; ++j) x[j] = xu[j] * fx;
   for (int64_t r = 0; r < m; ++r) {
     const int64_t orig = pr.row_perm[r];
+    if (orig < 0) continue;  // auxiliary row of an expanded SOC
     if (sl) sl[orig] = su[r] * fs;
     if (z) z[orig] = zu[r] * fz;
   }

@@ -170,6 +170,17 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
     if (fam == CLR_PSD_TRI) cl.psd_end = (int64_t)cl.cones.size();
   }
   cl.psd_k = psd_k;
+  // ---- large SOCs in sparse form (Sec. 3.3): H = eta^2 (I + u u' - v v'), the
+  // rank-two part carried by two auxiliary KKT rows per cone, appended after
+  // every cone row (rows m .. m + 2L - 1; no caller row) ----
+  int64_t n_expanded = 0;
+  for (int64_t c = cl.soc_begin; c < cl.soc_end; ++c)
+    if (st.soc_expand_dim > 0 && cl.cones[c].dim >= st.soc_expand_dim) cl.cones[c].aux = m + 2 * n_expanded++;
+  cl.aux_begin = m;
+  cl.n_aux = 2 * n_expanded;
+  const int64_t mi = m + cl.n_aux;  // internal constraint rows
+  for (int64_t k = 0; k < cl.n_aux; ++k) hp.row_perm.push_back(-1);
+  hp.m = mi;
   cl.nu = 0;
   cl.kval_z = 0;
   for (Cone& c : cl.cones) {
@@ -177,22 +188,27 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
     switch (c.type) {
       case CLR_ZERO: cl.kval_z += c.dim; break;
       case CLR_NONNEG: cl.kval_z += c.dim; cl.nu += c.dim; break;
-      case CLR_SOC: cl.kval_z += packed(c.dim); cl.nu += 1; cl.soc_max_dim = std::max(cl.soc_max_dim, c.dim); break;
+      case CLR_SOC:
+        cl.kval_z += c.aux >= 0 ? 3 * c.dim : packed(c.dim);
+        cl.nu += 1;
+        cl.soc_max_dim = std::max(cl.soc_max_dim, c.dim);
+        break;
       case CLR_EXP: case CLR_POW: cl.kval_z += 6; cl.nu += 3; cl.symmetric_only = false; break;
       case CLR_PSD_TRI: cl.kval_z += packed(c.dim); cl.nu += psd_order_of(c.dim); break;
     }
   }
+  cl.kval_z += cl.n_aux;  // the auxiliary rows' diagonals
 
   // ---- reordered A as CSR (unscaled) and full P as CSR ----
   std::vector<int64_t> inv_row(m);
   for (int64_t r = 0; r < m; ++r) inv_row[hp.row_perm[r]] = r;
   Sparse& Ar = hp.A;
   Ar = Sparse();
-  Ar.nrows = m;
+  Ar.nrows = mi;  // the auxiliary rows are empty
   Ar.ncols = n;
-  Ar.ptr.assign(m + 1, 0);
+  Ar.ptr.assign(mi + 1, 0);
   for (int64_t p = 0; p < A->nnz; ++p) Ar.ptr[inv_row[A->rowind[p]] + 1]++;
-  for (int64_t r = 0; r < m; ++r) Ar.ptr[r + 1] += Ar.ptr[r];
+  for (int64_t r = 0; r < mi; ++r) Ar.ptr[r + 1] += Ar.ptr[r];
   Ar.idx.resize(A->nnz);
   Ar.val.resize(A->nnz);
   std::vector<int64_t> ar_src(A->nnz);  // caller index of each Ar entry
@@ -245,9 +261,9 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
 
   // ---- modified Ruiz equilibration (reading of Alg. 1 step 1) ----
   hp.D.assign(n, 1.0);
-  hp.E.assign(m, 1.0);
+  hp.E.assign(mi, 1.0);
   hp.c = 1.0;
-  std::vector<double> colx(n), rowz(m);
+  std::vector<double> colx(n), rowz(mi);
   if (st.equilibrate) {
     for (int pass = 0; pass < st.ruiz_passes; ++pass) {
       std::fill(colx.begin(), colx.end(), 0.0);
@@ -257,7 +273,7 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
           double v = std::fabs(hp.D[i] * Pf.val[p] * hp.D[Pf.idx[p]]);
           colx[i] = std::max(colx[i], v);
         }
-      for (int64_t r = 0; r < m; ++r)
+      for (int64_t r = 0; r < mi; ++r)
         for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) {
           int64_t j = Ar.idx[p];
           double v = std::fabs(hp.E[r] * Ar.val[p] * hp.D[j]);
@@ -272,7 +288,7 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
       }
       for (int64_t j = 0; j < n; ++j)
         hp.D[j] = std::min(std::max(hp.D[j] * scale_factor(colx[j], st), st.scale_min), st.scale_max);
-      for (int64_t r = 0; r < m; ++r)
+      for (int64_t r = 0; r < mi; ++r)
         hp.E[r] = std::min(std::max(hp.E[r] * scale_factor(rowz[r], st), st.scale_min), st.scale_max);
     }
     // cost scaling
@@ -296,12 +312,12 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
       Pf.val[p] *= hp.c * hp.D[i] * hp.D[Pf.idx[p]];
       if (Pf.idx[p] == i) hp.maxPdiag = std::max(hp.maxPdiag, std::fabs(Pf.val[p]));
     }
-  for (int64_t r = 0; r < m; ++r)
+  for (int64_t r = 0; r < mi; ++r)
     for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) Ar.val[p] *= hp.E[r] * hp.D[Ar.idx[p]];
   Sparse& At = hp.At;
   At = Sparse();
   At.nrows = n;
-  At.ncols = m;
+  At.ncols = mi;
   At.ptr.assign(n + 1, 0);
   for (int64_t p = 0; p < Ar.nnz(); ++p) At.ptr[Ar.idx[p] + 1]++;
   for (int64_t j = 0; j < n; ++j) At.ptr[j + 1] += At.ptr[j];
@@ -310,7 +326,7 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
   std::vector<int64_t> at_src(Ar.nnz());  // caller index of each At entry
   {
     std::vector<int64_t> next(At.ptr.begin(), At.ptr.end() - 1);
-    for (int64_t r = 0; r < m; ++r)
+    for (int64_t r = 0; r < mi; ++r)
       for (int64_t p = Ar.ptr[r]; p < Ar.ptr[r + 1]; ++p) {
         int64_t j = Ar.idx[p];
         At.idx[next[j]] = (int32_t)r;
@@ -323,8 +339,10 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
 
   // ---- KKT lower triangle (CSC over KKT indices) and the kval layout ----
   // x column j: P(i, j) for i >= j with an explicit diagonal, then A(:, j) as rows n + r.
-  // z block of each cone: packed lower triangle of its H block (column-major).
-  const int64_t N = n + m;
+  // z block of each cone: packed lower triangle of its H block (column-major);
+  // an expanded SOC: per column its diagonal and its two auxiliary rows; the
+  // auxiliary columns: their diagonal (+1 for p, -1 for q; constant).
+  const int64_t N = n + mi;
   // value-update maps: equilibration factor of each caller value, P's diagonal
   hp.nnzP = P->nnz;
   hp.nnzA = A->nnz;
@@ -374,9 +392,8 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
   }
   hp.kval_x = (int64_t)hp.kval.size();
   // z columns: for each cone, columns off..off+dim-1; column c of a dense block has rows c..dim-1
-  int64_t zcol = n;
   for (const Cone& c : cl.cones) {
-    bool dense = (c.type != CLR_ZERO && c.type != CLR_NONNEG);
+    const bool dense = (c.type != CLR_ZERO && c.type != CLR_NONNEG && c.aux < 0);
     for (int64_t a = 0; a < c.dim; ++a) {
       const int64_t col = n + c.off + a;
       hp.kdiag[col] = (int64_t)hp.kval.size();
@@ -385,18 +402,29 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
         hp.krow.push_back(n + c.off + r);
         hp.kval.push_back(0.0);
       }
+      if (c.aux >= 0)
+        for (int64_t t = 0; t < 2; ++t) {  // eta u_a, eta v_a (written by the scaling)
+          hp.krow.push_back(n + c.aux + t);
+          hp.kval.push_back(0.0);
+        }
       hp.kcol_ptr[col + 1] = (int64_t)hp.kval.size();
-      ++zcol;
     }
   }
-  (void)zcol;
+  for (int64_t k = 0; k < cl.n_aux; ++k) {
+    const int64_t col = n + cl.aux_begin + k;
+    hp.kdiag[col] = (int64_t)hp.kval.size();
+    hp.krow.push_back(col);
+    hp.kval.push_back((k % 2 == 0) ? 1.0 : -1.0);
+    hp.kcol_ptr[col + 1] = (int64_t)hp.kval.size();
+  }
   return CLR_OK;
 }
 
 // q, b in the caller's order -> scaled, reordered copies and unscaled norms.
 int set_qb(HostProblem& hp, const double* q, const double* b) {
-  if ((hp.n && !q) || (hp.m && !b)) return CLR_E_INVALID;
-  if (!finite_all(q, hp.n) || !finite_all(b, hp.m)) return CLR_E_INVALID;
+  const int64_t m_caller = hp.m - hp.cl.n_aux;  // b has the caller's rows only
+  if ((hp.n && !q) || (m_caller && !b)) return CLR_E_INVALID;
+  if (!finite_all(q, hp.n) || !finite_all(b, m_caller)) return CLR_E_INVALID;
   hp.q.resize(hp.n);
   hp.b.resize(hp.m);
   hp.qnorm = 0.0;
@@ -406,7 +434,7 @@ int set_qb(HostProblem& hp, const double* q, const double* b) {
     hp.qnorm = std::max(hp.qnorm, std::fabs(q[j]));
   }
   for (int64_t r = 0; r < hp.m; ++r) {
-    double v = b[hp.row_perm[r]];
+    const double v = hp.row_perm[r] >= 0 ? b[hp.row_perm[r]] : 0.0;  // auxiliary rows: b = 0
     hp.b[r] = hp.E[r] * v;
     hp.bnorm = std::max(hp.bnorm, std::fabs(v));
   }

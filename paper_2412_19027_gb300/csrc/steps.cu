@@ -74,6 +74,7 @@ struct ConeBench {
           soc_off.push_back((int64_t)perm.size());
           soc_dim.push_back((int32_t)d);
           cd.soc_dmax = std::max<int>(cd.soc_dmax, (int)d);
+          if (d <= 8) cd.soc_nsmall++;  // a thread per cone
           soc_kb.push_back(kz);
         }
         if (f == CLR_POW) alpha.push_back(cones[i].alpha);
@@ -90,6 +91,7 @@ struct ConeBench {
     cd.m_zero = mz;
     cd.m_nonneg = mn;
     cd.n_soc = counts[CLR_SOC];
+    cd.soc_split = (cd.soc_nsmall > 0 && cd.soc_nsmall < cd.n_soc) ? 1 : 0;
     cd.soc_off = ar.upload(soc_off.data(), (int64_t)soc_off.size());
     cd.soc_dim = ar.upload(soc_dim.data(), (int64_t)soc_dim.size());
     cd.soc_kb = ar.upload(soc_kb.data(), (int64_t)soc_kb.size());

@@ -163,9 +163,11 @@ void kkt_factor_counts(int64_t N, const std::vector<int64_t>& colptr, const std:
 //   0  AMD on the whole KKT pattern;
 //   1  the constraint rows with a nonzero H block (nonnegative and cone rows)
 //      first, in row order -- H is block diagonal, so they cause no fill among
-//      themselves -- then x and the zero-cone rows in the AMD order of their
-//      Schur-complement pattern (K restricted to them, plus one clique per H
-//      block over the x columns its rows touch).
+//      themselves -- then x, the zero-cone rows and the auxiliary rows of the
+//      expanded SOCs in the AMD order of their Schur-complement pattern (K
+//      restricted to them, plus one clique per H block over the x columns its
+//      rows touch; an expanded SOC's rows are 1 x 1 blocks whose cliques also
+//      hold the cone's two auxiliary rows).
 // AMD alone eliminates the low-degree x columns of a sparse random A first and
 // fills the whole constraint block; candidate 1 leaves a dense x block instead.
 int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t& n_dense, int* which) {
@@ -174,17 +176,21 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
   build_adjacency(N, hp.kcol_ptr, hp.krow, aptr, aidx);
   amd_order(N, aptr, aidx, order, n_dense);
   *which = 0;
-  const int64_t mz = hp.cl.m_zero;
-  if (m - mz <= 0 || n == 0) return CLR_OK;
-  // Schur pattern on R = x u zero rows (local ids: x j -> j, zero row r -> n + r)
-  const int64_t R = n + mz;
+  const int64_t mz = hp.cl.m_zero, ab = hp.cl.n_aux ? hp.cl.aux_begin : m, na = hp.cl.n_aux;
+  if (ab - mz <= 0 || n == 0) return CLR_OK;
+  // Schur pattern on R = x u zero rows u auxiliary rows (local ids: x j -> j, zero
+  // row r -> n + r, auxiliary row r -> n + mz + (r - ab))
+  const int64_t R = n + mz + na;
+  auto local = [&](int64_t u) -> int64_t {
+    if (u < n || u - n < mz) return u;
+    return (u - n >= ab) ? n + mz + (u - n - ab) : -1;
+  };
   std::vector<std::vector<int64_t>> adj(R);
   for (int64_t u = 0; u < N; ++u) {
-    const int64_t lu = u < n ? u : (u - n < mz ? u : -1);
+    const int64_t lu = local(u);
     if (lu < 0) continue;
     for (int64_t p = aptr[u]; p < aptr[u + 1]; ++p) {
-      const int64_t v = aidx[p];
-      const int64_t lv = v < n ? v : (v - n < mz ? v : -1);
+      const int64_t lv = local(aidx[p]);
       if (lv >= 0) adj[lu].push_back(lv);
     }
   }
@@ -196,10 +202,15 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
   for (size_t ci = 0; ci < hp.cl.cones.size(); ++ci) {
     const Cone& c = hp.cl.cones[ci];
     if (c.type == CLR_ZERO) continue;
-    const bool rowwise = c.type == CLR_NONNEG;  // each nonneg row is its own 1x1 block
+    // each nonneg row, and each row of an expanded SOC, is its own 1x1 block
+    const bool rowwise = c.type == CLR_NONNEG || c.aux >= 0;
     const int64_t nblk = rowwise ? c.dim : 1, bdim = rowwise ? 1 : c.dim;
     for (int64_t bk = 0; bk < nblk; ++bk) {
       nb.clear();
+      if (c.aux >= 0) {  // the block's two auxiliary rows join its clique
+        nb.push_back(n + mz + (c.aux - ab));
+        nb.push_back(n + mz + (c.aux + 1 - ab));
+      }
       const int64_t tag = (int64_t)ci * (1LL << 32) + bk;
       for (int64_t r = c.off + bk * bdim; r < c.off + (bk + 1) * bdim; ++r)
         for (int64_t p = hp.A.ptr[r]; p < hp.A.ptr[r + 1]; ++p) {
@@ -233,8 +244,8 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
   amd_order(R, sptr, sidx, rperm, nd1);
   std::vector<int64_t> cand;
   cand.reserve(N);
-  for (int64_t r = mz; r < m; ++r) cand.push_back(n + r);
-  for (int64_t v : rperm) cand.push_back(v);  // local ids equal KKT indices for x and zero rows
+  for (int64_t r = mz; r < ab; ++r) cand.push_back(n + r);
+  for (int64_t v : rperm) cand.push_back(v < n + mz ? v : n + ab + (v - n - mz));  // local ids -> KKT indices
   int64_t nz0 = 0, nz1 = 0;
   double f0 = 0, f1 = 0;
   factor_counts(N, aptr, aidx, order, &nz0, &f0);

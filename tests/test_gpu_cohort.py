@@ -52,6 +52,9 @@ def _mixed_cohort():
         _infeasible_lp(),
         W.nonneg_qp(3),
         W.mixed_cone(2, n=200, n_zero=50, n_nonneg=300, n_soc=50, n_exp=10, n_pow=10, nnz_per_col=6),
+        # SOCs of 50 and 40 rows in the sparse KKT form (two auxiliary rows each)
+        W.mixed_cone(5, n=80, n_zero=10, n_nonneg=60, n_soc=2, soc_dim=50, n_exp=2, n_pow=2, nnz_per_col=5),
+        W.mixed_cone(6, n=60, n_zero=6, n_nonneg=40, n_soc=3, soc_dim=40, n_exp=0, n_pow=0, nnz_per_col=5),
     ]
 
 

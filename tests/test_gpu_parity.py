@@ -422,6 +422,42 @@ def test_cone_stress_inputs_and_timing(family, count):
         assert 0.0 < t[k] < 1e3, t
 
 
+@pytest.mark.parametrize("soc_dim,n_soc,n_exp,bits", [(100, 3, 0, 64), (1000, 1, 0, 64), (100, 3, 4, 64),
+                                                     (100, 3, 0, 32)])
+def test_large_soc_sparse_form_matches_oracle(soc_dim, n_soc, n_exp, bits):
+    """SOCs of 100 and 1000 rows in the sparse KKT form (Sec. 3.3: H = eta^2 (I + u u' - v v'),
+    two auxiliary KKT rows per cone) against the oracle, whose KKT matrix holds each cone's
+    dense H: status, objective, iterations and the host-recomputed termination test; with
+    exp/pow cones too (the unit initial point) and with the FP32 factor."""
+    prob = W.mixed_cone(4 + soc_dim, n=200, n_zero=20, n_nonneg=150, n_soc=n_soc, soc_dim=soc_dim, n_exp=n_exp,
+                        n_pow=n_exp, nnz_per_col=6)
+    _compare_solve(prob, bits, iters_tol=2 if bits == 64 else 4)
+
+
+def test_large_soc_sparse_and_dense_forms_agree():
+    """The same problem with its SOCs of 60 rows in the sparse KKT form (soc_expand_dim 33,
+    the default) and as dense H blocks (0): two more KKT rows per cone, the same answer."""
+    prob = W.mixed_cone(9, n=150, n_zero=10, n_nonneg=100, n_soc=2, soc_dim=60, n_exp=3, n_pow=3, nnz_per_col=6)
+    out = {}
+    for dim in (33, 0):
+        st = clr.clr_default_settings(64, soc_expand_dim=dim)
+        sv = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+        sv.solve()
+        x, sl, z, info = sv.solution()
+        out[dim] = (x, sl, z, info, sv.symbolic_stats())
+        sv.free()
+    (xe, se, ze, ie, ste), (xd, sd, zd, idn, std_) = out[33], out[0]
+    assert ste["kkt_dim"] == std_["kkt_dim"] + 4 and ste["m"] == std_["m"] + 4
+    assert ie["status_name"] == idn["status_name"] == "SOLVED", (ie, idn)
+    assert abs(ie["iterations"] - idn["iterations"]) <= 1
+    fe, fd = prob.objective(xe), prob.objective(xd)
+    assert abs(fe - fd) <= 1e-7 * max(1.0, abs(fd)), (fe, fd)
+    scale = max(1.0, np.abs(xd).max())
+    np.testing.assert_allclose(xe, xd, atol=1e-6 * scale)  # P positive definite: x is unique
+    np.testing.assert_allclose(se, sd, atol=1e-6 * max(1.0, np.abs(sd).max()))
+    assert len(ze) == len(zd) == prob.A.shape[0]
+
+
 def test_psd_mixed_orders_solve_matches_oracle():
     """PSD cones of orders 2 .. 16 in one problem (the future direction of Sec. 6):
     status, objective and iterations as the oracle's."""

@@ -273,6 +273,25 @@ def test_blocking_settings_validated_and_applied(clr):
     assert stats[2]["l_nnz"] >= stats[1]["l_nnz"] >= stats[0]["l_nnz"]
 
 
+def test_large_soc_sparse_form_layout(clr):
+    """SOCs of at least soc_expand_dim rows enter the KKT matrix in sparse form: two
+    auxiliary rows each (kkt_dim and m grow by 2 per cone), 3 values per cone row instead
+    of a packed d x d block; 0 keeps every SOC dense; a negative value is refused."""
+    p = W.mixed_cone(3, n=80, n_zero=10, n_nonneg=40, n_soc=3, soc_dim=50, n_exp=0, n_pow=0, nnz_per_col=5)
+    m = p.A.shape[0]
+    with pytest.raises(clr.ClrError):
+        clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, soc_expand_dim=-1))
+    stats = {}
+    for dim in (0, 33, 51):
+        s = clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, soc_expand_dim=dim))
+        stats[dim] = s.symbolic_stats()
+        s.free()
+    assert stats[0]["m"] == stats[51]["m"] == m and stats[0]["kkt_dim"] == 80 + m
+    assert stats[33]["m"] == m + 6 and stats[33]["kkt_dim"] == 80 + m + 6
+    # dense: 3 packed 50 x 50 blocks; sparse: 3 x 50 x 3 values plus 6 auxiliary diagonals
+    assert stats[0]["kkt_nnz_lower"] - stats[33]["kkt_nnz_lower"] == 3 * (50 * 51 // 2) - (3 * 50 * 3 + 6)
+
+
 def test_update_PA_validation(clr):
     """clr_update_PA on a host-analysed solver: values on the setup's patterns are
     accepted (as a matrix of that pattern or as a CSC-ordered array), a changed
