@@ -132,10 +132,12 @@ typedef struct {
                                  than escalate_ratio times the largest entry of the iterate's scaled residual G
                                  while the primal or dual residual is still more than 100 times its termination
                                  tolerance (the direction is then too inexact to reduce it); default 0.1, 0 = off */
-  int32_t soc_expand_dim;     /* second-order cones of at least this many rows enter the KKT matrix in sparse
-                                 form (Sec. 3.3: H = eta^2 (I + u u' - v v') as its diagonal plus two extra
-                                 rows and columns per cone, [-eta^2 I, eta u, eta v; eta u', 1, 0;
-                                 eta v', 0, -1]) instead of a dense d x d block; default 33, 0 = never */
+  int32_t soc_expand_dim;     /* second-order cones of at least this many rows (Sec. 3.3 names cones of
+                                 thousands of rows, multistage portfolios) enter the KKT matrix in sparse
+                                 form -- H = eta^2 (I + u u' - v v') as its diagonal plus two extra rows and
+                                 columns per cone, [-eta^2 I, eta u, eta v; eta u', 1, 0; eta v', 0, -1] --
+                                 instead of a dense d x d block (not in the paper, which factors with
+                                 cuDSS); default 33, 0 = never */
 } clr_settings;
 
 typedef struct {

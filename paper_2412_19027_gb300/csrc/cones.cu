@@ -371,7 +371,8 @@ __global__ void k_scale_soc(ConeDev cd, const double* __restrict__ s, const doub
     double mx = 0.0;
     const int64_t aux = (valid && cd.soc_aux) ? cd.soc_aux[cone] : -1;  // uniform over the group
     if (aux >= 0) {
-      // sparse form (the large-SOC expansion of Sec. 3.3): 2 wb wb' - J = I + 2 (wb wb' - e0 e0'),
+      // sparse form of a large SOC (Sec. 3.3 names cones of thousands of rows, whose dense H
+      // block would hold d (d + 1) / 2 KKT values): 2 wb wb' - J = I + 2 (wb wb' - e0 e0'),
       // and the rank-two part has, in the basis e0, w^ = (0, wb_1) / r (r = ||wb_1||, wb0^2 - r^2 = 1),
       // the matrix 2 [r^2, wb0 r; wb0 r, r^2]: eigenvectors (e0 +- w^) / sqrt 2, eigenvalues
       // 2 r (r +- wb0).  So H = eta^2 (I + u u' - v v') with u = sqrt(r (r + wb0)) (e0 + w^) and

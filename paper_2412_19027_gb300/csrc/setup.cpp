@@ -170,7 +170,7 @@ int build_problem(HostProblem& hp, const clr_csc* P, const double* q, const clr_
     if (fam == CLR_PSD_TRI) cl.psd_end = (int64_t)cl.cones.size();
   }
   cl.psd_k = psd_k;
-  // ---- large SOCs in sparse form (Sec. 3.3): H = eta^2 (I + u u' - v v'), the
+  // ---- large SOCs (Sec. 3.3: thousands of rows) in sparse form: H = eta^2 (I + u u' - v v'), the
   // rank-two part carried by two auxiliary KKT rows per cone, appended after
   // every cone row (rows m .. m + 2L - 1; no caller row) ----
   int64_t n_expanded = 0;

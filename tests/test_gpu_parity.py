@@ -425,8 +425,9 @@ def test_cone_stress_inputs_and_timing(family, count):
 @pytest.mark.parametrize("soc_dim,n_soc,n_exp,bits", [(100, 3, 0, 64), (1000, 1, 0, 64), (100, 3, 4, 64),
                                                      (100, 3, 0, 32)])
 def test_large_soc_sparse_form_matches_oracle(soc_dim, n_soc, n_exp, bits):
-    """SOCs of 100 and 1000 rows in the sparse KKT form (Sec. 3.3: H = eta^2 (I + u u' - v v'),
-    two auxiliary KKT rows per cone) against the oracle, whose KKT matrix holds each cone's
+    """SOCs of 100 and 1000 rows (Sec. 3.3 names cones of thousands of rows) in the sparse KKT
+    form (H = eta^2 (I + u u' - v v'), two auxiliary KKT rows per cone) against the oracle, whose
+    KKT matrix holds each cone's
     dense H: status, objective, iterations and the host-recomputed termination test; with
     exp/pow cones too (the unit initial point) and with the FP32 factor."""
     prob = W.mixed_cone(4 + soc_dim, n=200, n_zero=20, n_nonneg=150, n_soc=n_soc, soc_dim=soc_dim, n_exp=n_exp,
