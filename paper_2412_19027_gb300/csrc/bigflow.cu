@@ -221,6 +221,22 @@ constexpr size_t kTcSmemFlow = 2 * (size_t)kTcOpBytes + 2 * (size_t)kTcPkBytes +
 constexpr uint32_t kTf32Idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(64 >> 3) << 17) |
                                 ((uint32_t)(128 >> 4) << 24);
 
+// two consecutive rows r, r + 1 (r even) of K-row k of a K-major tile
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T (&v)[2]);
+template <>
+__device__ __forceinline__ void ld2<float>(const float* p, float (&v)[2]) {
+  const float2 a = *reinterpret_cast<const float2*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+}
+template <>
+__device__ __forceinline__ void ld2<double>(const double* p, double (&v)[2]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+}
+
 // D(p): LDL^T of the pw x pw diagonal block with dynamic regularisation (see
 // bfdiag.cuh); L and the pivots written back, Linv = L_KK^{-1} written into
 // E_KK, which it equals (the zeros above its diagonal are the E pool's).
@@ -273,32 +289,43 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     }
   }
   __syncthreads();
-  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3.  Linv is unit lower
-  // triangular, so columns 4 tc .. need only l <= 4 tc + 3 (the terms skipped are
-  // exact zeros); warp w takes column blocks w and 15 - w, which balances them
-  const int tr = tid % 16, tcw = tid / 16, tc = (tcw & 1) ? 15 - (tcw >> 1) : (tcw >> 1);
-  T acc[4][4];
+  // L_{p,p-1} = F_{p,p-1} Linv^T D^{-1} (divided by the pivots, as the separate panel-row
+  // task T divides).  Linv is unit lower triangular, so column
+  // block tc needs only l <= 4 tc + 3 (the terms skipped are exact zeros).  A warp
+  // instruction holds an FP64 sub-partition pipe as long whatever its active lanes,
+  // so the work is split evenly over the warps with one trip count per warp: warp w
+  // takes column blocks w and 15 - w, each lane the rows 2 lane, 2 lane + 1.
+  const int wid = tid >> 5, lane = tid & 31;
+  T acc[2][2][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int ph = 0; ph < 2; ++ph) {
+    const int tc = ph == 0 ? wid : 15 - wid;
 #pragma unroll
-    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
-  for (int l = 0; l < 4 * tc + 4; ++l) {
-    T av[4], bv[4];
-    ld4<T>(Xk + swz(l, 4 * tr), av);
-    ld4<T>(Bk + swz(l, 4 * tc), bv);
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int bb = 0; bb < 4; ++bb) acc[ph][a][bb] = (T)0;
+    for (int l = 0; l < 4 * tc + 4; ++l) {
+      T av[2], bv[4];
+      ld2<T>(Xk + swz(l, 2 * lane), av);
+      ld4<T>(Bk + swz(l, 4 * tc), bv);
 #pragma unroll
-      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) acc[ph][a][bb] += av[a] * bv[bb];
+    }
   }
   __syncthreads();  // every thread has read F_{p,p-1}
 #pragma unroll
-  for (int bb = 0; bb < 4; ++bb) {
-    const int j = 4 * tc + bb;
+  for (int ph = 0; ph < 2; ++ph) {
+    const int tc = ph == 0 ? wid : 15 - wid;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = 4 * tr + a;
-      Xk[swz(j, i)] = (i < pw) ? acc[a][bb] / dl[j] : (T)0;
+    for (int bb = 0; bb < 4; ++bb) {
+      const int j = 4 * tc + bb;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * lane + a;
+        Xk[swz(j, i)] = (i < pw) ? acc[ph][a][bb] / dl[j] : (T)0;
+      }
     }
   }
   __syncthreads();
@@ -316,37 +343,48 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     __threadfence();
     st_release(trsm_word, p);
   }
-  // A_ij -= sum_l L_il (L_jl d_l), i >= j: only the 136 4 x 4 blocks on or below
-  // the diagonal, one per thread (threads 136 .. 255 idle), each summed in the
-  // same order as a full-tile product would
-  if (tid < 136) {
-    int lr = 0;
-    while ((lr + 1) * (lr + 2) / 2 <= tid) ++lr;  // block row; tid = lr (lr + 1) / 2 + lc
-    const int lc = tid - lr * (lr + 1) / 2;
+  // A_ij -= sum_l L_il (L_jl d_l), i >= j: the 528 2 x 2 blocks on or below the
+  // diagonal, blocks t, t + 256 and t + 512 on thread t (even FP64 work per warp),
+  // each summed in the order of a full-tile product
+  {
+    T acc2[3][2][2];
+    int rp[3], cp[3];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 3; ++q) {
+      const int blk = tid + NT * q;
+      int r = 0;
+      while (blk < 528 && (r + 1) * (r + 2) / 2 <= blk) ++r;  // blk = r (r + 1) / 2 + c
+      rp[q] = blk < 528 ? r : -1;
+      cp[q] = blk < 528 ? blk - r * (r + 1) / 2 : 0;
 #pragma unroll
-      for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
+      for (int a = 0; a < 2; ++a) acc2[q][a][0] = acc2[q][a][1] = (T)0;
+    }
     for (int l = 0; l < NB; ++l) {
-      T av[4], bv[4];
-      ld4<T>(Xk + swz(l, 4 * lr), av);
-      ld4<T>(Xk + swz(l, 4 * lc), bv);
       const T dlv = dl[l];
 #pragma unroll
-      for (int bb = 0; bb < 4; ++bb) bv[bb] *= dlv;
+      for (int q = 0; q < 3; ++q) {
+        if (rp[q] < 0) continue;
+        T av[2], bv[2];
+        ld2<T>(Xk + swz(l, 2 * rp[q]), av);
+        ld2<T>(Xk + swz(l, 2 * cp[q]), bv);
+        bv[0] *= dlv;
+        bv[1] *= dlv;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+          for (int bb = 0; bb < 2; ++bb) acc2[q][a][bb] += av[a] * bv[bb];
+      }
     }
 #pragma unroll
-    for (int bb = 0; bb < 4; ++bb) {
-      const int j = 4 * lc + bb;
+    for (int q = 0; q < 3; ++q) {
+      if (rp[q] < 0) continue;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = 4 * lr + a;
-        if (i < pw && i >= j) A[i * LD + j] -= acc[a][bb];
-      }
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+          const int i = 2 * rp[q] + a, j = 2 * cp[q] + bb;
+          if (i < pw && i >= j) A[i * LD + j] -= acc2[q][a][bb];
+        }
     }
   }
   __syncthreads();
@@ -388,32 +426,40 @@ __device__ void task_trsm(const BigFrontDev& bf, int64_t b, const Geo& g, int p,
     }
   }
   __syncthreads();
-  // rows 4 tr .. 4 tr + 3, columns 4 tc .. 4 tc + 3; Linv lower triangular: only
-  // l <= 4 tc + 3 (as in the fused chain task)
-  const int tr = tid % 16, tcw = tid / 16, tc = (tcw & 1) ? 15 - (tcw >> 1) : (tcw >> 1);
-  T acc[4][4];
+  // the product of the fused chain task: warp w, column blocks w and 15 - w, rows
+  // 2 lane, 2 lane + 1; Linv lower triangular: only l <= 4 tc + 3
+  const int wid = tid >> 5, lane = tid & 31;
+  T acc[2][2][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int ph = 0; ph < 2; ++ph) {
+    const int tc = ph == 0 ? wid : 15 - wid;
 #pragma unroll
-    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
-  const int lend = min(pw, 4 * tc + 4);
-  for (int l = 0; l < lend; ++l) {
-    T av[4], bv[4];
-    ld4<T>(Xk + swz(l, 4 * tr), av);
-    ld4<T>(Bk + swz(l, 4 * tc), bv);
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int bb = 0; bb < 4; ++bb) acc[ph][a][bb] = (T)0;
+    const int lend = min(pw, 4 * tc + 4);
+    for (int l = 0; l < lend; ++l) {
+      T av[2], bv[4];
+      ld2<T>(Xk + swz(l, 2 * lane), av);
+      ld4<T>(Bk + swz(l, 4 * tc), bv);
 #pragma unroll
-      for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) acc[ph][a][bb] += av[a] * bv[bb];
+    }
   }
   __syncthreads();  // every thread has read F_IK
 #pragma unroll
-  for (int bb = 0; bb < 4; ++bb) {
-    const int j = 4 * tc + bb;
+  for (int ph = 0; ph < 2; ++ph) {
+    const int tc = ph == 0 ? wid : 15 - wid;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = 4 * tr + a;
-      if (j < pw) Xk[swz(j, i)] = acc[a][bb] / dl[j];
+    for (int bb = 0; bb < 4; ++bb) {
+      const int j = 4 * tc + bb;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * lane + a;
+        if (j < pw) Xk[swz(j, i)] = acc[ph][a][bb] / dl[j];
+      }
     }
   }
   __syncthreads();

@@ -61,6 +61,26 @@ def test_entropy_accuracy_reached():
     assert abs(xe.sum() - 1.0) < 1e-6
 
 
+@pytest.mark.parametrize("bits", [64, 32])
+@pytest.mark.parametrize("n", [20, 60])
+def test_entropy_solved_at_the_papers_tolerance(n, bits):
+    """Entropy maximisation at the tolerance the paper runs its benchmark classes at
+    (eps_feas = eps_inf = 1e-6): SOLVED on both sides, objective to 1e-6 relative,
+    iterations within 2 (4 with the FP32 factor)."""
+    prob = W.entropy_max(2, n=n)
+    st = clr.clr_default_settings(bits, eps_feas=1e-6, eps_inf=1e-6)
+    s = clr.clr_setup(prob.P, prob.q, prob.A, prob.b, prob.cones, st)
+    s.solve()
+    x, sl, z, info = s.solution()
+    s.free()
+    ref = oracle.solve(prob.P, prob.q, prob.A, prob.b, prob.cones, settings=dict(eps_feas=1e-6, eps_inf=1e-6))
+    assert info["status_name"] == ref["status_name"] == "SOLVED", (info, ref["status_name"])
+    f, fr = _objective(prob, x), _objective(prob, ref["x"])
+    assert abs(f - fr) <= 1e-6 * max(1.0, abs(fr)), (f, fr)
+    assert abs(info["iterations"] - ref["iterations"]) <= (2 if bits == 64 else 4), (info["iterations"],
+                                                                                      ref["iterations"])
+
+
 @pytest.mark.xfail(reason="entropy maximisation: every cone active at the optimum; the 1e-8 gap may not be reached",
                    strict=False)
 def test_entropy_solved():
