@@ -84,6 +84,21 @@ def cone_bytes(family, k):
             "ds": 8 * (4 * d + 2 * kk * kk + kk)}
 
 
+# FP64 flops per unit of each cone step, counted from the kernel sources (an FMA as
+# 2 flops, a square root or a division as 1, which favours the kernels: on a GB300
+# they cost several FMA slots each).  nonneg: lambda = sqrt(s z), w = s / lambda,
+# H = w^2; step: two ratios; d_s: the Jordan product, quotient and scaling.  SOC(5):
+# J-norms, gamma, eta, w-bar, lambda and the 15 packed H entries; step: both
+# quadratic root tests; d_s: W^{-1} ds_a, W dz_a, their Jordan product, the
+# quotient by lambda, W.  PSD(10): two 10 x 10 Cholesky factors, L_z^T L_s,
+# a one-sided Jacobi SVD (about 6 sweeps), R, R^{-1} and the 55 x 55 packed H;
+# step: per side a Cholesky, two triangular solves and a two-sided Jacobi
+# eigenvalue sweep set (about 8 sweeps); d_s: congruences with R, R^{-1}.
+CONE_FP64_FLOPS = {"nonneg": {"scaling": 4, "step": 4, "ds": 8},
+                   "soc": {"scaling": 150, "step": 80, "ds": 100},
+                   "psd": {"scaling": 30_000, "step": 110_000, "ds": 8_000}}
+
+
 def run_cone_roofline(clr, W, peaks, reps=10, shift=0):
     out = {}
     for fam, count, d in CONE_STRESS:
@@ -98,6 +113,11 @@ def run_cone_roofline(clr, W, peaks, reps=10, shift=0):
             gbs = b[step] * count / (ms / 1e3) / 1e9
             row[step] = {"ms": ms, "bytes_per_unit": b[step], "achieved_gbs": gbs,
                          "frac": gbs / peaks["hbm_gbs"]}
+            if peaks.get("fp64_tflops"):
+                fl = CONE_FP64_FLOPS[fam][step]
+                tf = fl * count / (ms / 1e3) / 1e12
+                row[step].update({"fp64_flops_per_unit": fl, "achieved_fp64_tflops": tf,
+                                  "frac_fp64": tf / peaks["fp64_tflops"]})
         out[fam] = row
     out["peak_gbs"] = peaks["hbm_gbs"]
     out["peak_source"] = peaks["source"] + " HBM copy"
@@ -769,7 +789,10 @@ def run_ours(args):
 
     cone_roof = None
     if not args.no_cone_roofline and rank == 0:
-        cone_roof = run_cone_roofline(clr, W, {"hbm_gbs": peaks["hbm_gbs"], "source": copy_peaks["source"]})
+        cone_roof = run_cone_roofline(clr, W, {"hbm_gbs": peaks["hbm_gbs"], "source": copy_peaks["source"],
+                                               "fp64_tflops": peaks["fp64_fma_tflops"]})
+        cone_roof["fp64_peak_tflops"] = peaks["fp64_fma_tflops"]
+        cone_roof["fp64_peak_source"] = "measured FP64 FMA (library probe)"
 
     serving = None
     if not args.no_serving:

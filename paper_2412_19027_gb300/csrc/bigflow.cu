@@ -343,48 +343,38 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
     __threadfence();
     st_release(trsm_word, p);
   }
-  // A_ij -= sum_l L_il (L_jl d_l), i >= j: the 528 2 x 2 blocks on or below the
-  // diagonal, blocks t, t + 256 and t + 512 on thread t (even FP64 work per warp),
-  // each summed in the order of a full-tile product
-  {
-    T acc2[3][2][2];
-    int rp[3], cp[3];
+  // A_ij -= sum_l L_il (L_jl d_l), i >= j: only the 136 4 x 4 blocks on or below
+  // the diagonal, one per thread (threads 136 .. 255 idle), each summed in the
+  // same order as a full-tile product would
+  if (tid < 136) {
+    int lr = 0;
+    while ((lr + 1) * (lr + 2) / 2 <= tid) ++lr;  // block row; tid = lr (lr + 1) / 2 + lc
+    const int lc = tid - lr * (lr + 1) / 2;
+    T acc[4][4];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int blk = tid + NT * q;
-      int r = 0;
-      while (blk < 528 && (r + 1) * (r + 2) / 2 <= blk) ++r;  // blk = r (r + 1) / 2 + c
-      rp[q] = blk < 528 ? r : -1;
-      cp[q] = blk < 528 ? blk - r * (r + 1) / 2 : 0;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int a = 0; a < 2; ++a) acc2[q][a][0] = acc2[q][a][1] = (T)0;
-    }
+      for (int bb = 0; bb < 4; ++bb) acc[a][bb] = (T)0;
     for (int l = 0; l < NB; ++l) {
+      T av[4], bv[4];
+      ld4<T>(Xk + swz(l, 4 * lr), av);
+      ld4<T>(Xk + swz(l, 4 * lc), bv);
       const T dlv = dl[l];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (rp[q] < 0) continue;
-        T av[2], bv[2];
-        ld2<T>(Xk + swz(l, 2 * rp[q]), av);
-        ld2<T>(Xk + swz(l, 2 * cp[q]), bv);
-        bv[0] *= dlv;
-        bv[1] *= dlv;
+      for (int bb = 0; bb < 4; ++bb) bv[bb] *= dlv;
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int bb = 0; bb < 2; ++bb) acc2[q][a][bb] += av[a] * bv[bb];
-      }
+        for (int bb = 0; bb < 4; ++bb) acc[a][bb] += av[a] * bv[bb];
     }
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (rp[q] < 0) continue;
+    for (int bb = 0; bb < 4; ++bb) {
+      const int j = 4 * lc + bb;
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int bb = 0; bb < 2; ++bb) {
-          const int i = 2 * rp[q] + a, j = 2 * cp[q] + bb;
-          if (i < pw && i >= j) A[i * LD + j] -= acc2[q][a][bb];
-        }
+      for (int a = 0; a < 4; ++a) {
+        const int i = 4 * lr + a;
+        if (i < pw && i >= j) A[i * LD + j] -= acc[a][bb];
+      }
     }
   }
   __syncthreads();
