@@ -5,7 +5,8 @@ chosen complementary (x*, s*, z*)), a hand-solved LP, vertex enumeration and
 scipy's LP solver on tiny LPs, the full 4x4 Newton system solved densely,
 exact algebraic identities (gap identity, linear-row contraction),
 invariance under equilibration / cone order, the PSD(1) = nonneg special
-case, and the paper's printed constants.
+case, the paper's printed constants, and hand-solved cases of the
+equilibration (Ruiz passes, clamps, cone-block rule) and of the initial point.
 """
 import itertools
 import json
@@ -377,3 +378,70 @@ def test_unique_qp_solution_within_posterior_bound(seed, rank):
     assert np.all(np.abs(r.z - p.z_star) <= 2.0 * e_z + slack)
     # the bound is informative: far below the size of the solution
     assert e_x.max() < 1e-5 * max(1.0, np.abs(p.x_star).max())
+
+
+# ---------------------------------------------------------------- equilibration and initial point
+# Both are readings of silent passages (Alg. 1 steps 1-2 name them without a method);
+# these pins hold the oracle to the reading as stated, on cases solved by hand.
+
+def test_ruiz_equilibration_hand_case():
+    """A = diag(4, 1/4), P = 0, q = (1, 1): the first pass scales by 1/sqrt of the
+    column and row infinity norms, D = E = (1/2, 2), after which E A D = I and every
+    later pass keeps it; the cost scale is 1 / max(mean col norm of P^, ||D q||) = 1/2."""
+    st = ipm.default_settings()
+    A = np.diag([4.0, 0.25])
+    D, E, c = ipm.equilibrate(np.zeros((2, 2)), A, np.ones(2), [(C.NONNEG, 2, 0.0, 0)], st)
+    np.testing.assert_allclose(D, [0.5, 2.0], rtol=1e-15)
+    np.testing.assert_allclose(E, [0.5, 2.0], rtol=1e-15)
+    assert c == pytest.approx(0.5, rel=1e-15)
+
+
+def test_ruiz_equilibration_tiny_norm_and_clamp():
+    """A = [1e-12, 1e12] (one row), P = 0: a column of norm < 1e-8 is left alone;
+    1/sqrt(1e12) = 1e-6 is clamped to scale_min = 1e-4 for the other column and the
+    row, and the accumulated factors stay clamped at 1e-4 in every later pass;
+    ||D q|| = 1 gives c = 1."""
+    st = ipm.default_settings()
+    A = np.array([[1e-12, 1e12]])
+    D, E, c = ipm.equilibrate(np.zeros((2, 2)), A, np.ones(2), [(C.NONNEG, 1, 0.0, 0)], st)
+    np.testing.assert_allclose(D, [1.0, 1e-4], rtol=1e-15)
+    np.testing.assert_allclose(E, [1e-4], rtol=1e-15)
+    assert c == 1.0
+
+
+def test_ruiz_equilibration_cone_rows_share_one_factor():
+    """A = diag(4, 1, 1/4) as one SOC(3): after one pass D = (1/2, 1, 2) (the columns'
+    own norms) while all three rows take the factor of the cone's largest row norm,
+    E = (1/2, 1/2, 1/2), so the scaled rows still form a second-order cone; as three
+    nonnegative rows they would take (1/2, 1, 2)."""
+    st = dict(ipm.default_settings(), ruiz_passes=1)
+    A = np.diag([4.0, 1.0, 0.25])
+    D, E, _ = ipm.equilibrate(np.zeros((3, 3)), A, np.zeros(3), [(C.SOC, 3, 0.0, 0)], st)
+    np.testing.assert_allclose(D, [0.5, 1.0, 2.0], rtol=1e-15)
+    np.testing.assert_allclose(E, [0.5, 0.5, 0.5], rtol=1e-15)
+    _, E2, _ = ipm.equilibrate(np.zeros((3, 3)), A, np.zeros(3), [(C.NONNEG, 3, 0.0, 0)], st)
+    np.testing.assert_allclose(E2, [0.5, 1.0, 2.0], rtol=1e-15)
+
+
+def test_initial_point_hand_solved_lp():
+    """min x s.t. x <= 1, -x <= 1 (equilibration off).  With H = I the two solves
+    give, by hand: [0; b] -> x = 0, z = (-1, -1), s = -z = (1, 1); [-q; 0] -> z =
+    (-1/2, 1/2).  The shift into the cone leaves s (least entry 1) and moves z by
+    1 - (-1/2): z = (1, 2).  max_iter = 0 returns that point."""
+    r = oracle.solve(np.zeros((1, 1)), np.array([1.0]), np.array([[1.0], [-1.0]]), np.array([1.0, 1.0]),
+                     [(C.NONNEG, 2, 0.0)], settings=dict(max_iter=0, equilibrate=0))
+    np.testing.assert_allclose(r.x, [0.0], atol=1e-10)
+    np.testing.assert_allclose(r.s, [1.0, 1.0], rtol=1e-10)
+    np.testing.assert_allclose(r.z, [1.0, 2.0], rtol=1e-10)
+
+
+def test_initial_point_hand_solved_soc():
+    """min x s.t. (2 - x, 3, 4) in SOC(3), i.e. A = (1, 0, 0)', b = (2, 3, 4), q = 1
+    (equilibration off).  [0; b] -> x = 2, s = (0, 3, 4), whose least Jordan
+    eigenvalue is 0 - 5 = -5, so s + 6 e = (6, 3, 4); [-q; 0] -> z = (-1, 0, 0),
+    shifted by 1 - (-1) = 2: z = (1, 0, 0)."""
+    r = oracle.solve(np.zeros((1, 1)), np.array([1.0]), np.array([[1.0], [0.0], [0.0]]),
+                     np.array([2.0, 3.0, 4.0]), [(C.SOC, 3, 0.0)], settings=dict(max_iter=0, equilibrate=0))
+    np.testing.assert_allclose(r.x, [2.0], rtol=1e-10)
+    np.testing.assert_allclose(r.s, [6.0, 3.0, 4.0], rtol=1e-10)
+    np.testing.assert_allclose(r.z, [1.0, 0.0, 0.0], atol=1e-10)
