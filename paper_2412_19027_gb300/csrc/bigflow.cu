@@ -68,7 +68,7 @@ __device__ __forceinline__ int bnrow(const Geo& g, int64_t b) {
   return (int)(b < g.P ? min((int64_t)NB, g.c - NB * b) : min((int64_t)NB, g.f - g.c - NB * (b - g.P)));
 }
 struct Words {
-  int *tile, *etile, *diag, *trsm, *pe;
+  int *tile, *etile, *diag, *trsm, *pe, *txc, *uxc;
   int64_t P;
   __device__ int* t(int64_t i, int64_t j) const { return tile + i * (i + 1) / 2 + j; }
   __device__ int* e(int64_t i, int64_t c) const { return etile + i * P + c; }
@@ -81,6 +81,8 @@ __device__ __forceinline__ Words words_of(int* base, const Geo& g) {
   w.diag = w.etile + g.nbf * g.P;
   w.trsm = w.diag + g.P;
   w.pe = w.trsm + g.nbf;
+  w.txc = w.pe + g.P;
+  w.uxc = w.txc + g.P;
   return w;
 }
 
@@ -382,6 +384,105 @@ __device__ int task_dx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, T*
   const int nhit = bf_diag_factor<T>(A, Bk, G + k0 + k0 * f, f, pw, Dp + kp, Eb + k0 + k0 * f, f, false, dsign + kp,
                                      eps, delta, sh);
   return nhit;
+}
+
+// TX(p, q), FP64 split chain: rows 16 q .. 16 q + 15 of T(p-1, p), L = F Linv^T D^{-1}
+// with the products of DX(p) (thread: row tid % 16, column block tid / 16; the
+// zero half of Linv skipped) -- same sums, same division.
+template <typename T>
+__device__ void task_tx(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int q, T* F, const T* E, const T* Dp,
+                        T* sm, T* dl) {
+  T* Bk = sm;             // K-major Linv of panel p - 1 (row j, k = l)
+  T* Xk = sm + NB * LDK;  // K-major F rows of the part (row rr, k = l)
+  const int64_t f = g.f, kq = (int64_t)(p - 1) * NB, k0 = (int64_t)p * NB;
+  const int pw = bnrow(g, p);  // panel p - 1 is a full 64-column panel
+  const int r0 = 16 * q, nr = max(0, min(16, pw - r0));
+  if (nr == 0) return;  // uniform over the CTA
+  T* G = F + bf.goff[b];
+  const T* Eb = E + bf.eoff[b];
+  const int tid = threadIdx.x;
+  {  // all loads in one batch, then into shared memory
+    T ra[16], rx[4];
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      const int i = idx % NB, l = idx / NB;
+      ra[it] = __ldcg(Eb + (kq + i) + (kq + l) * f);
+    }
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int idx = tid + NT * it;
+      const int rr = idx % 16, l = idx / 16;
+      rx[it] = (rr < nr) ? __ldcg(G + (k0 + r0 + rr) + (kq + l) * f) : (T)0;
+    }
+    if (tid < NB) dl[tid] = __ldcg(Dp + bf.k0pos[b] + kq + tid);
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      Bk[swz(idx / NB, idx % NB)] = ra[it];
+    }
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int idx = tid + NT * it;
+      Xk[swz(idx / 16, idx % 16)] = rx[it];
+    }
+  }
+  __syncthreads();
+  const int rr = tid % 16, cq = tid / 16;
+  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+  for (int l = 0; l < 4 * cq + 4; ++l) {
+    const T a = Xk[swz(l, rr)];
+    T bv[4];
+    ld4<T>(Bk + swz(l, 4 * cq), bv);
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) acc[bb] += a * bv[bb];
+  }
+  if (rr < nr)
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) G[(k0 + r0 + rr) + (kq + 4 * cq + bb) * f] = acc[bb] / dl[4 * cq + bb];
+}
+
+// UX(p, q), FP64 split chain: the lower entries of rows [cut_q, cut_{q+1}) of the
+// diagonal tile (p, p) minus sum_l L_rl (L_cl d_l), panel p-1 (equal-area row slabs
+// 0, 32, 45, 55, 64), an entry per thread at a time -- the sums of DX(p).
+template <typename T>
+__device__ void task_ux(const BigFrontDev& bf, int64_t b, const Geo& g, int p, int q, T* F, const T* Dp, T* sm,
+                        T* dl) {
+  T* Xk = sm;  // K-major L rows of block p, panel p - 1 (row i, k = l)
+  const int64_t f = g.f, kq = (int64_t)(p - 1) * NB, k0 = (int64_t)p * NB;
+  const int pw = bnrow(g, p);
+  constexpr int kCut[5] = {0, 32, 45, 55, 64};
+  const int r0 = min(kCut[q], pw), r1 = min(kCut[q + 1], pw);
+  if (r0 >= r1) return;  // uniform over the CTA
+  T* G = F + bf.goff[b];
+  const int tid = threadIdx.x;
+  {
+    T rl[16];
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      const int i = idx % NB, l = idx / NB;
+      rl[it] = (i < r1) ? __ldcg(G + (k0 + i) + (kq + l) * f) : (T)0;
+    }
+    if (tid < NB) dl[tid] = __ldcg(Dp + bf.k0pos[b] + kq + tid);
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int idx = tid + NT * it;
+      Xk[swz(idx / NB, idx % NB)] = rl[it];
+    }
+  }
+  __syncthreads();
+  const int base = r0 * (r0 + 1) / 2;
+  const int ne = r1 * (r1 + 1) / 2 - base;  // entries (r, c), r0 <= r < r1, c <= r
+  for (int e = tid; e < ne; e += NT) {
+    int r = r0;
+    while ((r + 1) * (r + 2) / 2 - base <= e) ++r;
+    const int c = e - (r * (r + 1) / 2 - base);
+    T acc = (T)0;
+    for (int l = 0; l < NB; ++l) acc += Xk[swz(l, r)] * (Xk[swz(l, c)] * dl[l]);
+    T* t = G + (k0 + r) + (k0 + c) * f;
+    *t = __ldcg(t) - acc;
+  }
 }
 
 // T(p, i): L_IK = F_IK Linv^T D_K^{-1} for the rows of block i (each thread 4 x 4).
@@ -778,6 +879,16 @@ __global__ void __launch_bounds__(NT, 2)
             wp[1] = w.t(tk.i, p), wv[1] = p;
             nw = 2;
             break;
+          case 6:  // TX(p, q): Linv of panel p - 1, F_{p,p-1} updated by panels < p - 1
+            wp[0] = w.diag + p - 1, wv[0] = 1;
+            wp[1] = w.t(p, p - 1), wv[1] = p - 1;
+            nw = 2;
+            break;
+          case 7:  // UX(p, q): every part of TX(p), the tile updated by panels < p - 1
+            wp[0] = w.trsm + p, wv[0] = p;
+            wp[1] = w.t(p, p), wv[1] = p - 1;
+            nw = 2;
+            break;
           case 2:
             wp[0] = w.diag + p, wv[0] = 1;
             wp[1] = w.e(p, tk.j), wv[1] = p - tk.j;
@@ -846,6 +957,12 @@ __global__ void __launch_bounds__(NT, 2)
       case 2:
         task_efin<T, TC>(bf, b, g, tk.p, tk.j, E, sm, pkr);
         break;
+      case 6:
+        task_tx<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
+        break;
+      case 7:
+        task_ux<T>(bf, b, g, tk.p, tk.i, F, Dp, sm, dl);
+        break;
       default:
         if constexpr (TC) {
           stop = !task_update_tc(bf, b, g, tk.p, tk.i, tk.j, tk.kind != 3, F, E, Dp, &tmap, pkr, smtc, dl,
@@ -878,6 +995,18 @@ __global__ void __launch_bounds__(NT, 2)
           break;
         case 2:
           st_release(w.e(p, tk.j), p - tk.j + 1);
+          break;
+        case 6:  // the last part of TX(p) publishes the L rows of block p
+          if (atomicAdd(w.txc + p, 1) == 3) {
+            __threadfence();
+            st_release(w.trsm + p, p);
+          }
+          break;
+        case 7:  // the last part of UX(p) publishes the updated diagonal tile
+          if (atomicAdd(w.uxc + p, 1) == 3) {
+            __threadfence();
+            st_release(w.t(p, p), p);
+          }
           break;
         case 3:
           st_release(w.t(tk.i, tk.j), p + 1);

@@ -60,20 +60,28 @@ struct BigLevelPlan {
 // current panel's updates); a task waits (bounded) on per-front version words
 // set by the tasks it depends on.  Every task it waits on was taken earlier by a
 // CTA that is running, so the launch needs no co-residency guarantee.
+// FP64 factors split the fused chain task (an FP64 warp instruction holds a
+// sub-partition's FP64 pipe ~64 cycles, so DX(p) alone takes ~200 us on one SM):
+// for 1 <= p < P, TX(p, q) (q = 0..3: rows 16 q .. 16 q + 15 of T(p-1, p)), then
+// UX(p, q) (four row slabs of equal area of the update of the diagonal tile (p, p)
+// by panel p-1), then D(p).  The last part of TX(p) (of UX(p)) to finish releases
+// the word the consumers of T(p-1, p) (of the tile) wait on.  Same arithmetic, in
+// the same order, as DX(p).
 struct FlowTask {
   int32_t bf;    // big-front id
-  int16_t kind;  // 0 D, 1 T, 2 Efin, 3 U, 4 EU, 5 DX
+  int16_t kind;  // 0 D, 1 T, 2 Efin, 3 U, 4 EU, 5 DX, 6 TX, 7 UX
   int16_t p;     // panel
-  int32_t i, j;  // block row; block column (Efin: e; EU: e)
+  int32_t i, j;  // block row; block column (Efin: e; EU: e; TX, UX: the part q in i)
 };
 // version words of one front: tile[tri(i, j)], etile[i * P + e], diag[P], trsm[nbf],
-// pe[P] (tensor-core flow: the packed E_KK tile of panel p is stored)
+// pe[P] (tensor-core flow: the packed E_KK tile of panel p is stored), txc[P] and
+// uxc[P] (FP64 split chain: parts of TX(p) and UX(p) done)
 __host__ __device__ inline int64_t flow_nbf(int64_t f, int64_t c) {
   return (c + kBfNB - 1) / kBfNB + (f - c + kBfNB - 1) / kBfNB;
 }
 __host__ __device__ inline int64_t flow_words(int64_t f, int64_t c) {
   const int64_t P = (c + kBfNB - 1) / kBfNB, n = flow_nbf(f, c);
-  return n * (n + 1) / 2 + n * P + P + n + P;
+  return n * (n + 1) / 2 + n * P + P + n + 3 * P;
 }
 constexpr int kFlowThreads = 256;
 

@@ -260,7 +260,7 @@ T* up(DeviceArena& ar, const std::vector<T>& v) {
 // dur: typical durations (microseconds) by kind D, T, Efin, U, EU, DX; span: the
 // simulated duration of the level.
 static bool flow_schedule_order(std::vector<FlowTask>& tasks, int64_t t0, const std::vector<int64_t>& P_of,
-                                int workers, const double* dur, double* span) {
+                                int workers, const double* dur, double* span, bool split = false) {
   const int64_t n = (int64_t)tasks.size() - t0;
   *span = 0.0;
   if (n <= 1) return true;
@@ -279,46 +279,75 @@ static bool flow_schedule_order(std::vector<FlowTask>& tasks, int64_t t0, const 
     auto it = idx.find(key(b, kind, p, i, j));
     return it == idx.end() ? -1 : it->second;
   };
-  auto dd = [&](int64_t b, int64_t p) { return p == 0 ? find(b, 0, 0, 0, 0) : find(b, 5, p, p, p); };
+  // split: FP64 chain tasks TX(p, q), UX(p, q), D(p) in place of DX(p) (bigfront.cuh)
+  auto dd = [&](int64_t b, int64_t p) {
+    return (p == 0 || split) ? find(b, 0, p, p, p) : find(b, 5, p, p, p);
+  };
   auto folded = [&](int64_t b, int64_t p, int64_t i) { return i == p + 1 && i < P_of[b]; };
-  auto tt = [&](int64_t b, int64_t p, int64_t i) { return folded(b, p, i) ? find(b, 5, i, i, i) : find(b, 1, p, i, p); };
   struct Edge {
     int64_t to;
     bool mid;  // the successor needs only the early-published rows of a DX task
   };
   std::vector<std::vector<Edge>> succ(n);
   std::vector<int> indeg(n, 0);
+  std::vector<std::pair<int64_t, bool>> d;  // predecessors of one task (index, mid)
+  // the producer(s) of L_IK, block row i of panel p: T(p, i), DX(p + 1) when folded
+  // (its early-published rows), or the four parts TX(p + 1, q) when split
+  auto add_tt = [&](int64_t b, int64_t p, int64_t i) {
+    if (!folded(b, p, i)) d.emplace_back(find(b, 1, p, i, p), false);
+    else if (!split) d.emplace_back(find(b, 5, i, i, i), true);
+    else
+      for (int64_t q = 0; q < 4; ++q) d.emplace_back(find(b, 6, i, q, 0), false);
+  };
   for (int64_t t = 0; t < n; ++t) {
     const FlowTask& k = tasks[t0 + t];
-    int64_t d[3] = {-1, -1, -1};
-    bool mid[3] = {false, false, false};
+    d.clear();
     const int64_t p = k.p, i = k.i, j = k.j, b = k.bf;
     switch (k.kind) {
-      case 0: break;
-      case 5:
-        d[0] = dd(b, p - 1);
-        d[1] = p >= 2 ? find(b, 3, p - 2, p, p - 1) : -1;
-        d[2] = p >= 2 ? find(b, 3, p - 2, p, p) : -1;
+      case 0:
+        if (split && p >= 1)
+          for (int64_t q = 0; q < 4; ++q) d.emplace_back(find(b, 7, p, q, 0), false);
         break;
-      case 1: d[0] = dd(b, p); d[1] = p > 0 ? find(b, 3, p - 1, i, p) : -1; break;
-      case 2: d[0] = dd(b, p); d[1] = p - 1 >= j ? find(b, 4, p - 1, p, j) : -1; break;
+      case 5:
+        d.emplace_back(dd(b, p - 1), false);
+        if (p >= 2) {
+          d.emplace_back(find(b, 3, p - 2, p, p - 1), false);
+          d.emplace_back(find(b, 3, p - 2, p, p), false);
+        }
+        break;
+      case 6:
+        d.emplace_back(dd(b, p - 1), false);
+        if (p >= 2) d.emplace_back(find(b, 3, p - 2, p, p - 1), false);
+        break;
+      case 7:
+        for (int64_t q = 0; q < 4; ++q) d.emplace_back(find(b, 6, p, q, 0), false);
+        if (p >= 2) d.emplace_back(find(b, 3, p - 2, p, p), false);
+        break;
+      case 1:
+        d.emplace_back(dd(b, p), false);
+        if (p > 0) d.emplace_back(find(b, 3, p - 1, i, p), false);
+        break;
+      case 2:
+        d.emplace_back(dd(b, p), false);
+        if (p - 1 >= j) d.emplace_back(find(b, 4, p - 1, p, j), false);
+        break;
       case 3:
-        d[0] = tt(b, p, i), mid[0] = folded(b, p, i);
-        d[1] = tt(b, p, j), mid[1] = folded(b, p, j);
-        d[2] = p > 0 ? find(b, 3, p - 1, i, j) : -1;
+        add_tt(b, p, i);
+        add_tt(b, p, j);
+        if (p > 0) d.emplace_back(find(b, 3, p - 1, i, j), false);
         break;
       default:
-        d[0] = tt(b, p, i), mid[0] = folded(b, p, i);
-        d[1] = j < p ? find(b, 2, p, p, j) : dd(b, p);
-        d[2] = p - 1 >= j ? find(b, 4, p - 1, i, j) : -1;
+        add_tt(b, p, i);
+        d.emplace_back(j < p ? find(b, 2, p, p, j) : dd(b, p), false);
+        if (p - 1 >= j) d.emplace_back(find(b, 4, p - 1, i, j), false);
         break;
     }
-    for (int q = 0; q < 3; ++q) {
-      if (d[q] < 0) continue;
+    for (size_t q = 0; q < d.size(); ++q) {
+      if (d[q].first < 0) continue;
       bool dup = false;
-      for (int r = 0; r < q; ++r) dup = dup || d[r] == d[q];
+      for (size_t r = 0; r < q; ++r) dup = dup || d[r].first == d[q].first;
       if (dup) continue;
-      succ[d[q]].push_back(Edge{t, mid[q]});
+      succ[d[q].first].push_back(Edge{t, d[q].second});
       ++indeg[t];
     }
   }
@@ -603,9 +632,9 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       // and of the tensor-core launch (two CTAs per SM; per-task timestamps on the
       // mixed-cone QP's root front: U and EU ~0.8x, the diagonal tasks ~1.1x and
       // the panel tasks ~1.08x those of the CUDA-core launch)
-      static const double dur2[6] = {22.0, 7.0, 5.5, 8.0, 8.0, 27.0};
-      static const double dur1[6] = {20.0, 6.5, 5.3, 5.8, 6.1, 25.0};
-      static const double dur2tc[6] = {25.2, 7.6, 5.9, 6.5, 5.9, 29.8};
+      static const double dur2[8] = {22.0, 7.0, 5.5, 8.0, 8.0, 27.0, 0.0, 0.0};
+      static const double dur1[8] = {20.0, 6.5, 5.3, 5.8, 6.1, 25.0, 0.0, 0.0};
+      static const double dur2tc[8] = {25.2, 7.6, 5.9, 6.5, 5.9, 29.8, 0.0, 0.0};
       std::vector<FlowTask> one(tasks.begin() + st.flow_t0[l], tasks.end()), tco(one);
       double span2 = 0.0, span1 = 0.0, spantc = 0.0;
       if (!flow_schedule_order(tasks, st.flow_t0[l], P_of, 2 * flow_sms, dur2, &span2) ||
@@ -623,10 +652,56 @@ int ldl_structure_upload(DeviceArena& ar, const Symbolic& sy, const NumericMaps&
       else if (st.flow_one[l]) std::copy(one.begin(), one.end(), tasks.begin() + st.flow_t0[l]);
     }
     st.flow_words = words;
+    // the FP64 factor's table: the same levels, fronts and version words, with the
+    // fused chain task split into TX(p, q), UX(p, q) and D(p) (bigfront.cuh)
+    std::vector<FlowTask> tasks64;
+    st.flow_t0_64.assign(sy.nlev, 0);
+    st.flow_nt_64.assign(sy.nlev, 0);
+    st.flow_one64.assign(sy.nlev, 0);
+    for (int64_t l = 0; l < sy.nlev; ++l) {
+      if (st.lev_big[l].empty()) continue;
+      st.flow_t0_64[l] = (int64_t)tasks64.size();
+      auto add = [&](int64_t b, int kind, int64_t p, int64_t i, int64_t j) {
+        tasks64.push_back(FlowTask{(int32_t)b, (int16_t)kind, (int16_t)p, (int32_t)i, (int32_t)j});
+      };
+      for (int64_t J : st.lev_big[l]) {
+        const int64_t b = bid_of[J];
+        const int64_t P = P_of[b], nb = flow_nbf(bf_f[b], bf_c[b]);
+        for (int64_t p = 0; p < P; ++p) {
+          if (p >= 1) {
+            for (int64_t q = 0; q < 4; ++q) add(b, 6, p, q, 0);
+            for (int64_t q = 0; q < 4; ++q) add(b, 7, p, q, 0);
+          }
+          add(b, 0, p, p, p);
+          for (int64_t i = p + 1; i < nb; ++i)
+            if (!(i == p + 1 && i < P)) add(b, 1, p, i, p);
+          for (int64_t e = 0; e < p; ++e) add(b, 2, p, p, e);
+          for (int64_t j = p + 1; j < nb; ++j)
+            for (int64_t i = j; i < nb; ++i)
+              if (!(i == p + 1 && j == p + 1 && i < P)) add(b, 3, p, i, j);
+          for (int64_t i = p + 1; i < nb; ++i)
+            for (int64_t e = 0; e <= p; ++e) add(b, 4, p, i, e);
+        }
+      }
+      st.flow_nt_64[l] = (int64_t)tasks64.size() - st.flow_t0_64[l];
+      // FP64 task times (microseconds; D, T, Efin, U, EU, -, TX, UX) from per-task
+      // timestamps on a GB300 at two CTAs per SM (banded LP generator), and estimates
+      // for one CTA per SM (a task then has the SM's FP64 pipe to itself)
+      static const double dur64_2[8] = {95.0, 41.0, 57.0, 57.0, 57.0, 204.0, 12.0, 14.0};
+      static const double dur64_1[8] = {70.0, 28.0, 38.0, 36.0, 36.0, 150.0, 8.0, 9.0};
+      std::vector<FlowTask> one(tasks64.begin() + st.flow_t0_64[l], tasks64.end());
+      double span2 = 0.0, span1 = 0.0;
+      if (!flow_schedule_order(tasks64, st.flow_t0_64[l], P_of, 2 * flow_sms, dur64_2, &span2, true) ||
+          !flow_schedule_order(one, 0, P_of, flow_sms, dur64_1, &span1, true))
+        return CLR_E_INVALID;
+      st.flow_one64[l] = span1 < 0.97 * span2 ? 1 : 0;
+      if (st.flow_one64[l]) std::copy(one.begin(), one.end(), tasks64.begin() + st.flow_t0_64[l]);
+    }
     if (!tasks.empty()) {
       st.flow_task = ar.upload(tasks.data(), (int64_t)tasks.size());
+      st.flow_task64 = ar.upload(tasks64.data(), (int64_t)tasks64.size());
       st.flow_soff = ar.upload(soff.data(), (int64_t)soff.size());
-      if (!st.flow_task || !st.flow_soff) return CLR_E_OOM;
+      if (!st.flow_task || !st.flow_task64 || !st.flow_soff) return CLR_E_OOM;
     }
   }
   st.sn_ptr = up(ar, sy.sn_ptr);
@@ -728,9 +803,14 @@ int LdlFactor<T>::factor(cudaStream_t stm, const double* kval, const IterScal* s
                                                                dyn_hits, skip);
     }
     if (!S.lev_big[l].empty()) {
-      int rc = use_flow ? BigFrontOps<T>::flow_level(stm, S.bfd, S.flow_task, S.flow_t0[l], S.flow_nt[l], flow_state,
+      // FP64: the table with the split chain task; FP32: the fused one
+      const bool f64 = sizeof(T) == 8;
+      const FlowTask* tab = f64 ? S.flow_task64 : S.flow_task;
+      const int64_t ft0 = f64 ? S.flow_t0_64[l] : S.flow_t0[l], fnt = f64 ? S.flow_nt_64[l] : S.flow_nt[l];
+      const bool one = f64 ? S.flow_one64[l] != 0 : S.flow_one[l] != 0;
+      int rc = use_flow ? BigFrontOps<T>::flow_level(stm, S.bfd, tab, ft0, fnt, flow_state,
                                                      S.flow_head[l], S.flow_soff,
-                                                     S.flow_one[l] ? flow_sms : flow_sms * flow_occ, S.flow_one[l] != 0,
+                                                     one ? flow_sms : flow_sms * flow_occ, one,
                                                      F, E, Dp, S.dsign, dyn_eps, dyn_delta, dyn_hits, tc_err, skip,
                                                      (use_flow_tc() && tcs.pk && (S.flow_tc[l] || flow_tc == 2)) ? &tcs : nullptr)
                         : BigFrontOps<T>::factor_level(stm, S.bfd, S.bplans[l], F, E, Dp, Linv, S.dsign, dyn_eps,

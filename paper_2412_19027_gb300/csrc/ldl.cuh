@@ -46,6 +46,10 @@ struct LdlStructure {
   std::vector<int64_t> flow_t0, flow_nt, flow_head;
   std::vector<int8_t> flow_one;  // per level: launch one CTA per SM (else two)
   std::vector<int8_t> flow_tc;   // per level: FP32 factors use the tensor-core launch
+  // the FP64 factor's task table (the fused chain task split, bigfront.cuh), per level
+  FlowTask* flow_task64 = nullptr;
+  std::vector<int64_t> flow_t0_64, flow_nt_64;
+  std::vector<int8_t> flow_one64;
   int64_t flow_words = 0;
   int64_t pk_tiles = 0;  // packed operand tiles of the largest level (tensor-core flow, FP32 factor)
   int small_max = 0;
