@@ -944,24 +944,25 @@ __global__ void __launch_bounds__(NT, 2)
       case 0:
         task_diag<T, TC>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, hits, sm, dsh, pkr);
         break;
-      case 5: {
-        const Words w = words_of(state + soff[b], g);
-        const int nhit =
-            task_dx<T, TC>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, sm, dsh, dl, w.trsm + tk.p, pkr);
-        if (tid == 0 && nhit) atomicAdd(hits, nhit);
+      case 5:  // the fused chain task: FP32 tables only (FP64 ones split it)
+        if constexpr (sizeof(T) == 4) {
+          const Words w = words_of(state + soff[b], g);
+          const int nhit =
+              task_dx<T, TC>(bf, b, g, tk.p, F, E, Dp, dsign, (T)eps_d, (T)delta_d, sm, dsh, dl, w.trsm + tk.p, pkr);
+          if (tid == 0 && nhit) atomicAdd(hits, nhit);
+        }
         break;
-      }
       case 1:
         task_trsm<T, TC>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl, pkr);
         break;
       case 2:
         task_efin<T, TC>(bf, b, g, tk.p, tk.j, E, sm, pkr);
         break;
-      case 6:
-        task_tx<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
+      case 6:  // the split chain tasks: FP64 tables only
+        if constexpr (sizeof(T) == 8) task_tx<T>(bf, b, g, tk.p, tk.i, F, E, Dp, sm, dl);
         break;
       case 7:
-        task_ux<T>(bf, b, g, tk.p, tk.i, F, Dp, sm, dl);
+        if constexpr (sizeof(T) == 8) task_ux<T>(bf, b, g, tk.p, tk.i, F, Dp, sm, dl);
         break;
       default:
         if constexpr (TC) {
