@@ -368,7 +368,13 @@ typedef struct {
 } clr_server_stats;
 
 /* Start a server on the current CUDA device.  st: settings of every solve
- * (NULL: clr_default_settings(.., 64); use_graph is forced on).  Errors:
+ * (NULL: clr_default_settings(.., 64); use_graph is forced on).  device_bytes
+ * is the admission budget: a new cohort is formed while the live cohorts hold
+ * less than it (or none is live).  One builder forms and uploads cohorts one
+ * at a time and a cohort's size is known once it is on the device, so the
+ * peak (clr_server_stats.peak_bytes) can exceed the budget by at most the
+ * last cohort admitted.  A cohort whose upload fails (the device has no room:
+ * CLR_E_OOM or CLR_E_CUDA) hands that error to each of its tickets.  Errors:
  * CLR_E_INVALID (zero budget, max_cohort < 1, max_active < 1), CLR_E_CUDA. */
 int clr_server_create(clr_server** out, size_t device_bytes, int32_t max_cohort, int32_t max_active,
                       const clr_settings* st);

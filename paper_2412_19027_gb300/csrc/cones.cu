@@ -823,12 +823,12 @@ __device__ __forceinline__ int64_t psd_cone_of(const ConeDev& cd, int64_t r) {
   return lo;
 }
 
-__global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ z, IterScal* sc,
-                            const int* skip) {
+__global__ void k_scale_psd(ConeDev cd, const int32_t* __restrict__ list, const double* __restrict__ s,
+                            const double* __restrict__ z, IterScal* sc, const int* skip) {
   if (skip && *skip) return;
   __shared__ double Ls[32 * LDP], Lz[32 * LDP], M[32 * LDP], V[32 * LDP], sig[32];
   __shared__ int bad, flag;
-  const int64_t cone = blockIdx.x;
+  const int64_t cone = list[blockIdx.x];
   const int k = cd.psd_ck[cone], d = k * (k + 1) / 2;
   const int64_t row = cd.psd_crow[cone];
   if (threadIdx.x == 0) bad = 0;
@@ -909,6 +909,232 @@ __global__ void k_scale_psd(ConeDev cd, const double* __restrict__ s, const doub
   if ((threadIdx.x & 31) == 0) atomicMax(&sc[cd.row_pid[row]].hmax_bits, dbits(mx));
 }
 
+// PSD scaling of the cones of order k <= KM (KM = 4, 8 or 16): a group of KM lanes
+// per cone, lane j holding column j of each k x k matrix in registers, so that the
+// scalar work of a Jacobi rotation (two norms, the angle, cos and sin) is done once
+// per column pair by its two lanes instead of once per pair by a whole warp (an
+// FP64 warp instruction occupies the FP64 pipe of its sub-partition whatever the
+// number of active lanes).  The same steps as k_scale_psd: Cholesky factors of S
+// and Z, M = Lz' Ls, one-sided cyclic Jacobi on M with the same round-robin pair
+// order, R = Ls V Lambda^{-1/2}, R^{-1} = Lambda^{-1/2} U' Lz', and the packed -H
+// block from W = R R'.  Differences in rounding only: the Cholesky scales a column
+// by the reciprocal of its pivot, and the column sums run over rows, not lanes.
+// Every loop that shuffles runs the warp's largest trip count; the extra rounds,
+// steps and sweeps are no-ops for a smaller cone, so a cone's result does not
+// depend on the cones sharing its warp.
+template <int KM>
+__global__ void __launch_bounds__(128, 1) k_scale_psd_lane(ConeDev cd, const int32_t* __restrict__ list, int64_t nlist,
+                                                        const double* __restrict__ s, const double* __restrict__ z,
+                                                        IterScal* sc, const int* skip) {
+  if (skip && *skip) return;
+  constexpr int LD = KM + 1;           // column stride in shared memory (column writes on distinct banks)
+  constexpr int MAT = KM * LD;         // one k x k matrix
+  constexpr int PER = 2 * MAT + 1;     // two per cone, odd stride between the cones of a warp
+  constexpr int CPB = 128 / KM;        // cones per block
+  constexpr int DM = KM * (KM + 1) / 2;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ double sm[CPB * PER];
+  __shared__ unsigned char tab_i[DM], tab_j[DM];  // svec index -> (i, j), i <= j
+  for (int t = threadIdx.x; t < DM; t += blockDim.x) {
+    int j = 0;
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    tab_j[t] = (unsigned char)j;
+    tab_i[t] = (unsigned char)(t - j * (j + 1) / 2);
+  }
+  __syncthreads();
+  const int c = threadIdx.x % KM;  // my column
+  const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / KM;
+  const bool live = slot < nlist;
+  const int64_t cone = live ? list[slot] : 0;
+  const int k = live ? cd.psd_ck[cone] : 0;
+  const int64_t row = live ? cd.psd_crow[cone] : 0;
+  double* A = sm + (threadIdx.x / KM) * PER;  // Ls, later R
+  double* B = A + MAT;                        // Lz, later W
+  int kw = k;  // the warp's largest order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) kw = max(kw, __shfl_xor_sync(FULL, kw, o));
+
+  // ---- Cholesky factors of S (into A) and Z (into B), column c in registers
+  int bad = 0;
+  double col[KM];
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* v = (pass == 0 ? s : z) + row;
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+      double x = 0.0;
+      if (c < k && i < k) {
+        const int a = min(i, c), b = max(i, c);
+        x = v[b * (b + 1) / 2 + a];
+        if (i != c) x /= kSqrt2;
+      }
+      col[i] = x;
+    }
+#pragma unroll 1
+    for (int p = 0; p < kw; ++p) {  // (kw: uniform over the warp)
+      if (c == p && p < k) {
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+          if (i == p) d = col[i];
+        if (!(d > 0)) bad = 1;
+        const double l = sqrt(fmax(d, 1e-300));
+        const double rl = 1.0 / l;
+#pragma unroll
+        for (int i = 0; i < KM; ++i) {
+          if (i == p) col[i] = l;
+          else if (i > p) col[i] *= rl;
+        }
+      }
+      // column p of L, from its owner; my own row's entry of it
+      double lpc = 0.0;
+      double lp[KM];
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        lp[i] = __shfl_sync(FULL, col[i], p, KM);
+        if (i == c) lpc = lp[i];
+      }
+      if (c > p && c < k) {
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+          if (i > p && i >= c && i < k) col[i] -= lp[i] * lpc;
+      }
+    }
+    double* X = pass == 0 ? A : B;
+#pragma unroll
+    for (int i = 0; i < KM; ++i) X[i + c * LD] = (i >= c) ? col[i] : 0.0;
+  }
+  const unsigned seg_bits = ((1u << KM) - 1u) << ((threadIdx.x & 31) & ~(KM - 1));  // my cone's lanes
+  const bool cone_bad = (__ballot_sync(FULL, bad) & seg_bits) != 0;
+  __syncwarp();
+
+  // ---- M = Lz' Ls (column c), V = I
+  double mc[KM], vc[KM];
+#pragma unroll
+  for (int i = 0; i < KM; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < KM; ++l)
+      if (l >= i && l >= c && l < k) acc += B[l + i * LD] * A[l + c * LD];
+    mc[i] = (i < k && c < k) ? acc : 0.0;
+    vc[i] = (i == c && c < k) ? 1.0 : 0.0;
+  }
+
+  // ---- one-sided cyclic Jacobi: round r pairs the columns as the round-robin
+  // tournament of kk = k + (k odd) players (column 0 fixed, the others rotating)
+  const int kk = k + (k & 1), kkw = kw + (kw & 1);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    int rot = 0;
+    for (int r = 0; r < kkw - 1; ++r) {
+      int partner = -1;
+      bool first = false;
+      if (c < k && r < kk - 1) {
+        const int x = (c == 0) ? 0 : 1 + ((c - 1 - r) % (kk - 1) + (kk - 1)) % (kk - 1);
+        const int y = kk - 1 - x;
+        partner = (y == 0) ? 0 : 1 + ((y - 1 + r) % (kk - 1));
+        first = x < kk / 2;
+        if (partner >= k) partner = -1;
+      }
+      const int src = partner >= 0 ? partner : c;
+      // rows k.. of a cone's columns are zero and stay zero, so the row loops run to
+      // the warp's largest order (a uniform exit) without changing any sum
+      double so = 0.0, sp = 0.0, ga = 0.0;
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        if (i >= kw) break;
+        const double o = __shfl_sync(FULL, mc[i], src, KM);
+        so += mc[i] * mc[i];
+        sp += o * o;
+        ga += mc[i] * o;
+      }
+      double cs = 1.0, sg = 0.0;
+      if (partner >= 0) {
+        const double al = first ? so : sp, be = first ? sp : so;  // the pair's (a, b) norms, same on both lanes
+        if (fabs(ga) > 1e-15 * sqrt(al * be) && fabs(ga) > 1e-300) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          cs = 1.0 / sqrt(1.0 + t * t);
+          const double sn = cs * t;
+          sg = first ? -sn : sn;  // a' = c a - s b,  b' = s a + c b
+          rot = 1;
+        }
+      }
+      // (cs, sg) = (1, 0) leaves a column that does not rotate unchanged
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        if (i >= kw) break;
+        const double om = __shfl_sync(FULL, mc[i], src, KM);
+        const double ov = __shfl_sync(FULL, vc[i], src, KM);
+        mc[i] = cs * mc[i] + sg * om;
+        vc[i] = cs * vc[i] + sg * ov;
+      }
+    }
+    if (!__any_sync(FULL, rot)) break;
+  }
+
+  // ---- Lambda, R = Ls V Lambda^{-1/2} (column c), R^{-1} = Lambda^{-1/2} U' Lz' (row c)
+  double nrm = 0.0;
+#pragma unroll
+  for (int i = 0; i < KM; ++i)
+    if (i < k) nrm += mc[i] * mc[i];
+  const double sig = sqrt(nrm), rs = sqrt(sig);
+  double* Rg = live ? cd.psd_R + cd.psd_cR[cone] : nullptr;
+  double* Rig = live ? cd.psd_Ri + cd.psd_cR[cone] : nullptr;
+  if (c < k) cd.psd_lam[cd.psd_cl[cone] + c] = cone_bad ? NAN : sig;
+#pragma unroll
+  for (int i = 0; i < KM; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < KM; ++l)
+      if (l <= i && l < k) acc += A[i + l * LD] * vc[l];
+    col[i] = acc / rs;
+    if (c < k && i < k) Rg[i + c * k] = col[i];
+  }
+#pragma unroll
+  for (int l = 0; l < KM; ++l) mc[l] = (l < k) ? mc[l] / sig : 0.0;  // column c of U
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < KM; ++l)
+      if (l <= j && l < k) acc += mc[l] * B[j + l * LD];
+    if (c < k && j < k) Rig[c + j * k] = acc / rs;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < KM; ++i) A[i + c * LD] = (c < k && i < k) ? col[i] : 0.0;  // R
+  __syncwarp();
+  // W = R R' (row c), then the packed lower -H over svec indices, column-major:
+  // H_{(i,j),(p,q)} = c_ij c_pq (W_ip W_jq + W_iq W_jp), c = 1/sqrt(2) on diagonal pairs
+#pragma unroll
+  for (int l = 0; l < KM; ++l) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) acc += A[c + j * LD] * A[l + j * LD];
+    B[c + l * LD] = acc;
+  }
+  __syncwarp();
+  const int d = k * (k + 1) / 2;
+  double* kb = live ? cd.kvz + cd.psd_ckb[cone] : nullptr;
+  double mx = 0.0;
+  for (int cc = 0; cc < d; ++cc) {
+    const int p = tab_i[cc], q = tab_j[cc];
+    const double cpq = (p == q) ? 1.0 / kSqrt2 : 1.0;
+    const int64_t start = (int64_t)cc * d - (int64_t)cc * (cc - 1) / 2;
+    for (int rr = cc + c; rr < d; rr += KM) {
+      const int i = tab_i[rr], j = tab_j[rr];
+      const double cij = (i == j) ? 1.0 / kSqrt2 : 1.0;
+      const double h = cij * cpq * (B[i + p * LD] * B[j + q * LD] + B[i + q * LD] * B[j + p * LD]);
+      kb[start + (rr - cc)] = -h;
+      if (rr == cc) mx = fmax(mx, fabs(h));
+    }
+  }
+#pragma unroll
+  for (int o = KM / 2; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULL, mx, o, KM));
+  if (live && c == 0) atomicMax(&sc[cd.row_pid[row]].hmax_bits, dbits(mx));
+}
+
 int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const double* z, IterScal* sc,
                   const int* skip) {
   if (cd.m_zero + cd.m_nonneg > 0)
@@ -922,8 +1148,21 @@ int cones_scaling(cudaStream_t st, const ConeDev& cd, const double* s, const dou
     k_scale_exppow<<<ep_launch(cd.n_exp + cd.n_pow).blocks, ep_launch(cd.n_exp + cd.n_pow).threads, 0, st>>>(
         cd, s, z, sc, skip);
   if (cd.n_psd > 0) {
-    const int threads = 32 * ((cd.psd_kmax + 1) / 2 > 0 ? (cd.psd_kmax + 1) / 2 : 1);
-    k_scale_psd<<<(unsigned)cd.n_psd, threads < 64 ? 64 : threads, 0, st>>>(cd, s, z, sc, skip);
+    // orders up to 16: a lane per column (4, 8 or 16 lanes per cone); larger: a block per cone
+    if (cd.psd_nlist[0] > 0)
+      k_scale_psd_lane<4><<<grid_for(cd.psd_nlist[0] * 4, 128, 1 << 30), 128, 0, st>>>(cd, cd.psd_list[0],
+                                                                                      cd.psd_nlist[0], s, z, sc, skip);
+    if (cd.psd_nlist[1] > 0)
+      k_scale_psd_lane<8><<<grid_for(cd.psd_nlist[1] * 8, 128, 1 << 30), 128, 0, st>>>(cd, cd.psd_list[1],
+                                                                                      cd.psd_nlist[1], s, z, sc, skip);
+    if (cd.psd_nlist[2] > 0)
+      k_scale_psd_lane<16><<<grid_for(cd.psd_nlist[2] * 16, 128, 1 << 30), 128, 0, st>>>(
+          cd, cd.psd_list[2], cd.psd_nlist[2], s, z, sc, skip);
+    if (cd.psd_nlist[3] > 0) {
+      const int threads = 32 * ((cd.psd_kmax + 1) / 2 > 0 ? (cd.psd_kmax + 1) / 2 : 1);
+      k_scale_psd<<<(unsigned)cd.psd_nlist[3], threads < 64 ? 64 : threads, 0, st>>>(cd, cd.psd_list[3], s, z, sc,
+                                                                                   skip);
+    }
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;

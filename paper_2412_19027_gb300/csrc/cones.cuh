@@ -1,8 +1,10 @@
 // Cone kernels of the per-iteration device step (Alg. 1 steps 4, 7, 8, 10 of
 // the paper): scaling H written into the KKT values, step lengths, and the
 // combined-step d_s.  Families are handled as Sec. 3.3 proposes, mapped to
-// GB300: zero/nonneg one flat pass, SOC one warp per cone (shuffle
-// reductions), exp/pow one thread per cone, PSD one block per cone.
+// GB300: zero/nonneg one flat pass, SOC a thread per cone up to 8 rows and a
+// warp per cone above (shuffle reductions), exp/pow a thread per cone, PSD
+// scaling a group of 4-16 lanes per cone up to order 16 (a lane per column) and a
+// block per cone above, the other PSD kernels a block per cone.
 #pragma once
 
 #include <algorithm>
@@ -47,6 +49,11 @@ struct ConeDev {
   const int64_t* psd_ckb = nullptr;
   const int64_t* psd_cR = nullptr;
   const int64_t* psd_cl = nullptr;
+  // PSD cones by scaling-kernel class: orders 1-4, 5-8 and 9-16 (psd_list[0..2]; a
+  // group of 4, 8 or 16 lanes per cone, lane j holding column j) and 17-32
+  // (psd_list[3]; a block per cone)
+  const int32_t* psd_list[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t psd_nlist[4] = {0, 0, 0, 0};
   int64_t nn_kb = 0;  // packed offset of the first nonneg diagonal (after the zero cone)
   double* kvz = nullptr;  // z part of the KKT values (-H blocks)
   int64_t nkz = 0;        // number of entries of kvz
@@ -101,6 +108,13 @@ inline bool cones_psd_setup(DeviceArena& ar, ConeDev& cd, const std::vector<int6
   cd.psd_R = ar.alloc_n<double>(nR);
   cd.psd_Ri = ar.alloc_n<double>(nR);
   cd.psd_lam = ar.alloc_n<double>(nl);
+  std::vector<int32_t> lists[4];
+  for (int64_t i = 0; i < n; ++i) lists[ck[i] <= 4 ? 0 : ck[i] <= 8 ? 1 : ck[i] <= 16 ? 2 : 3].push_back((int32_t)i);
+  for (int c = 0; c < 4; ++c) {
+    cd.psd_nlist[c] = (int64_t)lists[c].size();
+    cd.psd_list[c] = nullptr;
+    if (!lists[c].empty() && !(cd.psd_list[c] = ar.upload(lists[c].data(), cd.psd_nlist[c]))) return false;
+  }
   return cd.psd_ck && cd.psd_crow && cd.psd_ckb && cd.psd_cR && cd.psd_cl && cd.psd_R && cd.psd_Ri && cd.psd_lam;
 }
 

@@ -81,8 +81,17 @@ PSD_MIXED_CONES = ([(C.PSD, 3, 0.0), (C.PSD, 55, 0.0), (C.NONNEG, 2, 0.0), (C.PS
                     (C.PSD, 1, 0.0), (C.PSD, 21, 0.0)])
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4, PSD32_CONES, PSD_MIXED_CONES],
-                         ids=["mixed", "psd10", "psd3", "psd32", "psd_mixed_orders"])
+# PSD orders at the edges of the scaling kernel's classes (1-4, 5-8, 9-16 a lane per
+# column, 17-32 a block per cone), interleaved, and cones of different orders sharing a
+# warp (16 with 11, 9 with 12)
+PSD_CLASS_CONES = ([(C.PSD, 136, 0.0), (C.PSD, 66, 0.0), (C.NONNEG, 2, 0.0), (C.PSD, 1, 0.0), (C.PSD, 10, 0.0),
+                    (C.PSD, 15, 0.0), (C.PSD, 36, 0.0), (C.PSD, 45, 0.0), (C.PSD, 153, 0.0), (C.PSD, 28, 0.0)]
+                   + [(C.PSD, 78, 0.0)] * 3)
+
+
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, [(C.PSD, 6, 0.0)] * 4, PSD32_CONES, PSD_MIXED_CONES,
+                                   PSD_CLASS_CONES],
+                         ids=["mixed", "psd10", "psd3", "psd32", "psd_mixed_orders", "psd_class_edges"])
 def test_cone_scaling_matches_oracle(cones):
     rng = np.random.default_rng(0)
     s, z = _rand_cone_points(rng, cones)
@@ -132,7 +141,8 @@ def test_step_length_matches_oracle(cones):
         assert got == pytest.approx(alpha, rel=1e-9)
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, PSD32_CONES], ids=["mixed", "psd10", "psd32"])
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, PSD32_CONES, PSD_CLASS_CONES],
+                         ids=["mixed", "psd10", "psd32", "psd_class_edges"])
 def test_combined_ds_matches_oracle(cones):
     rng = np.random.default_rng(2)
     s, z = _rand_cone_points(rng, cones)
