@@ -177,6 +177,33 @@ def test_psd_nt_scaling(k):
         np.testing.assert_allclose(sc["H"], sc["H"].T, atol=1e-10)
 
 
+@pytest.mark.parametrize("k", [2, 4, 7])
+def test_psd_on_diagonal_matrices_is_nonneg(k):
+    """Diagonal S, Z, dS, dZ: the PSD cone restricted to diagonal matrices is the
+    nonnegative orthant, so its NT scaling, combined-step d_s and step length must
+    equal the nonneg closed forms entry by entry (H = s/z, lambda = sqrt(s z),
+    d_s = (s z + ds dz - sigma mu)/z, ratio test), whatever order the SVD gives the
+    singular values in (R, R^-1 and lambda must be permuted alike)."""
+    rng = np.random.default_rng(40 + k)
+    dg = lambda v: C.svec(np.diag(v))  # noqa: E731
+    for _ in range(5):
+        s, z = rng.uniform(0.2, 2.0, k), rng.uniform(0.2, 2.0, k)
+        ds, dz = rng.standard_normal(k), rng.standard_normal(k)
+        smu = 0.3
+        sc = C.nt_scaling(C.PSD, dg(s), dg(z))
+        np.testing.assert_allclose(np.sort(sc["lam"]), np.sort(np.sqrt(s * z)), rtol=1e-12)
+        np.testing.assert_allclose(sc["H"] @ dg(dz), dg(s / z * dz), rtol=1e-12, atol=1e-13)
+        lam = C.lam_vec(C.PSD, sc["lam"], len(dg(s)))
+        eta = C.jordan_prod(C.PSD, C.apply_scaling(C.PSD, sc, "WinvT", dg(ds)),
+                            C.apply_scaling(C.PSD, sc, "W", dg(dz)))
+        v = C.jordan_prod(C.PSD, lam, lam) + eta - smu * C.identity(C.PSD, len(lam))
+        d_s = C.apply_scaling(C.PSD, sc, "WT", C.jordan_div(C.PSD, sc["lam"], v))
+        np.testing.assert_allclose(d_s, dg((s * z + ds * dz - smu) / z), rtol=1e-11, atol=1e-12)
+        a_psd = C.step_length_symmetric(C.PSD, dg(s), dg(ds))
+        a_nn = C.step_length_symmetric(C.NONNEG, s, ds)
+        assert a_psd == pytest.approx(a_nn, rel=1e-12) or (math.isinf(a_nn) and a_psd > 1e12)
+
+
 def test_svec_is_an_isometry():
     X, Y = C.smat(_psd_pt(RNG, 4)), C.smat(_psd_pt(RNG, 4))
     assert C.svec(X) @ C.svec(Y) == pytest.approx(np.trace(X @ Y), rel=1e-13)
