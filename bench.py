@@ -92,11 +92,12 @@ def cone_bytes(family, k):
 # quadratic root tests; d_s: W^{-1} ds_a, W dz_a, their Jordan product, the
 # quotient by lambda, W.  PSD(10): two 10 x 10 Cholesky factors, L_z^T L_s,
 # a one-sided Jacobi SVD (about 6 sweeps), R, R^{-1} and the 55 x 55 packed H;
-# step: per side a Cholesky, two triangular solves and a two-sided Jacobi
-# eigenvalue sweep set (about 8 sweeps); d_s: congruences with R, R^{-1}.
+# step: per side a Cholesky, L^{-1} dS L^{-T}, a Householder tridiagonalisation
+# and about 48 Sturm counts of the bisection (4 flops per row each); d_s:
+# congruences with R, R^{-1}.
 CONE_FP64_FLOPS = {"nonneg": {"scaling": 4, "step": 4, "ds": 8},
                    "soc": {"scaling": 150, "step": 80, "ds": 100},
-                   "psd": {"scaling": 30_000, "step": 110_000, "ds": 8_000}}
+                   "psd": {"scaling": 30_000, "step": 11_000, "ds": 8_000}}
 
 
 def run_cone_roofline(clr, W, peaks, reps=10, shift=0):

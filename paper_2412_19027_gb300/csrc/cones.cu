@@ -1317,14 +1317,164 @@ __global__ void k_step_soc(ConeDev cd, const double* __restrict__ s, const doubl
   run.flush(sc, &IterScal::amin_bits);
 }
 
-__global__ void k_step_psd(ConeDev cd, const double* __restrict__ s, const double* __restrict__ ds,
-                           const double* __restrict__ z, const double* __restrict__ dz, IterScal* sc,
-                           const int* skip) {
+// Step length of one side of a PSD cone of order k <= KM (one thread): the largest
+// alpha with S + alpha dS PSD, alpha = -1 / lambda_min(L^{-1} dS L^{-T}), S = L L'
+// (Sec. 2.2: the symmetric-cone step is the cone's own ratio test).  lambda_min by
+// Householder tridiagonalisation of X = L^{-1} dS L^{-T} (Golub and Van Loan,
+// Matrix Computations, Sec. 8.3.1) and bisection on Sturm counts of the
+// tridiagonal matrix (the number of negative pivots of T - x I in its LDL'
+// recurrence is the number of eigenvalues below x), from the Gershgorin bound
+// to a relative width of 1e-14.  Infinity when lambda_min >= 0; zero when S is
+// not positive definite in floating point or X is not finite (no step).
+template <int KM>
+__device__ double psd_step_side(const double* __restrict__ v, const double* __restrict__ dv, int k) {
+  double L[KM * KM], W[KM * KM];  // row-major; L lower, W full then X in its lower part
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i <= j; ++i) {
+      double x = v[j * (j + 1) / 2 + i], y = dv[j * (j + 1) / 2 + i];
+      if (i != j) {
+        x /= kSqrt2;
+        y /= kSqrt2;
+      }
+      L[j * KM + i] = x;
+      W[i * KM + j] = y;
+      W[j * KM + i] = y;
+    }
+  // Cholesky S = L L' (by columns, left-looking)
+  for (int j = 0; j < k; ++j) {
+    double d = L[j * KM + j];
+    for (int l = 0; l < j; ++l) d -= L[j * KM + l] * L[j * KM + l];
+    if (!(d > 0)) return 0.0;
+    const double ljj = sqrt(d), r = 1.0 / ljj;
+    L[j * KM + j] = ljj;
+    for (int i = j + 1; i < k; ++i) {
+      double a = L[i * KM + j];
+      for (int l = 0; l < j; ++l) a -= L[i * KM + l] * L[j * KM + l];
+      L[i * KM + j] = a * r;
+    }
+  }
+  // W = L^{-1} dS, then X = W L^{-T} (lower part, over W's lower part)
+  for (int i = 0; i < k; ++i) {
+    const double r = 1.0 / L[i * KM + i];
+    for (int c = 0; c < k; ++c) {
+      double a = W[i * KM + c];
+      for (int l = 0; l < i; ++l) a -= L[i * KM + l] * W[l * KM + c];
+      W[i * KM + c] = a * r;
+    }
+  }
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double a = W[i * KM + j];
+      for (int l = 0; l < j; ++l) a -= W[i * KM + l] * L[j * KM + l];
+      W[i * KM + j] = a / L[j * KM + j];
+    }
+  // Householder tridiagonalisation of X (lower part): diagonal a, subdiagonal b
+  double a[KM], b[KM];
+  double* u = L;  // (L no longer needed) the Householder vector, then p
+  double* pv = L + KM;
+  for (int j = 0; j + 2 < k; ++j) {
+    const double x0 = W[(j + 1) * KM + j];
+    double al2 = 0.0;
+    for (int i = j + 1; i < k; ++i) al2 += W[i * KM + j] * W[i * KM + j];
+    if (al2 - x0 * x0 <= 0.0) {  // the column is already tridiagonal
+      b[j] = x0;
+      continue;
+    }
+    const double nrm = sqrt(al2);
+    const double be = x0 >= 0.0 ? -nrm : nrm;  // the new subdiagonal entry
+    const double tau = (be - x0) / be;         // H = I - tau u u', u_{j+1} = 1
+    const double sc = 1.0 / (x0 - be);
+    u[j + 1] = 1.0;
+    for (int i = j + 2; i < k; ++i) u[i] = W[i * KM + j] * sc;
+    double pu = 0.0;
+    for (int i = j + 1; i < k; ++i) {  // p = tau X22 u
+      double acc = 0.0;
+      for (int l = j + 1; l < k; ++l) acc += (i >= l ? W[i * KM + l] : W[l * KM + i]) * u[l];
+      pv[i] = tau * acc;
+      pu += pv[i] * u[i];
+    }
+    const double h = 0.5 * tau * pu;
+    for (int i = j + 1; i < k; ++i) pv[i] -= h * u[i];  // w = p - (tau/2)(p'u) u
+    for (int i = j + 1; i < k; ++i)                     // X22 -= u w' + w u'
+      for (int l = j + 1; l <= i; ++l) W[i * KM + l] -= u[i] * pv[l] + pv[i] * u[l];
+    b[j] = be;
+  }
+  bool fin = true;
+  for (int i = 0; i < k; ++i) {
+    a[i] = W[i * KM + i];
+    fin = fin && isfinite(a[i]);
+  }
+  if (k >= 2) b[k - 2] = W[(k - 1) * KM + (k - 2)];
+  for (int i = 0; i + 1 < k; ++i) fin = fin && isfinite(b[i]);
+  if (!fin) return 0.0;
+  // number of eigenvalues below x: negative pivots of T - x I
+  auto below = [&](double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+      double t = a[i] - x;
+      if (i > 0) t -= (b[i - 1] * b[i - 1]) / d;
+      if (t == 0.0) t = -1e-300;
+      cnt += t < 0.0;
+      d = t;
+    }
+    return cnt;
+  };
+  if (below(0.0) == 0) return INFINITY;
+  double lo = INFINITY;
+  for (int i = 0; i < k; ++i)
+    lo = fmin(lo, a[i] - (i > 0 ? fabs(b[i - 1]) : 0.0) - (i + 1 < k ? fabs(b[i]) : 0.0));
+  double hi = 0.0;
+  for (int it = 0; it < 80 && hi - lo > 1e-14 * fabs(lo); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (below(mid) > 0) hi = mid;
+    else lo = mid;
+  }
+  return -1.0 / (0.5 * (lo + hi));
+}
+
+// Step length of the PSD cones of order k <= KM, a thread per cone (the order-16
+// arithmetic fills every lane of an FP64 warp instruction); one atomic per warp
+// when the warp's cones belong to one problem.
+template <int KM>
+__global__ void __launch_bounds__(128) k_step_psd_thread(ConeDev cd, const int32_t* __restrict__ list, int64_t nlist,
+                                                         const double* __restrict__ s, const double* __restrict__ ds,
+                                                         const double* __restrict__ z, const double* __restrict__ dz,
+                                                         IterScal* sc, const int* skip) {
+  if (skip && *skip) return;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = t < nlist;
+  double amax = INFINITY;
+  int pid = -1;
+  if (live) {
+    const int64_t cone = list[t];
+    const int k = cd.psd_ck[cone];
+    const int64_t row = cd.psd_crow[cone];
+    pid = cd.row_pid[row];
+    amax = fmin(psd_step_side<KM>(s + row, ds + row, k), psd_step_side<KM>(z + row, dz + row, k));
+  }
+  const int pid0 = __shfl_sync(FULL, pid, 0);  // (dead lanes are the warp's last)
+  if (__all_sync(FULL, !live || pid == pid0)) {
+    double m = amax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0 && live && m < INFINITY) atomicMin(&sc[pid0].amin_bits, dbits(m));
+  } else if (live && amax < INFINITY) {
+    atomicMin(&sc[pid].amin_bits, dbits(amax));
+  }
+}
+
+__global__ void k_step_psd(ConeDev cd, const int32_t* __restrict__ list, const double* __restrict__ s,
+                           const double* __restrict__ ds, const double* __restrict__ z, const double* __restrict__ dz,
+                           IterScal* sc, const int* skip) {
   if (skip && *skip) return;
   __shared__ double L[32 * LDP], X[32 * LDP], Y[32 * LDP], csb[64];
   __shared__ int bad, flag;
-  const int k = cd.psd_ck[blockIdx.x];
-  const int64_t row = cd.psd_crow[blockIdx.x];
+  const int64_t cone = list[blockIdx.x];
+  const int k = cd.psd_ck[cone];
+  const int64_t row = cd.psd_crow[cone];
   double amax = INFINITY;
   for (int side = 0; side < 2; ++side) {
     const double* v = side == 0 ? s + row : z + row;
@@ -1374,8 +1524,24 @@ int cones_step_symmetric(cudaStream_t st, const ConeDev& cd, const double* s, co
     if (cd.soc_nsmall < cd.n_soc) k_step_soc<32><<<soc_grid(cd, 32), 256, 0, st>>>(cd, s, ds, z, dz, sc, skip);
   }
   if (cd.n_psd > 0) {
-    const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
-    k_step_psd<<<(unsigned)cd.n_psd, threads, 0, st>>>(cd, s, ds, z, dz, sc, skip);
+    // orders up to 16: a thread per cone (tridiagonalisation and Sturm bisection);
+    // larger: a block per cone (two-sided Jacobi)
+    if (cd.psd_nlist[0] > 0)
+      k_step_psd_thread<4><<<grid_for(cd.psd_nlist[0], 128, 1 << 30), 128, 0, st>>>(cd, cd.psd_list[0],
+                                                                                   cd.psd_nlist[0], s, ds, z, dz, sc,
+                                                                                   skip);
+    if (cd.psd_nlist[1] > 0)
+      k_step_psd_thread<8><<<grid_for(cd.psd_nlist[1], 128, 1 << 30), 128, 0, st>>>(cd, cd.psd_list[1],
+                                                                                   cd.psd_nlist[1], s, ds, z, dz, sc,
+                                                                                   skip);
+    if (cd.psd_nlist[2] > 0)
+      k_step_psd_thread<16><<<grid_for(cd.psd_nlist[2], 128, 1 << 30), 128, 0, st>>>(cd, cd.psd_list[2],
+                                                                                    cd.psd_nlist[2], s, ds, z, dz, sc,
+                                                                                    skip);
+    if (cd.psd_nlist[3] > 0) {
+      const int threads = std::max(64, 32 * ((cd.psd_kmax + 1) / 2));
+      k_step_psd<<<(unsigned)cd.psd_nlist[3], threads, 0, st>>>(cd, cd.psd_list[3], s, ds, z, dz, sc, skip);
+    }
   }
   CLR_CHECK_LAUNCH();
   return CLR_OK;

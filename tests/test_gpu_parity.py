@@ -110,7 +110,8 @@ def test_cone_scaling_matches_oracle(cones):
         off += d
 
 
-@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, PSD32_CONES], ids=["mixed", "psd10", "psd32"])
+@pytest.mark.parametrize("cones", [MIXED_CONES, PSD_CONES, PSD32_CONES, PSD_CLASS_CONES],
+                         ids=["mixed", "psd10", "psd32", "psd_class_edges"])
 def test_step_length_matches_oracle(cones):
     rng = np.random.default_rng(1)
     for trial in range(5):
