@@ -707,34 +707,46 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
         // two passes straight into the lists: count the sources of every target of
         // P's front, then place each source at its target's next slot -- targets in
         // increasing order, each target's sources in child / column / row order, as
-        // the sorted pairs below give them
+        // the sorted pairs below give them.  Done per block of kColBlock parent
+        // columns (targets are column-major, so the blocks come in target order and
+        // a target's sources all fall in its block), which keeps the counts and the
+        // block's slice of the lists in cache.
+        constexpr int64_t kColBlock = 16;
         std::vector<int64_t>& cntT = tcount;
-        cntT.assign((size_t)(fP * fP), 0);
-        auto each = [&](auto&& fn) {
-          for (int64_t ch : children[P]) {
-            if (is_pushed[ch]) continue;
-            const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
-            const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
-            const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
-            for (int64_t b = c; b < f; ++b) {
-              const int64_t lb = loc[rr[b]];
-              for (int64_t a = b; a < f; ++a) fn(loc[rr[a]] + lb * fP, sy.front_off[ch] + a + b * f);
+        cntT.assign((size_t)(kColBlock * fP), 0);
+        int64_t pos = (int64_t)mp.fa_src.size();
+        for (int64_t c0 = 0; c0 < fP; c0 += kColBlock) {
+          const int64_t c1 = std::min(fP, c0 + kColBlock);
+          // the update columns b of each child whose parent column loc[rr[b]] lies in
+          // [c0, c1): loc is increasing along a child's rows, so a contiguous range
+          auto each = [&](auto&& fn) {
+            for (int64_t ch : children[P]) {
+              if (is_pushed[ch]) continue;
+              const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+              const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+              const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+              const int64_t* lo = std::partition_point(rr + c, rr + f, [&](int64_t r) { return loc[r] < c0; });
+              const int64_t* hi = std::partition_point(lo, rr + f, [&](int64_t r) { return loc[r] < c1; });
+              for (int64_t b = lo - rr; b < hi - rr; ++b) {
+                const int64_t lb = loc[rr[b]] - c0;
+                for (int64_t a = b; a < f; ++a) fn(loc[rr[a]] + lb * fP, sy.front_off[ch] + a + b * f);
+              }
             }
+          };
+          const int64_t nb = (c1 - c0) * fP;
+          std::fill(cntT.begin(), cntT.begin() + nb, 0);
+          each([&](int64_t t, int64_t) { ++cntT[t]; });
+          for (int64_t t = 0; t < nb; ++t) {
+            if (!cntT[t]) continue;
+            mp.fa_tgt.push_back(sy.front_off[P] + c0 * fP + t);
+            mp.fa_ptr.push_back(pos);
+            const int64_t k = cntT[t];
+            cntT[t] = pos;
+            pos += k;
           }
-        };
-        each([&](int64_t t, int64_t) { ++cntT[t]; });
-        const int64_t s0 = (int64_t)mp.fa_src.size();
-        int64_t pos = s0;
-        for (int64_t t = 0; t < fP * fP; ++t) {
-          if (!cntT[t]) continue;
-          mp.fa_tgt.push_back(sy.front_off[P] + t);
-          mp.fa_ptr.push_back(pos);
-          const int64_t k = cntT[t];
-          cntT[t] = pos;
-          pos += k;
+          mp.fa_src.resize(pos);
+          each([&](int64_t t, int64_t src) { mp.fa_src[cntT[t]++] = src; });
         }
-        mp.fa_src.resize(pos);
-        each([&](int64_t t, int64_t src) { mp.fa_src[cntT[t]++] = src; });
       } else if (ne > 0) {
         contrib.clear();
         contrib.reserve(ne);
