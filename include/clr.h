@@ -138,6 +138,10 @@ typedef struct {
                                  columns per cone, [-eta^2 I, eta u, eta v; eta u', 1, 0; eta v', 0, -1] --
                                  instead of a dense d x d block (not in the paper, which factors with
                                  cuDSS); default 33, 0 = never */
+  int32_t pull_lists_direct;  /* 1 (default): the factorization's extend-add source lists of a front whose
+                                 children contribute densely are placed directly by counting each target's
+                                 sources; 0: always by sorting (target, source) pairs.  Both give the same
+                                 lists (clr_symbolic_stats.maps_digest); 0 is slower and exists to check that */
 } clr_settings;
 
 typedef struct {
@@ -175,6 +179,9 @@ typedef struct {
   int64_t l_nnz_exact;     /* nnz of the exact factor pattern (l_nnz adds the explicit zeros of merged supernodes) */
   int64_t l_nnz_counted;   /* the same from column counts of the order, without forming the factor */
   double factor_flops_stored; /* flops the supernodal factorization performs (explicit zeros included) */
+  uint64_t maps_digest;    /* FNV-1a hash of the elimination order and every index map of the numeric
+                              phase (value scatter, extend-add and solve pull lists, push rounds): equal
+                              digests mean the same device arithmetic, e.g. across hosts or settings */
 } clr_symbolic_stats;
 
 /* Device-side timing of the last clr_solve, from CUDA events recorded inside

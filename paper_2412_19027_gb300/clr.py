@@ -45,7 +45,7 @@ class clr_settings(C.Structure):
                 ("min_step", C.c_double), ("use_graph", C.c_int32), ("verbose", C.c_int32),
                 ("fp64_escalation", C.c_int32), ("big_front_schedule", C.c_int32),
                 ("small_front_max", C.c_int32), ("amalgamation", C.c_int32), ("escalate_ratio", C.c_double),
-                ("soc_expand_dim", C.c_int32)]
+                ("soc_expand_dim", C.c_int32), ("pull_lists_direct", C.c_int32)]
 
 
 class clr_info(C.Structure):
@@ -73,7 +73,7 @@ class clr_symbolic_stats(C.Structure):
                 ("l_nnz", C.c_int64), ("factor_flops", C.c_double), ("n_supernodes", C.c_int64),
                 ("n_levels", C.c_int64), ("max_front", C.c_int64), ("front_pool_entries", C.c_int64),
                 ("n_dense_rows", C.c_int64), ("ordering", C.c_int64), ("l_nnz_exact", C.c_int64),
-                ("l_nnz_counted", C.c_int64), ("factor_flops_stored", C.c_double)]
+                ("l_nnz_counted", C.c_int64), ("factor_flops_stored", C.c_double), ("maps_digest", C.c_uint64)]
 
 
 class clr_problem(C.Structure):

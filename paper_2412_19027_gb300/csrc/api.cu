@@ -57,6 +57,7 @@ int clr_default_settings(clr_settings* out, int32_t factor_bits) {
   s.amalgamation = 1;
   s.escalate_ratio = 0.1;
   s.soc_expand_dim = 33;
+  s.pull_lists_direct = 1;
   *out = s;
   return CLR_OK;
 }
@@ -71,6 +72,7 @@ static int check_settings(const clr_settings& s) {
     return CLR_E_INVALID;
   if (!(s.scale_min > 0) || !(s.scale_max >= s.scale_min)) return CLR_E_INVALID;
   if (!(s.escalate_ratio >= 0) || s.soc_expand_dim < 0) return CLR_E_INVALID;
+  if (s.pull_lists_direct != 0 && s.pull_lists_direct != 1) return CLR_E_INVALID;
   if (!(s.step_fraction > 0 && s.step_fraction <= 1) || !(s.backtrack > 0 && s.backtrack < 1)) return CLR_E_INVALID;
   return CLR_OK;
 }
@@ -364,6 +366,7 @@ int clr_get_symbolic_stats(const clr_solver* s, clr_symbolic_stats* out) {
   r.l_nnz_exact = v.sy.l_nnz_exact;
   r.l_nnz_counted = v.sy.pred_nnz;
   r.factor_flops_stored = v.sy.flops_stored;
+  r.maps_digest = maps_digest(v.sy, v.mp);
   *out = r;
   return CLR_OK;
 }

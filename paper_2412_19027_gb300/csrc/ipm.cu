@@ -991,7 +991,7 @@ int Solver::analyze_cohort(std::vector<HostProblem>&& ps, const std::vector<std:
   int rc = build_cohort(probs, orders, hp, lay, sy, err, st.verbose, st.amalgamation);
   if (rc != CLR_OK) return rc;
   const double t1 = now_s();
-  build_numeric_maps(sy, hp.kcol_ptr, hp.krow, mp);
+  build_numeric_maps(sy, hp.kcol_ptr, hp.krow, mp, st.pull_lists_direct != 0);
   if (st.verbose)
     std::fprintf(stderr, "[clr] setup: ordering + symbolic %.3f s, numeric maps %.3f s (N %lld, nnz(L) %lld, %.3g flops)\n",
                  t1 - t0, now_s() - t1, (long long)sy.N, (long long)sy.l_nnz, sy.flops);

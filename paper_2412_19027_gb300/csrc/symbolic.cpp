@@ -575,7 +575,7 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
 
 // Index maps for the numeric phase.
 void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr, const std::vector<int64_t>& krow,
-                        NumericMaps& mp) {
+                        NumericMaps& mp, bool direct) {
   const int64_t N = sy.N;
   mp = NumericMaps();
   std::vector<int64_t> sn_of(N);
@@ -703,7 +703,7 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
         if (!is_pushed[ch]) ne += upd_rows(ch) * (upd_rows(ch) + 1) / 2;
       // the direct path scans all fP^2 targets of the parent: taken when the
       // children's contributions are comparable to that (else the sorted pairs)
-      if (ne > 0 && fP * fP <= kDirectTargets && fP * fP <= 4 * ne) {
+      if (direct && ne > 0 && fP * fP <= kDirectTargets && fP * fP <= 4 * ne) {
         // two passes straight into the lists: count the sources of every target of
         // P's front, then place each source at its target's next slot -- targets in
         // increasing order, each target's sources in child / column / row order, as
@@ -800,6 +800,35 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
   // KKT index of every front row (the solves read and write vectors in KKT order)
   mp.rows_kkt.resize(sy.rows.size());
   for (size_t k = 0; k < sy.rows.size(); ++k) mp.rows_kkt[k] = (int32_t)sy.perm[sy.rows[k]];
+}
+
+uint64_t maps_digest(const Symbolic& sy, const NumericMaps& mp) {
+  uint64_t h = 1469598103934665603ull;  // FNV-1a, 64-bit
+  auto byte = [&](uint64_t x, int nb) {
+    for (int k = 0; k < nb; ++k) h = (h ^ ((x >> (8 * k)) & 0xffu)) * 1099511628211ull;
+  };
+  auto add = [&](const auto& v) {
+    byte((uint64_t)v.size(), 8);
+    for (const auto& x : v) byte((uint64_t)(int64_t)x, (int)sizeof(x));
+  };
+  add(sy.perm);
+  add(mp.kdest);
+  add(mp.diag_pos);
+  add(mp.fa_lev_ptr);
+  add(mp.fa_tgt);
+  add(mp.fa_ptr);
+  add(mp.fa_src);
+  add(mp.px_lev_ptr);
+  add(mp.px_round_ptr);
+  add(mp.px_child);
+  add(mp.rel_off);
+  add(mp.rel);
+  add(mp.sv_lev_ptr);
+  add(mp.sv_tgt);
+  add(mp.sv_ptr);
+  add(mp.sv_src);
+  add(mp.rows_kkt);
+  return h;
 }
 
 }  // namespace clr

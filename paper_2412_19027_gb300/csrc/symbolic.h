@@ -29,7 +29,10 @@ struct NumericMaps {
   std::vector<int32_t> rows_kkt;   // KKT index of every front row
 };
 
+// direct = false builds every extend-add list by sorting pairs (the same lists).
 void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr, const std::vector<int64_t>& krow,
-                        NumericMaps& mp);
+                        NumericMaps& mp, bool direct = true);
+// FNV-1a over the elimination order and every array of the maps.
+uint64_t maps_digest(const Symbolic& sy, const NumericMaps& mp);
 
 }  // namespace clr

@@ -319,3 +319,25 @@ def test_update_PA_validation(clr):
         s.update_PA(A=bad)
     assert e.value.code == -1
     s.free()
+
+
+def test_pull_lists_direct_and_sorted_agree(clr):
+    """The extend-add source lists of fronts whose children contribute densely are
+    placed directly by counting (per block of parent columns); the other fronts'
+    by sorting (target, source) pairs.  With pull_lists_direct = 0 every list is
+    sorted: the maps, and so the device arithmetic, must be the same
+    (maps_digest).  The problems cover fronts with thousands of children
+    (entropy, Huber, portfolio), cone blocks (PSD, SOC) and a banded LP."""
+    probs = [W.entropy_max(0, n=300), W.huber_qp(0, n=300), W.portfolio_qp(0, n=400),
+             W.psd_batch(0, n=1000, n_psd=100, n_nonneg=250), W.banded_lp(0, n=4000, m=8000),
+             W.mixed_cone(0, n=400, n_zero=100, n_nonneg=500, n_soc=100, n_exp=20, n_pow=20)]
+    for p in probs:
+        d = []
+        for direct in (1, 0):
+            s = clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, pull_lists_direct=direct))
+            d.append(s.symbolic_stats()["maps_digest"])
+            s.free()
+        assert d[0] == d[1] and d[0] != 0, p.name
+    with pytest.raises(RuntimeError):
+        clr.clr_analyze(probs[0].P, probs[0].q, probs[0].A, probs[0].b, probs[0].cones,
+                        clr.clr_default_settings(64, pull_lists_direct=2))
