@@ -179,9 +179,10 @@ typedef struct {
   int64_t l_nnz_exact;     /* nnz of the exact factor pattern (l_nnz adds the explicit zeros of merged supernodes) */
   int64_t l_nnz_counted;   /* the same from column counts of the order, without forming the factor */
   double factor_flops_stored; /* flops the supernodal factorization performs (explicit zeros included) */
-  uint64_t maps_digest;    /* FNV-1a hash of the elimination order and every index map of the numeric
-                              phase (value scatter, extend-add and solve pull lists, push rounds): equal
-                              digests mean the same device arithmetic, e.g. across hosts or settings */
+  uint64_t maps_digest;    /* hash (FNV-1a's step over whole entries) of the elimination order and of
+                              every index map of the numeric phase (value scatter, extend-add and solve
+                              pull lists, push rounds): equal digests mean the same device arithmetic,
+                              e.g. across hosts or settings */
 } clr_symbolic_stats;
 
 /* Device-side timing of the last clr_solve, from CUDA events recorded inside

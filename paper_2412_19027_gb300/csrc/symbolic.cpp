@@ -803,13 +803,13 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
 }
 
 uint64_t maps_digest(const Symbolic& sy, const NumericMaps& mp) {
-  uint64_t h = 1469598103934665603ull;  // FNV-1a, 64-bit
-  auto byte = [&](uint64_t x, int nb) {
-    for (int k = 0; k < nb; ++k) h = (h ^ ((x >> (8 * k)) & 0xffu)) * 1099511628211ull;
-  };
+  // FNV-1a's step (xor, then multiply by the 64-bit FNV prime) applied to whole
+  // entries rather than bytes: one multiply per index
+  uint64_t h = 1469598103934665603ull;
+  auto word = [&](uint64_t x) { h = (h ^ x) * 1099511628211ull; };
   auto add = [&](const auto& v) {
-    byte((uint64_t)v.size(), 8);
-    for (const auto& x : v) byte((uint64_t)(int64_t)x, (int)sizeof(x));
+    word((uint64_t)v.size());
+    for (const auto& x : v) word((uint64_t)(int64_t)x);
   };
   add(sy.perm);
   add(mp.kdest);

@@ -32,7 +32,8 @@ struct NumericMaps {
 // direct = false builds every extend-add list by sorting pairs (the same lists).
 void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr, const std::vector<int64_t>& krow,
                         NumericMaps& mp, bool direct = true);
-// FNV-1a over the elimination order and every array of the maps.
+// A hash (FNV-1a's step over whole entries) of the elimination order and every
+// array of the maps.
 uint64_t maps_digest(const Symbolic& sy, const NumericMaps& mp);
 
 }  // namespace clr
