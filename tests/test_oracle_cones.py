@@ -204,6 +204,28 @@ def test_psd_on_diagonal_matrices_is_nonneg(k):
         assert a_psd == pytest.approx(a_nn, rel=1e-12) or (math.isinf(a_nn) and a_psd > 1e12)
 
 
+@pytest.mark.parametrize("t,d", [(C.SOC, 2), (C.SOC, 5), (C.PSD, 6), (C.PSD, 15)])
+def test_combined_ds_at_equal_s_and_z(t, d):
+    """s = z: the NT scaling point is the identity (H = I, W = I, lambda = s), so
+    the combined-step d_s with no affine correction reduces to the closed form
+    s - sigma mu s^{-1}, the Jordan inverse being J s / (s_0^2 - |s_1|^2) for a SOC
+    and S^{-1} for a PSD cone."""
+    rng = np.random.default_rng(60 + d)
+    smu = 0.4
+    for _ in range(4):
+        v = _soc_pt(rng, d) if t == C.SOC else _psd_pt(rng, C.psd_order(d))
+        sc = C.nt_scaling(t, v, v)
+        np.testing.assert_allclose(sc["H"], np.eye(d), atol=1e-12)
+        lam = C.lam_vec(t, sc["lam"], d)
+        w = C.jordan_prod(t, lam, lam) - smu * C.identity(t, d)
+        d_s = C.apply_scaling(t, sc, "WT", C.jordan_div(t, sc["lam"], w))
+        if t == C.SOC:
+            inv = np.r_[v[0], -v[1:]] / (v[0] ** 2 - v[1:] @ v[1:])
+        else:
+            inv = C.svec(np.linalg.inv(C.smat(v)))
+        np.testing.assert_allclose(d_s, v - smu * inv, rtol=1e-11, atol=1e-12)
+
+
 def test_svec_is_an_isometry():
     X, Y = C.smat(_psd_pt(RNG, 4)), C.smat(_psd_pt(RNG, 4))
     assert C.svec(X) @ C.svec(Y) == pytest.approx(np.trace(X @ Y), rel=1e-13)
