@@ -9,7 +9,10 @@
 #include <algorithm>
 #include <cstdio>
 #include <numeric>
+#include <exception>
 #include <queue>
+#include <system_error>
+#include <thread>
 
 #include "internal.h"
 #include "symbolic.h"
@@ -174,83 +177,122 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
   const int64_t n = hp.n, m = hp.m, N = n + m;
   std::vector<int64_t> aptr, aidx;
   build_adjacency(N, hp.kcol_ptr, hp.krow, aptr, aidx);
-  amd_order(N, aptr, aidx, order, n_dense);
   *which = 0;
   const int64_t mz = hp.cl.m_zero, ab = hp.cl.n_aux ? hp.cl.aux_begin : m, na = hp.cl.n_aux;
-  if (ab - mz <= 0 || n == 0) return CLR_OK;
-  // Schur pattern on R = x u zero rows u auxiliary rows (local ids: x j -> j, zero
-  // row r -> n + r, auxiliary row r -> n + mz + (r - ab))
-  const int64_t R = n + mz + na;
-  auto local = [&](int64_t u) -> int64_t {
-    if (u < n || u - n < mz) return u;
-    return (u - n >= ab) ? n + mz + (u - n - ab) : -1;
+  if (ab - mz <= 0 || n == 0) {
+    amd_order(N, aptr, aidx, order, n_dense);
+    return CLR_OK;
+  }
+  // candidate 0 (AMD on the whole pattern and its flop count) on a second thread
+  // while candidate 1 is built here; the two only read the shared adjacency, so
+  // the result is the one a sequential run gives
+  int64_t nz0 = 0;
+  double f0 = 0;
+  std::exception_ptr err0;
+  auto cand0 = [&] {
+    try {
+      amd_order(N, aptr, aidx, order, n_dense);
+      factor_counts(N, aptr, aidx, order, &nz0, &f0);
+    } catch (...) {
+      err0 = std::current_exception();
+    }
   };
-  std::vector<std::vector<int64_t>> adj(R);
-  for (int64_t u = 0; u < N; ++u) {
-    const int64_t lu = local(u);
-    if (lu < 0) continue;
-    for (int64_t p = aptr[u]; p < aptr[u + 1]; ++p) {
-      const int64_t lv = local(aidx[p]);
-      if (lv >= 0) adj[lu].push_back(lv);
+  std::thread th;
+  try {
+    th = std::thread(cand0);
+  } catch (const std::system_error&) {
+    cand0();  // no thread to be had: in turn
+  }
+  struct Join {  // candidate 0 finishes before this function returns or throws
+    std::thread& t;
+    ~Join() {
+      if (t.joinable()) t.join();
     }
-  }
-  // one clique per H block over its x neighbours
-  int64_t pairs = 0;
-  const int64_t pair_cap = 64 * (int64_t)aidx.size() + 50'000'000;
-  std::vector<int64_t> nb;
-  std::vector<int64_t> mark(n, -1);
-  for (size_t ci = 0; ci < hp.cl.cones.size(); ++ci) {
-    const Cone& c = hp.cl.cones[ci];
-    if (c.type == CLR_ZERO) continue;
-    // each nonneg row, and each row of an expanded SOC, is its own 1x1 block
-    const bool rowwise = c.type == CLR_NONNEG || c.aux >= 0;
-    const int64_t nblk = rowwise ? c.dim : 1, bdim = rowwise ? 1 : c.dim;
-    for (int64_t bk = 0; bk < nblk; ++bk) {
-      nb.clear();
-      if (c.aux >= 0) {  // the block's two auxiliary rows join its clique
-        nb.push_back(n + mz + (c.aux - ab));
-        nb.push_back(n + mz + (c.aux + 1 - ab));
-      }
-      const int64_t tag = (int64_t)ci * (1LL << 32) + bk;
-      for (int64_t r = c.off + bk * bdim; r < c.off + (bk + 1) * bdim; ++r)
-        for (int64_t p = hp.A.ptr[r]; p < hp.A.ptr[r + 1]; ++p) {
-          const int64_t j = hp.A.idx[p];
-          if (mark[j] != tag) {
-            mark[j] = tag;
-            nb.push_back(j);
-          }
-        }
-      pairs += (int64_t)nb.size() * (int64_t)nb.size();
-      if (pairs > pair_cap) return CLR_OK;  // too dense to be worth it
-      for (int64_t a : nb)
-        for (int64_t b2 : nb)
-          if (a != b2) adj[a].push_back(b2);
-    }
-  }
-  std::vector<int64_t> sptr(R + 1, 0), sidx;
-  for (int64_t u = 0; u < R; ++u) {
-    std::vector<int64_t>& a = adj[u];
-    std::sort(a.begin(), a.end());
-    a.erase(std::unique(a.begin(), a.end()), a.end());
-    sptr[u + 1] = sptr[u] + (int64_t)a.size();
-  }
-  sidx.reserve(sptr[R]);
-  for (int64_t u = 0; u < R; ++u) {
-    sidx.insert(sidx.end(), adj[u].begin(), adj[u].end());
-    std::vector<int64_t>().swap(adj[u]);
-  }
-  std::vector<int64_t> rperm;
-  int64_t nd1 = 0;
-  amd_order(R, sptr, sidx, rperm, nd1);
+  } join{th};
   std::vector<int64_t> cand;
-  cand.reserve(N);
-  for (int64_t r = mz; r < ab; ++r) cand.push_back(n + r);
-  for (int64_t v : rperm) cand.push_back(v < n + mz ? v : n + ab + (v - n - mz));  // local ids -> KKT indices
-  int64_t nz0 = 0, nz1 = 0;
-  double f0 = 0, f1 = 0;
-  factor_counts(N, aptr, aidx, order, &nz0, &f0);
-  factor_counts(N, aptr, aidx, cand, &nz1, &f1);
-  if (f1 < f0) {
+  int64_t nd1 = 0;
+  bool have1 = false;
+  {
+    // Schur pattern on R = x u zero rows u auxiliary rows (local ids: x j -> j, zero
+    // row r -> n + r, auxiliary row r -> n + mz + (r - ab))
+    const int64_t R = n + mz + na;
+    auto local = [&](int64_t u) -> int64_t {
+      if (u < n || u - n < mz) return u;
+      return (u - n >= ab) ? n + mz + (u - n - ab) : -1;
+    };
+    std::vector<std::vector<int64_t>> adj(R);
+    for (int64_t u = 0; u < N; ++u) {
+      const int64_t lu = local(u);
+      if (lu < 0) continue;
+      for (int64_t p = aptr[u]; p < aptr[u + 1]; ++p) {
+        const int64_t lv = local(aidx[p]);
+        if (lv >= 0) adj[lu].push_back(lv);
+      }
+    }
+    // one clique per H block over its x neighbours
+    int64_t pairs = 0;
+    const int64_t pair_cap = 64 * (int64_t)aidx.size() + 50'000'000;
+    bool dense = false;
+    std::vector<int64_t> nb;
+    std::vector<int64_t> mark(n, -1);
+    for (size_t ci = 0; ci < hp.cl.cones.size() && !dense; ++ci) {
+      const Cone& c = hp.cl.cones[ci];
+      if (c.type == CLR_ZERO) continue;
+      // each nonneg row, and each row of an expanded SOC, is its own 1x1 block
+      const bool rowwise = c.type == CLR_NONNEG || c.aux >= 0;
+      const int64_t nblk = rowwise ? c.dim : 1, bdim = rowwise ? 1 : c.dim;
+      for (int64_t bk = 0; bk < nblk; ++bk) {
+        nb.clear();
+        if (c.aux >= 0) {  // the block's two auxiliary rows join its clique
+          nb.push_back(n + mz + (c.aux - ab));
+          nb.push_back(n + mz + (c.aux + 1 - ab));
+        }
+        const int64_t tag = (int64_t)ci * (1LL << 32) + bk;
+        for (int64_t r = c.off + bk * bdim; r < c.off + (bk + 1) * bdim; ++r)
+          for (int64_t p = hp.A.ptr[r]; p < hp.A.ptr[r + 1]; ++p) {
+            const int64_t j = hp.A.idx[p];
+            if (mark[j] != tag) {
+              mark[j] = tag;
+              nb.push_back(j);
+            }
+          }
+        pairs += (int64_t)nb.size() * (int64_t)nb.size();
+        if (pairs > pair_cap) {  // too dense to be worth it
+          dense = true;
+          break;
+        }
+        for (int64_t a : nb)
+          for (int64_t b2 : nb)
+            if (a != b2) adj[a].push_back(b2);
+      }
+    }
+    if (!dense) {
+      std::vector<int64_t> sptr(R + 1, 0), sidx;
+      for (int64_t u = 0; u < R; ++u) {
+        std::vector<int64_t>& a = adj[u];
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+        sptr[u + 1] = sptr[u] + (int64_t)a.size();
+      }
+      sidx.reserve(sptr[R]);
+      for (int64_t u = 0; u < R; ++u) {
+        sidx.insert(sidx.end(), adj[u].begin(), adj[u].end());
+        std::vector<int64_t>().swap(adj[u]);
+      }
+      std::vector<int64_t> rperm;
+      amd_order(R, sptr, sidx, rperm, nd1);
+      cand.reserve(N);
+      for (int64_t r = mz; r < ab; ++r) cand.push_back(n + r);
+      for (int64_t v : rperm) cand.push_back(v < n + mz ? v : n + ab + (v - n - mz));  // local ids -> KKT indices
+      have1 = true;
+    }
+  }
+  int64_t nz1 = 0;
+  double f1 = 0;
+  if (have1) factor_counts(N, aptr, aidx, cand, &nz1, &f1);
+  if (th.joinable()) th.join();
+  if (err0) std::rethrow_exception(err0);
+  if (have1 && f1 < f0) {
     order.swap(cand);
     n_dense = nd1;
     *which = 1;
