@@ -9,7 +9,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <numeric>
+#include <atomic>
 #include <exception>
+#include <mutex>
 #include <queue>
 #include <system_error>
 #include <thread>
@@ -615,6 +617,53 @@ int symbolic_analyze(int64_t N, const std::vector<int64_t>& colptr, const std::v
   return CLR_OK;
 }
 
+namespace {
+// fronts whose children contribute at least this many entries build their lists on
+// several host threads
+constexpr int64_t kParallelEntries = (int64_t)1 << 22;
+
+int host_threads() {
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h, 8u));
+}
+
+// fn(block, scratch) for blocks 0 .. nblk-1 on nthr threads (blocks handed out by a
+// counter), each thread with its own scratch of the given size; the first exception
+// is rethrown after all threads are done.
+template <class F>
+void for_blocks(int64_t nblk, int nthr, int64_t scratch, F&& fn) {
+  if (nthr <= 1) {
+    std::vector<int64_t> w((size_t)scratch);
+    for (int64_t bk = 0; bk < nblk; ++bk) fn(bk, w);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  auto body = [&] {
+    try {
+      std::vector<int64_t> w((size_t)scratch);
+      for (int64_t bk; (bk = next.fetch_add(1)) < nblk;) fn(bk, w);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!err) err = std::current_exception();
+      next.store(nblk);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthr; ++t) {
+    try {
+      th.emplace_back(body);
+    } catch (const std::system_error&) {
+      break;  // fewer threads
+    }
+  }
+  body();
+  for (std::thread& t : th) t.join();
+  if (err) std::rethrow_exception(err);
+}
+}  // namespace
+
 // Index maps for the numeric phase.
 void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr, const std::vector<int64_t>& krow,
                         NumericMaps& mp, bool direct) {
@@ -681,7 +730,7 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
     pushed[P] = std::move(big);
   }
   std::vector<std::pair<int64_t, int64_t>> contrib, ctmp;  // (target, source)
-  std::vector<int64_t> cnt, tcount;
+  std::vector<int64_t> cnt;
   // fronts up to this many entries get their pull lists by direct placement
   constexpr int64_t kDirectTargets = (int64_t)1 << 26;
   // counting pass: stable reorder of v by key(target) in [0, nb)
@@ -752,43 +801,64 @@ void build_numeric_maps(const Symbolic& sy, const std::vector<int64_t>& kcol_ptr
         // the sorted pairs below give them.  Done per block of kColBlock parent
         // columns (targets are column-major, so the blocks come in target order and
         // a target's sources all fall in its block), which keeps the counts and the
-        // block's slice of the lists in cache.
+        // block's slice of the lists in cache; the blocks are independent, so large
+        // fronts count and place them on several host threads (the lists do not
+        // depend on how the blocks are shared out).
         constexpr int64_t kColBlock = 16;
-        std::vector<int64_t>& cntT = tcount;
-        cntT.assign((size_t)(kColBlock * fP), 0);
-        int64_t pos = (int64_t)mp.fa_src.size();
-        for (int64_t c0 = 0; c0 < fP; c0 += kColBlock) {
-          const int64_t c1 = std::min(fP, c0 + kColBlock);
-          // the update columns b of each child whose parent column loc[rr[b]] lies in
-          // [c0, c1): loc is increasing along a child's rows, so a contiguous range
-          auto each = [&](auto&& fn) {
-            for (int64_t ch : children[P]) {
-              if (is_pushed[ch]) continue;
-              const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
-              const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
-              const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
-              const int64_t* lo = std::partition_point(rr + c, rr + f, [&](int64_t r) { return loc[r] < c0; });
-              const int64_t* hi = std::partition_point(lo, rr + f, [&](int64_t r) { return loc[r] < c1; });
-              for (int64_t b = lo - rr; b < hi - rr; ++b) {
-                const int64_t lb = loc[rr[b]] - c0;
-                for (int64_t a = b; a < f; ++a) fn(loc[rr[a]] + lb * fP, sy.front_off[ch] + a + b * f);
-              }
+        const int64_t nblk = (fP + kColBlock - 1) / kColBlock;
+        // the update columns b of each child whose parent column loc[rr[b]] lies in
+        // [c0, c1): loc is increasing along a child's rows, so a contiguous range
+        auto each_in = [&](int64_t c0, int64_t c1, auto&& fn) {
+          for (int64_t ch : children[P]) {
+            if (is_pushed[ch]) continue;
+            const int64_t f = sy.row_ptr[ch + 1] - sy.row_ptr[ch];
+            const int64_t c = sy.sn_ptr[ch + 1] - sy.sn_ptr[ch];
+            const int64_t* rr = sy.rows.data() + sy.row_ptr[ch];
+            const int64_t* lo = std::partition_point(rr + c, rr + f, [&](int64_t r) { return loc[r] < c0; });
+            const int64_t* hi = std::partition_point(lo, rr + f, [&](int64_t r) { return loc[r] < c1; });
+            for (int64_t b = lo - rr; b < hi - rr; ++b) {
+              const int64_t lb = loc[rr[b]] - c0;
+              for (int64_t a = b; a < f; ++a) fn(loc[rr[a]] + lb * fP, sy.front_off[ch] + a + b * f);
             }
-          };
-          const int64_t nb = (c1 - c0) * fP;
-          std::fill(cntT.begin(), cntT.begin() + nb, 0);
-          each([&](int64_t t, int64_t) { ++cntT[t]; });
-          for (int64_t t = 0; t < nb; ++t) {
-            if (!cntT[t]) continue;
-            mp.fa_tgt.push_back(sy.front_off[P] + c0 * fP + t);
-            mp.fa_ptr.push_back(pos);
-            const int64_t k = cntT[t];
-            cntT[t] = pos;
-            pos += k;
           }
-          mp.fa_src.resize(pos);
-          each([&](int64_t t, int64_t src) { mp.fa_src[cntT[t]++] = src; });
+        };
+        // per block: its targets that have sources (block-local index) and their counts
+        std::vector<std::vector<int32_t>> btgt(nblk);
+        std::vector<std::vector<int64_t>> bcnt(nblk);
+        std::vector<int64_t> bstart(nblk);
+        const int nthr = ne >= kParallelEntries ? std::min<int>(host_threads(), (int)nblk) : 1;
+        for_blocks(nblk, nthr, kColBlock * fP, [&](int64_t bk, std::vector<int64_t>& cnt) {
+          const int64_t c0 = bk * kColBlock, c1 = std::min(fP, c0 + kColBlock), nb = (c1 - c0) * fP;
+          std::fill(cnt.begin(), cnt.begin() + nb, 0);
+          each_in(c0, c1, [&](int64_t t, int64_t) { ++cnt[t]; });
+          for (int64_t t = 0; t < nb; ++t)
+            if (cnt[t]) {
+              btgt[bk].push_back((int32_t)t);
+              bcnt[bk].push_back(cnt[t]);
+            }
+        });
+        int64_t pos = (int64_t)mp.fa_src.size();
+        for (int64_t bk = 0; bk < nblk; ++bk) {
+          bstart[bk] = pos;
+          for (size_t q = 0; q < btgt[bk].size(); ++q) {
+            mp.fa_tgt.push_back(sy.front_off[P] + bk * kColBlock * fP + btgt[bk][q]);
+            mp.fa_ptr.push_back(pos);
+            pos += bcnt[bk][q];
+          }
         }
+        mp.fa_src.resize(pos);
+        for_blocks(nblk, nthr, kColBlock * fP, [&](int64_t bk, std::vector<int64_t>& slot) {
+          const int64_t c0 = bk * kColBlock, c1 = std::min(fP, c0 + kColBlock);
+          int64_t p = bstart[bk];
+          for (size_t q = 0; q < btgt[bk].size(); ++q) {
+            slot[btgt[bk][q]] = p;
+            p += bcnt[bk][q];
+          }
+          int64_t* out = mp.fa_src.data();
+          each_in(c0, c1, [&](int64_t t, int64_t src) { out[slot[t]++] = src; });
+          std::vector<int32_t>().swap(btgt[bk]);
+          std::vector<int64_t>().swap(bcnt[bk]);
+        });
       } else if (ne > 0) {
         contrib.clear();
         contrib.reserve(ne);
