@@ -186,8 +186,9 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
     return CLR_OK;
   }
   // candidate 0 (AMD on the whole pattern and its flop count) on a second thread
-  // while candidate 1 is built here; the two only read the shared adjacency, so
-  // the result is the one a sequential run gives
+  // while candidate 1 is built here, for patterns large enough to repay the thread;
+  // the two only read the shared adjacency, so the result is the one a sequential
+  // run gives
   int64_t nz0 = 0;
   double f0 = 0;
   std::exception_ptr err0;
@@ -200,10 +201,14 @@ int choose_kkt_order(const HostProblem& hp, std::vector<int64_t>& order, int64_t
     }
   };
   std::thread th;
-  try {
-    th = std::thread(cand0);
-  } catch (const std::system_error&) {
-    cand0();  // no thread to be had: in turn
+  if ((int64_t)aidx.size() >= ((int64_t)1 << 20)) {
+    try {
+      th = std::thread(cand0);
+    } catch (const std::system_error&) {
+      cand0();  // no thread to be had: in turn
+    }
+  } else {
+    cand0();
   }
   struct Join {  // candidate 0 finishes before this function returns or throws
     std::thread& t;
