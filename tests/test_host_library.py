@@ -341,3 +341,18 @@ def test_pull_lists_direct_and_sorted_agree(clr):
     with pytest.raises(RuntimeError):
         clr.clr_analyze(probs[0].P, probs[0].q, probs[0].A, probs[0].b, probs[0].cones,
                         clr.clr_default_settings(64, pull_lists_direct=2))
+
+
+def test_threaded_analysis_is_deterministic(clr):
+    """A pattern large enough for the threaded host analysis (the two ordering
+    candidates on two threads, a front's lists over several threads): repeated
+    analyses give the same order and maps, and the sorted lists agree with them."""
+    p = W.huber_qp(0, n=1800)
+    d = []
+    for direct in (1, 1, 0):
+        s = clr.clr_analyze(p.P, p.q, p.A, p.b, p.cones, clr.clr_default_settings(64, pull_lists_direct=direct))
+        st = s.symbolic_stats()
+        assert 2 * st["kkt_nnz_lower"] >= 1 << 20  # the threaded ordering path
+        d.append(st["maps_digest"])
+        s.free()
+    assert d[0] == d[1] == d[2]
